@@ -1,0 +1,217 @@
+"""Oracle closures: equations of state, mixture rules, strain and stress.
+
+TEST INFRASTRUCTURE ONLY.  Plain PyTorch CPU float64, written for reading
+against the paper, not for speed.  Nothing in the product path imports it.
+
+Cites (Wallis, Barton & Nikiforakis, arXiv 2009.14555):
+  * Section 2.2, Eqs. for E_s, J^2, sigma, p, dev(sigma) and the mixture rules
+    (phi, rho, rho*E, G, c^2, sigma weighted by phi/Gamma);
+  * Section 2.3, Mie-Grueneisen form p = p_ref + rho*Gamma*(E - E_ref) with the
+    stiffened-gas reference curves;
+  * Section 2.3.1, reactive physical mixture (lambda, Q shift of the product
+    reference energy, MiNi16 mixture sound speed);
+  * Section 3.2, Bazant approximation of the Hencky strain;
+  * Appendix B, pressure function and temperature.
+
+Readings taken where the paper is silent or garbled:
+  * sigma = -p I + dev(sigma) (the flux rho u u - sigma needs the minus sign);
+  * E = e + |u|^2 / 2;
+  * stiffened-gas solid with constant shear modulus G: the shear energy
+    G J^2 / rho enters E_ref, so p_ref = -gamma p_inf - G J^2 and
+    E_ref = e_inf + G J^2 / rho;
+  * mixture sound speed c^2 = sum(Y_l c_l^2 / Gamma_l) / sum(phi_l / Gamma_l)
+    (the printed numerator carries a spurious extra phi);
+  * dev(H) is taken as dev(1/4 (B - B^-1)) with B = V V^T (explicit deviator);
+  * a reactive material has identical ideal-gas reactant and product closures
+    (same gamma and C_V), so the temperature equality of Appendix B gives
+    rho_alpha = rho_beta = rho_y and the pressure function is closed form.
+"""
+from __future__ import annotations
+
+import torch
+
+F64 = torch.float64
+
+
+def Gamma(m) -> float:
+    """Grueneisen coefficient Gamma = gamma - 1 (Section 2.3, ideal/stiffened gas)."""
+    return m["gamma"] - 1.0
+
+
+# ----------------------------------------------------------------------------
+# Strain: Section 2.2 (J^2) and Section 3.2 (Bazant approximation).
+# ----------------------------------------------------------------------------
+def stretch_matrix(V11, V12, V21, V22, V33):
+    """Assemble the 3x3 stretch tensor of plane strain (z rows/cols diagonal)."""
+    z = torch.zeros_like(V11)
+    rows = [torch.stack([V11, V12, z], -1),
+            torch.stack([V21, V22, z], -1),
+            torch.stack([z, z, V33], -1)]
+    return torch.stack(rows, -2)
+
+
+def dev(M):
+    """Matrix deviator dev(M) = M - tr(M)/3 I (footnote of Section 2.2)."""
+    tr = torch.diagonal(M, dim1=-2, dim2=-1).sum(-1)
+    eye = torch.eye(3, dtype=M.dtype).expand(M.shape)
+    return M - (tr / 3.0)[..., None, None] * eye
+
+
+def hencky_dev(V):
+    """dev(H) ~ 1/2 H_B^(1)(V V^T),  H_B^(m)(X) = (X^m - X^-m) / (2m)  (Section 3.2).
+
+    Returns (devH, J2) with J2 = tr(devH devH^T) (Section 2.2).
+    """
+    B = V @ V.transpose(-1, -2)
+    HB1 = 0.5 * (B - torch.linalg.inv(B))
+    devH = dev(0.5 * HB1)
+    J2 = (devH * devH).sum((-1, -2))
+    return devH, J2
+
+
+# ----------------------------------------------------------------------------
+# Reference curves of the Mie-Grueneisen form (Section 2.3, reading above).
+# ----------------------------------------------------------------------------
+def p_ref(m, rho, J2):
+    return -m["gamma"] * m["p_inf"] - m["G"] * J2
+
+
+def e_ref(m, rho, J2):
+    return m["e_inf"] + m["G"] * J2 / rho
+
+
+def dp_ref_drho(m, rho, J2):
+    return torch.zeros_like(rho)
+
+
+def de_ref_drho(m, rho, J2):
+    return -m["G"] * J2 / (rho * rho)
+
+
+def material_energy(m, rho, p, J2, lam=None):
+    """Specific internal energy of one material from the MG form (Section 2.3).
+
+    For a reactive material, E = lam E_alpha + (1 - lam) E_beta with the product
+    reference energy shifted by -Q (Section 2.3.1) and rho_alpha = rho_beta = rho.
+    """
+    G = Gamma(m)
+    if m["reactive"]:
+        e_a = (p - p_ref(m, rho, J2)) / (rho * G) + e_ref(m, rho, J2)
+        e_b = (p - p_ref(m, rho, J2)) / (rho * G) + e_ref(m, rho, J2) - m["Q"]
+        return lam * e_a + (1.0 - lam) * e_b
+    return (p - p_ref(m, rho, J2)) / (rho * G) + e_ref(m, rho, J2)
+
+
+def mixture_pressure(phis, rhos, rhoe, J2, mats, lam=None):
+    """Pressure function of Appendix B (all materials at one pressure).
+
+    p = [rho e + sum_x phi_x rho_x (p_ref,x/(rho_x Gamma_x) - E_ref,x)
+               + phi_y rho_y lam (p_ref,a/(rho_a Gamma_a) - E_ref,a)
+               + phi_y rho_y (1-lam) (p_ref,b/(rho_b Gamma_b) - E_ref,b)]
+        / [sum_x phi_x/Gamma_x + phi_y rho_y lam/(rho_a Gamma_a)
+                               + phi_y rho_y (1-lam)/(rho_b Gamma_b)]
+    """
+    num = rhoe.clone()
+    den = torch.zeros_like(rhoe)
+    for m, phi, rho in zip(mats, phis, rhos):
+        G = Gamma(m)
+        if m["reactive"]:
+            ra = rb = rho  # temperature equality with equal Gamma, C_V
+            num = num + phi * rho * lam * (p_ref(m, ra, J2) / (ra * G) - e_ref(m, ra, J2))
+            num = num + phi * rho * (1 - lam) * (p_ref(m, rb, J2) / (rb * G)
+                                                 - (e_ref(m, rb, J2) - m["Q"]))
+            den = den + phi * rho * lam / (ra * G) + phi * rho * (1 - lam) / (rb * G)
+        else:
+            num = num + phi * rho * (p_ref(m, rho, J2) / (rho * G) - e_ref(m, rho, J2))
+            den = den + phi / G
+    return num / den
+
+
+def material_sound_speed2(m, rho, p, J2, lam=None):
+    """Squared sound speed of one material at fixed strain.
+
+    Inert material: c^2 = (dp/drho)_E + p/rho^2 (dp/dE)_rho of the MG form.
+    Reactive mixture: MiNi16 form of Section 2.3.1,
+      c^2 = [p/rho^2 - (dE/drho)_p] / (dE/dp)_rho,
+    with rho_alpha = rho_beta = rho so (d rho_alpha/d rho)_p = 1.
+    """
+    G = Gamma(m)
+    if m["reactive"]:
+        dEdp = lam / (rho * G) + (1 - lam) / (rho * G)
+        # (dE_k/drho_k)_p for the MG form: -(p - p_ref)/(rho^2 G) + dp_ref/drho/(... ) terms
+        dEa = (-(p - p_ref(m, rho, J2)) / (rho * rho * G)
+               - dp_ref_drho(m, rho, J2) / (rho * G) + de_ref_drho(m, rho, J2))
+        dEb = dEa
+        dEdrho = lam * dEa * 1.0 + (1 - lam) * dEb * 1.0
+        return (p / (rho * rho) - dEdrho) / dEdp
+    dpdrho = dp_ref_drho(m, rho, J2) + (p - p_ref(m, rho, J2)) / rho - rho * G * de_ref_drho(m, rho, J2)
+    dpde = rho * G
+    return dpdrho + p / (rho * rho) * dpde
+
+
+def temperature(m, rho, p, J2):
+    """T = (p - p_ref) / (rho Gamma C_V)  (Appendix B)."""
+    return (p - p_ref(m, rho, J2)) / (rho * Gamma(m) * m["cv"])
+
+
+# ----------------------------------------------------------------------------
+# Whole-state closures.  A state is a dict of tensors:
+#   phi1, rho1, rho2, u (...,3), p, V (...,3,3), lam      (primitive)
+#   phi1, ar1, ar2, mom (...,3), E, V (...,3,3), arl      (conservative)
+# ----------------------------------------------------------------------------
+def phases(phi1):
+    return [phi1, 1.0 - phi1]  # Eq. sum phi = 1 (Section 2.2)
+
+
+def mixture_props(phis, rhos, p, J2, mats, lam):
+    """Mixture G, c^2 and longitudinal c_L^2 (Section 2.2 mixture rules)."""
+    rho = sum(ph * r for ph, r in zip(phis, rhos))
+    xi = sum(ph / Gamma(m) for ph, m in zip(phis, mats))
+    Gm = sum(ph * m["G"] / Gamma(m) for ph, m in zip(phis, mats)) / xi
+    c2 = sum((ph * r / rho) * material_sound_speed2(m, r, p, J2, lam) / Gamma(m)
+             for ph, r, m in zip(phis, rhos, mats)) / xi
+    cL2 = c2 + (4.0 / 3.0) * Gm / rho
+    return rho, Gm, c2, cL2
+
+
+def stress(p, Gm, devH):
+    """sigma = -p I + 2 G devH (Section 2.2, sign reading above)."""
+    eye = torch.eye(3, dtype=p.dtype).expand(devH.shape)
+    return -p[..., None, None] * eye + 2.0 * Gm[..., None, None] * devH
+
+
+def prim_to_cons(w, mats):
+    """Conservative state from primitives (MG form solved for E, mixture rules)."""
+    phis = phases(w["phi1"])
+    rhos = [w["rho1"], w["rho2"]]
+    devH, J2 = hencky_dev(w["V"])
+    rho = phis[0] * rhos[0] + phis[1] * rhos[1]
+    rhoe = sum(ph * r * material_energy(m, r, w["p"], J2, w.get("lam"))
+               for ph, r, m in zip(phis, rhos, mats))
+    ke = 0.5 * rho * (w["u"] * w["u"]).sum(-1)
+    q = dict(phi1=w["phi1"], ar1=phis[0] * rhos[0], ar2=phis[1] * rhos[1],
+             mom=rho[..., None] * w["u"], E=rhoe + ke, V=w["V"])
+    if "lam" in w:
+        y = next(i for i, m in enumerate(mats) if m["reactive"])
+        q["arl"] = q["ar1" if y == 0 else "ar2"] * w["lam"]
+    return q
+
+
+def cons_to_prim(q, mats):
+    """Primitives from the conservative state (pressure function of Appendix B)."""
+    phis = phases(q["phi1"])
+    ars = [q["ar1"], q["ar2"]]
+    rhos = [ars[0] / phis[0], ars[1] / phis[1]]
+    rho = ars[0] + ars[1]
+    u = q["mom"] / rho[..., None]
+    rhoe = q["E"] - 0.5 * rho * (u * u).sum(-1)
+    devH, J2 = hencky_dev(q["V"])
+    lam = None
+    if "arl" in q:
+        y = next(i for i, m in enumerate(mats) if m["reactive"])
+        lam = q["arl"] / ars[y]
+    p = mixture_pressure(phis, rhos, rhoe, J2, mats, lam)
+    w = dict(phi1=q["phi1"], rho1=rhos[0], rho2=rhos[1], u=u, p=p, V=q["V"])
+    if lam is not None:
+        w["lam"] = lam
+    return w

@@ -1,0 +1,273 @@
+"""Seeded synthetic workloads shaped like the paper's problems.
+
+This module only lays out geometry, material parameter sets and seeded random
+draws.  It holds none of the scheme's arithmetic: no equation of state, no
+conversion from primitive to conservative variables, no flux.  Both the oracle
+(`oracle/`) and the CUDA path read the *primitive* fields it produces and each
+converts them with its own closure code.
+
+Primitive field layout (per cell), matching the state vector of Section 3
+(vector form of the system) with two materials, material 1 being the one whose
+volume fraction is stored:
+
+    1D : phi1, rho1, rho2, u, p, V11, V22, V33, [lam]
+    2D : phi1, rho1, rho2, u, v, p, V11, V12, V21, V22, V33, [lam]
+
+`lam` is the reaction progress variable of the reactive material (1 = reactant,
+0 = products, Section 2.3.1) and is present only when a material is reactive.
+Arrays are float64 with shape (nfields, ny, nx) (ny = 1 in 1D).
+
+Materials are plain dicts with the keys
+    gamma, p_inf, e_inf, G, plastic (0 none, 1 perfect, 2 rate), sigma_y, chi0,
+    reactive (0/1), Q, cv, A, T_act
+(stiffened-gas Mie-Grueneisen closures, Section 2.3; perfect plasticity is the
+chi0 -> infinity limit of the ideal-plasticity rate, Section 2.3.2; the
+Arrhenius rate parameters A, T_act only apply to a reactive material).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+EPS_PHI = 1e-8  # volume fraction given to the absent material in a pure cell
+
+BC_TRANSMISSIVE, BC_PERIODIC, BC_REFLECTIVE = 0, 1, 2
+
+PRIM_1D = ["phi1", "rho1", "rho2", "u", "p", "V11", "V22", "V33"]
+PRIM_2D = ["phi1", "rho1", "rho2", "u", "v", "p", "V11", "V12", "V21", "V22", "V33"]
+CONS_1D = ["phi1", "ar1", "ar2", "mx", "E", "V11", "V22", "V33"]
+CONS_2D = ["phi1", "ar1", "ar2", "mx", "my", "E", "V11", "V12", "V21", "V22", "V33"]
+
+
+def prim_names(dim: int, reactive: bool) -> list[str]:
+    base = PRIM_1D if dim == 1 else PRIM_2D
+    return base + (["lam"] if reactive else [])
+
+
+def cons_names(dim: int, reactive: bool) -> list[str]:
+    base = CONS_1D if dim == 1 else CONS_2D
+    return base + (["arl"] if reactive else [])
+
+
+def material(gamma, p_inf=0.0, e_inf=0.0, G=0.0, plastic=0, sigma_y=0.0, chi0=0.0,
+             reactive=0, Q=0.0, cv=0.0, A=0.0, T_act=0.0) -> dict:
+    return dict(gamma=float(gamma), p_inf=float(p_inf), e_inf=float(e_inf), G=float(G),
+                plastic=int(plastic), sigma_y=float(sigma_y), chi0=float(chi0),
+                reactive=int(reactive), Q=float(Q), cv=float(cv), A=float(A),
+                T_act=float(T_act))
+
+
+# Solid of the 1D solid|gas problem: stiffened-gas-form hydrostatic EOS,
+# constant shear modulus, perfect plasticity with radial return.
+SOLID = material(4.0, p_inf=6e10, G=5e10, plastic=1, sigma_y=4e8)
+SOLID_RHO0 = 8000.0
+AIR = material(1.4)
+R_AIR = 287.0
+
+
+@dataclass
+class Patch:
+    nx: int
+    ny: int
+    dx: float
+    dy: float
+    x0: float = 0.0
+    y0: float = 0.0
+    bc: tuple = (BC_TRANSMISSIVE,) * 4  # x-low, x-high, y-low, y-high
+    prim: np.ndarray | None = None       # (nfields, ny, nx) float64
+
+
+@dataclass
+class Workload:
+    name: str
+    dim: int
+    materials: list
+    patches: list
+    cfl: float
+    steps: int
+    thinc: bool
+    reactive_material: int = -1          # 0-based index of the reactive material, -1 none
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def reactive(self) -> bool:
+        return self.reactive_material >= 0
+
+    @property
+    def cells(self) -> int:
+        return sum(p.nx * p.ny for p in self.patches)
+
+
+def _blank(dim, reactive, ny, nx):
+    names = prim_names(dim, reactive)
+    w = np.zeros((len(names), ny, nx))
+    idx = {n: k for k, n in enumerate(names)}
+    for n in ("V11", "V22", "V33"):
+        w[idx[n]] = 1.0
+    if reactive:
+        w[idx["lam"]] = 1.0
+    return w, idx
+
+
+def _area_fraction_disc(xc, yc, r, x0, y0, dx, dy, nx, ny, sub=8):
+    """Fraction of each cell inside a disc, by sub x sub point sampling."""
+    off = (np.arange(sub) + 0.5) / sub
+    xs = x0 + (np.arange(nx)[:, None] + off[None, :]) * dx   # (nx, sub)
+    ys = y0 + (np.arange(ny)[:, None] + off[None, :]) * dy   # (ny, sub)
+    dxs = (xs - xc) ** 2
+    dys = (ys - yc) ** 2
+    inside = (dys[:, None, :, None] + dxs[None, :, None, :]) <= r * r  # ny,nx,sub,sub
+    return inside.mean(axis=(2, 3))
+
+
+def riemann_1d(n: int = 1000, left=None, right=None, x_int: float = 0.5,
+               cfl: float = 0.8, steps: int = 500, thinc: bool = False,
+               bc=BC_TRANSMISSIVE, materials=None, name="riemann_1d") -> Workload:
+    """Two-material 1D Riemann problem on [0, 1].
+
+    `left`/`right` are dicts with keys mat (0 = material 1, 1 = material 2),
+    rho, u, p.  Default: the 1D solid|gas impact (solid at 500 m/s into air).
+    """
+    left = left or dict(mat=0, rho=SOLID_RHO0, u=500.0, p=1e5)
+    right = right or dict(mat=1, rho=1.2, u=0.0, p=1e5)
+    mats = materials or [SOLID, AIR]
+    reactive = any(m["reactive"] for m in mats)
+    w, k = _blank(1, reactive, 1, n)
+    dx = 1.0 / n
+    xc = (np.arange(n) + 0.5) * dx
+    for side, mask in ((left, xc < x_int), (right, xc >= x_int)):
+        phi1 = 1.0 - EPS_PHI if side["mat"] == 0 else EPS_PHI
+        w[k["phi1"], 0, mask] = phi1
+        w[k["rho1"], 0, mask] = side.get("rho1", side["rho"])
+        w[k["rho2"], 0, mask] = side.get("rho2", side["rho"])
+        w[k["u"], 0, mask] = side["u"]
+        w[k["p"], 0, mask] = side["p"]
+    if left["mat"] == 0 and right["mat"] == 1 and "rho2" not in left:
+        # keep the absent phase at the density of the same material across the interface
+        w[k["rho2"], 0, xc < x_int] = right["rho"]
+        w[k["rho1"], 0, xc >= x_int] = left["rho"]
+    rmat = next((i for i, m in enumerate(mats) if m["reactive"]), -1)
+    p = Patch(nx=n, ny=1, dx=dx, dy=1.0, bc=(bc, bc, BC_TRANSMISSIVE, BC_TRANSMISSIVE), prim=w)
+    return Workload(name, 1, mats, [p], cfl, steps, thinc, rmat)
+
+
+def solid_gas_1d(n: int = 1000, steps: int = 500) -> Workload:
+    """1D solid|gas Riemann problem: 1000 cells, interface 0.5, CFL 0.8, 500 steps."""
+    return riemann_1d(n, steps=steps, name=f"1d_solid_gas_{n}")
+
+
+def mach2_shock_positions():
+    """Post-shock state of a Mach-2 shock in air (gamma 1.4) running into (1.2, 1e5, 0)."""
+    g, rho1, p1, M = 1.4, 1.2, 1e5, 2.0
+    c1 = math.sqrt(g * p1 / rho1)
+    rho2 = rho1 * (g + 1) * M * M / ((g - 1) * M * M + 2)
+    p2 = p1 * (1 + 2 * g / (g + 1) * (M * M - 1))
+    u2 = M * c1 * (1 - rho1 / rho2)
+    return rho2, p2, u2
+
+
+def shock_disc_2d(n: int = 512, steps: int = 2000, thinc: bool = True,
+                  shock_x: float = 0.25, name=None) -> Workload:
+    """Mach-2 air shock striking an elastoplastic disc (r 0.1 at (0.4, 0.5)) on [0,1]^2."""
+    w, k = _blank(2, False, n, n)
+    d = 1.0 / n
+    frac = _area_fraction_disc(0.4, 0.5, 0.1, 0.0, 0.0, d, d, n, n)
+    w[k["phi1"]] = EPS_PHI + (1 - 2 * EPS_PHI) * frac
+    w[k["rho1"]] = SOLID_RHO0
+    w[k["rho2"]] = 1.2
+    w[k["p"]] = 1e5
+    rho2, p2, u2 = mach2_shock_positions()
+    xc = (np.arange(n) + 0.5) * d
+    post = np.broadcast_to(xc[None, :] < shock_x, (n, n))
+    w[k["rho2"]][post] = rho2
+    w[k["p"]][post] = p2
+    w[k["u"]][post] = u2
+    p = Patch(nx=n, ny=n, dx=d, dy=d, prim=w)
+    return Workload(name or f"2d_shock_disc_{n}", 2, [SOLID, AIR], [p], 0.6, steps, thinc)
+
+
+def reactive_plate_2d(nx: int = 2048, ny: int = 1024, steps: int = 1000, seed: int = 2,
+                      A: float = 1.0e7, name=None) -> Workload:
+    """Premixed reactive air over an elastoplastic plate (y < 0.2) on [0,2]x[0,1].
+
+    Arrhenius single-step A -> B with T_act = 15 T0 and Q = 20 R T0, hot spot of
+    radius 0.02 at (1.0, 0.3) at 3 T0, density white noise of amplitude 1e-3.
+    """
+    rho0, p0, g = 1.2, 1e5, 1.4
+    T0 = p0 / (rho0 * R_AIR)
+    cv = R_AIR / (g - 1)
+    gas = material(g, reactive=1, Q=20 * R_AIR * T0, cv=cv, A=A, T_act=15 * T0)
+    w, k = _blank(2, True, ny, nx)
+    dx = 2.0 / nx
+    dy = 1.0 / ny
+    yc = (np.arange(ny) + 0.5) * dy
+    # exact fraction of each row below y = 0.2
+    ylo = np.arange(ny) * dy
+    frac = np.clip((0.2 - ylo) / dy, 0.0, 1.0)
+    w[k["phi1"]] = (EPS_PHI + (1 - 2 * EPS_PHI) * frac)[:, None]
+    w[k["rho1"]] = SOLID_RHO0
+    hot = _area_fraction_disc(1.0, 0.3, 0.02, 0.0, 0.0, dx, dy, nx, ny)
+    # hot spot at 3 T0 and ambient pressure: rho = rho0 / 3 (area-weighted specific volume)
+    rho_gas = 1.0 / ((1 - hot) / rho0 + hot * 3.0 / rho0)
+    rng = np.random.default_rng(seed)
+    xi = rng.uniform(-1.0, 1.0, size=(ny, nx))
+    gas_cells = (frac < 1.0)[:, None] & np.ones((1, nx), bool)
+    rho_gas = np.where(gas_cells, rho_gas * (1 + 1e-3 * xi), rho_gas)
+    w[k["rho2"]] = rho_gas
+    w[k["p"]] = p0
+    w[k["lam"]] = 1.0
+    del yc
+    p = Patch(nx=nx, ny=ny, dx=dx, dy=dy, prim=w)
+    return Workload(name or f"2d_reactive_plate_{nx}x{ny}", 2, [SOLID, gas], [p], 0.6,
+                    steps, True, reactive_material=1, extra=dict(T0=T0))
+
+
+def batched_riemann_1d(n_problems: int = 4096, seed: int = 3, steps: int = 300,
+                       nmin: int = 256, nmax: int = 4096, name=None) -> Workload:
+    """Many independent two-material 1D Riemann problems of log-uniform size."""
+    rng = np.random.default_rng(seed)
+    sizes = np.rint(np.exp(rng.uniform(math.log(nmin), math.log(nmax), n_problems))).astype(int)
+    patches = []
+    for b in range(n_problems):
+        n = int(sizes[b])
+        sides = []
+        for _ in range(2):
+            rho = math.exp(rng.uniform(0.0, math.log(1e4)))
+            p = math.exp(rng.uniform(math.log(1e5), math.log(1e10)))
+            u = rng.uniform(-500.0, 500.0)
+            mat = 0 if rng.uniform() < 0.5 else 1
+            sides.append(dict(mat=mat, rho=rho, u=u, p=p))
+        w, k = _blank(1, False, 1, n)
+        dx = 1.0 / n
+        xc = (np.arange(n) + 0.5) * dx
+        for side, mask in ((sides[0], xc < 0.5), (sides[1], xc >= 0.5)):
+            w[k["phi1"], 0, mask] = 1.0 - EPS_PHI if side["mat"] == 0 else EPS_PHI
+            w[k["rho1"], 0, mask] = side["rho"]
+            w[k["rho2"], 0, mask] = side["rho"]
+            w[k["u"], 0, mask] = side["u"]
+            w[k["p"], 0, mask] = side["p"]
+        patches.append(Patch(nx=n, ny=1, dx=dx, dy=1.0, prim=w))
+    return Workload(name or f"1d_batch_{n_problems}", 1, [SOLID, AIR], patches, 0.8,
+                    steps, False)
+
+
+def adjoint_case_2d(n: int = 256, steps: int = 200, seed: int = 4) -> Workload:
+    """256^2 shock-disc problem with a smooth Gaussian density perturbation field."""
+    wl = shock_disc_2d(n, steps=steps, name=f"2d_shock_disc_adjoint_{n}")
+    d = 1.0 / n
+    xc = (np.arange(n) + 0.5) * d
+    r2 = (xc[None, :] - 0.4) ** 2 + (xc[:, None] - 0.5) ** 2
+    wl.extra["drho_shape"] = np.exp(-r2 / (2 * 0.05 ** 2))
+    wl.extra["seed"] = seed
+    return wl
+
+
+CONFIGS = {
+    "1d_solid_gas": solid_gas_1d,
+    "2d_shock_disc": shock_disc_2d,
+    "2d_reactive_plate": reactive_plate_2d,
+    "1d_batch": batched_riemann_1d,
+    "2d_adjoint": adjoint_case_2d,
+}

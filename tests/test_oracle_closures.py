@@ -1,0 +1,243 @@
+"""Pins of the oracle's closures, reconstruction and Riemann solver.
+
+Each check compares the oracle with something other than itself: textbook
+special cases (ideal and stiffened gas), numerical derivatives, exact matrix
+functions, quadrature of the THINC profile, and the invariance of the flux
+under a mirror of the frame.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import closures as C
+from oracle import reconstruction as Rc
+from oracle import riemann as Rm
+from paper_2009_14555_gb300 import workloads as W
+
+F64 = torch.float64
+GAS = W.material(1.4)
+WATER = W.material(4.4, p_inf=6e8)
+SOLID = W.SOLID
+
+
+def t(x):
+    return torch.as_tensor(x, dtype=F64)
+
+
+def rand_stretch(n, amp, gen):
+    """Random plane-strain stretch near I (unimodular not required)."""
+    V = torch.eye(3, dtype=F64).repeat(n, 1, 1)
+    V[:, :2, :2] += amp * torch.randn(n, 2, 2, generator=gen, dtype=F64)
+    V[:, 2, 2] += amp * torch.randn(n, generator=gen, dtype=F64)
+    return V
+
+
+def test_ideal_gas_pressure_is_textbook():
+    rho, u, p = t([1.0, 0.125, 3.0]), t([0.0, 2.0, -1.0]), t([1.0, 0.1, 7.0])
+    phi1 = t([1e-6, 0.5, 1 - 1e-6])
+    w = dict(phi1=phi1, rho1=rho, rho2=rho, u=torch.stack([u, 0 * u, 0 * u], -1), p=p,
+             V=torch.eye(3, dtype=F64).repeat(3, 1, 1))
+    q = C.prim_to_cons(w, [GAS, GAS])
+    # textbook: E = p/(gamma-1) + rho u^2/2
+    assert torch.allclose(q["E"], p / 0.4 + 0.5 * rho * u * u, rtol=1e-14)
+    assert torch.allclose(C.cons_to_prim(q, [GAS, GAS])["p"], p, rtol=1e-13)
+
+
+def test_stiffened_gas_pressure_and_sound_speed_textbook():
+    rho, p = t([1000.0, 1100.0]), t([1e5, 3e9])
+    e = (p + WATER["gamma"] * WATER["p_inf"]) / ((WATER["gamma"] - 1) * rho)  # textbook SG
+    J2 = torch.zeros_like(rho)
+    phis = [torch.ones_like(rho), torch.zeros_like(rho)]
+    pp = C.mixture_pressure(phis, [rho, rho], rho * e, J2, [WATER, GAS])
+    assert torch.allclose(pp, p, rtol=1e-12)
+    c2 = C.material_sound_speed2(WATER, rho, p, J2)
+    assert torch.allclose(c2, WATER["gamma"] * (p + WATER["p_inf"]) / rho, rtol=1e-13)
+
+
+@pytest.mark.parametrize("J2v", [0.0, 1e-4, 4e-3])
+def test_sound_speed_is_isentropic_derivative(J2v):
+    """c^2 = (dp/drho)_s at fixed strain: central differences along de = p/rho^2 drho."""
+    rho0, p0 = 8000.0, 2e8
+    J2 = t([J2v])
+    phis = [t([1.0]), t([0.0])]
+    mats = [SOLID, GAS]
+
+    def p_of(rho, e):
+        return C.mixture_pressure(phis, [t([rho]), t([1.0])], t([rho * e]), J2, mats).item()
+
+    e0 = C.material_energy(SOLID, t([rho0]), t([p0]), J2).item()
+    h = 1e-3
+    # second-order isentrope step: de/drho = p/rho^2
+    ep = e0 + p0 / rho0 ** 2 * h
+    em = e0 - p0 / rho0 ** 2 * h
+    num = (p_of(rho0 + h, ep) - p_of(rho0 - h, em)) / (2 * h)
+    c2 = C.material_sound_speed2(SOLID, t([rho0]), t([p0]), J2).item()
+    assert abs(num - c2) / c2 < 1e-6
+
+
+def test_reactive_closure_textbook():
+    """Pure reactive ideal gas: p = (gamma-1)(rho e + (1-lam) rho Q), c^2 = gamma p / rho."""
+    gas = W.material(1.4, reactive=1, Q=2e6, cv=717.5, A=1.0, T_act=1.0)
+    rho, p, lam = t([1.2, 0.4]), t([1e5, 2e6]), t([1.0, 0.3])
+    w = dict(phi1=t([1e-12, 1e-12]), rho1=t([8000.0, 8000.0]), rho2=rho,
+             u=torch.zeros(2, 3, dtype=F64), p=p, V=torch.eye(3, dtype=F64).repeat(2, 1, 1),
+             lam=lam)
+    q = C.prim_to_cons(w, [GAS, gas])
+    rhoe_th = (q["E"] + (1 - lam) * rho * gas["Q"])  # thermal part for the pure gas
+    assert torch.allclose(0.4 * rhoe_th, p, rtol=1e-9)
+    c2 = C.material_sound_speed2(gas, rho, p, torch.zeros(2, dtype=F64), lam)
+    assert torch.allclose(c2, 1.4 * p / rho, rtol=1e-13)
+
+
+def test_mixture_pressure_equilibrium_all_fractions():
+    """Any phi with a common pressure recovers that pressure (Abgrall)."""
+    phi = t(np.linspace(1e-6, 1 - 1e-6, 11))
+    n = len(phi)
+    w = dict(phi1=phi, rho1=torch.full((n,), 8000.0, dtype=F64), rho2=torch.full((n,), 1.2, dtype=F64),
+             u=torch.zeros(n, 3, dtype=F64), p=torch.full((n,), 1e5, dtype=F64),
+             V=torch.eye(3, dtype=F64).repeat(n, 1, 1))
+    q = C.prim_to_cons(w, [SOLID, GAS])
+    assert torch.allclose(C.cons_to_prim(q, [SOLID, GAS])["p"], w["p"], rtol=1e-9)
+
+
+@pytest.mark.parametrize("sym", [True, False])
+def test_bazant_strain_third_order(sym):
+    """dev(H) ~ log V for symmetric unimodular V with error O(|H|^3) (Section 3.2)."""
+    gen = torch.Generator().manual_seed(0)
+    A = torch.randn(3, 3, generator=gen, dtype=F64)
+    A = 0.5 * (A + A.T) if sym else A
+    A[2, :2] = 0
+    A[:2, 2] = 0
+    A = A - torch.trace(A) / 3 * torch.eye(3, dtype=F64)
+    errs, jerrs = [], []
+    for h in (0.02, 0.01):
+        Hx = h * 0.5 * (A + A.T)
+        V = torch.linalg.matrix_exp(Hx)  # exact symmetric stretch with log = Hx
+        if not sym:
+            # a rotation on the left does not change V V^T when V is replaced by V R^T
+            R = torch.linalg.matrix_exp(h * 0.5 * (A - A.T))
+            V = V @ R.T
+        devH, J2 = C.hencky_dev(V[None])
+        errs.append((devH[0] - Hx).abs().max().item())
+        jerrs.append(abs(J2.item() - (Hx * Hx).sum().item()))
+    assert 6.0 < errs[0] / errs[1] < 10.0      # dev(H) error O(h^3)
+    assert 12.0 < jerrs[0] / jerrs[1] < 20.0   # J^2 error O(h^4)
+
+
+def test_minmod_and_muscl():
+    x = t(np.arange(8.0))
+    wL, wR = Rc.muscl_faces(2 * x + 1)
+    assert torch.allclose(wL[1:-1], 2 * x[1:-1], rtol=0, atol=1e-15)
+    assert torch.allclose(wR[1:-1], 2 * x[1:-1] + 2, rtol=0, atol=1e-15)
+    peak = t([0.0, 1.0, 3.0, 1.0, 0.0])
+    wL, wR = Rc.muscl_faces(peak)
+    assert wL[2] == 3.0 and wR[2] == 3.0
+    assert Rc.minmod(t(-2.0), t(-1.0)) == -1.0 and Rc.minmod(t(2.0), t(-1.0)) == 0.0
+
+
+@pytest.mark.parametrize("beta", [2.51, 0.5, 1.7])
+def test_thinc_edges_conserve_cell_average(beta):
+    """The tanh profile through the THINC edge values has cell average q_i (App. A)."""
+    gen = np.random.default_rng(1)
+    for _ in range(20):
+        qm, qp = gen.uniform(0, 1, 2)
+        lo, hi = min(qm, qp), max(qm, qp)
+        qc = lo + (hi - lo) * gen.uniform(0.05, 0.95)
+        q = t([qm, qc, qp])
+        qL, qR, mixed = Rc.thinc_faces(q, torch.full((3,), beta, dtype=F64))
+        assert bool(mixed[1])
+        qmin, jump, th = lo, hi - lo, math.copysign(1.0, qp - qm)
+        # invert the left edge value for the interface position x0: q_L = qmin + jump/2 (1 + th tanh(-beta x0))
+        tl = ((qL[1].item() - qmin) / (jump / 2) - 1) / th
+        x0 = -math.atanh(tl) / beta
+        xs = (np.arange(20000) + 0.5) / 20000
+        prof = qmin + jump / 2 * (1 + th * np.tanh(beta * (xs - x0)))
+        assert abs(prof.mean() - qc) < 1e-9
+        right = qmin + jump / 2 * (1 + th * math.tanh(beta * (1 - x0)))
+        assert abs(right - qR[1].item()) < 1e-12
+
+
+def test_thinc_mixed_cell_test():
+    beta = torch.full((3,), 2.51, dtype=F64)
+    _, _, m = Rc.thinc_faces(t([0.0, 0.5, 0.4]), beta)  # not monotone
+    assert not bool(m[1])
+    _, _, m = Rc.thinc_faces(t([0.0, 1e-7, 1.0]), beta)  # C below delta
+    assert not bool(m[1])
+
+
+def test_bvd_prefers_thinc_at_a_step_and_muscl_on_a_ramp():
+    step = t([0.0, 0.0, 0.0, 0.0, 0.5, 1.0, 1.0, 1.0, 1.0])
+    ramp = t(np.linspace(0, 1, 9))
+    for prof, expect_thinc in ((step, True), (ramp, False)):
+        mL, mR = Rc.muscl_faces(prof)
+        tL, tR, mixed = Rc.thinc_faces(prof, torch.full_like(prof, 2.51))
+        L, R = Rc.bvd_select(mL, mR, tL, tR, mixed)
+        used_thinc = bool(mixed[4]) and (L[4] != mL[4]).item()
+        assert used_thinc == expect_thinc
+
+
+def test_youngs_normal_of_a_plane():
+    ny, nx = 6, 7
+    yy, xx = torch.meshgrid(t(np.arange(ny)), t(np.arange(nx)), indexing="ij")
+    phi = 0.3 * xx * 0.5 - 0.2 * yy * 2.0
+    anx, any_ = Rc.youngs_abs_normal(phi, 0.5, 2.0)
+    gx, gy = 0.3, 0.2  # physical gradient components
+    assert torch.allclose(anx[1:-1, 1:-1], torch.full((ny - 2, nx - 2), gx / math.hypot(gx, gy), dtype=F64))
+    assert torch.allclose(any_[1:-1, 1:-1], torch.full((ny - 2, nx - 2), gy / math.hypot(gx, gy), dtype=F64))
+
+
+def _prim_batch(n, gen, solid=True):
+    phi = t(np.random.default_rng(2).uniform(0.1, 0.9, n))
+    return dict(phi1=phi, rho1=8000 * (1 + 0.1 * torch.rand(n, generator=gen, dtype=F64)),
+                rho2=1.2 * (1 + torch.rand(n, generator=gen, dtype=F64)),
+                u=100 * torch.randn(n, 3, generator=gen, dtype=F64) * t([1, 1, 0]),
+                p=1e5 + 1e8 * torch.rand(n, generator=gen, dtype=F64),
+                V=rand_stretch(n, 0.01 if solid else 0.0, gen))
+
+
+@pytest.mark.parametrize("d", [0, 1])
+def test_hllc_consistency(d):
+    """Equal left and right states: the flux is the physical flux (Section 3)."""
+    gen = torch.Generator().manual_seed(3)
+    w = _prim_batch(16, gen)
+    F, phi_f, u_f, V_f = Rm.hllc(w, w, d, [SOLID, GAS])
+    s = Rm.face_state(w, [SOLID, GAS])
+    Fp = Rm.physical_flux(s, d)
+    for k in Fp:
+        assert torch.allclose(F[k], Fp[k], rtol=1e-12, atol=1e-6)
+    assert torch.equal(phi_f, w["phi1"])
+    assert torch.allclose(u_f, w["u"]) and torch.allclose(V_f, w["V"])
+
+
+def test_hllc_mirror_symmetry():
+    """Mirroring x -> -x maps the flux of (L, R) to minus the mirrored flux of (R', L')."""
+    gen = torch.Generator().manual_seed(4)
+    wl, wr = _prim_batch(16, gen), _prim_batch(16, gen)
+    P = torch.diag(t([-1.0, 1.0, 1.0]))
+
+    def mirror(w):
+        m = dict(w)
+        m["u"] = w["u"] @ P
+        m["V"] = P @ w["V"] @ P
+        return m
+
+    F, phi_f, u_f, V_f = Rm.hllc(wl, wr, 0, [SOLID, GAS])
+    Fm, phi_m, u_m, V_m = Rm.hllc(mirror(wr), mirror(wl), 0, [SOLID, GAS])
+    for k in ("ar1", "ar2", "E"):
+        assert torch.allclose(F[k], -Fm[k], rtol=1e-10, atol=1e-3)
+    # momentum is odd under the mirror in its x component and the flux direction flips
+    assert torch.allclose(F["mom"], -(Fm["mom"] @ P), rtol=1e-10, atol=1e-3)
+    assert torch.allclose(u_f, u_m @ P, rtol=1e-12, atol=1e-9)
+    assert torch.allclose(V_f, P @ V_m @ P, rtol=1e-12, atol=1e-12)
+
+
+def test_hllc_star_stretch_keeps_determinant():
+    gen = torch.Generator().manual_seed(5)
+    wl, wr = _prim_batch(32, gen), _prim_batch(32, gen)
+    wr["u"][:, 0] -= 300.0  # compressive
+    _, _, _, V_f = Rm.hllc(wl, wr, 0, [SOLID, GAS])
+    detL, detR = torch.linalg.det(wl["V"]), torch.linalg.det(wr["V"])
+    dv = torch.linalg.det(V_f)
+    assert torch.all(torch.minimum((dv - detL).abs(), (dv - detR).abs()) < 1e-12)
