@@ -1,0 +1,262 @@
+"""Benchmark: cell-updates/s of the diffuse-interface step on one GB300.
+
+Workload: premixed reactive air over an elastoplastic plate on a 2048 x 1024
+grid (all rows of the step: ghost map, CFL reduction, primitive recovery,
+MUSCL/THINC-BVD, HLLC, RK3, plastic and reactive updates).  A bench "step" is
+one time step of the whole grid.  One cell-update = one full step of one cell.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  The reference arm (--impl reference) times the float64
+CPU oracle on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/s and % HBM peak, FP32-bulk vs plain FP64 on one GB300 at stated L1"
+UNIT = "cell-updates/s"
+NX, NY = 2048, 1024
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(nx=NX, ny=NY):
+    from paper_2009_14555_gb300 import workloads as W
+    return W.reactive_plate_2d(nx, ny)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2009_14555_gb300.solver import Solver, pack
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = workload()
+    cells = wl.cells
+    prim = pack([p.prim for p in wl.patches])
+    results = {}
+    precisions = ["fp64"]
+    for prec in precisions:
+        s = Solver.from_workload(wl, precision=prec)
+        s.set_state(prim, kind=1)
+        stream = s.stream
+        for _ in range(args.warmup):
+            s.step(1)
+        torch.cuda.synchronize()
+        launches = 0
+        # per-step device time, every step bracketed by events on the library's stream
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            for k in range(args.steps):
+                evs[k][0].record(stream)
+                s.step(1)
+                evs[k][1].record(stream)
+                launches += s.launches
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        if world > 1:
+            dist.barrier()
+        ms = [a.elapsed_time(b) for a, b in evs]
+        tot_ms = float(np.sum(ms))
+        if world > 1:
+            t = torch.tensor([tot_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot_ms = float(t.item())
+        rc, _, _ = s.check()
+        results[prec] = dict(ms_total=tot_ms, ms_per_step=tot_ms / args.steps, wall=wall,
+                             launches=launches, clocks=clk.summary(), ok=rc == 0, solver=s)
+    # end-to-end through the C ABI with host buffers: H2D of the step's input
+    # state from pinned memory, the step, D2H of the result, every step.
+    s = results["fp64"]["solver"]
+    hin = torch.from_numpy(prim).pin_memory()
+    hout = torch.empty(s.state_numel, dtype=torch.float64).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        from paper_2009_14555_gb300 import _lib as L
+        L.dis_set_state(s.ctx, 1, hin.data_ptr(), False)
+        s.step(1)
+        L.dis_get_state(s.ctx, 0, hout.data_ptr(), False)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    nbytes = prim.nbytes
+
+    r = results["fp64"]
+    value = cells * world / (r["ms_per_step"] * 1e-3)
+    hbm, kind = peaks()
+    alg_bytes = 2 * 12 * 8  # read + write the 12-field float64 state once per cell-update
+    achieved = alg_bytes * cells / (r["ms_per_step"] * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"2d_reactive_plate_{NX}x{NY}", "cells": cells, "precision": "fp64",
+                   "l2": "working set (state 201 MB + primitives + faces) larger than L2",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "note": f"whole step, algorithmic {alg_bytes} B/cell-update, peak {kind}"},
+        "e2e": {"value": cells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+        "status_ok": r["ok"],
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for v in results.values():
+        v["solver"].close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(budget_s=15.0, steps=None):
+    """The float64 CPU oracle on a bounded sample of the same workload."""
+    import torch
+    from oracle import scheme as OS
+    from oracle import closures as OC
+    nx, ny = 256, 128
+    wl = workload(nx, ny)
+    p = wl.patches[0]
+    grid = OS.grid_of(p, 2)
+    q = OC.prim_to_cons(OS.prim_from_array(p.prim, 2, True), wl.materials)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        q, _ = OS.step(q, grid, wl.materials, dict(cfl=wl.cfl, thinc=wl.thinc))
+        n += 1
+        el = time.perf_counter() - t0
+        if (steps is not None and n >= steps) or (steps is None and el > budget_s):
+            break
+    return {"value": nx * ny * n / el, "unit": UNIT, "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": f"{n} steps of the reactive plate at {nx}x{ny} (same physics, smaller grid)",
+            "seconds": el}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    per = []
+    for _ in range(args.warmup):
+        cpu_baseline(steps=1)
+    res = cpu_baseline(steps=max(1, args.steps))
+    line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["seconds"] / max(1, args.steps) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"2d_reactive_plate_{NX}x{NY}", "sample": res["sample"]},
+            "cpu_baseline": {"value": res["value"], "unit": UNIT, "cores": res["cores"],
+                             "kind": "oracle", "sample": res["sample"]},
+            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    del per
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,151 @@
+/*
+ * dis.h - C ABI of the GB300 diffuse-interface finite-volume step.
+ *
+ * One explicit time step of the unified diffuse-interface system for
+ * multiphase reactive fluids and elastoplastic solids on regular Cartesian
+ * patches (Wallis, Barton & Nikiforakis, arXiv 2009.14555, Section 3):
+ * CFL time step, SSP-RK3 hyperbolic update with MUSCL(-BVD-THINC)
+ * reconstruction of primitives and an HLLC-type elastic Riemann solver,
+ * then the plastic (Section 3.2) and reactive (Section 3.3) source steps.
+ *
+ * Conventions shared by every call:
+ *   - All functions return an int status (DIS_OK = 0, negative on error).
+ *     Nothing aborts or throws across this interface; the text of the last
+ *     error of the calling thread is returned by dis_last_error().
+ *   - A context is bound to the CUDA device that was current at dis_create
+ *     and to one CUDA stream; all device work is ordered on that stream.
+ *     Calls on one context are not thread-safe.
+ *   - Device pointers must be device memory of that device; host pointers
+ *     may be pageable.  The library never keeps a caller pointer after a call
+ *     returns, except workspace bound by dis_bind_workspace.
+ *   - State arrays ("packed" layout): for each patch in creation order, an
+ *     array [nfields][ny][nx] of float64 (x fastest), patches concatenated.
+ *     Field order (two materials, material 1 carries the stored volume
+ *     fraction; the last field exists only with a reactive material):
+ *       conservative 1D: phi1, phi1 rho1, phi2 rho2, rho u, rho E, V11, V22, V33, [phi_y rho_y lam]
+ *       conservative 2D: phi1, phi1 rho1, phi2 rho2, rho u, rho v, rho E,
+ *                        V11, V12, V21, V22, V33, [phi_y rho_y lam]
+ *       primitive    1D: phi1, rho1, rho2, u, p, V11, V22, V33, [lam]
+ *       primitive    2D: phi1, rho1, rho2, u, v, p, V11, V12, V21, V22, V33, [lam]
+ *     (state vector q of Section 3; V is the elastic stretch tensor in plane
+ *     strain; lam is the reaction progress variable, 1 = reactant.)
+ */
+#ifndef DIS_H
+#define DIS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  DIS_OK = 0,
+  DIS_EINVAL = -1,       /* bad argument; nothing was changed */
+  DIS_ENOMEM = -2,       /* workspace missing or too small, or allocation failed */
+  DIS_ECUDA = -3,        /* a CUDA runtime call failed (text in dis_last_error) */
+  DIS_ENONPHYSICAL = -4, /* a step produced a non-finite value or phi outside [-1e-6, 1+1e-6] */
+  DIS_ESTATE = -5        /* call out of order (e.g. step before set_state) */
+};
+
+enum { DIS_BC_TRANSMISSIVE = 0, DIS_BC_PERIODIC = 1, DIS_BC_REFLECTIVE = 2 };
+enum { DIS_CONSERVATIVE = 0, DIS_PRIMITIVE = 1 };
+enum { DIS_FP64 = 0, DIS_FP32_BULK = 1 };
+enum { DIS_PLASTIC_NONE = 0, DIS_PLASTIC_PERFECT = 1, DIS_PLASTIC_RATE = 2 };
+
+/* One material: stiffened-gas Mie-Grueneisen closure (Section 2.3) with a
+ * constant shear modulus G, plasticity (Section 2.3.2: none, perfect = the
+ * chi0 -> infinity limit of ideal plasticity, or ideal plasticity with rate
+ * chi0), and for a reactive material an ideal-gas reactant/product pair of
+ * equal gamma and C_V with heat release Q (Section 2.3.1) and an Arrhenius
+ * rate lam_dot = -A lam exp(-T_act / T). */
+typedef struct {
+  double gamma, p_inf, e_inf, G;
+  int32_t plastic;
+  double sigma_y, chi0;
+  int32_t reactive;
+  double Q, cv, A, T_act;
+} dis_material;
+
+/* One Cartesian patch (the single-grid unit of Section 3): nx x ny cells of
+ * size dx x dy (ny = 1 and dy ignored in 1D); bc = {x-low, x-high, y-low,
+ * y-high} boundary kinds. */
+typedef struct {
+  int32_t nx, ny;
+  double dx, dy;
+  int32_t bc[4];
+} dis_patch;
+
+/* Step options: CFL number (Section 3: fraction of the largest stable step),
+ * THINC interface steepening on/off (Appendix A), precision mode. */
+typedef struct {
+  double cfl;
+  int32_t thinc;
+  int32_t precision;
+} dis_options;
+
+typedef struct dis_ctx dis_ctx;
+
+/* Create a context for `n_patches` patches of dimension `dim` (1 or 2) with
+ * two materials, material `reactive_material` (0, 1, or -1 for none) being
+ * the reactive one.  `stream` is a cudaStream_t (NULL = legacy default).
+ * Copies `patches` and `opt`.  Returns DIS_EINVAL for bad sizes. */
+int dis_create(int dim, int n_patches, const dis_patch* patches, int reactive_material,
+               const dis_options* opt, void* stream, dis_ctx** out);
+
+/* Set the two materials (n must be 2).  Copies `m`. */
+int dis_set_materials(dis_ctx* ctx, const dis_material* m, int n);
+
+/* Bytes of device workspace the context needs (state buffers, primitives,
+ * face fluxes, staging).  Depends only on the patches, dim and materials. */
+size_t dis_workspace_bytes(const dis_ctx* ctx);
+
+/* Lend the context `bytes` of device memory at `dev` (256-byte aligned); the
+ * caller keeps it alive until dis_destroy or another bind.  If no workspace
+ * is bound when it is first needed, the library allocates its own. */
+int dis_bind_workspace(dis_ctx* ctx, void* dev, size_t bytes);
+
+/* Load the state of all patches from `src` (packed layout above).  kind =
+ * DIS_PRIMITIVE converts primitives to conservative variables on the device
+ * through the closures of Section 2.  src_on_device selects a device or host
+ * pointer.  Ordered on the context's stream. */
+int dis_set_state(dis_ctx* ctx, int kind, const double* src, int src_on_device);
+
+/* Store the state of all patches into `dst` (packed layout).  kind =
+ * DIS_PRIMITIVE returns the recovered primitives (pressure from the mixture
+ * pressure function, Appendix B).  A host destination synchronises the
+ * stream. */
+int dis_get_state(dis_ctx* ctx, int kind, double* dst, int dst_on_device);
+
+/* Advance every patch by n_steps time steps, each with its own CFL time step
+ * computed on the device from the state at the start of the step (Section
+ * 3).  If dt_out is not NULL it receives the last step's dt per patch (host
+ * array of n_patches; synchronises).  The step is device-resident: no host
+ * synchronisation inside. */
+int dis_step(dis_ctx* ctx, int n_steps, double* dt_out);
+
+/* Same with prescribed time steps dt[patch] (host array) for every step. */
+int dis_step_fixed_dt(dis_ctx* ctx, int n_steps, const double* dt);
+
+/* Read and clear the device status word: DIS_OK or DIS_ENONPHYSICAL, with the
+ * first offending patch and cell (x index + nx * y index) if not NULL.
+ * Synchronises the stream. */
+int dis_check(dis_ctx* ctx, int* bad_patch, int* bad_cell);
+
+/* Total bytes of the packed state for `kind` (nfields x cells x 8). */
+size_t dis_state_bytes(const dis_ctx* ctx, int kind);
+
+/* Number of kernel launches made by the last dis_step / dis_step_fixed_dt. */
+long long dis_last_launches(const dis_ctx* ctx);
+
+/* Thread-local text of the last error (never NULL). */
+const char* dis_last_error(void);
+
+void dis_destroy(dis_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIS_H */

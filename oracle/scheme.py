@@ -180,14 +180,27 @@ def _assemble(c):
     return w
 
 
+def _hyperbolic(w, mats):
+    """Mask of states with a positive longitudinal sound speed squared."""
+    _, J2 = hencky_dev(w["V"])
+    _, _, _, cL2 = mixture_props(phases(w["phi1"]), [w["rho1"], w["rho2"]], w["p"], J2, mats,
+                                 w.get("lam"))
+    return cL2 > 0
+
+
 def _sweep(wg, absn, d, n, mats, thinc):
     """Face fluxes along axis d for lines of cells (cells along the last axis).
 
     wg: primitive components on lines including NG ghosts on each end;
     absn: |n_d| on the same lines (None in 1D).  Returns the HLLC outputs on the
     n + 1 faces of the interior cells.
+
+    Reading: a reconstructed face state that is not hyperbolic (c_L^2 <= 0,
+    which THINC sharpening of phi next to a stiff material can produce when
+    the gas pressure is negative) is replaced by its cell-centre state
+    (first-order fallback on that side of that face).
     """
-    L, R = {}, {}
+    L, R, CL, CR = {}, {}, {}, {}
     for k, t in wg.items():
         mL, mR = muscl_faces(t)
         if k == "phi1" and thinc:
@@ -197,6 +210,13 @@ def _sweep(wg, absn, d, n, mats, thinc):
         # face f between cell NG-1+f and NG+f, f = 0..n
         L[k] = mR[..., NG - 1:NG + n]
         R[k] = mL[..., NG:NG + n + 1]
+        CL[k] = t[..., NG - 1:NG + n]
+        CR[k] = t[..., NG:NG + n + 1]
+    wL, wR = _assemble(L), _assemble(R)
+    okL, okR = _hyperbolic(wL, mats), _hyperbolic(wR, mats)
+    for k in L:
+        L[k] = torch.where(okL, L[k], CL[k])
+        R[k] = torch.where(okR, R[k], CR[k])
     return hllc(_assemble(L), _assemble(R), d, mats)
 
 

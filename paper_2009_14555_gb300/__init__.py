@@ -1,0 +1,7 @@
+"""GB300-native diffuse-interface finite-volume step (arXiv 2009.14555).
+
+  workloads   seeded synthetic inputs shaped like the paper's problems
+  solver      Solver: the C ABI of libdis.so over torch device memory
+  _lib        ctypes binding of include/dis.h
+  build       nvcc build of libdis.so for sm_103a
+"""

@@ -1,0 +1,144 @@
+"""ctypes binding of libdis.so (the C ABI of include/dis.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library.  Loading fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_int32, c_longlong, c_size_t, c_void_p, c_char_p
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdis.so")
+
+DIS_OK, DIS_EINVAL, DIS_ENOMEM, DIS_ECUDA, DIS_ENONPHYSICAL, DIS_ESTATE = 0, -1, -2, -3, -4, -5
+DIS_CONSERVATIVE, DIS_PRIMITIVE = 0, 1
+DIS_FP64, DIS_FP32_BULK = 0, 1
+
+
+class DisMaterial(ctypes.Structure):
+    _fields_ = [("gamma", c_double), ("p_inf", c_double), ("e_inf", c_double), ("G", c_double),
+                ("plastic", c_int32), ("sigma_y", c_double), ("chi0", c_double),
+                ("reactive", c_int32), ("Q", c_double), ("cv", c_double), ("A", c_double),
+                ("T_act", c_double)]
+
+
+class DisPatch(ctypes.Structure):
+    _fields_ = [("nx", c_int32), ("ny", c_int32), ("dx", c_double), ("dy", c_double),
+                ("bc", c_int32 * 4)]
+
+
+class DisOptions(ctypes.Structure):
+    _fields_ = [("cfl", c_double), ("thinc", c_int32), ("precision", c_int32)]
+
+
+class DisError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libdis error {code}: {msg}")
+        self.code = code
+
+
+# name -> (restype, argtypes); the full exported surface of include/dis.h
+SIGNATURES = {
+    "dis_create": (c_int, [c_int, c_int, POINTER(DisPatch), c_int, POINTER(DisOptions), c_void_p,
+                           POINTER(c_void_p)]),
+    "dis_set_materials": (c_int, [c_void_p, POINTER(DisMaterial), c_int]),
+    "dis_workspace_bytes": (c_size_t, [c_void_p]),
+    "dis_bind_workspace": (c_int, [c_void_p, c_void_p, c_size_t]),
+    "dis_set_state": (c_int, [c_void_p, c_int, c_void_p, c_int]),
+    "dis_get_state": (c_int, [c_void_p, c_int, c_void_p, c_int]),
+    "dis_step": (c_int, [c_void_p, c_int, c_void_p]),
+    "dis_step_fixed_dt": (c_int, [c_void_p, c_int, c_void_p]),
+    "dis_check": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int)]),
+    "dis_state_bytes": (c_size_t, [c_void_p, c_int]),
+    "dis_last_launches": (c_longlong, [c_void_p]),
+    "dis_last_error": (c_char_p, []),
+    "dis_destroy": (None, [c_void_p]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libdis.so and declare its signatures (no GPU needed to load)."""
+    global _lib
+    if _lib is not None and path == LIB_PATH:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path == LIB_PATH:
+        _lib = lib
+    return lib
+
+
+def check(rc: int):
+    if rc != DIS_OK:
+        raise DisError(rc, load().dis_last_error().decode())
+    return rc
+
+
+# thin wrappers with the C names
+def dis_create(dim, patches, reactive_material, opts, stream):
+    lib = load()
+    arr = (DisPatch * len(patches))(*patches)
+    out = c_void_p()
+    check(lib.dis_create(dim, len(patches), arr, reactive_material, ctypes.byref(opts),
+                         c_void_p(stream), ctypes.byref(out)))
+    return out
+
+
+def dis_set_materials(ctx, mats):
+    arr = (DisMaterial * len(mats))(*mats)
+    return check(load().dis_set_materials(ctx, arr, len(mats)))
+
+
+def dis_workspace_bytes(ctx):
+    return load().dis_workspace_bytes(ctx)
+
+
+def dis_bind_workspace(ctx, ptr, nbytes):
+    return check(load().dis_bind_workspace(ctx, c_void_p(ptr), nbytes))
+
+
+def dis_set_state(ctx, kind, ptr, on_device):
+    return check(load().dis_set_state(ctx, kind, c_void_p(ptr), int(on_device)))
+
+
+def dis_get_state(ctx, kind, ptr, on_device):
+    return check(load().dis_get_state(ctx, kind, c_void_p(ptr), int(on_device)))
+
+
+def dis_step(ctx, n, dt_out_ptr=None):
+    return check(load().dis_step(ctx, n, c_void_p(dt_out_ptr) if dt_out_ptr else None))
+
+
+def dis_step_fixed_dt(ctx, n, dt_ptr):
+    return check(load().dis_step_fixed_dt(ctx, n, c_void_p(dt_ptr)))
+
+
+def dis_check(ctx):
+    bp, bc = c_int(-1), c_int(-1)
+    rc = load().dis_check(ctx, ctypes.byref(bp), ctypes.byref(bc))
+    return rc, bp.value, bc.value
+
+
+def dis_state_bytes(ctx, kind):
+    return load().dis_state_bytes(ctx, kind)
+
+
+def dis_last_launches(ctx):
+    return load().dis_last_launches(ctx)
+
+
+def dis_last_error():
+    return load().dis_last_error().decode()
+
+
+def dis_destroy(ctx):
+    load().dis_destroy(ctx)

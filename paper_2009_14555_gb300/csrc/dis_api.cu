@@ -1,0 +1,480 @@
+// dis_api.cu - host side of the C ABI declared in include/dis.h.
+//
+// A context owns the patch description, the host-built segment tables (the
+// patch-batch schedule: every launch covers all patches of the batch), the
+// workspace carve-up and the launch sequence of one time step:
+//
+//   per step:  memset(rate)                      (CFL mode only)
+//   per stage: k_prim   (ghost map + primitive recovery [+ CFL rate max])
+//              k_flux x (+ k_flux y in 2D)       (MUSCL/THINC-BVD + HLLC)
+//              k_update (divergence, non-conservative terms, RK3 combination;
+//                        last stage: plastic + reactive steps, status)
+//
+// The time step is computed on the device (dt = CFL / max rate) and read by
+// the update kernels; dis_step therefore never synchronises with the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/dis.h"
+#include "step_kernels.cuh"
+
+using namespace dis;
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CU(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(DIS_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+struct dis_ctx {
+  int dim = 1, np = 0, y = -1, nf = 0;
+  dis_options opt{};
+  Phys phys{};
+  bool have_mats = false, have_state = false;
+  std::vector<dis_patch> patches;
+  std::vector<PatchDev> pd;
+  long long T = 0, NFX = 0, NFY = 0, ncells = 0;
+  std::vector<int4> seg_prim, seg_fx, seg_fy, seg_cell;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  // workspace
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_owned = false, ws_ready = false;
+  double* q[2] = {nullptr, nullptr};  // q^n, stage buffer
+  double* W = nullptr;
+  double* Fx = nullptr;
+  double* Fy = nullptr;
+  double* io = nullptr;
+  unsigned long long* rate = nullptr;
+  double* dtfix = nullptr;
+  double* dtlast = nullptr;
+  int* status = nullptr;
+  PatchDev* d_pd = nullptr;
+  int4 *d_seg_prim = nullptr, *d_seg_fx = nullptr, *d_seg_fy = nullptr, *d_seg_cell = nullptr;
+  long long launches = 0;
+};
+
+namespace {
+
+int n_extra(int dim) { return dim == 2 ? 3 : 2; }
+
+// Split rows of [lo, hi) into segments of at most SEG.
+void add_row(std::vector<int4>& v, int patch, int row, int lo, int hi) {
+  for (int s = lo; s < hi; s += SEG) v.push_back(make_int4(patch, row, s, std::min(SEG, hi - s)));
+}
+
+void layout(dis_ctx* c) {
+  const int g2 = c->dim == 2 ? NG : 0;
+  long long off = 0, fx = 0, fy = 0, po = 0;
+  c->pd.clear();
+  c->seg_prim.clear();
+  c->seg_fx.clear();
+  c->seg_fy.clear();
+  c->seg_cell.clear();
+  for (int p = 0; p < c->np; ++p) {
+    const dis_patch& P = c->patches[p];
+    PatchDev d{};
+    d.nx = P.nx;
+    d.ny = c->dim == 2 ? P.ny : 1;
+    d.pitch = P.nx + 2 * NG;
+    d.rows = d.ny + 2 * g2;
+    for (int k = 0; k < 4; ++k) d.bc[k] = P.bc[k];
+    d.off = off;
+    d.fxoff = fx;
+    d.fyoff = fy;
+    d.poff = po;
+    d.dx = P.dx;
+    d.dy = c->dim == 2 ? P.dy : 1.0;
+    off += ((long long)d.pitch * d.rows + 31) / 32 * 32;
+    fx += (long long)d.ny * (d.nx + 1);
+    if (c->dim == 2) fy += (long long)(d.ny + 1) * d.nx;
+    po += (long long)c->nf * d.nx * d.ny;
+    c->pd.push_back(d);
+    for (int j = -g2; j < d.ny + g2; ++j) add_row(c->seg_prim, p, j, -NG, d.nx + NG);
+    for (int j = 0; j < d.ny; ++j) add_row(c->seg_fx, p, j, 0, d.nx + 1);
+    if (c->dim == 2)
+      for (int j = 0; j <= d.ny; ++j) add_row(c->seg_fy, p, j, 0, d.nx);
+    for (int j = 0; j < d.ny; ++j) add_row(c->seg_cell, p, j, 0, d.nx);
+  }
+  c->T = off;
+  c->NFX = fx;
+  c->NFY = fy;
+  c->ncells = po / c->nf;
+}
+
+struct Carve {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    size_t o = off;
+    off += align256(bytes);
+    return o;
+  }
+};
+
+size_t carve(dis_ctx* c, char* base) {
+  Carve k;
+  const size_t dpl = sizeof(double) * (size_t)c->T;
+  size_t oq0 = k.take(c->nf * dpl), oq1 = k.take(c->nf * dpl), ow = k.take(c->nf * dpl);
+  size_t ofx = k.take(sizeof(double) * (size_t)(c->nf + n_extra(c->dim)) * c->NFX);
+  size_t ofy = k.take(sizeof(double) * (size_t)(c->nf + n_extra(c->dim)) * c->NFY);
+  size_t oio = k.take(sizeof(double) * (size_t)c->nf * c->ncells);
+  size_t ort = k.take(sizeof(unsigned long long) * c->np);
+  size_t odf = k.take(sizeof(double) * c->np);
+  size_t odl = k.take(sizeof(double) * c->np);
+  size_t ost = k.take(sizeof(int) * 4);
+  size_t opd = k.take(sizeof(PatchDev) * c->np);
+  size_t os1 = k.take(sizeof(int4) * c->seg_prim.size());
+  size_t os2 = k.take(sizeof(int4) * c->seg_fx.size());
+  size_t os3 = k.take(sizeof(int4) * std::max<size_t>(1, c->seg_fy.size()));
+  size_t os4 = k.take(sizeof(int4) * c->seg_cell.size());
+  if (base) {
+    c->q[0] = (double*)(base + oq0);
+    c->q[1] = (double*)(base + oq1);
+    c->W = (double*)(base + ow);
+    c->Fx = (double*)(base + ofx);
+    c->Fy = (double*)(base + ofy);
+    c->io = (double*)(base + oio);
+    c->rate = (unsigned long long*)(base + ort);
+    c->dtfix = (double*)(base + odf);
+    c->dtlast = (double*)(base + odl);
+    c->status = (int*)(base + ost);
+    c->d_pd = (PatchDev*)(base + opd);
+    c->d_seg_prim = (int4*)(base + os1);
+    c->d_seg_fx = (int4*)(base + os2);
+    c->d_seg_fy = (int4*)(base + os3);
+    c->d_seg_cell = (int4*)(base + os4);
+  }
+  return k.off;
+}
+
+int ensure_ws(dis_ctx* c) {
+  if (c->ws_ready) return DIS_OK;
+  if (!c->ws) {
+    const size_t need = carve(c, nullptr);
+    void* p = nullptr;
+    CU(cudaMalloc(&p, need));
+    c->ws = (char*)p;
+    c->ws_bytes = need;
+    c->ws_owned = true;
+  }
+  carve(c, c->ws);
+  CU(cudaMemcpyAsync(c->d_pd, c->pd.data(), sizeof(PatchDev) * c->np, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->d_seg_prim, c->seg_prim.data(), sizeof(int4) * c->seg_prim.size(),
+                     cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->d_seg_fx, c->seg_fx.data(), sizeof(int4) * c->seg_fx.size(),
+                     cudaMemcpyHostToDevice, c->stream));
+  if (!c->seg_fy.empty())
+    CU(cudaMemcpyAsync(c->d_seg_fy, c->seg_fy.data(), sizeof(int4) * c->seg_fy.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemcpyAsync(c->d_seg_cell, c->seg_cell.data(), sizeof(int4) * c->seg_cell.size(),
+                     cudaMemcpyHostToDevice, c->stream));
+  CU(cudaMemsetAsync(c->status, 0, sizeof(int) * 4, c->stream));
+  // The tables above come from host vectors that outlive this call; make sure
+  // the copies have finished before the caller may touch them.
+  CU(cudaStreamSynchronize(c->stream));
+  c->ws_ready = true;
+  return DIS_OK;
+}
+
+StepArgs base_args(dis_ctx* c) {
+  StepArgs a{};
+  a.pd = c->d_pd;
+  a.T = c->T;
+  a.NFX = c->NFX;
+  a.NFY = c->NFY;
+  a.W = c->W;
+  a.Fx = c->Fx;
+  a.Fy = c->Fy;
+  a.rate = c->rate;
+  a.dtlast = c->dtlast;
+  a.status = c->status;
+  return a;
+}
+
+template <int DIM, bool RX>
+int run_steps(dis_ctx* c, int n_steps, bool fixed) {
+  StepArgs a = base_args(c);
+  a.dtfix = fixed ? c->dtfix : nullptr;
+  const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+  const unsigned np = (unsigned)c->seg_prim.size(), nfx = (unsigned)c->seg_fx.size(),
+                 nfy = (unsigned)c->seg_fy.size(), nc = (unsigned)c->seg_cell.size();
+  long long launches = 0;
+  for (int s = 0; s < n_steps; ++s) {
+    if (!fixed) CU(cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, c->stream));
+    for (int st = 0; st < 3; ++st) {
+      a.qsrc = st == 0 ? c->q[0] : c->q[1];
+      a.qn = c->q[0];
+      a.qdst = st == 2 ? c->q[0] : c->q[1];
+      a.a = ca[st];
+      a.b = cb[st];
+      a.last = st == 2;
+      k_prim<DIM, RX><<<np, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_prim, (!fixed && st == 0) ? 1 : 0);
+      k_flux<DIM, RX, 0><<<nfx, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_fx);
+      launches += 2;
+      if constexpr (DIM == 2) {
+        k_flux<DIM, RX, 1><<<nfy, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_fy);
+        ++launches;
+      }
+      k_update<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_cell);
+      ++launches;
+    }
+  }
+  CU(cudaGetLastError());
+  c->launches = launches;
+  return DIS_OK;
+}
+
+int dispatch_steps(dis_ctx* c, int n, bool fixed) {
+  const bool rx = c->y >= 0;
+  if (c->dim == 1) return rx ? run_steps<1, true>(c, n, fixed) : run_steps<1, false>(c, n, fixed);
+  return rx ? run_steps<2, true>(c, n, fixed) : run_steps<2, false>(c, n, fixed);
+}
+
+template <int DIM, bool RX>
+int do_unpack(dis_ctx* c, const double* src, int prim) {
+  k_unpack<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, c->d_pd, c->d_seg_cell,
+                                                                         src, c->q[0], c->T, prim);
+  CU(cudaGetLastError());
+  return DIS_OK;
+}
+
+template <int DIM, bool RX>
+int do_pack(dis_ctx* c, double* dst, int prim) {
+  const double* from = c->q[0];
+  if (prim) {
+    StepArgs a = base_args(c);
+    a.qsrc = c->q[0];
+    k_prim<DIM, RX><<<(unsigned)c->seg_prim.size(), SEG, 0, c->stream>>>(c->phys, a, c->d_seg_prim, 0);
+    from = c->W;
+  }
+  k_pack<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, from, dst, c->T);
+  CU(cudaGetLastError());
+  return DIS_OK;
+}
+
+MatDev to_dev(const dis_material& m) {
+  MatDev d{};
+  d.gamma = m.gamma;
+  d.pinf = m.p_inf;
+  d.einf = m.e_inf;
+  d.G = m.G;
+  d.sigy = m.sigma_y;
+  d.chi0 = m.chi0;
+  d.Q = m.Q;
+  d.cv = m.cv;
+  d.A = m.A;
+  d.Tact = m.T_act;
+  d.plastic = m.plastic;
+  d.reactive = m.reactive;
+  d.iGm1 = 1.0 / (m.gamma - 1.0);
+  d.gi = m.gamma * d.iGm1;
+  d.kap = m.gamma * m.p_inf * d.iGm1;
+  d.gG = m.gamma * m.G * d.iGm1;
+  d.GoG = m.G * d.iGm1;
+  d.JY = (m.plastic && m.G > 0) ? m.sigma_y / (std::sqrt(6.0) * m.G) : INFINITY;
+  return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dis_last_error(void) { return g_err.c_str(); }
+
+int dis_create(int dim, int n_patches, const dis_patch* patches, int reactive_material,
+               const dis_options* opt, void* stream, dis_ctx** out) {
+  if (!out) return fail(DIS_EINVAL, "dis_create: out is NULL");
+  *out = nullptr;
+  if (dim != 1 && dim != 2) return fail(DIS_EINVAL, "dis_create: dim must be 1 or 2 (got %d)", dim);
+  if (n_patches <= 0 || !patches) return fail(DIS_EINVAL, "dis_create: need at least one patch");
+  if (!opt) return fail(DIS_EINVAL, "dis_create: opt is NULL");
+  if (reactive_material < -1 || reactive_material > 1)
+    return fail(DIS_EINVAL, "dis_create: reactive_material must be -1, 0 or 1");
+  if (!(opt->cfl > 0.0 && opt->cfl <= 1.0)) return fail(DIS_EINVAL, "dis_create: cfl must be in (0, 1]");
+  if (opt->precision != DIS_FP64 && opt->precision != DIS_FP32_BULK)
+    return fail(DIS_EINVAL, "dis_create: unknown precision %d", opt->precision);
+  if (opt->precision == DIS_FP32_BULK)
+    return fail(DIS_EINVAL, "dis_create: FP32-bulk precision is not available in this build");
+  for (int p = 0; p < n_patches; ++p) {
+    const dis_patch& P = patches[p];
+    const int ny = dim == 2 ? P.ny : 1;
+    if (P.nx < 4 || ny < (dim == 2 ? 4 : 1) || !(P.dx > 0) || (dim == 2 && !(P.dy > 0)))
+      return fail(DIS_EINVAL, "dis_create: patch %d has bad size (nx %d ny %d dx %g dy %g)", p, P.nx,
+                  P.ny, P.dx, P.dy);
+    if ((long long)P.nx * ny > (1LL << 31))
+      return fail(DIS_EINVAL, "dis_create: patch %d is too large", p);
+    for (int k = 0; k < (dim == 2 ? 4 : 2); ++k)
+      if (P.bc[k] < 0 || P.bc[k] > 2) return fail(DIS_EINVAL, "dis_create: patch %d bad bc", p);
+  }
+  dis_ctx* c = new (std::nothrow) dis_ctx();
+  if (!c) return fail(DIS_ENOMEM, "dis_create: out of host memory");
+  c->dim = dim;
+  c->np = n_patches;
+  c->y = reactive_material;
+  c->nf = (dim == 2 ? 11 : 8) + (reactive_material >= 0 ? 1 : 0);
+  c->opt = *opt;
+  c->patches.assign(patches, patches + n_patches);
+  c->stream = (cudaStream_t)stream;
+  cudaGetDevice(&c->device);
+  c->phys.y = reactive_material;
+  c->phys.thinc = opt->thinc ? 1 : 0;
+  c->phys.cfl = opt->cfl;
+  layout(c);
+  *out = c;
+  return DIS_OK;
+}
+
+int dis_set_materials(dis_ctx* c, const dis_material* m, int n) {
+  if (!c || !m) return fail(DIS_EINVAL, "dis_set_materials: NULL argument");
+  if (n != 2) return fail(DIS_EINVAL, "dis_set_materials: exactly 2 materials are supported (got %d)", n);
+  for (int l = 0; l < 2; ++l) {
+    if (!(m[l].gamma > 1.0)) return fail(DIS_EINVAL, "dis_set_materials: gamma must be > 1");
+    if (m[l].G < 0 || m[l].p_inf < 0) return fail(DIS_EINVAL, "dis_set_materials: negative G or p_inf");
+    if (m[l].plastic < 0 || m[l].plastic > 2) return fail(DIS_EINVAL, "dis_set_materials: bad plastic");
+    if ((l == c->y) != (m[l].reactive != 0))
+      return fail(DIS_EINVAL, "dis_set_materials: reactive flag disagrees with the context");
+    if (m[l].reactive && (m[l].p_inf != 0 || m[l].G != 0 || !(m[l].cv > 0)))
+      return fail(DIS_EINVAL, "dis_set_materials: a reactive material must be an ideal gas with cv > 0");
+    c->phys.m[l] = to_dev(m[l]);
+  }
+  c->have_mats = true;
+  return DIS_OK;
+}
+
+size_t dis_workspace_bytes(const dis_ctx* c) {
+  if (!c) return 0;
+  return carve(const_cast<dis_ctx*>(c), nullptr);
+}
+
+size_t dis_state_bytes(const dis_ctx* c, int kind) {
+  (void)kind;
+  return c ? sizeof(double) * (size_t)c->nf * c->ncells : 0;
+}
+
+int dis_bind_workspace(dis_ctx* c, void* dev, size_t bytes) {
+  if (!c || !dev) return fail(DIS_EINVAL, "dis_bind_workspace: NULL argument");
+  if (((uintptr_t)dev) & 255) return fail(DIS_EINVAL, "dis_bind_workspace: pointer not 256-byte aligned");
+  const size_t need = carve(c, nullptr);
+  if (bytes < need) return fail(DIS_ENOMEM, "dis_bind_workspace: %zu bytes given, %zu needed", bytes, need);
+  if (c->ws_owned) cudaFree(c->ws);
+  c->ws = (char*)dev;
+  c->ws_bytes = bytes;
+  c->ws_owned = false;
+  c->ws_ready = false;
+  c->have_state = false;
+  return ensure_ws(c);
+}
+
+int dis_set_state(dis_ctx* c, int kind, const double* src, int src_on_device) {
+  if (!c || !src) return fail(DIS_EINVAL, "dis_set_state: NULL argument");
+  if (kind != DIS_CONSERVATIVE && kind != DIS_PRIMITIVE) return fail(DIS_EINVAL, "dis_set_state: bad kind");
+  if (!c->have_mats) return fail(DIS_ESTATE, "dis_set_state: set materials first");
+  int rc = ensure_ws(c);
+  if (rc) return rc;
+  const double* dsrc = src;
+  if (!src_on_device) {
+    CU(cudaMemcpyAsync(c->io, src, dis_state_bytes(c, kind), cudaMemcpyHostToDevice, c->stream));
+    dsrc = c->io;
+  }
+  const bool rx = c->y >= 0;
+  const int prim = kind == DIS_PRIMITIVE;
+  if (c->dim == 1) rc = rx ? do_unpack<1, true>(c, dsrc, prim) : do_unpack<1, false>(c, dsrc, prim);
+  else rc = rx ? do_unpack<2, true>(c, dsrc, prim) : do_unpack<2, false>(c, dsrc, prim);
+  if (rc) return rc;
+  if (!src_on_device) CU(cudaStreamSynchronize(c->stream));  // the host buffer may be reused
+  c->have_state = true;
+  return DIS_OK;
+}
+
+int dis_get_state(dis_ctx* c, int kind, double* dst, int dst_on_device) {
+  if (!c || !dst) return fail(DIS_EINVAL, "dis_get_state: NULL argument");
+  if (kind != DIS_CONSERVATIVE && kind != DIS_PRIMITIVE) return fail(DIS_EINVAL, "dis_get_state: bad kind");
+  if (!c->have_state) return fail(DIS_ESTATE, "dis_get_state: no state loaded");
+  double* ddst = dst_on_device ? dst : c->io;
+  const bool rx = c->y >= 0;
+  const int prim = kind == DIS_PRIMITIVE;
+  int rc;
+  if (c->dim == 1) rc = rx ? do_pack<1, true>(c, ddst, prim) : do_pack<1, false>(c, ddst, prim);
+  else rc = rx ? do_pack<2, true>(c, ddst, prim) : do_pack<2, false>(c, ddst, prim);
+  if (rc) return rc;
+  if (!dst_on_device) {
+    CU(cudaMemcpyAsync(dst, c->io, dis_state_bytes(c, kind), cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+  }
+  return DIS_OK;
+}
+
+int dis_step(dis_ctx* c, int n_steps, double* dt_out) {
+  if (!c) return fail(DIS_EINVAL, "dis_step: NULL context");
+  if (n_steps < 0) return fail(DIS_EINVAL, "dis_step: negative step count");
+  if (!c->have_state) return fail(DIS_ESTATE, "dis_step: no state loaded");
+  int rc = dispatch_steps(c, n_steps, false);
+  if (rc) return rc;
+  if (dt_out && n_steps > 0) {
+    CU(cudaMemcpyAsync(dt_out, c->dtlast, sizeof(double) * c->np, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+  }
+  return DIS_OK;
+}
+
+int dis_step_fixed_dt(dis_ctx* c, int n_steps, const double* dt) {
+  if (!c || !dt) return fail(DIS_EINVAL, "dis_step_fixed_dt: NULL argument");
+  if (n_steps < 0) return fail(DIS_EINVAL, "dis_step_fixed_dt: negative step count");
+  if (!c->have_state) return fail(DIS_ESTATE, "dis_step_fixed_dt: no state loaded");
+  for (int p = 0; p < c->np; ++p)
+    if (!(dt[p] > 0.0) || !std::isfinite(dt[p])) return fail(DIS_EINVAL, "dis_step_fixed_dt: bad dt[%d]", p);
+  CU(cudaMemcpyAsync(c->dtfix, dt, sizeof(double) * c->np, cudaMemcpyHostToDevice, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  return dispatch_steps(c, n_steps, true);
+}
+
+int dis_check(dis_ctx* c, int* bad_patch, int* bad_cell) {
+  if (!c) return fail(DIS_EINVAL, "dis_check: NULL context");
+  if (!c->ws_ready) return DIS_OK;
+  int st[4] = {0, 0, 0, 0};
+  CU(cudaMemcpyAsync(st, c->status, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  CU(cudaMemsetAsync(c->status, 0, sizeof st, c->stream));
+  if (bad_patch) *bad_patch = st[0] ? st[1] : -1;
+  if (bad_cell) *bad_cell = st[0] ? st[2] : -1;
+  if (st[0]) return fail(DIS_ENONPHYSICAL, "non-physical state in patch %d cell %d", st[1], st[2]);
+  return DIS_OK;
+}
+
+long long dis_last_launches(const dis_ctx* c) { return c ? c->launches : 0; }
+
+void dis_destroy(dis_ctx* c) {
+  if (!c) return;
+  if (c->ws_owned && c->ws) cudaFree(c->ws);
+  delete c;
+}
+
+}  // extern "C"

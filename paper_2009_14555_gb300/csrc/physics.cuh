@@ -1,0 +1,308 @@
+// physics.cuh - device closures of the diffuse-interface step (sm_103a).
+//
+// Written for the GPU from the paper's equations (arXiv 2009.14555), in the
+// reduced forms that a stiffened-gas Mie-Grueneisen closure with constant
+// shear modulus allows:
+//   * mixture pressure (Appendix B pressure function, Section 2.2 mixture rules):
+//       p = [rhoE - KE - sum_l phi_l (kap_l + gG_l J2) - sum_l ar_l e_inf,l
+//            + Q_y (ar_y - arl)] / xi,     xi = sum_l phi_l / Gamma_l,
+//     kap_l = gamma_l p_inf,l / Gamma_l, gG_l = gamma_l G_l / Gamma_l (shear
+//     energy G J2 / rho enters the reference curves of the MG form);
+//   * rho xi c^2 = sum_l phi_l (gamma_l p + gamma_l p_inf,l + gamma_l G_l J2) / Gamma_l
+//     (frozen mixture sound speed; no phasic density needed), c_L^2 = c^2 + 4/3 G/rho;
+//   * dev(H) = dev(1/4 (B - B^-1)), B = V V^T, in plane-strain block form
+//     (Bazant approximation, Section 3.2), J2 = |dev H|^2;
+//   * sigma = -p I + 2 G_mix dev(H);
+//   * HLLC-type elastic Riemann solver (reading of the HLLD of Section 3.1),
+//     star stretch tensor rows scaled by r^-2/3 (normal) and r^1/3 (others),
+//     r = (S_K - u_nK) / (S_K - S*);
+//   * THINC edge values and BVD choice (Appendix A);
+//   * plastic update with the radial-return root of the objective and the
+//     first Pade approximant (Section 3.2); RK4 Arrhenius reaction (Section 3.3).
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace dis {
+
+constexpr int NG = 3;  // ghost layers: a face's BVD choice reaches 3 cells out
+
+struct MatDev {
+  double gamma, pinf, einf, G, sigy, chi0, Q, cv, A, Tact;
+  int plastic, reactive;
+  double iGm1;  // 1 / (gamma - 1)
+  double gi;    // gamma / (gamma - 1)
+  double kap;   // gamma p_inf / (gamma - 1)
+  double gG;    // gamma G / (gamma - 1)
+  double GoG;   // G / (gamma - 1)
+  double JY;    // yield strain invariant sigma_y / (sqrt(6) G)
+};
+
+struct Phys {
+  MatDev m[2];
+  int y;      // reactive material (0/1) or -1
+  int thinc;  // THINC-BVD steepening on phi1
+  double cfl;
+};
+
+// Field slots of the conservative and primitive states (same positions).
+template <int DIM, bool RX>
+struct Lay;
+template <bool RX>
+struct Lay<1, RX> {
+  static constexpr int PHI = 0, A1 = 1, A2 = 2, MX = 3, MY = -1, E = 4, V11 = 5, V12 = -1, V21 = -1,
+                       V22 = 6, V33 = 7, AL = RX ? 8 : -1, NF = RX ? 9 : 8;
+  static constexpr int NX_EXTRA = 2;  // x-face extras: u_n, V11
+};
+template <bool RX>
+struct Lay<2, RX> {
+  static constexpr int PHI = 0, A1 = 1, A2 = 2, MX = 3, MY = 4, E = 5, V11 = 6, V12 = 7, V21 = 8,
+                       V22 = 9, V33 = 10, AL = RX ? 11 : -1, NF = RX ? 12 : 11;
+  static constexpr int NX_EXTRA = 3;  // face extras: u_n, V_n1, V_n2
+};
+
+struct Prim {
+  double phi, r1, r2, u, v, p, V11, V12, V21, V22, V33, lam;
+};
+
+struct Strain {
+  double H11, H12, H22, H33, J2;
+};
+
+__device__ __forceinline__ Strain strain_of(double a, double b, double c, double d, double e) {
+  const double B11 = a * a + b * b, B12 = a * c + b * d, B22 = c * c + d * d, B33 = e * e;
+  const double idet = 1.0 / (B11 * B22 - B12 * B12);
+  const double M11 = 0.25 * (B11 - B22 * idet);
+  const double M22 = 0.25 * (B22 - B11 * idet);
+  const double M12 = 0.25 * (B12 + B12 * idet);
+  const double M33 = 0.25 * (B33 - 1.0 / B33);
+  const double t3 = (M11 + M22 + M33) * (1.0 / 3.0);
+  Strain s;
+  s.H11 = M11 - t3;
+  s.H22 = M22 - t3;
+  s.H33 = M33 - t3;
+  s.H12 = M12;
+  s.J2 = s.H11 * s.H11 + s.H22 * s.H22 + s.H33 * s.H33 + 2.0 * s.H12 * s.H12;
+  return s;
+}
+
+// The pieces of the pressure function that do not depend on the internal energy.
+__device__ __forceinline__ double ref_energy(const Phys& P, double phi1, double ar1, double ar2,
+                                             double arl, double J2) {
+  const double phi2 = 1.0 - phi1;
+  double s = phi1 * (P.m[0].kap + P.m[0].gG * J2) + phi2 * (P.m[1].kap + P.m[1].gG * J2) +
+             ar1 * P.m[0].einf + ar2 * P.m[1].einf;
+  if (P.y >= 0) {
+    const double ary = P.y == 0 ? ar1 : ar2;
+    s -= P.m[P.y].Q * (ary - arl);
+  }
+  return s;
+}
+
+__device__ __forceinline__ double xi_of(const Phys& P, double phi1) {
+  return phi1 * P.m[0].iGm1 + (1.0 - phi1) * P.m[1].iGm1;
+}
+
+// rho c_L^2 for a state (frozen mixture sound speed plus 4/3 G_mix).
+__device__ __forceinline__ double cL2_of(const Phys& P, double phi1, double rho, double p, double J2) {
+  const double phi2 = 1.0 - phi1;
+  const double xi = xi_of(P, phi1);
+  const double a = phi1 * (P.m[0].gi * p + P.m[0].kap + P.m[0].gG * J2) +
+                   phi2 * (P.m[1].gi * p + P.m[1].kap + P.m[1].gG * J2);
+  const double Gm = (phi1 * P.m[0].GoG + phi2 * P.m[1].GoG) / xi;
+  return (a / xi + (4.0 / 3.0) * Gm) / rho;
+}
+
+__device__ __forceinline__ double Gmix_of(const Phys& P, double phi1) {
+  return (phi1 * P.m[0].GoG + (1.0 - phi1) * P.m[1].GoG) / xi_of(P, phi1);
+}
+
+__device__ __forceinline__ double minmod(double a, double b) {
+  return (a * b > 0.0) ? copysign(fmin(fabs(a), fabs(b)), a) : 0.0;
+}
+
+// MUSCL and THINC edge candidates of phi in one cell (Appendix A).
+struct Cand {
+  double mL, mR, tL, tR;
+};
+
+__device__ __forceinline__ Cand phi_cand(double qm, double qc, double qp, double beta, bool thinc) {
+  Cand c;
+  const double s = minmod(qc - qm, qp - qc);
+  c.mL = qc - 0.5 * s;
+  c.mR = qc + 0.5 * s;
+  c.tL = c.mL;
+  c.tR = c.mR;
+  if (thinc) {
+    const double qmin = fmin(qm, qp);
+    const double jump = fmax(qm, qp) - qmin;
+    const double C = (qc - qmin + 1e-20) / (jump + 1e-20);
+    if (C > 1e-5 && C < 1.0 - 1e-5 && (qp - qc) * (qc - qm) > 0.0) {
+      const double th = (qp - qm) > 0.0 ? 1.0 : -1.0;
+      const double B = exp(th * beta * (2.0 * C - 1.0));
+      const double tb = tanh(beta);
+      const double A = (B / cosh(beta) - 1.0) / tb;
+      c.tL = qmin + 0.5 * jump * (1.0 + th * A);
+      c.tR = qmin + 0.5 * jump * (1.0 + th * (tb + A) / (1.0 + A * tb));
+    }
+  }
+  return c;
+}
+
+// BVD choice for the middle cell: THINC only if its total boundary variation
+// is strictly smaller (ties keep MUSCL).
+__device__ __forceinline__ void bvd(const Cand& km, const Cand& k, const Cand& kp, double& L,
+                                    double& R) {
+  const double tT = fmin(fabs(km.mR - k.tL), fabs(km.tR - k.tL)) +
+                    fmin(fabs(k.tR - kp.mL), fabs(k.tR - kp.tL));
+  const double tM = fmin(fabs(km.mR - k.mL), fabs(km.tR - k.mL)) +
+                    fmin(fabs(k.mR - kp.mL), fabs(k.mR - kp.tL));
+  const bool useT = tT < tM;
+  L = useT ? k.tL : k.mL;
+  R = useT ? k.tR : k.mR;
+}
+
+// Thermodynamic face state for the Riemann solver.  Direction: n = normal
+// velocity component, t = tangential; Vn* = row of V along the normal.
+struct FState {
+  double phi, ar1, ar2, arl, rho, un, ut, rhoE, snn, snt, cL;
+  double V11, V12, V21, V22, V33;
+};
+
+template <int DIR>
+__device__ __forceinline__ FState face_state(const Phys& P, const Prim& w) {
+  FState s;
+  const Strain st = strain_of(w.V11, w.V12, w.V21, w.V22, w.V33);
+  s.phi = w.phi;
+  s.ar1 = w.phi * w.r1;
+  s.ar2 = (1.0 - w.phi) * w.r2;
+  s.rho = s.ar1 + s.ar2;
+  s.arl = 0.0;
+  if (P.y >= 0) s.arl = (P.y == 0 ? s.ar1 : s.ar2) * w.lam;
+  const double xi = xi_of(P, w.phi);
+  s.rhoE = xi * w.p + ref_energy(P, w.phi, s.ar1, s.ar2, s.arl, st.J2) +
+           0.5 * s.rho * (w.u * w.u + w.v * w.v);
+  const double Gm = Gmix_of(P, w.phi);
+  if (DIR == 0) {
+    s.un = w.u;
+    s.ut = w.v;
+    s.snn = -w.p + 2.0 * Gm * st.H11;
+  } else {
+    s.un = w.v;
+    s.ut = w.u;
+    s.snn = -w.p + 2.0 * Gm * st.H22;
+  }
+  s.snt = 2.0 * Gm * st.H12;
+  s.cL = cL2_of(P, w.phi, s.rho, w.p, st.J2);  // squared here; k_flux takes the root
+  s.V11 = w.V11;
+  s.V12 = w.V12;
+  s.V21 = w.V21;
+  s.V22 = w.V22;
+  s.V33 = w.V33;
+  return s;
+}
+
+// Output of one face: conservative fluxes plus the face state at x/t = 0.
+struct FaceOut {
+  double Far1, Far2, Farl, Fmn, Fmt, FE;
+  double phi, un, ut, V11, V12, V21, V22, V33;
+};
+
+template <int DIR>
+__device__ __forceinline__ FaceOut hllc(const FState& L, const FState& R) {
+  const double SL = fmin(L.un - L.cL, R.un - R.cL);
+  const double SR = fmax(L.un + L.cL, R.un + R.cL);
+  const double mL = L.rho * (SL - L.un);
+  const double mR = R.rho * (SR - R.un);
+  const double Ss = (L.snn - R.snn + mL * L.un - mR * R.un) / (mL - mR);
+  FaceOut o;
+  const FState* K;
+  double S;
+  bool star;
+  if (SL >= 0.0) {
+    K = &L; S = SL; star = false;
+  } else if (Ss >= 0.0) {
+    K = &L; S = SL; star = true;
+  } else if (SR >= 0.0) {
+    K = &R; S = SR; star = true;
+  } else {
+    K = &R; S = SR; star = false;
+  }
+  const double un = K->un, ut = K->ut;
+  // physical flux of side K
+  double Far1 = K->ar1 * un, Far2 = K->ar2 * un, Farl = K->arl * un;
+  double Fmn = K->rho * un * un - K->snn;
+  double Fmt = K->rho * ut * un - K->snt;
+  double FE = K->rhoE * un - (un * K->snn + ut * K->snt);
+  o.phi = K->phi;
+  o.ut = ut;
+  if (!star) {
+    o.un = un;
+    o.V11 = K->V11; o.V12 = K->V12; o.V21 = K->V21; o.V22 = K->V22; o.V33 = K->V33;
+  } else {
+    const double r = (S - un) / (S - Ss);
+    const double m = K->rho * (S - un);
+    const double snn_s = K->snn - m * (Ss - un);
+    const double E_s = (K->rhoE * (S - un) + Ss * snn_s - un * K->snn) / (S - Ss);
+    Far1 += S * (r - 1.0) * K->ar1;
+    Far2 += S * (r - 1.0) * K->ar2;
+    Farl += S * (r - 1.0) * K->arl;
+    Fmn += S * (r * K->rho * Ss - K->rho * un);
+    Fmt += S * (r - 1.0) * K->rho * ut;
+    FE += S * (E_s - K->rhoE);
+    o.un = Ss;
+    const double c1 = cbrt(r);       // r^(1/3): rows off the normal
+    const double cn = 1.0 / (c1 * c1);  // r^(-2/3): row along the normal
+    if (DIR == 0) {
+      o.V11 = cn * K->V11; o.V12 = cn * K->V12;
+      o.V21 = c1 * K->V21; o.V22 = c1 * K->V22;
+    } else {
+      o.V11 = c1 * K->V11; o.V12 = c1 * K->V12;
+      o.V21 = cn * K->V21; o.V22 = cn * K->V22;
+    }
+    o.V33 = c1 * K->V33;
+  }
+  o.Far1 = Far1; o.Far2 = Far2; o.Farl = Farl; o.Fmn = Fmn; o.Fmt = Fmt; o.FE = FE;
+  return o;
+}
+
+// Plastic update of Section 3.2 on one cell's stretch tensor (in place).
+__device__ __forceinline__ void plastic(const Phys& P, double phi1, double dt, double& V11,
+                                        double& V12, double& V21, double& V22, double& V33) {
+  const Strain s = strain_of(V11, V12, V21, V22, V33);
+  const double Js = sqrt(s.J2);
+  double num = 0.0, den = 0.0;
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    const MatDev& m = P.m[l];
+    const double ph = l == 0 ? phi1 : 1.0 - phi1;
+    double Jl;
+    if (m.G == 0.0) {
+      Jl = 0.0;  // a fluid keeps no shear strain
+    } else if (m.plastic == 1) {
+      Jl = fmin(Js, m.JY);
+    } else if (m.plastic == 2) {
+      Jl = Js > m.JY ? fmax(Js - dt * m.chi0, m.JY) : Js;
+    } else {
+      Jl = Js;
+    }
+    num += ph * m.iGm1 * Jl;
+    den += ph * m.iGm1;
+  }
+  const double Jn = num / den;
+  const double sc = Js > 0.0 ? Jn / Js : 0.0;
+  const double h11 = sc * s.H11, h12 = sc * s.H12, h22 = sc * s.H22, h33 = sc * s.H33;
+  // V = (I - H/2)^-1 (I + H/2) on the in-plane block and the zz entry
+  const double x11 = 1.0 - 0.5 * h11, x12 = -0.5 * h12, x22 = 1.0 - 0.5 * h22;
+  const double y11 = 1.0 + 0.5 * h11, y12 = 0.5 * h12, y22 = 1.0 + 0.5 * h22;
+  const double id = 1.0 / (x11 * x22 - x12 * x12);
+  const double i11 = x22 * id, i12 = -x12 * id, i22 = x11 * id;
+  V11 = i11 * y11 + i12 * y12;
+  V12 = i11 * y12 + i12 * y22;
+  V21 = i12 * y11 + i22 * y12;
+  V22 = i12 * y12 + i22 * y22;
+  V33 = (1.0 + 0.5 * h33) / (1.0 - 0.5 * h33);
+}
+
+}  // namespace dis

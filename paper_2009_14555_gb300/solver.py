@@ -1,0 +1,132 @@
+"""High-level solver over the C ABI: one context = one batch of patches.
+
+PyTorch provides device memory (the workspace is a torch uint8 tensor lent
+to the library) and the stream; all arithmetic runs in libdis.so.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _material(m: dict) -> L.DisMaterial:
+    return L.DisMaterial(m["gamma"], m["p_inf"], m["e_inf"], m["G"], m["plastic"], m["sigma_y"],
+                         m["chi0"], m["reactive"], m["Q"], m["cv"], m["A"], m["T_act"])
+
+
+def _patch(p, dim) -> L.DisPatch:
+    bc = (ctypes.c_int32 * 4)(*[int(b) for b in p.bc])
+    return L.DisPatch(p.nx, p.ny if dim == 2 else 1, p.dx, p.dy if dim == 2 else 1.0, bc)
+
+
+def pack(arrays) -> np.ndarray:
+    """Concatenate per-patch (nfields, ny, nx) arrays into the packed layout."""
+    return np.ascontiguousarray(np.concatenate([np.asarray(a, np.float64).reshape(-1) for a in arrays]))
+
+
+def unpack(flat, shapes):
+    out, o = [], 0
+    for s in shapes:
+        n = int(np.prod(s))
+        out.append(flat[o:o + n].reshape(s))
+        o += n
+    return out
+
+
+class Solver:
+    """Diffuse-interface step on a batch of patches (see include/dis.h)."""
+
+    def __init__(self, dim, patches, materials, reactive_material=-1, cfl=0.8, thinc=False,
+                 precision="fp64", device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("Solver needs a CUDA device (no CPU fallback)")
+        dev = torch.device(device or "cuda")
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        self.device = dev
+        torch.cuda.set_device(self.device)
+        self.dim = dim
+        self.patches = list(patches)
+        self.reactive = reactive_material >= 0
+        self.nf = (11 if dim == 2 else 8) + (1 if self.reactive else 0)
+        prec = {"fp64": L.DIS_FP64, "fp32_bulk": L.DIS_FP32_BULK}[precision]
+        opts = L.DisOptions(float(cfl), int(bool(thinc)), prec)
+        self.stream = torch.cuda.current_stream(self.device)
+        self.ctx = L.dis_create(dim, [_patch(p, dim) for p in self.patches], reactive_material, opts,
+                                self.stream.cuda_stream)
+        L.dis_set_materials(self.ctx, [_material(m) for m in materials])
+        nbytes = L.dis_workspace_bytes(self.ctx)
+        self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self._ws.data_ptr()
+        aligned = (base + 255) & ~255
+        L.dis_bind_workspace(self.ctx, aligned, nbytes)
+        self.shapes = [(self.nf, p.ny if dim == 2 else 1, p.nx) for p in self.patches]
+        self.state_numel = sum(int(np.prod(s)) for s in self.shapes)
+
+    @classmethod
+    def from_workload(cls, wl, precision="fp64", **kw):
+        return cls(wl.dim, wl.patches, wl.materials, wl.reactive_material, wl.cfl, wl.thinc,
+                   precision, **kw)
+
+    # -- state ----------------------------------------------------------------
+    def set_state(self, x, kind=L.DIS_PRIMITIVE):
+        if isinstance(x, torch.Tensor) and x.is_cuda:
+            x = x.contiguous().to(torch.float64)
+            assert x.numel() == self.state_numel
+            L.dis_set_state(self.ctx, kind, x.data_ptr(), True)
+            self._keep = x
+        else:
+            x = np.ascontiguousarray(np.asarray(x, np.float64).reshape(-1))
+            assert x.size == self.state_numel, (x.size, self.state_numel)
+            L.dis_set_state(self.ctx, kind, x.ctypes.data, False)
+
+    def set_prim(self, prim_arrays):
+        self.set_state(pack(prim_arrays), L.DIS_PRIMITIVE)
+
+    def get_state(self, kind=L.DIS_CONSERVATIVE, out=None):
+        """Packed state as a numpy array (host) or into a CUDA tensor `out`."""
+        if out is not None:
+            assert out.is_cuda and out.dtype == torch.float64 and out.numel() == self.state_numel
+            L.dis_get_state(self.ctx, kind, out.data_ptr(), True)
+            return out
+        h = np.empty(self.state_numel, np.float64)
+        L.dis_get_state(self.ctx, kind, h.ctypes.data, False)
+        return h
+
+    def get_arrays(self, kind=L.DIS_CONSERVATIVE):
+        return unpack(self.get_state(kind), self.shapes)
+
+    # -- stepping ---------------------------------------------------------------
+    def step(self, n=1, return_dt=False):
+        if return_dt:
+            dt = np.empty(len(self.patches), np.float64)
+            L.dis_step(self.ctx, n, dt.ctypes.data)
+            return dt
+        L.dis_step(self.ctx, n, None)
+        return None
+
+    def step_fixed_dt(self, n, dt):
+        dt = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, np.float64), (len(self.patches),)))
+        L.dis_step_fixed_dt(self.ctx, n, dt.ctypes.data)
+
+    def check(self):
+        return L.dis_check(self.ctx)
+
+    @property
+    def launches(self):
+        return L.dis_last_launches(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            L.dis_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

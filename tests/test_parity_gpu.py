@@ -1,0 +1,128 @@
+"""GPU FP64 path against the float64 CPU oracle, through the C ABI.
+
+Bar: per-field relative L1 <= 1e-10 after the stated number of steps (the
+FP64 parity target).  Sizes are small enough for the oracle to finish in
+seconds while spanning several 128-cell segments and a ragged tail.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2009_14555_gb300 import workloads as W
+from tests.parity_util import cons_l1, oracle_prim, oracle_run, prim_l1
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+def gpu_run(wl, steps, dt_fixed=None, precision="fp64"):
+    from paper_2009_14555_gb300.solver import Solver
+    s = Solver.from_workload(wl, precision=precision)
+    s.set_prim([p.prim for p in wl.patches])
+    dts = []
+    for _ in range(steps):
+        if dt_fixed is None:
+            dts.append(s.step(1, return_dt=True))
+        else:
+            s.step_fixed_dt(1, dt_fixed)
+    rc, bp, bc = s.check()
+    assert rc == 0, (bp, bc)
+    out = s.get_arrays()
+    prim = s.get_arrays(kind=1)
+    s.close()
+    return out, prim, np.array(dts)
+
+
+def assert_parity(wl, steps, tol=TOL):
+    g, gp, gdt = gpu_run(wl, steps)
+    o, odt = oracle_run(wl, steps)
+    for k in range(len(o)):
+        err = cons_l1(wl, g[k], o[k])
+        assert err.max() <= tol, (k, err)
+        np.testing.assert_allclose(gdt[:, k], np.array(odt[k]), rtol=1e-11)
+    op = oracle_prim(wl, o)
+    for k in range(len(o)):
+        perr = prim_l1(wl, gp[k], op[k], o[k])
+        assert max(perr.values()) <= tol, (k, perr)
+
+
+def test_1d_solid_gas_100_steps():
+    assert_parity(W.solid_gas_1d(1000, steps=100), 100)
+
+
+def test_1d_solid_gas_thinc():
+    wl = W.solid_gas_1d(300, steps=60)
+    wl.thinc = True
+    assert_parity(wl, 60)
+
+
+@pytest.mark.parametrize("bc", [W.BC_PERIODIC, W.BC_REFLECTIVE])
+def test_1d_boundaries(bc):
+    # states chosen so that no interface or wall opens a cavity
+    if bc == W.BC_PERIODIC:
+        left, right = dict(mat=0, rho=8000.0, u=100.0, p=1e5), dict(mat=1, rho=1.2, u=100.0, p=3e5)
+    else:
+        left, right = dict(mat=0, rho=8000.0, u=200.0, p=1e5), dict(mat=1, rho=1.2, u=-300.0, p=3e5)
+    wl = W.riemann_1d(131, left, right, bc=bc, thinc=False)
+    assert_parity(wl, 40)
+
+
+def test_2d_shock_disc_small():
+    wl = W.shock_disc_2d(40, steps=30)
+    assert_parity(wl, 30)
+
+
+def test_2d_shock_disc_ragged_reflective():
+    wl = W.shock_disc_2d(36, steps=20)
+    p = wl.patches[0]
+    p.prim = p.prim[:, :, :]  # 36 x 36, not a multiple of the 128-cell segment
+    p.bc = (W.BC_TRANSMISSIVE, W.BC_REFLECTIVE, W.BC_REFLECTIVE, W.BC_PERIODIC)
+    assert_parity(wl, 20)
+
+
+def test_2d_reactive_small():
+    wl = W.reactive_plate_2d(64, 32, steps=20)
+    # make the hot spot large enough to react on this grid
+    assert_parity(wl, 20)
+
+
+def test_batched_1d_subset():
+    wl = W.batched_riemann_1d(12, seed=3, steps=40, nmin=16, nmax=300)
+    assert_parity(wl, 40)
+
+
+def test_fixed_dt_matches_oracle():
+    wl = W.solid_gas_1d(257, steps=10)
+    g, _, _ = gpu_run(wl, 10, dt_fixed=1e-7)
+    o, _ = oracle_run(wl, 10, dt_list=[[1e-7] * 10])
+    assert cons_l1(wl, g[0], o[0]).max() <= TOL
+
+
+def test_conservative_roundtrip_bit_exact():
+    from paper_2009_14555_gb300.solver import Solver
+    wl = W.shock_disc_2d(24, steps=1)
+    s = Solver.from_workload(wl)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(s.state_numel)
+    s.set_state(x, kind=0)
+    y = s.get_state(kind=0)
+    assert np.array_equal(x, y)
+    xd = torch.tensor(x, device="cuda")
+    s.set_state(xd, kind=0)
+    out = torch.empty_like(xd)
+    s.get_state(kind=0, out=out)
+    assert torch.equal(out, xd)
+    s.close()
+
+
+def test_nonphysical_state_is_flagged():
+    from paper_2009_14555_gb300.solver import Solver
+    wl = W.solid_gas_1d(64, steps=1)
+    s = Solver.from_workload(wl)
+    prim = wl.patches[0].prim.copy()
+    prim[4, 0, 10] = -1e12  # impossible pressure: the step must flag, not hang or fault
+    s.set_prim([prim])
+    s.step(1)
+    rc, bp, bc = s.check()
+    assert rc == -4 and bp == 0
+    s.close()
