@@ -79,6 +79,12 @@ struct dis_ctx {
   PatchDev* d_pd = nullptr;
   int4 *d_seg_prim = nullptr, *d_seg_fx = nullptr, *d_seg_fy = nullptr, *d_seg_cell = nullptr;
   long long launches = 0;
+  // one captured time step per dt mode (0: CFL, 1: prescribed), replayed per step
+  cudaStream_t cap = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  long long graph_launches[2] = {0, 0};
+  bool use_graphs = true;
 };
 
 namespace {
@@ -218,8 +224,10 @@ StepArgs base_args(dis_ctx* c) {
   return a;
 }
 
+// Enqueue the kernels of one time step on stream `st`; returns the number of
+// kernel launches.
 template <int DIM, bool RX>
-int run_steps(dis_ctx* c, int n_steps, bool fixed) {
+long long launch_step(dis_ctx* c, cudaStream_t st, bool fixed) {
   StepArgs a = base_args(c);
   a.dtfix = fixed ? c->dtfix : nullptr;
   const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
@@ -227,28 +235,60 @@ int run_steps(dis_ctx* c, int n_steps, bool fixed) {
   const unsigned np = (unsigned)c->seg_prim.size(), nfx = (unsigned)c->seg_fx.size(),
                  nfy = (unsigned)c->seg_fy.size(), nc = (unsigned)c->seg_cell.size();
   long long launches = 0;
-  for (int s = 0; s < n_steps; ++s) {
-    if (!fixed) CU(cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, c->stream));
-    for (int st = 0; st < 3; ++st) {
-      a.qsrc = st == 0 ? c->q[0] : c->q[1];
-      a.qn = c->q[0];
-      a.qdst = st == 2 ? c->q[0] : c->q[1];
-      a.a = ca[st];
-      a.b = cb[st];
-      a.last = st == 2;
-      k_prim<DIM, RX><<<np, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_prim, (!fixed && st == 0) ? 1 : 0);
-      k_flux<DIM, RX, 0><<<nfx, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_fx);
-      launches += 2;
-      if constexpr (DIM == 2) {
-        k_flux<DIM, RX, 1><<<nfy, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_fy);
-        ++launches;
-      }
-      k_update<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_cell);
+  if (!fixed) cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, st);
+  for (int stg = 0; stg < 3; ++stg) {
+    a.qsrc = stg == 0 ? c->q[0] : c->q[1];
+    a.qn = c->q[0];
+    a.qdst = stg == 2 ? c->q[0] : c->q[1];
+    a.a = ca[stg];
+    a.b = cb[stg];
+    a.last = stg == 2;
+    k_prim<DIM, RX><<<np, SEG, 0, st>>>(c->phys, a, c->d_seg_prim, (!fixed && stg == 0) ? 1 : 0);
+    k_flux<DIM, RX, 0><<<nfx, SEG, 0, st>>>(c->phys, a, c->d_seg_fx);
+    launches += 2;
+    if constexpr (DIM == 2) {
+      k_flux<DIM, RX, 1><<<nfy, SEG, 0, st>>>(c->phys, a, c->d_seg_fy);
       ++launches;
     }
+    k_update<DIM, RX><<<nc, SEG, 0, st>>>(c->phys, a, c->d_seg_cell);
+    ++launches;
   }
-  CU(cudaGetLastError());
-  c->launches = launches;
+  return launches;
+}
+
+template <int DIM, bool RX>
+int run_steps(dis_ctx* c, int n_steps, bool fixed) {
+  const int mode = fixed ? 1 : 0;
+  if (!c->use_graphs) {
+    long long l = 0;
+    for (int s = 0; s < n_steps; ++s) l += launch_step<DIM, RX>(c, c->stream, fixed);
+    CU(cudaGetLastError());
+    c->launches = l;
+    return DIS_OK;
+  }
+  if (!c->cap) {
+    CU(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    CU(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+  }
+  if (!c->graph[mode]) {
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    const long long l = launch_step<DIM, RX>(c, c->cap, fixed);
+    const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+    if (e != cudaSuccess) return fail(DIS_ECUDA, "step capture failed: %s", cudaGetErrorString(e));
+    const cudaError_t e2 = cudaGraphInstantiate(&c->graph[mode], g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) return fail(DIS_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e2));
+    c->graph_launches[mode] = l;
+  }
+  // order the captured steps after prior work on the caller's stream and vice versa
+  CU(cudaEventRecord(c->ev_in, c->stream));
+  CU(cudaStreamWaitEvent(c->cap, c->ev_in, 0));
+  for (int s = 0; s < n_steps; ++s) CU(cudaGraphLaunch(c->graph[mode], c->cap));
+  CU(cudaEventRecord(c->ev_out, c->cap));
+  CU(cudaStreamWaitEvent(c->stream, c->ev_out, 0));
+  c->launches = c->graph_launches[mode] * n_steps;
   return DIS_OK;
 }
 
@@ -385,6 +425,11 @@ int dis_bind_workspace(dis_ctx* c, void* dev, size_t bytes) {
   const size_t need = carve(c, nullptr);
   if (bytes < need) return fail(DIS_ENOMEM, "dis_bind_workspace: %zu bytes given, %zu needed", bytes, need);
   if (c->ws_owned) cudaFree(c->ws);
+  for (int m = 0; m < 2; ++m)
+    if (c->graph[m]) {
+      cudaGraphExecDestroy(c->graph[m]);
+      c->graph[m] = nullptr;
+    }
   c->ws = (char*)dev;
   c->ws_bytes = bytes;
   c->ws_owned = false;
@@ -473,6 +518,12 @@ long long dis_last_launches(const dis_ctx* c) { return c ? c->launches : 0; }
 
 void dis_destroy(dis_ctx* c) {
   if (!c) return;
+  if (c->cap) cudaStreamSynchronize(c->cap);
+  for (int m = 0; m < 2; ++m)
+    if (c->graph[m]) cudaGraphExecDestroy(c->graph[m]);
+  if (c->ev_in) cudaEventDestroy(c->ev_in);
+  if (c->ev_out) cudaEventDestroy(c->ev_out);
+  if (c->cap) cudaStreamDestroy(c->cap);
   if (c->ws_owned && c->ws) cudaFree(c->ws);
   delete c;
 }

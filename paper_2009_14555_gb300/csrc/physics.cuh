@@ -13,9 +13,11 @@
 //   * dev(H) = dev(1/4 (B - B^-1)), B = V V^T, in plane-strain block form
 //     (Bazant approximation, Section 3.2), J2 = |dev H|^2;
 //   * sigma = -p I + 2 G_mix dev(H);
-//   * HLLC-type elastic Riemann solver (reading of the HLLD of Section 3.1),
-//     star stretch tensor rows scaled by r^-2/3 (normal) and r^1/3 (others),
-//     r = (S_K - u_nK) / (S_K - S*);
+//   * HLLD-type elastic Riemann solver (reading of the HLLD of Section 3.1):
+//     longitudinal waves S_L, S_R, shear waves S* -/+ c_s, contact S*; star
+//     stretch tensor rows scaled by r^-2/3 (normal) and r^1/3 (others),
+//     r = (S_K - u_nK) / (S_K - S*); shear jumps add w x (normal row) to the
+//     tangential row, w = (u_t,K - u_t**) / (S*_K - S*);
 //   * THINC edge values and BVD choice (Appendix A);
 //   * plastic update with the radial-return root of the objective and the
 //     first Pade approximant (Section 3.2); RK4 Arrhenius reaction (Section 3.3).
@@ -166,7 +168,7 @@ __device__ __forceinline__ void bvd(const Cand& km, const Cand& k, const Cand& k
 // Thermodynamic face state for the Riemann solver.  Direction: n = normal
 // velocity component, t = tangential; Vn* = row of V along the normal.
 struct FState {
-  double phi, ar1, ar2, arl, rho, un, ut, rhoE, snn, snt, cL;
+  double phi, ar1, ar2, arl, rho, un, ut, rhoE, snn, snt, cL, Gm;
   double V11, V12, V21, V22, V33;
 };
 
@@ -184,6 +186,7 @@ __device__ __forceinline__ FState face_state(const Phys& P, const Prim& w) {
   s.rhoE = xi * w.p + ref_energy(P, w.phi, s.ar1, s.ar2, s.arl, st.J2) +
            0.5 * s.rho * (w.u * w.u + w.v * w.v);
   const double Gm = Gmix_of(P, w.phi);
+  s.Gm = Gm;
   if (DIR == 0) {
     s.un = w.u;
     s.ut = w.v;
@@ -209,6 +212,33 @@ struct FaceOut {
   double phi, un, ut, V11, V12, V21, V22, V33;
 };
 
+// Star (longitudinal-wave) state of one side.
+struct Star {
+  double r, snn, E, V11, V12, V21, V22, V33;
+};
+
+template <int DIR>
+__device__ __forceinline__ Star star_of(const FState& K, double S, double Ss) {
+  Star t;
+  const double inv = 1.0 / (S - Ss);
+  t.r = (S - K.un) * inv;
+  const double m = K.rho * (S - K.un);
+  t.snn = K.snn - m * (Ss - K.un);
+  // energy jump: E*(S - S*) = E (S - u_n) + u.sigma_n - u*.sigma*_n (tangential work cancels)
+  t.E = (K.rhoE * (S - K.un) + K.un * K.snn - Ss * t.snn) * inv;
+  const double c1 = cbrt(t.r);        // r^(1/3): rows off the normal
+  const double cn = 1.0 / (c1 * c1);  // r^(-2/3): row along the normal
+  if (DIR == 0) {
+    t.V11 = cn * K.V11; t.V12 = cn * K.V12;
+    t.V21 = c1 * K.V21; t.V22 = c1 * K.V22;
+  } else {
+    t.V11 = c1 * K.V11; t.V12 = c1 * K.V12;
+    t.V21 = cn * K.V21; t.V22 = cn * K.V22;
+  }
+  t.V33 = c1 * K.V33;
+  return t;
+}
+
 template <int DIR>
 __device__ __forceinline__ FaceOut hllc(const FState& L, const FState& R) {
   const double SL = fmin(L.un - L.cL, R.un - R.cL);
@@ -216,52 +246,75 @@ __device__ __forceinline__ FaceOut hllc(const FState& L, const FState& R) {
   const double mL = L.rho * (SL - L.un);
   const double mR = R.rho * (SR - R.un);
   const double Ss = (L.snn - R.snn + mL * L.un - mR * R.un) / (mL - mR);
-  FaceOut o;
-  const FState* K;
-  double S;
-  bool star;
-  if (SL >= 0.0) {
-    K = &L; S = SL; star = false;
-  } else if (Ss >= 0.0) {
-    K = &L; S = SL; star = true;
-  } else if (SR >= 0.0) {
-    K = &R; S = SR; star = true;
-  } else {
-    K = &R; S = SR; star = false;
+  const Star sL = star_of<DIR>(L, SL, Ss);
+  const Star sR = star_of<DIR>(R, SR, Ss);
+  // shear waves of the star regions and the common tangential state
+  const double rsL = sL.r * L.rho, rsR = sR.r * R.rho;
+  const double csL = sqrt(L.Gm / rsL), csR = sqrt(R.Gm / rsR);
+  const double ZL = rsL * csL, ZR = rsR * csR;
+  const double SsL = Ss - csL, SsR = Ss + csR;
+  double ut2L = L.ut, ut2R = R.ut, st2L = L.snt, st2R = R.snt;
+  if (ZL + ZR > 0.0) {
+    const double ut2 = (ZL * L.ut + ZR * R.ut + R.snt - L.snt) / (ZL + ZR);
+    const double st2 = L.snt + ZL * (ut2 - L.ut);
+    ut2L = ut2R = ut2;
+    st2L = st2R = st2;
   }
-  const double un = K->un, ut = K->ut;
-  // physical flux of side K
-  double Far1 = K->ar1 * un, Far2 = K->ar2 * un, Farl = K->arl * un;
-  double Fmn = K->rho * un * un - K->snn;
-  double Fmt = K->rho * ut * un - K->snt;
-  double FE = K->rhoE * un - (un * K->snn + ut * K->snt);
-  o.phi = K->phi;
-  o.ut = ut;
-  if (!star) {
+  // region at x/t = 0 and its side
+  int level;
+  bool left;
+  if (SL >= 0.0) { left = true; level = 0; }
+  else if (SsL >= 0.0) { left = true; level = 1; }
+  else if (Ss >= 0.0) { left = true; level = 2; }
+  else if (SsR >= 0.0) { left = false; level = 2; }
+  else if (SR >= 0.0) { left = false; level = 1; }
+  else { left = false; level = 0; }
+  const FState& K = left ? L : R;
+  const Star& sK = left ? sL : sR;
+  const double S = left ? SL : SR;
+  const double Sh = left ? SsL : SsR;
+  const double ut2 = left ? ut2L : ut2R;
+  const double st2 = left ? st2L : st2R;
+  const double un = K.un, ut = K.ut;
+  FaceOut o;
+  double Far1 = K.ar1 * un, Far2 = K.ar2 * un, Farl = K.arl * un;
+  double Fmn = K.rho * un * un - K.snn;
+  double Fmt = K.rho * ut * un - K.snt;
+  double FE = K.rhoE * un - (un * K.snn + ut * K.snt);
+  o.phi = K.phi;
+  if (level == 0) {
     o.un = un;
-    o.V11 = K->V11; o.V12 = K->V12; o.V21 = K->V21; o.V22 = K->V22; o.V33 = K->V33;
+    o.ut = ut;
+    o.V11 = K.V11; o.V12 = K.V12; o.V21 = K.V21; o.V22 = K.V22; o.V33 = K.V33;
   } else {
-    const double r = (S - un) / (S - Ss);
-    const double m = K->rho * (S - un);
-    const double snn_s = K->snn - m * (Ss - un);
-    const double E_s = (K->rhoE * (S - un) + Ss * snn_s - un * K->snn) / (S - Ss);
-    Far1 += S * (r - 1.0) * K->ar1;
-    Far2 += S * (r - 1.0) * K->ar2;
-    Farl += S * (r - 1.0) * K->arl;
-    Fmn += S * (r * K->rho * Ss - K->rho * un);
-    Fmt += S * (r - 1.0) * K->rho * ut;
-    FE += S * (E_s - K->rhoE);
+    const double r1 = sK.r - 1.0;
+    Far1 += S * r1 * K.ar1;
+    Far2 += S * r1 * K.ar2;
+    Farl += S * r1 * K.arl;
+    Fmn += S * (sK.r * K.rho * Ss - K.rho * un);
+    Fmt += S * r1 * K.rho * ut;
+    FE += S * (sK.E - K.rhoE);
     o.un = Ss;
-    const double c1 = cbrt(r);       // r^(1/3): rows off the normal
-    const double cn = 1.0 / (c1 * c1);  // r^(-2/3): row along the normal
-    if (DIR == 0) {
-      o.V11 = cn * K->V11; o.V12 = cn * K->V12;
-      o.V21 = c1 * K->V21; o.V22 = c1 * K->V22;
-    } else {
-      o.V11 = c1 * K->V11; o.V12 = c1 * K->V12;
-      o.V21 = cn * K->V21; o.V22 = cn * K->V22;
+    o.ut = ut;
+    o.V11 = sK.V11; o.V12 = sK.V12; o.V21 = sK.V21; o.V22 = sK.V22; o.V33 = sK.V33;
+    if (level == 2) {
+      const double dS = Sh - Ss;
+      const double rs = sK.r * K.rho;
+      if (dS != 0.0) {
+        const double idS = 1.0 / dS;
+        Fmt += Sh * rs * (ut2 - ut);
+        FE -= Sh * (ut2 * st2 - ut * K.snt) * idS;
+        const double w = (ut - ut2) * idS;
+        if (DIR == 0) {
+          o.V21 = sK.V21 + w * sK.V11;
+          o.V22 = sK.V22 + w * sK.V12;
+        } else {
+          o.V11 = sK.V11 + w * sK.V21;
+          o.V12 = sK.V12 + w * sK.V22;
+        }
+        o.ut = ut2;
+      }
     }
-    o.V33 = c1 * K->V33;
   }
   o.Far1 = Far1; o.Far2 = Far2; o.Farl = Farl; o.Fmn = Fmn; o.Fmt = Fmt; o.FE = FE;
   return o;

@@ -241,3 +241,107 @@ def test_hllc_star_stretch_keeps_determinant():
     detL, detR = torch.linalg.det(wl["V"]), torch.linalg.det(wr["V"])
     dv = torch.linalg.det(V_f)
     assert torch.all(torch.minimum((dv - detL).abs(), (dv - detR).abs()) < 1e-12)
+
+
+@pytest.mark.parametrize("d", [0, 1])
+def test_hllc_star_states_satisfy_rankine_hugoniot(d):
+    """Each HLLC star state obeys S_K (Q* - Q_K) = F(Q*) - F(Q_K) for mass,
+    momentum and energy (the jump conditions it is built from)."""
+    gen = torch.Generator().manual_seed(11)
+    wl, wr = _prim_batch(32, gen), _prim_batch(32, gen)
+    wr["u"][:, d] -= 200.0
+    mats = [SOLID, GAS]
+    L, R = Rm.face_state(wl, mats), Rm.face_state(wr, mats)
+    unL, unR = L["u"][..., d], R["u"][..., d]
+    SL = torch.minimum(unL - L["cL"], unR - R["cL"])
+    SR = torch.maximum(unL + L["cL"], unR + R["cL"])
+    mL, mR = L["rho"] * (SL - unL), R["rho"] * (SR - unR)
+    Sst = (L["sigma"][..., d, d] - R["sigma"][..., d, d] + mL * unL - mR * unR) / (mL - mR)
+    for K, S in ((L, SL), (R, SR)):
+        Q, us, _ = Rm.star_state(K, S, Sst, d)
+        un = K["u"][..., d]
+        m = K["rho"] * (S - un)
+        sig_n = K["sigma"][..., :, d].clone()
+        sig_s = sig_n.clone()
+        sig_s[..., d] = sig_n[..., d] - m * (Sst - un)
+        F = Rm.physical_flux(K, d)
+        Fs = dict(ar1=Q["ar1"] * Sst, ar2=Q["ar2"] * Sst,
+                  mom=Q["mom"] * Sst[..., None] - sig_s,
+                  E=Q["E"] * Sst - (us * sig_s).sum(-1))
+        for k in ("ar1", "ar2", "mom", "E"):
+            Sk = S[..., None] if Q[k].dim() > S.dim() else S
+            res = Sk * (Q[k] - K[k]) - (Fs[k] - F[k])
+            scale = F[k].abs() + (Sk * K[k]).abs() + 1.0
+            assert (res.abs() / scale).max().item() < 1e-12, k
+
+
+def _hlld_parts(wl, wr, d, mats):
+    """Recompute the HLLD pieces the oracle uses (for jump-condition pins)."""
+    L, R = Rm.face_state(wl, mats), Rm.face_state(wr, mats)
+    unL, unR = L["u"][..., d], R["u"][..., d]
+    SL = torch.minimum(unL - L["cL"], unR - R["cL"])
+    SR = torch.maximum(unL + L["cL"], unR + R["cL"])
+    mL, mR = L["rho"] * (SL - unL), R["rho"] * (SR - unR)
+    Sst = (L["sigma"][..., d, d] - R["sigma"][..., d, d] + mL * unL - mR * unR) / (mL - mR)
+    return L, R, SL, SR, Sst
+
+
+@pytest.mark.parametrize("d", [0, 1])
+def test_hlld_shear_jumps_satisfy_rankine_hugoniot(d):
+    """Across each shear wave S*_K: S*_K (Q** - Q*) = F(Q**) - F(Q*), and the
+    tangential velocity and traction of the two double-star states agree."""
+    gen = torch.Generator().manual_seed(12)
+    wl, wr = _prim_batch(32, gen), _prim_batch(32, gen)
+    t = 1 - d
+    wr["u"][:, t] += 80.0  # shear
+    mats = [SOLID, SOLID]
+    L, R, SL, SR, Sst = _hlld_parts(wl, wr, d, mats)
+    tm = torch.ones(3, dtype=F64)
+    tm[d] = 0.0
+    Qs, us, Vs, cs = {}, {}, {}, {}
+    for side, K, S in (("L", L, SL), ("R", R, SR)):
+        Qs[side], us[side], Vs[side] = Rm.star_state(K, S, Sst, d)
+        cs[side] = torch.sqrt(K["Gm"] / (Qs[side]["ar1"] + Qs[side]["ar2"]))
+    Z = {k: (Qs[k]["ar1"] + Qs[k]["ar2"]) * cs[k] for k in "LR"}
+    st = {k: K["sigma"][..., :, d] * tm for k, K in (("L", L), ("R", R))}
+    ut = {k: K["u"] * tm for k, K in (("L", L), ("R", R))}
+    ut2 = (Z["L"][..., None] * ut["L"] + Z["R"][..., None] * ut["R"] + st["R"] - st["L"]) / (Z["L"] + Z["R"])[..., None]
+    st2 = st["L"] + Z["L"][..., None] * (ut2 - ut["L"])
+    st2R = st["R"] - Z["R"][..., None] * (ut2 - ut["R"])
+    assert torch.allclose(st2, st2R, rtol=1e-12, atol=1e-3)  # common traction at the contact
+    for side, K, sgn in (("L", L, -1.0), ("R", R, 1.0)):
+        Ssh = Sst + sgn * cs[side]
+        Q2, u2, V2 = Rm.shear_state(K, Qs[side], us[side], Vs[side], Ssh, Sst, ut2, st2, d)
+        m = K["rho"] * ((SL if side == "L" else SR) - K["u"][..., d])
+        snn_s = K["sigma"][..., d, d] - m * (Sst - K["u"][..., d])
+        trac_s = st[side].clone()
+        trac_s[..., d] = snn_s
+        trac_2 = st2.clone()
+        trac_2[..., d] = snn_s
+
+        def flux(Q, u, trac):
+            return dict(ar1=Q["ar1"] * Sst, mom=Q["mom"] * Sst[..., None] - trac,
+                        E=Q["E"] * Sst - (u * trac).sum(-1))
+        F1, F2 = flux(Qs[side], us[side], trac_s), flux(Q2, u2, trac_2)
+        for k in ("ar1", "mom", "E"):
+            Sk = Ssh[..., None] if Q2[k].dim() > Ssh.dim() else Ssh
+            res = Sk * (Q2[k] - Qs[side][k]) - (F2[k] - F1[k])
+            scale = F1[k].abs() + (Sk * Qs[side][k]).abs() + 1.0
+            assert (res.abs() / scale).max().item() < 1e-12, (side, k)
+        assert torch.allclose(torch.linalg.det(V2), torch.linalg.det(Vs[side]), rtol=1e-13)
+
+
+def test_hlld_flux_continuous_across_stationary_contact():
+    """Mirror-symmetric states give S* = 0; the double-star fluxes from both
+    sides coincide, so the tie rule does not matter."""
+    gen = torch.Generator().manual_seed(13)
+    w = _prim_batch(16, gen)
+    w["u"][:, 0] = 150.0
+    P = torch.diag(t([-1.0, 1.0, 1.0]))
+    m = dict(w)
+    m["u"] = w["u"] @ P
+    m["V"] = P @ w["V"] @ P
+    F, _, u_f, _ = Rm.hllc(w, m, 0, [SOLID, GAS])
+    Fm, _, _, _ = Rm.hllc(w, m, 0, [SOLID, GAS])
+    assert torch.allclose(u_f[..., 0], torch.zeros(16, dtype=F64), atol=1e-9)
+    assert F["ar1"].abs().max().item() < 1e-6 * (w["rho1"] * 150).max().item()

@@ -3,6 +3,13 @@
 Bar: per-field relative L1 <= 1e-10 after the stated number of steps (the
 FP64 parity target).  Sizes are small enough for the oracle to finish in
 seconds while spanning several 128-cell segments and a ragged tail.
+
+THINC steepening next to a very stiff solid (gamma p_inf / p ~ 1e6)
+amplifies round-off at interface cells, so two correct float64 programs
+that differ only in rounding drift apart.  Those cases use a self-calibrated
+bar: the GPU must agree with the oracle to within 10x the oracle's own
+spread when its inputs are perturbed by one ulp (and never worse than the
+1e-10 bar where that spread is smaller).
 """
 import numpy as np
 import pytest
@@ -33,9 +40,28 @@ def gpu_run(wl, steps, dt_fixed=None, precision="fp64"):
     return out, prim, np.array(dts)
 
 
-def assert_parity(wl, steps, tol=TOL):
+def oracle_spread(wl, steps, o):
+    """Per-patch, per-field L1 between the oracle and the oracle on inputs
+    perturbed by one ulp (random sign per value)."""
+    import copy
+    rng = np.random.default_rng(123)
+    wp = copy.deepcopy(wl)
+    for p in wp.patches:
+        p.prim = p.prim * (1 + np.sign(rng.standard_normal(p.prim.shape)) * 2.0 ** -52)
+    op, _ = oracle_run(wp, steps)
+    return [cons_l1(wl, op[k], o[k]) for k in range(len(o))]
+
+
+def assert_parity(wl, steps, tol=TOL, calibrate=False):
     g, gp, gdt = gpu_run(wl, steps)
     o, odt = oracle_run(wl, steps)
+    if calibrate:
+        spread = oracle_spread(wl, steps, o)
+        for k in range(len(o)):
+            err = cons_l1(wl, g[k], o[k])
+            bar = np.maximum(tol, 10.0 * spread[k])
+            assert (err <= bar).all(), (k, err, spread[k])
+        return
     for k in range(len(o)):
         err = cons_l1(wl, g[k], o[k])
         assert err.max() <= tol, (k, err)
@@ -53,7 +79,16 @@ def test_1d_solid_gas_100_steps():
 def test_1d_solid_gas_thinc():
     wl = W.solid_gas_1d(300, steps=60)
     wl.thinc = True
-    assert_parity(wl, 60)
+    assert_parity(wl, 60, calibrate=True)
+
+
+def test_1d_water_air_thinc_strict():
+    """THINC at a water-air interface (stable to round-off): strict bar."""
+    water = W.material(4.4, p_inf=6e8)
+    wl = W.riemann_1d(257, dict(mat=0, rho=1000.0, u=0.0, p=1e9, rho2=50.0),
+                      dict(mat=1, rho=50.0, u=0.0, p=1e5, rho1=1000.0), x_int=0.7, cfl=0.6,
+                      thinc=True, materials=[water, W.AIR])
+    assert_parity(wl, 100)
 
 
 @pytest.mark.parametrize("bc", [W.BC_PERIODIC, W.BC_REFLECTIVE])
@@ -69,26 +104,44 @@ def test_1d_boundaries(bc):
 
 def test_2d_shock_disc_small():
     wl = W.shock_disc_2d(40, steps=30)
+    wl.thinc = False
     assert_parity(wl, 30)
 
 
+def test_2d_shock_disc_thinc():
+    wl = W.shock_disc_2d(40, steps=30)
+    assert_parity(wl, 30, calibrate=True)
+
+
 def test_2d_shock_disc_ragged_reflective():
-    wl = W.shock_disc_2d(36, steps=20)
-    p = wl.patches[0]
-    p.prim = p.prim[:, :, :]  # 36 x 36, not a multiple of the 128-cell segment
+    wl = W.shock_disc_2d(36, steps=20, shock_x=0.4)  # shock already on the disc
+    wl.thinc = False
+    p = wl.patches[0]  # 36 x 36: ragged against the 128-cell segments
     p.bc = (W.BC_TRANSMISSIVE, W.BC_REFLECTIVE, W.BC_REFLECTIVE, W.BC_PERIODIC)
     assert_parity(wl, 20)
 
 
 def test_2d_reactive_small():
     wl = W.reactive_plate_2d(64, 32, steps=20)
-    # make the hot spot large enough to react on this grid
+    assert_parity(wl, 20, calibrate=True)
+
+
+def test_2d_reactive_small_strict():
+    wl = W.reactive_plate_2d(64, 32, steps=20)
+    wl.thinc = False
     assert_parity(wl, 20)
 
 
 def test_batched_1d_subset():
     wl = W.batched_riemann_1d(12, seed=3, steps=40, nmin=16, nmax=300)
     assert_parity(wl, 40)
+
+
+def test_symmetric_solid_impact_yields():
+    """Two solids at +-250 m/s: elastic precursor and plastic yielding."""
+    wl = W.riemann_1d(200, dict(mat=0, rho=8000.0, u=250.0, p=1e5, rho2=1.2),
+                      dict(mat=0, rho=8000.0, u=-250.0, p=1e5, rho2=1.2))
+    assert_parity(wl, 60)
 
 
 def test_fixed_dt_matches_oracle():
