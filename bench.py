@@ -38,9 +38,9 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def workload(nx=NX, ny=NY):
+def workload(nx=None, ny=None):
     from paper_2009_14555_gb300 import workloads as W
-    return W.reactive_plate_2d(nx, ny)
+    return W.reactive_plate_2d(nx or NX, ny or NY)
 
 
 def dist_env():
@@ -110,7 +110,7 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    wl = workload()
+    wl = workload(args.nx, args.ny)
     cells = wl.cells
     prim = pack([p.prim for p in wl.patches])
     results = {}
@@ -175,7 +175,8 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"2d_reactive_plate_{NX}x{NY}", "cells": cells, "precision": "fp64",
+        "config": {"workload": f"2d_reactive_plate_{args.nx or NX}x{args.ny or NY}", "cells": cells,
+                   "precision": "fp64",
                    "l2": "working set (state 201 MB + primitives + faces) larger than L2",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
@@ -251,6 +252,8 @@ def main():
     ap.add_argument("--impl", default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--nx", type=int, default=None, help="profiling only: smaller grid")
+    ap.add_argument("--ny", type=int, default=None, help="profiling only: smaller grid")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
