@@ -139,6 +139,33 @@ size_t dis_state_bytes(const dis_ctx* ctx, int kind);
 /* Number of kernel launches made by the last dis_step / dis_step_fixed_dt. */
 long long dis_last_launches(const dis_ctx* ctx);
 
+/* Largest patch count accepted by dis_cfl_dt_static. */
+#define DIS_STATIC_MAX_PATCHES 16384
+
+/* Per-patch CFL time step of a conservative state, for callers that cannot
+ * allocate device memory (code running where an allocation could
+ * synchronise the device or be refused, e.g. inside a host callback, under a
+ * framework that owns the device allocator, or after all device memory was
+ * reserved up front).  The paper has no counterpart: this is the CFL
+ * reduction of the step (dt = cfl / max over the patch of
+ * sum_d (|u_d| + c_L) / dx_d) without a context.
+ *   d_state: device pointer to the packed conservative state of n_patches
+ *            patches (layout above) for materials[0..1];
+ *   d_dt:    device pointer receiving n_patches float64 time steps;
+ *   stream:  cudaStream_t the work is ordered on (NULL = legacy default).
+ * It allocates nothing: its scratch (per-patch maxima and descriptors) is a
+ * fixed area inside the library on each device, DIS_STATIC_MAX_PATCHES
+ * entries (about 0.6 MB), held by every GPU that loads the library until the
+ * process exits.  The first call on a device looks the area up (with that
+ * device current); make that first call before any stream capture.  Each call
+ * clears the maxima it uses; calls are serialised on the host, but calls
+ * whose device work overlaps (different streams) share the area and race.
+ * Returns DIS_EINVAL for n_patches outside 1..DIS_STATIC_MAX_PATCHES or other
+ * bad arguments (nothing is launched), DIS_ECUDA if a CUDA call fails. */
+int dis_cfl_dt_static(int dim, int n_patches, const dis_patch* patches,
+                      const dis_material* materials, int reactive_material, double cfl,
+                      const double* d_state, double* d_dt, void* stream);
+
 /* Thread-local text of the last error (never NULL). */
 const char* dis_last_error(void);
 

@@ -52,6 +52,17 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 }  // namespace
 
+// Error text for the other translation units of the library.
+int dis_internal_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
 struct dis_ctx {
   int dim = 1, np = 0, y = -1, nf = 0;
   dis_options opt{};
