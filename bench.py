@@ -25,6 +25,18 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "cell-updates/s and % HBM peak, FP32-bulk vs plain FP64 on one GB300 at stated L1"
+
+# Dominant kernel of the float64 step: the x-face flux kernel (40 % of the
+# step in the ncu launch list).  Its arithmetic per face, counted by ncu on the
+# 1024x512 reactive plate (2 x DFMA + DADD + DMUL per face; see
+# profiles/k_flux_2d_reactive_plate_1024x512.md):
+FLUX_FP64_FLOP_PER_FACE = 1193.0
+# DRAM bytes per x-flux launch from the same capture (73.8 MB for 524800
+# faces), per face; traffic grows with the face count.
+FLUX_DRAM_BYTES_PER_FACE = 73.80e6 / 524800
+# FP64 peak: 152 SMs x 2 DFMA/cycle (ncu sm__sass_thread_inst_executed_op_dfma
+# peak_sustained = 304/cycle) x 2 FLOP x 2.07 GHz maximum SM clock.
+FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
 UNIT = "cell-updates/s"
 NX, NY = 2048, 1024
 
@@ -147,8 +159,10 @@ def run_gpu(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             tot_ms = float(t.item())
         rc, _, _ = s.check()
+        kernel_ms = s.step_timed(2)  # per-launch device time, outside the timed region
         results[prec] = dict(ms_total=tot_ms, ms_per_step=tot_ms / args.steps, wall=wall,
-                             launches=launches, clocks=clk.summary(), ok=rc == 0, solver=s)
+                             launches=launches, clocks=clk.summary(), ok=rc == 0, solver=s,
+                             kernel_ms=kernel_ms)
     # end-to-end through the C ABI with host buffers: H2D of the step's input
     # state from pinned memory, the step, D2H of the result, every step.
     s = results["fp64"]["solver"]
@@ -170,7 +184,11 @@ def run_gpu(args):
     value = cells * world / (r["ms_per_step"] * 1e-3)
     hbm, kind = peaks()
     alg_bytes = 2 * 12 * 8  # read + write the 12-field float64 state once per cell-update
-    achieved = alg_bytes * cells / (r["ms_per_step"] * 1e-3) / 1e9
+    hbm_achieved = alg_bytes * cells / (r["ms_per_step"] * 1e-3) / 1e9
+    nxw, nyw = args.nx or NX, args.ny or NY
+    faces_x = (nxw + 1) * nyw
+    t_fx = r["kernel_ms"][1] * 1e-3
+    flux_tflops = FLUX_FP64_FLOP_PER_FACE * faces_x / t_fx / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
@@ -179,9 +197,16 @@ def run_gpu(args):
                    "precision": "fp64",
                    "l2": "working set (state 201 MB + primitives + faces) larger than L2",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
-                     "note": f"whole step, algorithmic {alg_bytes} B/cell-update, peak {kind}"},
+        "roofline": {"bound": "alu", "kernel": "k_flux x (float64)",
+                     "achieved": flux_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": flux_tflops / FP64_PEAK_TFLOPS,
+                     "traffic": FLUX_DRAM_BYTES_PER_FACE * faces_x,
+                     "note": "FP64 FLOP per face from ncu x faces / live event time per launch; "
+                             "peak = 304 DFMA/clk x 2 x 2.07 GHz; traffic scaled from a 1024x512 capture"},
+        "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": hbm, "frac": hbm_achieved / hbm,
+                "algorithmic_bytes_per_cell_update": alg_bytes, "peak_kind": kind},
+        "kernels_ms_per_launch": {"prim": r["kernel_ms"][0], "flux_x": r["kernel_ms"][1],
+                                  "flux_y": r["kernel_ms"][2], "update": r["kernel_ms"][3]},
         "e2e": {"value": cells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
         "gpu_launches": r["launches"],

@@ -139,6 +139,12 @@ size_t dis_state_bytes(const dis_ctx* ctx, int kind);
 /* Number of kernel launches made by the last dis_step / dis_step_fixed_dt. */
 long long dis_last_launches(const dis_ctx* ctx);
 
+/* Diagnostic: advance n_steps CFL steps like dis_step but launch kernel by
+ * kernel with CUDA events between launches, and return in kernel_ms[4] the
+ * mean device time per launch of the primitive-recovery, x-flux, y-flux (0 in
+ * 1D) and update kernels.  Synchronises after every stage. */
+int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
+
 /* Largest patch count accepted by dis_cfl_dt_static. */
 #define DIS_STATIC_MAX_PATCHES 16384
 

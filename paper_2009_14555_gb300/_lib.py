@@ -53,6 +53,7 @@ SIGNATURES = {
     "dis_check": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int)]),
     "dis_state_bytes": (c_size_t, [c_void_p, c_int]),
     "dis_last_launches": (c_longlong, [c_void_p]),
+    "dis_step_timed": (c_int, [c_void_p, c_int, c_void_p]),
     "dis_cfl_dt_static": (c_int, [c_int, c_int, POINTER(DisPatch), POINTER(DisMaterial), c_int,
                                    c_double, c_void_p, c_void_p, c_void_p]),
     "dis_last_error": (c_char_p, []),
@@ -136,6 +137,10 @@ def dis_state_bytes(ctx, kind):
 
 def dis_last_launches(ctx):
     return load().dis_last_launches(ctx)
+
+
+def dis_step_timed(ctx, n, ms_ptr):
+    return check(load().dis_step_timed(ctx, n, c_void_p(ms_ptr)))
 
 
 def dis_last_error():

@@ -267,6 +267,52 @@ long long launch_step(dis_ctx* c, cudaStream_t st, bool fixed) {
   return launches;
 }
 
+// One step with CUDA events around every kernel (no graph), accumulating the
+// device time of each kernel class: 0 prim, 1 flux x, 2 flux y, 3 update.
+template <int DIM, bool RX>
+int timed_steps(dis_ctx* c, int n_steps, double* ms) {
+  StepArgs a = base_args(c);
+  a.dtfix = nullptr;
+  const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+  const unsigned np = (unsigned)c->seg_prim.size(), nfx = (unsigned)c->seg_fx.size(),
+                 nfy = (unsigned)c->seg_fy.size(), nc = (unsigned)c->seg_cell.size();
+  cudaEvent_t ev[5];
+  for (int k = 0; k < 5; ++k) CU(cudaEventCreate(&ev[k]));
+  double acc[4] = {0, 0, 0, 0};
+  for (int s = 0; s < n_steps; ++s) {
+    CU(cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, c->stream));
+    for (int stg = 0; stg < 3; ++stg) {
+      a.qsrc = stg == 0 ? c->q[0] : c->q[1];
+      a.qn = c->q[0];
+      a.qdst = stg == 2 ? c->q[0] : c->q[1];
+      a.a = ca[stg];
+      a.b = cb[stg];
+      a.last = stg == 2;
+      CU(cudaEventRecord(ev[0], c->stream));
+      k_prim<DIM, RX><<<np, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_prim, stg == 0 ? 1 : 0);
+      CU(cudaEventRecord(ev[1], c->stream));
+      k_flux<DIM, RX, 0><<<nfx, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_fx);
+      CU(cudaEventRecord(ev[2], c->stream));
+      if constexpr (DIM == 2) k_flux<DIM, RX, 1><<<nfy, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_fy);
+      CU(cudaEventRecord(ev[3], c->stream));
+      k_update<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_cell);
+      CU(cudaEventRecord(ev[4], c->stream));
+      CU(cudaEventSynchronize(ev[4]));
+      for (int k = 0; k < 4; ++k) {
+        float t = 0.f;
+        CU(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+        acc[k] += t;
+      }
+    }
+  }
+  CU(cudaGetLastError());
+  for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
+  const double nl = 3.0 * n_steps;
+  for (int k = 0; k < 4; ++k) ms[k] = acc[k] / nl;
+  return DIS_OK;
+}
+
 template <int DIM, bool RX>
 int run_steps(dis_ctx* c, int n_steps, bool fixed) {
   const int mode = fixed ? 1 : 0;
@@ -526,6 +572,15 @@ int dis_check(dis_ctx* c, int* bad_patch, int* bad_cell) {
 }
 
 long long dis_last_launches(const dis_ctx* c) { return c ? c->launches : 0; }
+
+int dis_step_timed(dis_ctx* c, int n_steps, double* kernel_ms) {
+  if (!c || !kernel_ms) return fail(DIS_EINVAL, "dis_step_timed: NULL argument");
+  if (n_steps <= 0) return fail(DIS_EINVAL, "dis_step_timed: n_steps must be positive");
+  if (!c->have_state) return fail(DIS_ESTATE, "dis_step_timed: no state loaded");
+  const bool rx = c->y >= 0;
+  if (c->dim == 1) return rx ? timed_steps<1, true>(c, n_steps, kernel_ms) : timed_steps<1, false>(c, n_steps, kernel_ms);
+  return rx ? timed_steps<2, true>(c, n_steps, kernel_ms) : timed_steps<2, false>(c, n_steps, kernel_ms);
+}
 
 void dis_destroy(dis_ctx* c) {
   if (!c) return;
