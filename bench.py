@@ -37,6 +37,12 @@ FLUX_DRAM_BYTES_PER_FACE = 73.80e6 / 524800
 # FP64 peak: 152 SMs x 2 DFMA/cycle (ncu sm__sass_thread_inst_executed_op_dfma
 # peak_sustained = 304/cycle) x 2 FLOP x 2.07 GHz maximum SM clock.
 FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
+# FP32: 152 SMs x 128 FMA lanes x 2 FLOP x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP32 FLOP per cell of one fused FP32-bulk stage (recovery with halo, x and
+# y faces, update), ncu count (see profiles/).
+FUSED32_FLOP_PER_CELL = 2000.0
+FUSED32_DRAM_BYTES_PER_CELL = None
 UNIT = "cell-updates/s"
 NX, NY = 2048, 1024
 
@@ -83,6 +89,14 @@ class ClockSampler:
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
+            return self
+        # wait for the first sample so the sampler's start-up is outside the timed region
+        t0 = time.time()
+        while time.time() - t0 < 5.0:
+            self.f.flush()
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.05)
         return self
 
     def __exit__(self, *a):
@@ -126,7 +140,7 @@ def run_gpu(args):
     cells = wl.cells
     prim = pack([p.prim for p in wl.patches])
     results = {}
-    precisions = ["fp64"]
+    precisions = ["fp64", "fp32_bulk"]
     for prec in precisions:
         s = Solver.from_workload(wl, precision=prec)
         s.set_state(prim, kind=1)
@@ -135,37 +149,37 @@ def run_gpu(args):
             s.step(1)
         torch.cuda.synchronize()
         launches = 0
-        # per-step device time, every step bracketed by events on the library's stream
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         with ClockSampler(local) as clk:
+            torch.cuda.synchronize()
             t0 = time.perf_counter()
+            ev0.record(stream)
             for k in range(args.steps):
-                evs[k][0].record(stream)
                 s.step(1)
-                evs[k][1].record(stream)
                 launches += s.launches
+            ev1.record(stream)
             torch.cuda.synchronize()
             wall = time.perf_counter() - t0
         if world > 1:
             dist.barrier()
-        ms = [a.elapsed_time(b) for a, b in evs]
-        tot_ms = float(np.sum(ms))
+        tot_ms = float(ev0.elapsed_time(ev1))
         if world > 1:
             t = torch.tensor([tot_ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             tot_ms = float(t.item())
         rc, _, _ = s.check()
+        final = s.get_state(kind=0)  # state after warm-up + timed steps, for the L1 comparison
         kernel_ms = s.step_timed(2)  # per-launch device time, outside the timed region
+        tile = s.tile_choice()[:2] if prec == "fp32_bulk" else (0, 0)
         results[prec] = dict(ms_total=tot_ms, ms_per_step=tot_ms / args.steps, wall=wall,
                              launches=launches, clocks=clk.summary(), ok=rc == 0, solver=s,
-                             kernel_ms=kernel_ms)
+                             kernel_ms=kernel_ms, final=final, tile=tile)
     # end-to-end through the C ABI with host buffers: H2D of the step's input
     # state from pinned memory, the step, D2H of the result, every step.
-    s = results["fp64"]["solver"]
+    s = results["fp32_bulk"]["solver"]
     hin = torch.from_numpy(prim).pin_memory()
     hout = torch.empty(s.state_numel, dtype=torch.float64).pin_memory()
     e2e_steps = max(1, min(args.steps, 5))
@@ -180,39 +194,70 @@ def run_gpu(args):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     nbytes = prim.nbytes
 
-    r = results["fp64"]
+    r = results["fp32_bulk"]
+    r64 = results["fp64"]
     value = cells * world / (r["ms_per_step"] * 1e-3)
+    value64 = cells * world / (r64["ms_per_step"] * 1e-3)
     hbm, kind = peaks()
-    alg_bytes = 2 * 12 * 8  # read + write the 12-field float64 state once per cell-update
-    hbm_achieved = alg_bytes * cells / (r["ms_per_step"] * 1e-3) / 1e9
     nxw, nyw = args.nx or NX, args.ny or NY
     faces_x = (nxw + 1) * nyw
-    t_fx = r["kernel_ms"][1] * 1e-3
-    flux_tflops = FLUX_FP64_FLOP_PER_FACE * faces_x / t_fx / 1e12
+    # algorithmic bytes per cell-update: read + write the state once
+    alg32 = 2 * (2 * 8 + 10 * 4)   # phi1, rho E float64 + 10 float32 fields
+    alg64 = 2 * 12 * 8
+    hbm32 = alg32 * cells / (r["ms_per_step"] * 1e-3) / 1e9
+    hbm64 = alg64 * cells / (r64["ms_per_step"] * 1e-3) / 1e9
+    t64 = r64["kernel_ms"][1] * 1e-3
+    flux64_tflops = FLUX_FP64_FLOP_PER_FACE * faces_x / t64 / 1e12
+    t32 = r["kernel_ms"][1] * 1e-3  # one fused stage (recovery, x and y faces, update)
+    flux32_tflops = FUSED32_FLOP_PER_CELL * cells / t32 / 1e12
+    # per-field L1 of the FP32-bulk state against the float64 GPU state after the
+    # same number of steps (the float64 GPU path matches the oracle to 1e-10)
+    a32, a64 = r["final"].reshape(12, -1), r64["final"].reshape(12, -1)
+    names = ["phi1", "ar1", "ar2", "mx", "my", "E", "V11", "V12", "V21", "V22", "V33", "arl"]
+    floor = {"phi1": 1.0, "V11": 1.0, "V12": 1.0, "V21": 1.0, "V22": 1.0, "V33": 1.0}
+    rc_ = float(np.sqrt(np.abs(a64[1:3]).max() * np.abs(a64[5]).max()))
+    floor.update(mx=rc_, my=rc_)
+    l1 = {n: float(np.abs(a32[k] - a64[k]).sum() / max(np.abs(a64[k]).sum(), a64.shape[1] * floor.get(n, 0.0)))
+          for k, n in enumerate(names)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"2d_reactive_plate_{args.nx or NX}x{args.ny or NY}", "cells": cells,
-                   "precision": "fp64",
-                   "l2": "working set (state 201 MB + primitives + faces) larger than L2",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (phi1, rho E, pressure recovery in f64)",
+        "data": "synthetic",
+        "config": {"workload": f"2d_reactive_plate_{nxw}x{nyw}", "cells": cells,
+                   "precision": "fp32_bulk",
+                   "l2": "working set larger than L2 (state + primitives + faces > 129 MB)",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"bound": "alu", "kernel": "k_flux x (float64)",
-                     "achieved": flux_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": flux_tflops / FP64_PEAK_TFLOPS,
-                     "traffic": FLUX_DRAM_BYTES_PER_FACE * faces_x,
-                     "note": "FP64 FLOP per face from ncu x faces / live event time per launch; "
-                             "peak = 304 DFMA/clk x 2 x 2.07 GHz; traffic scaled from a 1024x512 capture"},
-        "hbm": {"achieved_gbs": hbm_achieved, "peak_gbs": hbm, "frac": hbm_achieved / hbm,
-                "algorithmic_bytes_per_cell_update": alg_bytes, "peak_kind": kind},
-        "kernels_ms_per_launch": {"prim": r["kernel_ms"][0], "flux_x": r["kernel_ms"][1],
-                                  "flux_y": r["kernel_ms"][2], "update": r["kernel_ms"][3]},
+        "roofline": {"bound": "alu", "kernel": "k_stage32 (fused stage, float32)",
+                     "achieved": flux32_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": flux32_tflops / FP32_PEAK_TFLOPS,
+                     "traffic": FUSED32_DRAM_BYTES_PER_CELL * cells if FUSED32_DRAM_BYTES_PER_CELL else None,
+                     "note": "FP32 FLOP per cell-stage from ncu x cells / live event time per launch; "
+                             "peak = 152 SMs x 128 FFMA lanes x 2 x 2.07 GHz"},
+        "l1_vs_fp64": l1,
+        "hbm": {"achieved_gbs": hbm32, "peak_gbs": hbm, "frac": hbm32 / hbm,
+                "algorithmic_bytes_per_cell_update": alg32, "peak_kind": kind},
+        "kernels_ms_per_launch": {"cfl_pass_per_stage": float(r["kernel_ms"][0]),
+                                  "fused_stage": float(r["kernel_ms"][1])},
+        "tile": list(r["tile"]),
+        "fp64": {"value": value64, "ms_per_step": r64["ms_per_step"],
+                 "speedup_fp32_bulk": value / value64,
+                 "hbm": {"achieved_gbs": hbm64, "frac": hbm64 / hbm, "algorithmic_bytes_per_cell_update": alg64},
+                 "roofline": {"bound": "alu", "kernel": "k_flux x (float64)", "achieved": flux64_tflops,
+                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                              "frac": flux64_tflops / FP64_PEAK_TFLOPS,
+                              "traffic": FLUX_DRAM_BYTES_PER_FACE * faces_x},
+                 "kernels_ms_per_launch": dict(zip(["prim", "flux_x", "flux_y", "update"],
+                                                   map(float, r64["kernel_ms"]))),
+                 "clocks": r64["clocks"]},
         "e2e": {"value": cells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
-        "status_ok": r["ok"],
+        "status_ok": bool(r["ok"] and r64["ok"]),
     }
+    if not args.no_batch:
+        line["batch_1d"] = batch_bench()
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -221,6 +266,37 @@ def run_gpu(args):
         v["solver"].close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def batch_bench(steps=10, warmup=3):
+    """4096 independent 1D two-material problems (256-4096 cells, seed 3) in one
+    batch: cell-updates/s for both precisions (each problem has its own dt)."""
+    import torch
+    from paper_2009_14555_gb300 import workloads as W
+    from paper_2009_14555_gb300.solver import Solver, pack
+    wl = W.batched_riemann_1d()
+    prim = pack([p.prim for p in wl.patches])
+    out = {"workload": "1d_batch_4096 (256-4096 cells log-uniform, seed 3)", "cells": wl.cells,
+           "problems": len(wl.patches)}
+    for prec in ("fp32_bulk", "fp64"):
+        s = Solver.from_workload(wl, precision=prec)
+        s.set_state(prim, kind=1)
+        for _ in range(warmup):
+            s.step(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s.stream)
+        for _ in range(steps):
+            s.step(1)
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        ok = s.check()[0] == 0
+        out[prec] = {"value": wl.cells / (ms * 1e-3), "ms_per_step": ms, "status_ok": ok}
+        if prec == "fp32_bulk":
+            out[prec]["tile"] = list(s.tile_choice()[:2])
+        s.close()
+    return out
 
 
 def cpu_baseline(budget_s=15.0, steps=None):
@@ -276,6 +352,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched 1D measurement")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--nx", type=int, default=None, help="profiling only: smaller grid")
     ap.add_argument("--ny", type=int, default=None, help="profiling only: smaller grid")

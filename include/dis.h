@@ -139,10 +139,18 @@ size_t dis_state_bytes(const dis_ctx* ctx, int kind);
 /* Number of kernel launches made by the last dis_step / dis_step_fixed_dt. */
 long long dis_last_launches(const dis_ctx* ctx);
 
+/* FP32-bulk contexts run one fused kernel per Runge-Kutta stage over tiles
+ * of TX x TY cells; the first dis_step times three tile shapes (on the stage
+ * buffer, leaving the state unchanged) and keeps the fastest.  Returns the
+ * chosen shape (0 x 0 before tuning or for float64 contexts) and, if
+ * stage_ms is not NULL, the measured stage times of the three shapes. */
+int dis_tile_choice(const dis_ctx* ctx, int* tx, int* ty, double* stage_ms);
+
 /* Diagnostic: advance n_steps CFL steps like dis_step but launch kernel by
  * kernel with CUDA events between launches, and return in kernel_ms[4] the
  * mean device time per launch of the primitive-recovery, x-flux, y-flux (0 in
- * 1D) and update kernels.  Synchronises after every stage. */
+ * 1D) and update kernels (float64), or of the CFL pass and the fused stage
+ * kernel in slots 0 and 1 (FP32-bulk).  Synchronises after every stage. */
 int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
 
 /* Largest patch count accepted by dis_cfl_dt_static. */

@@ -54,6 +54,7 @@ SIGNATURES = {
     "dis_state_bytes": (c_size_t, [c_void_p, c_int]),
     "dis_last_launches": (c_longlong, [c_void_p]),
     "dis_step_timed": (c_int, [c_void_p, c_int, c_void_p]),
+    "dis_tile_choice": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), c_void_p]),
     "dis_cfl_dt_static": (c_int, [c_int, c_int, POINTER(DisPatch), POINTER(DisMaterial), c_int,
                                    c_double, c_void_p, c_void_p, c_void_p]),
     "dis_last_error": (c_char_p, []),

@@ -23,7 +23,7 @@
 #include <vector>
 
 #include "../../include/dis.h"
-#include "step_kernels.cuh"
+#include "fused32.cuh"
 
 using namespace dis;
 
@@ -67,6 +67,8 @@ struct dis_ctx {
   int dim = 1, np = 0, y = -1, nf = 0;
   dis_options opt{};
   Phys phys{};
+  PhysF physf{};
+  bool fp32 = false;
   bool have_mats = false, have_state = false;
   std::vector<dis_patch> patches;
   std::vector<PatchDev> pd;
@@ -87,6 +89,17 @@ struct dis_ctx {
   double* dtfix = nullptr;
   double* dtlast = nullptr;
   int* status = nullptr;
+  // FP32-bulk fused stage kernel: tile tables per tile shape, chosen shape
+  std::vector<int4> tiles[3];
+  int4* d_tiles[3] = {nullptr, nullptr, nullptr};
+  int variant = -1;
+  double tune_ms[3] = {0, 0, 0};
+  // FP32-bulk buffers: (phi1, rho E) float64 pairs and float32 planes
+  double* q64[2] = {nullptr, nullptr};
+  float* q32[2] = {nullptr, nullptr};
+  float* W32 = nullptr;
+  float* Fx32 = nullptr;
+  float* Fy32 = nullptr;
   PatchDev* d_pd = nullptr;
   int4 *d_seg_prim = nullptr, *d_seg_fx = nullptr, *d_seg_fy = nullptr, *d_seg_cell = nullptr;
   long long launches = 0;
@@ -105,6 +118,26 @@ int n_extra(int dim) { return dim == 2 ? 3 : 2; }
 // Split rows of [lo, hi) into segments of at most SEG.
 void add_row(std::vector<int4>& v, int patch, int row, int lo, int hi) {
   for (int s = lo; s < hi; s += SEG) v.push_back(make_int4(patch, row, s, std::min(SEG, hi - s)));
+}
+
+// Tile shapes of the fused FP32-bulk stage kernel (TX x TY cells, 256 threads
+// in 2D): the face counts (TX+1) TY + TX (TY+1) fill two passes of the
+// threads (511, 512, 487 faces).  1D tiles of NT - 6 cells make the halo
+// (NT cells) and the faces (NT - 5) one pass each.
+constexpr int kTiles2D[3][2] = {{16, 15}, {20, 12}, {32, 7}};
+constexpr int kTiles1D[3] = {122, 250, 506};
+
+void tile_tables(dis_ctx* c) {
+  for (int v = 0; v < 3; ++v) {
+    c->tiles[v].clear();
+    const int TX = c->dim == 2 ? kTiles2D[v][0] : kTiles1D[v];
+    const int TY = c->dim == 2 ? kTiles2D[v][1] : 1;
+    for (int p = 0; p < c->np; ++p) {
+      const PatchDev& d = c->pd[p];
+      for (int j = 0; j < d.ny; j += TY)
+        for (int i = 0; i < d.nx; i += TX) c->tiles[v].push_back(make_int4(p, i, j, 0));
+    }
+  }
 }
 
 void layout(dis_ctx* c) {
@@ -144,6 +177,7 @@ void layout(dis_ctx* c) {
   c->NFX = fx;
   c->NFY = fy;
   c->ncells = po / c->nf;
+  tile_tables(c);
 }
 
 struct Carve {
@@ -157,10 +191,26 @@ struct Carve {
 
 size_t carve(dis_ctx* c, char* base) {
   Carve k;
-  const size_t dpl = sizeof(double) * (size_t)c->T;
-  size_t oq0 = k.take(c->nf * dpl), oq1 = k.take(c->nf * dpl), ow = k.take(c->nf * dpl);
-  size_t ofx = k.take(sizeof(double) * (size_t)(c->nf + n_extra(c->dim)) * c->NFX);
-  size_t ofy = k.take(sizeof(double) * (size_t)(c->nf + n_extra(c->dim)) * c->NFY);
+  const size_t T = (size_t)c->T;
+  const size_t nfx = (size_t)(c->nf + n_extra(c->dim));
+  size_t oq0 = 0, oq1 = 0, ow = 0, ofx = 0, ofy = 0;
+  size_t o64a = 0, o64b = 0, o32a = 0, o32b = 0, ow32 = 0, ofx32 = 0, ofy32 = 0;
+  if (!c->fp32) {
+    const size_t dpl = sizeof(double) * T;
+    oq0 = k.take(c->nf * dpl);
+    oq1 = k.take(c->nf * dpl);
+    ow = k.take(c->nf * dpl);
+    ofx = k.take(sizeof(double) * nfx * c->NFX);
+    ofy = k.take(sizeof(double) * nfx * c->NFY);
+  } else {
+    o64a = k.take(2 * sizeof(double) * T);
+    o64b = k.take(2 * sizeof(double) * T);
+    o32a = k.take(c->nf * sizeof(float) * T);
+    o32b = k.take(c->nf * sizeof(float) * T);
+    ow32 = k.take(c->nf * sizeof(float) * T);
+    ofx32 = k.take(sizeof(float) * (nfx + 2) * c->NFX);
+    ofy32 = k.take(sizeof(float) * (nfx + 2) * c->NFY);
+  }
   size_t oio = k.take(sizeof(double) * (size_t)c->nf * c->ncells);
   size_t ort = k.take(sizeof(unsigned long long) * c->np);
   size_t odf = k.take(sizeof(double) * c->np);
@@ -171,12 +221,25 @@ size_t carve(dis_ctx* c, char* base) {
   size_t os2 = k.take(sizeof(int4) * c->seg_fx.size());
   size_t os3 = k.take(sizeof(int4) * std::max<size_t>(1, c->seg_fy.size()));
   size_t os4 = k.take(sizeof(int4) * c->seg_cell.size());
+  size_t ot[3];
+  for (int v = 0; v < 3; ++v) ot[v] = k.take(sizeof(int4) * std::max<size_t>(1, c->tiles[v].size()));
   if (base) {
-    c->q[0] = (double*)(base + oq0);
-    c->q[1] = (double*)(base + oq1);
-    c->W = (double*)(base + ow);
-    c->Fx = (double*)(base + ofx);
-    c->Fy = (double*)(base + ofy);
+    for (int v = 0; v < 3; ++v) c->d_tiles[v] = (int4*)(base + ot[v]);
+    if (!c->fp32) {
+      c->q[0] = (double*)(base + oq0);
+      c->q[1] = (double*)(base + oq1);
+      c->W = (double*)(base + ow);
+      c->Fx = (double*)(base + ofx);
+      c->Fy = (double*)(base + ofy);
+    } else {
+      c->q64[0] = (double*)(base + o64a);
+      c->q64[1] = (double*)(base + o64b);
+      c->q32[0] = (float*)(base + o32a);
+      c->q32[1] = (float*)(base + o32b);
+      c->W32 = (float*)(base + ow32);
+      c->Fx32 = (float*)(base + ofx32);
+      c->Fy32 = (float*)(base + ofy32);
+    }
     c->io = (double*)(base + oio);
     c->rate = (unsigned long long*)(base + ort);
     c->dtfix = (double*)(base + odf);
@@ -212,6 +275,9 @@ int ensure_ws(dis_ctx* c) {
                        cudaMemcpyHostToDevice, c->stream));
   CU(cudaMemcpyAsync(c->d_seg_cell, c->seg_cell.data(), sizeof(int4) * c->seg_cell.size(),
                      cudaMemcpyHostToDevice, c->stream));
+  for (int v = 0; v < 3; ++v)
+    CU(cudaMemcpyAsync(c->d_tiles[v], c->tiles[v].data(), sizeof(int4) * c->tiles[v].size(),
+                       cudaMemcpyHostToDevice, c->stream));
   CU(cudaMemsetAsync(c->status, 0, sizeof(int) * 4, c->stream));
   // The tables above come from host vectors that outlive this call; make sure
   // the copies have finished before the caller may touch them.
@@ -235,10 +301,144 @@ StepArgs base_args(dis_ctx* c) {
   return a;
 }
 
+StepArgs32 base_args32(dis_ctx* c) {
+  StepArgs32 a{};
+  a.pd = c->d_pd;
+  a.T = c->T;
+  a.NFX = c->NFX;
+  a.NFY = c->NFY;
+  a.W = c->W32;
+  a.Fx = c->Fx32;
+  a.Fy = c->Fy32;
+  a.rate = c->rate;
+  a.dtlast = c->dtlast;
+  a.status = c->status;
+  a.kap2 = c->phys.m[1].kap;
+  a.dkap = c->phys.m[0].kap - c->phys.m[1].kap;
+  return a;
+}
+
+// Stage k of the FP32-bulk step (same sequence as launch_step).
+template <int DIM, bool RX>
+void enqueue_stage32(dis_ctx* c, cudaStream_t st, StepArgs32& a, int stg, bool fixed, cudaEvent_t* ev) {
+  const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+  const unsigned np = (unsigned)c->seg_prim.size(), nfx = (unsigned)c->seg_fx.size(),
+                 nfy = (unsigned)c->seg_fy.size(), nc = (unsigned)c->seg_cell.size();
+  a.q64src = stg == 0 ? c->q64[0] : c->q64[1];
+  a.q32src = stg == 0 ? c->q32[0] : c->q32[1];
+  a.q64n = c->q64[0];
+  a.q32n = c->q32[0];
+  a.q64dst = stg == 2 ? c->q64[0] : c->q64[1];
+  a.q32dst = stg == 2 ? c->q32[0] : c->q32[1];
+  a.a = ca[stg];
+  a.b = cb[stg];
+  a.last = stg == 2;
+  if (ev) cudaEventRecord(ev[0], st);
+  k_prim32<DIM, RX><<<np, SEG, 0, st>>>(c->phys, c->physf, a, c->d_seg_prim, (!fixed && stg == 0) ? 1 : 0);
+  if (ev) cudaEventRecord(ev[1], st);
+  k_flux32<DIM, RX, 0><<<nfx, SEG, 0, st>>>(c->physf, a, c->d_seg_fx);
+  if (ev) cudaEventRecord(ev[2], st);
+  if constexpr (DIM == 2) k_flux32<DIM, RX, 1><<<nfy, SEG, 0, st>>>(c->physf, a, c->d_seg_fy);
+  if (ev) cudaEventRecord(ev[3], st);
+  k_update32<DIM, RX><<<nc, SEG, 0, st>>>(c->phys, c->physf, a, c->d_seg_cell);
+  if (ev) cudaEventRecord(ev[4], st);
+}
+
+template <int DIM, bool RX, int TX, int TY, int NT>
+void stage_fused(dis_ctx* c, cudaStream_t st, StepArgs32& a, int v) {
+  constexpr size_t smem = fused32_smem<DIM, RX, TX, TY>();
+  static bool attr_set = false;  // per instantiation, per process
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr_set = true;
+  }
+  k_stage32<DIM, RX, TX, TY, NT><<<(unsigned)c->tiles[v].size(), NT, smem, st>>>(c->phys, c->physf, a,
+                                                                                 c->d_tiles[v]);
+}
+
+template <int DIM, bool RX>
+void stage_fused_v(dis_ctx* c, cudaStream_t st, StepArgs32& a, int v) {
+  if constexpr (DIM == 2) {
+    if (v == 0) stage_fused<DIM, RX, 16, 15, 256>(c, st, a, v);
+    else if (v == 1) stage_fused<DIM, RX, 20, 12, 256>(c, st, a, v);
+    else stage_fused<DIM, RX, 32, 7, 256>(c, st, a, v);
+  } else {
+    if (v == 0) stage_fused<DIM, RX, 122, 1, 128>(c, st, a, v);
+    else if (v == 1) stage_fused<DIM, RX, 250, 1, 256>(c, st, a, v);
+    else stage_fused<DIM, RX, 506, 1, 512>(c, st, a, v);
+  }
+}
+
+template <int DIM, bool RX>
+void set_stage_args32(dis_ctx* c, StepArgs32& a, int stg) {
+  const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+  a.q64src = stg == 0 ? c->q64[0] : c->q64[1];
+  a.q32src = stg == 0 ? c->q32[0] : c->q32[1];
+  a.q64n = c->q64[0];
+  a.q32n = c->q32[0];
+  a.q64dst = stg == 2 ? c->q64[0] : c->q64[1];
+  a.q32dst = stg == 2 ? c->q32[0] : c->q32[1];
+  a.a = ca[stg];
+  a.b = cb[stg];
+  a.last = stg == 2;
+}
+
+// Autotuner: time stage 1 of the fused kernel (it reads q^n and writes only
+// the stage buffer, so the state is untouched) for each tile shape and keep
+// the fastest.
+template <int DIM, bool RX>
+int autotune32(dis_ctx* c) {
+  StepArgs32 a = base_args32(c);
+  a.dtfix = nullptr;
+  CU(cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, c->stream));
+  set_stage_args32<DIM, RX>(c, a, 0);
+  k_cfl32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, c->physf, a, c->d_seg_cell);
+  cudaEvent_t e0, e1;
+  CU(cudaEventCreate(&e0));
+  CU(cudaEventCreate(&e1));
+  double best = 1e30;
+  int bv = 0;
+  for (int v = 0; v < 3; ++v) {
+    for (int w = 0; w < 2; ++w) stage_fused_v<DIM, RX>(c, c->stream, a, v);
+    CU(cudaEventRecord(e0, c->stream));
+    for (int r = 0; r < 3; ++r) stage_fused_v<DIM, RX>(c, c->stream, a, v);
+    CU(cudaEventRecord(e1, c->stream));
+    CU(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, e0, e1));
+    c->tune_ms[v] = ms / 3.0;
+    if (ms < best) { best = ms; bv = v; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CU(cudaGetLastError());
+  c->variant = bv;
+  return DIS_OK;
+}
+
 // Enqueue the kernels of one time step on stream `st`; returns the number of
 // kernel launches.
 template <int DIM, bool RX>
 long long launch_step(dis_ctx* c, cudaStream_t st, bool fixed) {
+  if (c->fp32) {
+    StepArgs32 a = base_args32(c);
+    a.dtfix = fixed ? c->dtfix : nullptr;
+    long long l = 0;
+    if (!fixed) {
+      cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, st);
+      set_stage_args32<DIM, RX>(c, a, 0);
+      k_cfl32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, st>>>(c->phys, c->physf, a, c->d_seg_cell);
+      ++l;
+    }
+    for (int stg = 0; stg < 3; ++stg) {
+      set_stage_args32<DIM, RX>(c, a, stg);
+      stage_fused_v<DIM, RX>(c, st, a, c->variant < 0 ? 0 : c->variant);
+      ++l;
+    }
+    return l;
+  }
   StepArgs a = base_args(c);
   a.dtfix = fixed ? c->dtfix : nullptr;
   const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
@@ -280,6 +480,36 @@ int timed_steps(dis_ctx* c, int n_steps, double* ms) {
   cudaEvent_t ev[5];
   for (int k = 0; k < 5; ++k) CU(cudaEventCreate(&ev[k]));
   double acc[4] = {0, 0, 0, 0};
+  if (c->fp32) {
+    // slot 0: CFL pass (once per step, reported per stage), slot 1: fused stage kernel
+    if (c->variant < 0) {
+      const int rc = autotune32<DIM, RX>(c);
+      if (rc) return rc;
+    }
+    StepArgs32 a32 = base_args32(c);
+    for (int s = 0; s < n_steps; ++s) {
+      CU(cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, c->stream));
+      set_stage_args32<DIM, RX>(c, a32, 0);
+      CU(cudaEventRecord(ev[0], c->stream));
+      k_cfl32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, c->physf, a32, c->d_seg_cell);
+      CU(cudaEventRecord(ev[1], c->stream));
+      CU(cudaEventSynchronize(ev[1]));
+      float t = 0.f;
+      CU(cudaEventElapsedTime(&t, ev[0], ev[1]));
+      acc[0] += t;
+      for (int stg = 0; stg < 3; ++stg) {
+        set_stage_args32<DIM, RX>(c, a32, stg);
+        CU(cudaEventRecord(ev[1], c->stream));
+        stage_fused_v<DIM, RX>(c, c->stream, a32, c->variant);
+        CU(cudaEventRecord(ev[2], c->stream));
+        CU(cudaEventSynchronize(ev[2]));
+        CU(cudaEventElapsedTime(&t, ev[1], ev[2]));
+        acc[1] += t;
+      }
+    }
+    acc[0] *= 3.0;  // reported per stage like the other slots
+    n_steps = -n_steps;  // skip the float64 loop below
+  }
   for (int s = 0; s < n_steps; ++s) {
     CU(cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, c->stream));
     for (int stg = 0; stg < 3; ++stg) {
@@ -308,7 +538,7 @@ int timed_steps(dis_ctx* c, int n_steps, double* ms) {
   }
   CU(cudaGetLastError());
   for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
-  const double nl = 3.0 * n_steps;
+  const double nl = 3.0 * (n_steps < 0 ? -n_steps : n_steps);
   for (int k = 0; k < 4; ++k) ms[k] = acc[k] / nl;
   return DIS_OK;
 }
@@ -327,6 +557,10 @@ int run_steps(dis_ctx* c, int n_steps, bool fixed) {
     CU(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
     CU(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
     CU(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+  }
+  if (c->fp32 && c->variant < 0) {
+    const int rc = autotune32<DIM, RX>(c);
+    if (rc) return rc;
   }
   if (!c->graph[mode]) {
     cudaGraph_t g = nullptr;
@@ -357,6 +591,12 @@ int dispatch_steps(dis_ctx* c, int n, bool fixed) {
 
 template <int DIM, bool RX>
 int do_unpack(dis_ctx* c, const double* src, int prim) {
+  if (c->fp32) {
+    k_unpack32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(
+        c->phys, c->d_pd, c->d_seg_cell, src, c->q64[0], c->q32[0], c->T, prim);
+    CU(cudaGetLastError());
+    return DIS_OK;
+  }
   k_unpack<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, c->d_pd, c->d_seg_cell,
                                                                          src, c->q[0], c->T, prim);
   CU(cudaGetLastError());
@@ -365,6 +605,21 @@ int do_unpack(dis_ctx* c, const double* src, int prim) {
 
 template <int DIM, bool RX>
 int do_pack(dis_ctx* c, double* dst, int prim) {
+  if (c->fp32) {
+    const unsigned ncs = (unsigned)c->seg_cell.size();
+    if (prim) {
+      StepArgs32 a = base_args32(c);
+      a.q64src = c->q64[0];
+      a.q32src = c->q32[0];
+      k_prim32<DIM, RX><<<(unsigned)c->seg_prim.size(), SEG, 0, c->stream>>>(c->phys, c->physf, a,
+                                                                             c->d_seg_prim, 0);
+      k_pack_w32<DIM, RX><<<ncs, SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, c->W32, dst, c->T);
+    } else {
+      k_pack32<DIM, RX><<<ncs, SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, c->q64[0], c->q32[0], dst, c->T);
+    }
+    CU(cudaGetLastError());
+    return DIS_OK;
+  }
   const double* from = c->q[0];
   if (prim) {
     StepArgs a = base_args(c);
@@ -418,8 +673,6 @@ int dis_create(int dim, int n_patches, const dis_patch* patches, int reactive_ma
   if (!(opt->cfl > 0.0 && opt->cfl <= 1.0)) return fail(DIS_EINVAL, "dis_create: cfl must be in (0, 1]");
   if (opt->precision != DIS_FP64 && opt->precision != DIS_FP32_BULK)
     return fail(DIS_EINVAL, "dis_create: unknown precision %d", opt->precision);
-  if (opt->precision == DIS_FP32_BULK)
-    return fail(DIS_EINVAL, "dis_create: FP32-bulk precision is not available in this build");
   for (int p = 0; p < n_patches; ++p) {
     const dis_patch& P = patches[p];
     const int ny = dim == 2 ? P.ny : 1;
@@ -438,6 +691,7 @@ int dis_create(int dim, int n_patches, const dis_patch* patches, int reactive_ma
   c->y = reactive_material;
   c->nf = (dim == 2 ? 11 : 8) + (reactive_material >= 0 ? 1 : 0);
   c->opt = *opt;
+  c->fp32 = opt->precision == DIS_FP32_BULK;
   c->patches.assign(patches, patches + n_patches);
   c->stream = (cudaStream_t)stream;
   cudaGetDevice(&c->device);
@@ -462,6 +716,7 @@ int dis_set_materials(dis_ctx* c, const dis_material* m, int n) {
       return fail(DIS_EINVAL, "dis_set_materials: a reactive material must be an ideal gas with cv > 0");
     c->phys.m[l] = to_dev(m[l]);
   }
+  c->physf = to_float(c->phys);
   c->have_mats = true;
   return DIS_OK;
 }
@@ -572,6 +827,20 @@ int dis_check(dis_ctx* c, int* bad_patch, int* bad_cell) {
 }
 
 long long dis_last_launches(const dis_ctx* c) { return c ? c->launches : 0; }
+
+int dis_tile_choice(const dis_ctx* c, int* tx, int* ty, double* stage_ms) {
+  if (!c) return fail(DIS_EINVAL, "dis_tile_choice: NULL context");
+  if (!c->fp32 || c->variant < 0) {
+    if (tx) *tx = 0;
+    if (ty) *ty = 0;
+    return DIS_OK;
+  }
+  if (tx) *tx = c->dim == 2 ? kTiles2D[c->variant][0] : kTiles1D[c->variant];
+  if (ty) *ty = c->dim == 2 ? kTiles2D[c->variant][1] : 1;
+  if (stage_ms)
+    for (int v = 0; v < 3; ++v) stage_ms[v] = c->tune_ms[v];
+  return DIS_OK;
+}
 
 int dis_step_timed(dis_ctx* c, int n_steps, double* kernel_ms) {
   if (!c || !kernel_ms) return fail(DIS_EINVAL, "dis_step_timed: NULL argument");

@@ -1,0 +1,373 @@
+// fused32.cuh - one fused kernel per SSP-RK3 stage for the FP32-bulk step.
+//
+// A CTA owns a tile of TX x TY interior cells (TX cells of one row in 1D).
+// It recovers the primitives of the tile plus a 3-cell halo into shared
+// memory (ghosts by index map), computes every x face and y face of the tile
+// (MUSCL/THINC-BVD + HLLD) into shared memory, and updates its cells
+// (divergence, non-conservative terms, RK3 combination, last stage: plastic
+// and reactive steps).  Primitives and face data never go to HBM: per stage
+// the tile reads q_src (with halo, mostly from L2) and q^n and writes q_dst.
+//
+// Energy flux split (float64 consistency with the phi1 update): a face keeps
+// F_phi = phi_K u_face, D = X - u_face (X the kappa flux factor, D small) and
+// phi_K; the update forms the kappa part of the energy flux as
+//   kappa_2 (u_face + D) + (kappa_1 - kappa_2) (F_phi + phi_K D)
+// in float64, with the same float F_phi differences that update phi1, so
+// rho E - kappa(phi1) changes only by the small float terms.
+#pragma once
+#include "step32.cuh"
+
+namespace dis {
+
+// shared-memory face slots (per face): nf fluxes (phi slot = F_phi, E slot =
+// soft energy flux), u_face, V row (1 or 2), phi_K, D
+template <int DIM, bool RX>
+struct FSlots {
+  using L = Lay<DIM, RX>;
+  static constexpr int NF = L::NF;
+  static constexpr int UF = NF, VA = NF + 1, VB = DIM == 2 ? NF + 2 : NF + 1;
+  static constexpr int PK = VB + 1, DD = VB + 2, N = VB + 3;
+};
+
+template <int DIM, bool RX, int DIR>
+__device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__ Wsm, int HX, int HY, int hx,
+                                       int hy, float dxn, float dxt, float* __restrict__ Fsm, int nfaces,
+                                       int fidx) {
+  // hx, hy: SMEM coordinates of the face's left (DIR 0) or lower (DIR 1) cell
+  using L = Lay<DIM, RX>;
+  using S = FSlots<DIM, RX>;
+  const int plane = HX * HY;
+  const int sx = DIR == 0 ? 1 : HX;  // along the sweep
+  const int sy = DIR == 0 ? HX : 1;  // across it
+  const int k0 = hy * HX + hx;       // cell a
+  auto Wv = [&](int f, int k) { return Wsm[f * plane + k]; };
+  float ph[6];
+#pragma unroll
+  for (int s = 0; s < 6; ++s) ph[s] = Wv(L::PHI, k0 + (s - 2) * sx);
+  float phiL, phiR;
+  {
+    CandF c[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      float beta = 2.51f;
+      if (DIM == 2 && P.thinc) {
+        const int k = k0 + (s - 1) * sx;
+        const float dn = (Wv(L::PHI, k + sx + sy) + 2.f * Wv(L::PHI, k + sx) + Wv(L::PHI, k + sx - sy)) -
+                         (Wv(L::PHI, k - sx + sy) + 2.f * Wv(L::PHI, k - sx) + Wv(L::PHI, k - sx - sy));
+        const float dt_ = (Wv(L::PHI, k + sy + sx) + 2.f * Wv(L::PHI, k + sy) + Wv(L::PHI, k + sy - sx)) -
+                          (Wv(L::PHI, k - sy + sx) + 2.f * Wv(L::PHI, k - sy) + Wv(L::PHI, k - sy - sx));
+        const float gn = dn / dxn, gt = dt_ / dxt;
+        const float nrm = sqrtf(gn * gn + gt * gt);
+        beta = 2.5f * (nrm == 0.f ? 1.f : fabsf(gn) / nrm) + 0.01f;
+      }
+      c[s] = phi_cand_f(ph[s], ph[s + 1], ph[s + 2], beta, P.thinc != 0);
+    }
+    float Lt, Rt;
+    bvd_f(c[0], c[1], c[2], Lt, Rt);
+    phiL = Rt;
+    bvd_f(c[1], c[2], c[3], Lt, Rt);
+    phiR = Lt;
+  }
+  PrimF w0, w1, w2, w3;
+  auto ld = [&](PrimF& w, int k) {
+    w.phi = Wv(L::PHI, k); w.r1 = Wv(L::A1, k); w.r2 = Wv(L::A2, k); w.u = Wv(L::MX, k);
+    w.p = Wv(L::E, k); w.V11 = Wv(L::V11, k); w.V22 = Wv(L::V22, k); w.V33 = Wv(L::V33, k);
+    w.v = 0.f; w.V12 = 0.f; w.V21 = 0.f; w.lam = 0.f;
+    if constexpr (DIM == 2) { w.v = Wv(L::MY, k); w.V12 = Wv(L::V12, k); w.V21 = Wv(L::V21, k); }
+    if constexpr (RX) w.lam = Wv(L::AL, k);
+  };
+  ld(w0, k0 - sx);
+  ld(w1, k0);
+  ld(w2, k0 + sx);
+  ld(w3, k0 + 2 * sx);
+  PrimF wl, wr;
+#define DIS_RECF(fld)                                            \
+  {                                                              \
+    const float s1 = minmod_f(w1.fld - w0.fld, w2.fld - w1.fld); \
+    const float s2 = minmod_f(w2.fld - w1.fld, w3.fld - w2.fld); \
+    wl.fld = w1.fld + 0.5f * s1;                                 \
+    wr.fld = w2.fld - 0.5f * s2;                                 \
+  }
+  DIS_RECF(r1) DIS_RECF(r2) DIS_RECF(u) DIS_RECF(p) DIS_RECF(V11) DIS_RECF(V22) DIS_RECF(V33)
+  if constexpr (DIM == 2) { DIS_RECF(v) DIS_RECF(V12) DIS_RECF(V21) }
+  else { wl.v = wr.v = 0.f; wl.V12 = wr.V12 = wl.V21 = wr.V21 = 0.f; }
+  if constexpr (RX) { DIS_RECF(lam) } else { wl.lam = wr.lam = 0.f; }
+#undef DIS_RECF
+  wl.phi = phiL;
+  wr.phi = phiR;
+  FStateF sl = face_state_f<DIR>(P, wl);
+  if (!(sl.cL > 0.f)) sl = face_state_f<DIR>(P, w1);
+  FStateF sr = face_state_f<DIR>(P, wr);
+  if (!(sr.cL > 0.f)) sr = face_state_f<DIR>(P, w2);
+  sl.cL = sqrtf(sl.cL);
+  sr.cL = sqrtf(sr.cL);
+  const FaceOutF o = hlld_f<DIR>(sl, sr);
+  const float fu = DIR == 0 ? o.un : o.ut;
+  const float fv = DIR == 0 ? o.ut : o.un;
+  auto put = [&](int slot, float v) { Fsm[slot * nfaces + fidx] = v; };
+  put(L::PHI, o.phi * o.un);
+  put(L::A1, o.Far1);
+  put(L::A2, o.Far2);
+  put(L::MX, DIR == 0 ? o.Fmn : o.Fmt);
+  if constexpr (DIM == 2) put(L::MY, DIR == 0 ? o.Fmt : o.Fmn);
+  put(L::E, o.FE);
+  if constexpr (RX) put(L::AL, o.Farl);
+  put(S::UF, o.un);
+  put(S::PK, o.phi);
+  put(S::DD, o.D);
+  if constexpr (DIR == 0) {
+    put(L::V11, 0.f);
+    if constexpr (DIM == 2) {
+      put(L::V12, 0.f);
+      put(L::V21, o.V21 * fu - o.V11 * fv);
+      put(L::V22, o.V22 * fu - o.V12 * fv);
+      put(S::VA, o.V11);
+      put(S::VB, o.V12);
+    } else {
+      put(L::V22, o.V22 * fu);
+      put(S::VA, o.V11);
+    }
+    put(L::V33, o.V33 * fu);
+  } else if constexpr (DIM == 2) {
+    put(L::V11, o.V11 * fv - o.V21 * fu);
+    put(L::V12, o.V12 * fv - o.V22 * fu);
+    put(L::V21, 0.f);
+    put(L::V22, 0.f);
+    put(L::V33, o.V33 * fv);
+    put(S::VA, o.V21);
+    put(S::VB, o.V22);
+  }
+}
+
+// Shared memory bytes of a tile.
+template <int DIM, bool RX, int TX, int TY>
+constexpr size_t fused32_smem() {
+  using S = FSlots<DIM, RX>;
+  constexpr int HX = TX + 2 * NG, HY = DIM == 2 ? TY + 2 * NG : 1;
+  constexpr int NFX = (TX + 1) * TY, NFY = DIM == 2 ? TX * (TY + 1) : 0;
+  return sizeof(float) * ((size_t)Lay<DIM, RX>::NF * HX * HY + (size_t)S::N * (NFX + NFY)) + 16 * sizeof(double);
+}
+
+template <int DIM, bool RX, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) k_stage32(Phys P, PhysF F, StepArgs32 A, const int4* __restrict__ tiles) {
+  static_assert(TX * TY <= NT, "one thread per tile cell in the update phase");
+  using L = Lay<DIM, RX>;
+  using S = FSlots<DIM, RX>;
+  constexpr int NF = L::NF;
+  constexpr int HX = TX + 2 * NG, HY = DIM == 2 ? TY + 2 * NG : 1;
+  constexpr int NFX = (TX + 1) * TY, NFY = DIM == 2 ? TX * (TY + 1) : 0;
+  extern __shared__ __align__(16) float sm[];
+  float* Wsm = sm;
+  float* Fxs = Wsm + NF * HX * HY;
+  float* Fys = Fxs + S::N * NFX;
+  const int4 t = tiles[blockIdx.x];
+  const PatchDev pd = A.pd[t.x];
+  const int i0 = t.y, j0 = t.z;
+  const int tid = threadIdx.x;
+  const float dxf = (float)pd.dx, dyf = (float)pd.dy;
+
+  // 1. primitives of the tile and its halo
+  for (int c = tid; c < HX * HY; c += NT) {
+    const int hx = c % HX, hy = c / HX;
+    const int i = i0 - NG + hx;
+    const int j = DIM == 2 ? j0 - NG + hy : 0;
+    if (i < -NG || i >= pd.nx + NG || (DIM == 2 && (j < -NG || j >= pd.ny + NG))) continue;
+    bool fx = false, fy = false;
+    const int si = ghost_map(i, pd.nx, pd.bc[0], pd.bc[1], fx);
+    const int sj = DIM == 2 ? ghost_map(j, pd.ny, pd.bc[2], pd.bc[3], fy) : 0;
+    PrimF w = cons_to_prim32<DIM, RX>(P, F, A.q64src, A.q32src, A.T, cidx(pd, si, sj));
+    if (fx) { w.u = -w.u; w.V12 = -w.V12; w.V21 = -w.V21; }
+    if (fy) { w.v = -w.v; w.V12 = -w.V12; w.V21 = -w.V21; }
+    const int plane = HX * HY;
+    Wsm[L::PHI * plane + c] = w.phi;
+    Wsm[L::A1 * plane + c] = w.r1;
+    Wsm[L::A2 * plane + c] = w.r2;
+    Wsm[L::MX * plane + c] = w.u;
+    if constexpr (DIM == 2) Wsm[L::MY * plane + c] = w.v;
+    Wsm[L::E * plane + c] = w.p;
+    Wsm[L::V11 * plane + c] = w.V11;
+    if constexpr (DIM == 2) { Wsm[L::V12 * plane + c] = w.V12; Wsm[L::V21 * plane + c] = w.V21; }
+    Wsm[L::V22 * plane + c] = w.V22;
+    Wsm[L::V33 * plane + c] = w.V33;
+    if constexpr (RX) Wsm[L::AL * plane + c] = w.lam;
+  }
+  __syncthreads();
+
+  // 2. all x faces ((TX + 1) per interior row) and y faces (TX per face row,
+  //    TY + 1 face rows) of the tile, in one loop so the threads stay busy
+  for (int f = tid; f < NFX + NFY; f += NT) {
+    if (f < NFX) {
+      const int fx = f % (TX + 1), fy = f / (TX + 1);
+      const int i = i0 + fx, j = j0 + fy;  // face between cells i-1 and i
+      if (i > pd.nx || (DIM == 2 && j >= pd.ny)) continue;
+      face32<DIM, RX, 0>(F, Wsm, HX, HY, fx + NG - 1, DIM == 2 ? fy + NG : 0, dxf, dyf, Fxs, NFX, f);
+    } else if constexpr (DIM == 2) {
+      const int g = f - NFX;
+      const int fx = g % TX, fy = g / TX;
+      const int i = i0 + fx, j = j0 + fy;  // face between rows j-1 and j
+      if (i >= pd.nx || j > pd.ny) continue;
+      face32<DIM, RX, 1>(F, Wsm, HX, HY, fx + NG, fy + NG - 1, dyf, dxf, Fys, NFY, g);
+    }
+  }
+  // the step's dt, once per CTA
+  __shared__ double dt_sh;
+  if (tid == 0) dt_sh = A.dtfix ? A.dtfix[t.x] : P.cfl / __longlong_as_double((long long)A.rate[t.x]);
+  __syncthreads();
+
+  // 4. update of the tile's cells
+  if (tid >= TX * TY) return;
+  const int lx = tid % TX, ly = tid / TX;
+  const int i = i0 + lx, j = j0 + ly;
+  if (i >= pd.nx || (DIM == 2 && j >= pd.ny)) return;
+  const long long k = cidx(pd, i, j);
+  const long long T = A.T;
+  float q[NF], D[NF];
+#pragma unroll
+  for (int c = 0; c < NF; ++c) q[c] = (c == L::PHI || c == L::E) ? 0.f : A.q32src[c * T + k];
+  const double phi_d = A.q64src[k];
+  const double E_d = A.q64src[T + k];
+  const float idx_ = 1.f / dxf;
+  const int fl = ly * (TX + 1) + lx, fr = fl + 1;
+  auto FX = [&](int s, int f) { return Fxs[s * NFX + f]; };
+#pragma unroll
+  for (int c = 0; c < NF; ++c) D[c] = (FX(c, fr) - FX(c, fl)) * idx_;
+  float divu = (FX(S::UF, fr) - FX(S::UF, fl)) * idx_;
+  float bx = (FX(S::VA, fr) - FX(S::VA, fl)) * idx_;
+  float by = 0.f;
+  // Float64 terms.  Per direction: the float phi1 flux difference dF (shared
+  // with the energy's kappa part, so rho E - kappa(phi1) cancels exactly) and
+  // the small terms (soft energy flux, kappa_2 (u + D), (kappa_1 - kappa_2) phi_K D)
+  // summed in float32.
+  const float k2f = (float)A.kap2, dkf = (float)A.dkap;
+  const double dFx = (double)(FX(L::PHI, fr) - FX(L::PHI, fl));
+  const float smx = (FX(L::E, fr) - FX(L::E, fl)) +
+                    k2f * ((FX(S::UF, fr) + FX(S::DD, fr)) - (FX(S::UF, fl) + FX(S::DD, fl))) +
+                    dkf * (FX(S::PK, fr) * FX(S::DD, fr) - FX(S::PK, fl) * FX(S::DD, fl));
+  const double idxd = (double)idx_;
+  double Dphi = dFx * idxd;
+  double DE = fma(A.dkap, dFx, (double)smx) * idxd;
+  if constexpr (DIM == 2) {
+    const float idy = 1.f / dyf;
+    const int fb = ly * TX + lx, ft = fb + TX;
+    auto FY = [&](int s_, int f) { return Fys[s_ * NFY + f]; };
+#pragma unroll
+    for (int c = 0; c < NF; ++c) D[c] += (FY(c, ft) - FY(c, fb)) * idy;
+    divu += (FY(S::UF, ft) - FY(S::UF, fb)) * idy;
+    bx += (FY(S::VA, ft) - FY(S::VA, fb)) * idy;
+    by = (FX(S::VB, fr) - FX(S::VB, fl)) * idx_ + (FY(S::VB, ft) - FY(S::VB, fb)) * idy;
+    const double dFy = (double)(FY(L::PHI, ft) - FY(L::PHI, fb));
+    const float smy = (FY(L::E, ft) - FY(L::E, fb)) +
+                      k2f * ((FY(S::UF, ft) + FY(S::DD, ft)) - (FY(S::UF, fb) + FY(S::DD, fb))) +
+                      dkf * (FY(S::PK, ft) * FY(S::DD, ft) - FY(S::PK, fb) * FY(S::DD, fb));
+    const double idyd = (double)idy;
+    Dphi = fma(dFy, idyd, Dphi);
+    DE = fma(fma(A.dkap, dFy, (double)smy), idyd, DE);
+  }
+  const float rho = q[L::A1] + q[L::A2];
+  const float uc = q[L::MX] / rho;
+  float vc = 0.f;
+  if constexpr (DIM == 2) vc = q[L::MY] / rho;
+  const float t23 = 2.f / 3.f;
+  Dphi -= phi_d * (double)divu;
+  D[L::V11] -= t23 * q[L::V11] * divu - uc * bx;
+  D[L::V22] -= t23 * q[L::V22] * divu - vc * by;
+  D[L::V33] -= t23 * q[L::V33] * divu;
+  if constexpr (DIM == 2) {
+    D[L::V12] -= t23 * q[L::V12] * divu - uc * by;
+    D[L::V21] -= t23 * q[L::V21] * divu - vc * bx;
+  }
+  const double dt = dt_sh;
+  const float dtf = (float)dt;
+  float o[NF];
+  double ophi, oE;
+  if (A.a == 0.0) {
+#pragma unroll
+    for (int c = 0; c < NF; ++c) o[c] = q[c] - dtf * D[c];
+    ophi = phi_d - dt * Dphi;
+    oE = E_d - dt * DE;
+  } else {
+    const float af = (float)A.a, bf = (float)A.b;
+#pragma unroll
+    for (int c = 0; c < NF; ++c)
+      o[c] = (c == L::PHI || c == L::E) ? 0.f : af * A.q32n[c * T + k] + bf * (q[c] - dtf * D[c]);
+    ophi = A.a * A.q64n[k] + A.b * (phi_d - dt * Dphi);
+    oE = A.a * A.q64n[T + k] + A.b * (E_d - dt * DE);
+  }
+  if (A.last) {
+    float v12 = 0.f, v21 = 0.f;
+    if constexpr (DIM == 2) { v12 = o[L::V12]; v21 = o[L::V21]; }
+    if (ophi > 1e-3 && ophi < 1.0 - 1e-3) {
+      double d11 = o[L::V11], d12 = v12, d21 = v21, d22 = o[L::V22], d33 = o[L::V33];
+      plastic(P, ophi, dt, d11, d12, d21, d22, d33);
+      o[L::V11] = (float)d11; v12 = (float)d12; v21 = (float)d21; o[L::V22] = (float)d22; o[L::V33] = (float)d33;
+    } else {
+      plastic_f(F, (float)ophi, dtf, o[L::V11], v12, v21, o[L::V22], o[L::V33]);
+    }
+    if constexpr (DIM == 2) { o[L::V12] = v12; o[L::V21] = v21; }
+    if constexpr (RX) {
+      const int y = P.y;
+      const MatT<float>& m = F.m[y];
+      const float phi1 = (float)ophi;
+      const float ary = y == 0 ? o[L::A1] : o[L::A2];
+      const float phy = y == 0 ? phi1 : (float)(1.0 - ophi);
+      const float rr = o[L::A1] + o[L::A2];
+      const float mx = o[L::MX];
+      float my = 0.f;
+      if constexpr (DIM == 2) my = o[L::MY];
+      const float KE = 0.5f * (mx * mx + my * my) / rr;
+      const StrainF s = strain_f(o[L::V11], v12, v21, o[L::V22], o[L::V33]);
+      const double kap = ophi * P.m[0].kap + (1.0 - ophi) * P.m[1].kap;
+      const double num = oE - kap - (double)KE - (double)soft_ref_f(F, phi1, o[L::A1], o[L::A2], 0.f, s.J2);
+      const float xi = xi_f(F, phi1);
+      const float p0 = (float)num / xi;
+      const float Tfac = m.iGm1 / ((ary / phy) * m.cv);
+      const float Qx = m.Q / xi;
+      auto fr_ = [&](float Lm) {
+        const float Tk = (p0 - Qx * Lm) * Tfac;
+        return Tk > 0.f ? -m.A * Lm * expf(-m.Tact / Tk) : 0.f;
+      };
+      const float L0 = o[L::AL];
+      const float k1 = fr_(L0);
+      const float k2 = fr_(L0 + 0.5f * dtf * k1);
+      const float k3 = fr_(L0 + 0.5f * dtf * k2);
+      const float k4 = fr_(L0 + dtf * k3);
+      o[L::AL] = L0 + dtf / 6.f * (k1 + 2.f * k2 + 2.f * k3 + k4);
+    }
+    bool bad = !(ophi >= -1e-6 && ophi <= 1.0 + 1e-6) || !isfinite(oE);
+#pragma unroll
+    for (int c = 0; c < NF; ++c) bad |= (c != L::PHI && c != L::E) && !isfinite(o[c]);
+    if (bad) flag_bad(A.status, t.x, i + pd.nx * j);
+    if (i == 0 && j == 0) A.dtlast[t.x] = dt;
+  }
+#pragma unroll
+  for (int c = 0; c < NF; ++c)
+    if (c != L::PHI && c != L::E) A.q32dst[c * T + k] = o[c];
+  A.q64dst[k] = ophi;
+  A.q64dst[T + k] = oE;
+}
+
+// CFL rate of the state at the start of a step (FP32-bulk): per-patch max of
+// sum_d (|u_d| + c_L) / dx_d over interior cells.
+template <int DIM, bool RX>
+__global__ void __launch_bounds__(SEG) k_cfl32(Phys P, PhysF F, StepArgs32 A, const int4* __restrict__ segs) {
+  const int4 g = segs[blockIdx.x];
+  const PatchDev pd = A.pd[g.x];
+  const int i = g.z + threadIdx.x, j = g.y;
+  float r = 0.f;
+  if (threadIdx.x < g.w) {
+    const PrimF w = cons_to_prim32<DIM, RX>(P, F, A.q64src, A.q32src, A.T, cidx(pd, i, j));
+    const StrainF s = strain_f(w.V11, w.V12, w.V21, w.V22, w.V33);
+    const float rho = w.phi * w.r1 + (1.f - w.phi) * w.r2;
+    const float cL2 = cL2_f(F, w.phi, rho, w.p, s.J2);
+    if (!(cL2 > 0.f) || !(rho > 0.f)) flag_bad(A.status, g.x, i + pd.nx * j);
+    const float cL = sqrtf(fmaxf(cL2, 0.f));
+    r = (fabsf(w.u) + cL) / (float)pd.dx;
+    if (DIM == 2) r += (fabsf(w.v) + cL) / (float)pd.dy;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+  if ((threadIdx.x & 31) == 0 && r > 0.f)
+    atomicMax(A.rate + g.x, (unsigned long long)__double_as_longlong((double)r));
+}
+
+}  // namespace dis

@@ -30,23 +30,46 @@ namespace dis {
 
 constexpr int NG = 3;  // ghost layers: a face's BVD choice reaches 3 cells out
 
-struct MatDev {
-  double gamma, pinf, einf, G, sigy, chi0, Q, cv, A, Tact;
+template <class R>
+struct MatT {
+  R gamma, pinf, einf, G, sigy, chi0, Q, cv, A, Tact;
   int plastic, reactive;
-  double iGm1;  // 1 / (gamma - 1)
-  double gi;    // gamma / (gamma - 1)
-  double kap;   // gamma p_inf / (gamma - 1)
-  double gG;    // gamma G / (gamma - 1)
-  double GoG;   // G / (gamma - 1)
-  double JY;    // yield strain invariant sigma_y / (sqrt(6) G)
+  R iGm1;  // 1 / (gamma - 1)
+  R gi;    // gamma / (gamma - 1)
+  R kap;   // gamma p_inf / (gamma - 1)
+  R gG;    // gamma G / (gamma - 1)
+  R GoG;   // G / (gamma - 1)
+  R JY;    // yield strain invariant sigma_y / (sqrt(6) G)
 };
 
-struct Phys {
-  MatDev m[2];
+template <class R>
+struct PhysT {
+  MatT<R> m[2];
   int y;      // reactive material (0/1) or -1
   int thinc;  // THINC-BVD steepening on phi1
-  double cfl;
+  R cfl;
 };
+
+using MatDev = MatT<double>;
+using Phys = PhysT<double>;
+
+// Single-precision copy of the closure parameters (for the FP32-bulk kernels).
+inline PhysT<float> to_float(const Phys& P) {
+  PhysT<float> f{};
+  for (int l = 0; l < 2; ++l) {
+    const MatDev& d = P.m[l];
+    MatT<float>& m = f.m[l];
+    m.gamma = (float)d.gamma; m.pinf = (float)d.pinf; m.einf = (float)d.einf; m.G = (float)d.G;
+    m.sigy = (float)d.sigy; m.chi0 = (float)d.chi0; m.Q = (float)d.Q; m.cv = (float)d.cv;
+    m.A = (float)d.A; m.Tact = (float)d.Tact; m.plastic = d.plastic; m.reactive = d.reactive;
+    m.iGm1 = (float)d.iGm1; m.gi = (float)d.gi; m.kap = (float)d.kap; m.gG = (float)d.gG;
+    m.GoG = (float)d.GoG; m.JY = (float)d.JY;
+  }
+  f.y = P.y;
+  f.thinc = P.thinc;
+  f.cfl = (float)P.cfl;
+  return f;
+}
 
 // Field slots of the conservative and primitive states (same positions).
 template <int DIM, bool RX>
@@ -64,13 +87,17 @@ struct Lay<2, RX> {
   static constexpr int NX_EXTRA = 3;  // face extras: u_n, V_n1, V_n2
 };
 
-struct Prim {
-  double phi, r1, r2, u, v, p, V11, V12, V21, V22, V33, lam;
+template <class R>
+struct PrimT {
+  R phi, r1, r2, u, v, p, V11, V12, V21, V22, V33, lam;
 };
+using Prim = PrimT<double>;
 
-struct Strain {
-  double H11, H12, H22, H33, J2;
+template <class R>
+struct StrainT {
+  R H11, H12, H22, H33, J2;
 };
+using Strain = StrainT<double>;
 
 __device__ __forceinline__ Strain strain_of(double a, double b, double c, double d, double e) {
   const double B11 = a * a + b * b, B12 = a * c + b * d, B22 = c * c + d * d, B33 = e * e;

@@ -119,6 +119,13 @@ class Solver:
         L.dis_step_timed(self.ctx, n, ms.ctypes.data)
         return ms
 
+    def tile_choice(self):
+        """(TX, TY, stage ms of the three tuned shapes) of an FP32-bulk context."""
+        tx, ty = ctypes.c_int(0), ctypes.c_int(0)
+        ms = np.zeros(3, np.float64)
+        L.load().dis_tile_choice(self.ctx, ctypes.byref(tx), ctypes.byref(ty), ms.ctypes.data)
+        return tx.value, ty.value, ms
+
     def check(self):
         return L.dis_check(self.ctx)
 
