@@ -60,6 +60,7 @@ def thinc_faces(q, beta):
     mixed = (C > THINC_DELTA) & (C < 1 - THINC_DELTA) & ((qp - qc) * (qc - qm) > 0)
     # keep the transcendental arguments finite where the mask is off
     th = torch.where(mixed, theta, torch.ones_like(theta))
+    C = torch.where(mixed, C, torch.full_like(C, 0.5))
     Bc = torch.exp(th * b * (2 * C - 1))
     tb = torch.tanh(b)
     Ac = (Bc / torch.cosh(b) - 1) / tb
@@ -111,7 +112,9 @@ def youngs_abs_normal(phi, dx, dy):
     gy = (phi[1:, 1:] + phi[1:, :-1] - phi[:-1, 1:] - phi[:-1, :-1]) / (2 * dy)
     cx = 0.25 * (gx[1:, 1:] + gx[:-1, 1:] + gx[1:, :-1] + gx[:-1, :-1])
     cy = 0.25 * (gy[1:, 1:] + gy[:-1, 1:] + gy[1:, :-1] + gy[:-1, :-1])
-    norm = torch.sqrt(cx * cx + cy * cy)
+    n2 = cx * cx + cy * cy
+    pos = n2 > 0  # sqrt taken only where positive so that its derivative stays finite
+    norm = torch.where(pos, torch.sqrt(torch.where(pos, n2, torch.ones_like(n2))), torch.zeros_like(n2))
     zero = norm == 0
     nx_ = torch.where(zero, torch.ones_like(cx), cx.abs() / torch.where(zero, torch.ones_like(norm), norm))
     ny_ = torch.where(zero, torch.ones_like(cy), cy.abs() / torch.where(zero, torch.ones_like(norm), norm))

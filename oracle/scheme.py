@@ -292,26 +292,38 @@ def _axpy(a, x, b, y):
     return {k: a * x[k] + b * y[k] for k in x}
 
 
+def _sqrt0(x):
+    """Square root whose derivative at 0 is taken as 0 (a strain norm at zero
+    strain is not differentiable; its subgradient 0 is used)."""
+    pos = x > 0
+    return torch.where(pos, torch.sqrt(torch.where(pos, x, torch.ones_like(x))), torch.zeros_like(x))
+
+
 def plastic_update(q, mats, dt, iters=64):
-    """Section 3.2: J*, per-material J* by bisection, mixture J*, Pade exp."""
+    """Section 3.2: J*, per-material relaxed J*, mixture J*, Pade exp.
+
+    Perfect plasticity returns radially onto the yield surface,
+    J*_l = min(J*, J_Y) with J_Y = sigma_Y / (sqrt(6) G) (the chi0 -> infinity
+    limit of the relaxation objective); a finite rate chi0 solves the objective
+    R(J) = J - J* + dt chi(J) by bisection on [0, J*]."""
     phis = phases(q["phi1"])
     devH, J2 = hencky_dev(q["V"])
-    Jst = torch.sqrt(J2)
+    Jst = _sqrt0(J2)
     num = torch.zeros_like(Jst)
     den = torch.zeros_like(Jst)
     for m, ph in zip(mats, phis):
         if m["G"] == 0.0:
             Jl = torch.zeros_like(Jst)  # fluid: no shear strain survives
+        elif m["plastic"] == 1:
+            JY = torch.as_tensor(m["sigma_y"] / (math.sqrt(6.0) * m["G"]), dtype=F64)
+            Jl = torch.minimum(Jst, JY)
+        elif m["plastic"] == 0:
+            Jl = Jst
         else:
-            JY = m["sigma_y"] / (math.sqrt(6.0) * m["G"]) if m["plastic"] else math.inf
-
             def chi(J):
-                # ideal plasticity rate chi0 H[sqrt(3/2) |dev sigma| - sigma_Y], |dev sigma| = 2 G J
+                # rate-dependent plasticity: chi0 H[sqrt(3/2) |dev sigma| - sigma_Y], |dev sigma| = 2 G J
                 on = math.sqrt(1.5) * 2.0 * m["G"] * J - m["sigma_y"] > 0
-                c0 = math.inf if m["plastic"] == 1 else m["chi0"]
-                if m["plastic"] == 0:
-                    return torch.zeros_like(J)
-                return torch.where(on, torch.full_like(J, c0), torch.zeros_like(J))
+                return torch.where(on, torch.full_like(J, m["chi0"]), torch.zeros_like(J))
 
             lo = torch.zeros_like(Jst)
             hi = Jst.clone()
@@ -322,7 +334,6 @@ def plastic_update(q, mats, dt, iters=64):
                 lo = torch.where(neg, mid, lo)
                 hi = torch.where(neg, hi, mid)
             Jl = 0.5 * (lo + hi)
-            del JY
         num = num + ph / Gamma(m) * Jl
         den = den + ph / Gamma(m)
     Jnew = num / den

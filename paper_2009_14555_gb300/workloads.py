@@ -253,6 +253,37 @@ def batched_riemann_1d(n_problems: int = 4096, seed: int = 3, steps: int = 300,
                     steps, False)
 
 
+def smooth_disc_2d(n: int = 16, steps: int = 10, u0: float = 100.0, seed: int = 5,
+                   sigma_y: float | None = None, name=None) -> Workload:
+    """Smooth solid|gas problem for derivative checks on [0, 1]^2 (periodic).
+
+    An elastoplastic disc (radius 0.25 at the centre) with a tanh-profiled
+    volume fraction (width 1.5 cells), a Gaussian x-velocity pulse of peak u0
+    (width 0.2), a 1 % seeded smooth density modulation and uniform pressure:
+    no shocks, no THINC.  sigma_y overrides the solid's yield stress.
+    """
+    w, k = _blank(2, False, n, n)
+    d = 1.0 / n
+    xc = (np.arange(n) + 0.5) * d
+    X, Y = np.meshgrid(xc, xc)
+    r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2)
+    phi = 0.5 * (1.0 + np.tanh((0.25 - r) / (1.5 * d)))
+    w[k["phi1"]] = EPS_PHI + (1 - 2 * EPS_PHI) * phi
+    rng = np.random.default_rng(seed)
+    a, b = rng.uniform(0, 2 * np.pi, 2)
+    mod = 1.0 + 0.01 * np.sin(2 * np.pi * X + a) * np.cos(2 * np.pi * Y + b)
+    w[k["rho1"]] = SOLID_RHO0 * mod
+    w[k["rho2"]] = 1.2 * mod
+    w[k["p"]] = 1e5
+    w[k["u"]] = u0 * np.exp(-r ** 2 / (2 * 0.2 ** 2))
+    solid = dict(SOLID)
+    if sigma_y is not None:
+        solid["sigma_y"] = sigma_y
+    per = (BC_PERIODIC,) * 4
+    p = Patch(nx=n, ny=n, dx=d, dy=d, bc=per, prim=w)
+    return Workload(name or f"2d_smooth_disc_{n}", 2, [solid, AIR], [p], 0.6, steps, False)
+
+
 def adjoint_case_2d(n: int = 256, steps: int = 200, seed: int = 4) -> Workload:
     """256^2 shock-disc problem with a smooth Gaussian density perturbation field."""
     wl = shock_disc_2d(n, steps=steps, name=f"2d_shock_disc_adjoint_{n}")
@@ -270,4 +301,5 @@ CONFIGS = {
     "2d_reactive_plate": reactive_plate_2d,
     "1d_batch": batched_riemann_1d,
     "2d_adjoint": adjoint_case_2d,
+    "2d_smooth_disc": smooth_disc_2d,
 }
