@@ -94,7 +94,8 @@ typedef struct dis_ctx dis_ctx;
 int dis_create(int dim, int n_patches, const dis_patch* patches, int reactive_material,
                const dis_options* opt, void* stream, dis_ctx** out);
 
-/* Set the two materials (n must be 2).  Copies `m`. */
+/* Set the two materials (n must be 2).  Copies `m`.  May be called again
+ * between steps (new parameters take effect from the next step). */
 int dis_set_materials(dis_ctx* ctx, const dis_material* m, int n);
 
 /* Bytes of device workspace the context needs (state buffers, primitives,
@@ -152,6 +153,49 @@ int dis_tile_choice(const dis_ctx* ctx, int* tx, int* ty, double* stage_ms);
  * 1D) and update kernels (float64), or of the CFL pass and the fused stage
  * kernel in slots 0 and 1 (FP32-bulk).  Synchronises after every stage. */
 int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
+
+/* ---- Adjoint (reverse mode) of the float64 step -------------------------
+ * The paper has no adjoint; these calls differentiate the discrete step of
+ * Section 3 (EOS recovery, MUSCL/THINC-BVD reconstruction, elastic HLLD-type
+ * fluxes, non-conservative terms, SSP-RK3, plastic radial return of Section
+ * 3.2, RK4 reaction of Section 3.3) with every time step frozen at its
+ * recorded value.  Branches (limiter, BVD choice, Riemann region, radial
+ * return) are differentiated on the side the forward run took. */
+
+/* Parameters with an adjoint: for material l, grad_params[3 l + k] is the
+ * derivative with respect to k = 0: shear modulus G, 1: yield stress
+ * sigma_y, 2: heat release Q (zero unless l is the reactive material). */
+#define DIS_NPARAM 6
+
+/* Forward run recorded for dis_adjoint, from the current state (float64
+ * contexts only).  Takes n_steps steps, with the CFL time step (dt_in NULL)
+ * or with dt_in[n * n_patches + p] (host array), copies the state to a
+ * library-owned checkpoint every checkpoint_every steps and records every
+ * dt.  If objective_material is 0 or 1 it accumulates the running objective
+ *   J = sum_n dt_n sum_cells phi_l (rho u) dx dy     (l = objective_material,
+ * states after each step, x momentum of the material's volume fraction) and
+ * returns it in J_out (may be NULL).  dt_out (host, n_steps x n_patches, may
+ * be NULL) receives the time steps.  Leaves the context at the final state,
+ * like dis_step.  Device memory: (ceil(n_steps / checkpoint_every) +
+ * checkpoint_every + 8) states, allocated here, kept for dis_adjoint and
+ * released by dis_destroy.  Returns DIS_EINVAL (bad arguments, FP32-bulk
+ * context), DIS_ESTATE (no state), DIS_ENOMEM, DIS_ECUDA.  Synchronises. */
+int dis_adj_forward(dis_ctx* ctx, int n_steps, int checkpoint_every, int objective_material,
+                    const double* dt_in, double* dt_out, double* J_out);
+
+/* Reverse sweep of the last dis_adj_forward run: given the adjoint of the
+ * final conservative state qbar_final (packed layout of dis_get_state, host
+ * or device per qbar_on_device; NULL for zero) and the adjoint jbar of the
+ * running objective, writes the gradient with respect to the initial state
+ * into grad_init (packed layout, conservative or primitive variables per
+ * out_kind; host or device per grad_on_device) and, if grad_params is not
+ * NULL, the DIS_NPARAM parameter gradients selected by param_mask (bit k for
+ * entry k; the others are set to 0).  Segments of checkpoint_every steps are
+ * recomputed from their checkpoints (the state of the context is not
+ * touched).  Returns DIS_ESTATE without a recorded run, DIS_EINVAL,
+ * DIS_ECUDA.  Synchronises. */
+int dis_adjoint(dis_ctx* ctx, const double* qbar_final, int qbar_on_device, double jbar, int out_kind,
+                double* grad_init, int grad_on_device, double* grad_params, unsigned param_mask);
 
 /* Largest patch count accepted by dis_cfl_dt_static. */
 #define DIS_STATIC_MAX_PATCHES 16384

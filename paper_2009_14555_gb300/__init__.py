@@ -2,6 +2,7 @@
 
   workloads   seeded synthetic inputs shaped like the paper's problems
   solver      Solver: the C ABI of libdis.so over torch device memory
+  autograd    torch.autograd.Function over the library's adjoint
   _lib        ctypes binding of include/dis.h
   build       nvcc build of libdis.so for sm_103a
 """

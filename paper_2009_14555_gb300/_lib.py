@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libdis.so")
 DIS_OK, DIS_EINVAL, DIS_ENOMEM, DIS_ECUDA, DIS_ENONPHYSICAL, DIS_ESTATE = 0, -1, -2, -3, -4, -5
 DIS_CONSERVATIVE, DIS_PRIMITIVE = 0, 1
 DIS_FP64, DIS_FP32_BULK = 0, 1
+DIS_NPARAM = 6  # per material l: G, sigma_y, Q at 3 l + k
 
 
 class DisMaterial(ctypes.Structure):
@@ -57,6 +58,9 @@ SIGNATURES = {
     "dis_tile_choice": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), c_void_p]),
     "dis_cfl_dt_static": (c_int, [c_int, c_int, POINTER(DisPatch), POINTER(DisMaterial), c_int,
                                    c_double, c_void_p, c_void_p, c_void_p]),
+    "dis_adj_forward": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, POINTER(c_double)]),
+    "dis_adjoint": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p, c_int, c_void_p,
+                            ctypes.c_uint]),
     "dis_last_error": (c_char_p, []),
     "dis_destroy": (None, [c_void_p]),
 }
@@ -142,6 +146,19 @@ def dis_last_launches(ctx):
 
 def dis_step_timed(ctx, n, ms_ptr):
     return check(load().dis_step_timed(ctx, n, c_void_p(ms_ptr)))
+
+
+def dis_adj_forward(ctx, n_steps, every, material, dt_in_ptr, dt_out_ptr):
+    J = c_double(0.0)
+    check(load().dis_adj_forward(ctx, n_steps, every, material, c_void_p(dt_in_ptr) if dt_in_ptr else None,
+                                 c_void_p(dt_out_ptr) if dt_out_ptr else None, ctypes.byref(J)))
+    return J.value
+
+
+def dis_adjoint(ctx, qbar_ptr, qbar_on_device, jbar, out_kind, grad_ptr, grad_on_device, params_ptr, mask):
+    return check(load().dis_adjoint(ctx, c_void_p(qbar_ptr) if qbar_ptr else None, int(qbar_on_device),
+                                    float(jbar), out_kind, c_void_p(grad_ptr), int(grad_on_device),
+                                    c_void_p(params_ptr) if params_ptr else None, mask))
 
 
 def dis_last_error():

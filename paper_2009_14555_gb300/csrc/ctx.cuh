@@ -1,0 +1,71 @@
+// ctx.cuh - the library context shared by the translation units of libdis
+// (internal; not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/dis.h"
+#include "fused32.cuh"
+
+using dis::PatchDev;
+using dis::Phys;
+using dis::PhysF;
+
+struct dis_adj;  // adjoint buffers and the recorded forward run (adjoint.cu)
+
+struct dis_ctx {
+  int dim = 1, np = 0, y = -1, nf = 0;
+  dis_options opt{};
+  Phys phys{};
+  PhysF physf{};
+  bool fp32 = false;
+  bool have_mats = false, have_state = false;
+  std::vector<dis_patch> patches;
+  std::vector<PatchDev> pd;
+  long long T = 0, NFX = 0, NFY = 0, ncells = 0;
+  std::vector<int4> seg_prim, seg_fx, seg_fy, seg_cell;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  // workspace
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_owned = false, ws_ready = false;
+  double* q[2] = {nullptr, nullptr};  // q^n, stage buffer
+  double* W = nullptr;
+  double* Fx = nullptr;
+  double* Fy = nullptr;
+  double* io = nullptr;
+  unsigned long long* rate = nullptr;
+  double* dtfix = nullptr;
+  double* dtlast = nullptr;
+  int* status = nullptr;
+  // FP32-bulk fused stage kernel: tile tables per tile shape, chosen shape
+  std::vector<int4> tiles[3];
+  int4* d_tiles[3] = {nullptr, nullptr, nullptr};
+  int variant = -1;
+  double tune_ms[3] = {0, 0, 0};
+  // FP32-bulk buffers: (phi1, rho E) float64 pairs and float32 planes
+  double* q64[2] = {nullptr, nullptr};
+  float* q32[2] = {nullptr, nullptr};
+  float* W32 = nullptr;
+  float* Fx32 = nullptr;
+  float* Fy32 = nullptr;
+  PatchDev* d_pd = nullptr;
+  int4 *d_seg_prim = nullptr, *d_seg_fx = nullptr, *d_seg_fy = nullptr, *d_seg_cell = nullptr;
+  long long launches = 0;
+  // one captured time step per dt mode (0: CFL, 1: prescribed), replayed per step
+  cudaStream_t cap = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  long long graph_launches[2] = {0, 0};
+  bool use_graphs = true;
+  dis_adj* adj = nullptr;  // created by the first dis_adj_forward
+};
+
+// Error text for the thread's dis_last_error (returns code).
+int dis_internal_error(int code, const char* fmt, ...);
+// Allocate (if the caller bound none) and fill the workspace tables.
+int dis_internal_ensure_ws(dis_ctx* c);
+// Release the adjoint buffers of a context.
+void dis_internal_adj_free(dis_ctx* c);

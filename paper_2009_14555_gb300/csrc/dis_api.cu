@@ -23,7 +23,7 @@
 #include <vector>
 
 #include "../../include/dis.h"
-#include "fused32.cuh"
+#include "ctx.cuh"
 
 using namespace dis;
 
@@ -63,53 +63,6 @@ int dis_internal_error(int code, const char* fmt, ...) {
   return code;
 }
 
-struct dis_ctx {
-  int dim = 1, np = 0, y = -1, nf = 0;
-  dis_options opt{};
-  Phys phys{};
-  PhysF physf{};
-  bool fp32 = false;
-  bool have_mats = false, have_state = false;
-  std::vector<dis_patch> patches;
-  std::vector<PatchDev> pd;
-  long long T = 0, NFX = 0, NFY = 0, ncells = 0;
-  std::vector<int4> seg_prim, seg_fx, seg_fy, seg_cell;
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  // workspace
-  char* ws = nullptr;
-  size_t ws_bytes = 0;
-  bool ws_owned = false, ws_ready = false;
-  double* q[2] = {nullptr, nullptr};  // q^n, stage buffer
-  double* W = nullptr;
-  double* Fx = nullptr;
-  double* Fy = nullptr;
-  double* io = nullptr;
-  unsigned long long* rate = nullptr;
-  double* dtfix = nullptr;
-  double* dtlast = nullptr;
-  int* status = nullptr;
-  // FP32-bulk fused stage kernel: tile tables per tile shape, chosen shape
-  std::vector<int4> tiles[3];
-  int4* d_tiles[3] = {nullptr, nullptr, nullptr};
-  int variant = -1;
-  double tune_ms[3] = {0, 0, 0};
-  // FP32-bulk buffers: (phi1, rho E) float64 pairs and float32 planes
-  double* q64[2] = {nullptr, nullptr};
-  float* q32[2] = {nullptr, nullptr};
-  float* W32 = nullptr;
-  float* Fx32 = nullptr;
-  float* Fy32 = nullptr;
-  PatchDev* d_pd = nullptr;
-  int4 *d_seg_prim = nullptr, *d_seg_fx = nullptr, *d_seg_fy = nullptr, *d_seg_cell = nullptr;
-  long long launches = 0;
-  // one captured time step per dt mode (0: CFL, 1: prescribed), replayed per step
-  cudaStream_t cap = nullptr;
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  long long graph_launches[2] = {0, 0};
-  bool use_graphs = true;
-};
 
 namespace {
 
@@ -657,6 +610,8 @@ MatDev to_dev(const dis_material& m) {
 
 }  // namespace
 
+int dis_internal_ensure_ws(dis_ctx* c) { return ensure_ws(c); }
+
 extern "C" {
 
 const char* dis_last_error(void) { return g_err.c_str(); }
@@ -718,6 +673,13 @@ int dis_set_materials(dis_ctx* c, const dis_material* m, int n) {
   }
   c->physf = to_float(c->phys);
   c->have_mats = true;
+  // captured steps hold the closure parameters by value: capture again
+  if (c->cap && (c->graph[0] || c->graph[1])) cudaStreamSynchronize(c->cap);
+  for (int g = 0; g < 2; ++g)
+    if (c->graph[g]) {
+      cudaGraphExecDestroy(c->graph[g]);
+      c->graph[g] = nullptr;
+    }
   return DIS_OK;
 }
 
@@ -860,6 +822,7 @@ void dis_destroy(dis_ctx* c) {
   if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->ws_owned && c->ws) cudaFree(c->ws);
+  dis_internal_adj_free(c);
   delete c;
 }
 

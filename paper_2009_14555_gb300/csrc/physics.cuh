@@ -99,15 +99,16 @@ struct StrainT {
 };
 using Strain = StrainT<double>;
 
-__device__ __forceinline__ Strain strain_of(double a, double b, double c, double d, double e) {
-  const double B11 = a * a + b * b, B12 = a * c + b * d, B22 = c * c + d * d, B33 = e * e;
-  const double idet = 1.0 / (B11 * B22 - B12 * B12);
-  const double M11 = 0.25 * (B11 - B22 * idet);
-  const double M22 = 0.25 * (B22 - B11 * idet);
-  const double M12 = 0.25 * (B12 + B12 * idet);
-  const double M33 = 0.25 * (B33 - 1.0 / B33);
-  const double t3 = (M11 + M22 + M33) * (1.0 / 3.0);
-  Strain s;
+template <class T>
+__device__ __forceinline__ StrainT<T> strain_of(T a, T b, T c, T d, T e) {
+  const T B11 = a * a + b * b, B12 = a * c + b * d, B22 = c * c + d * d, B33 = e * e;
+  const T idet = 1.0 / (B11 * B22 - B12 * B12);
+  const T M11 = 0.25 * (B11 - B22 * idet);
+  const T M22 = 0.25 * (B22 - B11 * idet);
+  const T M12 = 0.25 * (B12 + B12 * idet);
+  const T M33 = 0.25 * (B33 - 1.0 / B33);
+  const T t3 = (M11 + M22 + M33) * (1.0 / 3.0);
+  StrainT<T> s;
   s.H11 = M11 - t3;
   s.H22 = M22 - t3;
   s.H33 = M33 - t3;
@@ -117,61 +118,68 @@ __device__ __forceinline__ Strain strain_of(double a, double b, double c, double
 }
 
 // The pieces of the pressure function that do not depend on the internal energy.
-__device__ __forceinline__ double ref_energy(const Phys& P, double phi1, double ar1, double ar2,
-                                             double arl, double J2) {
-  const double phi2 = 1.0 - phi1;
-  double s = phi1 * (P.m[0].kap + P.m[0].gG * J2) + phi2 * (P.m[1].kap + P.m[1].gG * J2) +
+template <class T>
+__device__ __forceinline__ T ref_energy(const PhysT<T>& P, T phi1, T ar1, T ar2, T arl, T J2) {
+  const T phi2 = 1.0 - phi1;
+  T s = phi1 * (P.m[0].kap + P.m[0].gG * J2) + phi2 * (P.m[1].kap + P.m[1].gG * J2) +
              ar1 * P.m[0].einf + ar2 * P.m[1].einf;
   if (P.y >= 0) {
-    const double ary = P.y == 0 ? ar1 : ar2;
+    const T ary = P.y == 0 ? ar1 : ar2;
     s -= P.m[P.y].Q * (ary - arl);
   }
   return s;
 }
 
-__device__ __forceinline__ double xi_of(const Phys& P, double phi1) {
+template <class T>
+__device__ __forceinline__ T xi_of(const PhysT<T>& P, T phi1) {
   return phi1 * P.m[0].iGm1 + (1.0 - phi1) * P.m[1].iGm1;
 }
 
 // rho c_L^2 for a state (frozen mixture sound speed plus 4/3 G_mix).
-__device__ __forceinline__ double cL2_of(const Phys& P, double phi1, double rho, double p, double J2) {
-  const double phi2 = 1.0 - phi1;
-  const double xi = xi_of(P, phi1);
-  const double a = phi1 * (P.m[0].gi * p + P.m[0].kap + P.m[0].gG * J2) +
+template <class T>
+__device__ __forceinline__ T cL2_of(const PhysT<T>& P, T phi1, T rho, T p, T J2) {
+  const T phi2 = 1.0 - phi1;
+  const T xi = xi_of(P, phi1);
+  const T a = phi1 * (P.m[0].gi * p + P.m[0].kap + P.m[0].gG * J2) +
                    phi2 * (P.m[1].gi * p + P.m[1].kap + P.m[1].gG * J2);
-  const double Gm = (phi1 * P.m[0].GoG + phi2 * P.m[1].GoG) / xi;
+  const T Gm = (phi1 * P.m[0].GoG + phi2 * P.m[1].GoG) / xi;
   return (a / xi + (4.0 / 3.0) * Gm) / rho;
 }
 
-__device__ __forceinline__ double Gmix_of(const Phys& P, double phi1) {
+template <class T>
+__device__ __forceinline__ T Gmix_of(const PhysT<T>& P, T phi1) {
   return (phi1 * P.m[0].GoG + (1.0 - phi1) * P.m[1].GoG) / xi_of(P, phi1);
 }
 
-__device__ __forceinline__ double minmod(double a, double b) {
-  return (a * b > 0.0) ? copysign(fmin(fabs(a), fabs(b)), a) : 0.0;
+template <class T>
+__device__ __forceinline__ T minmod(T a, T b) {
+  return (a * b > 0.0) ? copysign(fmin(fabs(a), fabs(b)), a) : T(0.0);
 }
 
 // MUSCL and THINC edge candidates of phi in one cell (Appendix A).
-struct Cand {
-  double mL, mR, tL, tR;
+template <class T>
+struct CandT {
+  T mL, mR, tL, tR;
 };
+using Cand = CandT<double>;
 
-__device__ __forceinline__ Cand phi_cand(double qm, double qc, double qp, double beta, bool thinc) {
-  Cand c;
-  const double s = minmod(qc - qm, qp - qc);
+template <class T>
+__device__ __forceinline__ CandT<T> phi_cand(T qm, T qc, T qp, T beta, bool thinc) {
+  CandT<T> c;
+  const T s = minmod(qc - qm, qp - qc);
   c.mL = qc - 0.5 * s;
   c.mR = qc + 0.5 * s;
   c.tL = c.mL;
   c.tR = c.mR;
   if (thinc) {
-    const double qmin = fmin(qm, qp);
-    const double jump = fmax(qm, qp) - qmin;
-    const double C = (qc - qmin + 1e-20) / (jump + 1e-20);
+    const T qmin = fmin(qm, qp);
+    const T jump = fmax(qm, qp) - qmin;
+    const T C = (qc - qmin + 1e-20) / (jump + 1e-20);
     if (C > 1e-5 && C < 1.0 - 1e-5 && (qp - qc) * (qc - qm) > 0.0) {
-      const double th = (qp - qm) > 0.0 ? 1.0 : -1.0;
-      const double B = exp(th * beta * (2.0 * C - 1.0));
-      const double tb = tanh(beta);
-      const double A = (B / cosh(beta) - 1.0) / tb;
+      const T th = (qp - qm) > 0.0 ? T(1.0) : T(-1.0);
+      const T B = exp(th * beta * (2.0 * C - 1.0));
+      const T tb = tanh(beta);
+      const T A = (B / cosh(beta) - 1.0) / tb;
       c.tL = qmin + 0.5 * jump * (1.0 + th * A);
       c.tR = qmin + 0.5 * jump * (1.0 + th * (tb + A) / (1.0 + A * tb));
     }
@@ -181,11 +189,11 @@ __device__ __forceinline__ Cand phi_cand(double qm, double qc, double qp, double
 
 // BVD choice for the middle cell: THINC only if its total boundary variation
 // is strictly smaller (ties keep MUSCL).
-__device__ __forceinline__ void bvd(const Cand& km, const Cand& k, const Cand& kp, double& L,
-                                    double& R) {
-  const double tT = fmin(fabs(km.mR - k.tL), fabs(km.tR - k.tL)) +
+template <class T>
+__device__ __forceinline__ void bvd(const CandT<T>& km, const CandT<T>& k, const CandT<T>& kp, T& L, T& R) {
+  const T tT = fmin(fabs(km.mR - k.tL), fabs(km.tR - k.tL)) +
                     fmin(fabs(k.tR - kp.mL), fabs(k.tR - kp.tL));
-  const double tM = fmin(fabs(km.mR - k.mL), fabs(km.tR - k.mL)) +
+  const T tM = fmin(fabs(km.mR - k.mL), fabs(km.tR - k.mL)) +
                     fmin(fabs(k.mR - kp.mL), fabs(k.mR - kp.tL));
   const bool useT = tT < tM;
   L = useT ? k.tL : k.mL;
@@ -194,25 +202,27 @@ __device__ __forceinline__ void bvd(const Cand& km, const Cand& k, const Cand& k
 
 // Thermodynamic face state for the Riemann solver.  Direction: n = normal
 // velocity component, t = tangential; Vn* = row of V along the normal.
-struct FState {
-  double phi, ar1, ar2, arl, rho, un, ut, rhoE, snn, snt, cL, Gm;
-  double V11, V12, V21, V22, V33;
+template <class T>
+struct FStateT {
+  T phi, ar1, ar2, arl, rho, un, ut, rhoE, snn, snt, cL, Gm;
+  T V11, V12, V21, V22, V33;
 };
+using FState = FStateT<double>;
 
-template <int DIR>
-__device__ __forceinline__ FState face_state(const Phys& P, const Prim& w) {
-  FState s;
-  const Strain st = strain_of(w.V11, w.V12, w.V21, w.V22, w.V33);
+template <int DIR, class T>
+__device__ __forceinline__ FStateT<T> face_state(const PhysT<T>& P, const PrimT<T>& w) {
+  FStateT<T> s;
+  const StrainT<T> st = strain_of(w.V11, w.V12, w.V21, w.V22, w.V33);
   s.phi = w.phi;
   s.ar1 = w.phi * w.r1;
   s.ar2 = (1.0 - w.phi) * w.r2;
   s.rho = s.ar1 + s.ar2;
   s.arl = 0.0;
   if (P.y >= 0) s.arl = (P.y == 0 ? s.ar1 : s.ar2) * w.lam;
-  const double xi = xi_of(P, w.phi);
+  const T xi = xi_of(P, w.phi);
   s.rhoE = xi * w.p + ref_energy(P, w.phi, s.ar1, s.ar2, s.arl, st.J2) +
            0.5 * s.rho * (w.u * w.u + w.v * w.v);
-  const double Gm = Gmix_of(P, w.phi);
+  const T Gm = Gmix_of(P, w.phi);
   s.Gm = Gm;
   if (DIR == 0) {
     s.un = w.u;
@@ -234,27 +244,30 @@ __device__ __forceinline__ FState face_state(const Phys& P, const Prim& w) {
 }
 
 // Output of one face: conservative fluxes plus the face state at x/t = 0.
-struct FaceOut {
-  double Far1, Far2, Farl, Fmn, Fmt, FE;
-  double phi, un, ut, V11, V12, V21, V22, V33;
+template <class T>
+struct FaceOutT {
+  T Far1, Far2, Farl, Fmn, Fmt, FE;
+  T phi, un, ut, V11, V12, V21, V22, V33;
 };
+using FaceOut = FaceOutT<double>;
 
 // Star (longitudinal-wave) state of one side.
-struct Star {
-  double r, snn, E, V11, V12, V21, V22, V33;
+template <class T>
+struct StarT {
+  T r, snn, E, V11, V12, V21, V22, V33;
 };
 
-template <int DIR>
-__device__ __forceinline__ Star star_of(const FState& K, double S, double Ss) {
-  Star t;
-  const double inv = 1.0 / (S - Ss);
+template <int DIR, class T>
+__device__ __forceinline__ StarT<T> star_of(const FStateT<T>& K, T S, T Ss) {
+  StarT<T> t;
+  const T inv = 1.0 / (S - Ss);
   t.r = (S - K.un) * inv;
-  const double m = K.rho * (S - K.un);
+  const T m = K.rho * (S - K.un);
   t.snn = K.snn - m * (Ss - K.un);
   // energy jump: E*(S - S*) = E (S - u_n) + u.sigma_n - u*.sigma*_n (tangential work cancels)
   t.E = (K.rhoE * (S - K.un) + K.un * K.snn - Ss * t.snn) * inv;
-  const double c1 = cbrt(t.r);        // r^(1/3): rows off the normal
-  const double cn = 1.0 / (c1 * c1);  // r^(-2/3): row along the normal
+  const T c1 = cbrt(t.r);        // r^(1/3): rows off the normal
+  const T cn = 1.0 / (c1 * c1);  // r^(-2/3): row along the normal
   if (DIR == 0) {
     t.V11 = cn * K.V11; t.V12 = cn * K.V12;
     t.V21 = c1 * K.V21; t.V22 = c1 * K.V22;
@@ -266,24 +279,24 @@ __device__ __forceinline__ Star star_of(const FState& K, double S, double Ss) {
   return t;
 }
 
-template <int DIR>
-__device__ __forceinline__ FaceOut hllc(const FState& L, const FState& R) {
-  const double SL = fmin(L.un - L.cL, R.un - R.cL);
-  const double SR = fmax(L.un + L.cL, R.un + R.cL);
-  const double mL = L.rho * (SL - L.un);
-  const double mR = R.rho * (SR - R.un);
-  const double Ss = (L.snn - R.snn + mL * L.un - mR * R.un) / (mL - mR);
-  const Star sL = star_of<DIR>(L, SL, Ss);
-  const Star sR = star_of<DIR>(R, SR, Ss);
+template <int DIR, class T>
+__device__ __forceinline__ FaceOutT<T> hllc(const FStateT<T>& L, const FStateT<T>& R) {
+  const T SL = fmin(L.un - L.cL, R.un - R.cL);
+  const T SR = fmax(L.un + L.cL, R.un + R.cL);
+  const T mL = L.rho * (SL - L.un);
+  const T mR = R.rho * (SR - R.un);
+  const T Ss = (L.snn - R.snn + mL * L.un - mR * R.un) / (mL - mR);
+  const StarT<T> sL = star_of<DIR>(L, SL, Ss);
+  const StarT<T> sR = star_of<DIR>(R, SR, Ss);
   // shear waves of the star regions and the common tangential state
-  const double rsL = sL.r * L.rho, rsR = sR.r * R.rho;
-  const double csL = sqrt(L.Gm / rsL), csR = sqrt(R.Gm / rsR);
-  const double ZL = rsL * csL, ZR = rsR * csR;
-  const double SsL = Ss - csL, SsR = Ss + csR;
-  double ut2L = L.ut, ut2R = R.ut, st2L = L.snt, st2R = R.snt;
+  const T rsL = sL.r * L.rho, rsR = sR.r * R.rho;
+  const T csL = sqrt(L.Gm / rsL), csR = sqrt(R.Gm / rsR);
+  const T ZL = rsL * csL, ZR = rsR * csR;
+  const T SsL = Ss - csL, SsR = Ss + csR;
+  T ut2L = L.ut, ut2R = R.ut, st2L = L.snt, st2R = R.snt;
   if (ZL + ZR > 0.0) {
-    const double ut2 = (ZL * L.ut + ZR * R.ut + R.snt - L.snt) / (ZL + ZR);
-    const double st2 = L.snt + ZL * (ut2 - L.ut);
+    const T ut2 = (ZL * L.ut + ZR * R.ut + R.snt - L.snt) / (ZL + ZR);
+    const T st2 = L.snt + ZL * (ut2 - L.ut);
     ut2L = ut2R = ut2;
     st2L = st2R = st2;
   }
@@ -296,25 +309,25 @@ __device__ __forceinline__ FaceOut hllc(const FState& L, const FState& R) {
   else if (SsR >= 0.0) { left = false; level = 2; }
   else if (SR >= 0.0) { left = false; level = 1; }
   else { left = false; level = 0; }
-  const FState& K = left ? L : R;
-  const Star& sK = left ? sL : sR;
-  const double S = left ? SL : SR;
-  const double Sh = left ? SsL : SsR;
-  const double ut2 = left ? ut2L : ut2R;
-  const double st2 = left ? st2L : st2R;
-  const double un = K.un, ut = K.ut;
-  FaceOut o;
-  double Far1 = K.ar1 * un, Far2 = K.ar2 * un, Farl = K.arl * un;
-  double Fmn = K.rho * un * un - K.snn;
-  double Fmt = K.rho * ut * un - K.snt;
-  double FE = K.rhoE * un - (un * K.snn + ut * K.snt);
+  const FStateT<T>& K = left ? L : R;
+  const StarT<T>& sK = left ? sL : sR;
+  const T S = left ? SL : SR;
+  const T Sh = left ? SsL : SsR;
+  const T ut2 = left ? ut2L : ut2R;
+  const T st2 = left ? st2L : st2R;
+  const T un = K.un, ut = K.ut;
+  FaceOutT<T> o;
+  T Far1 = K.ar1 * un, Far2 = K.ar2 * un, Farl = K.arl * un;
+  T Fmn = K.rho * un * un - K.snn;
+  T Fmt = K.rho * ut * un - K.snt;
+  T FE = K.rhoE * un - (un * K.snn + ut * K.snt);
   o.phi = K.phi;
   if (level == 0) {
     o.un = un;
     o.ut = ut;
     o.V11 = K.V11; o.V12 = K.V12; o.V21 = K.V21; o.V22 = K.V22; o.V33 = K.V33;
   } else {
-    const double r1 = sK.r - 1.0;
+    const T r1 = sK.r - 1.0;
     Far1 += S * r1 * K.ar1;
     Far2 += S * r1 * K.ar2;
     Farl += S * r1 * K.arl;
@@ -325,13 +338,13 @@ __device__ __forceinline__ FaceOut hllc(const FState& L, const FState& R) {
     o.ut = ut;
     o.V11 = sK.V11; o.V12 = sK.V12; o.V21 = sK.V21; o.V22 = sK.V22; o.V33 = sK.V33;
     if (level == 2) {
-      const double dS = Sh - Ss;
-      const double rs = sK.r * K.rho;
+      const T dS = Sh - Ss;
+      const T rs = sK.r * K.rho;
       if (dS != 0.0) {
-        const double idS = 1.0 / dS;
+        const T idS = 1.0 / dS;
         Fmt += Sh * rs * (ut2 - ut);
         FE -= Sh * (ut2 * st2 - ut * K.snt) * idS;
-        const double w = (ut - ut2) * idS;
+        const T w = (ut - ut2) * idS;
         if (DIR == 0) {
           o.V21 = sK.V21 + w * sK.V11;
           o.V22 = sK.V22 + w * sK.V12;
@@ -348,18 +361,19 @@ __device__ __forceinline__ FaceOut hllc(const FState& L, const FState& R) {
 }
 
 // Plastic update of Section 3.2 on one cell's stretch tensor (in place).
-__device__ __forceinline__ void plastic(const Phys& P, double phi1, double dt, double& V11,
-                                        double& V12, double& V21, double& V22, double& V33) {
-  const Strain s = strain_of(V11, V12, V21, V22, V33);
-  const double Js = sqrt(s.J2);
-  double num = 0.0, den = 0.0;
+template <class T>
+__device__ __forceinline__ void plastic(const PhysT<T>& P, T phi1, T dt, T& V11,
+                                        T& V12, T& V21, T& V22, T& V33) {
+  const StrainT<T> s = strain_of(V11, V12, V21, V22, V33);
+  const T Js = sqrt(s.J2);
+  T num = 0.0, den = 0.0;
 #pragma unroll
   for (int l = 0; l < 2; ++l) {
-    const MatDev& m = P.m[l];
-    const double ph = l == 0 ? phi1 : 1.0 - phi1;
-    double Jl;
+    const MatT<T>& m = P.m[l];
+    const T ph = l == 0 ? phi1 : 1.0 - phi1;
+    T Jl;
     if (m.G == 0.0) {
-      Jl = 0.0;  // a fluid keeps no shear strain
+      Jl = T(0.0);  // a fluid keeps no shear strain
     } else if (m.plastic == 1) {
       Jl = fmin(Js, m.JY);
     } else if (m.plastic == 2) {
@@ -370,14 +384,14 @@ __device__ __forceinline__ void plastic(const Phys& P, double phi1, double dt, d
     num += ph * m.iGm1 * Jl;
     den += ph * m.iGm1;
   }
-  const double Jn = num / den;
-  const double sc = Js > 0.0 ? Jn / Js : 0.0;
-  const double h11 = sc * s.H11, h12 = sc * s.H12, h22 = sc * s.H22, h33 = sc * s.H33;
+  const T Jn = num / den;
+  const T sc = Js > 0.0 ? Jn / Js : T(0.0);
+  const T h11 = sc * s.H11, h12 = sc * s.H12, h22 = sc * s.H22, h33 = sc * s.H33;
   // V = (I - H/2)^-1 (I + H/2) on the in-plane block and the zz entry
-  const double x11 = 1.0 - 0.5 * h11, x12 = -0.5 * h12, x22 = 1.0 - 0.5 * h22;
-  const double y11 = 1.0 + 0.5 * h11, y12 = 0.5 * h12, y22 = 1.0 + 0.5 * h22;
-  const double id = 1.0 / (x11 * x22 - x12 * x12);
-  const double i11 = x22 * id, i12 = -x12 * id, i22 = x11 * id;
+  const T x11 = 1.0 - 0.5 * h11, x12 = -0.5 * h12, x22 = 1.0 - 0.5 * h22;
+  const T y11 = 1.0 + 0.5 * h11, y12 = 0.5 * h12, y22 = 1.0 + 0.5 * h22;
+  const T id = 1.0 / (x11 * x22 - x12 * x12);
+  const T i11 = x22 * id, i12 = -x12 * id, i22 = x11 * id;
   V11 = i11 * y11 + i12 * y12;
   V12 = i11 * y12 + i12 * y22;
   V21 = i12 * y11 + i22 * y12;

@@ -10,7 +10,7 @@
 // segment = (patch, row, first index, count), so every launch covers any
 // batch of uneven patches and accesses are unit-stride along x.
 #pragma once
-#include "physics.cuh"
+#include "face.cuh"
 
 namespace dis {
 
@@ -65,38 +65,11 @@ __device__ __forceinline__ int ghost_map(int i, int n, int bclo, int bchi, bool&
 
 template <int DIM, bool RX>
 __device__ __forceinline__ Prim cons_to_prim(const Phys& P, const double* q, long long T, long long k) {
-  using L = Lay<DIM, RX>;
-  Prim w;
-  const double phi = q[L::PHI * T + k], a1 = q[L::A1 * T + k], a2 = q[L::A2 * T + k];
-  const double rho = a1 + a2;
-  const double mx = q[L::MX * T + k];
-  double my = 0.0;
-  if constexpr (DIM == 2) my = q[L::MY * T + k];
-  const double E = q[L::E * T + k];
-  w.phi = phi;
-  w.r1 = a1 / phi;
-  w.r2 = a2 / (1.0 - phi);
-  w.u = mx / rho;
-  w.v = my / rho;
-  w.V11 = q[L::V11 * T + k];
-  w.V12 = 0.0;
-  w.V21 = 0.0;
-  if constexpr (DIM == 2) {
-    w.V12 = q[L::V12 * T + k];
-    w.V21 = q[L::V21 * T + k];
-  }
-  w.V22 = q[L::V22 * T + k];
-  w.V33 = q[L::V33 * T + k];
-  double arl = 0.0;
-  w.lam = 0.0;
-  if constexpr (RX) {
-    arl = q[L::AL * T + k];
-    w.lam = arl / (P.y == 0 ? a1 : a2);
-  }
-  const Strain s = strain_of(w.V11, w.V12, w.V21, w.V22, w.V33);
-  const double KE = 0.5 * (mx * w.u + my * w.v);
-  w.p = (E - KE - ref_energy(P, phi, a1, a2, arl, s.J2)) / xi_of(P, phi);
-  return w;
+  constexpr int NF = Lay<DIM, RX>::NF;
+  double v[NF];
+#pragma unroll
+  for (int c = 0; c < NF; ++c) v[c] = q[c * T + k];
+  return prim_of<DIM, RX, double>(P, v);
 }
 
 template <int DIM, bool RX>
@@ -210,42 +183,24 @@ __global__ void __launch_bounds__(SEG) k_flux(Phys P, StepArgs A, const int4* __
   };
   const long long stride_t = DIR == 0 ? (long long)pd.pitch : 1;  // transverse neighbour step
 
-  // volume fraction on the line, cells a-2 .. a+3
-  double ph[6];
+  // volume fraction on the line (cells a-2 .. a+3) and, for the 2D Youngs
+  // normal, on the two neighbouring lines
+  double B[3][6];
 #pragma unroll
-  for (int s = 0; s < 6; ++s) ph[s] = W[L::PHI * T + at(a - 2 + s)];
-
-  // phi edge values of cells a (right edge) and a+1 (left edge)
-  double phiL, phiR;
-  {
-    Cand c[4];
+  for (int c = 0; c < 6; ++c) B[1][c] = W[L::PHI * T + at(a - 2 + c)];
+  const bool normals = DIM == 2 && P.thinc;
+  if (normals) {
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      double beta = 2.51;  // beta0 |n_d| + 0.01 with |n_d| = 1 in 1D
-      if (DIM == 2 && P.thinc) {
-        // Youngs normal from the (1,2,1)-weighted central differences of phi
-        const long long k = at(a - 1 + s);
-        const double* Ph = W + L::PHI * T;
-        const long long sx = DIR == 0 ? 1 : (long long)pd.pitch;  // along the sweep
-        const long long sy = DIR == 0 ? (long long)pd.pitch : 1;  // across it
-        const double dn = (Ph[k + sx + sy] + 2.0 * Ph[k + sx] + Ph[k + sx - sy]) -
-                          (Ph[k - sx + sy] + 2.0 * Ph[k - sx] + Ph[k - sx - sy]);
-        const double dt_ = (Ph[k + sy + sx] + 2.0 * Ph[k + sy] + Ph[k + sy - sx]) -
-                           (Ph[k - sy + sx] + 2.0 * Ph[k - sy] + Ph[k - sy - sx]);
-        const double hn = DIR == 0 ? pd.dx : pd.dy, ht = DIR == 0 ? pd.dy : pd.dx;
-        const double gn = dn / hn, gt = dt_ / ht;
-        const double nrm = sqrt(gn * gn + gt * gt);
-        beta = 2.5 * (nrm == 0.0 ? 1.0 : fabs(gn) / nrm) + 0.01;
-      }
-      c[s] = phi_cand(ph[s], ph[s + 1], ph[s + 2], beta, P.thinc != 0);
+    for (int c = 0; c < 6; ++c) {
+      B[0][c] = W[L::PHI * T + at(a - 2 + c) - stride_t];
+      B[2][c] = W[L::PHI * T + at(a - 2 + c) + stride_t];
     }
-    double Lt, Rt;
-    bvd(c[0], c[1], c[2], Lt, Rt);
-    phiL = Rt;  // right edge of cell a
-    bvd(c[1], c[2], c[3], Lt, Rt);
-    phiR = Lt;  // left edge of cell a+1
+  } else {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) B[0][c] = B[2][c] = 0.0;
   }
-  (void)stride_t;
+  double phiL, phiR;
+  face_phi<DIM, double>(B, P.thinc != 0, DIR == 0 ? pd.dx : pd.dy, DIR == 0 ? pd.dy : pd.dx, phiL, phiR);
 
   // MUSCL on the other primitives: cells a-1, a, a+1, a+2
   const Prim w0 = load_prim<DIM, RX>(W, T, at(a - 1));
@@ -253,18 +208,23 @@ __global__ void __launch_bounds__(SEG) k_flux(Phys P, StepArgs A, const int4* __
   const Prim w2 = load_prim<DIM, RX>(W, T, at(a + 1));
   const Prim w3 = load_prim<DIM, RX>(W, T, at(a + 2));
   Prim wl, wr;
-#define DIS_REC(fld)                                            \
-  {                                                             \
-    const double s1 = minmod(w1.fld - w0.fld, w2.fld - w1.fld); \
-    const double s2 = minmod(w2.fld - w1.fld, w3.fld - w2.fld); \
-    wl.fld = w1.fld + 0.5 * s1;                                 \
-    wr.fld = w2.fld - 0.5 * s2;                                 \
+  muscl_pair(w0.r1, w1.r1, w2.r1, w3.r1, wl.r1, wr.r1);
+  muscl_pair(w0.r2, w1.r2, w2.r2, w3.r2, wl.r2, wr.r2);
+  muscl_pair(w0.u, w1.u, w2.u, w3.u, wl.u, wr.u);
+  muscl_pair(w0.p, w1.p, w2.p, w3.p, wl.p, wr.p);
+  muscl_pair(w0.V11, w1.V11, w2.V11, w3.V11, wl.V11, wr.V11);
+  muscl_pair(w0.V22, w1.V22, w2.V22, w3.V22, wl.V22, wr.V22);
+  muscl_pair(w0.V33, w1.V33, w2.V33, w3.V33, wl.V33, wr.V33);
+  if constexpr (DIM == 2) {
+    muscl_pair(w0.v, w1.v, w2.v, w3.v, wl.v, wr.v);
+    muscl_pair(w0.V12, w1.V12, w2.V12, w3.V12, wl.V12, wr.V12);
+    muscl_pair(w0.V21, w1.V21, w2.V21, w3.V21, wl.V21, wr.V21);
+  } else {
+    wl.v = wr.v = 0.0;
+    wl.V12 = wr.V12 = wl.V21 = wr.V21 = 0.0;
   }
-  DIS_REC(r1) DIS_REC(r2) DIS_REC(u) DIS_REC(p) DIS_REC(V11) DIS_REC(V22) DIS_REC(V33)
-  if constexpr (DIM == 2) { DIS_REC(v) DIS_REC(V12) DIS_REC(V21) }
-  else { wl.v = wr.v = 0.0; wl.V12 = wr.V12 = wl.V21 = wr.V21 = 0.0; }
-  if constexpr (RX) { DIS_REC(lam) } else { wl.lam = wr.lam = 0.0; }
-#undef DIS_REC
+  if constexpr (RX) muscl_pair(w0.lam, w1.lam, w2.lam, w3.lam, wl.lam, wr.lam);
+  else wl.lam = wr.lam = 0.0;
   wl.phi = phiL;
   wr.phi = phiR;
 
@@ -274,48 +234,16 @@ __global__ void __launch_bounds__(SEG) k_flux(Phys P, StepArgs A, const int4* __
   if (!(sl.cL > 0.0)) sl = face_state<DIR>(P, w1);
   FState sr = face_state<DIR>(P, wr);
   if (!(sr.cL > 0.0)) sr = face_state<DIR>(P, w2);
-  sl.cL = sqrt(sl.cL);
-  sr.cL = sqrt(sr.cL);
-  const FaceOut o = hllc<DIR>(sl, sr);
+  constexpr int NO = n_face_out<DIM, RX>();
+  double out[NO];
+  riemann_outputs<DIM, RX, DIR>(sl, sr, out);
 
-  // velocity of the face state in x/y components
-  const double fu = DIR == 0 ? o.un : o.ut;
-  const double fv = DIR == 0 ? o.ut : o.un;
   double* F = DIR == 0 ? A.Fx : A.Fy;
   const long long NFc = DIR == 0 ? A.NFX : A.NFY;
   const long long fi = DIR == 0 ? pd.fxoff + (long long)col * (pd.nx + 1) + f
                                 : pd.fyoff + (long long)g.y * pd.nx + col;
-  F[L::PHI * NFc + fi] = o.phi * o.un;
-  F[L::A1 * NFc + fi] = o.Far1;
-  F[L::A2 * NFc + fi] = o.Far2;
-  F[L::MX * NFc + fi] = DIR == 0 ? o.Fmn : o.Fmt;
-  if constexpr (DIM == 2) F[L::MY * NFc + fi] = DIR == 0 ? o.Fmt : o.Fmn;
-  F[L::E * NFc + fi] = o.FE;
-  if constexpr (RX) F[L::AL * NFc + fi] = o.Farl;
-  // stretch fluxes V_ij u_d - V_dj u_i at the face state
-  if constexpr (DIR == 0) {
-    F[L::V11 * NFc + fi] = 0.0;
-    if constexpr (DIM == 2) {
-      F[L::V12 * NFc + fi] = 0.0;
-      F[L::V21 * NFc + fi] = o.V21 * fu - o.V11 * fv;
-      F[L::V22 * NFc + fi] = o.V22 * fu - o.V12 * fv;
-    } else {
-      F[L::V22 * NFc + fi] = o.V22 * fu;
-    }
-    F[L::V33 * NFc + fi] = o.V33 * fu;
-    F[(L::NF + 0) * NFc + fi] = o.un;
-    F[(L::NF + 1) * NFc + fi] = o.V11;
-    if constexpr (DIM == 2) F[(L::NF + 2) * NFc + fi] = o.V12;
-  } else if constexpr (DIM == 2) {
-    F[L::V11 * NFc + fi] = o.V11 * fv - o.V21 * fu;
-    F[L::V12 * NFc + fi] = o.V12 * fv - o.V22 * fu;
-    F[L::V21 * NFc + fi] = 0.0;
-    F[L::V22 * NFc + fi] = 0.0;
-    F[L::V33 * NFc + fi] = o.V33 * fv;
-    F[(L::NF + 0) * NFc + fi] = o.un;
-    F[(L::NF + 1) * NFc + fi] = o.V21;
-    F[(L::NF + 2) * NFc + fi] = o.V22;
-  }
+#pragma unroll
+  for (int c = 0; c < NO; ++c) F[c * NFc + fi] = out[c];
 }
 
 // ---------------------------------------------------------------------------
@@ -378,37 +306,7 @@ __global__ void __launch_bounds__(SEG) k_update(Phys P, StepArgs A, const int4* 
     for (int c = 0; c < NF; ++c) o[c] = A.a * A.qn[c * T + k] + A.b * (q[c] - dt * D[c]);
   }
   if (A.last) {
-    double v12 = 0.0, v21 = 0.0;
-    if constexpr (DIM == 2) { v12 = o[L::V12]; v21 = o[L::V21]; }
-    plastic(P, o[L::PHI], dt, o[L::V11], v12, v21, o[L::V22], o[L::V33]);
-    if constexpr (DIM == 2) { o[L::V12] = v12; o[L::V21] = v21; }
-    if constexpr (RX) {
-      const int y = P.y;
-      const MatDev& m = P.m[y];
-      const double phi1 = o[L::PHI];
-      const double ary = y == 0 ? o[L::A1] : o[L::A2];
-      const double phy = y == 0 ? phi1 : 1.0 - phi1;
-      const double rr = o[L::A1] + o[L::A2];
-      const double mx = o[L::MX];
-      double my = 0.0;
-      if constexpr (DIM == 2) my = o[L::MY];
-      const double KE = 0.5 * (mx * mx + my * my) / rr;
-      const Strain s = strain_of(o[L::V11], v12, v21, o[L::V22], o[L::V33]);
-      const double xi = xi_of(P, phi1);
-      const double p0 = (o[L::E] - KE - ref_energy(P, phi1, o[L::A1], o[L::A2], 0.0, s.J2)) / xi;
-      const double Tfac = m.iGm1 / ((ary / phy) * m.cv);  // T = p / (rho_y Gamma c_V)
-      const double Qx = m.Q / xi;
-      auto f = [&](double Lm) {
-        const double Tk = (p0 - Qx * Lm) * Tfac;
-        return Tk > 0.0 ? -m.A * Lm * exp(-m.Tact / Tk) : 0.0;
-      };
-      const double L0 = o[L::AL];
-      const double k1 = f(L0);
-      const double k2 = f(L0 + 0.5 * dt * k1);
-      const double k3 = f(L0 + 0.5 * dt * k2);
-      const double k4 = f(L0 + dt * k3);
-      o[L::AL] = L0 + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
-    }
+    sources<DIM, RX, double>(P, dt, o);
     bool bad = !(o[L::PHI] >= -1e-6 && o[L::PHI] <= 1.0 + 1e-6);
 #pragma unroll
     for (int c = 0; c < NF; ++c) bad |= !isfinite(o[c]);
@@ -439,21 +337,7 @@ __global__ void __launch_bounds__(SEG) k_unpack(Phys P, const PatchDev* __restri
   double v[NF];
 #pragma unroll
   for (int c = 0; c < NF; ++c) v[c] = src[s0 + c * ncell];
-  if (primitive) {
-    const double phi = v[L::PHI], r1 = v[L::A1], r2 = v[L::A2];
-    const double u = v[L::MX], p = v[L::E];
-    double vv = 0.0, v12 = 0.0, v21 = 0.0, arl = 0.0;
-    const double a1 = phi * r1, a2 = (1.0 - phi) * r2, rho = a1 + a2;
-    if constexpr (DIM == 2) { vv = v[L::MY]; v12 = v[L::V12]; v21 = v[L::V21]; }
-    if constexpr (RX) arl = (P.y == 0 ? a1 : a2) * v[L::AL];
-    const Strain s = strain_of(v[L::V11], v12, v21, v[L::V22], v[L::V33]);
-    v[L::A1] = a1;
-    v[L::A2] = a2;
-    v[L::MX] = rho * u;
-    if constexpr (DIM == 2) v[L::MY] = rho * vv;
-    v[L::E] = xi_of(P, phi) * p + ref_energy(P, phi, a1, a2, arl, s.J2) + 0.5 * rho * (u * u + vv * vv);
-    if constexpr (RX) v[L::AL] = arl;
-  }
+  if (primitive) cons_of<DIM, RX, double>(P, v);
 #pragma unroll
   for (int c = 0; c < NF; ++c) q[c * T + k] = v[c];
 }

@@ -58,7 +58,8 @@ class Solver:
         self.stream = torch.cuda.current_stream(self.device)
         self.ctx = L.dis_create(dim, [_patch(p, dim) for p in self.patches], reactive_material, opts,
                                 self.stream.cuda_stream)
-        L.dis_set_materials(self.ctx, [_material(m) for m in materials])
+        self.materials = [dict(m) for m in materials]
+        L.dis_set_materials(self.ctx, [_material(m) for m in self.materials])
         nbytes = L.dis_workspace_bytes(self.ctx)
         self._ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
         base = self._ws.data_ptr()
@@ -128,6 +129,57 @@ class Solver:
 
     def check(self):
         return L.dis_check(self.ctx)
+
+    # -- parameters and adjoint ---------------------------------------------------
+    PARAM_KEYS = ("G", "sigma_y", "Q")
+
+    def params(self) -> np.ndarray:
+        """Differentiable parameters [G_l, sigma_y_l, Q_l for l = 0, 1]."""
+        return np.array([m[k] for m in self.materials for k in self.PARAM_KEYS], np.float64)
+
+    def set_params(self, theta):
+        theta = np.asarray(theta, np.float64).reshape(L.DIS_NPARAM)
+        for l, m in enumerate(self.materials):
+            for k, key in enumerate(self.PARAM_KEYS):
+                m[key] = float(theta[3 * l + k])
+        L.dis_set_materials(self.ctx, [_material(m) for m in self.materials])
+
+    def adj_forward(self, n_steps, every=20, material=-1, dts=None):
+        """Recorded forward run for `adjoint` (include/dis.h: dis_adj_forward).
+        Returns (J, dts[n_steps, n_patches])."""
+        out = np.empty((n_steps, len(self.patches)), np.float64)
+        din = None
+        if dts is not None:
+            din = np.ascontiguousarray(np.broadcast_to(np.asarray(dts, np.float64).reshape(n_steps, -1),
+                                                       (n_steps, len(self.patches))))
+        J = L.dis_adj_forward(self.ctx, n_steps, every, material, din.ctypes.data if din is not None else None,
+                              out.ctypes.data)
+        return J, out
+
+    def adjoint(self, qbar=None, jbar=0.0, kind=L.DIS_CONSERVATIVE, param_mask=(1 << L.DIS_NPARAM) - 1,
+                out=None):
+        """Gradient of <qbar, q_final> + jbar J with respect to the initial state
+        (`kind` variables, packed) and the parameters.  qbar / out may be CUDA
+        tensors (device path) or host arrays."""
+        gp = np.zeros(L.DIS_NPARAM, np.float64)
+        keep = []
+        if qbar is None:
+            qp, qdev = None, False
+        elif isinstance(qbar, torch.Tensor) and qbar.is_cuda:
+            qbar = qbar.contiguous().to(torch.float64)
+            keep.append(qbar)
+            qp, qdev = qbar.data_ptr(), True
+        else:
+            qbar = np.ascontiguousarray(np.asarray(qbar, np.float64).reshape(-1))
+            keep.append(qbar)
+            qp, qdev = qbar.ctypes.data, False
+        if out is not None:
+            assert out.is_cuda and out.dtype == torch.float64 and out.numel() == self.state_numel
+            L.dis_adjoint(self.ctx, qp, qdev, jbar, kind, out.data_ptr(), True, gp.ctypes.data, param_mask)
+            return out, gp
+        g = np.empty(self.state_numel, np.float64)
+        L.dis_adjoint(self.ctx, qp, qdev, jbar, kind, g.ctypes.data, False, gp.ctypes.data, param_mask)
+        return g, gp
 
     @property
     def launches(self):

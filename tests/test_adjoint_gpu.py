@@ -1,0 +1,273 @@
+"""Adjoint of the float64 GPU step (dis_adj_forward / dis_adjoint) against
+the oracle's own reverse mode (PyTorch autograd through the float64 CPU
+oracle) and against central finite differences.
+
+Parity metric (per field f of the initial-state gradient):
+    err_f = max |g_gpu - g_oracle| / max(max |g_oracle|, floor)
+with the floor 1e-300 (fields whose oracle gradient is exactly zero must be
+zero on the GPU).  Both sides differentiate the same discrete step with the
+time steps frozen; each uses its own CFL time steps, which agree to
+round-off.  Bar: 1e-8 for state and parameter gradients (round-off of two
+float64 programs propagated through the reverse sweep; THINC next to the
+stiff solid amplifies it, as in the forward parity tests, so that case uses
+1e-6).  Finite differences: 1e-4 relative (central, relative step 1e-6,
+smooth inputs, time steps held at the recorded values).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2009_14555_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
+_record = {}
+
+
+def _save():
+    os.makedirs(OUT, exist_ok=True)
+    with open(os.path.join(OUT, "adjoint_err.json"), "w") as f:
+        json.dump(_record, f, indent=1)
+
+
+def gpu_grad(wl, steps, material, qbar=None, every=3, kind=1, dts=None):
+    """GPU J, gradient w.r.t. the initial state (primitive kind=1 or
+    conservative kind=0, per patch arrays), parameter gradients and dts."""
+    from paper_2009_14555_gb300.solver import Solver, pack, unpack
+    s = Solver.from_workload(wl)
+    s.set_prim([p.prim for p in wl.patches])
+    J, used = s.adj_forward(steps, every=every, material=material, dts=dts)
+    rc, bp, bc = s.check()
+    assert rc == 0, (bp, bc)
+    qN = s.get_arrays()
+    qb = None if qbar is None else pack(qbar)
+    if qb is not None:
+        J = J + float(sum((a * b).sum() for a, b in zip(qbar, qN)))
+    g, gp = s.adjoint(qb, 1.0 if material >= 0 else 0.0, kind=kind)
+    s.close()
+    return J, unpack(g, [p.prim.shape for p in wl.patches]), gp, used
+
+
+def oracle_grad(wl, steps, material, qbar=None, kind="prim"):
+    from oracle import adjoint as OA
+    from oracle import scheme as OS
+    from oracle.closures import prim_to_cons
+    p = wl.patches[0]
+    theta = torch.tensor([m[k] for m in wl.materials for k in OA.PARAM_KEYS], dtype=torch.float64,
+                         requires_grad=True)
+    if kind == "prim":
+        init = torch.tensor(p.prim, dtype=torch.float64, requires_grad=True)
+    else:
+        q0 = prim_to_cons(OS.prim_from_array(p.prim, wl.dim, wl.reactive), wl.materials)
+        init = OS.cons_to_array(q0, wl.dim, wl.reactive).detach().clone().requires_grad_(True)
+    J, _, dts = OA.rollout(init, kind, wl.dim, OA.with_params(wl.materials, theta), p,
+                           dict(cfl=wl.cfl, thinc=wl.thinc), steps, material,
+                           None if qbar is None else qbar[0])
+    J.backward()
+    return float(J), init.grad.numpy(), theta.grad.numpy(), dts
+
+
+def field_err(g, o):
+    g, o = np.asarray(g), np.asarray(o)
+    out = []
+    for f in range(o.shape[0]):
+        sc = max(np.abs(o[f]).max(), 1e-300)
+        out.append(float(np.abs(g[f] - o[f]).max() / sc))
+    return out
+
+
+def param_err(gp, op, mask):
+    return [float(abs(gp[k] - op[k]) / max(abs(op[k]), 1e-300)) for k in mask]
+
+
+def _case(name, wl, steps, material, qbar_seed=None, tol=1e-8, params=(0, 1), kind="prim"):
+    qbar = None
+    if qbar_seed is not None:
+        rng = np.random.default_rng(qbar_seed)
+        # adjoint weights scaled so every field contributes comparably
+        sc = np.abs(wl.patches[0].prim).reshape(wl.patches[0].prim.shape[0], -1).max(1)
+        qbar = [rng.standard_normal(p.prim.shape) / np.maximum(sc, 1.0)[:, None, None] * 1e-3
+                for p in wl.patches]
+    Jg, gg, gpg, gdt = gpu_grad(wl, steps, material, qbar, kind=1 if kind == "prim" else 0)
+    Jo, go, gpo, odt = oracle_grad(wl, steps, material, qbar, kind)
+    e = field_err(gg[0], go)
+    ep = param_err(gpg, gpo, params)
+    _record[name] = dict(J_gpu=Jg, J_oracle=Jo, field_err=e, param_err=ep,
+                         params_gpu=[float(gpg[k]) for k in params],
+                         params_oracle=[float(gpo[k]) for k in params],
+                         dt_rel=float(np.max(np.abs(np.asarray(gdt)[:, 0] - np.asarray(odt)) / np.asarray(odt))))
+    _save()
+    assert abs(Jg - Jo) <= 1e-10 * abs(Jo) + 1e-300, (Jg, Jo)
+    assert max(e) <= tol, e
+    assert max(ep) <= tol, (ep, gpg, gpo)
+
+
+def test_adjoint_1d_solid_gas_vs_oracle():
+    wl = W.solid_gas_1d(n=100, steps=12)
+    _case("1d_solid_gas_100_12", wl, 12, material=0, qbar_seed=1)
+
+
+def test_adjoint_1d_conservative_vs_oracle():
+    wl = W.solid_gas_1d(n=100, steps=6)
+    _case("1d_solid_gas_100_6_cons", wl, 6, material=0, qbar_seed=2, kind="cons")
+
+
+def test_adjoint_2d_shock_disc_vs_oracle():
+    wl = W.shock_disc_2d(n=20, steps=4, thinc=False, shock_x=0.3)
+    _case("2d_shock_disc_20_4", wl, 4, material=0, qbar_seed=3)
+
+
+def test_adjoint_2d_thinc_vs_oracle():
+    wl = W.shock_disc_2d(n=20, steps=4, thinc=True, shock_x=0.3)
+    _case("2d_shock_disc_thinc_20_4", wl, 4, material=0, qbar_seed=4, tol=1e-6)
+
+
+def test_adjoint_reactive_vs_oracle():
+    # fast reaction (A = 1e9 /s) so that the heat release matters within 3 steps
+    wl = W.reactive_plate_2d(nx=24, ny=12, steps=3, A=1e9)
+    _case("2d_reactive_plate_24x12_3", wl, 3, material=1, qbar_seed=5, params=(0, 1, 5))
+
+
+def test_adjoint_smooth_vs_oracle():
+    wl = W.smooth_disc_2d(n=16, steps=8, sigma_y=4e7)
+    _case("2d_smooth_disc_16_8", wl, 8, material=0)
+
+
+def _fd_check(name, wl, steps, material, direction, params, every=4, rel=1e-6, tol=1e-4):
+    """Central differences of the GPU objective with the recorded dts held."""
+    from paper_2009_14555_gb300.solver import Solver, pack
+    s = Solver.from_workload(wl)
+    w0 = pack([p.prim for p in wl.patches])
+    s.set_state(w0)
+    J0, dts = s.adj_forward(steps, every=every, material=material)
+    g, gp = s.adjoint(None, 1.0, kind=1)
+    theta0 = s.params()
+
+    def J_at(w, th):
+        s.set_params(th)
+        s.set_state(w)
+        J, _ = s.adj_forward(steps, every=every, material=material, dts=dts)
+        return J
+
+    rec = {}
+    d = pack(direction)
+    eps = rel * np.abs(w0).max() / max(np.abs(d).max(), 1e-300)
+    fd = (J_at(w0 + eps * d, theta0) - J_at(w0 - eps * d, theta0)) / (2 * eps)
+    an = float(g @ d)
+    rec["state"] = dict(fd=fd, adjoint=an, rel=abs(fd - an) / abs(an))
+    for k in params:
+        h = rel * theta0[k]
+        e = np.zeros_like(theta0)
+        e[k] = h
+        fdk = (J_at(w0, theta0 + e) - J_at(w0, theta0 - e)) / (2 * h)
+        rec[f"param{k}"] = dict(fd=fdk, adjoint=float(gp[k]), rel=abs(fdk - gp[k]) / abs(gp[k]))
+    s.close()
+    _record[name] = rec
+    _save()
+    for key, r in rec.items():
+        assert r["rel"] <= tol, (key, r)
+
+
+def test_adjoint_fd_smooth():
+    wl = W.smooth_disc_2d(n=32, steps=20, sigma_y=4e7)
+    p = wl.patches[0]
+    rng = np.random.default_rng(7)
+    k = {n: i for i, n in enumerate(W.prim_names(2, False))}
+    d = np.zeros_like(p.prim)
+    xc = (np.arange(p.nx) + 0.5) * p.dx
+    X, Y = np.meshgrid(xc, xc)
+    a, b = rng.uniform(0, 2 * np.pi, 2)
+    d[k["rho1"]] = p.prim[k["rho1"]] * np.sin(2 * np.pi * X + a)
+    d[k["rho2"]] = p.prim[k["rho2"]] * np.sin(2 * np.pi * X + a)
+    d[k["u"]] = 10.0 * np.cos(2 * np.pi * Y + b)
+    d[k["p"]] = 1e4 * np.sin(2 * np.pi * (X + Y))
+    _fd_check("fd_smooth_disc_32_20", wl, 20, 0, [d], params=(0, 1))
+
+
+def test_adjoint_fd_reactive():
+    wl = W.reactive_plate_2d(nx=32, ny=16, steps=6, A=1e9)
+    p = wl.patches[0]
+    k = {n: i for i, n in enumerate(W.prim_names(2, True))}
+    d = np.zeros_like(p.prim)
+    d[k["rho2"]] = p.prim[k["rho2"]]
+    _fd_check("fd_reactive_plate_32x16_6", wl, 6, 1, [d], params=(5,))
+
+
+def test_adjoint_checkpoint_interval_invariance():
+    wl = W.smooth_disc_2d(n=16, steps=9, sigma_y=4e7)
+    from paper_2009_14555_gb300.solver import Solver
+    res = []
+    for every in (1, 4, 9):
+        s = Solver.from_workload(wl)
+        s.set_prim([p.prim for p in wl.patches])
+        s.adj_forward(9, every=every, material=0)
+        res.append(s.adjoint(None, 1.0, kind=1))
+        s.close()
+    for g, gp in res[1:]:
+        assert np.allclose(g, res[0][0], rtol=1e-12, atol=1e-12 * np.abs(res[0][0]).max())
+        assert np.allclose(gp, res[0][1], rtol=1e-10, atol=0)
+
+
+def test_adjoint_fullsize_shock_disc():
+    """The 256^2 shock-disc adjoint case: 200 steps, checkpoint every 20,
+    gradient of the solid's time-integrated x momentum with respect to the
+    initial density field, checked along the seeded Gaussian perturbation by
+    central differences; forward and reverse times are recorded."""
+    import time
+    from paper_2009_14555_gb300.solver import Solver, pack
+    wl = W.adjoint_case_2d(256, steps=200)
+    p = wl.patches[0]
+    k = {n: i for i, n in enumerate(W.prim_names(2, False))}
+    d = np.zeros_like(p.prim)
+    shape = wl.extra["drho_shape"]
+    d[k["rho1"]] = p.prim[k["rho1"]] * shape
+    d[k["rho2"]] = p.prim[k["rho2"]] * shape
+    s = Solver.from_workload(wl)
+    w0 = pack([p.prim])
+    s.set_state(w0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J0, dts = s.adj_forward(200, every=20, material=0)
+    t1 = time.perf_counter()
+    g, gp = s.adjoint(None, 1.0, kind=1)
+    t2 = time.perf_counter()
+    dd = pack([d])
+    an = float(g @ dd)
+    rec = dict(J=J0, forward_s=t1 - t0, reverse_s=t2 - t1, dG=float(gp[0]), dsigma_y=float(gp[1]))
+    for eps in (1e-4, 1e-6):
+        def J_at(w):
+            s.set_state(w)
+            return s.adj_forward(200, every=20, material=0, dts=dts)[0]
+        fd = (J_at(w0 + eps * dd) - J_at(w0 - eps * dd)) / (2 * eps)
+        rec[f"fd_{eps:g}"] = dict(fd=fd, adjoint=an, rel=abs(fd - an) / abs(an))
+    s.close()
+    _record["fullsize_shock_disc_256_200"] = rec
+    _save()
+    assert min(rec["fd_0.0001"]["rel"], rec["fd_1e-06"]["rel"]) <= 1e-4, rec
+
+
+def test_autograd_function_matches_library_adjoint():
+    """torch.autograd through Rollout equals the direct dis_adjoint call for a
+    combined objective J + <c, q_final>."""
+    from paper_2009_14555_gb300.autograd import rollout
+    from paper_2009_14555_gb300.solver import Solver, pack
+    wl = W.smooth_disc_2d(n=16, steps=6, sigma_y=4e7)
+    s = Solver.from_workload(wl)
+    w0 = torch.tensor(pack([p.prim for p in wl.patches]), device=s.device, requires_grad=True)
+    theta = torch.tensor(s.params(), dtype=torch.float64, requires_grad=True)
+    c = torch.linspace(-1e-3, 1e-3, s.state_numel, dtype=torch.float64, device=s.device)
+    qN, J = rollout(s, w0, theta, 6, every=2, material=0)
+    L_ = J + (c * qN).sum()
+    L_.backward()
+    s2 = Solver.from_workload(wl)
+    s2.set_prim([p.prim for p in wl.patches])
+    s2.adj_forward(6, every=2, material=0)
+    g, gp = s2.adjoint(c.cpu().numpy(), 1.0, kind=1)
+    assert np.allclose(w0.grad.cpu().numpy(), g, rtol=1e-12, atol=1e-12 * np.abs(g).max())
+    assert np.allclose(theta.grad.numpy(), gp, rtol=1e-10, atol=0)
+    s.close()
+    s2.close()
