@@ -39,10 +39,18 @@ FLUX_DRAM_BYTES_PER_FACE = 73.80e6 / 524800
 FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
 # FP32: 152 SMs x 128 FMA lanes x 2 FLOP x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# FP32 FLOP per cell of one fused FP32-bulk stage (recovery with halo, x and
-# y faces, update), ncu count (see profiles/).
-FUSED32_FLOP_PER_CELL = 2000.0
-FUSED32_DRAM_BYTES_PER_CELL = None
+# FP32-bulk stage kernel k_stage32, per tuned variant (TX, TY, primitives
+# precomputed by k_prim32), counted by ncu (profiles/k_stage32_2d_reactive_plate.md):
+# executed FP32 FLOP (FADD + FMUL + 2 FFMA) and FP64 FLOP per cell-stage on the
+# 1024 x 512 reactive plate (halo recovery included where the kernel
+# recovers), and DRAM bytes (read + write) per cell of one launch on the full
+# 2048 x 1024 grid.
+STAGE32 = {
+    (16, 15, False): dict(flop32=1145.7e6 / 524288, flop64=14.07e6 / 524288,
+                          dram=(118531840 + 78248448) / 2097152),
+    (16, 15, True): dict(flop32=1007.4e6 / 524288, flop64=8.42e6 / 524288,
+                         dram=(220302080 + 90135296) / 2097152),
+}
 UNIT = "cell-updates/s"
 NX, NY = 2048, 1024
 
@@ -173,7 +181,7 @@ def run_gpu(args):
         rc, _, _ = s.check()
         final = s.get_state(kind=0)  # state after warm-up + timed steps, for the L1 comparison
         kernel_ms = s.step_timed(2)  # per-launch device time, outside the timed region
-        tile = s.tile_choice()[:2] if prec == "fp32_bulk" else (0, 0)
+        tile = s.tile_choice() if prec == "fp32_bulk" else (0, 0, False, None)
         results[prec] = dict(ms_total=tot_ms, ms_per_step=tot_ms / args.steps, wall=wall,
                              launches=launches, clocks=clk.summary(), ok=rc == 0, solver=s,
                              kernel_ms=kernel_ms, final=final, tile=tile)
@@ -208,8 +216,10 @@ def run_gpu(args):
     hbm64 = alg64 * cells / (r64["ms_per_step"] * 1e-3) / 1e9
     t64 = r64["kernel_ms"][1] * 1e-3
     flux64_tflops = FLUX_FP64_FLOP_PER_FACE * faces_x / t64 / 1e12
-    t32 = r["kernel_ms"][1] * 1e-3  # one fused stage (recovery, x and y faces, update)
-    flux32_tflops = FUSED32_FLOP_PER_CELL * cells / t32 / 1e12
+    t32 = r["kernel_ms"][1] * 1e-3  # one stage-kernel launch (live event timing)
+    tx, ty, pre = r["tile"][0], r["tile"][1], bool(r["tile"][2])
+    cnt = STAGE32.get((tx, ty, pre))
+    flux32_tflops = cnt["flop32"] * cells / t32 / 1e12 if cnt else None
     # per-field L1 of the FP32-bulk state against the float64 GPU state after the
     # same number of steps (the float64 GPU path matches the oracle to 1e-10)
     a32, a64 = r["final"].reshape(12, -1), r64["final"].reshape(12, -1)
@@ -228,18 +238,22 @@ def run_gpu(args):
                    "precision": "fp32_bulk",
                    "l2": "working set larger than L2 (state + primitives + faces > 129 MB)",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"bound": "alu", "kernel": "k_stage32 (fused stage, float32)",
+        "roofline": {"bound": "alu",
+                     "kernel": f"k_stage32<{tx}x{ty}{', precomputed primitives' if pre else ''}> (FP32-bulk stage)",
                      "achieved": flux32_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": flux32_tflops / FP32_PEAK_TFLOPS,
-                     "traffic": FUSED32_DRAM_BYTES_PER_CELL * cells if FUSED32_DRAM_BYTES_PER_CELL else None,
-                     "note": "FP32 FLOP per cell-stage from ncu x cells / live event time per launch; "
-                             "peak = 152 SMs x 128 FFMA lanes x 2 x 2.07 GHz"},
+                     "frac": flux32_tflops / FP32_PEAK_TFLOPS if flux32_tflops else None,
+                     "traffic": cnt["dram"] * cells if cnt else None,
+                     "fp64_flop_per_cell": cnt["flop64"] if cnt else None,
+                     "note": "executed FP32 FLOP per cell-stage (ncu) x cells / live event time per launch; "
+                             "peak = 152 SMs x 128 FFMA lanes x 2 x 2.07 GHz (nominal clock, no measured "
+                             "FP32 peak exists); traffic = ncu DRAM bytes of one launch"},
         "l1_vs_fp64": l1,
         "hbm": {"achieved_gbs": hbm32, "peak_gbs": hbm, "frac": hbm32 / hbm,
                 "algorithmic_bytes_per_cell_update": alg32, "peak_kind": kind},
-        "kernels_ms_per_launch": {"cfl_pass_per_stage": float(r["kernel_ms"][0]),
-                                  "fused_stage": float(r["kernel_ms"][1])},
-        "tile": list(r["tile"]),
+        "kernels_ms_per_launch": {("prim_pass" if r["tile"][2] else "cfl_pass"): float(r["kernel_ms"][0]),
+                                  "stage": float(r["kernel_ms"][1])},
+        "tile": {"tx": r["tile"][0], "ty": r["tile"][1], "precomputed_primitives": r["tile"][2],
+                 "tuned_ms_per_step": [round(float(x), 4) for x in r["tile"][3]]},
         "fp64": {"value": value64, "ms_per_step": r64["ms_per_step"],
                  "speedup_fp32_bulk": value / value64,
                  "hbm": {"achieved_gbs": hbm64, "frac": hbm64 / hbm, "algorithmic_bytes_per_cell_update": alg64},
@@ -294,7 +308,7 @@ def batch_bench(steps=10, warmup=3):
         ok = s.check()[0] == 0
         out[prec] = {"value": wl.cells / (ms * 1e-3), "ms_per_step": ms, "status_ok": ok}
         if prec == "fp32_bulk":
-            out[prec]["tile"] = list(s.tile_choice()[:2])
+            out[prec]["tile"] = list(s.tile_choice()[:3])
         s.close()
     return out
 

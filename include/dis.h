@@ -140,18 +140,33 @@ size_t dis_state_bytes(const dis_ctx* ctx, int kind);
 /* Number of kernel launches made by the last dis_step / dis_step_fixed_dt. */
 long long dis_last_launches(const dis_ctx* ctx);
 
-/* FP32-bulk contexts run one fused kernel per Runge-Kutta stage over tiles
- * of TX x TY cells; the first dis_step times three tile shapes (on the stage
- * buffer, leaving the state unchanged) and keeps the fastest.  Returns the
- * chosen shape (0 x 0 before tuning or for float64 contexts) and, if
- * stage_ms is not NULL, the measured stage times of the three shapes. */
-int dis_tile_choice(const dis_ctx* ctx, int* tx, int* ty, double* stage_ms);
+/* FP32-bulk contexts run one kernel per Runge-Kutta stage over tiles of
+ * TX x TY cells (primitives of the tile and its halo, faces, update).  In 2D
+ * there are DIS_NVARIANTS variants: tile shape v % 3; primitives recovered in
+ * the stage kernel ((v / 3) even) or copied from a pre-pass that recovers
+ * every cell once and also takes the CFL rate ((v / 3) odd); register budget
+ * for 3 (v < 6) or 4 resident CTAs per SM.  1D contexts have variants 0..2
+ * (the three shapes, recovery in the kernel).  The first dis_step times
+ * stage 1 of every variant (on the stage buffer, leaving the state unchanged)
+ * and keeps the one with the smallest time per step.  Returns the chosen
+ * shape (0 x 0 before tuning or for float64 contexts), whether it uses the
+ * pre-pass, and, if step_ms is not NULL, the tuned time per step of each
+ * variant (0 for variants the context does not have). */
+#define DIS_NVARIANTS 12
+int dis_tile_choice(const dis_ctx* ctx, int* tx, int* ty, int* precomputed, double* step_ms);
+
+/* Fix the FP32-bulk stage variant (0 .. DIS_NVARIANTS - 1 in 2D, 0 .. 2 in 1D) or
+ * return to tuning on the next step (-1).  For tests and measurements; the
+ * result of a step does not depend on the variant beyond float32 rounding
+ * order.  DIS_EINVAL for float64 contexts or an out-of-range variant. */
+int dis_set_variant(dis_ctx* ctx, int variant);
 
 /* Diagnostic: advance n_steps CFL steps like dis_step but launch kernel by
  * kernel with CUDA events between launches, and return in kernel_ms[4] the
  * mean device time per launch of the primitive-recovery, x-flux, y-flux (0 in
- * 1D) and update kernels (float64), or of the CFL pass and the fused stage
- * kernel in slots 0 and 1 (FP32-bulk).  Synchronises after every stage. */
+ * 1D) and update kernels (float64), or, FP32-bulk: slot 0 the CFL pass (one
+ * launch per step) or the primitive pre-pass (one per stage), slot 1 the
+ * stage kernel.  Synchronises after every stage. */
 int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
 
 /* ---- Adjoint (reverse mode) of the float64 step -------------------------

@@ -16,6 +16,7 @@ DIS_OK, DIS_EINVAL, DIS_ENOMEM, DIS_ECUDA, DIS_ENONPHYSICAL, DIS_ESTATE = 0, -1,
 DIS_CONSERVATIVE, DIS_PRIMITIVE = 0, 1
 DIS_FP64, DIS_FP32_BULK = 0, 1
 DIS_NPARAM = 6  # per material l: G, sigma_y, Q at 3 l + k
+DIS_NVARIANTS = 12  # FP32-bulk stage variants (2D: 3 tile shapes x 2 primitive sources x 2 register budgets)
 
 
 class DisMaterial(ctypes.Structure):
@@ -55,7 +56,8 @@ SIGNATURES = {
     "dis_state_bytes": (c_size_t, [c_void_p, c_int]),
     "dis_last_launches": (c_longlong, [c_void_p]),
     "dis_step_timed": (c_int, [c_void_p, c_int, c_void_p]),
-    "dis_tile_choice": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), c_void_p]),
+    "dis_set_variant": (c_int, [c_void_p, c_int]),
+    "dis_tile_choice": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), c_void_p]),
     "dis_cfl_dt_static": (c_int, [c_int, c_int, POINTER(DisPatch), POINTER(DisMaterial), c_int,
                                    c_double, c_void_p, c_void_p, c_void_p]),
     "dis_adj_forward": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, POINTER(c_double)]),

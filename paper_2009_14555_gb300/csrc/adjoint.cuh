@@ -87,13 +87,14 @@ __device__ __forceinline__ void add_nz(double* p, double v) {
   if (v != 0.0) atomicAdd(p, v);
 }
 
-// d minmod(a, b) / da and / db on the branch the forward took (ties pick a,
-// as fmin does in the Dual evaluation).
+// d minmod(a, b) / da and / db on the branch the forward took; equal
+// magnitudes split the derivative (the min convention of dual.cuh).
 __device__ __forceinline__ void minmod_grad(double a, double b, double& da, double& db) {
   da = db = 0.0;
   if (a * b > 0.0) {
     if (fabs(b) < fabs(a)) db = 1.0;
-    else da = 1.0;
+    else if (fabs(a) < fabs(b)) da = 1.0;
+    else da = db = 0.5;
   }
 }
 

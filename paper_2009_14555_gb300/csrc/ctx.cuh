@@ -40,17 +40,20 @@ struct dis_ctx {
   double* dtfix = nullptr;
   double* dtlast = nullptr;
   int* status = nullptr;
-  // FP32-bulk fused stage kernel: tile tables per tile shape, chosen shape
+  // FP32-bulk stage kernel: tile tables per tile shape; variant v = tile
+  // shape v % 3, primitives recovered in the kernel ((v / 3) even) or
+  // precomputed by k_prim32 ((v / 3) odd), 3 (v < 6) or 4 resident CTAs per SM
+  // (2D only); chosen variant and tuned per-step times
   std::vector<int4> tiles[3];
   int4* d_tiles[3] = {nullptr, nullptr, nullptr};
   int variant = -1;
-  double tune_ms[3] = {0, 0, 0};
+  double tune_ms[DIS_NVARIANTS] = {};
   // FP32-bulk buffers: (phi1, rho E) float64 pairs and float32 planes
-  double* q64[2] = {nullptr, nullptr};
-  float* q32[2] = {nullptr, nullptr};
+  // q^n and two stage buffers: a stage kernel reads the halo of its source
+  // from neighbouring tiles, so no stage may write the buffer it reads
+  double* q64[3] = {nullptr, nullptr, nullptr};
+  float* q32[3] = {nullptr, nullptr, nullptr};
   float* W32 = nullptr;
-  float* Fx32 = nullptr;
-  float* Fy32 = nullptr;
   PatchDev* d_pd = nullptr;
   int4 *d_seg_prim = nullptr, *d_seg_fx = nullptr, *d_seg_fy = nullptr, *d_seg_cell = nullptr;
   long long launches = 0;

@@ -147,7 +147,7 @@ size_t carve(dis_ctx* c, char* base) {
   const size_t T = (size_t)c->T;
   const size_t nfx = (size_t)(c->nf + n_extra(c->dim));
   size_t oq0 = 0, oq1 = 0, ow = 0, ofx = 0, ofy = 0;
-  size_t o64a = 0, o64b = 0, o32a = 0, o32b = 0, ow32 = 0, ofx32 = 0, ofy32 = 0;
+  size_t o64[3] = {0, 0, 0}, o32[3] = {0, 0, 0}, ow32 = 0;
   if (!c->fp32) {
     const size_t dpl = sizeof(double) * T;
     oq0 = k.take(c->nf * dpl);
@@ -156,13 +156,11 @@ size_t carve(dis_ctx* c, char* base) {
     ofx = k.take(sizeof(double) * nfx * c->NFX);
     ofy = k.take(sizeof(double) * nfx * c->NFY);
   } else {
-    o64a = k.take(2 * sizeof(double) * T);
-    o64b = k.take(2 * sizeof(double) * T);
-    o32a = k.take(c->nf * sizeof(float) * T);
-    o32b = k.take(c->nf * sizeof(float) * T);
+    for (int b = 0; b < 3; ++b) {
+      o64[b] = k.take(2 * sizeof(double) * T);
+      o32[b] = k.take(c->nf * sizeof(float) * T);
+    }
     ow32 = k.take(c->nf * sizeof(float) * T);
-    ofx32 = k.take(sizeof(float) * (nfx + 2) * c->NFX);
-    ofy32 = k.take(sizeof(float) * (nfx + 2) * c->NFY);
   }
   size_t oio = k.take(sizeof(double) * (size_t)c->nf * c->ncells);
   size_t ort = k.take(sizeof(unsigned long long) * c->np);
@@ -185,13 +183,11 @@ size_t carve(dis_ctx* c, char* base) {
       c->Fx = (double*)(base + ofx);
       c->Fy = (double*)(base + ofy);
     } else {
-      c->q64[0] = (double*)(base + o64a);
-      c->q64[1] = (double*)(base + o64b);
-      c->q32[0] = (float*)(base + o32a);
-      c->q32[1] = (float*)(base + o32b);
+      for (int b = 0; b < 3; ++b) {
+        c->q64[b] = (double*)(base + o64[b]);
+        c->q32[b] = (float*)(base + o32[b]);
+      }
       c->W32 = (float*)(base + ow32);
-      c->Fx32 = (float*)(base + ofx32);
-      c->Fy32 = (float*)(base + ofy32);
     }
     c->io = (double*)(base + oio);
     c->rate = (unsigned long long*)(base + ort);
@@ -261,8 +257,6 @@ StepArgs32 base_args32(dis_ctx* c) {
   a.NFX = c->NFX;
   a.NFY = c->NFY;
   a.W = c->W32;
-  a.Fx = c->Fx32;
-  a.Fy = c->Fy32;
   a.rate = c->rate;
   a.dtlast = c->dtlast;
   a.status = c->status;
@@ -271,98 +265,140 @@ StepArgs32 base_args32(dis_ctx* c) {
   return a;
 }
 
-// Stage k of the FP32-bulk step (same sequence as launch_step).
-template <int DIM, bool RX>
-void enqueue_stage32(dis_ctx* c, cudaStream_t st, StepArgs32& a, int stg, bool fixed, cudaEvent_t* ev) {
-  const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
-  const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
-  const unsigned np = (unsigned)c->seg_prim.size(), nfx = (unsigned)c->seg_fx.size(),
-                 nfy = (unsigned)c->seg_fy.size(), nc = (unsigned)c->seg_cell.size();
-  a.q64src = stg == 0 ? c->q64[0] : c->q64[1];
-  a.q32src = stg == 0 ? c->q32[0] : c->q32[1];
-  a.q64n = c->q64[0];
-  a.q32n = c->q32[0];
-  a.q64dst = stg == 2 ? c->q64[0] : c->q64[1];
-  a.q32dst = stg == 2 ? c->q32[0] : c->q32[1];
-  a.a = ca[stg];
-  a.b = cb[stg];
-  a.last = stg == 2;
-  if (ev) cudaEventRecord(ev[0], st);
-  k_prim32<DIM, RX><<<np, SEG, 0, st>>>(c->phys, c->physf, a, c->d_seg_prim, (!fixed && stg == 0) ? 1 : 0);
-  if (ev) cudaEventRecord(ev[1], st);
-  k_flux32<DIM, RX, 0><<<nfx, SEG, 0, st>>>(c->physf, a, c->d_seg_fx);
-  if (ev) cudaEventRecord(ev[2], st);
-  if constexpr (DIM == 2) k_flux32<DIM, RX, 1><<<nfy, SEG, 0, st>>>(c->physf, a, c->d_seg_fy);
-  if (ev) cudaEventRecord(ev[3], st);
-  k_update32<DIM, RX><<<nc, SEG, 0, st>>>(c->phys, c->physf, a, c->d_seg_cell);
-  if (ev) cudaEventRecord(ev[4], st);
-}
-
-template <int DIM, bool RX, int TX, int TY, int NT>
-void stage_fused(dis_ctx* c, cudaStream_t st, StepArgs32& a, int v) {
+template <int DIM, bool RX, int TX, int TY, int NT, bool PRE, int MINB>
+void stage_fused(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
   constexpr size_t smem = fused32_smem<DIM, RX, TX, TY>();
   static bool attr_set = false;  // per instantiation, per process
   if (!attr_set) {
-    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT, PRE, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT, PRE, MINB>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr_set = true;
   }
-  k_stage32<DIM, RX, TX, TY, NT><<<(unsigned)c->tiles[v].size(), NT, smem, st>>>(c->phys, c->physf, a,
-                                                                                 c->d_tiles[v]);
+  k_stage32<DIM, RX, TX, TY, NT, PRE, MINB><<<(unsigned)c->tiles[shape].size(), NT, smem, st>>>(
+      c->phys, c->physf, a, c->d_tiles[shape]);
 }
 
+// Number of FP32-bulk stage variants: 2D: 3 tile shapes x (recovery in the
+// stage kernel, primitives from the pre-pass) x (3, 4 resident CTAs per SM
+// requested from the register allocator); 1D: the 3 shapes.
+int n_variants(const dis_ctx* c) { return c->dim == 2 ? DIS_NVARIANTS : 3; }
+bool variant_pre(int v) { return (v / 3) % 2 == 1; }
+
+template <int DIM, bool RX, bool PRE, int MINB>
+void stage_kernel_2d(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
+  if (shape == 0) stage_fused<DIM, RX, 16, 15, 256, PRE, MINB>(c, st, a, shape);
+  else if (shape == 1) stage_fused<DIM, RX, 20, 12, 256, PRE, MINB>(c, st, a, shape);
+  else stage_fused<DIM, RX, 32, 7, 256, PRE, MINB>(c, st, a, shape);
+}
+
+// The stage kernel of variant v (without the primitive pre-pass).
 template <int DIM, bool RX>
-void stage_fused_v(dis_ctx* c, cudaStream_t st, StepArgs32& a, int v) {
+void stage_kernel_v(dis_ctx* c, cudaStream_t st, StepArgs32& a, int v) {
+  const int shape = v % 3;
   if constexpr (DIM == 2) {
-    if (v == 0) stage_fused<DIM, RX, 16, 15, 256>(c, st, a, v);
-    else if (v == 1) stage_fused<DIM, RX, 20, 12, 256>(c, st, a, v);
-    else stage_fused<DIM, RX, 32, 7, 256>(c, st, a, v);
+    const bool pre = variant_pre(v), mb4 = v >= 6;
+    if (pre) {
+      if (mb4) stage_kernel_2d<DIM, RX, true, 4>(c, st, a, shape);
+      else stage_kernel_2d<DIM, RX, true, 3>(c, st, a, shape);
+    } else {
+      if (mb4) stage_kernel_2d<DIM, RX, false, 4>(c, st, a, shape);
+      else stage_kernel_2d<DIM, RX, false, 3>(c, st, a, shape);
+    }
   } else {
-    if (v == 0) stage_fused<DIM, RX, 122, 1, 128>(c, st, a, v);
-    else if (v == 1) stage_fused<DIM, RX, 250, 1, 256>(c, st, a, v);
-    else stage_fused<DIM, RX, 506, 1, 512>(c, st, a, v);
+    if (shape == 0) stage_fused<DIM, RX, 122, 1, 128, false, 1>(c, st, a, shape);
+    else if (shape == 1) stage_fused<DIM, RX, 250, 1, 256, false, 1>(c, st, a, shape);
+    else stage_fused<DIM, RX, 506, 1, 512, false, 1>(c, st, a, shape);
   }
 }
 
+// Primitive pre-pass of the precomputed-primitive variants; with rate_on it
+// also takes the CFL rate, so those variants need no separate CFL pass.
 template <int DIM, bool RX>
-void set_stage_args32(dis_ctx* c, StepArgs32& a, int stg) {
+void prim_pass32(dis_ctx* c, cudaStream_t st, StepArgs32& a, bool rate_on) {
+  k_prim32<DIM, RX><<<(unsigned)c->seg_prim.size(), SEG, 0, st>>>(c->phys, c->physf, a, c->d_seg_prim,
+                                                                 rate_on ? 1 : 0);
+}
+
+// One stage of variant v: [k_prim32 +] k_stage32; returns the launch count.
+template <int DIM, bool RX>
+int stage_fused_v(dis_ctx* c, cudaStream_t st, StepArgs32& a, int v, bool rate_on) {
+  int l = 1;
+  if (variant_pre(v)) {
+    prim_pass32<DIM, RX>(c, st, a, rate_on);
+    ++l;
+  }
+  stage_kernel_v<DIM, RX>(c, st, a, v);
+  return l;
+}
+
+// Buffers of the FP32-bulk stages: q^n (0) -> q1 (1) -> q2 (2) -> q^{n+1} (0).
+// A stage kernel that recovers its tile reads the halo of its source from
+// neighbouring tiles, so it must not write that source; with the primitive
+// pre-pass (in_place) it reads only its own cells of the source, and stage 2
+// updates buffer 1 in place (better L2 reuse).  The last stage overwrites q^n
+// cell by cell, read only at the same cell.  scratch_last: the tuner's full
+// step ends in buffer 1 (in_place: buffer 2) instead of q^n.
+template <int DIM, bool RX>
+void set_stage_args32(dis_ctx* c, StepArgs32& a, int stg, bool in_place, bool scratch_last = false) {
   const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
   const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
-  a.q64src = stg == 0 ? c->q64[0] : c->q64[1];
-  a.q32src = stg == 0 ? c->q32[0] : c->q32[1];
+  int src, dst;
+  if (in_place) {
+    src = stg == 0 ? 0 : 1;
+    dst = stg == 2 ? (scratch_last ? 2 : 0) : 1;
+  } else {
+    src = stg;
+    dst = stg == 2 ? (scratch_last ? 1 : 0) : stg + 1;
+  }
+  a.q64src = c->q64[src];
+  a.q32src = c->q32[src];
   a.q64n = c->q64[0];
   a.q32n = c->q32[0];
-  a.q64dst = stg == 2 ? c->q64[0] : c->q64[1];
-  a.q32dst = stg == 2 ? c->q32[0] : c->q32[1];
+  a.q64dst = c->q64[dst];
+  a.q32dst = c->q32[dst];
   a.a = ca[stg];
   a.b = cb[stg];
   a.last = stg == 2;
 }
 
-// Autotuner: time stage 1 of the fused kernel (it reads q^n and writes only
-// the stage buffer, so the state is untouched) for each tile shape and keep
-// the fastest.
+// Autotuner: time one full step of every variant with the last stage
+// writing a scratch buffer (the state is untouched) and keep the fastest.
+// The CFL rate of q^n is taken once first; dt is then the step's dt.
 template <int DIM, bool RX>
 int autotune32(dis_ctx* c) {
   StepArgs32 a = base_args32(c);
   a.dtfix = nullptr;
-  CU(cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, c->stream));
-  set_stage_args32<DIM, RX>(c, a, 0);
-  k_cfl32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, c->physf, a, c->d_seg_cell);
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
+  CU(cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, c->stream));
+  set_stage_args32<DIM, RX>(c, a, 0, false);
+  k_cfl32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, c->physf, a, c->d_seg_cell);
   double best = 1e30;
   int bv = 0;
-  for (int v = 0; v < 3; ++v) {
-    for (int w = 0; w < 2; ++w) stage_fused_v<DIM, RX>(c, c->stream, a, v);
-    CU(cudaEventRecord(e0, c->stream));
-    for (int r = 0; r < 3; ++r) stage_fused_v<DIM, RX>(c, c->stream, a, v);
-    CU(cudaEventRecord(e1, c->stream));
-    CU(cudaEventSynchronize(e1));
-    float ms = 0.f;
-    CU(cudaEventElapsedTime(&ms, e0, e1));
-    c->tune_ms[v] = ms / 3.0;
-    if (ms < best) { best = ms; bv = v; }
+  for (int v = 0; v < n_variants(c); ++v) {
+    const bool pre = variant_pre(v);
+    for (int rep = 0; rep < 3; ++rep) {  // rep 0 warms up
+      CU(cudaEventRecord(e0, c->stream));
+      if (!pre) {  // the step's CFL pass (rate unchanged: the max is idempotent)
+        set_stage_args32<DIM, RX>(c, a, 0, false);
+        k_cfl32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, c->physf, a,
+                                                                               c->d_seg_cell);
+      }
+      for (int stg = 0; stg < 3; ++stg) {
+        set_stage_args32<DIM, RX>(c, a, stg, pre, true);
+        stage_fused_v<DIM, RX>(c, c->stream, a, v, false);
+      }
+      CU(cudaEventRecord(e1, c->stream));
+      CU(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CU(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep == 1) c->tune_ms[v] = ms;
+      if (rep == 2) c->tune_ms[v] = 0.5 * (c->tune_ms[v] + ms);
+    }
+    if (c->tune_ms[v] < best) { best = c->tune_ms[v]; bv = v; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -379,16 +415,18 @@ long long launch_step(dis_ctx* c, cudaStream_t st, bool fixed) {
     StepArgs32 a = base_args32(c);
     a.dtfix = fixed ? c->dtfix : nullptr;
     long long l = 0;
+    const int v = c->variant < 0 ? 0 : c->variant;
     if (!fixed) {
       cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, st);
-      set_stage_args32<DIM, RX>(c, a, 0);
-      k_cfl32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, st>>>(c->phys, c->physf, a, c->d_seg_cell);
-      ++l;
+      if (!variant_pre(v)) {
+        set_stage_args32<DIM, RX>(c, a, 0, false);
+        k_cfl32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, st>>>(c->phys, c->physf, a, c->d_seg_cell);
+        ++l;
+      }
     }
     for (int stg = 0; stg < 3; ++stg) {
-      set_stage_args32<DIM, RX>(c, a, stg);
-      stage_fused_v<DIM, RX>(c, st, a, c->variant < 0 ? 0 : c->variant);
-      ++l;
+      set_stage_args32<DIM, RX>(c, a, stg, variant_pre(v));
+      l += stage_fused_v<DIM, RX>(c, st, a, v, !fixed && stg == 0);
     }
     return l;
   }
@@ -434,33 +472,44 @@ int timed_steps(dis_ctx* c, int n_steps, double* ms) {
   for (int k = 0; k < 5; ++k) CU(cudaEventCreate(&ev[k]));
   double acc[4] = {0, 0, 0, 0};
   if (c->fp32) {
-    // slot 0: CFL pass (once per step, reported per stage), slot 1: fused stage kernel
+    // slot 0: CFL pass (in-kernel recovery: once per step, reported per stage)
+    // or primitive pre-pass (precomputed primitives: per stage); slot 1: stage kernel
     if (c->variant < 0) {
       const int rc = autotune32<DIM, RX>(c);
       if (rc) return rc;
     }
+    const int v = c->variant;
     StepArgs32 a32 = base_args32(c);
     for (int s = 0; s < n_steps; ++s) {
       CU(cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, c->stream));
-      set_stage_args32<DIM, RX>(c, a32, 0);
-      CU(cudaEventRecord(ev[0], c->stream));
-      k_cfl32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, c->physf, a32, c->d_seg_cell);
-      CU(cudaEventRecord(ev[1], c->stream));
-      CU(cudaEventSynchronize(ev[1]));
       float t = 0.f;
-      CU(cudaEventElapsedTime(&t, ev[0], ev[1]));
-      acc[0] += t;
-      for (int stg = 0; stg < 3; ++stg) {
-        set_stage_args32<DIM, RX>(c, a32, stg);
+      if (!variant_pre(v)) {
+        set_stage_args32<DIM, RX>(c, a32, 0, false);
+        CU(cudaEventRecord(ev[0], c->stream));
+        k_cfl32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, c->physf, a32, c->d_seg_cell);
         CU(cudaEventRecord(ev[1], c->stream));
-        stage_fused_v<DIM, RX>(c, c->stream, a32, c->variant);
+        CU(cudaEventSynchronize(ev[1]));
+        CU(cudaEventElapsedTime(&t, ev[0], ev[1]));
+        acc[0] += 3.0 * t;
+      }
+      for (int stg = 0; stg < 3; ++stg) {
+        set_stage_args32<DIM, RX>(c, a32, stg, variant_pre(v));
+        if (variant_pre(v)) {
+          CU(cudaEventRecord(ev[0], c->stream));
+          prim_pass32<DIM, RX>(c, c->stream, a32, stg == 0);
+          CU(cudaEventRecord(ev[1], c->stream));
+          CU(cudaEventSynchronize(ev[1]));
+          CU(cudaEventElapsedTime(&t, ev[0], ev[1]));
+          acc[0] += t;
+        }
+        CU(cudaEventRecord(ev[1], c->stream));
+        stage_kernel_v<DIM, RX>(c, c->stream, a32, v);
         CU(cudaEventRecord(ev[2], c->stream));
         CU(cudaEventSynchronize(ev[2]));
         CU(cudaEventElapsedTime(&t, ev[1], ev[2]));
         acc[1] += t;
       }
     }
-    acc[0] *= 3.0;  // reported per stage like the other slots
     n_steps = -n_steps;  // skip the float64 loop below
   }
   for (int s = 0; s < n_steps; ++s) {
@@ -790,17 +839,35 @@ int dis_check(dis_ctx* c, int* bad_patch, int* bad_cell) {
 
 long long dis_last_launches(const dis_ctx* c) { return c ? c->launches : 0; }
 
-int dis_tile_choice(const dis_ctx* c, int* tx, int* ty, double* stage_ms) {
+int dis_tile_choice(const dis_ctx* c, int* tx, int* ty, int* precomputed, double* step_ms) {
   if (!c) return fail(DIS_EINVAL, "dis_tile_choice: NULL context");
+  if (precomputed) *precomputed = 0;
   if (!c->fp32 || c->variant < 0) {
     if (tx) *tx = 0;
     if (ty) *ty = 0;
     return DIS_OK;
   }
-  if (tx) *tx = c->dim == 2 ? kTiles2D[c->variant][0] : kTiles1D[c->variant];
-  if (ty) *ty = c->dim == 2 ? kTiles2D[c->variant][1] : 1;
-  if (stage_ms)
-    for (int v = 0; v < 3; ++v) stage_ms[v] = c->tune_ms[v];
+  const int shape = c->variant % 3;
+  if (tx) *tx = c->dim == 2 ? kTiles2D[shape][0] : kTiles1D[shape];
+  if (ty) *ty = c->dim == 2 ? kTiles2D[shape][1] : 1;
+  if (precomputed) *precomputed = variant_pre(c->variant);
+  if (step_ms)
+    for (int v = 0; v < DIS_NVARIANTS; ++v) step_ms[v] = v < n_variants(c) ? c->tune_ms[v] : 0.0;
+  return DIS_OK;
+}
+
+int dis_set_variant(dis_ctx* c, int variant) {
+  if (!c) return fail(DIS_EINVAL, "dis_set_variant: NULL context");
+  if (!c->fp32) return fail(DIS_EINVAL, "dis_set_variant: only FP32-bulk contexts have variants");
+  if (variant < -1 || variant >= n_variants(c))
+    return fail(DIS_EINVAL, "dis_set_variant: variant %d outside -1..%d", variant, n_variants(c) - 1);
+  if (c->cap && (c->graph[0] || c->graph[1])) cudaStreamSynchronize(c->cap);
+  for (int g = 0; g < 2; ++g)
+    if (c->graph[g]) {
+      cudaGraphExecDestroy(c->graph[g]);
+      c->graph[g] = nullptr;
+    }
+  c->variant = variant;
   return DIS_OK;
 }
 

@@ -86,9 +86,16 @@ __device__ __forceinline__ Dual tanh(Dual a) {
   return Dual(t, (1.0 - t * t) * a.d);
 }
 __device__ __forceinline__ Dual cosh(Dual a) { return Dual(::cosh(a.v), ::sinh(a.v) * a.d); }
-__device__ __forceinline__ Dual fabs(Dual a) { return a.v < 0.0 ? -a : a; }
-__device__ __forceinline__ Dual fmin(Dual a, Dual b) { return b.v < a.v ? b : a; }
-__device__ __forceinline__ Dual fmax(Dual a, Dual b) { return b.v > a.v ? b : a; }
+// Non-differentiable points take the conventions of PyTorch's autograd (the
+// float64 oracle's reverse mode): |x| has derivative 0 at 0, and min / max of
+// two equal values pass half of the derivative to each argument.
+__device__ __forceinline__ Dual fabs(Dual a) { return a.v < 0.0 ? -a : (a.v > 0.0 ? a : Dual(0.0, 0.0)); }
+__device__ __forceinline__ Dual fmin(Dual a, Dual b) {
+  return b.v < a.v ? b : (a.v < b.v ? a : Dual(a.v, 0.5 * (a.d + b.d)));
+}
+__device__ __forceinline__ Dual fmax(Dual a, Dual b) {
+  return b.v > a.v ? b : (a.v > b.v ? a : Dual(a.v, 0.5 * (a.d + b.d)));
+}
 __device__ __forceinline__ Dual copysign(Dual a, Dual b) {
   return ((a.v < 0.0) != (b.v < 0.0)) ? -a : a;
 }

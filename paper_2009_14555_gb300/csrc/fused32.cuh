@@ -2,7 +2,8 @@
 //
 // A CTA owns a tile of TX x TY interior cells (TX cells of one row in 1D).
 // It recovers the primitives of the tile plus a 3-cell halo into shared
-// memory (ghosts by index map), computes every x face and y face of the tile
+// memory (ghosts by index map; or, PRE, copies them from the planes of a
+// primitive pre-pass, which recovers every cell once), computes every x face and y face of the tile
 // (MUSCL/THINC-BVD + HLLD) into shared memory, and updates its cells
 // (divergence, non-conservative terms, RK3 combination, last stage: plastic
 // and reactive steps).  Primitives and face data never go to HBM: per stage
@@ -148,8 +149,8 @@ constexpr size_t fused32_smem() {
   return sizeof(float) * ((size_t)Lay<DIM, RX>::NF * HX * HY + (size_t)S::N * (NFX + NFY)) + 16 * sizeof(double);
 }
 
-template <int DIM, bool RX, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) k_stage32(Phys P, PhysF F, StepArgs32 A, const int4* __restrict__ tiles) {
+template <int DIM, bool RX, int TX, int TY, int NT, bool PRE, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_stage32(Phys P, PhysF F, StepArgs32 A, const int4* __restrict__ tiles) {
   static_assert(TX * TY <= NT, "one thread per tile cell in the update phase");
   using L = Lay<DIM, RX>;
   using S = FSlots<DIM, RX>;
@@ -166,12 +167,20 @@ __global__ void __launch_bounds__(NT) k_stage32(Phys P, PhysF F, StepArgs32 A, c
   const int tid = threadIdx.x;
   const float dxf = (float)pd.dx, dyf = (float)pd.dy;
 
-  // 1. primitives of the tile and its halo
+  // 1. primitives of the tile and its halo: recovered here, or (PRE) copied
+  //    from the pre-pass planes, which already hold the ghost cells
   for (int c = tid; c < HX * HY; c += NT) {
     const int hx = c % HX, hy = c / HX;
     const int i = i0 - NG + hx;
     const int j = DIM == 2 ? j0 - NG + hy : 0;
     if (i < -NG || i >= pd.nx + NG || (DIM == 2 && (j < -NG || j >= pd.ny + NG))) continue;
+    if constexpr (PRE) {
+      const long long kk = cidx(pd, i, j);
+      const int plane = HX * HY;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) Wsm[f * plane + c] = A.W[f * A.T + kk];
+      continue;
+    }
     bool fx = false, fy = false;
     const int si = ghost_map(i, pd.nx, pd.bc[0], pd.bc[1], fx);
     const int sj = DIM == 2 ? ghost_map(j, pd.ny, pd.bc[2], pd.bc[3], fy) : 0;

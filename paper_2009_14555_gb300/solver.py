@@ -115,17 +115,24 @@ class Solver:
         L.dis_step_fixed_dt(self.ctx, n, dt.ctypes.data)
 
     def step_timed(self, n=1):
-        """Mean device ms per launch of [prim, flux x, flux y, update] over n steps."""
+        """Mean device ms per launch over n steps: float64 [prim, flux x, flux y,
+        update]; FP32-bulk [CFL pass or primitive pre-pass, stage kernel, 0, 0]."""
         ms = np.zeros(4, np.float64)
         L.dis_step_timed(self.ctx, n, ms.ctypes.data)
         return ms
 
     def tile_choice(self):
-        """(TX, TY, stage ms of the three tuned shapes) of an FP32-bulk context."""
-        tx, ty = ctypes.c_int(0), ctypes.c_int(0)
-        ms = np.zeros(3, np.float64)
-        L.load().dis_tile_choice(self.ctx, ctypes.byref(tx), ctypes.byref(ty), ms.ctypes.data)
-        return tx.value, ty.value, ms
+        """(TX, TY, precomputed primitives, tuned ms per step of each variant)
+        of an FP32-bulk context (include/dis.h: dis_tile_choice)."""
+        tx, ty, pre = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        ms = np.zeros(L.DIS_NVARIANTS, np.float64)
+        L.check(L.load().dis_tile_choice(self.ctx, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(pre),
+                                         ms.ctypes.data))
+        return tx.value, ty.value, bool(pre.value), ms
+
+    def set_variant(self, v):
+        """Fix the FP32-bulk stage variant (-1: tune on the next step)."""
+        L.check(L.load().dis_set_variant(self.ctx, int(v)))
 
     def check(self):
         return L.dis_check(self.ctx)

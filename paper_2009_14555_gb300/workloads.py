@@ -259,8 +259,10 @@ def smooth_disc_2d(n: int = 16, steps: int = 10, u0: float = 100.0, seed: int = 
 
     An elastoplastic disc (radius 0.25 at the centre) with a tanh-profiled
     volume fraction (width 1.5 cells), a Gaussian x-velocity pulse of peak u0
-    (width 0.2), a 1 % seeded smooth density modulation and uniform pressure:
-    no shocks, no THINC.  sigma_y overrides the solid's yield stress.
+    (width 0.2), and seeded smooth periodic modulations of every other field
+    (densities 1 %, pressure 1 %, y velocity 0.1 u0, stretch components 1e-4),
+    so that no field is uniform: no shocks, no THINC, no exactly equal
+    neighbour differences.  sigma_y overrides the solid's yield stress.
     """
     w, k = _blank(2, False, n, n)
     d = 1.0 / n
@@ -270,12 +272,19 @@ def smooth_disc_2d(n: int = 16, steps: int = 10, u0: float = 100.0, seed: int = 
     phi = 0.5 * (1.0 + np.tanh((0.25 - r) / (1.5 * d)))
     w[k["phi1"]] = EPS_PHI + (1 - 2 * EPS_PHI) * phi
     rng = np.random.default_rng(seed)
-    a, b = rng.uniform(0, 2 * np.pi, 2)
-    mod = 1.0 + 0.01 * np.sin(2 * np.pi * X + a) * np.cos(2 * np.pi * Y + b)
+    ph = rng.uniform(0, 2 * np.pi, size=(8, 2))
+
+    def wave(m):
+        return np.sin(2 * np.pi * X + ph[m, 0]) * np.cos(2 * np.pi * Y + ph[m, 1])
+
+    mod = 1.0 + 0.01 * wave(0)
     w[k["rho1"]] = SOLID_RHO0 * mod
     w[k["rho2"]] = 1.2 * mod
-    w[k["p"]] = 1e5
+    w[k["p"]] = 1e5 * (1.0 + 0.01 * wave(1))
     w[k["u"]] = u0 * np.exp(-r ** 2 / (2 * 0.2 ** 2))
+    w[k["v"]] = 0.1 * u0 * wave(2)
+    for m, f in enumerate(("V11", "V12", "V21", "V22", "V33")):
+        w[k[f]] = w[k[f]] + 1e-4 * wave(3 + m)
     solid = dict(SOLID)
     if sigma_y is not None:
         solid["sigma_y"] = sigma_y
@@ -284,13 +293,58 @@ def smooth_disc_2d(n: int = 16, steps: int = 10, u0: float = 100.0, seed: int = 
     return Workload(name or f"2d_smooth_disc_{n}", 2, [solid, AIR], [p], 0.6, steps, False)
 
 
+def perturbed(wl: Workload, seed: int = 11, amp: float = 1e-4) -> Workload:
+    """Copy of a workload whose primitive fields carry a seeded cell-wise
+    random perturbation of relative size amp (velocities amp x 100 m/s,
+    stretch components amp x 1e-2, the volume fraction amp x min(phi, 1 - phi),
+    the reactant fraction amp x lam downwards), so that no two neighbouring
+    values are equal: limiter, min / max and region choices then have margins
+    far above round-off (derivative checks are well posed)."""
+    import copy
+    out = copy.deepcopy(wl)
+    rng = np.random.default_rng(seed)
+    k = {n: i for i, n in enumerate(prim_names(wl.dim, wl.reactive))}
+    for p in out.patches:
+        x = p.prim
+
+        def u():
+            return rng.uniform(-1.0, 1.0, size=x.shape[1:])
+
+        phi = x[k["phi1"]]
+        x[k["phi1"]] = phi + amp * np.minimum(phi, 1.0 - phi) * u()
+        for f in ("rho1", "rho2", "p"):
+            x[k[f]] = x[k[f]] * (1.0 + amp * u())
+        for f in ("u", "v"):
+            if f in k:
+                x[k[f]] = x[k[f]] + amp * 100.0 * u()
+        for f in ("V11", "V12", "V21", "V22", "V33"):
+            if f in k:
+                x[k[f]] = x[k[f]] + amp * 1e-2 * u()
+        if "lam" in k:
+            x[k["lam"]] = x[k["lam"]] * (1.0 - amp * np.abs(u()))
+    out.name = wl.name + "_perturbed"
+    return out
+
+
 def adjoint_case_2d(n: int = 256, steps: int = 200, seed: int = 4) -> Workload:
-    """256^2 shock-disc problem with a smooth Gaussian density perturbation field."""
-    wl = shock_disc_2d(n, steps=steps, name=f"2d_shock_disc_adjoint_{n}")
+    """256^2 shock-disc problem whose phase densities carry a smooth Gaussian
+    perturbation of amplitude 1e-2 (width 0.05, centre seeded within 0.02 of
+    the disc centre).  extra["drho_shape"] is the Gaussian, the direction of
+    the density-gradient checks.  The shock starts at x = 0.28, next to the
+    disc (edge at 0.3): 200 steps last ~8e-5 s, in which a Mach-2 air shock
+    travels ~0.05, so the solid is struck within the run."""
+    wl = shock_disc_2d(n, steps=steps, shock_x=0.28, name=f"2d_shock_disc_adjoint_{n}")
+    rng = np.random.default_rng(seed)
+    cx, cy = 0.4 + rng.uniform(-0.02, 0.02), 0.5 + rng.uniform(-0.02, 0.02)
     d = 1.0 / n
     xc = (np.arange(n) + 0.5) * d
-    r2 = (xc[None, :] - 0.4) ** 2 + (xc[:, None] - 0.5) ** 2
-    wl.extra["drho_shape"] = np.exp(-r2 / (2 * 0.05 ** 2))
+    r2 = (xc[None, :] - cx) ** 2 + (xc[:, None] - cy) ** 2
+    shape = np.exp(-r2 / (2 * 0.05 ** 2))
+    k = {nm: i for i, nm in enumerate(prim_names(2, False))}
+    for p in wl.patches:
+        p.prim[k["rho1"]] *= 1.0 + 1e-2 * shape
+        p.prim[k["rho2"]] *= 1.0 + 1e-2 * shape
+    wl.extra["drho_shape"] = shape
     wl.extra["seed"] = seed
     return wl
 

@@ -2,16 +2,22 @@
 the oracle's own reverse mode (PyTorch autograd through the float64 CPU
 oracle) and against central finite differences.
 
+Inputs: the gradient of a limited scheme is only defined away from its kinks
+(minmod at a zero or tied slope, min / max of equal wave speeds, the yield
+surface).  The seeded workloads have exactly uniform regions, where every
+limiter sits on a kink and a one-ulp difference between two float64 programs
+flips the derivative (the oracle's own gradient moves by up to 85 % under
+one-ulp input perturbations there).  The parity cases therefore add a seeded
+cell-wise perturbation of relative size 1e-4 to every primitive field
+(workloads.perturbed), which puts every choice far from its kink.
+
 Parity metric (per field f of the initial-state gradient):
-    err_f = max |g_gpu - g_oracle| / max(max |g_oracle|, floor)
-with the floor 1e-300 (fields whose oracle gradient is exactly zero must be
-zero on the GPU).  Both sides differentiate the same discrete step with the
-time steps frozen; each uses its own CFL time steps, which agree to
-round-off.  Bar: 1e-8 for state and parameter gradients (round-off of two
-float64 programs propagated through the reverse sweep; THINC next to the
-stiff solid amplifies it, as in the forward parity tests, so that case uses
-1e-6).  Finite differences: 1e-4 relative (central, relative step 1e-6,
-smooth inputs, time steps held at the recorded values).
+    err_f = max |g_gpu - g_oracle| / max |g_oracle|
+Bar: max(1e-8, 10 x the oracle's own spread under one-ulp input
+perturbations), the same calibration as the forward THINC parity tests; the
+measured spreads are 1e-14 .. 2e-8.  Parameters: same rule.  Finite
+differences: 1e-4 relative (central, relative step 1e-6, time steps held at
+the recorded values).
 """
 import json
 import os
@@ -52,17 +58,18 @@ def gpu_grad(wl, steps, material, qbar=None, every=3, kind=1, dts=None):
     return J, unpack(g, [p.prim.shape for p in wl.patches]), gp, used
 
 
-def oracle_grad(wl, steps, material, qbar=None, kind="prim"):
+def oracle_grad(wl, steps, material, qbar=None, kind="prim", prim=None):
     from oracle import adjoint as OA
     from oracle import scheme as OS
     from oracle.closures import prim_to_cons
     p = wl.patches[0]
     theta = torch.tensor([m[k] for m in wl.materials for k in OA.PARAM_KEYS], dtype=torch.float64,
                          requires_grad=True)
+    w0 = p.prim if prim is None else prim
     if kind == "prim":
-        init = torch.tensor(p.prim, dtype=torch.float64, requires_grad=True)
+        init = torch.tensor(w0, dtype=torch.float64, requires_grad=True)
     else:
-        q0 = prim_to_cons(OS.prim_from_array(p.prim, wl.dim, wl.reactive), wl.materials)
+        q0 = prim_to_cons(OS.prim_from_array(w0, wl.dim, wl.reactive), wl.materials)
         init = OS.cons_to_array(q0, wl.dim, wl.reactive).detach().clone().requires_grad_(True)
     J, _, dts = OA.rollout(init, kind, wl.dim, OA.with_params(wl.materials, theta), p,
                            dict(cfl=wl.cfl, thinc=wl.thinc), steps, material,
@@ -84,7 +91,7 @@ def param_err(gp, op, mask):
     return [float(abs(gp[k] - op[k]) / max(abs(op[k]), 1e-300)) for k in mask]
 
 
-def _case(name, wl, steps, material, qbar_seed=None, tol=1e-8, params=(0, 1), kind="prim"):
+def _case(name, wl, steps, material, qbar_seed=None, params=(0, 1), kind="prim"):
     qbar = None
     if qbar_seed is not None:
         rng = np.random.default_rng(qbar_seed)
@@ -94,63 +101,77 @@ def _case(name, wl, steps, material, qbar_seed=None, tol=1e-8, params=(0, 1), ki
                 for p in wl.patches]
     Jg, gg, gpg, gdt = gpu_grad(wl, steps, material, qbar, kind=1 if kind == "prim" else 0)
     Jo, go, gpo, odt = oracle_grad(wl, steps, material, qbar, kind)
+    # the oracle's own one-ulp spread calibrates the bar
+    rng = np.random.default_rng(123)
+    p0 = wl.patches[0].prim
+    pu = p0 * (1 + np.sign(rng.standard_normal(p0.shape)) * 2.0 ** -52)
+    _, gu, gpu_, _ = oracle_grad(wl, steps, material, qbar, kind, prim=pu)
+    spread = field_err(gu, go)
+    pspread = param_err(gpu_, gpo, params)
     e = field_err(gg[0], go)
     ep = param_err(gpg, gpo, params)
-    _record[name] = dict(J_gpu=Jg, J_oracle=Jo, field_err=e, param_err=ep,
-                         params_gpu=[float(gpg[k]) for k in params],
+    bar = [max(1e-8, 10 * x) for x in spread]
+    pbar = [max(1e-8, 10 * x) for x in pspread]
+    _record[name] = dict(J_gpu=Jg, J_oracle=Jo, field_err=e, field_spread=spread, param_err=ep,
+                         param_spread=pspread, params_gpu=[float(gpg[k]) for k in params],
                          params_oracle=[float(gpo[k]) for k in params],
                          dt_rel=float(np.max(np.abs(np.asarray(gdt)[:, 0] - np.asarray(odt)) / np.asarray(odt))))
     _save()
     assert abs(Jg - Jo) <= 1e-10 * abs(Jo) + 1e-300, (Jg, Jo)
-    assert max(e) <= tol, e
-    assert max(ep) <= tol, (ep, gpg, gpo)
+    assert all(x <= b for x, b in zip(e, bar)), (e, bar)
+    assert all(x <= b for x, b in zip(ep, pbar)), (ep, pbar, gpg, gpo)
 
 
 def test_adjoint_1d_solid_gas_vs_oracle():
-    wl = W.solid_gas_1d(n=100, steps=12)
+    wl = W.perturbed(W.solid_gas_1d(n=100, steps=12))
     _case("1d_solid_gas_100_12", wl, 12, material=0, qbar_seed=1)
 
 
 def test_adjoint_1d_conservative_vs_oracle():
-    wl = W.solid_gas_1d(n=100, steps=6)
+    wl = W.perturbed(W.solid_gas_1d(n=100, steps=6), seed=12)
     _case("1d_solid_gas_100_6_cons", wl, 6, material=0, qbar_seed=2, kind="cons")
 
 
 def test_adjoint_2d_shock_disc_vs_oracle():
-    wl = W.shock_disc_2d(n=20, steps=4, thinc=False, shock_x=0.3)
+    wl = W.perturbed(W.shock_disc_2d(n=20, steps=4, thinc=False, shock_x=0.3))
     _case("2d_shock_disc_20_4", wl, 4, material=0, qbar_seed=3)
 
 
 def test_adjoint_2d_thinc_vs_oracle():
-    wl = W.shock_disc_2d(n=20, steps=4, thinc=True, shock_x=0.3)
-    _case("2d_shock_disc_thinc_20_4", wl, 4, material=0, qbar_seed=4, tol=1e-6)
+    wl = W.perturbed(W.shock_disc_2d(n=20, steps=4, thinc=True, shock_x=0.3))
+    _case("2d_shock_disc_thinc_20_4", wl, 4, material=0, qbar_seed=4)
 
 
 def test_adjoint_reactive_vs_oracle():
-    # fast reaction (A = 1e9 /s) so that the heat release matters within 3 steps
-    wl = W.reactive_plate_2d(nx=24, ny=12, steps=3, A=1e9)
-    _case("2d_reactive_plate_24x12_3", wl, 3, material=1, qbar_seed=5, params=(0, 1, 5))
+    # 96 x 48 resolves the hot spot (radius 0.02) so the reaction progresses
+    # within 3 steps; the heat release gradient (entry 5) is then not small
+    wl = W.perturbed(W.reactive_plate_2d(nx=96, ny=48, steps=3))
+    _case("2d_reactive_plate_96x48_3", wl, 3, material=1, qbar_seed=5, params=(0, 1, 5))
 
 
 def test_adjoint_smooth_vs_oracle():
-    wl = W.smooth_disc_2d(n=16, steps=8, sigma_y=4e7)
+    wl = W.perturbed(W.smooth_disc_2d(n=16, steps=8, sigma_y=4e7))
     _case("2d_smooth_disc_16_8", wl, 8, material=0)
 
 
-def _fd_check(name, wl, steps, material, direction, params, every=4, rel=1e-6, tol=1e-4):
-    """Central differences of the GPU objective with the recorded dts held."""
+def _fd_check(name, wl, steps, material, direction, params, every=4, rel=1e-6, tol=1e-4, qbar=None):
+    """Central differences of the GPU objective J + <qbar, q_final> with the
+    recorded dts held."""
     from paper_2009_14555_gb300.solver import Solver, pack
     s = Solver.from_workload(wl)
     w0 = pack([p.prim for p in wl.patches])
+    qb = None if qbar is None else pack(qbar)
     s.set_state(w0)
     J0, dts = s.adj_forward(steps, every=every, material=material)
-    g, gp = s.adjoint(None, 1.0, kind=1)
+    g, gp = s.adjoint(qb, 1.0 if material >= 0 else 0.0, kind=1)
     theta0 = s.params()
 
     def J_at(w, th):
         s.set_params(th)
         s.set_state(w)
         J, _ = s.adj_forward(steps, every=every, material=material, dts=dts)
+        if qb is not None:
+            J += float(qb @ s.get_state())
         return J
 
     rec = {}
@@ -165,15 +186,17 @@ def _fd_check(name, wl, steps, material, direction, params, every=4, rel=1e-6, t
         e[k] = h
         fdk = (J_at(w0, theta0 + e) - J_at(w0, theta0 - e)) / (2 * h)
         rec[f"param{k}"] = dict(fd=fdk, adjoint=float(gp[k]), rel=abs(fdk - gp[k]) / abs(gp[k]))
+    rec["J"] = J_at(w0, theta0)
     s.close()
     _record[name] = rec
     _save()
     for key, r in rec.items():
-        assert r["rel"] <= tol, (key, r)
+        if key != "J":
+            assert r["rel"] <= tol, (key, r)
 
 
 def test_adjoint_fd_smooth():
-    wl = W.smooth_disc_2d(n=32, steps=20, sigma_y=4e7)
+    wl = W.perturbed(W.smooth_disc_2d(n=32, steps=20, sigma_y=4e7))
     p = wl.patches[0]
     rng = np.random.default_rng(7)
     k = {n: i for i, n in enumerate(W.prim_names(2, False))}
@@ -189,16 +212,21 @@ def test_adjoint_fd_smooth():
 
 
 def test_adjoint_fd_reactive():
-    wl = W.reactive_plate_2d(nx=32, ny=16, steps=6, A=1e9)
+    """Heat release and the gas density against central differences; the
+    objective is the final reaction-progress density sum(phi_y rho_y lam)
+    (Q raises the recovered pressure, hence the temperature and the rate)."""
+    wl = W.perturbed(W.reactive_plate_2d(nx=96, ny=48, steps=6))
     p = wl.patches[0]
     k = {n: i for i, n in enumerate(W.prim_names(2, True))}
     d = np.zeros_like(p.prim)
     d[k["rho2"]] = p.prim[k["rho2"]]
-    _fd_check("fd_reactive_plate_32x16_6", wl, 6, 1, [d], params=(5,))
+    qbar = np.zeros_like(p.prim)
+    qbar[k["lam"]] = 1.0  # slot of phi_y rho_y lam in the conservative layout
+    _fd_check("fd_reactive_plate_96x48_6", wl, 6, -1, [d], params=(5,), qbar=[qbar])
 
 
 def test_adjoint_checkpoint_interval_invariance():
-    wl = W.smooth_disc_2d(n=16, steps=9, sigma_y=4e7)
+    wl = W.perturbed(W.smooth_disc_2d(n=16, steps=9, sigma_y=4e7))
     from paper_2009_14555_gb300.solver import Solver
     res = []
     for every in (1, 4, 9):
@@ -216,10 +244,13 @@ def test_adjoint_fullsize_shock_disc():
     """The 256^2 shock-disc adjoint case: 200 steps, checkpoint every 20,
     gradient of the solid's time-integrated x momentum with respect to the
     initial density field, checked along the seeded Gaussian perturbation by
-    central differences; forward and reverse times are recorded."""
+    central differences (relative steps 1e-4, 1e-5, 1e-6; bar 1e-4 on each);
+    forward and reverse times are recorded.  The input carries the 1e-4
+    cell-wise perturbation that removes exact ties (uniform regions put every
+    limiter on a kink, where finite differences and the adjoint disagree)."""
     import time
     from paper_2009_14555_gb300.solver import Solver, pack
-    wl = W.adjoint_case_2d(256, steps=200)
+    wl = W.perturbed(W.adjoint_case_2d(256, steps=200))
     p = wl.patches[0]
     k = {n: i for i, n in enumerate(W.prim_names(2, False))}
     d = np.zeros_like(p.prim)
@@ -237,8 +268,9 @@ def test_adjoint_fullsize_shock_disc():
     t2 = time.perf_counter()
     dd = pack([d])
     an = float(g @ dd)
-    rec = dict(J=J0, forward_s=t1 - t0, reverse_s=t2 - t1, dG=float(gp[0]), dsigma_y=float(gp[1]))
-    for eps in (1e-4, 1e-6):
+    rec = dict(J=J0, forward_s=t1 - t0, reverse_s=t2 - t1, dG=float(gp[0]), dsigma_y=float(gp[1]),
+               cells=p.nx * p.ny, steps=200)
+    for eps in (1e-4, 1e-5, 1e-6):
         def J_at(w):
             s.set_state(w)
             return s.adj_forward(200, every=20, material=0, dts=dts)[0]
@@ -247,7 +279,7 @@ def test_adjoint_fullsize_shock_disc():
     s.close()
     _record["fullsize_shock_disc_256_200"] = rec
     _save()
-    assert min(rec["fd_0.0001"]["rel"], rec["fd_1e-06"]["rel"]) <= 1e-4, rec
+    assert max(r["rel"] for key, r in rec.items() if key.startswith("fd_")) <= 1e-4, rec
 
 
 def test_autograd_function_matches_library_adjoint():
@@ -255,7 +287,7 @@ def test_autograd_function_matches_library_adjoint():
     combined objective J + <c, q_final>."""
     from paper_2009_14555_gb300.autograd import rollout
     from paper_2009_14555_gb300.solver import Solver, pack
-    wl = W.smooth_disc_2d(n=16, steps=6, sigma_y=4e7)
+    wl = W.perturbed(W.smooth_disc_2d(n=16, steps=6, sigma_y=4e7))
     s = Solver.from_workload(wl)
     w0 = torch.tensor(pack([p.prim for p in wl.patches]), device=s.device, requires_grad=True)
     theta = torch.tensor(s.params(), dtype=torch.float64, requires_grad=True)
