@@ -69,6 +69,24 @@ def workload(nx=None, ny=None):
     return W.reactive_plate_2d(nx or NX, ny or NY)
 
 
+def max_over_ranks(x, device=None):
+    """Largest value of x over the ranks of the process group (x itself
+    without one): the job's time is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(cells_per_rank, world, ms_per_step):
+    """Whole-job cell-updates/s: every rank advances its own replica of the
+    workload (replicas only: the step has no collective)."""
+    return cells_per_rank * world / (ms_per_step * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -173,11 +191,7 @@ def run_gpu(args):
             wall = time.perf_counter() - t0
         if world > 1:
             dist.barrier()
-        tot_ms = float(ev0.elapsed_time(ev1))
-        if world > 1:
-            t = torch.tensor([tot_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot_ms = float(t.item())
+        tot_ms = max_over_ranks(ev0.elapsed_time(ev1), dev)
         rc, _, _ = s.check()
         final = s.get_state(kind=0)  # state after warm-up + timed steps, for the L1 comparison
         kernel_ms = s.step_timed(2)  # per-launch device time, outside the timed region
@@ -199,13 +213,13 @@ def run_gpu(args):
         s.step(1)
         L.dis_get_state(s.ctx, 0, hout.data_ptr(), False)
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dev)
     nbytes = prim.nbytes
 
     r = results["fp32_bulk"]
     r64 = results["fp64"]
-    value = cells * world / (r["ms_per_step"] * 1e-3)
-    value64 = cells * world / (r64["ms_per_step"] * 1e-3)
+    value = job_throughput(cells, world, r["ms_per_step"])
+    value64 = job_throughput(cells, world, r64["ms_per_step"])
     hbm, kind = peaks()
     nxw, nyw = args.nx or NX, args.ny or NY
     faces_x = (nxw + 1) * nyw
@@ -264,7 +278,7 @@ def run_gpu(args):
                  "kernels_ms_per_launch": dict(zip(["prim", "flux_x", "flux_y", "update"],
                                                    map(float, r64["kernel_ms"]))),
                  "clocks": r64["clocks"]},
-        "e2e": {"value": cells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+        "e2e": {"value": job_throughput(cells, world, e2e_s * 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
@@ -272,6 +286,8 @@ def run_gpu(args):
     }
     if not args.no_batch:
         line["batch_1d"] = batch_bench()
+    if not args.no_adjoint:
+        line["adjoint"] = adjoint_bench()
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank == 0:
@@ -280,6 +296,38 @@ def run_gpu(args):
         v["solver"].close()
     if world > 1:
         dist.destroy_process_group()
+
+
+def adjoint_bench(n=256, steps=200, every=20):
+    """The adjoint case (256^2 shock-disc, 200 steps, checkpoint every 20):
+    time of the recorded forward run and of the checkpointed reverse sweep
+    (gradients with respect to the initial primitive state and the six
+    material parameters), float64."""
+    import torch
+    from paper_2009_14555_gb300 import workloads as W
+    from paper_2009_14555_gb300.solver import Solver, pack
+    wl = W.adjoint_case_2d(n, steps=steps)
+    s = Solver.from_workload(wl)
+    prim = pack([p.prim for p in wl.patches])
+    s.set_state(prim)
+    s.adj_forward(2, every=2, material=0)  # warm-up (allocation, first launches)
+    s.adjoint(None, 1.0, kind=1)
+    s.set_state(prim)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, _ = s.adj_forward(steps, every=every, material=0)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    g, gp = s.adjoint(None, 1.0, kind=1)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    ok = s.check()[0] == 0 and bool(np.isfinite(g).all())
+    s.close()
+    cells = wl.cells
+    return {"workload": f"2d_shock_disc_adjoint_{n} ({steps} steps, checkpoint every {every})",
+            "forward_s": t1 - t0, "reverse_s": t2 - t1,
+            "reverse_cell_updates_per_s": cells * steps / (t2 - t1),
+            "reverse_over_forward": (t2 - t1) / (t1 - t0), "J": J, "status_ok": ok}
 
 
 def batch_bench(steps=10, warmup=3):
@@ -367,6 +415,7 @@ def main():
     ap.add_argument("--impl", default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 1D measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-case measurement")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--nx", type=int, default=None, help="profiling only: smaller grid")
     ap.add_argument("--ny", type=int, default=None, help="profiling only: smaller grid")
