@@ -204,14 +204,19 @@ def run_gpu(args):
     s = results["fp32_bulk"]["solver"]
     hin = torch.from_numpy(prim).pin_memory()
     hout = torch.empty(s.state_numel, dtype=torch.float64).pin_memory()
-    e2e_steps = max(1, min(args.steps, 5))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        from paper_2009_14555_gb300 import _lib as L
+    from paper_2009_14555_gb300 import _lib as L
+
+    def e2e_step():
         L.dis_set_state(s.ctx, 1, hin.data_ptr(), False)
         s.step(1)
         L.dis_get_state(s.ctx, 0, hout.data_ptr(), False)
+
+    e2e_step()  # warm-up
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
     torch.cuda.synchronize()
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dev)
     nbytes = prim.nbytes
@@ -300,34 +305,36 @@ def run_gpu(args):
 
 def adjoint_bench(n=256, steps=200, every=20):
     """The adjoint case (256^2 shock-disc, 200 steps, checkpoint every 20):
-    time of the recorded forward run and of the checkpointed reverse sweep
-    (gradients with respect to the initial primitive state and the six
-    material parameters), float64."""
+    time of the recorded forward run (float64, and FP32-bulk with float64
+    checkpoints) and of the checkpointed float64 reverse sweep (gradients with
+    respect to the initial primitive state and the six material parameters)."""
     import torch
     from paper_2009_14555_gb300 import workloads as W
     from paper_2009_14555_gb300.solver import Solver, pack
     wl = W.adjoint_case_2d(n, steps=steps)
-    s = Solver.from_workload(wl)
     prim = pack([p.prim for p in wl.patches])
-    s.set_state(prim)
-    s.adj_forward(2, every=2, material=0)  # warm-up (allocation, first launches)
-    s.adjoint(None, 1.0, kind=1)
-    s.set_state(prim)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    J, _ = s.adj_forward(steps, every=every, material=0)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    g, gp = s.adjoint(None, 1.0, kind=1)
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
-    ok = s.check()[0] == 0 and bool(np.isfinite(g).all())
-    s.close()
     cells = wl.cells
-    return {"workload": f"2d_shock_disc_adjoint_{n} ({steps} steps, checkpoint every {every})",
-            "forward_s": t1 - t0, "reverse_s": t2 - t1,
-            "reverse_cell_updates_per_s": cells * steps / (t2 - t1),
-            "reverse_over_forward": (t2 - t1) / (t1 - t0), "J": J, "status_ok": ok}
+    out = {"workload": f"2d_shock_disc_adjoint_{n} ({steps} steps, checkpoint every {every})"}
+    for prec in ("fp64", "fp32_bulk"):
+        s = Solver.from_workload(wl, precision=prec)
+        s.set_state(prim)
+        s.adj_forward(2, every=2, material=0)  # warm-up (allocation, tuning, first launches)
+        s.adjoint(None, 1.0, kind=1)
+        s.set_state(prim)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        J, _ = s.adj_forward(steps, every=every, material=0)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        g, gp = s.adjoint(None, 1.0, kind=1)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        ok = s.check()[0] == 0 and bool(np.isfinite(g).all())
+        s.close()
+        out[prec] = {"forward_s": t1 - t0, "reverse_s": t2 - t1,
+                     "reverse_cell_updates_per_s": cells * steps / (t2 - t1),
+                     "reverse_over_forward": (t2 - t1) / (t1 - t0), "J": J, "status_ok": ok}
+    return out
 
 
 def batch_bench(steps=10, warmup=3):

@@ -182,8 +182,9 @@ int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
  * sigma_y, 2: heat release Q (zero unless l is the reactive material). */
 #define DIS_NPARAM 6
 
-/* Forward run recorded for dis_adjoint, from the current state (float64
- * contexts only).  Takes n_steps steps, with the CFL time step (dt_in NULL)
+/* Forward run recorded for dis_adjoint, from the current state.  Takes
+ * n_steps steps of the context's own step (float64 or FP32-bulk), with the
+ * CFL time step (dt_in NULL)
  * or with dt_in[n * n_patches + p] (host array), copies the state to a
  * library-owned checkpoint every checkpoint_every steps and records every
  * dt.  If objective_material is 0 or 1 it accumulates the running objective
@@ -193,8 +194,10 @@ int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
  * be NULL) receives the time steps.  Leaves the context at the final state,
  * like dis_step.  Device memory: (ceil(n_steps / checkpoint_every) +
  * checkpoint_every + 8) states, allocated here, kept for dis_adjoint and
- * released by dis_destroy.  Returns DIS_EINVAL (bad arguments, FP32-bulk
- * context), DIS_ESTATE (no state), DIS_ENOMEM, DIS_ECUDA.  Synchronises. */
+ * released by dis_destroy.  FP32-bulk contexts checkpoint their states in
+ * float64 (plus float64 primitive and face buffers for the reverse sweep).
+ * Returns DIS_EINVAL (bad arguments), DIS_ESTATE (no state), DIS_ENOMEM,
+ * DIS_ECUDA.  Synchronises. */
 int dis_adj_forward(dis_ctx* ctx, int n_steps, int checkpoint_every, int objective_material,
                     const double* dt_in, double* dt_out, double* J_out);
 
@@ -206,8 +209,10 @@ int dis_adj_forward(dis_ctx* ctx, int n_steps, int checkpoint_every, int objecti
  * out_kind; host or device per grad_on_device) and, if grad_params is not
  * NULL, the DIS_NPARAM parameter gradients selected by param_mask (bit k for
  * entry k; the others are set to 0).  Segments of checkpoint_every steps are
- * recomputed from their checkpoints (the state of the context is not
- * touched).  Returns DIS_ESTATE without a recorded run, DIS_EINVAL,
+ * recomputed from their checkpoints with the float64 step (the state of the
+ * context is not touched); for an FP32-bulk run the result is the float64
+ * adjoint along a trajectory restarted from the FP32-bulk states at every
+ * checkpoint.  Returns DIS_ESTATE without a recorded run, DIS_EINVAL,
  * DIS_ECUDA.  Synchronises. */
 int dis_adjoint(dis_ctx* ctx, const double* qbar_final, int qbar_on_device, double jbar, int out_kind,
                 double* grad_init, int grad_on_device, double* grad_params, unsigned param_mask);

@@ -19,6 +19,11 @@ LIB = os.path.join(HERE, "libdis.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]
+# dis_api.cu instantiates the FP32-bulk kernels: their float32 divisions and
+# square roots use the approximate (2 ulp) forms and float32 denormals flush
+# to zero.  Float64 arithmetic (the whole float64 path, the float64 parts of
+# FP32-bulk) is unaffected by these options.
+FILE_FLAGS = {"dis_api.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]}
 
 
 def nvcc() -> str:
@@ -40,7 +45,8 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmd = [nv, *ARCH, *FLAGS, *(extra or []), "-c", src, "-o", obj]
+        cmd = [nv, *ARCH, *FLAGS, *FILE_FLAGS.get(os.path.basename(src), []), *(extra or []), "-c", src,
+               "-o", obj]
         if verbose:
             print(" ".join(cmd), flush=True)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))

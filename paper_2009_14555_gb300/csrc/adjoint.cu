@@ -11,6 +11,11 @@
 // pre-source state are recomputed and the stages reversed (adjoint.cuh).
 // Memory: (number of checkpoints + K + 8) states plus the face coefficients,
 // all library-owned and released by dis_destroy.
+// FP32-bulk contexts: the forward run is the FP32-bulk step; its states are
+// checkpointed in float64 and the reverse sweep recomputes each segment with
+// the float64 step from those checkpoints (its own float64 primitive and face
+// buffers), so the gradient is the float64 adjoint along a trajectory that
+// restarts from the FP32-bulk states every K steps.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,6 +43,13 @@ struct dis_adj {
   double* dts = nullptr;  // n_steps x n_patches
   double* J = nullptr;
   double* theta = nullptr;
+  // float64 primitives and face outputs: the context's own (float64
+  // contexts) or allocated here (FP32-bulk contexts); tmp: float64 copy of an
+  // FP32-bulk state for the objective
+  double* W = nullptr;
+  double* Fx = nullptr;
+  double* Fy = nullptr;
+  double* tmp = nullptr;
 };
 
 #define ACU(call)                                                                              \
@@ -67,10 +79,13 @@ int adj_alloc(dis_ctx* c, int n_steps, int every) {
   const size_t S = sizeof(double) * (size_t)c->nf * c->T;
   const int n_ck = (n_steps + every - 1) / every;
   // states: checkpoints, the segment, q1 / q3 / pre-source, obar / xbar / qn_acc, Wbar
-  const size_t need = a256(S) * (size_t)(n_ck + (every + 1) + 7) +
-                      a256(sizeof(double) * (size_t)(c->nf + n_extra(c->dim)) * c->T) +
+  const size_t nfo = (size_t)(c->nf + n_extra(c->dim));
+  const size_t own = c->fp32 ? 2 * a256(S) + a256(sizeof(double) * nfo * c->NFX) +
+                                   a256(sizeof(double) * nfo * std::max<long long>(1, c->NFY))
+                             : 0;
+  const size_t need = a256(S) * (size_t)(n_ck + (every + 1) + 7) + a256(sizeof(double) * nfo * c->T) +
                       a256(sizeof(double) * (size_t)n_steps * c->np) + a256(sizeof(double)) +
-                      a256(sizeof(double) * NPARAM);
+                      a256(sizeof(double) * NPARAM) + own;
   if (need > d->mem_bytes) {
     if (d->mem) cudaFree(d->mem);
     d->mem = nullptr;
@@ -100,6 +115,17 @@ int adj_alloc(dis_ctx* c, int n_steps, int every) {
   d->dts = take(sizeof(double) * (size_t)n_steps * c->np);
   d->J = take(sizeof(double));
   d->theta = take(sizeof(double) * NPARAM);
+  if (c->fp32) {
+    d->W = take(S);
+    d->tmp = take(S);
+    d->Fx = take(sizeof(double) * nfo * c->NFX);
+    d->Fy = take(sizeof(double) * nfo * std::max<long long>(1, c->NFY));
+  } else {
+    d->W = c->W;
+    d->Fx = c->Fx;
+    d->Fy = c->Fy;
+    d->tmp = nullptr;
+  }
   if ((size_t)(b - d->mem) > d->mem_bytes)
     return dis_internal_error(DIS_EINVAL, "dis_adj_forward: internal layout exceeds its allocation");
   d->n_steps = n_steps;
@@ -115,9 +141,9 @@ StepArgs fwd_args(dis_ctx* c) {
   a.T = c->T;
   a.NFX = c->NFX;
   a.NFY = c->NFY;
-  a.W = c->W;
-  a.Fx = c->Fx;
-  a.Fy = c->Fy;
+  a.W = c->adj->W;
+  a.Fx = c->adj->Fx;
+  a.Fy = c->adj->Fy;
   a.rate = c->rate;
   a.dtlast = c->dtlast;
   a.status = c->status;
@@ -164,14 +190,31 @@ void fwd_step_fixed(dis_ctx* c, const double* src, double* dst, const double* dt
 template <int DIM, bool RX>
 int adj_forward(dis_ctx* c, int n_steps, int mat, bool prescribed) {
   dis_adj* d = c->adj;
-  const size_t S = sizeof(double) * (size_t)c->nf * c->T;
+  const size_t SD = (size_t)c->nf * c->T;  // doubles per state
   const unsigned nc = (unsigned)c->seg_cell.size();
   ACU(cudaMemsetAsync(d->J, 0, sizeof(double), c->stream));
   for (int n = 0; n < n_steps; ++n) {
-    if (n % d->every == 0)
-      ACU(cudaMemcpyAsync(d->ck + (size_t)(n / d->every) * (S / sizeof(double)), c->q[0], S,
-                          cudaMemcpyDeviceToDevice, c->stream));
+    double* ck = d->ck + (size_t)(n / d->every) * SD;
     double* dtn = d->dts + (size_t)n * c->np;
+    if (c->fp32) {
+      // FP32-bulk step; float64 checkpoints of its states
+      if (n % d->every == 0)
+        k_state32_to_64<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, c->q64[0], c->q32[0], ck, c->T);
+      if (prescribed)
+        ACU(cudaMemcpyAsync(c->dtfix, dtn, sizeof(double) * c->np, cudaMemcpyDeviceToDevice, c->stream));
+      const int rc = dis_internal_steps(c, 1, prescribed);
+      if (rc) return rc;
+      if (!prescribed)
+        ACU(cudaMemcpyAsync(dtn, c->dtlast, sizeof(double) * c->np, cudaMemcpyDeviceToDevice, c->stream));
+      if (mat >= 0) {
+        k_state32_to_64<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, c->q64[0], c->q32[0], d->tmp,
+                                                            c->T);
+        k_obj<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, d->tmp, c->T, dtn, mat, d->J);
+      }
+      continue;
+    }
+    if (n % d->every == 0)
+      ACU(cudaMemcpyAsync(ck, c->q[0], sizeof(double) * SD, cudaMemcpyDeviceToDevice, c->stream));
     if (prescribed) {
       fwd_step_fixed<DIM, RX>(c, c->q[0], c->q[0], dtn);
     } else {
@@ -198,9 +241,9 @@ void reverse_stage(dis_ctx* c, const double* x, const double* opre, double a_, d
   A.NFX = c->NFX;
   A.NFY = c->NFY;
   A.x = x;
-  A.W = c->W;
-  A.Fx = c->Fx;
-  A.Fy = c->Fy;
+  A.W = d->W;
+  A.Fx = d->Fx;
+  A.Fy = d->Fy;
   A.obar = d->ob;
   A.opre = opre;
   A.xbar = d->xb;
@@ -262,7 +305,7 @@ int adj_backward(dis_ctx* c, const double* qbar_packed, double jbar, int out_kin
     k_pack<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, d->ob, out_packed, c->T);
   } else {
     fwd_faces<DIM, RX>(c, d->ck, false);  // primitives of the initial state
-    k_adj_p2c<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->phys, c->d_pd, c->d_seg_cell, c->W, d->ob, out_packed,
+    k_adj_p2c<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->phys, c->d_pd, c->d_seg_cell, d->W, d->ob, out_packed,
                                                   c->T, d->theta, pmask);
   }
   ACU(cudaGetLastError());
@@ -276,7 +319,6 @@ extern "C" {
 int dis_adj_forward(dis_ctx* c, int n_steps, int checkpoint_every, int objective_material, const double* dt_in,
                     double* dt_out, double* J_out) {
   if (!c) return dis_internal_error(DIS_EINVAL, "dis_adj_forward: NULL context");
-  if (c->fp32) return dis_internal_error(DIS_EINVAL, "dis_adj_forward: the adjoint needs a float64 context");
   if (!c->have_state) return dis_internal_error(DIS_ESTATE, "dis_adj_forward: no state loaded");
   if (n_steps <= 0 || checkpoint_every <= 0)
     return dis_internal_error(DIS_EINVAL, "dis_adj_forward: n_steps and checkpoint_every must be positive");

@@ -59,7 +59,6 @@ struct dis_ctx {
   long long launches = 0;
   // one captured time step per dt mode (0: CFL, 1: prescribed), replayed per step
   cudaStream_t cap = nullptr;
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   long long graph_launches[2] = {0, 0};
   bool use_graphs = true;
@@ -70,5 +69,7 @@ struct dis_ctx {
 int dis_internal_error(int code, const char* fmt, ...);
 // Allocate (if the caller bound none) and fill the workspace tables.
 int dis_internal_ensure_ws(dis_ctx* c);
+// Enqueue n time steps (CFL dt, or the per-patch dt in c->dtfix when fixed).
+int dis_internal_steps(dis_ctx* c, int n, bool fixed);
 // Release the adjoint buffers of a context.
 void dis_internal_adj_free(dis_ctx* c);

@@ -224,6 +224,7 @@ int ensure_ws(dis_ctx* c) {
                        cudaMemcpyHostToDevice, c->stream));
   CU(cudaMemcpyAsync(c->d_seg_cell, c->seg_cell.data(), sizeof(int4) * c->seg_cell.size(),
                      cudaMemcpyHostToDevice, c->stream));
+
   for (int v = 0; v < 3; ++v)
     CU(cudaMemcpyAsync(c->d_tiles[v], c->tiles[v].data(), sizeof(int4) * c->tiles[v].size(),
                        cudaMemcpyHostToDevice, c->stream));
@@ -416,16 +417,17 @@ long long launch_step(dis_ctx* c, cudaStream_t st, bool fixed) {
     a.dtfix = fixed ? c->dtfix : nullptr;
     long long l = 0;
     const int v = c->variant < 0 ? 0 : c->variant;
+    const bool pre = variant_pre(v);
     if (!fixed) {
       cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, st);
-      if (!variant_pre(v)) {
+      if (!pre) {
         set_stage_args32<DIM, RX>(c, a, 0, false);
         k_cfl32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, st>>>(c->phys, c->physf, a, c->d_seg_cell);
         ++l;
       }
     }
     for (int stg = 0; stg < 3; ++stg) {
-      set_stage_args32<DIM, RX>(c, a, stg, variant_pre(v));
+      set_stage_args32<DIM, RX>(c, a, stg, pre);
       l += stage_fused_v<DIM, RX>(c, st, a, v, !fixed && stg == 0);
     }
     return l;
@@ -472,18 +474,19 @@ int timed_steps(dis_ctx* c, int n_steps, double* ms) {
   for (int k = 0; k < 5; ++k) CU(cudaEventCreate(&ev[k]));
   double acc[4] = {0, 0, 0, 0};
   if (c->fp32) {
-    // slot 0: CFL pass (in-kernel recovery: once per step, reported per stage)
-    // or primitive pre-pass (precomputed primitives: per stage); slot 1: stage kernel
+    // slot 0: CFL pass (in-kernel recovery, once per step) or the primitive
+    // pre-pass (precomputed primitives, per stage); slot 1: stage kernel
     if (c->variant < 0) {
       const int rc = autotune32<DIM, RX>(c);
       if (rc) return rc;
     }
     const int v = c->variant;
+    const bool pre = variant_pre(v);
     StepArgs32 a32 = base_args32(c);
     for (int s = 0; s < n_steps; ++s) {
       CU(cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, c->stream));
       float t = 0.f;
-      if (!variant_pre(v)) {
+      if (!pre) {
         set_stage_args32<DIM, RX>(c, a32, 0, false);
         CU(cudaEventRecord(ev[0], c->stream));
         k_cfl32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, c->physf, a32, c->d_seg_cell);
@@ -493,8 +496,8 @@ int timed_steps(dis_ctx* c, int n_steps, double* ms) {
         acc[0] += 3.0 * t;
       }
       for (int stg = 0; stg < 3; ++stg) {
-        set_stage_args32<DIM, RX>(c, a32, stg, variant_pre(v));
-        if (variant_pre(v)) {
+        set_stage_args32<DIM, RX>(c, a32, stg, pre);
+        if (pre) {
           CU(cudaEventRecord(ev[0], c->stream));
           prim_pass32<DIM, RX>(c, c->stream, a32, stg == 0);
           CU(cudaEventRecord(ev[1], c->stream));
@@ -548,6 +551,10 @@ int timed_steps(dis_ctx* c, int n_steps, double* ms) {
 template <int DIM, bool RX>
 int run_steps(dis_ctx* c, int n_steps, bool fixed) {
   const int mode = fixed ? 1 : 0;
+  if (c->fp32 && c->variant < 0) {
+    const int rc = autotune32<DIM, RX>(c);
+    if (rc) return rc;
+  }
   if (!c->use_graphs) {
     long long l = 0;
     for (int s = 0; s < n_steps; ++s) l += launch_step<DIM, RX>(c, c->stream, fixed);
@@ -557,12 +564,6 @@ int run_steps(dis_ctx* c, int n_steps, bool fixed) {
   }
   if (!c->cap) {
     CU(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
-    CU(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
-    CU(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
-  }
-  if (c->fp32 && c->variant < 0) {
-    const int rc = autotune32<DIM, RX>(c);
-    if (rc) return rc;
   }
   if (!c->graph[mode]) {
     cudaGraph_t g = nullptr;
@@ -575,12 +576,9 @@ int run_steps(dis_ctx* c, int n_steps, bool fixed) {
     if (e2 != cudaSuccess) return fail(DIS_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e2));
     c->graph_launches[mode] = l;
   }
-  // order the captured steps after prior work on the caller's stream and vice versa
-  CU(cudaEventRecord(c->ev_in, c->stream));
-  CU(cudaStreamWaitEvent(c->cap, c->ev_in, 0));
-  for (int s = 0; s < n_steps; ++s) CU(cudaGraphLaunch(c->graph[mode], c->cap));
-  CU(cudaEventRecord(c->ev_out, c->cap));
-  CU(cudaStreamWaitEvent(c->stream, c->ev_out, 0));
+  // captured on the private stream, replayed on the caller's stream (no
+  // cross-stream waits between steps)
+  for (int s = 0; s < n_steps; ++s) CU(cudaGraphLaunch(c->graph[mode], c->stream));
   c->launches = c->graph_launches[mode] * n_steps;
   return DIS_OK;
 }
@@ -661,6 +659,8 @@ MatDev to_dev(const dis_material& m) {
 
 int dis_internal_ensure_ws(dis_ctx* c) { return ensure_ws(c); }
 
+int dis_internal_steps(dis_ctx* c, int n, bool fixed) { return dispatch_steps(c, n, fixed); }
+
 extern "C" {
 
 const char* dis_last_error(void) { return g_err.c_str(); }
@@ -723,7 +723,7 @@ int dis_set_materials(dis_ctx* c, const dis_material* m, int n) {
   c->physf = to_float(c->phys);
   c->have_mats = true;
   // captured steps hold the closure parameters by value: capture again
-  if (c->cap && (c->graph[0] || c->graph[1])) cudaStreamSynchronize(c->cap);
+  if (c->graph[0] || c->graph[1]) cudaStreamSynchronize(c->stream);  // replays may be in flight
   for (int g = 0; g < 2; ++g)
     if (c->graph[g]) {
       cudaGraphExecDestroy(c->graph[g]);
@@ -747,6 +747,7 @@ int dis_bind_workspace(dis_ctx* c, void* dev, size_t bytes) {
   if (((uintptr_t)dev) & 255) return fail(DIS_EINVAL, "dis_bind_workspace: pointer not 256-byte aligned");
   const size_t need = carve(c, nullptr);
   if (bytes < need) return fail(DIS_ENOMEM, "dis_bind_workspace: %zu bytes given, %zu needed", bytes, need);
+  if (c->graph[0] || c->graph[1] || c->ws_owned) cudaStreamSynchronize(c->stream);  // work may be in flight
   if (c->ws_owned) cudaFree(c->ws);
   for (int m = 0; m < 2; ++m)
     if (c->graph[m]) {
@@ -861,7 +862,7 @@ int dis_set_variant(dis_ctx* c, int variant) {
   if (!c->fp32) return fail(DIS_EINVAL, "dis_set_variant: only FP32-bulk contexts have variants");
   if (variant < -1 || variant >= n_variants(c))
     return fail(DIS_EINVAL, "dis_set_variant: variant %d outside -1..%d", variant, n_variants(c) - 1);
-  if (c->cap && (c->graph[0] || c->graph[1])) cudaStreamSynchronize(c->cap);
+  if (c->graph[0] || c->graph[1]) cudaStreamSynchronize(c->stream);  // replays may be in flight
   for (int g = 0; g < 2; ++g)
     if (c->graph[g]) {
       cudaGraphExecDestroy(c->graph[g]);
@@ -882,11 +883,9 @@ int dis_step_timed(dis_ctx* c, int n_steps, double* kernel_ms) {
 
 void dis_destroy(dis_ctx* c) {
   if (!c) return;
-  if (c->cap) cudaStreamSynchronize(c->cap);
+  cudaStreamSynchronize(c->stream);  // replays of the step graphs run on the caller's stream
   for (int m = 0; m < 2; ++m)
     if (c->graph[m]) cudaGraphExecDestroy(c->graph[m]);
-  if (c->ev_in) cudaEventDestroy(c->ev_in);
-  if (c->ev_out) cudaEventDestroy(c->ev_out);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->ws_owned && c->ws) cudaFree(c->ws);
   dis_internal_adj_free(c);

@@ -218,9 +218,18 @@ __global__ void __launch_bounds__(NT, MINB) k_stage32(Phys P, PhysF F, StepArgs3
       face32<DIM, RX, 1>(F, Wsm, HX, HY, fx + NG, fy + NG - 1, dyf, dxf, Fys, NFY, g);
     }
   }
-  // the step's dt, once per CTA
-  __shared__ double dt_sh;
-  if (tid == 0) dt_sh = A.dtfix ? A.dtfix[t.x] : P.cfl / __longlong_as_double((long long)A.rate[t.x]);
+  // per-CTA constants of the update: the step's dt and the inverse cell
+  // sizes, in float64 and float32 (no per-thread conversions)
+  __shared__ double dt_sh, ihx_sh, ihy_sh;
+  __shared__ float dtf_sh, af_sh, bf_sh;
+  if (tid == 0) {
+    dt_sh = A.dtfix ? A.dtfix[t.x] : P.cfl / __longlong_as_double((long long)A.rate[t.x]);
+    dtf_sh = (float)dt_sh;
+    ihx_sh = (double)(1.f / dxf);
+    ihy_sh = (double)(1.f / dyf);
+    af_sh = (float)A.a;
+    bf_sh = (float)A.b;
+  }
   __syncthreads();
 
   // 4. update of the tile's cells
@@ -243,18 +252,17 @@ __global__ void __launch_bounds__(NT, MINB) k_stage32(Phys P, PhysF F, StepArgs3
   float divu = (FX(S::UF, fr) - FX(S::UF, fl)) * idx_;
   float bx = (FX(S::VA, fr) - FX(S::VA, fl)) * idx_;
   float by = 0.f;
-  // Float64 terms.  Per direction: the float phi1 flux difference dF (shared
-  // with the energy's kappa part, so rho E - kappa(phi1) cancels exactly) and
-  // the small terms (soft energy flux, kappa_2 (u + D), (kappa_1 - kappa_2) phi_K D)
-  // summed in float32.
+  // Float64 terms: the conservative part of the phi1 divergence, Dc, from the
+  // float phi1 flux differences, and the energy divergence as
+  // (kappa_1 - kappa_2) Dc plus the small terms (soft energy flux,
+  // kappa_2 (u + D), (kappa_1 - kappa_2) phi_K D) summed in float32 - the same
+  // Dc that moves phi1 moves the kappa part of rho E.
   const float k2f = (float)A.kap2, dkf = (float)A.dkap;
   const double dFx = (double)(FX(L::PHI, fr) - FX(L::PHI, fl));
-  const float smx = (FX(L::E, fr) - FX(L::E, fl)) +
-                    k2f * ((FX(S::UF, fr) + FX(S::DD, fr)) - (FX(S::UF, fl) + FX(S::DD, fl))) +
-                    dkf * (FX(S::PK, fr) * FX(S::DD, fr) - FX(S::PK, fl) * FX(S::DD, fl));
-  const double idxd = (double)idx_;
-  double Dphi = dFx * idxd;
-  double DE = fma(A.dkap, dFx, (double)smx) * idxd;
+  float small = ((FX(L::E, fr) - FX(L::E, fl)) +
+                 k2f * ((FX(S::UF, fr) + FX(S::DD, fr)) - (FX(S::UF, fl) + FX(S::DD, fl))) +
+                 dkf * (FX(S::PK, fr) * FX(S::DD, fr) - FX(S::PK, fl) * FX(S::DD, fl))) * idx_;
+  double Dc = dFx * ihx_sh;
   if constexpr (DIM == 2) {
     const float idy = 1.f / dyf;
     const int fb = ly * TX + lx, ft = fb + TX;
@@ -265,19 +273,18 @@ __global__ void __launch_bounds__(NT, MINB) k_stage32(Phys P, PhysF F, StepArgs3
     bx += (FY(S::VA, ft) - FY(S::VA, fb)) * idy;
     by = (FX(S::VB, fr) - FX(S::VB, fl)) * idx_ + (FY(S::VB, ft) - FY(S::VB, fb)) * idy;
     const double dFy = (double)(FY(L::PHI, ft) - FY(L::PHI, fb));
-    const float smy = (FY(L::E, ft) - FY(L::E, fb)) +
-                      k2f * ((FY(S::UF, ft) + FY(S::DD, ft)) - (FY(S::UF, fb) + FY(S::DD, fb))) +
-                      dkf * (FY(S::PK, ft) * FY(S::DD, ft) - FY(S::PK, fb) * FY(S::DD, fb));
-    const double idyd = (double)idy;
-    Dphi = fma(dFy, idyd, Dphi);
-    DE = fma(fma(A.dkap, dFy, (double)smy), idyd, DE);
+    small += ((FY(L::E, ft) - FY(L::E, fb)) +
+              k2f * ((FY(S::UF, ft) + FY(S::DD, ft)) - (FY(S::UF, fb) + FY(S::DD, fb))) +
+              dkf * (FY(S::PK, ft) * FY(S::DD, ft) - FY(S::PK, fb) * FY(S::DD, fb))) * idy;
+    Dc = fma(dFy, ihy_sh, Dc);
   }
+  const double DE = fma(A.dkap, Dc, (double)small);
+  const double Dphi = fma(-phi_d, (double)divu, Dc);
   const float rho = q[L::A1] + q[L::A2];
   const float uc = q[L::MX] / rho;
   float vc = 0.f;
   if constexpr (DIM == 2) vc = q[L::MY] / rho;
   const float t23 = 2.f / 3.f;
-  Dphi -= phi_d * (double)divu;
   D[L::V11] -= t23 * q[L::V11] * divu - uc * bx;
   D[L::V22] -= t23 * q[L::V22] * divu - vc * by;
   D[L::V33] -= t23 * q[L::V33] * divu;
@@ -286,7 +293,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stage32(Phys P, PhysF F, StepArgs3
     D[L::V21] -= t23 * q[L::V21] * divu - vc * bx;
   }
   const double dt = dt_sh;
-  const float dtf = (float)dt;
+  const float dtf = dtf_sh;
   float o[NF];
   double ophi, oE;
   if (A.a == 0.0) {
@@ -295,7 +302,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stage32(Phys P, PhysF F, StepArgs3
     ophi = phi_d - dt * Dphi;
     oE = E_d - dt * DE;
   } else {
-    const float af = (float)A.a, bf = (float)A.b;
+    const float af = af_sh, bf = bf_sh;
 #pragma unroll
     for (int c = 0; c < NF; ++c)
       o[c] = (c == L::PHI || c == L::E) ? 0.f : af * A.q32n[c * T + k] + bf * (q[c] - dtf * D[c]);
@@ -303,20 +310,21 @@ __global__ void __launch_bounds__(NT, MINB) k_stage32(Phys P, PhysF F, StepArgs3
     oE = A.a * A.q64n[T + k] + A.b * (E_d - dt * DE);
   }
   if (A.last) {
+    const float ophf = (float)ophi;
     float v12 = 0.f, v21 = 0.f;
     if constexpr (DIM == 2) { v12 = o[L::V12]; v21 = o[L::V21]; }
-    if (ophi > 1e-3 && ophi < 1.0 - 1e-3) {
+    if (ophf > 1e-3f && ophf < 1.f - 1e-3f) {
       double d11 = o[L::V11], d12 = v12, d21 = v21, d22 = o[L::V22], d33 = o[L::V33];
       plastic(P, ophi, dt, d11, d12, d21, d22, d33);
       o[L::V11] = (float)d11; v12 = (float)d12; v21 = (float)d21; o[L::V22] = (float)d22; o[L::V33] = (float)d33;
     } else {
-      plastic_f(F, (float)ophi, dtf, o[L::V11], v12, v21, o[L::V22], o[L::V33]);
+      plastic_f(F, ophf, dtf, o[L::V11], v12, v21, o[L::V22], o[L::V33]);
     }
     if constexpr (DIM == 2) { o[L::V12] = v12; o[L::V21] = v21; }
     if constexpr (RX) {
       const int y = P.y;
       const MatT<float>& m = F.m[y];
-      const float phi1 = (float)ophi;
+      const float phi1 = ophf;
       const float ary = y == 0 ? o[L::A1] : o[L::A2];
       const float phy = y == 0 ? phi1 : (float)(1.0 - ophi);
       const float rr = o[L::A1] + o[L::A2];
@@ -325,7 +333,7 @@ __global__ void __launch_bounds__(NT, MINB) k_stage32(Phys P, PhysF F, StepArgs3
       if constexpr (DIM == 2) my = o[L::MY];
       const float KE = 0.5f * (mx * mx + my * my) / rr;
       const StrainF s = strain_f(o[L::V11], v12, v21, o[L::V22], o[L::V33]);
-      const double kap = ophi * P.m[0].kap + (1.0 - ophi) * P.m[1].kap;
+      const double kap = fma(ophi, A.dkap, A.kap2);
       const double num = oE - kap - (double)KE - (double)soft_ref_f(F, phi1, o[L::A1], o[L::A2], 0.f, s.J2);
       const float xi = xi_f(F, phi1);
       const float p0 = (float)num / xi;
@@ -342,7 +350,9 @@ __global__ void __launch_bounds__(NT, MINB) k_stage32(Phys P, PhysF F, StepArgs3
       const float k4 = fr_(L0 + dtf * k3);
       o[L::AL] = L0 + dtf / 6.f * (k1 + 2.f * k2 + 2.f * k3 + k4);
     }
-    bool bad = !(ophi >= -1e-6 && ophi <= 1.0 + 1e-6) || !isfinite(oE);
+    // range and finiteness checks without float64 compares
+    const bool E_finite = ((__double_as_longlong(oE) >> 52) & 0x7ff) != 0x7ff;
+    bool bad = !(ophf >= -1e-6f && ophf <= 1.f + 1e-6f) || !E_finite;
 #pragma unroll
     for (int c = 0; c < NF; ++c) bad |= (c != L::PHI && c != L::E) && !isfinite(o[c]);
     if (bad) flag_bad(A.status, t.x, i + pd.nx * j);

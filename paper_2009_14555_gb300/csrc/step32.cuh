@@ -37,38 +37,39 @@ struct StepArgs32 {
   double kap2, dkap;  // kappa_2 and kappa_1 - kappa_2 (float64): energy flux kappa part
 };
 
+// Primitives of one cell from its FP32-bulk conservative state: phi1 and
+// rho E in float64, the other fields in v (float32, conservative slots; the
+// phi1 and rho E slots are not read).
 template <int DIM, bool RX>
-__device__ __forceinline__ PrimF cons_to_prim32(const Phys& P, const PhysF& F, const double* q64,
-                                                const float* q32, long long T, long long k) {
+__device__ __forceinline__ PrimF prim32_of(const Phys& P, const PhysF& F, double phi_d, double E,
+                                           const float* v) {
   using L = Lay<DIM, RX>;
   PrimF w;
-  const double phi_d = q64[k];
-  const double E = q64[T + k];
   const float phi = (float)phi_d;
-  const float a1 = q32[L::A1 * T + k], a2 = q32[L::A2 * T + k];
+  const float a1 = v[L::A1], a2 = v[L::A2];
   const float rho = a1 + a2;
-  const float mx = q32[L::MX * T + k];
+  const float mx = v[L::MX];
   float my = 0.f;
-  if constexpr (DIM == 2) my = q32[L::MY * T + k];
+  if constexpr (DIM == 2) my = v[L::MY];
   w.phi = phi;
   w.r1 = a1 / phi;
   w.r2 = a2 / (float)(1.0 - phi_d);
   const float irho = 1.f / rho;
   w.u = mx * irho;
   w.v = my * irho;
-  w.V11 = q32[L::V11 * T + k];
+  w.V11 = v[L::V11];
   w.V12 = 0.f;
   w.V21 = 0.f;
   if constexpr (DIM == 2) {
-    w.V12 = q32[L::V12 * T + k];
-    w.V21 = q32[L::V21 * T + k];
+    w.V12 = v[L::V12];
+    w.V21 = v[L::V21];
   }
-  w.V22 = q32[L::V22 * T + k];
-  w.V33 = q32[L::V33 * T + k];
+  w.V22 = v[L::V22];
+  w.V33 = v[L::V33];
   float arl = 0.f;
   w.lam = 0.f;
   if constexpr (RX) {
-    arl = q32[L::AL * T + k];
+    arl = v[L::AL];
     w.lam = arl / (P.y == 0 ? a1 : a2);
   }
   const StrainF s = strain_f(w.V11, w.V12, w.V21, w.V22, w.V33);
@@ -79,6 +80,16 @@ __device__ __forceinline__ PrimF cons_to_prim32(const Phys& P, const PhysF& F, c
   const double num = (E - kap) - (double)(KE + soft_ref_f(F, phi, a1, a2, arl, s.J2));
   w.p = (float)num / xi_f(F, phi);
   return w;
+}
+
+template <int DIM, bool RX>
+__device__ __forceinline__ PrimF cons_to_prim32(const Phys& P, const PhysF& F, const double* q64,
+                                                const float* q32, long long T, long long k) {
+  constexpr int NF = Lay<DIM, RX>::NF;
+  float v[NF];
+#pragma unroll
+  for (int c = 0; c < NF; ++c) v[c] = (c == Lay<DIM, RX>::PHI || c == Lay<DIM, RX>::E) ? 0.f : q32[c * T + k];
+  return prim32_of<DIM, RX>(P, F, q64[k], q64[T + k], v);
 }
 
 template <int DIM, bool RX>

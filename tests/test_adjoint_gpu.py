@@ -282,6 +282,36 @@ def test_adjoint_fullsize_shock_disc():
     assert max(r["rel"] for key, r in rec.items() if key.startswith("fd_")) <= 1e-4, rec
 
 
+def test_adjoint_of_fp32_bulk_run_matches_float64_adjoint():
+    """FP32-bulk forward run with float64 checkpoints and the float64 reverse
+    sweep, against the float64 run's adjoint: they differ by the float32
+    trajectory error.  Bars: objective 1e-5, parameter gradients 1e-4,
+    per-field relative L1 of the state gradient 5e-2 (the stretch-component
+    gradients depend on strains of 1e-6 that float32 V keeps to ~6 %; their
+    max-norm differences reach 8e-2, the others' 6e-3)."""
+    from paper_2009_14555_gb300.solver import Solver
+    wl = W.perturbed(W.smooth_disc_2d(n=32, steps=20, sigma_y=4e7))
+    res = {}
+    for prec in ("fp64", "fp32_bulk"):
+        s = Solver.from_workload(wl, precision=prec)
+        s.set_prim([p.prim for p in wl.patches])
+        J, _ = s.adj_forward(20, every=5, material=0)
+        g, gp = s.adjoint(None, 1.0, kind=1)
+        s.close()
+        res[prec] = (J, g.reshape(wl.patches[0].prim.shape), gp)
+    J64, g64, p64 = res["fp64"]
+    J32, g32, p32 = res["fp32_bulk"]
+    emax = field_err(g32, g64)
+    el1 = [float(np.abs(g32[f] - g64[f]).sum() / max(np.abs(g64[f]).sum(), 1e-300)) for f in range(g64.shape[0])]
+    ep = param_err(p32, p64, (0, 1))
+    _record["fp32_bulk_vs_fp64_adjoint_smooth_disc_32_20"] = dict(J64=J64, J32=J32, field_max_err=emax,
+                                                                  field_l1_err=el1, param_err=ep)
+    _save()
+    assert abs(J32 - J64) <= 1e-5 * abs(J64)
+    assert max(ep) <= 1e-4, ep
+    assert max(el1) <= 5e-2, el1
+
+
 def test_autograd_function_matches_library_adjoint():
     """torch.autograd through Rollout equals the direct dis_adjoint call for a
     combined objective J + <c, q_final>."""
