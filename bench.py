@@ -40,16 +40,16 @@ FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
 # FP32: 152 SMs x 128 FMA lanes x 2 FLOP x 2.07 GHz.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # FP32-bulk stage kernel k_stage32, per tuned variant (TX, TY, primitives
-# precomputed by k_prim32), counted by ncu (profiles/k_stage32_2d_reactive_plate.md):
-# executed FP32 FLOP (FADD + FMUL + 2 FFMA) and FP64 FLOP per cell-stage on the
-# 1024 x 512 reactive plate (halo recovery included where the kernel
-# recovers), and DRAM bytes (read + write) per cell of one launch on the full
-# 2048 x 1024 grid.
+# precomputed by k_prim32), counted by ncu over the three stages of one step
+# (profiles/k_stage32_2d_reactive_plate.md): executed FP32 FLOP (FADD + FMUL +
+# 2 FFMA) and FP64 FLOP per cell-stage on the 1024 x 512 reactive plate (halo
+# recovery included where the kernel recovers), and DRAM bytes (read + write)
+# per cell-stage on the full 2048 x 1024 grid.  The register budget (3 or 4
+# CTAs per SM) does not change these counts.
 STAGE32 = {
-    (16, 15, False): dict(flop32=1145.7e6 / 524288, flop64=14.07e6 / 524288,
-                          dram=(118531840 + 78248448) / 2097152),
-    (16, 15, True): dict(flop32=1007.4e6 / 524288, flop64=8.42e6 / 524288,
-                         dram=(220302080 + 90135296) / 2097152),
+    (16, 15, False): dict(flop32=1601.7, flop64=27.97, dram=135.7),
+    (16, 15, True): dict(flop32=1436.9, flop64=17.19, dram=186.3),
+    (32, 7, True): dict(flop32=1461.8, flop64=17.19, dram=185.9),
 }
 UNIT = "cell-updates/s"
 NX, NY = 2048, 1024

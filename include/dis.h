@@ -217,6 +217,12 @@ int dis_adj_forward(dis_ctx* ctx, int n_steps, int checkpoint_every, int objecti
 int dis_adjoint(dis_ctx* ctx, const double* qbar_final, int qbar_on_device, double jbar, int out_kind,
                 double* grad_init, int grad_on_device, double* grad_params, unsigned param_mask);
 
+/* Diagnostic: with on != 0, later dis_adjoint calls reverse the face Riemann
+ * problems with dual numbers (one forward evaluation per input direction, the
+ * reference form) instead of the hand-written reverse; both give the same
+ * gradient up to rounding.  Returns DIS_EINVAL for a NULL context. */
+int dis_adj_reference(dis_ctx* ctx, int on);
+
 /* Largest patch count accepted by dis_cfl_dt_static. */
 #define DIS_STATIC_MAX_PATCHES 16384
 

@@ -63,6 +63,7 @@ SIGNATURES = {
     "dis_adj_forward": (c_int, [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p, POINTER(c_double)]),
     "dis_adjoint": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p, c_int, c_void_p,
                             ctypes.c_uint]),
+    "dis_adj_reference": (c_int, [c_void_p, c_int]),
     "dis_last_error": (c_char_p, []),
     "dis_destroy": (None, [c_void_p]),
 }

@@ -30,6 +30,7 @@ using namespace dis;
 struct dis_adj {
   int n_steps = 0, every = 0, n_ck = 0, mat = -1;
   bool ready = false;
+  int dual_riemann = 0;  // reference form of the Riemann-problem reverse
   char* mem = nullptr;
   size_t mem_bytes = 0;
   double* ck = nullptr;   // n_ck checkpoints
@@ -257,6 +258,7 @@ void reverse_stage(dis_ctx* c, const double* x, const double* opre, double a_, d
   A.last = last;
   A.first = first;
   A.pmask = pmask;
+  A.dual_riemann = d->dual_riemann;
   k_adj_cell<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, A, c->d_seg_cell);
   cudaMemsetAsync(d->Wb, 0, sizeof(double) * (size_t)c->nf * c->T, c->stream);
   k_adj_face<DIM, RX, 0><<<(unsigned)c->seg_fx.size(), SEG, 0, c->stream>>>(c->phys, A, c->d_seg_fx);
@@ -383,6 +385,14 @@ int dis_adjoint(dis_ctx* c, const double* qbar_final, int qbar_on_device, double
   ACU(cudaStreamSynchronize(c->stream));
   if (grad_params)
     for (int k = 0; k < NPARAM; ++k) grad_params[k] = ((pmask >> k) & 1u) ? th[k] : 0.0;
+  return DIS_OK;
+}
+
+int dis_adj_reference(dis_ctx* c, int on) {
+  if (!c) return dis_internal_error(DIS_EINVAL, "dis_adj_reference: NULL context");
+  if (!c->adj) c->adj = new (std::nothrow) dis_adj();
+  if (!c->adj) return dis_internal_error(DIS_ENOMEM, "dis_adj_reference: out of host memory");
+  c->adj->dual_riemann = on ? 1 : 0;
   return DIS_OK;
 }
 

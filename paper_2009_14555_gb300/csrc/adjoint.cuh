@@ -18,9 +18,14 @@
 //   k_adj_prim  (per padded cell, ghosts included) Wbar -> xbar of the source
 //                            cell of the ghost map (sign flips of reflective
 //                            walls applied), again by atomics.
-// Local Jacobians are never formed: each input direction is one Dual-number
-// evaluation of the forward code (face.cuh), contracted with the adjoint.
+// Local Jacobians are never formed.  The Riemann problem of a face is reversed
+// by hand (riemann_vjp.cuh); every other local map is reversed one input
+// direction at a time by a Dual-number evaluation of the forward code
+// (face.cuh), contracted with the adjoint.  dual_riemann selects the Dual form
+// for the Riemann problem too (the reference the hand-written reverse is
+// tested against).
 #pragma once
+#include "riemann_vjp.cuh"
 #include "step_kernels.cuh"
 
 namespace dis {
@@ -117,7 +122,16 @@ struct AdjArgs {
   int last;
   int first;           // qnacc = a obar (else +=)
   unsigned pmask;      // parameters to differentiate
+  int dual_riemann;    // 1: Riemann part by dual numbers (reference), 0: hand-written reverse
 };
+
+// <a, b.d> over the fields of two face states.
+__device__ __forceinline__ double fstate_dot(const FState& a, const FStateT<Dual>& b) {
+  return a.phi * b.phi.d + a.ar1 * b.ar1.d + a.ar2 * b.ar2.d + a.arl * b.arl.d + a.rho * b.rho.d +
+         a.un * b.un.d + a.ut * b.ut.d + a.rhoE * b.rhoE.d + a.snn * b.snn.d + a.snt * b.snt.d +
+         a.cL * b.cL.d + a.Gm * b.Gm.d + a.V11 * b.V11.d + a.V12 * b.V12.d + a.V21 * b.V21.d +
+         a.V22 * b.V22.d + a.V33 * b.V33.d;
+}
 
 // ---------------------------------------------------------------------------
 // Per interior cell: source-step adjoint, RK combination, non-conservative
@@ -327,7 +341,28 @@ __global__ void __launch_bounds__(SEG) k_adj_face(Phys P, AdjArgs A, const int4*
 
     // Riemann solver: gradient with respect to the two chosen face states
     double gL[NF], gR[NF];
-    {
+    if (!A.dual_riemann) {
+      // hand-written reverse of the Riemann problem into the face states, then
+      // the face-state map (primitives -> face state) by dual numbers
+      FState Lb{}, Rb{};
+      riemann_outputs_vjp<DIM, RX, DIR>(face_state<DIR>(P, pl), face_state<DIR>(P, pr), Fb, Lb, Rb);
+      const PhysT<Dual> PD = lift_phys(P, -1);
+#pragma unroll 1
+      for (int s = 0; s < 2 * NF; ++s) {
+        PrimT<Dual> d = lift_prim(s < NF ? pl : pr);
+        prim_slot<DIM, RX>(d, s < NF ? s : s - NF).d = 1.0;
+        const double acc = fstate_dot(s < NF ? Lb : Rb, face_state<DIR>(PD, d));
+        if (s < NF) gL[s] = acc;
+        else gR[s - NF] = acc;
+      }
+#pragma unroll 1
+      for (int kk = 0; kk < NPARAM; ++kk) {
+        if (!((A.pmask >> kk) & 1u)) continue;
+        const PhysT<Dual> PK = lift_phys(P, kk);
+        th[kk] += fstate_dot(Lb, face_state<DIR>(PK, lift_prim(pl))) +
+                  fstate_dot(Rb, face_state<DIR>(PK, lift_prim(pr)));
+      }
+    } else {
       const PhysT<Dual> PD = lift_phys(P, -1);
 #pragma unroll 1
       for (int s = 0; s < 2 * NF; ++s) {

@@ -163,6 +163,11 @@ class Solver:
                               out.ctypes.data)
         return J, out
 
+    def adj_reference(self, on=True):
+        """Diagnostic: reverse the face Riemann problems with dual numbers
+        (include/dis.h: dis_adj_reference)."""
+        L.check(L.load().dis_adj_reference(self.ctx, int(bool(on))))
+
     def adjoint(self, qbar=None, jbar=0.0, kind=L.DIS_CONSERVATIVE, param_mask=(1 << L.DIS_NPARAM) - 1,
                 out=None):
         """Gradient of <qbar, q_final> + jbar J with respect to the initial state
