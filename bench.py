@@ -111,7 +111,7 @@ class ClockSampler:
                  "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                 "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.f,
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -169,6 +169,8 @@ def run_gpu(args):
     precisions = ["fp64", "fp32_bulk"]
     for prec in precisions:
         s = Solver.from_workload(wl, precision=prec)
+        if prec == "fp32_bulk" and args.variant is not None:
+            s.set_variant(args.variant)
         s.set_state(prim, kind=1)
         stream = s.stream
         for _ in range(args.warmup):
@@ -363,17 +365,19 @@ def batch_bench(steps=10, warmup=3):
         ok = s.check()[0] == 0
         out[prec] = {"value": wl.cells / (ms * 1e-3), "ms_per_step": ms, "status_ok": ok}
         if prec == "fp32_bulk":
-            out[prec]["tile"] = list(s.tile_choice()[:3])
+            t = s.tile_choice()
+            out[prec]["tile"] = list(t[:3])
+            out[prec]["tuned_ms_per_step"] = [round(float(x), 4) for x in t[3]]
         s.close()
     return out
 
 
-def cpu_baseline(budget_s=15.0, steps=None):
-    """The float64 CPU oracle on a bounded sample of the same workload."""
+def cpu_baseline(budget_s=15.0, steps=None, nx=256, ny=128):
+    """The float64 CPU oracle on a bounded sample of the same workload (the
+    reactive plate on an nx x ny grid)."""
     import torch
     from oracle import scheme as OS
     from oracle import closures as OC
-    nx, ny = 256, 128
     wl = workload(nx, ny)
     p = wl.patches[0]
     grid = OS.grid_of(p, 2)
@@ -396,10 +400,14 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    per = []
+    # each step samples a grid sized so that the whole run stays near 90 s
+    # (the oracle advances ~6e3 cells per second on 16 cores)
+    per_step_s = 90.0 / (max(1, args.steps) + args.warmup)
+    ny = int(max(8, min(128, np.sqrt(6.0e3 * per_step_s / 2.0))))
+    nx = 2 * ny
     for _ in range(args.warmup):
-        cpu_baseline(steps=1)
-    res = cpu_baseline(steps=max(1, args.steps))
+        cpu_baseline(steps=1, nx=nx, ny=ny)
+    res = cpu_baseline(steps=max(1, args.steps), nx=nx, ny=ny)
     line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": res["seconds"] / max(1, args.steps) * 1e3, "higher_is_better": True,
@@ -410,14 +418,13 @@ def run_reference(args):
                              "kind": "oracle", "sample": res["sample"]},
             "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
-    del per
     print(json.dumps(line), flush=True)
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -426,6 +433,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--nx", type=int, default=None, help="profiling only: smaller grid")
     ap.add_argument("--ny", type=int, default=None, help="profiling only: smaller grid")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="profiling only: fix the FP32-bulk stage variant instead of tuning")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

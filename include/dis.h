@@ -146,7 +146,8 @@ long long dis_last_launches(const dis_ctx* ctx);
  * the stage kernel ((v / 3) even) or copied from a pre-pass that recovers
  * every cell once and also takes the CFL rate ((v / 3) odd); register budget
  * for 3 (v < 6) or 4 resident CTAs per SM.  1D contexts have variants 0..2
- * (the three shapes, recovery in the kernel).  The first dis_step times
+ * and 6..8 (the three shapes, recovery in the kernel; no register limit, or
+ * at most 64 registers per thread for v >= 6).  The first dis_step times
  * stage 1 of every variant (on the stage buffer, leaving the state unchanged)
  * and keeps the one with the smallest time per step.  Returns the chosen
  * shape (0 x 0 before tuning or for float64 contexts), whether it uses the
@@ -155,7 +156,7 @@ long long dis_last_launches(const dis_ctx* ctx);
 #define DIS_NVARIANTS 12
 int dis_tile_choice(const dis_ctx* ctx, int* tx, int* ty, int* precomputed, double* step_ms);
 
-/* Fix the FP32-bulk stage variant (0 .. DIS_NVARIANTS - 1 in 2D, 0 .. 2 in 1D) or
+/* Fix the FP32-bulk stage variant (0 .. DIS_NVARIANTS - 1 in 2D, 0..2 and 6..8 in 1D) or
  * return to tuning on the next step (-1).  For tests and measurements; the
  * result of a step does not depend on the variant beyond float32 rounding
  * order.  DIS_EINVAL for float64 contexts or an out-of-range variant. */
@@ -218,9 +219,10 @@ int dis_adjoint(dis_ctx* ctx, const double* qbar_final, int qbar_on_device, doub
                 double* grad_init, int grad_on_device, double* grad_params, unsigned param_mask);
 
 /* Diagnostic: with on != 0, later dis_adjoint calls reverse the face Riemann
- * problems with dual numbers (one forward evaluation per input direction, the
- * reference form) instead of the hand-written reverse; both give the same
- * gradient up to rounding.  Returns DIS_EINVAL for a NULL context. */
+ * problems, the face-state map and the primitive recovery with dual numbers
+ * (one forward evaluation per input direction, the reference form) instead
+ * of the hand-written reverses; both give the same gradient up to rounding.
+ * Returns DIS_EINVAL for a NULL context. */
 int dis_adj_reference(dis_ctx* ctx, int on);
 
 /* Largest patch count accepted by dis_cfl_dt_static. */

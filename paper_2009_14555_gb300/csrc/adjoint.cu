@@ -30,7 +30,7 @@ using namespace dis;
 struct dis_adj {
   int n_steps = 0, every = 0, n_ck = 0, mat = -1;
   bool ready = false;
-  int dual_riemann = 0;  // reference form of the Riemann-problem reverse
+  int dual_riemann = 0;  // dual-number reference form of the hand-reversed local maps
   char* mem = nullptr;
   size_t mem_bytes = 0;
   double* ck = nullptr;   // n_ck checkpoints
@@ -232,6 +232,16 @@ int adj_forward(dis_ctx* c, int n_steps, int mat, bool prescribed) {
   return DIS_OK;
 }
 
+// Face and primitive reverse kernels of one stage (REF: dual-number reference
+// form of the hand-reversed local maps).
+template <int DIM, bool RX, bool REF>
+void reverse_faces(dis_ctx* c, const AdjArgs& A) {
+  k_adj_face<DIM, RX, 0, REF><<<(unsigned)c->seg_fx.size(), SEG, 0, c->stream>>>(c->phys, A, c->d_seg_fx);
+  if constexpr (DIM == 2)
+    k_adj_face<DIM, RX, 1, REF><<<(unsigned)c->seg_fy.size(), SEG, 0, c->stream>>>(c->phys, A, c->d_seg_fy);
+  k_adj_prim<DIM, RX, REF><<<(unsigned)c->seg_prim.size(), SEG, 0, c->stream>>>(c->phys, A, c->d_seg_prim);
+}
+
 template <int DIM, bool RX>
 void reverse_stage(dis_ctx* c, const double* x, const double* opre, double a_, double b_, int last, int first,
                    const double* dt, unsigned pmask) {
@@ -258,13 +268,10 @@ void reverse_stage(dis_ctx* c, const double* x, const double* opre, double a_, d
   A.last = last;
   A.first = first;
   A.pmask = pmask;
-  A.dual_riemann = d->dual_riemann;
   k_adj_cell<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, A, c->d_seg_cell);
   cudaMemsetAsync(d->Wb, 0, sizeof(double) * (size_t)c->nf * c->T, c->stream);
-  k_adj_face<DIM, RX, 0><<<(unsigned)c->seg_fx.size(), SEG, 0, c->stream>>>(c->phys, A, c->d_seg_fx);
-  if constexpr (DIM == 2)
-    k_adj_face<DIM, RX, 1><<<(unsigned)c->seg_fy.size(), SEG, 0, c->stream>>>(c->phys, A, c->d_seg_fy);
-  k_adj_prim<DIM, RX><<<(unsigned)c->seg_prim.size(), SEG, 0, c->stream>>>(c->phys, A, c->d_seg_prim);
+  if (d->dual_riemann) reverse_faces<DIM, RX, true>(c, A);
+  else reverse_faces<DIM, RX, false>(c, A);
 }
 
 template <int DIM, bool RX>

@@ -18,14 +18,15 @@
 //   k_adj_prim  (per padded cell, ghosts included) Wbar -> xbar of the source
 //                            cell of the ghost map (sign flips of reflective
 //                            walls applied), again by atomics.
-// Local Jacobians are never formed.  The Riemann problem of a face is reversed
-// by hand (riemann_vjp.cuh); every other local map is reversed one input
-// direction at a time by a Dual-number evaluation of the forward code
-// (face.cuh), contracted with the adjoint.  dual_riemann selects the Dual form
-// for the Riemann problem too (the reference the hand-written reverse is
-// tested against).
+// Local Jacobians are never formed.  The Riemann problem of a face, the map
+// from face primitives to face states, the THINC-BVD edge values of phi and
+// the recovery of primitives are reversed by hand (local_vjp.cuh); the source
+// steps are reversed one input direction at a time by a Dual-number
+// evaluation of the forward code (face.cuh), contracted with the adjoint.
+// REF = true instantiates the Dual form for the hand-reversed maps too (the
+// reference the hand-written reverses are tested against).
 #pragma once
-#include "riemann_vjp.cuh"
+#include "local_vjp.cuh"
 #include "step_kernels.cuh"
 
 namespace dis {
@@ -92,17 +93,6 @@ __device__ __forceinline__ void add_nz(double* p, double v) {
   if (v != 0.0) atomicAdd(p, v);
 }
 
-// d minmod(a, b) / da and / db on the branch the forward took; equal
-// magnitudes split the derivative (the min convention of dual.cuh).
-__device__ __forceinline__ void minmod_grad(double a, double b, double& da, double& db) {
-  da = db = 0.0;
-  if (a * b > 0.0) {
-    if (fabs(b) < fabs(a)) db = 1.0;
-    else if (fabs(a) < fabs(b)) da = 1.0;
-    else da = db = 0.5;
-  }
-}
-
 struct AdjArgs {
   const PatchDev* pd;
   long long T, NFX, NFY;
@@ -122,7 +112,6 @@ struct AdjArgs {
   int last;
   int first;           // qnacc = a obar (else +=)
   unsigned pmask;      // parameters to differentiate
-  int dual_riemann;    // 1: Riemann part by dual numbers (reference), 0: hand-written reverse
 };
 
 // <a, b.d> over the fields of two face states.
@@ -272,7 +261,7 @@ __global__ void __launch_bounds__(SEG) k_adj_cell(Phys P, AdjArgs A, const int4*
 // Per face: adjoint of the face outputs, then back through the Riemann solver,
 // the non-hyperbolic fallback and the reconstruction into Wbar.
 // ---------------------------------------------------------------------------
-template <int DIM, bool RX, int DIR>
+template <int DIM, bool RX, int DIR, bool REF>
 __global__ void __launch_bounds__(SEG) k_adj_face(Phys P, AdjArgs A, const int4* __restrict__ segs) {
   using L = Lay<DIM, RX>;
   constexpr int NF = L::NF;
@@ -341,27 +330,23 @@ __global__ void __launch_bounds__(SEG) k_adj_face(Phys P, AdjArgs A, const int4*
 
     // Riemann solver: gradient with respect to the two chosen face states
     double gL[NF], gR[NF];
-    if (!A.dual_riemann) {
+    if constexpr (!REF) {
       // hand-written reverse of the Riemann problem into the face states, then
-      // the face-state map (primitives -> face state) by dual numbers
+      // of the face-state map (primitives -> face state)
       FState Lb{}, Rb{};
       riemann_outputs_vjp<DIM, RX, DIR>(face_state<DIR>(P, pl), face_state<DIR>(P, pr), Fb, Lb, Rb);
-      const PhysT<Dual> PD = lift_phys(P, -1);
-#pragma unroll 1
-      for (int s = 0; s < 2 * NF; ++s) {
-        PrimT<Dual> d = lift_prim(s < NF ? pl : pr);
-        prim_slot<DIM, RX>(d, s < NF ? s : s - NF).d = 1.0;
-        const double acc = fstate_dot(s < NF ? Lb : Rb, face_state<DIR>(PD, d));
-        if (s < NF) gL[s] = acc;
-        else gR[s - NF] = acc;
+      Prim pbL{}, pbR{};
+      double thf[NPARAM] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      face_state_vjp<DIR>(P, pl, Lb, pbL, thf);
+      face_state_vjp<DIR>(P, pr, Rb, pbR, thf);
+#pragma unroll
+      for (int c = 0; c < NF; ++c) {
+        gL[c] = prim_slot<DIM, RX>(pbL, c);
+        gR[c] = prim_slot<DIM, RX>(pbR, c);
       }
-#pragma unroll 1
-      for (int kk = 0; kk < NPARAM; ++kk) {
-        if (!((A.pmask >> kk) & 1u)) continue;
-        const PhysT<Dual> PK = lift_phys(P, kk);
-        th[kk] += fstate_dot(Lb, face_state<DIR>(PK, lift_prim(pl))) +
-                  fstate_dot(Rb, face_state<DIR>(PK, lift_prim(pr)));
-      }
+#pragma unroll
+      for (int kk = 0; kk < NPARAM; ++kk)
+        if ((A.pmask >> kk) & 1u) th[kk] += thf[kk];
     } else {
       const PhysT<Dual> PD = lift_phys(P, -1);
 #pragma unroll 1
@@ -431,7 +416,21 @@ __global__ void __launch_bounds__(SEG) k_adj_face(Phys P, AdjArgs A, const int4*
     const double gpL = okL ? gL[L::PHI] : 0.0, gpR = okR ? gR[L::PHI] : 0.0;
     if (!okL) add_nz(A.Wbar + L::PHI * T + at(a), gL[L::PHI]);
     if (!okR) add_nz(A.Wbar + L::PHI * T + at(a + 1), gR[L::PHI]);
-    if (gpL != 0.0 || gpR != 0.0) {
+    if ((gpL != 0.0 || gpR != 0.0) && !REF) {
+      double Bb[3][6];
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) Bb[r][c] = 0.0;
+      face_phi_vjp<DIM>(B, P.thinc != 0, hn, ht, gpL, gpR, Bb);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        if (!normals && r != 1) continue;
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+          add_nz(A.Wbar + L::PHI * T + at(a - 2 + c) + (long long)(r - 1) * stride_t, Bb[r][c]);
+      }
+    } else if (REF && (gpL != 0.0 || gpR != 0.0)) {
       const int r0 = normals ? 0 : 1, r1 = normals ? 2 : 1;
 #pragma unroll 1
       for (int r = r0; r <= r1; ++r) {
@@ -456,7 +455,7 @@ __global__ void __launch_bounds__(SEG) k_adj_face(Phys P, AdjArgs A, const int4*
 // ---------------------------------------------------------------------------
 // Per padded cell (ghosts by the index map): Wbar -> xbar of the source cell.
 // ---------------------------------------------------------------------------
-template <int DIM, bool RX>
+template <int DIM, bool RX, bool REF>
 __global__ void __launch_bounds__(SEG) k_adj_prim(Phys P, AdjArgs A, const int4* __restrict__ segs) {
   using L = Lay<DIM, RX>;
   constexpr int NF = L::NF;
@@ -493,30 +492,45 @@ __global__ void __launch_bounds__(SEG) k_adj_prim(Phys P, AdjArgs A, const int4*
       double q[NF];
 #pragma unroll
       for (int c = 0; c < NF; ++c) q[c] = A.x[c * T + ks];
-      const PhysT<Dual> PD = lift_phys(P, -1);
+      if constexpr (!REF) {
+        Prim w{};
+#pragma unroll
+        for (int c = 0; c < NF; ++c) prim_slot<DIM, RX>(w, c) = wb[c];
+        double qb[NF], thp[NPARAM] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int c = 0; c < NF; ++c) qb[c] = 0.0;
+        prim_of_vjp<DIM, RX>(P, q, w, qb, thp);
+#pragma unroll
+        for (int c = 0; c < NF; ++c) add_nz(A.xbar + c * T + ks, qb[c]);
+#pragma unroll
+        for (int kk = 0; kk < NPARAM; ++kk)
+          if ((A.pmask >> kk) & 1u) th[kk] += thp[kk];
+      } else {
+        const PhysT<Dual> PD = lift_phys(P, -1);
 #pragma unroll 1
-      for (int s = 0; s < NF; ++s) {
-        Dual qd[NF];
+        for (int s = 0; s < NF; ++s) {
+          Dual qd[NF];
 #pragma unroll
-        for (int c = 0; c < NF; ++c) qd[c] = Dual(q[c], c == s ? 1.0 : 0.0);
-        PrimT<Dual> w = prim_of<DIM, RX, Dual>(PD, qd);
-        double acc = 0.0;
+          for (int c = 0; c < NF; ++c) qd[c] = Dual(q[c], c == s ? 1.0 : 0.0);
+          PrimT<Dual> w = prim_of<DIM, RX, Dual>(PD, qd);
+          double acc = 0.0;
 #pragma unroll
-        for (int c = 0; c < NF; ++c) acc += wb[c] * prim_slot<DIM, RX>(w, c).d;
-        add_nz(A.xbar + s * T + ks, acc);
-      }
+          for (int c = 0; c < NF; ++c) acc += wb[c] * prim_slot<DIM, RX>(w, c).d;
+          add_nz(A.xbar + s * T + ks, acc);
+        }
 #pragma unroll 1
-      for (int kk = 0; kk < NPARAM; ++kk) {
-        if (!((A.pmask >> kk) & 1u)) continue;
-        const PhysT<Dual> PK = lift_phys(P, kk);
-        Dual qd[NF];
+        for (int kk = 0; kk < NPARAM; ++kk) {
+          if (!((A.pmask >> kk) & 1u)) continue;
+          const PhysT<Dual> PK = lift_phys(P, kk);
+          Dual qd[NF];
 #pragma unroll
-        for (int c = 0; c < NF; ++c) qd[c] = Dual(q[c]);
-        PrimT<Dual> w = prim_of<DIM, RX, Dual>(PK, qd);
-        double acc = 0.0;
+          for (int c = 0; c < NF; ++c) qd[c] = Dual(q[c]);
+          PrimT<Dual> w = prim_of<DIM, RX, Dual>(PK, qd);
+          double acc = 0.0;
 #pragma unroll
-        for (int c = 0; c < NF; ++c) acc += wb[c] * prim_slot<DIM, RX>(w, c).d;
-        th[kk] += acc;
+          for (int c = 0; c < NF; ++c) acc += wb[c] * prim_slot<DIM, RX>(w, c).d;
+          th[kk] += acc;
+        }
       }
     }
   }

@@ -281,11 +281,15 @@ void stage_fused(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
       c->phys, c->physf, a, c->d_tiles[shape]);
 }
 
-// Number of FP32-bulk stage variants: 2D: 3 tile shapes x (recovery in the
-// stage kernel, primitives from the pre-pass) x (3, 4 resident CTAs per SM
-// requested from the register allocator); 1D: the 3 shapes.
-int n_variants(const dis_ctx* c) { return c->dim == 2 ? DIS_NVARIANTS : 3; }
+// FP32-bulk stage variants v = shape + 3 pre + 6 budget: 2D: 3 tile shapes x
+// (recovery in the stage kernel, primitives from the pre-pass) x (3, 4
+// resident CTAs per SM requested from the register allocator); 1D: the 3
+// shapes x (no register limit, 64 registers per thread), recovery in the
+// kernel (pre = 0: variants 0..2 and 6..8).
 bool variant_pre(int v) { return (v / 3) % 2 == 1; }
+bool variant_valid(const dis_ctx* c, int v) {
+  return v >= 0 && v < DIS_NVARIANTS && (c->dim == 2 || !variant_pre(v));
+}
 
 template <int DIM, bool RX, bool PRE, int MINB>
 void stage_kernel_2d(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
@@ -307,10 +311,14 @@ void stage_kernel_v(dis_ctx* c, cudaStream_t st, StepArgs32& a, int v) {
       if (mb4) stage_kernel_2d<DIM, RX, false, 4>(c, st, a, shape);
       else stage_kernel_2d<DIM, RX, false, 3>(c, st, a, shape);
     }
-  } else {
+  } else if (v < 6) {
     if (shape == 0) stage_fused<DIM, RX, 122, 1, 128, false, 1>(c, st, a, shape);
     else if (shape == 1) stage_fused<DIM, RX, 250, 1, 256, false, 1>(c, st, a, shape);
     else stage_fused<DIM, RX, 506, 1, 512, false, 1>(c, st, a, shape);
+  } else {  // 1024 threads per SM requested: at most 64 registers per thread
+    if (shape == 0) stage_fused<DIM, RX, 122, 1, 128, false, 8>(c, st, a, shape);
+    else if (shape == 1) stage_fused<DIM, RX, 250, 1, 256, false, 4>(c, st, a, shape);
+    else stage_fused<DIM, RX, 506, 1, 512, false, 2>(c, st, a, shape);
   }
 }
 
@@ -379,7 +387,8 @@ int autotune32(dis_ctx* c) {
   k_cfl32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, c->physf, a, c->d_seg_cell);
   double best = 1e30;
   int bv = 0;
-  for (int v = 0; v < n_variants(c); ++v) {
+  for (int v = 0; v < DIS_NVARIANTS; ++v) {
+    if (!variant_valid(c, v)) continue;
     const bool pre = variant_pre(v);
     for (int rep = 0; rep < 3; ++rep) {  // rep 0 warms up
       CU(cudaEventRecord(e0, c->stream));
@@ -853,15 +862,16 @@ int dis_tile_choice(const dis_ctx* c, int* tx, int* ty, int* precomputed, double
   if (ty) *ty = c->dim == 2 ? kTiles2D[shape][1] : 1;
   if (precomputed) *precomputed = variant_pre(c->variant);
   if (step_ms)
-    for (int v = 0; v < DIS_NVARIANTS; ++v) step_ms[v] = v < n_variants(c) ? c->tune_ms[v] : 0.0;
+    for (int v = 0; v < DIS_NVARIANTS; ++v) step_ms[v] = variant_valid(c, v) ? c->tune_ms[v] : 0.0;
   return DIS_OK;
 }
 
 int dis_set_variant(dis_ctx* c, int variant) {
   if (!c) return fail(DIS_EINVAL, "dis_set_variant: NULL context");
   if (!c->fp32) return fail(DIS_EINVAL, "dis_set_variant: only FP32-bulk contexts have variants");
-  if (variant < -1 || variant >= n_variants(c))
-    return fail(DIS_EINVAL, "dis_set_variant: variant %d outside -1..%d", variant, n_variants(c) - 1);
+  if (variant != -1 && !variant_valid(c, variant))
+    return fail(DIS_EINVAL, "dis_set_variant: variant %d is not one of this context's (%s)", variant,
+                c->dim == 2 ? "0..11" : "0..2, 6..8");
   if (c->graph[0] || c->graph[1]) cudaStreamSynchronize(c->stream);  // replays may be in flight
   for (int g = 0; g < 2; ++g)
     if (c->graph[g]) {

@@ -313,12 +313,13 @@ def test_adjoint_of_fp32_bulk_run_matches_float64_adjoint():
 
 
 @pytest.mark.parametrize("case", ["1d", "2d_thinc", "reactive"])
-def test_hand_written_riemann_reverse_matches_dual_numbers(case):
-    """The hand-written reverse of the face Riemann problem (all six regions of
-    the HLLD-type solver, shear coupling, wave-speed ties) gives the gradient
-    of the dual-number reference to rounding: measured 1e-15 .. 2.5e-10 per
-    field and parameter (the larger values in partial-density and shear-modulus
-    gradients, sums with cancellation); bar 1e-9."""
+def test_hand_written_reverses_match_dual_numbers(case):
+    """The hand-written reverses of the face Riemann problem (all six regions
+    of the HLLD-type solver, shear coupling, wave-speed ties), of the face-state
+    map and of the primitive recovery give the gradient of the dual-number
+    reference to rounding: measured 1e-15 .. 2.5e-10 per field and parameter
+    (the larger values in partial-density and shear-modulus gradients, sums
+    with cancellation); bar 1e-9."""
     from paper_2009_14555_gb300.solver import Solver
     wl, steps, mat = {
         "1d": (W.perturbed(W.solid_gas_1d(n=100, steps=12)), 12, 0),
@@ -338,7 +339,7 @@ def test_hand_written_riemann_reverse_matches_dual_numbers(case):
     shape = wl.patches[0].prim.shape
     e = field_err(g.reshape(shape), gr.reshape(shape))
     ep = [abs(a - b) / max(abs(b), 1e-300) for a, b in zip(gp, gpr) if b != 0.0]
-    _record[f"hand_vs_dual_riemann_{case}"] = dict(field_err=e, param_err=ep)
+    _record[f"hand_vs_dual_{case}"] = dict(field_err=e, param_err=ep)
     _save()
     assert max(e) <= 1e-9, e
     assert max(ep, default=0.0) <= 1e-9, ep

@@ -22,6 +22,7 @@ pytestmark = pytest.mark.gpu
 TOL32 = 1e-4
 TOL32_PARTIAL = 5e-3
 RESULTS = {}
+_ORACLE = {}  # oracle results shared by the parametrised cases
 
 
 def check32(name, wl, steps):
@@ -94,6 +95,36 @@ def test_fp32_every_stage_variant(variant):
     bars = np.array([TOL32_PARTIAL if n in ("ar1", "ar2", "arl") else TOL32 for n in names])
     RESULTS[f"2d_reactive_plate_45x23_12steps_variant{variant}"] = dict(steps=12, l1=[float(x) for x in err])
     assert (err <= bars).all(), dict(zip(names, err))
+
+
+@pytest.mark.parametrize("variant", (0, 1, 2, 6, 7, 8))
+def test_fp32_every_1d_variant(variant):
+    """Every 1D stage variant (3 tile lengths x two register budgets) meets the
+    bar on a batch of uneven problems, shorter and longer than a tile; the
+    pre-pass variants do not exist in 1D."""
+    from paper_2009_14555_gb300.solver import Solver
+    wl = W.batched_riemann_1d(12, seed=5, steps=20, nmin=16, nmax=700)
+    s = Solver.from_workload(wl, precision="fp32_bulk")
+    with pytest.raises(RuntimeError):
+        s.set_variant(3)
+    s.set_variant(variant)
+    s.set_prim([p.prim for p in wl.patches])
+    for _ in range(20):
+        s.step(1)
+    rc, bp, bc = s.check()
+    assert rc == 0, (bp, bc)
+    g = s.get_arrays()
+    s.close()
+    if "batch_12" not in _ORACLE:
+        _ORACLE["batch_12"] = oracle_run(wl, 20)[0]
+    o = _ORACLE["batch_12"]
+    names = W.cons_names(wl.dim, wl.reactive)
+    bars = np.array([TOL32_PARTIAL if n in ("ar1", "ar2", "arl") else TOL32 for n in names])
+    worst = np.zeros(len(names))
+    for k in range(len(o)):
+        worst = np.maximum(worst, cons_l1(wl, g[k], o[k]))
+    RESULTS[f"1d_batch_12_20steps_variant{variant}"] = dict(steps=20, l1=[float(x) for x in worst])
+    assert (worst <= bars).all(), dict(zip(names, worst))
 
 
 def test_fp32_variants_agree_at_full_size():
