@@ -220,35 +220,20 @@ def _sweep(wg, absn, d, n, mats, thinc):
     return hllc(_assemble(L), _assemble(R), d, mats)
 
 
-def spatial_operator(q, grid, mats, thinc):
-    """D(q) of Section 3.1 for all interior cells of one patch."""
-    ny, nx = q["phi1"].shape
-    qg = fill_ghosts(q, grid)
-    wg = cons_to_prim(qg, mats)
-    comps = _components(wg)
-    dims = [0] if grid["dim"] == 1 else [0, 1]
+def operator_from_faces(q, faces, grid):
+    """D of Section 3.1 from the face outputs of each axis.
+
+    faces[d] = (F, phi_f, u_f, V_f) on the faces normal to axis d ((ny, nx+1)
+    for d = 0, (ny+1, nx) for d = 1): flux differences, the phi and V fluxes
+    of the face state, minus the non-conservative terms with cell-centre
+    coefficients phi_i, V_i, u_i of q."""
     hs = [grid["dx"], grid["dy"]]
-    if grid["dim"] == 2 and thinc:
-        anx, any_ = youngs_abs_normal(comps["phi1"], grid["dx"], grid["dy"])
     D = {k: torch.zeros_like(v) for k, v in q.items()}
     divu = torch.zeros_like(q["phi1"])
     beta = torch.zeros_like(q["mom"])
     Vc = q["V"]
     uc = q["mom"] / (q["ar1"] + q["ar2"])[..., None]
-    for d in dims:
-        if d == 0:
-            rows = slice(NG, NG + ny) if grid["dim"] == 2 else slice(0, 1)
-            lines = {k: t[rows, :] for k, t in comps.items()}
-            absn = anx[rows, :] if (grid["dim"] == 2 and thinc) else None
-            n = nx
-        else:
-            lines = {k: t[:, NG:NG + nx].transpose(0, 1) for k, t in comps.items()}
-            absn = any_[:, NG:NG + nx].transpose(0, 1) if thinc else None
-            n = ny
-        F, phi_f, u_f, V_f = _sweep(lines, absn, d, n, mats, thinc)
-        if d == 1:  # back to (ny+1, nx) face layout
-            F = {k: v.transpose(0, 1) for k, v in F.items()}
-            phi_f, u_f, V_f = phi_f.transpose(0, 1), u_f.transpose(0, 1), V_f.transpose(0, 1)
+    for d, (F, phi_f, u_f, V_f) in enumerate(faces):
 
         def diff(t):
             return (t[:, 1:] - t[:, :-1]) if d == 0 else (t[1:, :] - t[:-1, :])
@@ -266,6 +251,34 @@ def spatial_operator(q, grid, mats, thinc):
     D["V"] = D["V"] - ((2.0 / 3.0) * Vc * divu[..., None, None]
                        - uc[..., :, None] * beta[..., None, :])
     return D
+
+
+def spatial_operator(q, grid, mats, thinc):
+    """D(q) of Section 3.1 for all interior cells of one patch."""
+    ny, nx = q["phi1"].shape
+    qg = fill_ghosts(q, grid)
+    wg = cons_to_prim(qg, mats)
+    comps = _components(wg)
+    dims = [0] if grid["dim"] == 1 else [0, 1]
+    if grid["dim"] == 2 and thinc:
+        anx, any_ = youngs_abs_normal(comps["phi1"], grid["dx"], grid["dy"])
+    faces = []
+    for d in dims:
+        if d == 0:
+            rows = slice(NG, NG + ny) if grid["dim"] == 2 else slice(0, 1)
+            lines = {k: t[rows, :] for k, t in comps.items()}
+            absn = anx[rows, :] if (grid["dim"] == 2 and thinc) else None
+            n = nx
+        else:
+            lines = {k: t[:, NG:NG + nx].transpose(0, 1) for k, t in comps.items()}
+            absn = any_[:, NG:NG + nx].transpose(0, 1) if thinc else None
+            n = ny
+        F, phi_f, u_f, V_f = _sweep(lines, absn, d, n, mats, thinc)
+        if d == 1:  # back to (ny+1, nx) face layout
+            F = {k: v.transpose(0, 1) for k, v in F.items()}
+            phi_f, u_f, V_f = phi_f.transpose(0, 1), u_f.transpose(0, 1), V_f.transpose(0, 1)
+        faces.append((F, phi_f, u_f, V_f))
+    return operator_from_faces(q, faces, grid)
 
 
 # ----------------------------------------------------------------------------
@@ -374,8 +387,10 @@ def reaction_update(q, mats, dt):
 
 
 def step(q, grid, mats, opts, dt=None):
-    """One full time step: CFL dt from q^n, SSP-RK3 hyperbolic update,
-    then the plastic and reactive source steps (Section 3, fractional steps)."""
+    """One full time step: CFL dt from q^n, SSP-RK3 hyperbolic update (or,
+    with opts["scheme"] == "hancock", the single-stage MUSCL-Hancock update of
+    oracle.hancock), then the plastic and reactive source steps (Section 3,
+    fractional steps)."""
     if dt is None:
         dt = cfl_dt(q, grid, mats, opts["cfl"])
     th = opts.get("thinc", False)
@@ -383,11 +398,15 @@ def step(q, grid, mats, opts, dt=None):
     def D(x):
         return spatial_operator(x, grid, mats, th)
 
-    q1 = _axpy(1.0, q, -dt, D(q))
-    q2 = _axpy(1.0, q1, -dt, D(q1))
-    q3 = _axpy(0.75, q, 0.25, q2)
-    q4 = _axpy(1.0, q3, -dt, D(q3))
-    qs = _axpy(1.0 / 3.0, q, 2.0 / 3.0, q4)
+    if opts.get("scheme", "rk3") == "hancock":
+        from .hancock import hancock_operator
+        qs = _axpy(1.0, q, -dt, hancock_operator(q, grid, mats, th, dt))
+    else:
+        q1 = _axpy(1.0, q, -dt, D(q))
+        q2 = _axpy(1.0, q1, -dt, D(q1))
+        q3 = _axpy(0.75, q, 0.25, q2)
+        q4 = _axpy(1.0, q3, -dt, D(q3))
+        qs = _axpy(1.0 / 3.0, q, 2.0 / 3.0, q4)
     qs = plastic_update(qs, mats, dt)
     if any(m["reactive"] for m in mats):
         qs = reaction_update(qs, mats, dt)
