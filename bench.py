@@ -291,6 +291,8 @@ def run_gpu(args):
         "clocks": r["clocks"],
         "status_ok": bool(r["ok"] and r64["ok"]),
     }
+    line["fp64"]["hancock"] = hancock_bench(wl, prim, args.steps, args.warmup)
+    line["fp64"]["hancock"]["speedup_vs_rk3"] = line["fp64"]["hancock"]["value"] / value64
     if not args.no_batch:
         line["batch_1d"] = batch_bench()
     if not args.no_adjoint:
@@ -339,9 +341,33 @@ def adjoint_bench(n=256, steps=200, every=20):
     return out
 
 
-def batch_bench(steps=10, warmup=3):
+def hancock_bench(wl, prim, steps, warmup):
+    """The float64 step with the single-stage MUSCL-Hancock update on the same
+    workload: cell-updates/s (device events, inputs resident)."""
+    import torch
+    from paper_2009_14555_gb300.solver import Solver
+    s = Solver.from_workload(wl, precision="fp64", scheme="hancock")
+    s.set_state(prim, kind=1)
+    s.step(warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s.stream)
+    s.step(steps)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    rc = s.check()[0]
+    launches = s.launches
+    s.close()
+    return {"value": wl.cells / (ms * 1e-3), "ms_per_step": ms, "steps": steps,
+            "launches_per_step": launches // steps, "status_ok": rc == 0}
+
+
+def batch_bench(steps=300, warmup=3):
     """4096 independent 1D two-material problems (256-4096 cells, seed 3) in one
-    batch: cell-updates/s for both precisions (each problem has its own dt)."""
+    batch, 300 steps in one dis_step call: cell-updates/s for both precisions
+    (each problem has its own dt; FP32-bulk: the tuner's schedule, per-step
+    launches or the persistent batch kernel)."""
     import torch
     from paper_2009_14555_gb300 import workloads as W
     from paper_2009_14555_gb300.solver import Solver, pack
@@ -352,22 +378,27 @@ def batch_bench(steps=10, warmup=3):
     for prec in ("fp32_bulk", "fp64"):
         s = Solver.from_workload(wl, precision=prec)
         s.set_state(prim, kind=1)
-        for _ in range(warmup):
-            s.step(1)
+        s.step(warmup)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(s.stream)
-        for _ in range(steps):
-            s.step(1)
+        s.step(steps)
         e1.record(s.stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
-        ok = s.check()[0] == 0
-        out[prec] = {"value": wl.cells / (ms * 1e-3), "ms_per_step": ms, "status_ok": ok}
+        rc, bp, bc = s.check()
+        # problems whose state left the finite range (each problem is independent)
+        bad = sum(int(not np.isfinite(a).all()) for a in s.get_arrays())
+        out[prec] = {"value": wl.cells / (ms * 1e-3), "ms_per_step": ms, "steps": steps,
+                     "launches": s.launches, "nonfinite_problems": bad,
+                     "first_flagged": [int(bp), int(bc)] if rc else None}
         if prec == "fp32_bulk":
             t = s.tile_choice()
+            sc, bms = s.schedule()
             out[prec]["tile"] = list(t[:3])
+            out[prec]["schedule"] = "persistent" if sc == 1 else "per-step launches"
             out[prec]["tuned_ms_per_step"] = [round(float(x), 4) for x in t[3]]
+            out[prec]["tuned_ms_persistent_one_step"] = [round(float(x), 4) for x in bms]
         s.close()
     return out
 

@@ -77,12 +77,22 @@ typedef struct {
   int32_t bc[4];
 } dis_patch;
 
+/* Hyperbolic update of a step: DIS_RK3 is the paper's three-stage
+ * Runge-Kutta scheme (Section 3.1, three Riemann solves per face and step);
+ * DIS_HANCOCK the single-stage MUSCL-Hancock predictor-corrector (one Riemann
+ * solve per face and step, second order; no counterpart in the paper): the
+ * per-cell edge states of the same reconstruction move by half a step of the
+ * cell's own operator before the face Riemann problems.  Float64 only. */
+enum { DIS_RK3 = 0, DIS_HANCOCK = 1 };
+
 /* Step options: CFL number (Section 3: fraction of the largest stable step),
- * THINC interface steepening on/off (Appendix A), precision mode. */
+ * THINC interface steepening on/off (Appendix A), precision mode, hyperbolic
+ * scheme (DIS_RK3 or DIS_HANCOCK; 0 = the paper's). */
 typedef struct {
   double cfl;
   int32_t thinc;
   int32_t precision;
+  int32_t scheme;
 } dis_options;
 
 typedef struct dis_ctx dis_ctx;
@@ -162,12 +172,34 @@ int dis_tile_choice(const dis_ctx* ctx, int* tx, int* ty, int* precomputed, doub
  * order.  DIS_EINVAL for float64 contexts or an out-of-range variant. */
 int dis_set_variant(dis_ctx* ctx, int variant);
 
+/* Schedule of a 1D FP32-bulk batch (independent problems, one per patch):
+ * 0 = per step one CFL launch and one stage-kernel launch per Runge-Kutta
+ * stage over the tiles of all problems (captured as one CUDA graph per
+ * step); 1 = one persistent launch per dis_step / dis_step_fixed_dt call
+ * that runs all its steps, one CTA per problem (longest problems first),
+ * with the problem's CFL rate and stages in turn, so a problem's state stays
+ * in L2 between stages and steps; -1 (default) = the autotuner of the first
+ * step times both and keeps the faster.  Both run the same tile arithmetic;
+ * compiled as separate kernels they may contract multiply-adds differently,
+ * so states agree to rounding, not bit for bit.
+ * The variant (dis_set_variant) selects the tile length and register budget
+ * in either schedule.  DIS_EINVAL for a NULL context, a schedule outside
+ * -1..1, or 1 on a float64 or 2D context. */
+int dis_set_schedule(dis_ctx* ctx, int schedule);
+
+/* The schedule a step uses (0 or 1; -1 while a tuned context has not stepped)
+ * and, if batch_ms is not NULL, the tuned one-step time of the persistent
+ * kernel per variant (DIS_NVARIANTS values, 0 where not timed).  DIS_EINVAL
+ * for a NULL context. */
+int dis_schedule(const dis_ctx* ctx, int* schedule, double* batch_ms);
+
 /* Diagnostic: advance n_steps CFL steps like dis_step but launch kernel by
  * kernel with CUDA events between launches, and return in kernel_ms[4] the
  * mean device time per launch of the primitive-recovery, x-flux, y-flux (0 in
  * 1D) and update kernels (float64), or, FP32-bulk: slot 0 the CFL pass (one
  * launch per step) or the primitive pre-pass (one per stage), slot 1 the
- * stage kernel.  Synchronises after every stage. */
+ * stage kernel.  Synchronises after every stage.  DIS_EINVAL for a
+ * DIS_HANCOCK context. */
 int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
 
 /* ---- Adjoint (reverse mode) of the float64 step -------------------------
@@ -197,7 +229,8 @@ int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
  * checkpoint_every + 8) states, allocated here, kept for dis_adjoint and
  * released by dis_destroy.  FP32-bulk contexts checkpoint their states in
  * float64 (plus float64 primitive and face buffers for the reverse sweep).
- * Returns DIS_EINVAL (bad arguments), DIS_ESTATE (no state), DIS_ENOMEM,
+ * Returns DIS_EINVAL (bad arguments, or a DIS_HANCOCK context: the adjoint
+ * covers the Runge-Kutta scheme), DIS_ESTATE (no state), DIS_ENOMEM,
  * DIS_ECUDA.  Synchronises. */
 int dis_adj_forward(dis_ctx* ctx, int n_steps, int checkpoint_every, int objective_material,
                     const double* dt_in, double* dt_out, double* J_out);

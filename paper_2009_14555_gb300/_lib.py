@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libdis.so")
 DIS_OK, DIS_EINVAL, DIS_ENOMEM, DIS_ECUDA, DIS_ENONPHYSICAL, DIS_ESTATE = 0, -1, -2, -3, -4, -5
 DIS_CONSERVATIVE, DIS_PRIMITIVE = 0, 1
 DIS_FP64, DIS_FP32_BULK = 0, 1
+DIS_RK3, DIS_HANCOCK = 0, 1
 DIS_NPARAM = 6  # per material l: G, sigma_y, Q at 3 l + k
 DIS_NVARIANTS = 12  # FP32-bulk stage variants (2D: 3 tile shapes x 2 primitive sources x 2 register budgets)
 
@@ -32,7 +33,7 @@ class DisPatch(ctypes.Structure):
 
 
 class DisOptions(ctypes.Structure):
-    _fields_ = [("cfl", c_double), ("thinc", c_int32), ("precision", c_int32)]
+    _fields_ = [("cfl", c_double), ("thinc", c_int32), ("precision", c_int32), ("scheme", c_int32)]
 
 
 class DisError(RuntimeError):
@@ -57,6 +58,8 @@ SIGNATURES = {
     "dis_last_launches": (c_longlong, [c_void_p]),
     "dis_step_timed": (c_int, [c_void_p, c_int, c_void_p]),
     "dis_set_variant": (c_int, [c_void_p, c_int]),
+    "dis_set_schedule": (c_int, [c_void_p, c_int]),
+    "dis_schedule": (c_int, [c_void_p, POINTER(c_int), c_void_p]),
     "dis_tile_choice": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), c_void_p]),
     "dis_cfl_dt_static": (c_int, [c_int, c_int, POINTER(DisPatch), POINTER(DisMaterial), c_int,
                                    c_double, c_void_p, c_void_p, c_void_p]),

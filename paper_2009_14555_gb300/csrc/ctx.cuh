@@ -33,6 +33,8 @@ struct dis_ctx {
   bool ws_owned = false, ws_ready = false;
   double* q[2] = {nullptr, nullptr};  // q^n, stage buffer
   double* W = nullptr;
+  double* E = nullptr;  // MUSCL-Hancock evolved edge states (2 dim nf planes)
+  bool hancock = false;
   double* Fx = nullptr;
   double* Fy = nullptr;
   double* io = nullptr;
@@ -48,6 +50,17 @@ struct dis_ctx {
   int4* d_tiles[3] = {nullptr, nullptr, nullptr};
   int variant = -1;
   double tune_ms[DIS_NVARIANTS] = {};
+  // 1D FP32-bulk batches: schedule 0 = one launch per kernel and stage
+  // (captured per step), 1 = the persistent batch kernel (one launch for all
+  // steps of a dis_step call, one CTA per problem), -1 = chosen by the tuner;
+  // problems in launch order (longest first) and the first tile of each
+  // problem per tile shape; tuned one-step times of the persistent kernel
+  int schedule = -1, schedule_req = -1;
+  std::vector<int> order;
+  std::vector<int> tile0[3];
+  int* d_order = nullptr;
+  int* d_tile0[3] = {nullptr, nullptr, nullptr};
+  double tune_batch_ms[DIS_NVARIANTS] = {};
   // FP32-bulk buffers: (phi1, rho E) float64 pairs and float32 planes
   // q^n and two stage buffers: a stage kernel reads the halo of its source
   // from neighbouring tiles, so no stage may write the buffer it reads

@@ -83,14 +83,21 @@ constexpr int kTiles1D[3] = {122, 250, 506};
 void tile_tables(dis_ctx* c) {
   for (int v = 0; v < 3; ++v) {
     c->tiles[v].clear();
+    c->tile0[v].assign(1, 0);
     const int TX = c->dim == 2 ? kTiles2D[v][0] : kTiles1D[v];
     const int TY = c->dim == 2 ? kTiles2D[v][1] : 1;
     for (int p = 0; p < c->np; ++p) {
       const PatchDev& d = c->pd[p];
       for (int j = 0; j < d.ny; j += TY)
         for (int i = 0; i < d.nx; i += TX) c->tiles[v].push_back(make_int4(p, i, j, 0));
+      c->tile0[v].push_back((int)c->tiles[v].size());
     }
   }
+  // launch order of the persistent batch kernel: longest problems first
+  c->order.resize(c->np);
+  for (int p = 0; p < c->np; ++p) c->order[p] = p;
+  std::stable_sort(c->order.begin(), c->order.end(),
+                   [&](int a, int b) { return c->pd[a].nx * c->pd[a].ny > c->pd[b].nx * c->pd[b].ny; });
 }
 
 void layout(dis_ctx* c) {
@@ -146,7 +153,7 @@ size_t carve(dis_ctx* c, char* base) {
   Carve k;
   const size_t T = (size_t)c->T;
   const size_t nfx = (size_t)(c->nf + n_extra(c->dim));
-  size_t oq0 = 0, oq1 = 0, ow = 0, ofx = 0, ofy = 0;
+  size_t oq0 = 0, oq1 = 0, ow = 0, ofx = 0, ofy = 0, oe = 0;
   size_t o64[3] = {0, 0, 0}, o32[3] = {0, 0, 0}, ow32 = 0;
   if (!c->fp32) {
     const size_t dpl = sizeof(double) * T;
@@ -155,6 +162,7 @@ size_t carve(dis_ctx* c, char* base) {
     ow = k.take(c->nf * dpl);
     ofx = k.take(sizeof(double) * nfx * c->NFX);
     ofy = k.take(sizeof(double) * nfx * c->NFY);
+    if (c->hancock) oe = k.take((size_t)2 * c->dim * c->nf * dpl);
   } else {
     for (int b = 0; b < 3; ++b) {
       o64[b] = k.take(2 * sizeof(double) * T);
@@ -172,16 +180,23 @@ size_t carve(dis_ctx* c, char* base) {
   size_t os2 = k.take(sizeof(int4) * c->seg_fx.size());
   size_t os3 = k.take(sizeof(int4) * std::max<size_t>(1, c->seg_fy.size()));
   size_t os4 = k.take(sizeof(int4) * c->seg_cell.size());
-  size_t ot[3];
+  size_t ot[3], ot0[3];
   for (int v = 0; v < 3; ++v) ot[v] = k.take(sizeof(int4) * std::max<size_t>(1, c->tiles[v].size()));
+  for (int v = 0; v < 3; ++v) ot0[v] = k.take(sizeof(int) * (size_t)(c->np + 1));
+  const size_t oord = k.take(sizeof(int) * (size_t)c->np);
   if (base) {
-    for (int v = 0; v < 3; ++v) c->d_tiles[v] = (int4*)(base + ot[v]);
+    for (int v = 0; v < 3; ++v) {
+      c->d_tiles[v] = (int4*)(base + ot[v]);
+      c->d_tile0[v] = (int*)(base + ot0[v]);
+    }
+    c->d_order = (int*)(base + oord);
     if (!c->fp32) {
       c->q[0] = (double*)(base + oq0);
       c->q[1] = (double*)(base + oq1);
       c->W = (double*)(base + ow);
       c->Fx = (double*)(base + ofx);
       c->Fy = (double*)(base + ofy);
+      c->E = c->hancock ? (double*)(base + oe) : nullptr;
     } else {
       for (int b = 0; b < 3; ++b) {
         c->q64[b] = (double*)(base + o64[b]);
@@ -225,9 +240,14 @@ int ensure_ws(dis_ctx* c) {
   CU(cudaMemcpyAsync(c->d_seg_cell, c->seg_cell.data(), sizeof(int4) * c->seg_cell.size(),
                      cudaMemcpyHostToDevice, c->stream));
 
-  for (int v = 0; v < 3; ++v)
+  for (int v = 0; v < 3; ++v) {
     CU(cudaMemcpyAsync(c->d_tiles[v], c->tiles[v].data(), sizeof(int4) * c->tiles[v].size(),
                        cudaMemcpyHostToDevice, c->stream));
+    CU(cudaMemcpyAsync(c->d_tile0[v], c->tile0[v].data(), sizeof(int) * c->tile0[v].size(),
+                       cudaMemcpyHostToDevice, c->stream));
+  }
+  CU(cudaMemcpyAsync(c->d_order, c->order.data(), sizeof(int) * c->order.size(), cudaMemcpyHostToDevice,
+                     c->stream));
   CU(cudaMemsetAsync(c->status, 0, sizeof(int) * 4, c->stream));
   // The tables above come from host vectors that outlive this call; make sure
   // the copies have finished before the caller may touch them.
@@ -245,6 +265,7 @@ StepArgs base_args(dis_ctx* c) {
   a.W = c->W;
   a.Fx = c->Fx;
   a.Fy = c->Fy;
+  a.E = c->E;
   a.rate = c->rate;
   a.dtlast = c->dtlast;
   a.status = c->status;
@@ -342,6 +363,42 @@ int stage_fused_v(dis_ctx* c, cudaStream_t st, StepArgs32& a, int v, bool rate_o
   return l;
 }
 
+// Persistent 1D batch kernel (FP32-bulk), variant v: tile length v % 3,
+// 64 registers per thread for v >= 6; n steps in one launch, one CTA per
+// problem.  scratch_last (tuning, n = 1): the step ends in buffer 1.
+template <bool RX, int TX, int NT, int MINB>
+void batch_fused(dis_ctx* c, cudaStream_t st, const StepArgs32& a, int n, int scratch_last, int shape) {
+  constexpr size_t smem = fused32_smem<1, RX, TX, 1>();
+  static bool attr_set = false;  // per instantiation, per process
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_batch32<RX, TX, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_batch32<RX, TX, NT, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    attr_set = true;
+  }
+  Bufs32 b;
+  for (int k = 0; k < 3; ++k) {
+    b.q64[k] = c->q64[k];
+    b.q32[k] = c->q32[k];
+  }
+  k_batch32<RX, TX, NT, MINB><<<(unsigned)c->np, NT, smem, st>>>(c->phys, c->physf, a, b, c->d_order,
+                                                                 c->d_tile0[shape], c->d_tiles[shape], n,
+                                                                 scratch_last);
+}
+
+template <bool RX>
+void batch_kernel_v(dis_ctx* c, cudaStream_t st, const StepArgs32& a, int n, int scratch_last, int v) {
+  const int shape = v % 3;
+  if (v < 6) {
+    if (shape == 0) batch_fused<RX, 122, 128, 1>(c, st, a, n, scratch_last, shape);
+    else if (shape == 1) batch_fused<RX, 250, 256, 1>(c, st, a, n, scratch_last, shape);
+    else batch_fused<RX, 506, 512, 1>(c, st, a, n, scratch_last, shape);
+  } else {
+    if (shape == 0) batch_fused<RX, 122, 128, 8>(c, st, a, n, scratch_last, shape);
+    else if (shape == 1) batch_fused<RX, 250, 256, 4>(c, st, a, n, scratch_last, shape);
+    else batch_fused<RX, 506, 512, 2>(c, st, a, n, scratch_last, shape);
+  }
+}
+
 // Buffers of the FP32-bulk stages: q^n (0) -> q1 (1) -> q2 (2) -> q^{n+1} (0).
 // A stage kernel that recovers its tile reads the halo of its source from
 // neighbouring tiles, so it must not write that source; with the primitive
@@ -410,10 +467,41 @@ int autotune32(dis_ctx* c) {
     }
     if (c->tune_ms[v] < best) { best = c->tune_ms[v]; bv = v; }
   }
+  // 1D: the persistent batch kernel, one step per variant (its own CFL pass;
+  // the last stage writes buffer 1), against the best per-step schedule
+  double best_b = 1e30;
+  int bb = -1;
+  if constexpr (DIM == 1) {
+    if (c->schedule_req != 0) {
+      StepArgs32 ab = base_args32(c);
+      ab.dtfix = nullptr;
+      for (int v = 0; v < DIS_NVARIANTS; ++v) {
+        c->tune_batch_ms[v] = 0.0;
+        if (!variant_valid(c, v)) continue;
+        for (int rep = 0; rep < 3; ++rep) {
+          CU(cudaEventRecord(e0, c->stream));
+          batch_kernel_v<RX>(c, c->stream, ab, 1, 1, v);
+          CU(cudaEventRecord(e1, c->stream));
+          CU(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          CU(cudaEventElapsedTime(&ms, e0, e1));
+          if (rep == 1) c->tune_batch_ms[v] = ms;
+          if (rep == 2) c->tune_batch_ms[v] = 0.5 * (c->tune_batch_ms[v] + ms);
+        }
+        if (c->tune_batch_ms[v] < best_b) { best_b = c->tune_batch_ms[v]; bb = v; }
+      }
+    }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   CU(cudaGetLastError());
-  c->variant = bv;
+  if (c->schedule_req == 1 || (c->schedule_req < 0 && bb >= 0 && best_b < best)) {
+    c->variant = bb;
+    c->schedule = 1;
+  } else {
+    c->variant = bv;
+    c->schedule = 0;
+  }
   return DIS_OK;
 }
 
@@ -449,6 +537,24 @@ long long launch_step(dis_ctx* c, cudaStream_t st, bool fixed) {
                  nfy = (unsigned)c->seg_fy.size(), nc = (unsigned)c->seg_cell.size();
   long long launches = 0;
   if (!fixed) cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, st);
+  if (c->hancock) {  // single stage: q^{n+1} = S(q^n - dt D_H(q^n)), in place
+    a.qsrc = c->q[0];
+    a.qn = c->q[0];
+    a.qdst = c->q[0];
+    a.a = 0.0;
+    a.b = 1.0;
+    a.last = 1;
+    k_prim<DIM, RX><<<np, SEG, 0, st>>>(c->phys, a, c->d_seg_prim, fixed ? 0 : 1);
+    k_hancock<DIM, RX><<<np, SEG, 0, st>>>(c->phys, a, c->d_seg_prim);
+    k_flux_h<DIM, RX, 0><<<nfx, SEG, 0, st>>>(c->phys, a, c->d_seg_fx);
+    launches += 3;
+    if constexpr (DIM == 2) {
+      k_flux_h<DIM, RX, 1><<<nfy, SEG, 0, st>>>(c->phys, a, c->d_seg_fy);
+      ++launches;
+    }
+    k_update<DIM, RX><<<nc, SEG, 0, st>>>(c->phys, a, c->d_seg_cell);
+    return launches + 1;
+  }
   for (int stg = 0; stg < 3; ++stg) {
     a.qsrc = stg == 0 ? c->q[0] : c->q[1];
     a.qn = c->q[0];
@@ -563,6 +669,17 @@ int run_steps(dis_ctx* c, int n_steps, bool fixed) {
   if (c->fp32 && c->variant < 0) {
     const int rc = autotune32<DIM, RX>(c);
     if (rc) return rc;
+  }
+  if constexpr (DIM == 1) {
+    const int sched = c->schedule_req >= 0 ? c->schedule_req : std::max(c->schedule, 0);
+    if (c->fp32 && sched == 1) {  // all n steps in one persistent launch
+      StepArgs32 a = base_args32(c);
+      a.dtfix = fixed ? c->dtfix : nullptr;
+      batch_kernel_v<RX>(c, c->stream, a, n_steps, 0, c->variant);
+      CU(cudaGetLastError());
+      c->launches = 1;
+      return DIS_OK;
+    }
   }
   if (!c->use_graphs) {
     long long l = 0;
@@ -686,6 +803,10 @@ int dis_create(int dim, int n_patches, const dis_patch* patches, int reactive_ma
   if (!(opt->cfl > 0.0 && opt->cfl <= 1.0)) return fail(DIS_EINVAL, "dis_create: cfl must be in (0, 1]");
   if (opt->precision != DIS_FP64 && opt->precision != DIS_FP32_BULK)
     return fail(DIS_EINVAL, "dis_create: unknown precision %d", opt->precision);
+  if (opt->scheme != DIS_RK3 && opt->scheme != DIS_HANCOCK)
+    return fail(DIS_EINVAL, "dis_create: unknown scheme %d", opt->scheme);
+  if (opt->scheme == DIS_HANCOCK && opt->precision != DIS_FP64)
+    return fail(DIS_EINVAL, "dis_create: the MUSCL-Hancock scheme is built for float64 only");
   for (int p = 0; p < n_patches; ++p) {
     const dis_patch& P = patches[p];
     const int ny = dim == 2 ? P.ny : 1;
@@ -705,6 +826,7 @@ int dis_create(int dim, int n_patches, const dis_patch* patches, int reactive_ma
   c->nf = (dim == 2 ? 11 : 8) + (reactive_material >= 0 ? 1 : 0);
   c->opt = *opt;
   c->fp32 = opt->precision == DIS_FP32_BULK;
+  c->hancock = opt->scheme == DIS_HANCOCK;
   c->patches.assign(patches, patches + n_patches);
   c->stream = (cudaStream_t)stream;
   cudaGetDevice(&c->device);
@@ -882,10 +1004,32 @@ int dis_set_variant(dis_ctx* c, int variant) {
   return DIS_OK;
 }
 
+int dis_set_schedule(dis_ctx* c, int schedule) {
+  if (!c) return fail(DIS_EINVAL, "dis_set_schedule: NULL context");
+  if (schedule < -1 || schedule > 1) return fail(DIS_EINVAL, "dis_set_schedule: schedule %d outside -1..1", schedule);
+  if (schedule == 1 && (!c->fp32 || c->dim != 1))
+    return fail(DIS_EINVAL, "dis_set_schedule: the persistent batch schedule needs a 1D FP32-bulk context");
+  c->schedule_req = schedule;
+  return DIS_OK;
+}
+
+int dis_schedule(const dis_ctx* c, int* schedule, double* batch_ms) {
+  if (!c) return fail(DIS_EINVAL, "dis_schedule: NULL context");
+  if (schedule) {
+    if (c->schedule_req >= 0) *schedule = c->schedule_req;
+    else if (c->variant >= 0) *schedule = std::max(c->schedule, 0);
+    else *schedule = -1;
+  }
+  if (batch_ms)
+    for (int v = 0; v < DIS_NVARIANTS; ++v) batch_ms[v] = c->tune_batch_ms[v];
+  return DIS_OK;
+}
+
 int dis_step_timed(dis_ctx* c, int n_steps, double* kernel_ms) {
   if (!c || !kernel_ms) return fail(DIS_EINVAL, "dis_step_timed: NULL argument");
   if (n_steps <= 0) return fail(DIS_EINVAL, "dis_step_timed: n_steps must be positive");
   if (!c->have_state) return fail(DIS_ESTATE, "dis_step_timed: no state loaded");
+  if (c->hancock) return fail(DIS_EINVAL, "dis_step_timed: Runge-Kutta contexts only");
   const bool rx = c->y >= 0;
   if (c->dim == 1) return rx ? timed_steps<1, true>(c, n_steps, kernel_ms) : timed_steps<1, false>(c, n_steps, kernel_ms);
   return rx ? timed_steps<2, true>(c, n_steps, kernel_ms) : timed_steps<2, false>(c, n_steps, kernel_ms);

@@ -119,6 +119,29 @@ __device__ __forceinline__ void face_phi(const T (&B)[3][6], bool thinc, double 
   phiR = Lt;  // left edge of cell a+1
 }
 
+// Left and right edge values of phi in the middle cell of a 3 x 5 stencil
+// (columns: cells i-2 .. i+2 along the axis; rows: tangential neighbours, used
+// only by the 2D Youngs normal): MUSCL and THINC candidates of cells i-1, i,
+// i+1 and the BVD choice for cell i (Appendix A), as in face_phi.
+template <int DIM, class T>
+__device__ __forceinline__ void cell_phi_edges(const T (&B)[3][5], bool thinc, double hn, double ht,
+                                               T& eL, T& eR) {
+  CandT<T> c[3];
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {
+    T beta = 2.51;
+    if (DIM == 2 && thinc) {
+      const T dn = (B[2][s + 2] + 2.0 * B[1][s + 2] + B[0][s + 2]) - (B[2][s] + 2.0 * B[1][s] + B[0][s]);
+      const T dt_ = (B[2][s + 2] + 2.0 * B[2][s + 1] + B[2][s]) - (B[0][s + 2] + 2.0 * B[0][s + 1] + B[0][s]);
+      const T gn = dn / hn, gt = dt_ / ht;
+      const T nrm = sqrt(gn * gn + gt * gt);
+      beta = 2.5 * (nrm == 0.0 ? T(1.0) : fabs(gn) / nrm) + 0.01;
+    }
+    c[s] = phi_cand(B[1][s], B[1][s + 1], B[1][s + 2], beta, thinc);
+  }
+  bvd(c[0], c[1], c[2], eL, eR);
+}
+
 // MUSCL face values of one primitive from cells a-1 .. a+2 (minmod slopes).
 template <class T>
 __device__ __forceinline__ void muscl_pair(T w0, T w1, T w2, T w3, T& l, T& r) {
@@ -139,12 +162,39 @@ __host__ __device__ constexpr int n_face_out() {
 // c_L still squared; the caller has applied the non-hyperbolic fallback) and
 // the outputs of the face: fluxes and extras.
 template <int DIM, bool RX, int DIR, class T>
+__device__ __forceinline__ void face_outputs(const FaceOutT<T>& o, T* F);
+
+template <int DIM, bool RX, int DIR, class T>
 __device__ __forceinline__ void riemann_outputs(FStateT<T> sl, FStateT<T> sr, T* F) {
-  using L = Lay<DIM, RX>;
-  constexpr int NF = L::NF;
   sl.cL = sqrt(sl.cL);
   sr.cL = sqrt(sr.cL);
-  const FaceOutT<T> o = hllc<DIR>(sl, sr);
+  face_outputs<DIM, RX, DIR, T>(hllc<DIR>(sl, sr), F);
+}
+
+// Physical flux of one state along DIR as a face output (the flux of a face
+// whose two sides are that state; single-stage MUSCL-Hancock predictor).
+template <int DIR, class T>
+__device__ __forceinline__ FaceOutT<T> physical_faceout(const FStateT<T>& K) {
+  FaceOutT<T> o;
+  o.Far1 = K.ar1 * K.un;
+  o.Far2 = K.ar2 * K.un;
+  o.Farl = K.arl * K.un;
+  o.Fmn = K.rho * K.un * K.un - K.snn;
+  o.Fmt = K.rho * K.ut * K.un - K.snt;
+  o.FE = K.rhoE * K.un - (K.un * K.snn + K.ut * K.snt);
+  o.phi = K.phi;
+  o.un = K.un;
+  o.ut = K.ut;
+  o.V11 = K.V11; o.V12 = K.V12; o.V21 = K.V21; o.V22 = K.V22; o.V33 = K.V33;
+  return o;
+}
+
+// Conservative fluxes (NF slots) and face extras (u_n, normal row of V) of a
+// face output.
+template <int DIM, bool RX, int DIR, class T>
+__device__ __forceinline__ void face_outputs(const FaceOutT<T>& o, T* F) {
+  using L = Lay<DIM, RX>;
+  constexpr int NF = L::NF;
   const T fu = DIR == 0 ? o.un : o.ut;
   const T fv = DIR == 0 ? o.ut : o.un;
   F[L::PHI] = o.phi * o.un;

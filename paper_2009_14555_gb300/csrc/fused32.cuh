@@ -149,19 +149,22 @@ constexpr size_t fused32_smem() {
   return sizeof(float) * ((size_t)Lay<DIM, RX>::NF * HX * HY + (size_t)S::N * (NFX + NFY)) + 16 * sizeof(double);
 }
 
-template <int DIM, bool RX, int TX, int TY, int NT, bool PRE, int MINB>
-__global__ void __launch_bounds__(NT, MINB) k_stage32(Phys P, PhysF F, StepArgs32 A, const int4* __restrict__ tiles) {
+// One stage on one tile t = (patch, i0, j0) by the NT threads of a CTA, with
+// the tile's primitives and faces in the shared memory sm.  The stage kernel
+// runs it once per CTA; the persistent 1D batch kernel runs it for every tile
+// of its problem in turn (the caller synchronises the CTA between tiles).
+template <int DIM, bool RX, int TX, int TY, int NT, bool PRE>
+__device__ __forceinline__ void stage32_tile(const Phys& P, const PhysF& F, const StepArgs32& A, const int4 t,
+                                             float* __restrict__ sm) {
   static_assert(TX * TY <= NT, "one thread per tile cell in the update phase");
   using L = Lay<DIM, RX>;
   using S = FSlots<DIM, RX>;
   constexpr int NF = L::NF;
   constexpr int HX = TX + 2 * NG, HY = DIM == 2 ? TY + 2 * NG : 1;
   constexpr int NFX = (TX + 1) * TY, NFY = DIM == 2 ? TX * (TY + 1) : 0;
-  extern __shared__ __align__(16) float sm[];
   float* Wsm = sm;
   float* Fxs = Wsm + NF * HX * HY;
   float* Fys = Fxs + S::N * NFX;
-  const int4 t = tiles[blockIdx.x];
   const PatchDev pd = A.pd[t.x];
   const int i0 = t.y, j0 = t.z;
   const int tid = threadIdx.x;
@@ -365,28 +368,108 @@ __global__ void __launch_bounds__(NT, MINB) k_stage32(Phys P, PhysF F, StepArgs3
   A.q64dst[T + k] = oE;
 }
 
+template <int DIM, bool RX, int TX, int TY, int NT, bool PRE, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_stage32(Phys P, PhysF F, StepArgs32 A, const int4* __restrict__ tiles) {
+  extern __shared__ __align__(16) float sm[];
+  stage32_tile<DIM, RX, TX, TY, NT, PRE>(P, F, A, tiles[blockIdx.x], sm);
+}
+
 // CFL rate of the state at the start of a step (FP32-bulk): per-patch max of
 // sum_d (|u_d| + c_L) / dx_d over interior cells.
+// sum_d (|u_d| + c_L) / dx_d of one interior cell of the source state;
+// flags a cell without a real sound speed.
+template <int DIM, bool RX>
+__device__ __forceinline__ float cfl_rate32(const Phys& P, const PhysF& F, const StepArgs32& A,
+                                            const PatchDev& pd, int patch, int i, int j) {
+  const PrimF w = cons_to_prim32<DIM, RX>(P, F, A.q64src, A.q32src, A.T, cidx(pd, i, j));
+  const StrainF s = strain_f(w.V11, w.V12, w.V21, w.V22, w.V33);
+  const float rho = w.phi * w.r1 + (1.f - w.phi) * w.r2;
+  const float cL2 = cL2_f(F, w.phi, rho, w.p, s.J2);
+  if (!(cL2 > 0.f) || !(rho > 0.f)) flag_bad(A.status, patch, i + pd.nx * j);
+  const float cL = sqrtf(fmaxf(cL2, 0.f));
+  float r = (fabsf(w.u) + cL) / (float)pd.dx;
+  if (DIM == 2) r += (fabsf(w.v) + cL) / (float)pd.dy;
+  return r;
+}
+
 template <int DIM, bool RX>
 __global__ void __launch_bounds__(SEG) k_cfl32(Phys P, PhysF F, StepArgs32 A, const int4* __restrict__ segs) {
   const int4 g = segs[blockIdx.x];
   const PatchDev pd = A.pd[g.x];
   const int i = g.z + threadIdx.x, j = g.y;
   float r = 0.f;
-  if (threadIdx.x < g.w) {
-    const PrimF w = cons_to_prim32<DIM, RX>(P, F, A.q64src, A.q32src, A.T, cidx(pd, i, j));
-    const StrainF s = strain_f(w.V11, w.V12, w.V21, w.V22, w.V33);
-    const float rho = w.phi * w.r1 + (1.f - w.phi) * w.r2;
-    const float cL2 = cL2_f(F, w.phi, rho, w.p, s.J2);
-    if (!(cL2 > 0.f) || !(rho > 0.f)) flag_bad(A.status, g.x, i + pd.nx * j);
-    const float cL = sqrtf(fmaxf(cL2, 0.f));
-    r = (fabsf(w.u) + cL) / (float)pd.dx;
-    if (DIM == 2) r += (fabsf(w.v) + cL) / (float)pd.dy;
-  }
+  if (threadIdx.x < g.w) r = cfl_rate32<DIM, RX>(P, F, A, pd, g.x, i, j);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
   if ((threadIdx.x & 31) == 0 && r > 0.f)
     atomicMax(A.rate + g.x, (unsigned long long)__double_as_longlong((double)r));
+}
+
+// State buffers of the persistent batch kernel: q^n (0) and two stage buffers.
+struct Bufs32 {
+  double* q64[3];
+  float* q32[3];
+};
+
+// Persistent 1D batch kernel: CTA b owns problem order[b] (the problems sorted
+// by length, longest first, so the block scheduler balances them) and runs
+// n_steps whole time steps of it in one launch: per step the CFL rate of its
+// cells (a CTA max, stored as the patch's rate; skipped for prescribed dt),
+// then the three stages, each over the problem's tiles tiles[tile0[p] ..
+// tile0[p + 1]) in turn, with the buffer rotation of the per-step path
+// (0 -> 1 -> 2 -> 0).  A problem's three state buffers stay in L2 between
+// stages and steps.  The tile arithmetic is stage32_tile and the rate that of
+// k_cfl32; compiled as another kernel, its multiply-add contractions may
+// differ, so the result matches the per-step launches to rounding.
+// scratch_last (tuning, n_steps = 1): the last stage writes buffer 1.
+template <bool RX, int TX, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_batch32(Phys P, PhysF F, StepArgs32 A, Bufs32 B,
+                                                      const int* __restrict__ order,
+                                                      const int* __restrict__ tile0,
+                                                      const int4* __restrict__ tiles, int n_steps,
+                                                      int scratch_last) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ float wmax[NT / 32];
+  const int p = order[blockIdx.x];
+  const int ta = tile0[p], tb = tile0[p + 1];
+  const PatchDev pd = A.pd[p];
+  for (int n = 0; n < n_steps; ++n) {
+    if (!A.dtfix) {
+      StepArgs32 a = A;
+      a.q64src = B.q64[0];
+      a.q32src = B.q32[0];
+      float r = 0.f;
+      for (int i = threadIdx.x; i < pd.nx; i += NT) r = fmaxf(r, cfl_rate32<1, RX>(P, F, a, pd, p, i, 0));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+      if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = r;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        float m = 0.f;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) m = fmaxf(m, wmax[w]);
+        A.rate[p] = (unsigned long long)__double_as_longlong((double)m);
+      }
+      __syncthreads();
+    }
+    for (int stg = 0; stg < 3; ++stg) {
+      StepArgs32 a = A;
+      const bool s0 = stg == 0, s1 = stg == 1, to1 = s0 || (!s1 && scratch_last);
+      a.q64src = s0 ? B.q64[0] : (s1 ? B.q64[1] : B.q64[2]);
+      a.q32src = s0 ? B.q32[0] : (s1 ? B.q32[1] : B.q32[2]);
+      a.q64n = B.q64[0];
+      a.q32n = B.q32[0];
+      a.q64dst = to1 ? B.q64[1] : (s1 ? B.q64[2] : B.q64[0]);
+      a.q32dst = to1 ? B.q32[1] : (s1 ? B.q32[2] : B.q32[0]);
+      a.a = s0 ? 0.0 : (s1 ? 0.75 : 1.0 / 3.0);
+      a.b = s0 ? 1.0 : (s1 ? 0.25 : 2.0 / 3.0);
+      a.last = stg == 2;
+      for (int t = ta; t < tb; ++t) {
+        stage32_tile<1, RX, TX, 1, NT, false>(P, F, a, tiles[t], sm);
+        __syncthreads();
+      }
+    }
+  }
 }
 
 }  // namespace dis

@@ -41,6 +41,7 @@ struct StepArgs {
   int* status;               // [flag, patch, cell]
   double a, b;               // q_dst = a q_n + b (q_src - dt D(q_src)), a = 0 -> no q_n
   int last;                  // apply plastic and reactive steps, record dt
+  double* E;                 // MUSCL-Hancock: evolved edge states, plane (2 d + side) NF + field
 };
 
 __device__ __forceinline__ long long cidx(const PatchDev& p, int i, int j) {
@@ -356,6 +357,188 @@ __global__ void __launch_bounds__(SEG) k_pack(const PatchDev* __restrict__ pds,
   const long long k = cidx(pd, i, j);
 #pragma unroll
   for (int c = 0; c < NF; ++c) dst[s0 + c * ncell] = q[c * T + k];
+}
+
+// ---------------------------------------------------------------------------
+// Single-stage MUSCL-Hancock update (the Runge-Kutta alternative with one
+// Riemann solve per face and step).  k_hancock, per padded cell within one
+// cell of the interior: the left and right edge states along each axis (MUSCL
+// on the primitives, MUSCL-BVD-THINC on phi, cell-centre state where not
+// hyperbolic), moved by -dt/2 D_c with D_c the operator of the cell evaluated
+// on its own edge states (physical fluxes, non-conservative terms with the
+// cell-centre coefficients), back to primitives (cell-centre state where not
+// hyperbolic), stored in E.  k_flux_h: the Riemann problem of each face
+// between the evolved edge states of its two cells; k_update (a = 0, b = 1,
+// last) completes the step.
+// ---------------------------------------------------------------------------
+// c_L^2 > 0 for a primitive state (the value face_state returns as cL).
+__device__ __forceinline__ bool hyperbolic(const Phys& P, const Prim& w) {
+  const Strain st = strain_of(w.V11, w.V12, w.V21, w.V22, w.V33);
+  const double rho = w.phi * w.r1 + (1.0 - w.phi) * w.r2;
+  return cL2_of(P, w.phi, rho, w.p, st.J2) > 0.0;
+}
+
+// Edge states of cell k along axis D (MUSCL, MUSCL-BVD-THINC on phi, the
+// cell-centre state wc where not hyperbolic) and their physical outputs.
+template <int DIM, bool RX, int D>
+__device__ __forceinline__ void hancock_edges(const Phys& P, const double* __restrict__ W, long long T,
+                                              long long k, const PatchDev& pd, const Prim& wc, Prim& lo,
+                                              Prim& hi, double* Fm, double* Fp) {
+  using L = Lay<DIM, RX>;
+  constexpr int NF = L::NF;
+  const long long st = D == 0 ? 1 : (long long)pd.pitch;  // along the axis
+  const long long sx = D == 0 ? (long long)pd.pitch : 1;  // across it
+  double B[3][5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) B[1][c] = W[L::PHI * T + k + (c - 2) * st];
+  const bool normals = DIM == 2 && P.thinc;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    B[0][c] = normals ? W[L::PHI * T + k + (c - 2) * st - sx] : 0.0;
+    B[2][c] = normals ? W[L::PHI * T + k + (c - 2) * st + sx] : 0.0;
+  }
+  double eL, eR;
+  cell_phi_edges<DIM, double>(B, P.thinc != 0, D == 0 ? pd.dx : pd.dy, D == 0 ? pd.dy : pd.dx, eL, eR);
+  Prim wm = load_prim<DIM, RX>(W, T, k - st);
+  Prim wp = load_prim<DIM, RX>(W, T, k + st);
+  Prim m = wc;
+  lo = wc;
+  hi = wc;
+#pragma unroll
+  for (int c = 0; c < NF; ++c) {
+    if (c == L::PHI) continue;
+    const double sl = minmod(prim_slot<DIM, RX>(m, c) - prim_slot<DIM, RX>(wm, c),
+                             prim_slot<DIM, RX>(wp, c) - prim_slot<DIM, RX>(m, c));
+    prim_slot<DIM, RX>(lo, c) = prim_slot<DIM, RX>(m, c) - 0.5 * sl;
+    prim_slot<DIM, RX>(hi, c) = prim_slot<DIM, RX>(m, c) + 0.5 * sl;
+  }
+  lo.phi = eL;
+  hi.phi = eR;
+  FState fl = face_state<D>(P, lo), fh = face_state<D>(P, hi);
+  const bool okl = fl.cL > 0.0, okh = fh.cL > 0.0;
+  if (!okl || !okh) {
+    const FState fc = face_state<D>(P, wc);
+    if (!okl) { lo = wc; fl = fc; }
+    if (!okh) { hi = wc; fh = fc; }
+  }
+  face_outputs<DIM, RX, D, double>(physical_faceout<D>(fl), Fm);
+  face_outputs<DIM, RX, D, double>(physical_faceout<D>(fh), Fp);
+}
+
+template <int DIM, bool RX>
+__global__ void __launch_bounds__(SEG) k_hancock(Phys P, StepArgs A, const int4* __restrict__ segs) {
+  using L = Lay<DIM, RX>;
+  constexpr int NF = L::NF;
+  constexpr int NO = n_face_out<DIM, RX>();
+  const int4 g = segs[blockIdx.x];
+  if (threadIdx.x >= g.w) return;
+  const PatchDev pd = A.pd[g.x];
+  const int i = g.z + threadIdx.x, j = g.y;
+  if (i < -1 || i > pd.nx || (DIM == 2 && (j < -1 || j > pd.ny))) return;
+  const long long T = A.T;
+  const double* __restrict__ W = A.W;
+  const long long k = cidx(pd, i, j);
+  const Prim wc = load_prim<DIM, RX>(W, T, k);
+  // edge states e[2 d] (left / lower), e[2 d + 1] (right / upper) and D_c of
+  // the cell from their physical outputs
+  Prim e[2 * DIM];
+  double D[NF];
+  double divu, bx, by = 0.0;
+  {
+    double Fm[NO], Fp[NO];
+    hancock_edges<DIM, RX, 0>(P, W, T, k, pd, wc, e[0], e[1], Fm, Fp);
+    const double ih = 1.0 / pd.dx;
+#pragma unroll
+    for (int c = 0; c < NF; ++c) D[c] = (Fp[c] - Fm[c]) * ih;
+    divu = (Fp[NF] - Fm[NF]) * ih;
+    bx = (Fp[NF + 1] - Fm[NF + 1]) * ih;
+    if constexpr (DIM == 2) by = (Fp[NF + 2] - Fm[NF + 2]) * ih;
+  }
+  if constexpr (DIM == 2) {
+    double Fm[NO], Fp[NO];
+    hancock_edges<DIM, RX, 1>(P, W, T, k, pd, wc, e[2], e[3], Fm, Fp);
+    const double ih = 1.0 / pd.dy;
+#pragma unroll
+    for (int c = 0; c < NF; ++c) D[c] += (Fp[c] - Fm[c]) * ih;
+    divu += (Fp[NF] - Fm[NF]) * ih;
+    bx += (Fp[NF + 1] - Fm[NF + 1]) * ih;
+    by += (Fp[NF + 2] - Fm[NF + 2]) * ih;
+  }
+  // cell-centre conservative coefficients (ghosts by the index map, reflective flips)
+  double q[NF];
+  {
+    bool fx = false, fy = false;
+    const int si = ghost_map(i, pd.nx, pd.bc[0], pd.bc[1], fx);
+    const int sj = DIM == 2 ? ghost_map(j, pd.ny, pd.bc[2], pd.bc[3], fy) : 0;
+    const long long ks = cidx(pd, si, sj);
+#pragma unroll
+    for (int c = 0; c < NF; ++c) q[c] = A.qsrc[c * T + ks];
+    if (fx) {
+      q[L::MX] = -q[L::MX];
+      if constexpr (DIM == 2) { q[L::V12] = -q[L::V12]; q[L::V21] = -q[L::V21]; }
+    }
+    if constexpr (DIM == 2) {
+      if (fy) { q[L::MY] = -q[L::MY]; q[L::V12] = -q[L::V12]; q[L::V21] = -q[L::V21]; }
+    }
+  }
+  const double rho = q[L::A1] + q[L::A2];
+  const double uc = q[L::MX] / rho;
+  double vc = 0.0;
+  if constexpr (DIM == 2) vc = q[L::MY] / rho;
+  const double t23 = 2.0 / 3.0;
+  D[L::PHI] -= q[L::PHI] * divu;
+  D[L::V11] -= t23 * q[L::V11] * divu - uc * bx;
+  D[L::V22] -= t23 * q[L::V22] * divu - vc * by;
+  D[L::V33] -= t23 * q[L::V33] * divu;
+  if constexpr (DIM == 2) {
+    D[L::V12] -= t23 * q[L::V12] * divu - uc * by;
+    D[L::V21] -= t23 * q[L::V21] * divu - vc * bx;
+  }
+  const double dt = A.dtfix ? A.dtfix[g.x] : P.cfl / __longlong_as_double((long long)A.rate[g.x]);
+  const double h = 0.5 * dt;
+#pragma unroll
+  for (int s = 0; s < 2 * DIM; ++s) {
+    double v[NF];
+#pragma unroll
+    for (int c = 0; c < NF; ++c) v[c] = prim_slot<DIM, RX>(e[s], c);
+    cons_of<DIM, RX, double>(P, v);
+#pragma unroll
+    for (int c = 0; c < NF; ++c) v[c] -= h * D[c];
+    Prim w = prim_of<DIM, RX, double>(P, v);
+    if (!hyperbolic(P, w)) w = wc;
+#pragma unroll
+    for (int c = 0; c < NF; ++c) A.E[((long long)s * NF + c) * T + k] = prim_slot<DIM, RX>(w, c);
+  }
+}
+
+template <int DIM, bool RX, int DIR>
+__global__ void __launch_bounds__(SEG) k_flux_h(Phys P, StepArgs A, const int4* __restrict__ segs) {
+  using L = Lay<DIM, RX>;
+  constexpr int NF = L::NF;
+  const int4 g = segs[blockIdx.x];
+  if (threadIdx.x >= g.w) return;
+  const PatchDev pd = A.pd[g.x];
+  const long long T = A.T;
+  const int f = (DIR == 0 ? g.z : g.y) + (DIR == 0 ? threadIdx.x : 0);
+  const int col = DIR == 0 ? g.y : g.z + threadIdx.x;
+  const int a = (DIR == 0 ? f : g.y) - 1;
+  const long long ka = DIR == 0 ? cidx(pd, a, col) : cidx(pd, col, a);
+  const long long kb = DIR == 0 ? cidx(pd, a + 1, col) : cidx(pd, col, a + 1);
+  Prim wl{}, wr{};
+#pragma unroll
+  for (int c = 0; c < NF; ++c) {
+    prim_slot<DIM, RX>(wl, c) = A.E[((long long)(2 * DIR + 1) * NF + c) * T + ka];
+    prim_slot<DIM, RX>(wr, c) = A.E[((long long)(2 * DIR) * NF + c) * T + kb];
+  }
+  constexpr int NO = n_face_out<DIM, RX>();
+  double out[NO];
+  riemann_outputs<DIM, RX, DIR>(face_state<DIR>(P, wl), face_state<DIR>(P, wr), out);
+  double* F = DIR == 0 ? A.Fx : A.Fy;
+  const long long NFc = DIR == 0 ? A.NFX : A.NFY;
+  const long long fi = DIR == 0 ? pd.fxoff + (long long)col * (pd.nx + 1) + f
+                                : pd.fyoff + (long long)g.y * pd.nx + col;
+#pragma unroll
+  for (int c = 0; c < NO; ++c) F[c * NFc + fi] = out[c];
 }
 
 }  // namespace dis

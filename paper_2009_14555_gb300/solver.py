@@ -41,7 +41,7 @@ class Solver:
     """Diffuse-interface step on a batch of patches (see include/dis.h)."""
 
     def __init__(self, dim, patches, materials, reactive_material=-1, cfl=0.8, thinc=False,
-                 precision="fp64", device=None):
+                 precision="fp64", device=None, scheme="rk3"):
         if not torch.cuda.is_available():
             raise RuntimeError("Solver needs a CUDA device (no CPU fallback)")
         dev = torch.device(device or "cuda")
@@ -54,7 +54,8 @@ class Solver:
         self.reactive = reactive_material >= 0
         self.nf = (11 if dim == 2 else 8) + (1 if self.reactive else 0)
         prec = {"fp64": L.DIS_FP64, "fp32_bulk": L.DIS_FP32_BULK}[precision]
-        opts = L.DisOptions(float(cfl), int(bool(thinc)), prec)
+        sch = {"rk3": L.DIS_RK3, "hancock": L.DIS_HANCOCK}[scheme]
+        opts = L.DisOptions(float(cfl), int(bool(thinc)), prec, sch)
         self.stream = torch.cuda.current_stream(self.device)
         self.ctx = L.dis_create(dim, [_patch(p, dim) for p in self.patches], reactive_material, opts,
                                 self.stream.cuda_stream)
@@ -70,6 +71,7 @@ class Solver:
 
     @classmethod
     def from_workload(cls, wl, precision="fp64", **kw):
+        kw.setdefault("scheme", getattr(wl, "scheme", "rk3"))
         return cls(wl.dim, wl.patches, wl.materials, wl.reactive_material, wl.cfl, wl.thinc,
                    precision, **kw)
 
@@ -133,6 +135,19 @@ class Solver:
     def set_variant(self, v):
         """Fix the FP32-bulk stage variant (-1: tune on the next step)."""
         L.check(L.load().dis_set_variant(self.ctx, int(v)))
+
+    def set_schedule(self, schedule):
+        """1D FP32-bulk batches: 0 per-step launches, 1 the persistent batch
+        kernel, -1 chosen by the tuner (include/dis.h: dis_set_schedule)."""
+        L.check(L.load().dis_set_schedule(self.ctx, int(schedule)))
+
+    def schedule(self):
+        """(schedule in use, tuned one-step ms of the persistent kernel per
+        variant) (include/dis.h: dis_schedule)."""
+        sc = ctypes.c_int(0)
+        ms = np.zeros(L.DIS_NVARIANTS, np.float64)
+        L.check(L.load().dis_schedule(self.ctx, ctypes.byref(sc), ms.ctypes.data))
+        return sc.value, ms
 
     def check(self):
         return L.dis_check(self.ctx)

@@ -90,6 +90,7 @@ class Workload:
     thinc: bool
     reactive_material: int = -1          # 0-based index of the reactive material, -1 none
     extra: dict = field(default_factory=dict)
+    scheme: str = "rk3"                  # hyperbolic update: "rk3" (the paper's) or "hancock"
 
     @property
     def reactive(self) -> bool:

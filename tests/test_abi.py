@@ -49,6 +49,26 @@ def test_create_validates_arguments(lib):
     assert lib.dis_create(1, 1, tiny, -1, ctypes.byref(opts), None, ctypes.byref(out)) == L.DIS_EINVAL
     assert lib.dis_create(1, 0, arr, -1, ctypes.byref(opts), None, ctypes.byref(out)) == L.DIS_EINVAL
     assert lib.dis_create(1, 1, arr, 2, ctypes.byref(opts), None, ctypes.byref(out)) == L.DIS_EINVAL
+    unknown = L.DisOptions(0.8, 0, 0, 7)
+    assert lib.dis_create(1, 1, arr, -1, ctypes.byref(unknown), None, ctypes.byref(out)) == L.DIS_EINVAL
+    assert b"scheme" in lib.dis_last_error()
+    hancock32 = L.DisOptions(0.8, 0, L.DIS_FP32_BULK, L.DIS_HANCOCK)
+    assert lib.dis_create(1, 1, arr, -1, ctypes.byref(hancock32), None, ctypes.byref(out)) == L.DIS_EINVAL
+    assert b"float64" in lib.dis_last_error()
+
+
+def test_hancock_workspace_holds_the_evolved_edge_states(lib):
+    """A MUSCL-Hancock context adds 2 x dim x nf planes of the padded cells."""
+    out = ctypes.c_void_p()
+    arr = (L.DisPatch * 1)(_patch(100))
+    sizes = []
+    for scheme in (L.DIS_RK3, L.DIS_HANCOCK):
+        opts = L.DisOptions(0.8, 0, L.DIS_FP64, scheme)
+        assert lib.dis_create(1, 1, arr, -1, ctypes.byref(opts), None, ctypes.byref(out)) == L.DIS_OK
+        sizes.append(lib.dis_workspace_bytes(out))
+        lib.dis_destroy(out)
+    T = (100 + 6 + 31) // 32 * 32
+    assert sizes[1] - sizes[0] >= 2 * 1 * 8 * 8 * T
 
 
 def test_host_side_sizes_and_materials(lib):

@@ -127,6 +127,71 @@ def test_fp32_every_1d_variant(variant):
     assert (worst <= bars).all(), dict(zip(names, worst))
 
 
+@pytest.mark.parametrize("variant", (1, 6))
+def test_fp32_persistent_batch_matches_per_step_launches(variant):
+    """The persistent batch kernel (all steps of a call in one launch, one CTA
+    per problem, longest first) gives the state and time steps of the
+    per-step launches to rounding, with CFL and with prescribed dt, on an
+    uneven batch (problems shorter and longer than a tile), and meets the
+    oracle bar.  The two kernels run the same tile code but are compiled
+    separately, so the code generator may contract multiply-adds differently:
+    measured after 30 steps 8e-11 (float64 contractions only, variant 1) and
+    5e-7 (float32 ones too, variant 6) relative; bar 1e-5, float32 rounding."""
+    from paper_2009_14555_gb300.solver import Solver
+    wl = W.batched_riemann_1d(40, seed=6, steps=30, nmin=16, nmax=1200)
+    prims = [p.prim for p in wl.patches]
+    runs = {}
+    for sched in (0, 1):
+        s = Solver.from_workload(wl, precision="fp32_bulk")
+        s.set_variant(variant)
+        s.set_schedule(sched)
+        s.set_prim(prims)
+        dts = [s.step(10, return_dt=True) for _ in range(3)]
+        assert s.launches == (1 if sched == 1 else 10 * 4)
+        assert s.schedule()[0] == sched
+        rc, bp, bc = s.check()
+        assert rc == 0, (bp, bc)
+        cfl_state = s.get_state()
+        s.set_prim(prims)
+        s.step_fixed_dt(7, dts[0])
+        fixed_state = s.get_state()
+        runs[sched] = (cfl_state, np.array(dts), fixed_state, s.get_arrays())
+        s.close()
+    nf = len(W.cons_names(wl.dim, wl.reactive))
+    for k in (0, 2):
+        a, b = runs[0][k].reshape(nf, -1), runs[1][k].reshape(nf, -1)
+        rel = np.abs(a - b).max(axis=1) / np.abs(a).max(axis=1)
+        RESULTS[f"1d_batch_40_schedules_max_rel_diff_{'cfl' if k == 0 else 'fixed'}_variant{variant}"] = \
+            rel.tolist()
+        assert rel.max() <= 1e-5, (k, rel)
+    np.testing.assert_allclose(runs[0][1], runs[1][1], rtol=1e-5)
+    if "batch_40" not in _ORACLE:
+        _ORACLE["batch_40"] = oracle_run(wl, 30)[0]
+    s = Solver.from_workload(wl, precision="fp32_bulk")
+    s.set_variant(variant)
+    s.set_schedule(1)
+    s.set_prim(prims)
+    s.step(30)
+    g = s.get_arrays()
+    s.close()
+    o = _ORACLE["batch_40"]
+    names = W.cons_names(wl.dim, wl.reactive)
+    bars = np.array([TOL32_PARTIAL if n in ("ar1", "ar2", "arl") else TOL32 for n in names])
+    worst = np.zeros(len(names))
+    for k in range(len(o)):
+        worst = np.maximum(worst, cons_l1(wl, g[k], o[k]))
+    RESULTS[f"1d_batch_40_30steps_persistent_variant{variant}"] = dict(steps=30, l1=[float(x) for x in worst])
+    assert (worst <= bars).all(), dict(zip(names, worst))
+
+
+def test_fp32_persistent_schedule_rejected_in_2d():
+    from paper_2009_14555_gb300.solver import Solver
+    s = Solver.from_workload(W.reactive_plate_2d(16, 8, steps=1), precision="fp32_bulk")
+    with pytest.raises(RuntimeError):
+        s.set_schedule(1)
+    s.close()
+
+
 def test_fp32_variants_agree_at_full_size():
     """On the full 2048 x 1024 reactive plate (thousands of tiles, many waves
     of CTAs) every variant gives the bit-identical state after 3 steps: the

@@ -1,0 +1,135 @@
+"""GPU float64 MUSCL-Hancock step (DIS_HANCOCK) against the oracle's
+MUSCL-Hancock update (oracle/hancock.py), through the C ABI: per-field
+relative L1 <= 1e-10 after the stated steps, or the self-calibrated bar of
+tests/test_parity_gpu.py for THINC next to a very stiff solid."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import closures as OC
+from oracle import scheme as OS
+from paper_2009_14555_gb300 import workloads as W
+from tests.parity_util import cons_l1, oracle_run
+from tests.test_parity_gpu import TOL, assert_parity, gpu_run
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_spread_per_step(wl, steps, o):
+    """Per-field L1 between the oracle and the oracle whose state gets a
+    one-ulp random-sign perturbation of every value after every step - the
+    size of the differences two correct float64 programs accumulate when the
+    scheme amplifies round-off (patch 0)."""
+    p = wl.patches[0]
+    grid = OS.grid_of(p, wl.dim)
+    q = OC.prim_to_cons(OS.prim_from_array(p.prim, wl.dim, wl.reactive), wl.materials)
+    rng = np.random.default_rng(7)
+    for _ in range(steps):
+        q, _ = OS.step(q, grid, wl.materials, dict(cfl=wl.cfl, thinc=wl.thinc, scheme="hancock"))
+        q = {k: v * (1 + torch.sign(torch.as_tensor(rng.standard_normal(tuple(v.shape)))) * 2.0 ** -52)
+             for k, v in q.items()}
+    return cons_l1(wl, OS.cons_to_array(q, wl.dim, wl.reactive).numpy(), o[0])
+
+
+def hancock(wl):
+    wl.scheme = "hancock"
+    return wl
+
+
+def test_1d_solid_gas_100_steps():
+    assert_parity(hancock(W.solid_gas_1d(1000, steps=100)), 100)
+
+
+def test_1d_water_air_thinc():
+    water = W.material(4.4, p_inf=6e8)
+    wl = W.riemann_1d(257, dict(mat=0, rho=1000.0, u=0.0, p=1e9, rho2=50.0),
+                      dict(mat=1, rho=50.0, u=0.0, p=1e5, rho1=1000.0), x_int=0.7, cfl=0.6,
+                      thinc=True, materials=[water, W.AIR])
+    assert_parity(hancock(wl), 100)
+
+
+@pytest.mark.parametrize("bc", [W.BC_PERIODIC, W.BC_REFLECTIVE])
+def test_1d_boundaries(bc):
+    if bc == W.BC_PERIODIC:
+        left, right = dict(mat=0, rho=8000.0, u=100.0, p=1e5), dict(mat=1, rho=1.2, u=100.0, p=3e5)
+    else:
+        left, right = dict(mat=0, rho=8000.0, u=200.0, p=1e5), dict(mat=1, rho=1.2, u=-300.0, p=3e5)
+    assert_parity(hancock(W.riemann_1d(131, left, right, bc=bc, thinc=False)), 40)
+
+
+def test_2d_shock_disc():
+    wl = W.shock_disc_2d(40, steps=30)
+    wl.thinc = False
+    assert_parity(hancock(wl), 30)
+
+
+def test_2d_shock_disc_thinc():
+    assert_parity(hancock(W.shock_disc_2d(40, steps=30)), 30, calibrate=True)
+
+
+def test_2d_ragged_reflective():
+    """Shock started inside the disc (the solid's two halves collide), mixed
+    boundaries.  The MUSCL-Hancock update amplifies round-off here: GPU and
+    oracle agree to 1e-16 after two steps, and after 20 steps differ exactly
+    as much as the oracle differs from itself under one-ulp perturbations of
+    its state after every step (1.8e-8 in the solid's partial density and
+    the energy; the Runge-Kutta update reaches 3e-9 under the same
+    perturbation).  Bar: strict after 2 steps, 10x that spread after 20."""
+    wl = W.shock_disc_2d(36, steps=20, shock_x=0.4)
+    wl.thinc = False
+    wl.patches[0].bc = (W.BC_TRANSMISSIVE, W.BC_REFLECTIVE, W.BC_REFLECTIVE, W.BC_PERIODIC)
+    hancock(wl)
+    assert_parity(wl, 2)
+    g, _, _ = gpu_run(wl, 20)
+    o, _ = oracle_run(wl, 20)
+    err = cons_l1(wl, g[0], o[0])
+    spread = oracle_spread_per_step(wl, 20, o)
+    assert (err <= np.maximum(TOL, 10.0 * spread)).all(), (err, spread)
+
+
+def test_2d_reactive():
+    wl = W.reactive_plate_2d(64, 32, steps=20)
+    wl.thinc = False
+    assert_parity(hancock(wl), 20)
+
+
+def test_2d_reactive_thinc():
+    assert_parity(hancock(W.reactive_plate_2d(64, 32, steps=20)), 20, calibrate=True)
+
+
+def test_batched_1d_subset():
+    assert_parity(hancock(W.batched_riemann_1d(12, seed=3, steps=40, nmin=16, nmax=300)), 40)
+
+
+def test_fixed_dt_and_launch_count():
+    """Prescribed dt, and one step = prim + predictor + one flux launch per
+    axis + update (4 launches in 1D, 5 in 2D)."""
+    from paper_2009_14555_gb300.solver import Solver
+    wl = hancock(W.solid_gas_1d(200, steps=10))
+    dt = 2e-7
+    s = Solver.from_workload(wl)
+    s.set_prim([p.prim for p in wl.patches])
+    s.step_fixed_dt(10, dt)
+    assert s.launches == 10 * 4
+    g = s.get_arrays()
+    s.close()
+    o, _ = oracle_run(wl, 10, dt_list=[[dt] * 10])
+    assert cons_l1(wl, g[0], o[0]).max() <= TOL
+    wl2 = hancock(W.shock_disc_2d(16, steps=1))
+    s = Solver.from_workload(wl2)
+    s.set_prim([p.prim for p in wl2.patches])
+    s.step(2)
+    assert s.launches == 2 * 5
+    s.close()
+
+
+def test_hancock_refuses_adjoint_and_fp32():
+    from paper_2009_14555_gb300.solver import Solver
+    wl = hancock(W.solid_gas_1d(64, steps=2))
+    s = Solver.from_workload(wl)
+    s.set_prim([p.prim for p in wl.patches])
+    with pytest.raises(RuntimeError):
+        s.adj_forward(2, every=1, material=0)
+    s.close()
+    with pytest.raises(RuntimeError):
+        Solver.from_workload(wl, precision="fp32_bulk")
