@@ -30,10 +30,10 @@ METRIC = "cell-updates/s and % HBM peak, FP32-bulk vs plain FP64 on one GB300 at
 # step in the ncu launch list).  Its arithmetic per face, counted by ncu on the
 # 1024x512 reactive plate (2 x DFMA + DADD + DMUL per face; see
 # profiles/k_flux_2d_reactive_plate_1024x512.md):
-FLUX_FP64_FLOP_PER_FACE = 1193.0
-# DRAM bytes per x-flux launch from the same capture (73.8 MB for 524800
+FLUX_FP64_FLOP_PER_FACE = 868.1
+# DRAM bytes per x-flux launch from the same capture (73.07 MB for 524800
 # faces), per face; traffic grows with the face count.
-FLUX_DRAM_BYTES_PER_FACE = 73.80e6 / 524800
+FLUX_DRAM_BYTES_PER_FACE = 73.07e6 / 524800
 # FP64 peak: 152 SMs x 2 DFMA/cycle (ncu sm__sass_thread_inst_executed_op_dfma
 # peak_sustained = 304/cycle) x 2 FLOP x 2.07 GHz maximum SM clock.
 FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
@@ -47,9 +47,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # per cell-stage on the full 2048 x 1024 grid.  The register budget (3 or 4
 # CTAs per SM) does not change these counts.
 STAGE32 = {
-    (16, 15, False): dict(flop32=1601.7, flop64=27.97, dram=135.7),
-    (16, 15, True): dict(flop32=1436.9, flop64=17.19, dram=186.3),
-    (32, 7, True): dict(flop32=1461.8, flop64=17.19, dram=185.9),
+    (16, 15, False): dict(flop32=1422.8, flop64=27.97, dram=133.6),
+    (16, 15, True): dict(flop32=1258.0, flop64=17.18, dram=184.7),
+    (32, 7, True): dict(flop32=1279.1, flop64=17.18, dram=184.4),
 }
 UNIT = "cell-updates/s"
 NX, NY = 2048, 1024

@@ -102,15 +102,18 @@ __device__ __forceinline__ void face_phi(const T (&B)[3][6], bool thinc, double 
   CandT<T> c[4];
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
-    T beta = 2.51;  // beta0 |n_d| + 0.01 with |n_d| = 1 in 1D
-    if (DIM == 2 && thinc) {
-      const T dn = (B[2][s + 2] + 2.0 * B[1][s + 2] + B[0][s + 2]) - (B[2][s] + 2.0 * B[1][s] + B[0][s]);
-      const T dt_ = (B[2][s + 2] + 2.0 * B[2][s + 1] + B[2][s]) - (B[0][s + 2] + 2.0 * B[0][s + 1] + B[0][s]);
-      const T gn = dn / hn, gt = dt_ / ht;
-      const T nrm = sqrt(gn * gn + gt * gt);
-      beta = 2.5 * (nrm == 0.0 ? T(1.0) : fabs(gn) / nrm) + 0.01;
-    }
-    c[s] = phi_cand(B[1][s], B[1][s + 1], B[1][s + 2], beta, thinc);
+    auto beta_of = [&]() -> T {
+      T beta = 2.51;  // beta0 |n_d| + 0.01 with |n_d| = 1 in 1D
+      if (DIM == 2 && thinc) {
+        const T dn = (B[2][s + 2] + 2.0 * B[1][s + 2] + B[0][s + 2]) - (B[2][s] + 2.0 * B[1][s] + B[0][s]);
+        const T dt_ = (B[2][s + 2] + 2.0 * B[2][s + 1] + B[2][s]) - (B[0][s + 2] + 2.0 * B[0][s + 1] + B[0][s]);
+        const T gn = dn / hn, gt = dt_ / ht;
+        const T nrm = sqrt(gn * gn + gt * gt);
+        beta = 2.5 * (nrm == 0.0 ? T(1.0) : fabs(gn) / nrm) + 0.01;
+      }
+      return beta;
+    };
+    c[s] = phi_cand_lazy(B[1][s], B[1][s + 1], B[1][s + 2], beta_of, thinc);
   }
   T Lt, Rt;
   bvd(c[0], c[1], c[2], Lt, Rt);
@@ -129,15 +132,18 @@ __device__ __forceinline__ void cell_phi_edges(const T (&B)[3][5], bool thinc, d
   CandT<T> c[3];
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
-    T beta = 2.51;
-    if (DIM == 2 && thinc) {
-      const T dn = (B[2][s + 2] + 2.0 * B[1][s + 2] + B[0][s + 2]) - (B[2][s] + 2.0 * B[1][s] + B[0][s]);
-      const T dt_ = (B[2][s + 2] + 2.0 * B[2][s + 1] + B[2][s]) - (B[0][s + 2] + 2.0 * B[0][s + 1] + B[0][s]);
-      const T gn = dn / hn, gt = dt_ / ht;
-      const T nrm = sqrt(gn * gn + gt * gt);
-      beta = 2.5 * (nrm == 0.0 ? T(1.0) : fabs(gn) / nrm) + 0.01;
-    }
-    c[s] = phi_cand(B[1][s], B[1][s + 1], B[1][s + 2], beta, thinc);
+    auto beta_of = [&]() -> T {
+      T beta = 2.51;
+      if (DIM == 2 && thinc) {
+        const T dn = (B[2][s + 2] + 2.0 * B[1][s + 2] + B[0][s + 2]) - (B[2][s] + 2.0 * B[1][s] + B[0][s]);
+        const T dt_ = (B[2][s + 2] + 2.0 * B[2][s + 1] + B[2][s]) - (B[0][s + 2] + 2.0 * B[0][s + 1] + B[0][s]);
+        const T gn = dn / hn, gt = dt_ / ht;
+        const T nrm = sqrt(gn * gn + gt * gt);
+        beta = 2.5 * (nrm == 0.0 ? T(1.0) : fabs(gn) / nrm) + 0.01;
+      }
+      return beta;
+    };
+    c[s] = phi_cand_lazy(B[1][s], B[1][s + 1], B[1][s + 2], beta_of, thinc);
   }
   bvd(c[0], c[1], c[2], eL, eR);
 }

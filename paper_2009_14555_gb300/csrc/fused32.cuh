@@ -50,18 +50,21 @@ __device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__
     CandF c[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
-      float beta = 2.51f;
-      if (DIM == 2 && P.thinc) {
-        const int k = k0 + (s - 1) * sx;
-        const float dn = (Wv(L::PHI, k + sx + sy) + 2.f * Wv(L::PHI, k + sx) + Wv(L::PHI, k + sx - sy)) -
-                         (Wv(L::PHI, k - sx + sy) + 2.f * Wv(L::PHI, k - sx) + Wv(L::PHI, k - sx - sy));
-        const float dt_ = (Wv(L::PHI, k + sy + sx) + 2.f * Wv(L::PHI, k + sy) + Wv(L::PHI, k + sy - sx)) -
-                          (Wv(L::PHI, k - sy + sx) + 2.f * Wv(L::PHI, k - sy) + Wv(L::PHI, k - sy - sx));
-        const float gn = dn / dxn, gt = dt_ / dxt;
-        const float nrm = sqrtf(gn * gn + gt * gt);
-        beta = 2.5f * (nrm == 0.f ? 1.f : fabsf(gn) / nrm) + 0.01f;
-      }
-      c[s] = phi_cand_f(ph[s], ph[s + 1], ph[s + 2], beta, P.thinc != 0);
+      auto beta_of = [&]() -> float {
+        float beta = 2.51f;
+        if (DIM == 2 && P.thinc) {
+          const int k = k0 + (s - 1) * sx;
+          const float dn = (Wv(L::PHI, k + sx + sy) + 2.f * Wv(L::PHI, k + sx) + Wv(L::PHI, k + sx - sy)) -
+                           (Wv(L::PHI, k - sx + sy) + 2.f * Wv(L::PHI, k - sx) + Wv(L::PHI, k - sx - sy));
+          const float dt_ = (Wv(L::PHI, k + sy + sx) + 2.f * Wv(L::PHI, k + sy) + Wv(L::PHI, k + sy - sx)) -
+                            (Wv(L::PHI, k - sy + sx) + 2.f * Wv(L::PHI, k - sy) + Wv(L::PHI, k - sy - sx));
+          const float gn = dn / dxn, gt = dt_ / dxt;
+          const float nrm = sqrtf(gn * gn + gt * gt);
+          beta = 2.5f * (nrm == 0.f ? 1.f : fabsf(gn) / nrm) + 0.01f;
+        }
+        return beta;
+      };
+      c[s] = phi_cand_f(ph[s], ph[s + 1], ph[s + 2], beta_of, P.thinc != 0);
     }
     float Lt, Rt;
     bvd_f(c[0], c[1], c[2], Lt, Rt);

@@ -163,8 +163,9 @@ struct CandT {
 };
 using Cand = CandT<double>;
 
-template <class T>
-__device__ __forceinline__ CandT<T> phi_cand(T qm, T qc, T qp, T beta, bool thinc) {
+// beta_of() gives the THINC steepness; it is evaluated only in a mixed cell.
+template <class T, class BetaFn>
+__device__ __forceinline__ CandT<T> phi_cand_lazy(T qm, T qc, T qp, const BetaFn& beta_of, bool thinc) {
   CandT<T> c;
   const T s = minmod(qc - qm, qp - qc);
   c.mL = qc - 0.5 * s;
@@ -176,6 +177,7 @@ __device__ __forceinline__ CandT<T> phi_cand(T qm, T qc, T qp, T beta, bool thin
     const T jump = fmax(qm, qp) - qmin;
     const T C = (qc - qmin + 1e-20) / (jump + 1e-20);
     if (C > 1e-5 && C < 1.0 - 1e-5 && (qp - qc) * (qc - qm) > 0.0) {
+      const T beta = beta_of();
       const T th = (qp - qm) > 0.0 ? T(1.0) : T(-1.0);
       const T B = exp(th * beta * (2.0 * C - 1.0));
       const T tb = tanh(beta);
@@ -185,6 +187,11 @@ __device__ __forceinline__ CandT<T> phi_cand(T qm, T qc, T qp, T beta, bool thin
     }
   }
   return c;
+}
+
+template <class T>
+__device__ __forceinline__ CandT<T> phi_cand(T qm, T qc, T qp, T beta, bool thinc) {
+  return phi_cand_lazy(qm, qc, qp, [&]() { return beta; }, thinc);
 }
 
 // BVD choice for the middle cell: THINC only if its total boundary variation

@@ -72,7 +72,9 @@ struct CandF {
   float mL, mR, tL, tR;
 };
 
-__device__ __forceinline__ CandF phi_cand_f(float qm, float qc, float qp, float beta, bool thinc) {
+// beta_of() gives the THINC steepness; it is evaluated only in a mixed cell.
+template <class BetaFn>
+__device__ __forceinline__ CandF phi_cand_f(float qm, float qc, float qp, const BetaFn& beta_of, bool thinc) {
   CandF c;
   const float s = minmod_f(qc - qm, qp - qc);
   c.mL = qc - 0.5f * s;
@@ -84,6 +86,7 @@ __device__ __forceinline__ CandF phi_cand_f(float qm, float qc, float qp, float 
     const float jump = fmaxf(qm, qp) - qmin;
     const float C = (qc - qmin + 1e-20f) / (jump + 1e-20f);
     if (C > 1e-5f && C < 1.f - 1e-5f && (qp - qc) * (qc - qm) > 0.f) {
+      const float beta = beta_of();
       const float th = (qp - qm) > 0.f ? 1.f : -1.f;
       const float B = expf(th * beta * (2.f * C - 1.f));
       const float tb = tanhf(beta);
