@@ -226,7 +226,7 @@ int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
  * returns it in J_out (may be NULL).  dt_out (host, n_steps x n_patches, may
  * be NULL) receives the time steps.  Leaves the context at the final state,
  * like dis_step.  Device memory: (ceil(n_steps / checkpoint_every) +
- * checkpoint_every + 8) states, allocated here, kept for dis_adjoint and
+ * 4 checkpoint_every + 8) states, allocated here, kept for dis_adjoint and
  * released by dis_destroy.  FP32-bulk contexts checkpoint their states in
  * float64 (plus float64 primitive and face buffers for the reverse sweep).
  * Returns DIS_EINVAL (bad arguments, or a DIS_HANCOCK context: the adjoint
@@ -251,11 +251,12 @@ int dis_adj_forward(dis_ctx* ctx, int n_steps, int checkpoint_every, int objecti
 int dis_adjoint(dis_ctx* ctx, const double* qbar_final, int qbar_on_device, double jbar, int out_kind,
                 double* grad_init, int grad_on_device, double* grad_params, unsigned param_mask);
 
-/* Diagnostic: with on != 0, later dis_adjoint calls reverse the face Riemann
- * problems, the face-state map and the primitive recovery with dual numbers
- * (one forward evaluation per input direction, the reference form) instead
- * of the hand-written reverses; both give the same gradient up to rounding.
- * Returns DIS_EINVAL for a NULL context. */
+/* Diagnostic: with on != 0, later dis_adjoint calls reverse every local map
+ * (face Riemann problems, face states, THINC-BVD edge values, primitive
+ * recovery, source steps) with dual numbers (one forward evaluation per input
+ * direction, the reference form) instead of the hand-written reverses; both
+ * give the same gradient up to rounding.  Returns DIS_EINVAL for a NULL
+ * context. */
 int dis_adj_reference(dis_ctx* ctx, int on);
 
 /* Largest patch count accepted by dis_cfl_dt_static. */

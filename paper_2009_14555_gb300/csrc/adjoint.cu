@@ -7,10 +7,11 @@
 // accumulated on the device.
 // Reverse: segments of K steps are taken last to first.  A segment is
 // recomputed from its checkpoint with the recorded dt (bit-identical to the
-// forward run); then, step by step backwards, the three stage inputs and the
-// pre-source state are recomputed and the stages reversed (adjoint.cuh).
-// Memory: (number of checkpoints + K + 8) states plus the face coefficients,
-// all library-owned and released by dis_destroy.
+// forward run), keeping each step's stage inputs and pre-source state; then,
+// step by step backwards, the primitives and face outputs of each stage input
+// are recomputed and the stages reversed (adjoint.cuh).
+// Memory: (number of checkpoints + 4 K + 8) states plus the face
+// coefficients, all library-owned and released by dis_destroy.
 // FP32-bulk contexts: the forward run is the FP32-bulk step; its states are
 // checkpointed in float64 and the reverse sweep recomputes each segment with
 // the float64 step from those checkpoints (its own float64 primitive and face
@@ -35,7 +36,8 @@ struct dis_adj {
   size_t mem_bytes = 0;
   double* ck = nullptr;   // n_ck checkpoints
   double* seg = nullptr;  // every + 1 states of one segment
-  double* st[3] = {nullptr, nullptr, nullptr};  // q1, q3, pre-source state of one step
+  double* st[3] = {nullptr, nullptr, nullptr};  // scratch stage states of one step
+  double* stg = nullptr;  // per step of a segment: q1, q3 and the pre-source state
   double* ob = nullptr;
   double* xb = nullptr;
   double* acc = nullptr;
@@ -79,12 +81,13 @@ int adj_alloc(dis_ctx* c, int n_steps, int every) {
   dis_adj* d = c->adj;
   const size_t S = sizeof(double) * (size_t)c->nf * c->T;
   const int n_ck = (n_steps + every - 1) / every;
-  // states: checkpoints, the segment, q1 / q3 / pre-source, obar / xbar / qn_acc, Wbar
+  // states: checkpoints, the segment, its stage states (3 per step), scratch
+  // q1 / q3 / pre-source, obar / xbar / qn_acc, Wbar
   const size_t nfo = (size_t)(c->nf + n_extra(c->dim));
   const size_t own = c->fp32 ? 2 * a256(S) + a256(sizeof(double) * nfo * c->NFX) +
                                    a256(sizeof(double) * nfo * std::max<long long>(1, c->NFY))
                              : 0;
-  const size_t need = a256(S) * (size_t)(n_ck + (every + 1) + 7) + a256(sizeof(double) * nfo * c->T) +
+  const size_t need = a256(S) * (size_t)(n_ck + (every + 1) + 3 * every + 7) + a256(sizeof(double) * nfo * c->T) +
                       a256(sizeof(double) * (size_t)n_steps * c->np) + a256(sizeof(double)) +
                       a256(sizeof(double) * NPARAM) + own;
   if (need > d->mem_bytes) {
@@ -107,6 +110,7 @@ int adj_alloc(dis_ctx* c, int n_steps, int every) {
   };
   d->ck = take(S * n_ck);
   d->seg = take(S * (every + 1));
+  d->stg = take(S * 3 * (size_t)every);
   for (int k = 0; k < 3; ++k) d->st[k] = take(S);
   d->ob = take(S);
   d->xb = take(S);
@@ -232,10 +236,12 @@ int adj_forward(dis_ctx* c, int n_steps, int mat, bool prescribed) {
   return DIS_OK;
 }
 
-// Face and primitive reverse kernels of one stage (REF: dual-number reference
-// form of the hand-reversed local maps).
+// Reverse kernels of one stage (REF: dual-number reference form of the
+// hand-reversed local maps).
 template <int DIM, bool RX, bool REF>
-void reverse_faces(dis_ctx* c, const AdjArgs& A) {
+void reverse_kernels(dis_ctx* c, const AdjArgs& A) {
+  k_adj_cell<DIM, RX, REF><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, A, c->d_seg_cell);
+  cudaMemsetAsync(c->adj->Wb, 0, sizeof(double) * (size_t)c->nf * c->T, c->stream);
   k_adj_face<DIM, RX, 0, REF><<<(unsigned)c->seg_fx.size(), SEG, 0, c->stream>>>(c->phys, A, c->d_seg_fx);
   if constexpr (DIM == 2)
     k_adj_face<DIM, RX, 1, REF><<<(unsigned)c->seg_fy.size(), SEG, 0, c->stream>>>(c->phys, A, c->d_seg_fy);
@@ -268,10 +274,8 @@ void reverse_stage(dis_ctx* c, const double* x, const double* opre, double a_, d
   A.last = last;
   A.first = first;
   A.pmask = pmask;
-  k_adj_cell<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, A, c->d_seg_cell);
-  cudaMemsetAsync(d->Wb, 0, sizeof(double) * (size_t)c->nf * c->T, c->stream);
-  if (d->dual_riemann) reverse_faces<DIM, RX, true>(c, A);
-  else reverse_faces<DIM, RX, false>(c, A);
+  if (d->dual_riemann) reverse_kernels<DIM, RX, true>(c, A);
+  else reverse_kernels<DIM, RX, false>(c, A);
 }
 
 template <int DIM, bool RX>
@@ -286,24 +290,39 @@ int adj_backward(dis_ctx* c, const double* qbar_packed, double jbar, int out_kin
   for (int s = d->n_ck - 1; s >= 0; --s) {
     const int n0 = s * d->every, n1 = std::min(d->n_steps, n0 + d->every);
     ACU(cudaMemcpyAsync(d->seg, d->ck + (size_t)s * SD, sizeof(double) * SD, cudaMemcpyDeviceToDevice, c->stream));
-    for (int m = 0; m < n1 - n0; ++m)
-      fwd_step_fixed<DIM, RX>(c, d->seg + (size_t)m * SD, d->seg + (size_t)(m + 1) * SD,
-                              d->dts + (size_t)(n0 + m) * c->np);
+    // recompute the segment from its checkpoint with the recorded dt (the
+    // forward run's kernels, so bit-identical), keeping every step's stage
+    // states: q1, q3 and the state before the source steps
+    for (int m = 0; m < n1 - n0; ++m) {
+      const double* qn = d->seg + (size_t)m * SD;
+      double* s3 = d->stg + (size_t)3 * m * SD;
+      const double* dt = d->dts + (size_t)(n0 + m) * c->np;
+      fwd_stage<DIM, RX>(c, qn, qn, s3, 0.0, 1.0, 0, dt, false);
+      fwd_stage<DIM, RX>(c, s3, qn, s3 + SD, 0.75, 0.25, 0, dt, false);
+      fwd_stage<DIM, RX>(c, s3 + SD, qn, s3 + 2 * SD, 1.0 / 3.0, 2.0 / 3.0, 0, dt, false);
+      StepArgs a = fwd_args(c);  // the same stage with the source steps: q^{n+1}
+      a.qsrc = s3 + SD;
+      a.qn = qn;
+      a.qdst = d->seg + (size_t)(m + 1) * SD;
+      a.a = 1.0 / 3.0;
+      a.b = 2.0 / 3.0;
+      a.last = 1;
+      a.dtfix = dt;
+      k_update<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_cell);
+    }
     for (int n = n1 - 1; n >= n0; --n) {
       const double* qn = d->seg + (size_t)(n - n0) * SD;
       const double* qnext = d->seg + (size_t)(n - n0 + 1) * SD;
+      const double* s3 = d->stg + (size_t)3 * (n - n0) * SD;
       const double* dt = d->dts + (size_t)n * c->np;
       if (d->mat >= 0)
         k_obj_adj<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, qnext, d->ob, c->T, dt, d->mat, jbar);
-      // stage inputs q1 (st0), q3 (st1) and the pre-source state (st2); the
-      // last forward call leaves W, F of q3 in the context
-      fwd_stage<DIM, RX>(c, qn, qn, d->st[0], 0.0, 1.0, 0, dt, false);
-      fwd_stage<DIM, RX>(c, d->st[0], qn, d->st[1], 0.75, 0.25, 0, dt, false);
-      fwd_stage<DIM, RX>(c, d->st[1], qn, d->st[2], 1.0 / 3.0, 2.0 / 3.0, 0, dt, false);
-      reverse_stage<DIM, RX>(c, d->st[1], d->st[2], 1.0 / 3.0, 2.0 / 3.0, 1, 1, dt, pmask);
+      // stage inputs q1 (s3), q3 (s3 + SD) and the pre-source state (s3 + 2 SD)
+      fwd_faces<DIM, RX>(c, s3 + SD, false);
+      reverse_stage<DIM, RX>(c, s3 + SD, s3 + 2 * SD, 1.0 / 3.0, 2.0 / 3.0, 1, 1, dt, pmask);
       std::swap(d->ob, d->xb);
-      fwd_faces<DIM, RX>(c, d->st[0], false);
-      reverse_stage<DIM, RX>(c, d->st[0], nullptr, 0.75, 0.25, 0, 0, dt, pmask);
+      fwd_faces<DIM, RX>(c, s3, false);
+      reverse_stage<DIM, RX>(c, s3, nullptr, 0.75, 0.25, 0, 0, dt, pmask);
       std::swap(d->ob, d->xb);
       fwd_faces<DIM, RX>(c, qn, false);
       reverse_stage<DIM, RX>(c, qn, nullptr, 0.0, 1.0, 0, 0, dt, pmask);

@@ -18,13 +18,13 @@
 //   k_adj_prim  (per padded cell, ghosts included) Wbar -> xbar of the source
 //                            cell of the ghost map (sign flips of reflective
 //                            walls applied), again by atomics.
-// Local Jacobians are never formed.  The Riemann problem of a face, the map
-// from face primitives to face states, the THINC-BVD edge values of phi and
-// the recovery of primitives are reversed by hand (local_vjp.cuh); the source
-// steps are reversed one input direction at a time by a Dual-number
-// evaluation of the forward code (face.cuh), contracted with the adjoint.
-// REF = true instantiates the Dual form for the hand-reversed maps too (the
-// reference the hand-written reverses are tested against).
+// Local Jacobians are never formed.  Every local map - the Riemann problem of
+// a face, the map from face primitives to face states, the THINC-BVD edge
+// values of phi, the recovery of primitives and the source steps - is
+// reversed by hand (local_vjp.cuh).  REF = true instantiates the reference
+// form instead: each map reversed one input direction at a time by a
+// Dual-number evaluation of the forward code (face.cuh), contracted with the
+// adjoint (the reference the hand-written reverses are tested against).
 #pragma once
 #include "local_vjp.cuh"
 #include "step_kernels.cuh"
@@ -126,7 +126,7 @@ __device__ __forceinline__ double fstate_dot(const FState& a, const FStateT<Dual
 // Per interior cell: source-step adjoint, RK combination, non-conservative
 // terms; writes xbar (direct part), qnacc and the face coefficients G.
 // ---------------------------------------------------------------------------
-template <int DIM, bool RX>
+template <int DIM, bool RX, bool REF>
 __global__ void __launch_bounds__(SEG) k_adj_cell(Phys P, AdjArgs A, const int4* __restrict__ segs) {
   using L = Lay<DIM, RX>;
   constexpr int NF = L::NF;
@@ -144,8 +144,19 @@ __global__ void __launch_bounds__(SEG) k_adj_cell(Phys P, AdjArgs A, const int4*
     double ob[NF];
 #pragma unroll
     for (int c = 0; c < NF; ++c) ob[c] = A.obar[c * T + k];
-    if (A.last) {
-      // adjoint of the source steps about the pre-source state
+    if constexpr (!REF) {
+      if (A.last) {
+        // adjoint of the source steps about the pre-source state (by hand)
+        double op[NF], thp[NPARAM] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+        for (int c = 0; c < NF; ++c) op[c] = A.opre[c * T + k];
+        sources_vjp<DIM, RX>(P, dt, op, ob, thp);
+#pragma unroll
+        for (int kk = 0; kk < NPARAM; ++kk)
+          if ((A.pmask >> kk) & 1u) th[kk] += thp[kk];
+      }
+    } else if (A.last) {
+      // the same with dual numbers (reference form)
       double op[NF], nb[NF];
 #pragma unroll
       for (int c = 0; c < NF; ++c) op[c] = A.opre[c * T + k];
@@ -294,39 +305,48 @@ __global__ void __launch_bounds__(SEG) k_adj_face(Phys P, AdjArgs A, const int4*
   if (active) {
     const double* __restrict__ W = A.W;
     const long long stride_t = DIR == 0 ? (long long)pd.pitch : 1;
-    double B[3][6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) B[1][c] = W[L::PHI * T + at(a - 2 + c)];
     const bool normals = DIM == 2 && P.thinc;
-#pragma unroll
-    for (int c = 0; c < 6; ++c) {
-      B[0][c] = normals ? W[L::PHI * T + at(a - 2 + c) - stride_t] : 0.0;
-      B[2][c] = normals ? W[L::PHI * T + at(a - 2 + c) + stride_t] : 0.0;
-    }
     const double hn = DIR == 0 ? pd.dx : pd.dy, ht = DIR == 0 ? pd.dy : pd.dx;
-    double phiL, phiR;
-    face_phi<DIM, double>(B, P.thinc != 0, hn, ht, phiL, phiR);
-    Prim w[4];
+    // phi stencil of the face (line a-2 .. a+3 and, for the Youngs normal, the
+    // neighbouring lines); loaded again where the reverse needs it
+    auto load_B = [&](double (&B)[3][6]) {
 #pragma unroll
-    for (int s = 0; s < 4; ++s) w[s] = load_prim<DIM, RX>(W, T, at(a - 1 + s));
-    Prim wl, wr;
+      for (int c = 0; c < 6; ++c) {
+        B[1][c] = W[L::PHI * T + at(a - 2 + c)];
+        B[0][c] = normals ? W[L::PHI * T + at(a - 2 + c) - stride_t] : 0.0;
+        B[2][c] = normals ? W[L::PHI * T + at(a - 2 + c) + stride_t] : 0.0;
+      }
+    };
+    // forward reconstruction: the two face states the Riemann solver saw
+    Prim pl, pr;
+    bool okL, okR;
+    {
+      double B[3][6];
+      load_B(B);
+      double phiL, phiR;
+      face_phi<DIM, double>(B, P.thinc != 0, hn, ht, phiL, phiR);
+      Prim w[4];
 #pragma unroll
-    for (int c = 0; c < NF; ++c) {
-      if (c == L::PHI) continue;
-      muscl_pair(prim_slot<DIM, RX>(w[0], c), prim_slot<DIM, RX>(w[1], c), prim_slot<DIM, RX>(w[2], c),
-                 prim_slot<DIM, RX>(w[3], c), prim_slot<DIM, RX>(wl, c), prim_slot<DIM, RX>(wr, c));
+      for (int s = 0; s < 4; ++s) w[s] = load_prim<DIM, RX>(W, T, at(a - 1 + s));
+      Prim wl, wr;
+#pragma unroll
+      for (int c = 0; c < NF; ++c) {
+        if (c == L::PHI) continue;
+        muscl_pair(prim_slot<DIM, RX>(w[0], c), prim_slot<DIM, RX>(w[1], c), prim_slot<DIM, RX>(w[2], c),
+                   prim_slot<DIM, RX>(w[3], c), prim_slot<DIM, RX>(wl, c), prim_slot<DIM, RX>(wr, c));
+      }
+      if constexpr (DIM == 1) {
+        wl.v = wr.v = 0.0;
+        wl.V12 = wr.V12 = wl.V21 = wr.V21 = 0.0;
+      }
+      if constexpr (!RX) wl.lam = wr.lam = 0.0;
+      wl.phi = phiL;
+      wr.phi = phiR;
+      okL = face_state<DIR>(P, wl).cL > 0.0;
+      okR = face_state<DIR>(P, wr).cL > 0.0;
+      pl = okL ? wl : w[1];
+      pr = okR ? wr : w[2];
     }
-    if constexpr (DIM == 1) {
-      wl.v = wr.v = 0.0;
-      wl.V12 = wr.V12 = wl.V21 = wr.V21 = 0.0;
-    }
-    if constexpr (!RX) wl.lam = wr.lam = 0.0;
-    wl.phi = phiL;
-    wr.phi = phiR;
-    const bool okL = face_state<DIR>(P, wl).cL > 0.0;
-    const bool okR = face_state<DIR>(P, wr).cL > 0.0;
-    const Prim pl = okL ? wl : w[1];
-    const Prim pr = okR ? wr : w[2];
 
     // Riemann solver: gradient with respect to the two chosen face states
     double gL[NF], gR[NF];
@@ -384,8 +404,8 @@ __global__ void __launch_bounds__(SEG) k_adj_face(Phys P, AdjArgs A, const int4*
 #pragma unroll
     for (int c = 0; c < NF; ++c) {
       if (c == L::PHI) continue;
-      const double v0 = prim_slot<DIM, RX>(w[0], c), v1 = prim_slot<DIM, RX>(w[1], c);
-      const double v2 = prim_slot<DIM, RX>(w[2], c), v3 = prim_slot<DIM, RX>(w[3], c);
+      const double v0 = W[c * T + at(a - 1)], v1 = W[c * T + at(a)];
+      const double v2 = W[c * T + at(a + 1)], v3 = W[c * T + at(a + 2)];
       if (okL) {  // wl = w1 + minmod(w1 - w0, w2 - w1) / 2
         double da, db;
         minmod_grad(v1 - v0, v2 - v1, da, db);
@@ -417,7 +437,8 @@ __global__ void __launch_bounds__(SEG) k_adj_face(Phys P, AdjArgs A, const int4*
     if (!okL) add_nz(A.Wbar + L::PHI * T + at(a), gL[L::PHI]);
     if (!okR) add_nz(A.Wbar + L::PHI * T + at(a + 1), gR[L::PHI]);
     if ((gpL != 0.0 || gpR != 0.0) && !REF) {
-      double Bb[3][6];
+      double B[3][6], Bb[3][6];
+      load_B(B);
 #pragma unroll
       for (int r = 0; r < 3; ++r)
 #pragma unroll
@@ -431,6 +452,8 @@ __global__ void __launch_bounds__(SEG) k_adj_face(Phys P, AdjArgs A, const int4*
           add_nz(A.Wbar + L::PHI * T + at(a - 2 + c) + (long long)(r - 1) * stride_t, Bb[r][c]);
       }
     } else if (REF && (gpL != 0.0 || gpR != 0.0)) {
+      double B[3][6];
+      load_B(B);
       const int r0 = normals ? 0 : 1, r1 = normals ? 2 : 1;
 #pragma unroll 1
       for (int r = r0; r <= r1; ++r) {

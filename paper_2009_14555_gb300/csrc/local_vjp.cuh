@@ -1,8 +1,8 @@
 // local_vjp.cuh - hand-written reverses (vector-Jacobian products) of the
 // local maps of the float64 step: the face Riemann problem (riemann_outputs /
 // hllc of face.cuh and physics.cuh), the face-state map (face_state), the
-// conservative -> primitive recovery (prim_of) and the THINC-BVD edge values
-// of phi (face_phi).
+// conservative -> primitive recovery (prim_of), the THINC-BVD edge values of
+// phi (face_phi) and the source steps (plastic, sources).
 //
 // Given the adjoint of the face outputs (NF fluxes + the face-state extras),
 // accumulate the adjoints of the two face states (FState fields, c_L still
@@ -365,13 +365,13 @@ __device__ void riemann_outputs_vjp(const FState& L0, const FState& R0, const do
   Rb.cL = R.cL > 0.0 ? cLRb / (2.0 * R.cL) : 0.0;
 }
 
-// Adjoint of strain_of (physics.cuh): given the adjoints of H11, H12, H22 and
-// J2 (H33 enters only through J2), add those of V11, V12, V21, V22, V33.  The
+// Adjoint of strain_of (physics.cuh): given the adjoints of H11, H12, H22,
+// H33 and J2, add those of V11, V12, V21, V22, V33.  The
 // map dev(1/4 (B - B^-1)), B = V V^T in plane-strain block form, is reversed
 // through B and the 2 x 2 inverse.
 __device__ __forceinline__ void strain_vjp(double a, double b, double c, double d, double e, double H11b,
-                                           double H12b, double H22b, double J2b, double& ab, double& bb,
-                                           double& cb, double& db, double& eb) {
+                                           double H12b, double H22b, double H33b_in, double J2b, double& ab,
+                                           double& bb, double& cb, double& db, double& eb) {
   const double B11 = a * a + b * b, B12 = a * c + b * d, B22 = c * c + d * d, B33 = e * e;
   const double idet = 1.0 / (B11 * B22 - B12 * B12);
   const double M11 = 0.25 * (B11 - B22 * idet);
@@ -383,7 +383,7 @@ __device__ __forceinline__ void strain_vjp(double a, double b, double c, double 
   // J2 = H11^2 + H22^2 + H33^2 + 2 H12^2, H_ii = M_ii - t3
   H11b += 2.0 * H11 * J2b;
   H22b += 2.0 * H22 * J2b;
-  const double H33b = 2.0 * H33 * J2b;
+  const double H33b = H33b_in + 2.0 * H33 * J2b;
   H12b += 4.0 * H12 * J2b;
   const double t3b = -(H11b + H22b + H33b) * (1.0 / 3.0);
   const double M11b = H11b + t3b, M22b = H22b + t3b, M33b = H33b + t3b, M12b = H12b;
@@ -503,7 +503,8 @@ __device__ __forceinline__ void face_state_vjp(const Phys& P, const Prim& w, con
   wb.V21 += Sb.V21;
   wb.V22 += Sb.V22;
   wb.V33 += Sb.V33;
-  strain_vjp(w.V11, w.V12, w.V21, w.V22, w.V33, H11b, H12b, H22b, J2b, wb.V11, wb.V12, wb.V21, wb.V22, wb.V33);
+  strain_vjp(w.V11, w.V12, w.V21, w.V22, w.V33, H11b, H12b, H22b, 0.0, J2b, wb.V11, wb.V12, wb.V21, wb.V22,
+             wb.V33);
   if (thb) {
     // G_l enters through gG_l = gamma_l G_l / (gamma_l - 1), GoG_l = G_l / (gamma_l - 1)
     thb[0] += gG0b * m0.gi + GoG0b * m0.iGm1;
@@ -574,7 +575,7 @@ __device__ __forceinline__ void prim_of_vjp(const Phys& P, const double* q, cons
   a2b += wb.r2 / phi2 + rhob;
   phib += -wb.r1 * (a1 / phi) / phi + wb.r2 * (a2 / phi2) / phi2;
   double V11b = wb.V11, V12b = wb.V12, V21b = wb.V21, V22b = wb.V22, V33b = wb.V33;
-  strain_vjp(V11, V12, V21, V22, V33, 0.0, 0.0, 0.0, J2b, V11b, V12b, V21b, V22b, V33b);
+  strain_vjp(V11, V12, V21, V22, V33, 0.0, 0.0, 0.0, 0.0, J2b, V11b, V12b, V21b, V22b, V33b);
   qb[L::PHI] += phib;
   qb[L::A1] += a1b;
   qb[L::A2] += a2b;
@@ -600,7 +601,8 @@ __device__ __forceinline__ void prim_of_vjp(const Phys& P, const double* q, cons
 // along the edge the BVD choice kept: side 0 = left edge, 1 = right edge;
 // thinc_kept: the THINC value was chosen.  Adds the adjoints of q_{i-1},
 // q_i, q_{i+1} to qb[0..2] and returns that of beta.
-__device__ __forceinline__ double phi_cand_vjp(double qm, double qc, double qp, double beta, bool thinc,
+template <class BetaFn>
+__device__ __forceinline__ double phi_cand_vjp(double qm, double qc, double qp, const BetaFn& beta_of, bool thinc,
                                                int side, bool thinc_kept, double gb, double* qb) {
   const bool mixed = [&] {
     if (!thinc) return false;
@@ -620,6 +622,7 @@ __device__ __forceinline__ double phi_cand_vjp(double qm, double qc, double qp, 
     qb[2] += h * db;
     return 0.0;
   }
+  const double beta = beta_of();
   const bool up = qp > qm;  // ordering of the neighbours (strict in a mixed cell)
   const double qmin = up ? qm : qp, qmax = up ? qp : qm;
   const double jump = qmax - qmin;
@@ -669,20 +672,18 @@ template <int DIM>
 __device__ __forceinline__ void face_phi_vjp(const double (&B)[3][6], bool thinc, double hn, double ht,
                                              double gpL, double gpR, double (&Bb)[3][6]) {
   const bool normals = DIM == 2 && thinc;
-  double beta[4];
+  // THINC steepness of candidate cell s, evaluated only where a mixed cell needs it
+  auto beta_of = [&](int s) -> double {
+    if (!normals) return 2.51;
+    const double dn = (B[2][s + 2] + 2.0 * B[1][s + 2] + B[0][s + 2]) - (B[2][s] + 2.0 * B[1][s] + B[0][s]);
+    const double dt_ = (B[2][s + 2] + 2.0 * B[2][s + 1] + B[2][s]) - (B[0][s + 2] + 2.0 * B[0][s + 1] + B[0][s]);
+    const double gn = dn / hn, gt = dt_ / ht;
+    const double nrm = sqrt(gn * gn + gt * gt);
+    return 2.5 * (nrm == 0.0 ? 1.0 : fabs(gn) / nrm) + 0.01;
+  };
   Cand c[4];
 #pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    beta[s] = 2.51;
-    if (normals) {
-      const double dn = (B[2][s + 2] + 2.0 * B[1][s + 2] + B[0][s + 2]) - (B[2][s] + 2.0 * B[1][s] + B[0][s]);
-      const double dt_ = (B[2][s + 2] + 2.0 * B[2][s + 1] + B[2][s]) - (B[0][s + 2] + 2.0 * B[0][s + 1] + B[0][s]);
-      const double gn = dn / hn, gt = dt_ / ht;
-      const double nrm = sqrt(gn * gn + gt * gt);
-      beta[s] = 2.5 * (nrm == 0.0 ? 1.0 : fabs(gn) / nrm) + 0.01;
-    }
-    c[s] = phi_cand(B[1][s], B[1][s + 1], B[1][s + 2], beta[s], thinc);
-  }
+  for (int s = 0; s < 4; ++s) c[s] = phi_cand_lazy(B[1][s], B[1][s + 1], B[1][s + 2], [&]() { return beta_of(s); }, thinc);
   // BVD choices (the test of bvd in physics.cuh): the right edge of cell 1
   // (phiL) and the left edge of cell 2 (phiR)
   auto use_thinc = [](const Cand& km, const Cand& k, const Cand& kp) {
@@ -695,14 +696,14 @@ __device__ __forceinline__ void face_phi_vjp(const double (&B)[3][6], bool thinc
   double betab[4] = {0.0, 0.0, 0.0, 0.0};
   if (gpL != 0.0) {
     double qb[3] = {0.0, 0.0, 0.0};
-    betab[1] = phi_cand_vjp(B[1][1], B[1][2], B[1][3], beta[1], thinc, 1, t1, gpL, qb);
+    betab[1] = phi_cand_vjp(B[1][1], B[1][2], B[1][3], [&]() { return beta_of(1); }, thinc, 1, t1, gpL, qb);
     Bb[1][1] += qb[0];
     Bb[1][2] += qb[1];
     Bb[1][3] += qb[2];
   }
   if (gpR != 0.0) {
     double qb[3] = {0.0, 0.0, 0.0};
-    betab[2] = phi_cand_vjp(B[1][2], B[1][3], B[1][4], beta[2], thinc, 0, t2, gpR, qb);
+    betab[2] = phi_cand_vjp(B[1][2], B[1][3], B[1][4], [&]() { return beta_of(2); }, thinc, 0, t2, gpR, qb);
     Bb[1][2] += qb[0];
     Bb[1][3] += qb[1];
     Bb[1][4] += qb[2];
@@ -733,6 +734,220 @@ __device__ __forceinline__ void face_phi_vjp(const double (&B)[3][6], bool thinc
     Bb[2][s + 1] += 2.0 * dtb;
     Bb[0][s + 1] += -2.0 * dtb;
   }
+  }
+}
+
+// Adjoint of plastic (physics.cuh) on one cell: V[5] = (V11, V12, V21, V22,
+// V33) before the plastic step, Vb[5] the adjoint of its output, replaced by
+// the adjoint of its input; adds the adjoint of phi1 to phib and, where thb
+// is not null, those of G_l (3 l) and sigma_y,l (3 l + 1) through the yield
+// strain J_Y = sigma_y / (sqrt(6) G).  The output of the 2 x 2 block is
+// V = X^-1 Y with X = I - h/2, Y = I + h/2, so dV = X^-1 dh (I + V) / 2.
+__device__ __forceinline__ void plastic_vjp(const Phys& P, double phi1, double dt, const double (&V)[5],
+                                            double (&Vb)[5], double& phib, double* thb) {
+  // forward
+  const Strain st = strain_of(V[0], V[1], V[2], V[3], V[4]);
+  const double Js = sqrt(st.J2);
+  double num = 0.0, den = 0.0, Jl[2];
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    const MatDev& m = P.m[l];
+    const double ph = l == 0 ? phi1 : 1.0 - phi1;
+    if (m.G == 0.0) Jl[l] = 0.0;
+    else if (m.plastic == 1) Jl[l] = fmin(Js, m.JY);
+    else if (m.plastic == 2) Jl[l] = Js > m.JY ? fmax(Js - dt * m.chi0, m.JY) : Js;
+    else Jl[l] = Js;
+    num += ph * m.iGm1 * Jl[l];
+    den += ph * m.iGm1;
+  }
+  const double Jn = num / den;
+  const double sc = Js > 0.0 ? Jn / Js : 0.0;
+  const double h11 = sc * st.H11, h12 = sc * st.H12, h22 = sc * st.H22, h33 = sc * st.H33;
+  const double x11 = 1.0 - 0.5 * h11, x12 = -0.5 * h12, x22 = 1.0 - 0.5 * h22;
+  const double y11 = 1.0 + 0.5 * h11, y12 = 0.5 * h12, y22 = 1.0 + 0.5 * h22;
+  const double id = 1.0 / (x11 * x22 - x12 * x12);
+  const double i11 = x22 * id, i12 = -x12 * id, i22 = x11 * id;
+  const double o11 = i11 * y11 + i12 * y12, o12 = i11 * y12 + i12 * y22;
+  const double o21 = i12 * y11 + i22 * y12, o22 = i12 * y12 + i22 * y22;
+  // reverse: hb = X^-1 Vb (I + V_out)^T / 2 (X^-1 symmetric)
+  const double t00 = i11 * Vb[0] + i12 * Vb[2], t01 = i11 * Vb[1] + i12 * Vb[3];
+  const double t10 = i12 * Vb[0] + i22 * Vb[2], t11 = i12 * Vb[1] + i22 * Vb[3];
+  const double hb00 = 0.5 * (t00 * (1.0 + o11) + t01 * o12);
+  const double hb01 = 0.5 * (t00 * o21 + t01 * (1.0 + o22));
+  const double hb10 = 0.5 * (t10 * (1.0 + o11) + t11 * o12);
+  const double hb11 = 0.5 * (t10 * o21 + t11 * (1.0 + o22));
+  const double h11b = hb00, h22b = hb11, h12b = hb01 + hb10;
+  const double d33 = 1.0 - 0.5 * h33;
+  const double h33b = Vb[4] / (d33 * d33);  // V33 = (1 + h33/2) / (1 - h33/2)
+  double H11b = sc * h11b, H12b = sc * h12b, H22b = sc * h22b, H33b = sc * h33b;
+  const double scb = h11b * st.H11 + h12b * st.H12 + h22b * st.H22 + h33b * st.H33;
+  double Jsb = 0.0, Jnb = 0.0;
+  if (Js > 0.0) {
+    Jnb = scb / Js;
+    Jsb = -scb * sc / Js;
+  }
+  const double numb = Jnb / den, denb = -Jnb * Jn / den;
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    const MatDev& m = P.m[l];
+    const double ph = l == 0 ? phi1 : 1.0 - phi1;
+    const double sg = l == 0 ? 1.0 : -1.0;
+    phib += sg * (numb * m.iGm1 * Jl[l] + denb * m.iGm1);
+    const double Jlb = numb * ph * m.iGm1;
+    double JYb = 0.0;
+    if (m.G == 0.0) {
+    } else if (m.plastic == 1) {  // min(Js, J_Y), equal values split
+      if (m.JY < Js) JYb += Jlb;
+      else if (Js < m.JY) Jsb += Jlb;
+      else { Jsb += 0.5 * Jlb; JYb += 0.5 * Jlb; }
+    } else if (m.plastic == 2 && Js > m.JY) {  // max(Js - dt chi0, J_Y)
+      const double a = Js - dt * m.chi0;
+      if (m.JY > a) JYb += Jlb;
+      else if (a > m.JY) Jsb += Jlb;
+      else { Jsb += 0.5 * Jlb; JYb += 0.5 * Jlb; }
+    } else {
+      Jsb += Jlb;
+    }
+    if (thb && JYb != 0.0 && m.plastic && m.G > 0.0) {
+      thb[3 * l] += JYb * (-m.JY / m.G);
+      thb[3 * l + 1] += JYb / (sqrt(6.0) * m.G);
+    }
+  }
+  const double J2b = Js > 0.0 ? Jsb / (2.0 * Js) : 0.0;
+  double Vin_b[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  strain_vjp(V[0], V[1], V[2], V[3], V[4], H11b, H12b, H22b, H33b, J2b, Vin_b[0], Vin_b[1], Vin_b[2], Vin_b[3],
+             Vin_b[4]);
+#pragma unroll
+  for (int c = 0; c < 5; ++c) Vb[c] = Vin_b[c];
+}
+
+// Adjoint of sources (face.cuh: the plastic step, then, with RX, the RK4
+// reaction step) on one cell: o is the conservative state before the source
+// steps, ob the adjoint of the state after them (replaced by the adjoint of
+// the state before); parameter adjoints are added to thb where not null
+// (G_l at 3 l, sigma_y,l at 3 l + 1, Q_l at 3 l + 2).
+template <int DIM, bool RX>
+__device__ __forceinline__ void sources_vjp(const Phys& P, double dt, const double* o, double* ob, double* thb) {
+  using L = Lay<DIM, RX>;
+  double V[5] = {o[L::V11], 0.0, 0.0, o[L::V22], o[L::V33]};
+  if constexpr (DIM == 2) {
+    V[1] = o[L::V12];
+    V[2] = o[L::V21];
+  }
+  double Vb[5] = {ob[L::V11], 0.0, 0.0, ob[L::V22], ob[L::V33]};
+  if constexpr (DIM == 2) {
+    Vb[1] = ob[L::V12];
+    Vb[2] = ob[L::V21];
+  }
+  double phib = 0.0;
+  if constexpr (RX) {
+    // forward: V after the plastic step, then the reaction's frozen quantities
+    double Vp[5] = {V[0], V[1], V[2], V[3], V[4]};
+    plastic(P, o[L::PHI], dt, Vp[0], Vp[1], Vp[2], Vp[3], Vp[4]);
+    const int y = P.y;
+    const MatDev& m = P.m[y];
+    const double phi1 = o[L::PHI], a1 = o[L::A1], a2 = o[L::A2];
+    const double ary = y == 0 ? a1 : a2;
+    const double phy = y == 0 ? phi1 : 1.0 - phi1;
+    const double rr = a1 + a2;
+    const double mx = o[L::MX];
+    double my = 0.0;
+    if constexpr (DIM == 2) my = o[L::MY];
+    const double KE = 0.5 * (mx * mx + my * my) / rr;
+    const Strain st = strain_of(Vp[0], Vp[1], Vp[2], Vp[3], Vp[4]);
+    const double xi = xi_of(P, phi1);
+    const double ref0 = ref_energy(P, phi1, a1, a2, 0.0, st.J2);
+    const double p0 = (o[L::E] - KE - ref0) / xi;
+    const double cTy = m.iGm1 / m.cv;
+    const double Tfac = m.iGm1 / ((ary / phy) * m.cv);
+    const double Qx = m.Q / xi;
+    const double L0 = o[L::AL];
+    auto f = [&](double Lm) {
+      const double Tk = (p0 - Qx * Lm) * Tfac;
+      return Tk > 0.0 ? -m.A * Lm * exp(-m.Tact / Tk) : 0.0;
+    };
+    const double k1 = f(L0);
+    const double L2 = L0 + 0.5 * dt * k1;
+    const double k2 = f(L2);
+    const double L3 = L0 + 0.5 * dt * k2;
+    const double k3 = f(L3);
+    const double L4 = L0 + dt * k3;
+    // reverse of the RK4 combination and stages
+    const double outb = ob[L::AL];
+    double L0b = outb;
+    double kb[4] = {dt / 6.0 * outb, dt / 3.0 * outb, dt / 3.0 * outb, dt / 6.0 * outb};
+    double p0b = 0.0, Qxb = 0.0, Tfacb = 0.0;
+    auto stage_b = [&](double Lm, double kbar) -> double {  // returns the adjoint of Lm
+      const double Tk = (p0 - Qx * Lm) * Tfac;
+      if (!(Tk > 0.0) || kbar == 0.0) return 0.0;
+      const double e = exp(-m.Tact / Tk);
+      const double fTk = -m.A * Lm * e * m.Tact / (Tk * Tk);
+      const double Tkb = kbar * fTk;
+      p0b += Tkb * Tfac;
+      Qxb -= Tkb * Lm * Tfac;
+      Tfacb += Tkb * (p0 - Qx * Lm);
+      return kbar * (-m.A * e) + Tkb * (-Qx * Tfac);
+    };
+    const double L4b = stage_b(L4, kb[3]);
+    L0b += L4b;
+    kb[2] += dt * L4b;
+    const double L3b = stage_b(L3, kb[2]);
+    L0b += L3b;
+    kb[1] += 0.5 * dt * L3b;
+    const double L2b = stage_b(L2, kb[1]);
+    L0b += L2b;
+    kb[0] += 0.5 * dt * L2b;
+    L0b += stage_b(L0, kb[0]);
+    ob[L::AL] = L0b;
+    // p0 = (E - KE - ref0) / xi, Qx = Q / xi, Tfac = cTy phy / ary
+    double xib = -p0b * p0 / xi - Qxb * Qx / xi;
+    ob[L::E] += p0b / xi;
+    const double KEb = -p0b / xi, ref0b = -p0b / xi;
+    double Qb = Qxb / xi;
+    const double phyb = Tfacb * cTy / ary;
+    double aryb = -Tfacb * Tfac / ary;
+    double a1b = 0.0, a2b = 0.0;
+    phib += y == 0 ? phyb : -phyb;
+    // KE = (mx^2 + my^2) / (2 rr), rr = a1 + a2
+    ob[L::MX] += KEb * mx / rr;
+    if constexpr (DIM == 2) ob[L::MY] += KEb * my / rr;
+    const double rrb = -KEb * KE / rr;
+    a1b += rrb;
+    a2b += rrb;
+    // ref0 = sum_l phi_l (kap_l + gG_l J2) + a1 einf_1 + a2 einf_2 - Q_y a_y
+    const MatDev& m0 = P.m[0];
+    const MatDev& m1 = P.m[1];
+    phib += ref0b * ((m0.kap + m0.gG * st.J2) - (m1.kap + m1.gG * st.J2));
+    const double J2b = ref0b * (phi1 * m0.gG + (1.0 - phi1) * m1.gG);
+    a1b += ref0b * m0.einf;
+    a2b += ref0b * m1.einf;
+    aryb -= ref0b * m.Q;
+    Qb -= ref0b * ary;
+    phib += xib * (m0.iGm1 - m1.iGm1);
+    if (y == 0) a1b += aryb;
+    else a2b += aryb;
+    ob[L::A1] += a1b;
+    ob[L::A2] += a2b;
+    if (thb) {
+      thb[3 * y + 2] += Qb;
+      thb[0] += ref0b * phi1 * st.J2 * m0.gi;
+      thb[3] += ref0b * (1.0 - phi1) * st.J2 * m1.gi;
+    }
+    // the reaction reads the stretch after the plastic step through J2
+    double Vpb[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    strain_vjp(Vp[0], Vp[1], Vp[2], Vp[3], Vp[4], 0.0, 0.0, 0.0, 0.0, J2b, Vpb[0], Vpb[1], Vpb[2], Vpb[3],
+               Vpb[4]);
+#pragma unroll
+    for (int c = 0; c < 5; ++c) Vb[c] += Vpb[c];
+  }
+  plastic_vjp(P, o[L::PHI], dt, V, Vb, phib, thb);
+  ob[L::PHI] += phib;
+  ob[L::V11] = Vb[0];
+  ob[L::V22] = Vb[3];
+  ob[L::V33] = Vb[4];
+  if constexpr (DIM == 2) {
+    ob[L::V12] = Vb[1];
+    ob[L::V21] = Vb[2];
   }
 }
 

@@ -315,9 +315,10 @@ def test_adjoint_of_fp32_bulk_run_matches_float64_adjoint():
 @pytest.mark.parametrize("case", ["1d", "2d_thinc", "reactive"])
 def test_hand_written_reverses_match_dual_numbers(case):
     """The hand-written reverses of the face Riemann problem (all six regions
-    of the HLLD-type solver, shear coupling, wave-speed ties), of the face-state
-    map and of the primitive recovery give the gradient of the dual-number
-    reference to rounding: measured 1e-15 .. 2.5e-10 per field and parameter
+    of the HLLD-type solver, shear coupling, wave-speed ties), the face-state
+    map, the THINC-BVD edge values, the primitive recovery and the source steps
+    (plastic return, RK4 reaction) give the gradient of the dual-number
+    reference to rounding: measured 1e-15 .. 2.6e-10 per field and parameter
     (the larger values in partial-density and shear-modulus gradients, sums
     with cancellation); bar 1e-9."""
     from paper_2009_14555_gb300.solver import Solver
