@@ -11,7 +11,9 @@ Cites arXiv 2009.14555:
     minus the non-conservative sources; the three-stage Runge-Kutta scheme;
   * Section 3.2: plastic update (J*, mixture J*, scaled dev(H), first Pade
     approximant, bisection of the objective on [0, J*]);
-  * Section 3.3: reactive update with classical RK4.
+  * Section 3.3: reactive update with classical RK4;
+  * Section 3 (cylindrical symmetry): the geometric source s_g, with x = r and
+    y = z (geometric_source_terms), added to the operator of the stages.
 
 Readings: the non-conservative terms use the face velocity and face stretch of
 the Riemann solution, with cell-centred coefficients phi_i, V_i, u_i;
@@ -28,7 +30,7 @@ import math
 import torch
 
 from .closures import (Gamma, cons_to_prim, hencky_dev, mixture_props, phases,
-                       prim_to_cons, temperature)
+                       prim_to_cons, stress, temperature)
 from .reconstruction import (bvd_select, muscl_faces, thinc_beta, thinc_faces,
                              youngs_abs_normal)
 from .riemann import hllc
@@ -253,8 +255,52 @@ def operator_from_faces(q, faces, grid):
     return D
 
 
+def geometric_source_terms(q, mats):
+    """The bracket of the cylindrical geometric source (Section 3, cylindrical
+    symmetry): s_g = -(1/r) (0, phi_l rho_l u_r, phi_y rho_y lam u_r,
+    rho u_r^2 - sigma_rr + sigma_thth, rho u_z u_r - sigma_rz,
+    rho E u_r - (u_r sigma_rr + u_z sigma_zr), V_ij u_r / 3 - delta_{i th} V_ij u_r).
+    Axis order: 0 = r (x), 1 = z (y), 2 = theta."""
+    w = cons_to_prim(q, mats)
+    devH, J2 = hencky_dev(w["V"])
+    phis = phases(w["phi1"])
+    _, Gm, _, _ = mixture_props(phis, [w["rho1"], w["rho2"]], w["p"], J2, mats, w.get("lam"))
+    sig = stress(w["p"], Gm, devH)
+    rho = q["ar1"] + q["ar2"]
+    ur, uz = w["u"][..., 0], w["u"][..., 1]
+    t = {"phi1": torch.zeros_like(q["phi1"]), "ar1": q["ar1"] * ur, "ar2": q["ar2"] * ur}
+    if "arl" in q:
+        t["arl"] = q["arl"] * ur
+    mom = torch.zeros_like(q["mom"])
+    mom[..., 0] = rho * ur * ur - sig[..., 0, 0] + sig[..., 2, 2]
+    mom[..., 1] = rho * uz * ur - sig[..., 1, 0]
+    t["mom"] = mom
+    t["E"] = q["E"] * ur - (ur * sig[..., 0, 0] + uz * sig[..., 1, 0])
+    factor = torch.tensor([1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0 - 1.0], dtype=F64)
+    t["V"] = factor[:, None] * q["V"] * ur[..., None, None]
+    return t
+
+
+def cell_radius(grid, nx):
+    """Cell-centre radius r = x0 + (i + 1/2) dx of the interior columns."""
+    return grid.get("x0", 0.0) + (torch.arange(nx, dtype=F64) + 0.5) * grid["dx"]
+
+
 def spatial_operator(q, grid, mats, thinc):
-    """D(q) of Section 3.1 for all interior cells of one patch."""
+    """D(q) of Section 3.1 for all interior cells of one patch; in cylindrical
+    geometry (grid["geometry"] == "cyl", x = r, y = z) minus the geometric
+    source s_g."""
+    D = _planar_operator(q, grid, mats, thinc)
+    if grid.get("geometry", "planar") == "cyl":
+        r = cell_radius(grid, q["phi1"].shape[1])[None, :]
+        t = geometric_source_terms(q, mats)
+        for k in D:
+            rr = r.reshape(r.shape + (1,) * (D[k].dim() - 2))
+            D[k] = D[k] + t[k] / rr
+    return D
+
+
+def _planar_operator(q, grid, mats, thinc):
     ny, nx = q["phi1"].shape
     qg = fill_ghosts(q, grid)
     wg = cons_to_prim(qg, mats)
@@ -399,6 +445,8 @@ def step(q, grid, mats, opts, dt=None):
         return spatial_operator(x, grid, mats, th)
 
     if opts.get("scheme", "rk3") == "hancock":
+        if grid.get("geometry", "planar") != "planar":
+            raise NotImplementedError("the MUSCL-Hancock form is planar only")
         from .hancock import hancock_operator
         qs = _axpy(1.0, q, -dt, hancock_operator(q, grid, mats, th, dt))
     else:
@@ -413,8 +461,9 @@ def step(q, grid, mats, opts, dt=None):
     return qs, dt
 
 
-def grid_of(patch, dim):
-    return dict(dim=dim, dx=patch.dx, dy=patch.dy, bc=tuple(patch.bc))
+def grid_of(patch, dim, geometry="planar"):
+    return dict(dim=dim, dx=patch.dx, dy=patch.dy, bc=tuple(patch.bc), x0=getattr(patch, "x0", 0.0),
+                geometry=geometry)
 
 
 def run(prim_array, dim, mats, grid, opts, steps, dt_list=None):

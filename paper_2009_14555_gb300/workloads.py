@@ -91,6 +91,7 @@ class Workload:
     reactive_material: int = -1          # 0-based index of the reactive material, -1 none
     extra: dict = field(default_factory=dict)
     scheme: str = "rk3"                  # hyperbolic update: "rk3" (the paper's) or "hancock"
+    geometry: str = "planar"             # "planar" (plane strain) or "cyl" (axisymmetric, x = r, y = z)
 
     @property
     def reactive(self) -> bool:

@@ -22,7 +22,7 @@ def oracle_run(wl, steps, patch_ids=None, dt_list=None):
     ids = range(len(wl.patches)) if patch_ids is None else patch_ids
     for k in ids:
         p = wl.patches[k]
-        q, d = OS.run(p.prim, wl.dim, wl.materials, OS.grid_of(p, wl.dim),
+        q, d = OS.run(p.prim, wl.dim, wl.materials, OS.grid_of(p, wl.dim, getattr(wl, "geometry", "planar")),
                       dict(cfl=wl.cfl, thinc=wl.thinc, scheme=getattr(wl, "scheme", "rk3")), steps,
                       None if dt_list is None else dt_list[k])
         outs.append(q.numpy())
