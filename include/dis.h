@@ -75,6 +75,9 @@ typedef struct {
   int32_t nx, ny;
   double dx, dy;
   int32_t bc[4];
+  double x0; /* x of the patch's low face: the radius of its axis-side face in
+                cylindrical geometry (0 when the patch touches the axis);
+                unused in planar geometry */
 } dis_patch;
 
 /* Hyperbolic update of a step: DIS_RK3 is the paper's three-stage
@@ -85,14 +88,26 @@ typedef struct {
  * cell's own operator before the face Riemann problems.  Float64 only. */
 enum { DIS_RK3 = 0, DIS_HANCOCK = 1 };
 
+/* Geometry: DIS_PLANAR is the Cartesian plane-strain system; DIS_CYLINDRICAL
+ * the axisymmetric one of Section 3 (x = r, y = z, theta the third axis): the
+ * operator subtracts the geometric source s_g = -(1/r) (0, phi_l rho_l u_r,
+ * phi_y rho_y lam u_r, rho u_r^2 - sigma_rr + sigma_thth, rho u_z u_r -
+ * sigma_rz, rho E u_r - (u_r sigma_rr + u_z sigma_zr), V_ij u_r / 3 -
+ * delta_{i theta} V_ij u_r) at each cell centre r = x0 + (i + 1/2) dx.  A
+ * patch on the axis has x0 = 0 and a reflective x-low boundary.
+ * Runge-Kutta contexts only (float64 and FP32-bulk). */
+enum { DIS_PLANAR = 0, DIS_CYLINDRICAL = 1 };
+
 /* Step options: CFL number (Section 3: fraction of the largest stable step),
  * THINC interface steepening on/off (Appendix A), precision mode, hyperbolic
- * scheme (DIS_RK3 or DIS_HANCOCK; 0 = the paper's). */
+ * scheme (DIS_RK3 or DIS_HANCOCK; 0 = the paper's), geometry (DIS_PLANAR or
+ * DIS_CYLINDRICAL). */
 typedef struct {
   double cfl;
   int32_t thinc;
   int32_t precision;
   int32_t scheme;
+  int32_t geometry;
 } dis_options;
 
 typedef struct dis_ctx dis_ctx;
@@ -229,8 +244,9 @@ int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
  * 4 checkpoint_every + 8) states, allocated here, kept for dis_adjoint and
  * released by dis_destroy.  FP32-bulk contexts checkpoint their states in
  * float64 (plus float64 primitive and face buffers for the reverse sweep).
- * Returns DIS_EINVAL (bad arguments, or a DIS_HANCOCK context: the adjoint
- * covers the Runge-Kutta scheme), DIS_ESTATE (no state), DIS_ENOMEM,
+ * Returns DIS_EINVAL (bad arguments, or a DIS_HANCOCK or DIS_CYLINDRICAL
+ * context: the adjoint covers the planar Runge-Kutta scheme), DIS_ESTATE (no
+ * state), DIS_ENOMEM,
  * DIS_ECUDA.  Synchronises. */
 int dis_adj_forward(dis_ctx* ctx, int n_steps, int checkpoint_every, int objective_material,
                     const double* dt_in, double* dt_out, double* J_out);

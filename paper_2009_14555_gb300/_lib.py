@@ -16,6 +16,7 @@ DIS_OK, DIS_EINVAL, DIS_ENOMEM, DIS_ECUDA, DIS_ENONPHYSICAL, DIS_ESTATE = 0, -1,
 DIS_CONSERVATIVE, DIS_PRIMITIVE = 0, 1
 DIS_FP64, DIS_FP32_BULK = 0, 1
 DIS_RK3, DIS_HANCOCK = 0, 1
+DIS_PLANAR, DIS_CYLINDRICAL = 0, 1
 DIS_NPARAM = 6  # per material l: G, sigma_y, Q at 3 l + k
 DIS_NVARIANTS = 12  # FP32-bulk stage variants (2D: 3 tile shapes x 2 primitive sources x 2 register budgets)
 
@@ -29,11 +30,12 @@ class DisMaterial(ctypes.Structure):
 
 class DisPatch(ctypes.Structure):
     _fields_ = [("nx", c_int32), ("ny", c_int32), ("dx", c_double), ("dy", c_double),
-                ("bc", c_int32 * 4)]
+                ("bc", c_int32 * 4), ("x0", c_double)]
 
 
 class DisOptions(ctypes.Structure):
-    _fields_ = [("cfl", c_double), ("thinc", c_int32), ("precision", c_int32), ("scheme", c_int32)]
+    _fields_ = [("cfl", c_double), ("thinc", c_int32), ("precision", c_int32), ("scheme", c_int32),
+                ("geometry", c_int32)]
 
 
 class DisError(RuntimeError):

@@ -348,8 +348,9 @@ int dis_adj_forward(dis_ctx* c, int n_steps, int checkpoint_every, int objective
                     double* dt_out, double* J_out) {
   if (!c) return dis_internal_error(DIS_EINVAL, "dis_adj_forward: NULL context");
   if (!c->have_state) return dis_internal_error(DIS_ESTATE, "dis_adj_forward: no state loaded");
-  if (c->hancock)
-    return dis_internal_error(DIS_EINVAL, "dis_adj_forward: the adjoint covers the Runge-Kutta scheme only");
+  if (c->hancock || c->phys.cyl)
+    return dis_internal_error(DIS_EINVAL,
+                              "dis_adj_forward: the adjoint covers the planar Runge-Kutta scheme only");
   if (n_steps <= 0 || checkpoint_every <= 0)
     return dis_internal_error(DIS_EINVAL, "dis_adj_forward: n_steps and checkpoint_every must be positive");
   if (objective_material < -1 || objective_material > 1)

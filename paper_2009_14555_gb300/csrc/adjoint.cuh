@@ -50,6 +50,7 @@ __device__ __forceinline__ PhysT<Dual> lift_phys(const Phys& P, int k) {
   D.y = P.y;
   D.thinc = P.thinc;
   D.cfl = P.cfl;
+  D.cyl = P.cyl;
   if (k >= 0) {
     const int l = k / 3, kind = k % 3;
     const MatDev& m = P.m[l];

@@ -121,6 +121,7 @@ void layout(dis_ctx* c) {
     d.fyoff = fy;
     d.poff = po;
     d.dx = P.dx;
+    d.x0 = c->phys.cyl ? P.x0 : 0.0;
     d.dy = c->dim == 2 ? P.dy : 1.0;
     off += ((long long)d.pitch * d.rows + 31) / 32 * 32;
     fx += (long long)d.ny * (d.nx + 1);
@@ -287,19 +288,27 @@ StepArgs32 base_args32(dis_ctx* c) {
   return a;
 }
 
-template <int DIM, bool RX, int TX, int TY, int NT, bool PRE, int MINB>
-void stage_fused(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
+template <int DIM, bool RX, int TX, int TY, int NT, bool PRE, int MINB, bool CYL>
+void stage_fused_c(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
   constexpr size_t smem = fused32_smem<DIM, RX, TX, TY>();
   static bool attr_set = false;  // per instantiation, per process
   if (!attr_set) {
-    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT, PRE, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT, PRE, MINB>,
+    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT, PRE, MINB, CYL>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT, PRE, MINB, CYL>,
                          cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr_set = true;
   }
-  k_stage32<DIM, RX, TX, TY, NT, PRE, MINB><<<(unsigned)c->tiles[shape].size(), NT, smem, st>>>(
+  k_stage32<DIM, RX, TX, TY, NT, PRE, MINB, CYL><<<(unsigned)c->tiles[shape].size(), NT, smem, st>>>(
       c->phys, c->physf, a, c->d_tiles[shape]);
+}
+
+// Planar and cylindrical contexts run separate instantiations, so the
+// geometric source costs the planar kernels nothing.
+template <int DIM, bool RX, int TX, int TY, int NT, bool PRE, int MINB>
+void stage_fused(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
+  if (c->phys.cyl) stage_fused_c<DIM, RX, TX, TY, NT, PRE, MINB, true>(c, st, a, shape);
+  else stage_fused_c<DIM, RX, TX, TY, NT, PRE, MINB, false>(c, st, a, shape);
 }
 
 // FP32-bulk stage variants v = shape + 3 pre + 6 budget: 2D: 3 tile shapes x
@@ -366,13 +375,14 @@ int stage_fused_v(dis_ctx* c, cudaStream_t st, StepArgs32& a, int v, bool rate_o
 // Persistent 1D batch kernel (FP32-bulk), variant v: tile length v % 3,
 // 64 registers per thread for v >= 6; n steps in one launch, one CTA per
 // problem.  scratch_last (tuning, n = 1): the step ends in buffer 1.
-template <bool RX, int TX, int NT, int MINB>
-void batch_fused(dis_ctx* c, cudaStream_t st, const StepArgs32& a, int n, int scratch_last, int shape) {
+template <bool RX, int TX, int NT, int MINB, bool CYL>
+void batch_fused_c(dis_ctx* c, cudaStream_t st, const StepArgs32& a, int n, int scratch_last, int shape) {
   constexpr size_t smem = fused32_smem<1, RX, TX, 1>();
   static bool attr_set = false;  // per instantiation, per process
   if (!attr_set) {
-    cudaFuncSetAttribute(k_batch32<RX, TX, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_batch32<RX, TX, NT, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_batch32<RX, TX, NT, MINB, CYL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    cudaFuncSetAttribute(k_batch32<RX, TX, NT, MINB, CYL>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr_set = true;
   }
   Bufs32 b;
@@ -380,9 +390,15 @@ void batch_fused(dis_ctx* c, cudaStream_t st, const StepArgs32& a, int n, int sc
     b.q64[k] = c->q64[k];
     b.q32[k] = c->q32[k];
   }
-  k_batch32<RX, TX, NT, MINB><<<(unsigned)c->np, NT, smem, st>>>(c->phys, c->physf, a, b, c->d_order,
-                                                                 c->d_tile0[shape], c->d_tiles[shape], n,
-                                                                 scratch_last);
+  k_batch32<RX, TX, NT, MINB, CYL><<<(unsigned)c->np, NT, smem, st>>>(c->phys, c->physf, a, b, c->d_order,
+                                                                      c->d_tile0[shape], c->d_tiles[shape], n,
+                                                                      scratch_last);
+}
+
+template <bool RX, int TX, int NT, int MINB>
+void batch_fused(dis_ctx* c, cudaStream_t st, const StepArgs32& a, int n, int scratch_last, int shape) {
+  if (c->phys.cyl) batch_fused_c<RX, TX, NT, MINB, true>(c, st, a, n, scratch_last, shape);
+  else batch_fused_c<RX, TX, NT, MINB, false>(c, st, a, n, scratch_last, shape);
 }
 
 template <bool RX>
@@ -807,6 +823,10 @@ int dis_create(int dim, int n_patches, const dis_patch* patches, int reactive_ma
     return fail(DIS_EINVAL, "dis_create: unknown scheme %d", opt->scheme);
   if (opt->scheme == DIS_HANCOCK && opt->precision != DIS_FP64)
     return fail(DIS_EINVAL, "dis_create: the MUSCL-Hancock scheme is built for float64 only");
+  if (opt->geometry != DIS_PLANAR && opt->geometry != DIS_CYLINDRICAL)
+    return fail(DIS_EINVAL, "dis_create: unknown geometry %d", opt->geometry);
+  if (opt->geometry == DIS_CYLINDRICAL && opt->scheme != DIS_RK3)
+    return fail(DIS_EINVAL, "dis_create: cylindrical geometry is built for the Runge-Kutta scheme only");
   for (int p = 0; p < n_patches; ++p) {
     const dis_patch& P = patches[p];
     const int ny = dim == 2 ? P.ny : 1;
@@ -817,6 +837,8 @@ int dis_create(int dim, int n_patches, const dis_patch* patches, int reactive_ma
       return fail(DIS_EINVAL, "dis_create: patch %d is too large", p);
     for (int k = 0; k < (dim == 2 ? 4 : 2); ++k)
       if (P.bc[k] < 0 || P.bc[k] > 2) return fail(DIS_EINVAL, "dis_create: patch %d bad bc", p);
+    if (opt->geometry == DIS_CYLINDRICAL && !(P.x0 >= 0.0))
+      return fail(DIS_EINVAL, "dis_create: patch %d has x0 %g < 0 (a radius)", p, P.x0);
   }
   dis_ctx* c = new (std::nothrow) dis_ctx();
   if (!c) return fail(DIS_ENOMEM, "dis_create: out of host memory");
@@ -833,6 +855,7 @@ int dis_create(int dim, int n_patches, const dis_patch* patches, int reactive_ma
   c->phys.y = reactive_material;
   c->phys.thinc = opt->thinc ? 1 : 0;
   c->phys.cfl = opt->cfl;
+  c->phys.cyl = opt->geometry == DIS_CYLINDRICAL ? 1 : 0;
   layout(c);
   *out = c;
   return DIS_OK;

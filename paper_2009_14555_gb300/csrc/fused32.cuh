@@ -156,7 +156,7 @@ constexpr size_t fused32_smem() {
 // the tile's primitives and faces in the shared memory sm.  The stage kernel
 // runs it once per CTA; the persistent 1D batch kernel runs it for every tile
 // of its problem in turn (the caller synchronises the CTA between tiles).
-template <int DIM, bool RX, int TX, int TY, int NT, bool PRE>
+template <int DIM, bool RX, int TX, int TY, int NT, bool PRE, bool CYL = false>
 __device__ __forceinline__ void stage32_tile(const Phys& P, const PhysF& F, const StepArgs32& A, const int4 t,
                                              float* __restrict__ sm) {
   static_assert(TX * TY <= NT, "one thread per tile cell in the update phase");
@@ -284,12 +284,45 @@ __device__ __forceinline__ void stage32_tile(const Phys& P, const PhysF& F, cons
               dkf * (FY(S::PK, ft) * FY(S::DD, ft) - FY(S::PK, fb) * FY(S::DD, fb))) * idy;
     Dc = fma(dFy, ihy_sh, Dc);
   }
-  const double DE = fma(A.dkap, Dc, (double)small);
+  double DE = fma(A.dkap, Dc, (double)small);
   const double Dphi = fma(-phi_d, (double)divu, Dc);
   const float rho = q[L::A1] + q[L::A2];
   const float uc = q[L::MX] / rho;
   float vc = 0.f;
   if constexpr (DIM == 2) vc = q[L::MY] / rho;
+  if constexpr (CYL) {
+    // cylindrical geometric source (x = r, y = z) from the cell's primitives
+    // in shared memory; the energy term in float64 with rho E
+    const int plane = HX * HY, kc = (ly + (DIM == 2 ? NG : 0)) * HX + lx + NG;
+    const float wp = Wsm[L::E * plane + kc], wphi = Wsm[L::PHI * plane + kc];
+    const float wu = Wsm[L::MX * plane + kc];
+    float wv = 0.f, v12 = 0.f, v21 = 0.f;
+    if constexpr (DIM == 2) {
+      wv = Wsm[L::MY * plane + kc];
+      v12 = Wsm[L::V12 * plane + kc];
+      v21 = Wsm[L::V21 * plane + kc];
+    }
+    const StrainF st = strain_f(Wsm[L::V11 * plane + kc], v12, v21, Wsm[L::V22 * plane + kc],
+                                Wsm[L::V33 * plane + kc]);
+    const float Gm2 = 2.f * (wphi * F.m[0].GoG + (1.f - wphi) * F.m[1].GoG) / xi_f(F, wphi);
+    const float srr = -wp + Gm2 * st.H11, szr = Gm2 * st.H12, stt = -wp + Gm2 * st.H33;
+    const double r = pd.x0 + (i + 0.5) * pd.dx;
+    const float ir = (float)(1.0 / r);
+    D[L::A1] += q[L::A1] * wu * ir;
+    D[L::A2] += q[L::A2] * wu * ir;
+    if constexpr (RX) D[L::AL] += q[L::AL] * wu * ir;
+    D[L::MX] += (rho * wu * wu - srr + stt) * ir;
+    if constexpr (DIM == 2) D[L::MY] += (rho * wv * wu - szr) * ir;
+    DE += (E_d * (double)wu - (double)(wu * srr + wv * szr)) / r;
+    const float t = wu * ir * (1.f / 3.f);
+    D[L::V11] += t * q[L::V11];
+    D[L::V22] += t * q[L::V22];
+    D[L::V33] -= 2.f * t * q[L::V33];
+    if constexpr (DIM == 2) {
+      D[L::V12] += t * q[L::V12];
+      D[L::V21] += t * q[L::V21];
+    }
+  }
   const float t23 = 2.f / 3.f;
   D[L::V11] -= t23 * q[L::V11] * divu - uc * bx;
   D[L::V22] -= t23 * q[L::V22] * divu - vc * by;
@@ -371,10 +404,10 @@ __device__ __forceinline__ void stage32_tile(const Phys& P, const PhysF& F, cons
   A.q64dst[T + k] = oE;
 }
 
-template <int DIM, bool RX, int TX, int TY, int NT, bool PRE, int MINB>
+template <int DIM, bool RX, int TX, int TY, int NT, bool PRE, int MINB, bool CYL = false>
 __global__ void __launch_bounds__(NT, MINB) k_stage32(Phys P, PhysF F, StepArgs32 A, const int4* __restrict__ tiles) {
   extern __shared__ __align__(16) float sm[];
-  stage32_tile<DIM, RX, TX, TY, NT, PRE>(P, F, A, tiles[blockIdx.x], sm);
+  stage32_tile<DIM, RX, TX, TY, NT, PRE, CYL>(P, F, A, tiles[blockIdx.x], sm);
 }
 
 // CFL rate of the state at the start of a step (FP32-bulk): per-patch max of
@@ -425,7 +458,7 @@ struct Bufs32 {
 // k_cfl32; compiled as another kernel, its multiply-add contractions may
 // differ, so the result matches the per-step launches to rounding.
 // scratch_last (tuning, n_steps = 1): the last stage writes buffer 1.
-template <bool RX, int TX, int NT, int MINB>
+template <bool RX, int TX, int NT, int MINB, bool CYL = false>
 __global__ void __launch_bounds__(NT, MINB) k_batch32(Phys P, PhysF F, StepArgs32 A, Bufs32 B,
                                                       const int* __restrict__ order,
                                                       const int* __restrict__ tile0,
@@ -468,7 +501,7 @@ __global__ void __launch_bounds__(NT, MINB) k_batch32(Phys P, PhysF F, StepArgs3
       a.b = s0 ? 1.0 : (s1 ? 0.25 : 2.0 / 3.0);
       a.last = stg == 2;
       for (int t = ta; t < tb; ++t) {
-        stage32_tile<1, RX, TX, 1, NT, false>(P, F, a, tiles[t], sm);
+        stage32_tile<1, RX, TX, 1, NT, false, CYL>(P, F, a, tiles[t], sm);
         __syncthreads();
       }
     }

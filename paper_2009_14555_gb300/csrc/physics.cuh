@@ -48,6 +48,7 @@ struct PhysT {
   int y;      // reactive material (0/1) or -1
   int thinc;  // THINC-BVD steepening on phi1
   R cfl;
+  int cyl;    // axisymmetric geometry (x = r, y = z): geometric source s_g
 };
 
 using MatDev = MatT<double>;
@@ -68,6 +69,7 @@ inline PhysT<float> to_float(const Phys& P) {
   f.y = P.y;
   f.thinc = P.thinc;
   f.cfl = (float)P.cfl;
+  f.cyl = P.cyl;
   return f;
 }
 

@@ -24,6 +24,7 @@ struct PatchDev {
   long long fyoff;  // first y face
   long long poff;   // first cell in the packed (interior-only) layout
   double dx, dy;
+  double x0;        // x of the low face (radius in cylindrical geometry)
 };
 
 struct StepArgs {
@@ -247,6 +248,34 @@ __global__ void __launch_bounds__(SEG) k_flux(Phys P, StepArgs A, const int4* __
   for (int c = 0; c < NO; ++c) F[c * NFc + fi] = out[c];
 }
 
+// Cylindrical geometry (x = r, y = z): add to the operator D of a cell at
+// radius r the bracket of s_g = -(1/r) (...) of Section 3, from the cell's
+// conservative state q and primitives w (stress sigma = -p I + 2 G dev H).
+template <int DIM, bool RX>
+__device__ __forceinline__ void add_geometric(const Phys& P, const double* q, const Prim& w, double r, double* D) {
+  using L = Lay<DIM, RX>;
+  const double ir = 1.0 / r;
+  const Strain st = strain_of(w.V11, w.V12, w.V21, w.V22, w.V33);
+  const double Gm2 = 2.0 * Gmix_of(P, w.phi);
+  const double srr = -w.p + Gm2 * st.H11, szr = Gm2 * st.H12, stt = -w.p + Gm2 * st.H33;
+  const double ur = w.u, uz = w.v;
+  const double rho = q[L::A1] + q[L::A2];
+  D[L::A1] += q[L::A1] * ur * ir;
+  D[L::A2] += q[L::A2] * ur * ir;
+  if constexpr (RX) D[L::AL] += q[L::AL] * ur * ir;
+  D[L::MX] += (rho * ur * ur - srr + stt) * ir;
+  if constexpr (DIM == 2) D[L::MY] += (rho * uz * ur - szr) * ir;
+  D[L::E] += (q[L::E] * ur - (ur * srr + uz * szr)) * ir;
+  const double t = (1.0 / 3.0) * ur * ir;
+  D[L::V11] += t * q[L::V11];
+  D[L::V22] += t * q[L::V22];
+  D[L::V33] += (1.0 / 3.0 - 1.0) * ur * ir * q[L::V33];
+  if constexpr (DIM == 2) {
+    D[L::V12] += t * q[L::V12];
+    D[L::V21] += t * q[L::V21];
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Divergence, non-conservative terms, RK combination; on the last stage the
 // plastic and reactive source steps (pointwise) and the status check.
@@ -297,6 +326,7 @@ __global__ void __launch_bounds__(SEG) k_update(Phys P, StepArgs A, const int4* 
     D[L::V12] -= t23 * q[L::V12] * divu - uc * by;
     D[L::V21] -= t23 * q[L::V21] * divu - vc * bx;
   }
+  if (P.cyl) add_geometric<DIM, RX>(P, q, load_prim<DIM, RX>(A.W, T, k), pd.x0 + (i + 0.5) * pd.dx, D);
   const double dt = A.dtfix ? A.dtfix[g.x] : P.cfl / __longlong_as_double((long long)A.rate[g.x]);
   double o[NF];
   if (A.a == 0.0) {

@@ -20,7 +20,8 @@ def _material(m: dict) -> L.DisMaterial:
 
 def _patch(p, dim) -> L.DisPatch:
     bc = (ctypes.c_int32 * 4)(*[int(b) for b in p.bc])
-    return L.DisPatch(p.nx, p.ny if dim == 2 else 1, p.dx, p.dy if dim == 2 else 1.0, bc)
+    return L.DisPatch(p.nx, p.ny if dim == 2 else 1, p.dx, p.dy if dim == 2 else 1.0, bc,
+                      float(getattr(p, "x0", 0.0)))
 
 
 def pack(arrays) -> np.ndarray:
@@ -41,7 +42,7 @@ class Solver:
     """Diffuse-interface step on a batch of patches (see include/dis.h)."""
 
     def __init__(self, dim, patches, materials, reactive_material=-1, cfl=0.8, thinc=False,
-                 precision="fp64", device=None, scheme="rk3"):
+                 precision="fp64", device=None, scheme="rk3", geometry="planar"):
         if not torch.cuda.is_available():
             raise RuntimeError("Solver needs a CUDA device (no CPU fallback)")
         dev = torch.device(device or "cuda")
@@ -55,7 +56,8 @@ class Solver:
         self.nf = (11 if dim == 2 else 8) + (1 if self.reactive else 0)
         prec = {"fp64": L.DIS_FP64, "fp32_bulk": L.DIS_FP32_BULK}[precision]
         sch = {"rk3": L.DIS_RK3, "hancock": L.DIS_HANCOCK}[scheme]
-        opts = L.DisOptions(float(cfl), int(bool(thinc)), prec, sch)
+        geo = {"planar": L.DIS_PLANAR, "cyl": L.DIS_CYLINDRICAL}[geometry]
+        opts = L.DisOptions(float(cfl), int(bool(thinc)), prec, sch, geo)
         self.stream = torch.cuda.current_stream(self.device)
         self.ctx = L.dis_create(dim, [_patch(p, dim) for p in self.patches], reactive_material, opts,
                                 self.stream.cuda_stream)
@@ -72,6 +74,7 @@ class Solver:
     @classmethod
     def from_workload(cls, wl, precision="fp64", **kw):
         kw.setdefault("scheme", getattr(wl, "scheme", "rk3"))
+        kw.setdefault("geometry", getattr(wl, "geometry", "planar"))
         return cls(wl.dim, wl.patches, wl.materials, wl.reactive_material, wl.cfl, wl.thinc,
                    precision, **kw)
 

@@ -190,6 +190,51 @@ def shock_disc_2d(n: int = 512, steps: int = 2000, thinc: bool = True,
     return Workload(name or f"2d_shock_disc_{n}", 2, [SOLID, AIR], [p], 0.6, steps, thinc)
 
 
+def sphere_shock_rz(n: int = 128, steps: int = 200, thinc: bool = True, shock_z: float = 0.25,
+                    name=None) -> Workload:
+    """Axisymmetric (x = r, y = z) form of the shock-disc problem: an
+    elastoplastic sphere of radius 0.1 centred on the axis at z = 0.4 in air,
+    struck by a Mach-2 air shock travelling in +z.  (r, z) in [0, 0.5] x [0, 1],
+    n cells per unit length; reflective axis, transmissive elsewhere."""
+    nx, ny = n // 2, n
+    w, k = _blank(2, False, ny, nx)
+    d = 1.0 / n
+    frac = _area_fraction_disc(0.0, 0.4, 0.1, 0.0, 0.0, d, d, nx, ny)
+    w[k["phi1"]] = EPS_PHI + (1 - 2 * EPS_PHI) * frac
+    w[k["rho1"]] = SOLID_RHO0
+    w[k["rho2"]] = 1.2
+    w[k["p"]] = 1e5
+    rho2, p2, u2 = mach2_shock_positions()
+    zc = (np.arange(ny) + 0.5) * d
+    post = np.broadcast_to(zc[:, None] < shock_z, (ny, nx))
+    w[k["rho2"]][post] = rho2
+    w[k["p"]][post] = p2
+    w[k["v"]][post] = u2
+    p = Patch(nx=nx, ny=ny, dx=d, dy=d, x0=0.0,
+              bc=(BC_REFLECTIVE, BC_TRANSMISSIVE, BC_TRANSMISSIVE, BC_TRANSMISSIVE), prim=w)
+    return Workload(name or f"2d_sphere_shock_rz_{n}", 2, [SOLID, AIR], [p], 0.6, steps, thinc,
+                    geometry="cyl")
+
+
+def cylinder_core_1d(n: int = 400, steps: int = 200, r_core: float = 0.3, x0: float = 0.0,
+                     name=None) -> Workload:
+    """1D cylindrical (radius only): an elastoplastic core r < r_core at rest
+    under 1e5 Pa inside air at 5e6 Pa that implodes onto it; [x0, x0 + 1],
+    reflective at the low face (the axis when x0 = 0), transmissive outside."""
+    w, k = _blank(1, False, 1, n)
+    d = 1.0 / n
+    rc = x0 + (np.arange(n) + 0.5) * d
+    core = rc < r_core
+    w[k["phi1"], 0] = np.where(core, 1.0 - EPS_PHI, EPS_PHI)
+    w[k["rho1"], 0] = SOLID_RHO0
+    w[k["rho2"], 0] = 1.2
+    w[k["p"], 0] = np.where(core, 1e5, 5e6)
+    p = Patch(nx=n, ny=1, dx=d, dy=1.0, x0=x0,
+              bc=(BC_REFLECTIVE, BC_TRANSMISSIVE, BC_TRANSMISSIVE, BC_TRANSMISSIVE), prim=w)
+    return Workload(name or f"1d_cylinder_core_{n}", 1, [SOLID, AIR], [p], 0.8, steps, False,
+                    geometry="cyl")
+
+
 def reactive_plate_2d(nx: int = 2048, ny: int = 1024, steps: int = 1000, seed: int = 2,
                       A: float = 1.0e7, name=None) -> Workload:
     """Premixed reactive air over an elastoplastic plate (y < 0.2) on [0,2]x[0,1].

@@ -52,6 +52,17 @@ def test_create_validates_arguments(lib):
     unknown = L.DisOptions(0.8, 0, 0, 7)
     assert lib.dis_create(1, 1, arr, -1, ctypes.byref(unknown), None, ctypes.byref(out)) == L.DIS_EINVAL
     assert b"scheme" in lib.dis_last_error()
+    geo = L.DisOptions(0.8, 0, 0, 0, 5)
+    assert lib.dis_create(1, 1, arr, -1, ctypes.byref(geo), None, ctypes.byref(out)) == L.DIS_EINVAL
+    assert b"geometry" in lib.dis_last_error()
+    cyl_h = L.DisOptions(0.8, 0, L.DIS_FP64, L.DIS_HANCOCK, L.DIS_CYLINDRICAL)
+    assert lib.dis_create(1, 1, arr, -1, ctypes.byref(cyl_h), None, ctypes.byref(out)) == L.DIS_EINVAL
+    cyl = L.DisOptions(0.8, 0, L.DIS_FP64, L.DIS_RK3, L.DIS_CYLINDRICAL)
+    neg = (L.DisPatch * 1)(L.DisPatch(16, 1, 1.0 / 16, 1.0, (ctypes.c_int32 * 4)(2, 0, 0, 0), -0.5))
+    assert lib.dis_create(1, 1, neg, -1, ctypes.byref(cyl), None, ctypes.byref(out)) == L.DIS_EINVAL
+    assert b"x0" in lib.dis_last_error()
+    assert lib.dis_create(1, 1, arr, -1, ctypes.byref(cyl), None, ctypes.byref(out)) == L.DIS_OK
+    lib.dis_destroy(out)
     hancock32 = L.DisOptions(0.8, 0, L.DIS_FP32_BULK, L.DIS_HANCOCK)
     assert lib.dis_create(1, 1, arr, -1, ctypes.byref(hancock32), None, ctypes.byref(out)) == L.DIS_EINVAL
     assert b"float64" in lib.dis_last_error()
