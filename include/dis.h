@@ -208,6 +208,23 @@ int dis_set_schedule(dis_ctx* ctx, int schedule);
  * for a NULL context. */
 int dis_schedule(const dis_ctx* ctx, int* schedule, double* batch_ms);
 
+/* Pipelined host transfers (no counterpart in the paper).  dis_set_state_async
+ * copies a host state (the packed layout of dis_set_state; pinned memory for
+ * the copies to overlap anything) into one of two library staging buffers on a
+ * copy stream and converts it into the context's state on the context's
+ * stream, after the copy.  dis_get_state_async converts the state into one of
+ * two other staging buffers on the context's stream and copies it to the host
+ * buffer on a second copy stream.  Neither waits: a host-to-device copy for
+ * the next step, the current step and a device-to-host copy of the previous
+ * step can run at the same time.  The caller keeps the host buffers alive and
+ * unchanged (resp. unread) until dis_sync, which waits for all three streams.
+ * The staging buffers (4 states) are allocated by the first call and released
+ * by dis_destroy.  Returns DIS_EINVAL (NULL argument, bad kind), DIS_ESTATE
+ * (materials or state missing), DIS_ENOMEM, DIS_ECUDA. */
+int dis_set_state_async(dis_ctx* ctx, int kind, const double* host_src);
+int dis_get_state_async(dis_ctx* ctx, int kind, double* host_dst);
+int dis_sync(dis_ctx* ctx);
+
 /* Diagnostic: advance n_steps CFL steps like dis_step but launch kernel by
  * kernel with CUDA events between launches, and return in kernel_ms[4] the
  * mean device time per launch of the primitive-recovery, x-flux, y-flux (0 in

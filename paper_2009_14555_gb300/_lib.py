@@ -61,6 +61,9 @@ SIGNATURES = {
     "dis_step_timed": (c_int, [c_void_p, c_int, c_void_p]),
     "dis_set_variant": (c_int, [c_void_p, c_int]),
     "dis_set_schedule": (c_int, [c_void_p, c_int]),
+    "dis_set_state_async": (c_int, [c_void_p, c_int, c_void_p]),
+    "dis_get_state_async": (c_int, [c_void_p, c_int, c_void_p]),
+    "dis_sync": (c_int, [c_void_p]),
     "dis_schedule": (c_int, [c_void_p, POINTER(c_int), c_void_p]),
     "dis_tile_choice": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), c_void_p]),
     "dis_cfl_dt_static": (c_int, [c_int, c_int, POINTER(DisPatch), POINTER(DisMaterial), c_int,
@@ -128,6 +131,18 @@ def dis_set_state(ctx, kind, ptr, on_device):
 
 def dis_get_state(ctx, kind, ptr, on_device):
     return check(load().dis_get_state(ctx, kind, c_void_p(ptr), int(on_device)))
+
+
+def dis_set_state_async(ctx, kind, host_ptr):
+    return check(load().dis_set_state_async(ctx, kind, c_void_p(host_ptr)))
+
+
+def dis_get_state_async(ctx, kind, host_ptr):
+    return check(load().dis_get_state_async(ctx, kind, c_void_p(host_ptr)))
+
+
+def dis_sync(ctx):
+    return check(load().dis_sync(ctx))
 
 
 def dis_step(ctx, n, dt_out_ptr=None):

@@ -76,6 +76,15 @@ struct dis_ctx {
   long long graph_launches[2] = {0, 0};
   bool use_graphs = true;
   dis_adj* adj = nullptr;  // created by the first dis_adj_forward
+  // pipelined host transfers (dis_set_state_async / dis_get_state_async): two
+  // staging buffers per direction, a copy stream per direction, and events
+  // that order the copies against the conversions on the context's stream
+  double* xin[2] = {nullptr, nullptr};
+  double* xout[2] = {nullptr, nullptr};
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t in_done[2] = {nullptr, nullptr}, in_free[2] = {nullptr, nullptr};
+  cudaEvent_t out_ready[2] = {nullptr, nullptr}, out_free[2] = {nullptr, nullptr};
+  int in_idx = 0, out_idx = 0;
 };
 
 // Error text for the thread's dis_last_error (returns code).

@@ -955,6 +955,80 @@ int dis_get_state(dis_ctx* c, int kind, double* dst, int dst_on_device) {
   return DIS_OK;
 }
 
+// Staging buffers, copy streams and events of the pipelined transfers
+// (created on first use, released by dis_destroy).
+static int ensure_async(dis_ctx* c) {
+  if (c->s_in) return DIS_OK;
+  const size_t bytes = sizeof(double) * (size_t)c->nf * c->ncells;
+  for (int b = 0; b < 2; ++b) {
+    if (cudaMalloc(&c->xin[b], bytes) != cudaSuccess || cudaMalloc(&c->xout[b], bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(DIS_ENOMEM, "async transfers: cannot allocate %zu-byte staging buffers", bytes);
+    }
+    CU(cudaEventCreateWithFlags(&c->in_done[b], cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&c->in_free[b], cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&c->out_ready[b], cudaEventDisableTiming));
+    CU(cudaEventCreateWithFlags(&c->out_free[b], cudaEventDisableTiming));
+  }
+  CU(cudaStreamCreateWithFlags(&c->s_in, cudaStreamNonBlocking));
+  CU(cudaStreamCreateWithFlags(&c->s_out, cudaStreamNonBlocking));
+  return DIS_OK;
+}
+
+int dis_set_state_async(dis_ctx* c, int kind, const double* src) {
+  if (!c || !src) return fail(DIS_EINVAL, "dis_set_state_async: NULL argument");
+  if (kind != DIS_CONSERVATIVE && kind != DIS_PRIMITIVE) return fail(DIS_EINVAL, "dis_set_state_async: bad kind");
+  if (!c->have_mats) return fail(DIS_ESTATE, "dis_set_state_async: set materials first");
+  int rc = ensure_ws(c);
+  if (!rc) rc = ensure_async(c);
+  if (rc) return rc;
+  const int b = c->in_idx;
+  c->in_idx ^= 1;
+  // the copy may start once the conversion that last read this buffer is done
+  CU(cudaStreamWaitEvent(c->s_in, c->in_free[b], 0));
+  CU(cudaMemcpyAsync(c->xin[b], src, dis_state_bytes(c, kind), cudaMemcpyHostToDevice, c->s_in));
+  CU(cudaEventRecord(c->in_done[b], c->s_in));
+  CU(cudaStreamWaitEvent(c->stream, c->in_done[b], 0));
+  const bool rx = c->y >= 0;
+  const int prim = kind == DIS_PRIMITIVE;
+  if (c->dim == 1) rc = rx ? do_unpack<1, true>(c, c->xin[b], prim) : do_unpack<1, false>(c, c->xin[b], prim);
+  else rc = rx ? do_unpack<2, true>(c, c->xin[b], prim) : do_unpack<2, false>(c, c->xin[b], prim);
+  if (rc) return rc;
+  CU(cudaEventRecord(c->in_free[b], c->stream));
+  c->have_state = true;
+  return DIS_OK;
+}
+
+int dis_get_state_async(dis_ctx* c, int kind, double* dst) {
+  if (!c || !dst) return fail(DIS_EINVAL, "dis_get_state_async: NULL argument");
+  if (kind != DIS_CONSERVATIVE && kind != DIS_PRIMITIVE) return fail(DIS_EINVAL, "dis_get_state_async: bad kind");
+  if (!c->have_state) return fail(DIS_ESTATE, "dis_get_state_async: no state loaded");
+  int rc = ensure_async(c);
+  if (rc) return rc;
+  const int b = c->out_idx;
+  c->out_idx ^= 1;
+  // the conversion may overwrite this buffer once its last copy has left
+  CU(cudaStreamWaitEvent(c->stream, c->out_free[b], 0));
+  const bool rx = c->y >= 0;
+  const int prim = kind == DIS_PRIMITIVE;
+  if (c->dim == 1) rc = rx ? do_pack<1, true>(c, c->xout[b], prim) : do_pack<1, false>(c, c->xout[b], prim);
+  else rc = rx ? do_pack<2, true>(c, c->xout[b], prim) : do_pack<2, false>(c, c->xout[b], prim);
+  if (rc) return rc;
+  CU(cudaEventRecord(c->out_ready[b], c->stream));
+  CU(cudaStreamWaitEvent(c->s_out, c->out_ready[b], 0));
+  CU(cudaMemcpyAsync(dst, c->xout[b], dis_state_bytes(c, kind), cudaMemcpyDeviceToHost, c->s_out));
+  CU(cudaEventRecord(c->out_free[b], c->s_out));
+  return DIS_OK;
+}
+
+int dis_sync(dis_ctx* c) {
+  if (!c) return fail(DIS_EINVAL, "dis_sync: NULL context");
+  if (c->s_in) CU(cudaStreamSynchronize(c->s_in));
+  CU(cudaStreamSynchronize(c->stream));
+  if (c->s_out) CU(cudaStreamSynchronize(c->s_out));
+  return DIS_OK;
+}
+
 int dis_step(dis_ctx* c, int n_steps, double* dt_out) {
   if (!c) return fail(DIS_EINVAL, "dis_step: NULL context");
   if (n_steps < 0) return fail(DIS_EINVAL, "dis_step: negative step count");
@@ -1064,6 +1138,16 @@ void dis_destroy(dis_ctx* c) {
   for (int m = 0; m < 2; ++m)
     if (c->graph[m]) cudaGraphExecDestroy(c->graph[m]);
   if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->s_in) cudaStreamSynchronize(c->s_in);
+  if (c->s_out) cudaStreamSynchronize(c->s_out);
+  for (int b = 0; b < 2; ++b) {
+    if (c->xin[b]) cudaFree(c->xin[b]);
+    if (c->xout[b]) cudaFree(c->xout[b]);
+    for (cudaEvent_t e : {c->in_done[b], c->in_free[b], c->out_ready[b], c->out_free[b]})
+      if (e) cudaEventDestroy(e);
+  }
+  if (c->s_in) cudaStreamDestroy(c->s_in);
+  if (c->s_out) cudaStreamDestroy(c->s_out);
   if (c->ws_owned && c->ws) cudaFree(c->ws);
   dis_internal_adj_free(c);
   delete c;

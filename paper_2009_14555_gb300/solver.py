@@ -90,6 +90,23 @@ class Solver:
             assert x.size == self.state_numel, (x.size, self.state_numel)
             L.dis_set_state(self.ctx, kind, x.ctypes.data, False)
 
+    def set_state_async(self, host, kind=L.DIS_PRIMITIVE):
+        """Pipelined host -> device transfer of a pinned CPU tensor (include/dis.h:
+        dis_set_state_async); keep it alive and unchanged until sync()."""
+        assert isinstance(host, torch.Tensor) and not host.is_cuda and host.dtype == torch.float64
+        assert host.numel() == self.state_numel and host.is_contiguous()
+        L.dis_set_state_async(self.ctx, kind, host.data_ptr())
+
+    def get_state_async(self, host, kind=L.DIS_CONSERVATIVE):
+        """Pipelined device -> host transfer into a pinned CPU tensor (include/dis.h:
+        dis_get_state_async); its contents are valid after sync()."""
+        assert isinstance(host, torch.Tensor) and not host.is_cuda and host.dtype == torch.float64
+        assert host.numel() == self.state_numel and host.is_contiguous()
+        L.dis_get_state_async(self.ctx, kind, host.data_ptr())
+
+    def sync(self):
+        L.dis_sync(self.ctx)
+
     def set_prim(self, prim_arrays):
         self.set_state(pack(prim_arrays), L.DIS_PRIMITIVE)
 

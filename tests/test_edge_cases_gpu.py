@@ -86,3 +86,28 @@ def test_smallest_2d_patch_matches_oracle():
     g, _, _ = gpu_run(wl, 10)
     o, _ = oracle_run(wl, 10)
     assert cons_l1(wl, g[0], o[0]).max() <= 1e-10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_bulk"])
+def test_async_transfers_match_synchronous_calls(precision):
+    """Pipelined transfers (set_state_async / step / get_state_async, three
+    rounds in flight, one dis_sync) give the states the synchronous calls
+    give, bit for bit, in every round's own output buffer."""
+    import torch
+    from paper_2009_14555_gb300.solver import Solver, pack
+    wl = W.reactive_plate_2d(64, 32, steps=2)
+    prim = pack([p.prim for p in wl.patches])
+    s = Solver.from_workload(wl, precision=precision)
+    s.set_state(prim)
+    s.step(2)
+    ref = s.get_state()
+    hin = torch.from_numpy(prim.copy()).pin_memory()
+    outs = [torch.full((s.state_numel,), float("nan"), dtype=torch.float64).pin_memory() for _ in range(3)]
+    for k in range(3):
+        s.set_state_async(hin)
+        s.step(2)
+        s.get_state_async(outs[k])
+    s.sync()
+    s.close()
+    for k in range(3):
+        assert np.array_equal(outs[k].numpy(), ref), k
