@@ -320,6 +320,7 @@ __global__ void __launch_bounds__(SEG) k_adj_face(Phys P, AdjArgs A, const int4*
     };
     // forward reconstruction: the two face states the Riemann solver saw
     Prim pl, pr;
+    FState fsl, fsr;  // their face states, as the forward Riemann solver saw them
     bool okL, okR;
     {
       double B[3][6];
@@ -343,10 +344,14 @@ __global__ void __launch_bounds__(SEG) k_adj_face(Phys P, AdjArgs A, const int4*
       if constexpr (!RX) wl.lam = wr.lam = 0.0;
       wl.phi = phiL;
       wr.phi = phiR;
-      okL = face_state<DIR>(P, wl).cL > 0.0;
-      okR = face_state<DIR>(P, wr).cL > 0.0;
+      fsl = face_state<DIR>(P, wl);
+      fsr = face_state<DIR>(P, wr);
+      okL = fsl.cL > 0.0;
+      okR = fsr.cL > 0.0;
       pl = okL ? wl : w[1];
       pr = okR ? wr : w[2];
+      if (!okL) fsl = face_state<DIR>(P, pl);
+      if (!okR) fsr = face_state<DIR>(P, pr);
     }
 
     // Riemann solver: gradient with respect to the two chosen face states
@@ -355,7 +360,7 @@ __global__ void __launch_bounds__(SEG) k_adj_face(Phys P, AdjArgs A, const int4*
       // hand-written reverse of the Riemann problem into the face states, then
       // of the face-state map (primitives -> face state)
       FState Lb{}, Rb{};
-      riemann_outputs_vjp<DIM, RX, DIR>(face_state<DIR>(P, pl), face_state<DIR>(P, pr), Fb, Lb, Rb);
+      riemann_outputs_vjp<DIM, RX, DIR>(fsl, fsr, Fb, Lb, Rb);
       Prim pbL{}, pbR{};
       double thf[NPARAM] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
       face_state_vjp<DIR>(P, pl, Lb, pbL, thf);
