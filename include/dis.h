@@ -258,7 +258,8 @@ int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
  * returns it in J_out (may be NULL).  dt_out (host, n_steps x n_patches, may
  * be NULL) receives the time steps.  Leaves the context at the final state,
  * like dis_step.  Device memory: (ceil(n_steps / checkpoint_every) +
- * 4 checkpoint_every + 8) states, allocated here, kept for dis_adjoint and
+ * 4 checkpoint_every + 8) states and 3 checkpoint_every sets of primitives
+ * and face outputs (about 3.5 states each), allocated here, kept for dis_adjoint and
  * released by dis_destroy.  FP32-bulk contexts checkpoint their states in
  * float64 (plus float64 primitive and face buffers for the reverse sweep).
  * Returns DIS_EINVAL (bad arguments, or a DIS_HANCOCK or DIS_CYLINDRICAL

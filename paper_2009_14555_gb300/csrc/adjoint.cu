@@ -7,11 +7,12 @@
 // accumulated on the device.
 // Reverse: segments of K steps are taken last to first.  A segment is
 // recomputed from its checkpoint with the recorded dt (bit-identical to the
-// forward run), keeping each step's stage inputs and pre-source state; then,
-// step by step backwards, the primitives and face outputs of each stage input
-// are recomputed and the stages reversed (adjoint.cuh).
-// Memory: (number of checkpoints + 4 K + 8) states plus the face
-// coefficients, all library-owned and released by dis_destroy.
+// forward run), keeping each step's stage inputs, pre-source state and the
+// primitives and face outputs of each stage input; then, step by step
+// backwards, the stages are reversed (adjoint.cuh).
+// Memory: (number of checkpoints + 4 K + 8) states, 3 K sets of primitives
+// and face outputs, and the face coefficients, all library-owned and released
+// by dis_destroy.
 // FP32-bulk contexts: the forward run is the FP32-bulk step; its states are
 // checkpointed in float64 and the reverse sweep recomputes each segment with
 // the float64 step from those checkpoints (its own float64 primitive and face
@@ -38,6 +39,8 @@ struct dis_adj {
   double* seg = nullptr;  // every + 1 states of one segment
   double* st[3] = {nullptr, nullptr, nullptr};  // scratch stage states of one step
   double* stg = nullptr;  // per step of a segment: q1, q3 and the pre-source state
+  char* wf = nullptr;     // per stage input of a segment: primitives and face outputs
+  size_t wf_bytes = 0;    // bytes of one such set
   double* ob = nullptr;
   double* xb = nullptr;
   double* acc = nullptr;
@@ -87,9 +90,12 @@ int adj_alloc(dis_ctx* c, int n_steps, int every) {
   const size_t own = c->fp32 ? 2 * a256(S) + a256(sizeof(double) * nfo * c->NFX) +
                                    a256(sizeof(double) * nfo * std::max<long long>(1, c->NFY))
                              : 0;
+  // per stage input of a segment: primitives (nf planes) and x / y face outputs
+  const size_t wfb = a256(S) + a256(sizeof(double) * nfo * c->NFX) +
+                     a256(sizeof(double) * nfo * std::max<long long>(1, c->NFY));
   const size_t need = a256(S) * (size_t)(n_ck + (every + 1) + 3 * every + 7) + a256(sizeof(double) * nfo * c->T) +
                       a256(sizeof(double) * (size_t)n_steps * c->np) + a256(sizeof(double)) +
-                      a256(sizeof(double) * NPARAM) + own;
+                      a256(sizeof(double) * NPARAM) + own + wfb * 3 * (size_t)every;
   if (need > d->mem_bytes) {
     if (d->mem) cudaFree(d->mem);
     d->mem = nullptr;
@@ -111,6 +117,8 @@ int adj_alloc(dis_ctx* c, int n_steps, int every) {
   d->ck = take(S * n_ck);
   d->seg = take(S * (every + 1));
   d->stg = take(S * 3 * (size_t)every);
+  d->wf_bytes = wfb;
+  d->wf = (char*)take(wfb * 3 * (size_t)every);
   for (int k = 0; k < 3; ++k) d->st[k] = take(S);
   d->ob = take(S);
   d->xb = take(S);
@@ -140,15 +148,37 @@ int adj_alloc(dis_ctx* c, int n_steps, int every) {
   return DIS_OK;
 }
 
-StepArgs fwd_args(dis_ctx* c) {
+// Primitive and face-output buffers of one stage input.
+struct WF {
+  double* W;
+  double* Fx;
+  double* Fy;
+};
+
+// The adjoint's scratch buffers (idx < 0), or the stored set idx of the segment.
+WF wf_at(dis_ctx* c, int idx) {
+  dis_adj* d = c->adj;
+  if (idx < 0) return WF{d->W, d->Fx, d->Fy};
+  const size_t S = sizeof(double) * (size_t)c->nf * c->T;
+  const size_t nfo = (size_t)(c->nf + n_extra(c->dim));
+  char* b = d->wf + d->wf_bytes * (size_t)idx;
+  WF w;
+  w.W = (double*)b;
+  w.Fx = (double*)(b + a256(S));
+  w.Fy = (double*)(b + a256(S) + a256(sizeof(double) * nfo * c->NFX));
+  return w;
+}
+
+StepArgs fwd_args(dis_ctx* c, int wf = -1) {
   StepArgs a{};
   a.pd = c->d_pd;
   a.T = c->T;
   a.NFX = c->NFX;
   a.NFY = c->NFY;
-  a.W = c->adj->W;
-  a.Fx = c->adj->Fx;
-  a.Fy = c->adj->Fy;
+  const WF w = wf_at(c, wf);
+  a.W = w.W;
+  a.Fx = w.Fx;
+  a.Fy = w.Fy;
   a.rate = c->rate;
   a.dtlast = c->dtlast;
   a.status = c->status;
@@ -157,8 +187,8 @@ StepArgs fwd_args(dis_ctx* c) {
 
 // Primitives and face outputs of state `src` into the context's W, Fx, Fy.
 template <int DIM, bool RX>
-void fwd_faces(dis_ctx* c, const double* src, bool rate_on) {
-  StepArgs a = fwd_args(c);
+void fwd_faces(dis_ctx* c, const double* src, bool rate_on, int wf = -1) {
+  StepArgs a = fwd_args(c, wf);
   a.qsrc = src;
   k_prim<DIM, RX><<<(unsigned)c->seg_prim.size(), SEG, 0, c->stream>>>(c->phys, a, c->d_seg_prim, rate_on ? 1 : 0);
   k_flux<DIM, RX, 0><<<(unsigned)c->seg_fx.size(), SEG, 0, c->stream>>>(c->phys, a, c->d_seg_fx);
@@ -170,9 +200,9 @@ void fwd_faces(dis_ctx* c, const double* src, bool rate_on) {
 // dt per patch from `dt`, or from the CFL rate when dt is null.
 template <int DIM, bool RX>
 void fwd_stage(dis_ctx* c, const double* src, const double* qn, double* dst, double a_, double b_, int last,
-               const double* dt, bool rate_on) {
-  fwd_faces<DIM, RX>(c, src, rate_on);
-  StepArgs a = fwd_args(c);
+               const double* dt, bool rate_on, int wf = -1) {
+  fwd_faces<DIM, RX>(c, src, rate_on, wf);
+  StepArgs a = fwd_args(c, wf);
   a.qsrc = src;
   a.qn = qn;
   a.qdst = dst;
@@ -250,17 +280,18 @@ void reverse_kernels(dis_ctx* c, const AdjArgs& A) {
 
 template <int DIM, bool RX>
 void reverse_stage(dis_ctx* c, const double* x, const double* opre, double a_, double b_, int last, int first,
-                   const double* dt, unsigned pmask) {
+                   const double* dt, unsigned pmask, int wf) {
   dis_adj* d = c->adj;
+  const WF w = wf_at(c, wf);
   AdjArgs A{};
   A.pd = c->d_pd;
   A.T = c->T;
   A.NFX = c->NFX;
   A.NFY = c->NFY;
   A.x = x;
-  A.W = d->W;
-  A.Fx = d->Fx;
-  A.Fy = d->Fy;
+  A.W = w.W;
+  A.Fx = w.Fx;
+  A.Fy = w.Fy;
   A.obar = d->ob;
   A.opre = opre;
   A.xbar = d->xb;
@@ -297,10 +328,10 @@ int adj_backward(dis_ctx* c, const double* qbar_packed, double jbar, int out_kin
       const double* qn = d->seg + (size_t)m * SD;
       double* s3 = d->stg + (size_t)3 * m * SD;
       const double* dt = d->dts + (size_t)(n0 + m) * c->np;
-      fwd_stage<DIM, RX>(c, qn, qn, s3, 0.0, 1.0, 0, dt, false);
-      fwd_stage<DIM, RX>(c, s3, qn, s3 + SD, 0.75, 0.25, 0, dt, false);
-      fwd_stage<DIM, RX>(c, s3 + SD, qn, s3 + 2 * SD, 1.0 / 3.0, 2.0 / 3.0, 0, dt, false);
-      StepArgs a = fwd_args(c);  // the same stage with the source steps: q^{n+1}
+      fwd_stage<DIM, RX>(c, qn, qn, s3, 0.0, 1.0, 0, dt, false, 3 * m);
+      fwd_stage<DIM, RX>(c, s3, qn, s3 + SD, 0.75, 0.25, 0, dt, false, 3 * m + 1);
+      fwd_stage<DIM, RX>(c, s3 + SD, qn, s3 + 2 * SD, 1.0 / 3.0, 2.0 / 3.0, 0, dt, false, 3 * m + 2);
+      StepArgs a = fwd_args(c, 3 * m + 2);  // the same stage with the source steps: q^{n+1}
       a.qsrc = s3 + SD;
       a.qn = qn;
       a.qdst = d->seg + (size_t)(m + 1) * SD;
@@ -317,15 +348,14 @@ int adj_backward(dis_ctx* c, const double* qbar_packed, double jbar, int out_kin
       const double* dt = d->dts + (size_t)n * c->np;
       if (d->mat >= 0)
         k_obj_adj<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, qnext, d->ob, c->T, dt, d->mat, jbar);
-      // stage inputs q1 (s3), q3 (s3 + SD) and the pre-source state (s3 + 2 SD)
-      fwd_faces<DIM, RX>(c, s3 + SD, false);
-      reverse_stage<DIM, RX>(c, s3 + SD, s3 + 2 * SD, 1.0 / 3.0, 2.0 / 3.0, 1, 1, dt, pmask);
+      // stage inputs q1 (s3), q3 (s3 + SD) and the pre-source state (s3 + 2 SD),
+      // with the primitives and face outputs the recomputation stored
+      const int m = n - n0;
+      reverse_stage<DIM, RX>(c, s3 + SD, s3 + 2 * SD, 1.0 / 3.0, 2.0 / 3.0, 1, 1, dt, pmask, 3 * m + 2);
       std::swap(d->ob, d->xb);
-      fwd_faces<DIM, RX>(c, s3, false);
-      reverse_stage<DIM, RX>(c, s3, nullptr, 0.75, 0.25, 0, 0, dt, pmask);
+      reverse_stage<DIM, RX>(c, s3, nullptr, 0.75, 0.25, 0, 0, dt, pmask, 3 * m + 1);
       std::swap(d->ob, d->xb);
-      fwd_faces<DIM, RX>(c, qn, false);
-      reverse_stage<DIM, RX>(c, qn, nullptr, 0.0, 1.0, 0, 0, dt, pmask);
+      reverse_stage<DIM, RX>(c, qn, nullptr, 0.0, 1.0, 0, 0, dt, pmask, 3 * m);
       k_adj_sum<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, d->xb, d->acc, d->ob, c->T);
     }
   }
