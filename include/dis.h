@@ -54,18 +54,30 @@ enum { DIS_CONSERVATIVE = 0, DIS_PRIMITIVE = 1 };
 enum { DIS_FP64 = 0, DIS_FP32_BULK = 1 };
 enum { DIS_PLASTIC_NONE = 0, DIS_PLASTIC_PERFECT = 1, DIS_PLASTIC_RATE = 2 };
 
+enum { DIS_RATE_ARRHENIUS = 0, DIS_RATE_SQRT = 1 };
+
 /* One material: stiffened-gas Mie-Grueneisen closure (Section 2.3) with a
  * constant shear modulus G, plasticity (Section 2.3.2: none, perfect = the
  * chi0 -> infinity limit of ideal plasticity, or ideal plasticity with rate
  * chi0), and for a reactive material an ideal-gas reactant/product pair of
- * equal gamma and C_V with heat release Q (Section 2.3.1) and an Arrhenius
- * rate lam_dot = -A lam exp(-T_act / T). */
+ * equal gamma and C_V with heat release Q (Section 2.3.1) and a rate law for
+ * the reactant fraction lam (1 = reactant):
+ *   DIS_RATE_ARRHENIUS  lam_dot = -A lam exp(-T_act / T)   (zero where T <= 0);
+ *   DIS_RATE_SQRT       lam_dot = -A sqrt(lam) where p > p_ign, else 0 (the
+ *                       k sqrt(lam) law with a pressure switch of the paper's
+ *                       one-dimensional detonation test, Section 4.1; A = k;
+ *                       sqrt of max(lam, 0), and the reaction step's result
+ *                       is clamped at lam >= 0).
+ * rate_law and p_ign are read only for the reactive material; zero-filled
+ * (the default of a C initialiser without them) selects Arrhenius. */
 typedef struct {
   double gamma, p_inf, e_inf, G;
   int32_t plastic;
   double sigma_y, chi0;
   int32_t reactive;
   double Q, cv, A, T_act;
+  int32_t rate_law; /* DIS_RATE_ARRHENIUS or DIS_RATE_SQRT */
+  double p_ign;     /* DIS_RATE_SQRT: pressure above which the reaction runs, Pa */
 } dis_material;
 
 /* One Cartesian patch (the single-grid unit of Section 3): nx x ny cells of

@@ -21,7 +21,11 @@ the CFL rate of a cell is sum_d (|u_d| + c_L)/dx_d with
 c_L^2 = c^2 + 4/3 G/rho; a fluid (G = 0) relaxes fully in the plastic step
 (J*_l = 0) so V returns to I; perfect plasticity is the chi0 -> infinity limit
 of the ideal-plasticity rate; the reaction rate of the reactive material is
-Arrhenius, lam_dot = -A lam exp(-T_act / T), zero where T <= 0.
+Arrhenius, lam_dot = -A lam exp(-T_act / T), zero where T <= 0, or (rate_law
+1) the k sqrt(lam) law of Section 4.1 for the reactant fraction,
+lam_dot = -k sqrt(lam) with k = A, switched on where the pressure of the
+state the rate is evaluated at exceeds p_ign; sqrt of max(lam, 0), and the
+RK4 result is clamped at lam >= 0.
 """
 from __future__ import annotations
 
@@ -412,12 +416,20 @@ def reaction_update(q, mats, dt):
     m = mats[y]
     ary = q["ar1" if y == 0 else "ar2"]
 
+    law = int(m.get("rate_law", 0))
+
     def f(arl):
         w = cons_to_prim(dict(q, arl=arl), mats)
+        lam = arl / ary
+        if law == 1:
+            # Section 4.1: lam_dot = -k sqrt(lam) while p > p_ign
+            on = (w["p"] > m["p_ign"]) & (lam > 0)
+            # (1 in the switched-off cells keeps the reverse mode free of 0 / 0)
+            lam_dot = -m["A"] * torch.sqrt(torch.where(on, lam, torch.ones_like(lam)))
+            return ary * torch.where(on, lam_dot, torch.zeros_like(lam))
         rho_y = w["rho1" if y == 0 else "rho2"]
         _, J2 = hencky_dev(w["V"])
         T = temperature(m, rho_y, w["p"], J2)
-        lam = arl / ary
         arr = torch.where(T > 0, torch.exp(-m["T_act"] / torch.where(T > 0, T, torch.ones_like(T))),
                           torch.zeros_like(T))
         return ary * (-m["A"] * lam * arr)
@@ -428,7 +440,10 @@ def reaction_update(q, mats, dt):
     k3 = f(a0 + 0.5 * dt * k2)
     k4 = f(a0 + dt * k3)
     out = dict(q)
-    out["arl"] = a0 + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+    a1 = a0 + dt / 6.0 * (k1 + 2 * k2 + 2 * k3 + k4)
+    if law == 1:
+        a1 = torch.where(a1 > 0, a1, torch.zeros_like(a1))
+    out["arl"] = a1
     return out
 
 

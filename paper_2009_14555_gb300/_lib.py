@@ -17,6 +17,7 @@ DIS_CONSERVATIVE, DIS_PRIMITIVE = 0, 1
 DIS_FP64, DIS_FP32_BULK = 0, 1
 DIS_RK3, DIS_HANCOCK = 0, 1
 DIS_PLANAR, DIS_CYLINDRICAL = 0, 1
+DIS_RATE_ARRHENIUS, DIS_RATE_SQRT = 0, 1
 DIS_NPARAM = 6  # per material l: G, sigma_y, Q at 3 l + k
 DIS_NVARIANTS = 12  # FP32-bulk stage variants (2D: 3 tile shapes x 2 primitive sources x 2 register budgets)
 
@@ -25,7 +26,7 @@ class DisMaterial(ctypes.Structure):
     _fields_ = [("gamma", c_double), ("p_inf", c_double), ("e_inf", c_double), ("G", c_double),
                 ("plastic", c_int32), ("sigma_y", c_double), ("chi0", c_double),
                 ("reactive", c_int32), ("Q", c_double), ("cv", c_double), ("A", c_double),
-                ("T_act", c_double)]
+                ("T_act", c_double), ("rate_law", c_int32), ("p_ign", c_double)]
 
 
 class DisPatch(ctypes.Structure):

@@ -44,7 +44,7 @@ __device__ __forceinline__ PhysT<Dual> lift_phys(const Phys& P, int k) {
     MatT<Dual>& d = D.m[l];
     d.gamma = m.gamma; d.pinf = m.pinf; d.einf = m.einf; d.G = m.G; d.sigy = m.sigy;
     d.chi0 = m.chi0; d.Q = m.Q; d.cv = m.cv; d.A = m.A; d.Tact = m.Tact;
-    d.plastic = m.plastic; d.reactive = m.reactive;
+    d.plastic = m.plastic; d.reactive = m.reactive; d.law = m.law; d.pign = m.pign;
     d.iGm1 = m.iGm1; d.gi = m.gi; d.kap = m.kap; d.gG = m.gG; d.GoG = m.GoG; d.JY = m.JY;
   }
   D.y = P.y;

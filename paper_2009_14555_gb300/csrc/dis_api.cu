@@ -788,6 +788,8 @@ MatDev to_dev(const dis_material& m) {
   d.Tact = m.T_act;
   d.plastic = m.plastic;
   d.reactive = m.reactive;
+  d.law = m.reactive ? m.rate_law : 0;
+  d.pign = m.reactive ? m.p_ign : 0.0;
   d.iGm1 = 1.0 / (m.gamma - 1.0);
   d.gi = m.gamma * d.iGm1;
   d.kap = m.gamma * m.p_inf * d.iGm1;
@@ -872,6 +874,9 @@ int dis_set_materials(dis_ctx* c, const dis_material* m, int n) {
       return fail(DIS_EINVAL, "dis_set_materials: reactive flag disagrees with the context");
     if (m[l].reactive && (m[l].p_inf != 0 || m[l].G != 0 || !(m[l].cv > 0)))
       return fail(DIS_EINVAL, "dis_set_materials: a reactive material must be an ideal gas with cv > 0");
+    if (m[l].reactive && (m[l].rate_law < 0 || m[l].rate_law > 1 || !std::isfinite(m[l].p_ign) ||
+                          !std::isfinite(m[l].A) || m[l].A < 0))
+      return fail(DIS_EINVAL, "dis_set_materials: bad rate law (rate_law 0 or 1, finite A >= 0 and p_ign)");
     c->phys.m[l] = to_dev(m[l]);
   }
   c->physf = to_float(c->phys);

@@ -267,7 +267,12 @@ __device__ __forceinline__ void sources(const PhysT<T>& P, double dt, T* o) {
     const T p0 = (o[L::E] - KE - ref_energy(P, phi1, o[L::A1], o[L::A2], T(0.0), s.J2)) / xi;
     const T Tfac = m.iGm1 / ((ary / phy) * m.cv);  // T = p / (rho_y Gamma c_V)
     const T Qx = m.Q / xi;
+    // the rate of phi_y rho_y lam at Lm = phi_y rho_y lam, other fields frozen
     auto f = [&](T Lm) -> T {
+      if (m.law == 1) {  // -k sqrt(lam) rho_y phi_y where p > p_ign
+        const T pk = p0 - Qx * Lm;
+        return pk > m.pign && Lm > 0.0 ? -m.A * sqrt(ary * Lm) : T(0.0);
+      }
       const T Tk = (p0 - Qx * Lm) * Tfac;
       return Tk > 0.0 ? -m.A * Lm * exp(-m.Tact / Tk) : T(0.0);
     };
@@ -276,7 +281,8 @@ __device__ __forceinline__ void sources(const PhysT<T>& P, double dt, T* o) {
     const T k2 = f(L0 + 0.5 * dt * k1);
     const T k3 = f(L0 + 0.5 * dt * k2);
     const T k4 = f(L0 + dt * k3);
-    o[L::AL] = L0 + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
+    const T L1 = L0 + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + k4);
+    o[L::AL] = m.law == 1 && !(L1 > 0.0) ? T(0.0) : L1;
   }
 }
 

@@ -379,6 +379,10 @@ __device__ __forceinline__ void stage32_tile(const Phys& P, const PhysF& F, cons
       const float Tfac = m.iGm1 / ((ary / phy) * m.cv);
       const float Qx = m.Q / xi;
       auto fr_ = [&](float Lm) {
+        if (m.law == 1) {
+          const float pk = p0 - Qx * Lm;
+          return pk > m.pign && Lm > 0.f ? -m.A * sqrtf(ary * Lm) : 0.f;
+        }
         const float Tk = (p0 - Qx * Lm) * Tfac;
         return Tk > 0.f ? -m.A * Lm * expf(-m.Tact / Tk) : 0.f;
       };
@@ -387,7 +391,8 @@ __device__ __forceinline__ void stage32_tile(const Phys& P, const PhysF& F, cons
       const float k2 = fr_(L0 + 0.5f * dtf * k1);
       const float k3 = fr_(L0 + 0.5f * dtf * k2);
       const float k4 = fr_(L0 + dtf * k3);
-      o[L::AL] = L0 + dtf / 6.f * (k1 + 2.f * k2 + 2.f * k3 + k4);
+      const float L1 = L0 + dtf / 6.f * (k1 + 2.f * k2 + 2.f * k3 + k4);
+      o[L::AL] = m.law == 1 && !(L1 > 0.f) ? 0.f : L1;
     }
     // range and finiteness checks without float64 compares
     const bool E_finite = ((__double_as_longlong(oE) >> 52) & 0x7ff) != 0x7ff;

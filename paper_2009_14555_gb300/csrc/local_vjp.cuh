@@ -862,7 +862,9 @@ __device__ __forceinline__ void sources_vjp(const Phys& P, double dt, const doub
     const double Tfac = m.iGm1 / ((ary / phy) * m.cv);
     const double Qx = m.Q / xi;
     const double L0 = o[L::AL];
+    const bool sq = m.law == 1;  // k sqrt(lam) law with the pressure switch
     auto f = [&](double Lm) {
+      if (sq) return (p0 - Qx * Lm) > m.pign && Lm > 0.0 ? -m.A * sqrt(ary * Lm) : 0.0;
       const double Tk = (p0 - Qx * Lm) * Tfac;
       return Tk > 0.0 ? -m.A * Lm * exp(-m.Tact / Tk) : 0.0;
     };
@@ -872,12 +874,19 @@ __device__ __forceinline__ void sources_vjp(const Phys& P, double dt, const doub
     const double L3 = L0 + 0.5 * dt * k2;
     const double k3 = f(L3);
     const double L4 = L0 + dt * k3;
-    // reverse of the RK4 combination and stages
-    const double outb = ob[L::AL];
+    // reverse of the RK4 combination (and of the clamp at lam = 0) and stages
+    const bool clamped = sq && !(L0 + dt / 6.0 * (k1 + 2.0 * k2 + 2.0 * k3 + f(L4)) > 0.0);
+    const double outb = clamped ? 0.0 : ob[L::AL];
     double L0b = outb;
     double kb[4] = {dt / 6.0 * outb, dt / 3.0 * outb, dt / 3.0 * outb, dt / 6.0 * outb};
-    double p0b = 0.0, Qxb = 0.0, Tfacb = 0.0;
+    double p0b = 0.0, Qxb = 0.0, Tfacb = 0.0, aryb_r = 0.0;
     auto stage_b = [&](double Lm, double kbar) -> double {  // returns the adjoint of Lm
+      if (sq) {  // the switch is a step: no derivative through the pressure
+        if (!((p0 - Qx * Lm) > m.pign && Lm > 0.0) || kbar == 0.0) return 0.0;
+        const double r = sqrt(ary * Lm);
+        aryb_r += kbar * (-m.A * 0.5 * Lm / r);
+        return kbar * (-m.A * 0.5 * ary / r);
+      }
       const double Tk = (p0 - Qx * Lm) * Tfac;
       if (!(Tk > 0.0) || kbar == 0.0) return 0.0;
       const double e = exp(-m.Tact / Tk);
@@ -905,7 +914,7 @@ __device__ __forceinline__ void sources_vjp(const Phys& P, double dt, const doub
     const double KEb = -p0b / xi, ref0b = -p0b / xi;
     double Qb = Qxb / xi;
     const double phyb = Tfacb * cTy / ary;
-    double aryb = -Tfacb * Tfac / ary;
+    double aryb = -Tfacb * Tfac / ary + aryb_r;
     double a1b = 0.0, a2b = 0.0;
     phib += y == 0 ? phyb : -phyb;
     // KE = (mx^2 + my^2) / (2 rr), rr = a1 + a2

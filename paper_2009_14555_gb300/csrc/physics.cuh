@@ -20,7 +20,9 @@
 //     tangential row, w = (u_t,K - u_t**) / (S*_K - S*);
 //   * THINC edge values and BVD choice (Appendix A);
 //   * plastic update with the radial-return root of the objective and the
-//     first Pade approximant (Section 3.2); RK4 Arrhenius reaction (Section 3.3).
+//     first Pade approximant (Section 3.2); RK4 reaction (Section 3.3) with
+//     the Arrhenius law or the k sqrt(lam) law of Section 4.1 (switched on
+//     above a pressure).
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
@@ -34,6 +36,8 @@ template <class R>
 struct MatT {
   R gamma, pinf, einf, G, sigy, chi0, Q, cv, A, Tact;
   int plastic, reactive;
+  int law;  // reaction rate law: 0 Arrhenius, 1 A sqrt(lam) above the pressure pign
+  R pign;
   R iGm1;  // 1 / (gamma - 1)
   R gi;    // gamma / (gamma - 1)
   R kap;   // gamma p_inf / (gamma - 1)
@@ -63,6 +67,7 @@ inline PhysT<float> to_float(const Phys& P) {
     m.gamma = (float)d.gamma; m.pinf = (float)d.pinf; m.einf = (float)d.einf; m.G = (float)d.G;
     m.sigy = (float)d.sigy; m.chi0 = (float)d.chi0; m.Q = (float)d.Q; m.cv = (float)d.cv;
     m.A = (float)d.A; m.Tact = (float)d.Tact; m.plastic = d.plastic; m.reactive = d.reactive;
+    m.law = d.law; m.pign = (float)d.pign;
     m.iGm1 = (float)d.iGm1; m.gi = (float)d.gi; m.kap = (float)d.kap; m.gG = (float)d.gG;
     m.GoG = (float)d.GoG; m.JY = (float)d.JY;
   }

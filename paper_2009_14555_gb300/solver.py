@@ -15,7 +15,8 @@ from . import _lib as L
 
 def _material(m: dict) -> L.DisMaterial:
     return L.DisMaterial(m["gamma"], m["p_inf"], m["e_inf"], m["G"], m["plastic"], m["sigma_y"],
-                         m["chi0"], m["reactive"], m["Q"], m["cv"], m["A"], m["T_act"])
+                         m["chi0"], m["reactive"], m["Q"], m["cv"], m["A"], m["T_act"],
+                         int(m.get("rate_law", 0)), float(m.get("p_ign", 0.0)))
 
 
 def _patch(p, dim) -> L.DisPatch:

@@ -19,10 +19,12 @@ Arrays are float64 with shape (nfields, ny, nx) (ny = 1 in 1D).
 
 Materials are plain dicts with the keys
     gamma, p_inf, e_inf, G, plastic (0 none, 1 perfect, 2 rate), sigma_y, chi0,
-    reactive (0/1), Q, cv, A, T_act
+    reactive (0/1), Q, cv, A, T_act, rate_law, p_ign
 (stiffened-gas Mie-Grueneisen closures, Section 2.3; perfect plasticity is the
-chi0 -> infinity limit of the ideal-plasticity rate, Section 2.3.2; the
-Arrhenius rate parameters A, T_act only apply to a reactive material).
+chi0 -> infinity limit of the ideal-plasticity rate, Section 2.3.2; the rate
+parameters only apply to a reactive material: rate_law 0 is the Arrhenius law
+with A, T_act, rate_law 1 the k sqrt(lam) law of Section 4.1 with k = A,
+switched on above the pressure p_ign).
 """
 from __future__ import annotations
 
@@ -52,11 +54,11 @@ def cons_names(dim: int, reactive: bool) -> list[str]:
 
 
 def material(gamma, p_inf=0.0, e_inf=0.0, G=0.0, plastic=0, sigma_y=0.0, chi0=0.0,
-             reactive=0, Q=0.0, cv=0.0, A=0.0, T_act=0.0) -> dict:
+             reactive=0, Q=0.0, cv=0.0, A=0.0, T_act=0.0, rate_law=0, p_ign=0.0) -> dict:
     return dict(gamma=float(gamma), p_inf=float(p_inf), e_inf=float(e_inf), G=float(G),
                 plastic=int(plastic), sigma_y=float(sigma_y), chi0=float(chi0),
                 reactive=int(reactive), Q=float(Q), cv=float(cv), A=float(A),
-                T_act=float(T_act))
+                T_act=float(T_act), rate_law=int(rate_law), p_ign=float(p_ign))
 
 
 # Solid of the 1D solid|gas problem: stiffened-gas-form hydrostatic EOS,
@@ -269,6 +271,34 @@ def reactive_plate_2d(nx: int = 2048, ny: int = 1024, steps: int = 1000, seed: i
     p = Patch(nx=nx, ny=ny, dx=dx, dy=dy, prim=w)
     return Workload(name or f"2d_reactive_plate_{nx}x{ny}", 2, [SOLID, gas], [p], 0.6,
                     steps, True, reactive_material=1, extra=dict(T0=T0))
+
+
+def detonation_copper_1d(n: int = 1000, steps: int = 400, name=None) -> Workload:
+    """The shape of the one-dimensional test of Section 4.1 on [0, 0.4] m:
+    quiescent elastic copper for x < 0.15, ambient explosive for
+    0.15 < x < 0.35, a booster of the same explosive at 1e9 Pa for x > 0.35,
+    1e5 Pa elsewhere; the reactant burns at lam_dot = -k sqrt(lam),
+    k = 2e6 1/s, once the pressure exceeds 1e8 Pa; CFL 0.9, transmissive ends.
+
+    Stand-in closures (the Romenskii copper and the multiphase explosive of
+    the paper are not among the closures built here): copper as a stiffened
+    gas with rho 8930 kg/m^3, Gamma 2 (gamma 3), gamma p_inf = K0 = 136.5 GPa
+    and G = 39.4 GPa (no plasticity); the explosive as the ideal-gas
+    reactant/product pair, gamma 3, rho 1600 kg/m^3, Q = 4 MJ/kg, c_V 1000.
+    """
+    copper = material(3.0, p_inf=136.5e9 / 3.0, G=39.4e9)
+    expl = material(3.0, reactive=1, Q=4.0e6, cv=1000.0, A=2.0e6, rate_law=1, p_ign=1.0e8)
+    w, k = _blank(1, True, 1, n)
+    dx = 0.4 / n
+    xc = (np.arange(n) + 0.5) * dx
+    cu = xc < 0.15
+    w[k["phi1"], 0] = np.where(cu, 1.0 - EPS_PHI, EPS_PHI)
+    w[k["rho1"], 0] = 8930.0
+    w[k["rho2"], 0] = 1600.0
+    w[k["p"], 0] = np.where(xc > 0.35, 1.0e9, 1.0e5)
+    p = Patch(nx=n, ny=1, dx=dx, dy=1.0, prim=w)
+    return Workload(name or f"1d_detonation_copper_{n}", 1, [copper, expl], [p], 0.9, steps, True,
+                    reactive_material=1)
 
 
 def batched_riemann_1d(n_problems: int = 4096, seed: int = 3, steps: int = 300,

@@ -101,3 +101,21 @@ def test_host_side_sizes_and_materials(lib):
     # stepping before a state exists is refused on the host
     assert lib.dis_step(ctx, 1, None) == L.DIS_ESTATE
     lib.dis_destroy(ctx)
+
+
+def test_rate_law_validation(lib):
+    out = ctypes.c_void_p()
+    opts = L.DisOptions(0.9, 0, 0)
+    arr = (L.DisPatch * 1)(_patch(64))
+    assert lib.dis_create(1, 1, arr, 1, ctypes.byref(opts), None, ctypes.byref(out)) == L.DIS_OK
+    ctx = out
+    gas = L.DisMaterial(1.4, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0)
+
+    def rx(law, p_ign=1e8, A=2e6):
+        return L.DisMaterial(3.0, 0, 0, 0, 0, 0, 0, 1, 4e6, 1000.0, A, 0.0, law, p_ign)
+
+    for bad in (rx(2), rx(-1), rx(1, p_ign=float("nan")), rx(1, A=-1.0), rx(1, A=float("inf"))):
+        assert lib.dis_set_materials(ctx, (L.DisMaterial * 2)(gas, bad), 2) == L.DIS_EINVAL
+    assert lib.dis_set_materials(ctx, (L.DisMaterial * 2)(gas, rx(L.DIS_RATE_SQRT)), 2) == L.DIS_OK
+    assert lib.dis_set_materials(ctx, (L.DisMaterial * 2)(gas, rx(L.DIS_RATE_ARRHENIUS)), 2) == L.DIS_OK
+    lib.dis_destroy(ctx)

@@ -149,6 +149,20 @@ def test_adjoint_reactive_vs_oracle():
     _case("2d_reactive_plate_96x48_3", wl, 3, material=1, qbar_seed=5, params=(0, 1, 5))
 
 
+def _detonation_partial_burn():
+    # the k sqrt(lam) law with its pressure switch (Section 4.1), k lowered to
+    # 2e5 1/s so that at 100 cells the booster burns over several steps
+    # (partially burnt cells rather than a clamp to lam = 0 in one step)
+    wl = W.perturbed(W.detonation_copper_1d(100, steps=8))
+    wl.materials[1]["A"] = 2e5
+    return wl
+
+
+def test_adjoint_sqrt_rate_law_vs_oracle():
+    _case("1d_detonation_sqrt_law_100_8", _detonation_partial_burn(), 8, material=1, qbar_seed=6,
+          params=(0, 5))
+
+
 def test_adjoint_smooth_vs_oracle():
     wl = W.perturbed(W.smooth_disc_2d(n=16, steps=8, sigma_y=4e7))
     _case("2d_smooth_disc_16_8", wl, 8, material=0)
@@ -312,38 +326,52 @@ def test_adjoint_of_fp32_bulk_run_matches_float64_adjoint():
     assert max(el1) <= 5e-2, el1
 
 
-@pytest.mark.parametrize("case", ["1d", "2d_thinc", "reactive"])
+@pytest.mark.parametrize("case", ["1d", "2d_thinc", "reactive", "sqrt_law"])
 def test_hand_written_reverses_match_dual_numbers(case):
     """The hand-written reverses of the face Riemann problem (all six regions
     of the HLLD-type solver, shear coupling, wave-speed ties), the face-state
     map, the THINC-BVD edge values, the primitive recovery and the source steps
-    (plastic return, RK4 reaction) give the gradient of the dual-number
-    reference to rounding: measured 1e-15 .. 2.6e-10 per field and parameter
+    (plastic return, RK4 reaction with either rate law) give the gradient of the dual-number
+    reference to rounding: measured 1e-15 .. 4.4e-10 per field and parameter
     (the larger values in partial-density and shear-modulus gradients, sums
-    with cancellation); bar 1e-9."""
+    with cancellation), 2e-9 for the 3e-13 shear-modulus gradient of the
+    detonation case; bar max(1e-9, 10 x the reference's one-ulp spread)."""
     from paper_2009_14555_gb300.solver import Solver
     wl, steps, mat = {
         "1d": (W.perturbed(W.solid_gas_1d(n=100, steps=12)), 12, 0),
         "2d_thinc": (W.perturbed(W.shock_disc_2d(n=20, steps=4, thinc=True, shock_x=0.3)), 4, 0),
         "reactive": (W.perturbed(W.reactive_plate_2d(nx=48, ny=24, steps=3)), 3, 1),
+        "sqrt_law": (_detonation_partial_burn(), 8, 1),
     }[case]
+    rng = np.random.default_rng(123)
+    p0 = wl.patches[0].prim
+    pu = p0 * (1 + np.sign(rng.standard_normal(p0.shape)) * 2.0 ** -52)
     out = []
-    for ref in (False, True):
+    for ref, prim in ((False, p0), (True, p0), (True, pu)):
         s = Solver.from_workload(wl)
         s.adj_reference(ref)
-        s.set_prim([p.prim for p in wl.patches])
+        s.set_prim([prim])
         s.adj_forward(steps, every=3, material=mat)
         rng = np.random.default_rng(8)
         out.append(s.adjoint(rng.standard_normal(s.state_numel) * 1e-3, 1.0, kind=1))
         s.close()
-    (g, gp), (gr, gpr) = out
-    shape = wl.patches[0].prim.shape
+    (g, gp), (gr, gpr), (gu, gpu_) = out
+    shape = p0.shape
+
+    def perr(a, b):
+        return [abs(x - y) / max(abs(y), 1e-300) if y != 0.0 else abs(x) for x, y in zip(a, b)]
+
     e = field_err(g.reshape(shape), gr.reshape(shape))
-    ep = [abs(a - b) / max(abs(b), 1e-300) for a, b in zip(gp, gpr) if b != 0.0]
-    _record[f"hand_vs_dual_{case}"] = dict(field_err=e, param_err=ep)
+    ep = perr(gp, gpr)
+    # the reference form's own spread under one-ulp input perturbations: a
+    # parameter gradient that is a sum with heavy cancellation (the copper's
+    # shear modulus before any wave reaches it, 3e-13) is only that well defined
+    bar = [max(1e-9, 10 * x) for x in field_err(gu.reshape(shape), gr.reshape(shape))]
+    pbar = [max(1e-9, 10 * x) for x in perr(gpu_, gpr)]
+    _record[f"hand_vs_dual_{case}"] = dict(field_err=e, param_err=ep, field_bar=bar, param_bar=pbar)
     _save()
-    assert max(e) <= 1e-9, e
-    assert max(ep, default=0.0) <= 1e-9, ep
+    assert all(x <= b for x, b in zip(e, bar)), (e, bar)
+    assert all(x <= b for x, b in zip(ep, pbar)), (ep, pbar)
 
 
 def test_autograd_function_matches_library_adjoint():
