@@ -299,6 +299,11 @@ def run_gpu(args):
     line["fp64"]["hancock"]["speedup_vs_rk3"] = line["fp64"]["hancock"]["value"] / value64
     if not args.no_batch:
         line["batch_1d"] = batch_bench()
+    if not args.no_widened:
+        try:
+            line["widened_rows"] = widened_bench(args.warmup)
+        except Exception as e:  # the headline line above is measured: still print it
+            line["widened_rows"] = {"error": repr(e)}
     if not args.no_adjoint:
         line["adjoint"] = adjoint_bench()
     if rank == 0 and not args.no_cpu_baseline and world == 1:
@@ -342,6 +347,59 @@ def adjoint_bench(n=256, steps=200, every=20):
         out[prec] = {"forward_s": t1 - t0, "reverse_s": t2 - t1,
                      "reverse_cell_updates_per_s": cells * steps / (t2 - t1),
                      "reverse_over_forward": (t2 - t1) / (t1 - t0), "J": J, "status_ok": ok}
+    return out
+
+
+def _timed_steps(wl, prim, precision, steps, warmup, **kw):
+    """cell-updates/s of `steps` steps after `warmup` (device events on the
+    solver's stream, inputs resident)."""
+    import torch
+    from paper_2009_14555_gb300.solver import Solver
+    s = Solver.from_workload(wl, precision=precision, **kw)
+    s.set_state(prim, kind=1)
+    s.step(warmup)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s.stream)
+    s.step(steps)
+    e1.record(s.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    rc = s.check()[0]
+    s.close()
+    return {"value": wl.cells / (ms * 1e-3), "ms_per_step": ms, "steps": steps, "status_ok": rc == 0}
+
+
+def widened_bench(warmup=3):
+    """The rows beyond the planar Arrhenius step, on full-size inputs.
+
+    Cylindrical geometry: the shock-sphere problem in (r, z), 1024 x 2048
+    cells, stepped with the geometric source and, for the cost of s_g, the
+    same input in planar geometry.  The k sqrt(lam) reaction law: 1024 copies
+    of the 4000-cell detonation-into-copper problem (the resolution of the
+    paper's one-dimensional test) in one batch."""
+    import copy
+    from paper_2009_14555_gb300 import workloads as W
+    from paper_2009_14555_gb300.solver import pack
+    out = {}
+    wl = W.sphere_shock_rz(2048, steps=0)
+    prim = pack([p.prim for p in wl.patches])
+    cyl = {"workload": "2d_sphere_shock_rz_1024x2048 (x = r, y = z)", "cells": wl.cells}
+    for prec, steps in (("fp32_bulk", 200), ("fp64", 30)):
+        c = _timed_steps(wl, prim, prec, steps, warmup)
+        p = _timed_steps(wl, prim, prec, steps, warmup, geometry="planar")
+        cyl[prec] = dict(c, planar_ms_per_step=p["ms_per_step"],
+                         cyl_over_planar=c["ms_per_step"] / p["ms_per_step"])
+    out["cylindrical"] = cyl
+    one = W.detonation_copper_1d(4000, steps=0)
+    wl = copy.copy(one)
+    wl.patches = [one.patches[0]] * 1024
+    prim = pack([p.prim for p in wl.patches])
+    det = {"workload": "1d_detonation_copper_4000 x 1024 (k sqrt(lam) law, pressure switch)",
+           "cells": wl.cells}
+    for prec, steps in (("fp32_bulk", 200), ("fp64", 30)):
+        det[prec] = _timed_steps(wl, prim, prec, steps, warmup)
+    out["sqrt_rate_law"] = det
     return out
 
 
@@ -465,6 +523,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 1D measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-case measurement")
+    ap.add_argument("--no-widened", action="store_true",
+                    help="skip the cylindrical-geometry and k sqrt(lam) measurements")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--nx", type=int, default=None, help="profiling only: smaller grid")
     ap.add_argument("--ny", type=int, default=None, help="profiling only: smaller grid")

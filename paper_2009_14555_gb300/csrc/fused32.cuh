@@ -306,14 +306,19 @@ __device__ __forceinline__ void stage32_tile(const Phys& P, const PhysF& F, cons
                                 Wsm[L::V33 * plane + kc]);
     const float Gm2 = 2.f * (wphi * F.m[0].GoG + (1.f - wphi) * F.m[1].GoG) / xi_f(F, wphi);
     const float srr = -wp + Gm2 * st.H11, szr = Gm2 * st.H12, stt = -wp + Gm2 * st.H33;
-    const double r = pd.x0 + (i + 0.5) * pd.dx;
-    const float ir = (float)(1.0 / r);
+    // 1/r without a float64 division (the FP64 pipe also carries the
+    // phi1 / rho E update): the float32 reciprocal, refined by one
+    // Newton-Raphson step x <- x + x (1 - r x) to ~1e-14 relative
+    const double r = fma((double)(i) + 0.5, pd.dx, pd.x0);
+    double ird = (double)(1.f / (float)r);
+    ird = fma(ird, fma(-r, ird, 1.0), ird);
+    const float ir = (float)ird;
     D[L::A1] += q[L::A1] * wu * ir;
     D[L::A2] += q[L::A2] * wu * ir;
     if constexpr (RX) D[L::AL] += q[L::AL] * wu * ir;
     D[L::MX] += (rho * wu * wu - srr + stt) * ir;
     if constexpr (DIM == 2) D[L::MY] += (rho * wv * wu - szr) * ir;
-    DE += (E_d * (double)wu - (double)(wu * srr + wv * szr)) / r;
+    DE = fma(fma(E_d, (double)wu, -(double)(wu * srr + wv * szr)), ird, DE);
     const float t = wu * ir * (1.f / 3.f);
     D[L::V11] += t * q[L::V11];
     D[L::V22] += t * q[L::V22];
