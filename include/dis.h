@@ -274,9 +274,11 @@ int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
  * and face outputs (about 3.5 states each), allocated here, kept for dis_adjoint and
  * released by dis_destroy.  FP32-bulk contexts checkpoint their states in
  * float64 (plus float64 primitive and face buffers for the reverse sweep).
- * Returns DIS_EINVAL (bad arguments, or a DIS_HANCOCK or DIS_CYLINDRICAL
- * context: the adjoint covers the planar Runge-Kutta scheme), DIS_ESTATE (no
- * state), DIS_ENOMEM,
+ * In a 1D DIS_CYLINDRICAL context the geometric source of Section 3 is
+ * reversed with the rest of the stage, and J is the same plain sum over cells
+ * (no factor r).  Returns DIS_EINVAL (bad arguments, a DIS_HANCOCK context:
+ * the adjoint covers the Runge-Kutta scheme, or a 2D DIS_CYLINDRICAL
+ * context), DIS_ESTATE (no state), DIS_ENOMEM,
  * DIS_ECUDA.  Synchronises. */
 int dis_adj_forward(dis_ctx* ctx, int n_steps, int checkpoint_every, int objective_material,
                     const double* dt_in, double* dt_out, double* J_out);

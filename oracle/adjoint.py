@@ -29,7 +29,7 @@ def rollout(init, kind, dim, mats, patch, opts, steps, material=-1, qbar=None, d
         q = prim_to_cons(prim_from_array(init, dim, reactive), mats)
     else:
         q = cons_from_array(init, dim, reactive)
-    grid = grid_of(patch, dim)
+    grid = grid_of(patch, dim, opts.get("geometry", "planar"))
     dA = patch.dx * (patch.dy if dim == 2 else 1.0)
     J = torch.zeros((), dtype=torch.float64)
     used = []

@@ -270,8 +270,8 @@ int adj_forward(dis_ctx* c, int n_steps, int mat, bool prescribed) {
 // hand-reversed local maps).
 template <int DIM, bool RX, bool REF>
 void reverse_kernels(dis_ctx* c, const AdjArgs& A) {
-  k_adj_cell<DIM, RX, REF><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, A, c->d_seg_cell);
   cudaMemsetAsync(c->adj->Wb, 0, sizeof(double) * (size_t)c->nf * c->T, c->stream);
+  k_adj_cell<DIM, RX, REF><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, A, c->d_seg_cell);
   k_adj_face<DIM, RX, 0, REF><<<(unsigned)c->seg_fx.size(), SEG, 0, c->stream>>>(c->phys, A, c->d_seg_fx);
   if constexpr (DIM == 2)
     k_adj_face<DIM, RX, 1, REF><<<(unsigned)c->seg_fy.size(), SEG, 0, c->stream>>>(c->phys, A, c->d_seg_fy);
@@ -378,9 +378,10 @@ int dis_adj_forward(dis_ctx* c, int n_steps, int checkpoint_every, int objective
                     double* dt_out, double* J_out) {
   if (!c) return dis_internal_error(DIS_EINVAL, "dis_adj_forward: NULL context");
   if (!c->have_state) return dis_internal_error(DIS_ESTATE, "dis_adj_forward: no state loaded");
-  if (c->hancock || c->phys.cyl)
-    return dis_internal_error(DIS_EINVAL,
-                              "dis_adj_forward: the adjoint covers the planar Runge-Kutta scheme only");
+  if (c->hancock)
+    return dis_internal_error(DIS_EINVAL, "dis_adj_forward: the adjoint covers the Runge-Kutta scheme only");
+  if (c->phys.cyl && c->dim == 2)
+    return dis_internal_error(DIS_EINVAL, "dis_adj_forward: cylindrical geometry is covered in 1D only");
   if (n_steps <= 0 || checkpoint_every <= 0)
     return dis_internal_error(DIS_EINVAL, "dis_adj_forward: n_steps and checkpoint_every must be positive");
   if (objective_material < -1 || objective_material > 1)

@@ -106,7 +106,7 @@ struct AdjArgs {
   double* xbar;        // adjoint of x (written by k_adj_cell, accumulated by k_adj_prim)
   double* qnacc;       // accumulated adjoint of q^n
   double* G;           // per-cell face coefficients, NF + NX_EXTRA planes
-  double* Wbar;        // adjoint of W, NF planes (zeroed before k_adj_face)
+  double* Wbar;        // adjoint of W, NF planes (zeroed before k_adj_cell)
   double* theta;       // parameter adjoints [NPARAM]
   const double* dt;    // per-patch dt of the step
   double a, b;
@@ -257,6 +257,18 @@ __global__ void __launch_bounds__(SEG) k_adj_cell(Phys P, AdjArgs A, const int4*
     }
     xb[L::A1] += rb;
     xb[L::A2] += rb;
+    if (P.cyl) {
+      // geometric source: into xbar and into Wbar of this cell (zeroed
+      // before this kernel; the face kernels add to it afterwards)
+      Prim wb{};
+      double thg[NPARAM] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      geometric_vjp<DIM, RX>(P, q, load_prim<DIM, RX>(A.W, T, k), pd.x0 + (i + 0.5) * pd.dx, Db, xb, wb, thg);
+#pragma unroll
+      for (int c = 0; c < NF; ++c) A.Wbar[c * T + k] = prim_slot<DIM, RX>(wb, c);
+#pragma unroll
+      for (int kk = 0; kk < NPARAM; ++kk)
+        if ((A.pmask >> kk) & 1u) th[kk] += thg[kk];
+    }
 #pragma unroll
     for (int c = 0; c < NF; ++c) {
       A.xbar[c * T + k] = xb[c];

@@ -403,6 +403,81 @@ __device__ __forceinline__ void strain_vjp(double a, double b, double c, double 
   eb += 2.0 * e * B33b;
 }
 
+// Adjoint of the cylindrical geometric source (add_geometric, step_kernels.cuh;
+// the s_g of Section 3 with x = r): given Db, the adjoint of the stage operator
+// D at a cell of radius r, add the adjoints of the cell's conservative state q
+// (qb), of its primitives w (wb: p, u, v, phi and V through the stress) and of
+// the shear moduli G_1, G_2 (thb[0], thb[3]; may be null).
+template <int DIM, bool RX>
+__device__ __forceinline__ void geometric_vjp(const Phys& P, const double* q, const Prim& w, double r,
+                                              const double* Db, double* qb, Prim& wb, double* thb) {
+  using L = Lay<DIM, RX>;
+  const double ir = 1.0 / r;
+  const Strain st = strain_of(w.V11, w.V12, w.V21, w.V22, w.V33);
+  const double xi = xi_of(P, w.phi);
+  const double Nm = w.phi * P.m[0].GoG + (1.0 - w.phi) * P.m[1].GoG;
+  const double Gm2 = 2.0 * Nm / xi;
+  const double srr = -w.p + Gm2 * st.H11, szr = Gm2 * st.H12;
+  const double ur = w.u, uz = DIM == 2 ? w.v : 0.0;
+  const double rho = q[L::A1] + q[L::A2];
+  double urb = 0.0, uzb = 0.0, srrb = 0.0, szrb = 0.0, sttb = 0.0, rhob = 0.0;
+  // D_l += q_l u_r / r for the partial densities (and phi_y rho_y lam)
+  qb[L::A1] += Db[L::A1] * ur * ir;
+  qb[L::A2] += Db[L::A2] * ur * ir;
+  urb += (Db[L::A1] * q[L::A1] + Db[L::A2] * q[L::A2]) * ir;
+  if constexpr (RX) {
+    qb[L::AL] += Db[L::AL] * ur * ir;
+    urb += Db[L::AL] * q[L::AL] * ir;
+  }
+  // D_mr += (rho u_r^2 - s_rr + s_tt) / r
+  rhob += Db[L::MX] * ur * ur * ir;
+  urb += Db[L::MX] * 2.0 * rho * ur * ir;
+  srrb -= Db[L::MX] * ir;
+  sttb += Db[L::MX] * ir;
+  if constexpr (DIM == 2) {  // D_mz += (rho u_z u_r - s_zr) / r
+    rhob += Db[L::MY] * uz * ur * ir;
+    uzb += Db[L::MY] * rho * ur * ir;
+    urb += Db[L::MY] * rho * uz * ir;
+    szrb -= Db[L::MY] * ir;
+  }
+  // D_E += (rho E u_r - u_r s_rr - u_z s_zr) / r
+  qb[L::E] += Db[L::E] * ur * ir;
+  urb += Db[L::E] * (q[L::E] - srr) * ir;
+  uzb -= Db[L::E] * szr * ir;
+  srrb -= Db[L::E] * ur * ir;
+  szrb -= Db[L::E] * uz * ir;
+  // D_Vij += u_r V_ij / (3 r) (i not theta), D_V33 += (1/3 - 1) u_r V33 / r
+  const double t = (1.0 / 3.0) * ur * ir;
+  double tb = Db[L::V11] * q[L::V11] + Db[L::V22] * q[L::V22];
+  qb[L::V11] += Db[L::V11] * t;
+  qb[L::V22] += Db[L::V22] * t;
+  if constexpr (DIM == 2) {
+    tb += Db[L::V12] * q[L::V12] + Db[L::V21] * q[L::V21];
+    qb[L::V12] += Db[L::V12] * t;
+    qb[L::V21] += Db[L::V21] * t;
+  }
+  urb += tb * (1.0 / 3.0) * ir;
+  qb[L::V33] += Db[L::V33] * (1.0 / 3.0 - 1.0) * ur * ir;
+  urb += Db[L::V33] * (1.0 / 3.0 - 1.0) * q[L::V33] * ir;
+  qb[L::A1] += rhob;
+  qb[L::A2] += rhob;
+  // s_rr = -p + Gm2 H11, s_zr = Gm2 H12, s_tt = -p + Gm2 H33
+  wb.p -= srrb + sttb;
+  const double Gm2b = srrb * st.H11 + szrb * st.H12 + sttb * st.H33;
+  strain_vjp(w.V11, w.V12, w.V21, w.V22, w.V33, srrb * Gm2, szrb * Gm2, 0.0, sttb * Gm2, 0.0, wb.V11, wb.V12,
+             wb.V21, wb.V22, wb.V33);
+  // Gm2 = 2 N / xi, N = phi GoG_1 + (1 - phi) GoG_2, xi = phi iGm1_1 + (1 - phi) iGm1_2
+  const double Nb = 2.0 * Gm2b / xi, xib = -Gm2b * Gm2 / xi;
+  wb.phi += Nb * (P.m[0].GoG - P.m[1].GoG) + xib * (P.m[0].iGm1 - P.m[1].iGm1);
+  if (thb) {  // GoG_l = G_l / Gamma_l
+    thb[0] += Nb * w.phi * P.m[0].iGm1;
+    thb[3] += Nb * (1.0 - w.phi) * P.m[1].iGm1;
+  }
+  wb.u += urb;
+  if constexpr (DIM == 2) wb.v += uzb;
+}
+
+
 // Adjoint of face_state (primitives -> face state, physics.cuh) at the
 // primitive state w: Sb is the adjoint of the face state (c_L squared, as
 // face_state returns it); the primitive adjoints are added to wb and, where

@@ -72,7 +72,8 @@ def oracle_grad(wl, steps, material, qbar=None, kind="prim", prim=None):
         q0 = prim_to_cons(OS.prim_from_array(w0, wl.dim, wl.reactive), wl.materials)
         init = OS.cons_to_array(q0, wl.dim, wl.reactive).detach().clone().requires_grad_(True)
     J, _, dts = OA.rollout(init, kind, wl.dim, OA.with_params(wl.materials, theta), p,
-                           dict(cfl=wl.cfl, thinc=wl.thinc), steps, material,
+                           dict(cfl=wl.cfl, thinc=wl.thinc, geometry=getattr(wl, "geometry", "planar")),
+                           steps, material,
                            None if qbar is None else qbar[0])
     J.backward()
     return float(J), init.grad.numpy(), theta.grad.numpy(), dts
@@ -161,6 +162,22 @@ def _detonation_partial_burn():
 def test_adjoint_sqrt_rate_law_vs_oracle():
     _case("1d_detonation_sqrt_law_100_8", _detonation_partial_burn(), 8, material=1, qbar_seed=6,
           params=(0, 5))
+
+
+def test_adjoint_cylindrical_1d_vs_oracle():
+    # implosion onto a solid core in r (the geometric source of Section 3)
+    wl = W.perturbed(W.cylinder_core_1d(100, steps=12))
+    _case("1d_cylinder_core_100_12", wl, 12, material=0, qbar_seed=7, params=(0,))  # no yield: dJ/dsigma_Y = 0
+
+
+def test_adjoint_refuses_2d_cylindrical():
+    from paper_2009_14555_gb300.solver import Solver
+    wl = W.sphere_shock_rz(24, steps=2, thinc=False)
+    s = Solver.from_workload(wl)
+    s.set_prim([p.prim for p in wl.patches])
+    with pytest.raises(RuntimeError):
+        s.adj_forward(2, every=1, material=0)
+    s.close()
 
 
 def test_adjoint_smooth_vs_oracle():

@@ -63,13 +63,3 @@ def test_homologous_expansion_doubles_the_density_rate():
     d_pl = (g_pl[0][1, 0, inner] + g_pl[0][2, 0, inner]) - rho0
     ratio = d_cyl.mean() / d_pl.mean()
     assert 1.9 < ratio < 2.1, ratio
-
-
-def test_adjoint_refuses_cylindrical():
-    from paper_2009_14555_gb300.solver import Solver
-    wl = W.cylinder_core_1d(64, steps=2)
-    s = Solver.from_workload(wl)
-    s.set_prim([p.prim for p in wl.patches])
-    with pytest.raises(RuntimeError):
-        s.adj_forward(2, every=1, material=0)
-    s.close()

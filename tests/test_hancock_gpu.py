@@ -133,3 +133,13 @@ def test_hancock_refuses_adjoint_and_fp32():
     s.close()
     with pytest.raises(RuntimeError):
         Solver.from_workload(wl, precision="fp32_bulk")
+
+
+def test_adjoint_refuses_hancock():
+    from paper_2009_14555_gb300.solver import Solver
+    wl = W.solid_gas_1d(n=64, steps=2)
+    s = Solver.from_workload(wl, scheme="hancock")
+    s.set_prim([p.prim for p in wl.patches])
+    with pytest.raises(RuntimeError):
+        s.adj_forward(2, every=1, material=0)
+    s.close()
