@@ -10,15 +10,19 @@ it; the CUDA library never does, and it shares no code with it.
 Modules:
   closures        equations of state, mixture rules, strain, stress (Sec. 2.2-2.3, App. B)
   reconstruction  MUSCL, THINC, BVD, Youngs normal (Sec. 3.1, App. A)
-  riemann         HLLC-type elastic Riemann solver (Sec. 3.1; reading of the
-                  unprinted HLLD of Barton 2019)
+  riemann         HLLD-type elastic Riemann solver (Sec. 3.1; a reading of the
+                  unprinted HLLD of Barton 2019, from the jump conditions)
   scheme          ghost cells, spatial operator, RK3, CFL, plastic and reactive
-                  updates (Sec. 3, 3.1-3.3)
+                  updates (Arrhenius or k sqrt(lam) rate), cylindrical
+                  geometric source (Sec. 3, 3.1-3.3, 4.1)
+  hancock         single-stage MUSCL-Hancock form of the hyperbolic update
+  adjoint         reverse mode of the step (PyTorch autograd through the above)
 
-Parity pins live in tests/test_oracle_*.py.  Functions without an independent
-pin are listed as "parity unpinned" there and in the design notes: the full 2D
-shock-disc and reactive-plate dynamics (checked only through conservation,
-boundedness and symmetry).
+Pins live in tests/test_oracle_*.py: exact Riemann solutions, closed forms,
+invariants, convergence orders and brute-force checks, one or more per
+function.  Whole 2D runs (shock-disc, reactive plate) have no closed form; on
+top of their functions' pins they are checked through conservation,
+boundedness and symmetry.
 """
 from .scheme import (run, step, spatial_operator, cfl_dt, cfl_rate, plastic_update,  # noqa: F401
                      reaction_update, prim_from_array, cons_from_array, cons_to_array,

@@ -1,4 +1,4 @@
-"""Oracle Riemann solver: HLLC-type flux for the elastic diffuse-interface system.
+"""Oracle Riemann solver: HLLD-type flux for the elastic diffuse-interface system.
 
 TEST INFRASTRUCTURE ONLY (plain PyTorch CPU float64).
 
