@@ -4,8 +4,9 @@
  * One explicit time step of the unified diffuse-interface system for
  * multiphase reactive fluids and elastoplastic solids on regular Cartesian
  * patches (Wallis, Barton & Nikiforakis, arXiv 2009.14555, Section 3):
- * CFL time step, SSP-RK3 hyperbolic update with MUSCL(-BVD-THINC)
- * reconstruction of primitives and an HLLC-type elastic Riemann solver,
+ * CFL time step, SSP-RK3 (or single-stage MUSCL-Hancock) hyperbolic update
+ * with MUSCL(-BVD-THINC) reconstruction of primitives and an HLLD-type
+ * elastic Riemann solver (Section 3.1), in planar or cylindrical geometry,
  * then the plastic (Section 3.2) and reactive (Section 3.3) source steps.
  *
  * Conventions shared by every call:
