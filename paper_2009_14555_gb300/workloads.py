@@ -283,11 +283,13 @@ def detonation_copper_1d(n: int = 1000, steps: int = 400, name=None) -> Workload
     Stand-in closures (the Romenskii copper and the multiphase explosive of
     the paper are not among the closures built here): copper as a stiffened
     gas with rho 8930 kg/m^3, Gamma 2 (gamma 3), gamma p_inf = K0 = 136.5 GPa
-    and G = 39.4 GPa (no plasticity); the explosive as the ideal-gas
-    reactant/product pair, gamma 3, rho 1600 kg/m^3, Q = 4 MJ/kg, c_V 1000.
+    and G = 39.4 GPa (no plasticity), the Romenskii table's rho_0, K_0, G_0
+    and Gamma; the explosive as an ideal-gas reactant/product pair with the
+    product's gamma 3, c_V 1000 and Q = 3.68 MJ/kg and the reactant's
+    rho_0 = 1600 kg/m^3 from the table of the generic explosive.
     """
     copper = material(3.0, p_inf=136.5e9 / 3.0, G=39.4e9)
-    expl = material(3.0, reactive=1, Q=4.0e6, cv=1000.0, A=2.0e6, rate_law=1, p_ign=1.0e8)
+    expl = material(3.0, reactive=1, Q=3.68e6, cv=1000.0, A=2.0e6, rate_law=1, p_ign=1.0e8)
     w, k = _blank(1, True, 1, n)
     dx = 0.4 / n
     xc = (np.arange(n) + 0.5) * dx

@@ -30,7 +30,7 @@ def test_detonation_fp64_into_copper():
 def test_detonation_burns_and_reaches_copper():
     """The GPU run itself: the booster initiates a detonation near the
     ideal-gas Chapman-Jouguet pressure rho0 D^2 / (gamma + 1), D^2 =
-    2 (gamma^2 - 1) Q (2.6e10 Pa here), the burnt region has lam = 0 exactly
+    2 (gamma^2 - 1) Q (2.4e10 Pa here), the burnt region has lam = 0 exactly
     (the clamp), and the copper ahead is shocked."""
     wl = W.detonation_copper_1d(200, steps=140)
     _, prim, _ = gpu_run(wl, 140)
