@@ -234,7 +234,7 @@ int adj_forward(dis_ctx* c, int n_steps, int mat, bool prescribed) {
     if (c->fp32) {
       // FP32-bulk step; float64 checkpoints of its states
       if (n % d->every == 0)
-        k_state32_to_64<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, c->q64[0], c->q32[0], ck, c->T);
+        k_state32_to_64<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->phys, c->d_pd, c->d_seg_cell, c->q32[0], ck, c->T);
       if (prescribed)
         ACU(cudaMemcpyAsync(c->dtfix, dtn, sizeof(double) * c->np, cudaMemcpyDeviceToDevice, c->stream));
       const int rc = dis_internal_steps(c, 1, prescribed);
@@ -242,7 +242,7 @@ int adj_forward(dis_ctx* c, int n_steps, int mat, bool prescribed) {
       if (!prescribed)
         ACU(cudaMemcpyAsync(dtn, c->dtlast, sizeof(double) * c->np, cudaMemcpyDeviceToDevice, c->stream));
       if (mat >= 0) {
-        k_state32_to_64<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, c->q64[0], c->q32[0], d->tmp,
+        k_state32_to_64<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->phys, c->d_pd, c->d_seg_cell, c->q32[0], d->tmp,
                                                             c->T);
         k_obj<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, d->tmp, c->T, dtn, mat, d->J);
       }
@@ -380,8 +380,6 @@ int dis_adj_forward(dis_ctx* c, int n_steps, int checkpoint_every, int objective
   if (!c->have_state) return dis_internal_error(DIS_ESTATE, "dis_adj_forward: no state loaded");
   if (c->hancock)
     return dis_internal_error(DIS_EINVAL, "dis_adj_forward: the adjoint covers the Runge-Kutta scheme only");
-  if (c->phys.cyl && c->dim == 2)
-    return dis_internal_error(DIS_EINVAL, "dis_adj_forward: cylindrical geometry is covered in 1D only");
   if (n_steps <= 0 || checkpoint_every <= 0)
     return dis_internal_error(DIS_EINVAL, "dis_adj_forward: n_steps and checkpoint_every must be positive");
   if (objective_material < -1 || objective_material > 1)

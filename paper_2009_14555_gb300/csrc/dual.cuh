@@ -44,6 +44,8 @@ __device__ __forceinline__ Dual operator+(double a, Dual b) { return Dual(a + b.
 __device__ __forceinline__ Dual operator-(Dual a, double b) { return Dual(a.v - b, a.d); }
 __device__ __forceinline__ Dual operator-(double a, Dual b) { return Dual(a - b.v, -b.d); }
 __device__ __forceinline__ Dual operator*(Dual a, double b) { return Dual(a.v * b, a.d * b); }
+// the value rounded on its own (physics.cuh: contact speed numerator)
+__device__ __forceinline__ Dual mul_rn(Dual a, Dual b) { return Dual(__dmul_rn(a.v, b.v), a.d * b.v + a.v * b.d); }
 __device__ __forceinline__ Dual operator*(double a, Dual b) { return Dual(a * b.v, a * b.d); }
 __device__ __forceinline__ Dual operator/(Dual a, double b) { return Dual(a.v / b, a.d / b); }
 __device__ __forceinline__ Dual operator/(double a, Dual b) {

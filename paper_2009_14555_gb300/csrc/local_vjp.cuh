@@ -113,7 +113,7 @@ __device__ void riemann_outputs_vjp(const FState& L0, const FState& R0, const do
   const double aL = L.un - L.cL, aR = R.un - R.cL, bL = L.un + L.cL, bR = R.un + R.cL;
   const double SL = fmin(aL, aR), SR = fmax(bL, bR);
   const double mL = L.rho * (SL - L.un), mR = R.rho * (SR - R.un);
-  const double num = L.snn - R.snn + mL * L.un - mR * R.un, den = mL - mR;
+  const double num = (L.snn - R.snn) + mul_rn(mL, L.un) - mul_rn(mR, R.un), den = mL - mR;
   const double Ss = num / den;
   const StarT<double> sL = star_of<DIR>(L, SL, Ss), sR = star_of<DIR>(R, SR, Ss);
   const double rsL = sL.r * L.rho, rsR = sR.r * R.rho;

@@ -293,13 +293,22 @@ __device__ __forceinline__ StarT<T> star_of(const FStateT<T>& K, T S, T Ss) {
   return t;
 }
 
+// A product rounded on its own, never fused into a neighbouring addition.
+// The numerator of the contact speed S* must cancel exactly for mirrored
+// face states (a reflective wall: u_n,L = -u_n,R, equal sigma_nn), as it does
+// in plain float64 arithmetic; with one product fused into the subtraction
+// the rounding error of the other decides the sign of S* = 0 and so which
+// star state (whose V12 differs in sign) becomes the face state.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+
 template <int DIR, class T>
 __device__ __forceinline__ FaceOutT<T> hllc(const FStateT<T>& L, const FStateT<T>& R) {
   const T SL = fmin(L.un - L.cL, R.un - R.cL);
   const T SR = fmax(L.un + L.cL, R.un + R.cL);
   const T mL = L.rho * (SL - L.un);
   const T mR = R.rho * (SR - R.un);
-  const T Ss = (L.snn - R.snn + mL * L.un - mR * R.un) / (mL - mR);
+  const T Ss = ((L.snn - R.snn) + mul_rn(mL, L.un) - mul_rn(mR, R.un)) / (mL - mR);
   const StarT<T> sL = star_of<DIR>(L, SL, Ss);
   const StarT<T> sR = star_of<DIR>(R, SR, Ss);
   // shear waves of the star regions and the common tangential state

@@ -158,7 +158,7 @@ __device__ __forceinline__ FaceOutF hlld_f(const FStateF& L, const FStateF& R) {
   const float SR = fmaxf(L.un + L.cL, R.un + R.cL);
   const float mL = L.rho * (SL - L.un);
   const float mR = R.rho * (SR - R.un);
-  const float Ss = (L.snn - R.snn + mL * L.un - mR * R.un) / (mL - mR);
+  const float Ss = ((L.snn - R.snn) + mul_rn(mL, L.un) - mul_rn(mR, R.un)) / (mL - mR);
   const float rL = (SL - L.un) / (SL - Ss), rR = (SR - R.un) / (SR - Ss);
   const float rsL = rL * L.rho, rsR = rR * R.rho;
   const float csL = sqrtf(L.Gm / rsL), csR = sqrtf(R.Gm / rsR);

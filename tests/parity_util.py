@@ -91,3 +91,13 @@ def prim_l1(wl, gpu_prim, ora_prim, ora_cons):
         s = {"p": E, "u": c_ref, "v": c_ref}.get(nme, 1.0)
         out[nme] = float(np.abs(g[k] - o[k]).sum() / max(np.abs(o[k]).sum(), g.shape[1] * s))
     return out
+
+
+def record_path(name):
+    """Path of a side file (measured errors as JSON) named `name`, in the
+    directory given by DIS_RECORD_DIR (default: the system temp directory)."""
+    import os
+    import tempfile
+    d = os.environ.get("DIS_RECORD_DIR") or tempfile.gettempdir()
+    os.makedirs(d, exist_ok=True)
+    return os.path.join(d, name)

@@ -30,13 +30,12 @@ from paper_2009_14555_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-OUT = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "gpurun_out")
 _record = {}
 
 
 def _save():
-    os.makedirs(OUT, exist_ok=True)
-    with open(os.path.join(OUT, "adjoint_err.json"), "w") as f:
+    from tests.parity_util import record_path
+    with open(record_path("adjoint_err.json"), "w") as f:
         json.dump(_record, f, indent=1)
 
 
@@ -170,14 +169,31 @@ def test_adjoint_cylindrical_1d_vs_oracle():
     _case("1d_cylinder_core_100_12", wl, 12, material=0, qbar_seed=7, params=(0,))  # no yield: dJ/dsigma_Y = 0
 
 
-def test_adjoint_refuses_2d_cylindrical():
-    from paper_2009_14555_gb300.solver import Solver
-    wl = W.sphere_shock_rz(24, steps=2, thinc=False)
-    s = Solver.from_workload(wl)
-    s.set_prim([p.prim for p in wl.patches])
-    with pytest.raises(RuntimeError):
-        s.adj_forward(2, every=1, material=0)
-    s.close()
+def _reflective_planar(thinc):
+    """Planar 2D case with reflective walls on two sides: the half disc of
+    sphere_shock_rz (40 cells per unit length) sits on the x-low wall and the
+    Mach-2 shock, started at y = 0.28, strikes it within the first steps; the
+    y-high boundary is a reflective wall too."""
+    from paper_2009_14555_gb300.workloads import BC_REFLECTIVE, BC_TRANSMISSIVE
+    wl = W.sphere_shock_rz(40, steps=4, thinc=thinc, shock_z=0.28)
+    wl.geometry = "planar"
+    wl.patches[0].bc = (BC_REFLECTIVE, BC_TRANSMISSIVE, BC_TRANSMISSIVE, BC_REFLECTIVE)
+    return W.perturbed(wl, seed=21)
+
+
+def test_adjoint_2d_reflective_walls_vs_oracle():
+    _case("2d_reflective_walls_40_4", _reflective_planar(False), 4, material=0, qbar_seed=8)
+
+
+def test_adjoint_2d_reflective_walls_thinc_vs_oracle():
+    _case("2d_reflective_walls_thinc_40_4", _reflective_planar(True), 4, material=0, qbar_seed=9)
+
+
+def test_adjoint_cylindrical_2d_vs_oracle():
+    """The shock-sphere problem in (r, z): the geometric source of Section 3
+    with the reflective axis, the sphere on the axis struck within the run."""
+    wl = W.perturbed(W.sphere_shock_rz(40, steps=4, thinc=False, shock_z=0.28), seed=22)
+    _case("2d_sphere_shock_rz_40_4", wl, 4, material=0, qbar_seed=10)
 
 
 def test_adjoint_smooth_vs_oracle():

@@ -345,3 +345,31 @@ def test_hlld_flux_continuous_across_stationary_contact():
     Fm, _, _, _ = Rm.hllc(w, m, 0, [SOLID, GAS])
     assert torch.allclose(u_f[..., 0], torch.zeros(16, dtype=F64), atol=1e-9)
     assert F["ar1"].abs().max().item() < 1e-6 * (w["rho1"] * 150).max().item()
+
+
+def test_reflective_wall_face_takes_the_left_star_state():
+    """At a reflective wall the two face states are exact mirror images
+    (u_n, V12, V21 negated).  The contact speed's numerator then cancels
+    exactly, S* = 0 (as -0.0), and the tie rule S* >= 0 picks the left
+    (x-low side) star state: u_face has a zero normal component, and V12 of
+    the face is the left star value, which is minus the right one."""
+    gen = torch.Generator().manual_seed(12)
+    w = _prim_batch(16, gen, solid=True)
+    w["u"][:, 0] += 50.0 * torch.sign(w["u"][:, 0])  # flow into / out of the wall
+    P = torch.diag(t([-1.0, 1.0, 1.0]))
+    m = dict(w)
+    m["u"] = w["u"] @ P
+    m["V"] = P @ w["V"] @ P
+    F, phi_f, u_f, V_f = Rm.hllc(m, w, 0, [SOLID, GAS])
+    assert torch.all(u_f[:, 0] == 0.0)
+    # moving the right state by +-1e-7 m/s puts S* just right or left of the
+    # face: the exact tie takes the limit from the S* > 0 side (left star state)
+    wp, wm = dict(w), dict(w)
+    wp["u"] = w["u"] + t([1e-7, 0.0, 0.0])
+    wm["u"] = w["u"] - t([1e-7, 0.0, 0.0])
+    _, _, up, Vp = Rm.hllc(m, wp, 0, [SOLID, GAS])
+    _, _, um, Vm = Rm.hllc(m, wm, 0, [SOLID, GAS])
+    assert torch.all(up[:, 0] > 0) and torch.all(um[:, 0] < 0)
+    assert torch.allclose(V_f, Vp, rtol=1e-6, atol=1e-12)
+    assert torch.allclose(V_f[:, 0, 1], -Vm[:, 0, 1], rtol=1e-6, atol=1e-12)
+    assert torch.all(V_f[:, 0, 1].abs() > 1e-8)
