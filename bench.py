@@ -100,7 +100,10 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # the samples go to a temporary file (DIS_RECORD_DIR keeps them)
+        import tempfile
+        d = os.environ.get("DIS_RECORD_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:

@@ -157,6 +157,16 @@ int dis_set_state(dis_ctx* ctx, int kind, const double* src, int src_on_device);
  * stream. */
 int dis_get_state(dis_ctx* ctx, int kind, double* dst, int dst_on_device);
 
+/* The state of one patch only, in that patch's packed layout
+ * ([nfields][ny][nx], the slice of the whole-state array): the other patches
+ * keep theirs.  A context steps once every patch holds a state (set by
+ * dis_set_state, dis_set_state_async or per patch).  Host pointers
+ * synchronise the stream; device pointers are ordered on it.  Returns
+ * DIS_EINVAL (bad patch index, kind or NULL), DIS_ESTATE (materials missing;
+ * get: the patch holds no state), DIS_ENOMEM, DIS_ECUDA. */
+int dis_set_patch_state(dis_ctx* ctx, int patch, int kind, const double* src, int src_on_device);
+int dis_get_patch_state(dis_ctx* ctx, int patch, int kind, double* dst, int dst_on_device);
+
 /* Advance every patch by n_steps time steps, each with its own CFL time step
  * computed on the device from the state at the start of the step (Section
  * 3).  If dt_out is not NULL it receives the last step's dt per patch (host
@@ -172,6 +182,34 @@ int dis_step_fixed_dt(dis_ctx* ctx, int n_steps, const double* dt);
  * Synchronises the stream. */
 int dis_check(dis_ctx* ctx, int* bad_patch, int* bad_cell);
 
+/* Diagnostics of the current state and of the last step call, reduced on the
+ * device.  Totals are sums over every interior cell of every patch of the
+ * conserved quantities of Section 3 times the cell volume (dx dy; dx in 1D;
+ * times 2 pi r in cylindrical geometry): with periodic or reflective
+ * boundaries the mass, momentum and energy totals stay constant up to
+ * rounding (the source steps conserve them), which is how the step's
+ * conservation is checked. */
+typedef struct {
+  double mass[2];      /* phi_l rho_l, l = 1, 2 */
+  double momentum[2];  /* rho u, rho v (0 in 1D) */
+  double energy;       /* rho E */
+  double reactant;     /* phi_y rho_y lam (0 without a reactive material) */
+  double phi_min, phi_max; /* range of the stored volume fraction phi1 */
+  double dt_min, dt_max;   /* time step of the last step over the patches (0 before any step) */
+  double kernel_ms;        /* device time of the last dis_step / dis_step_fixed_dt call */
+  double bytes;            /* algorithmic state traffic of that call: the state read
+                              and written once per step (float64: 8 nfields bytes a
+                              cell; FP32-bulk: 4 (nfields + 1)) x cells x steps x 2 */
+  long long steps;         /* steps since the state was last set */
+  long long launches;      /* kernel launches of the last step call */
+  int status;              /* DIS_OK or DIS_ENONPHYSICAL (the device status word; not cleared) */
+  int bad_patch, bad_cell; /* the first offending patch and cell (x + nx y), or -1 */
+} dis_stats;
+
+/* Fill *s (see dis_stats).  Synchronises the stream.  DIS_EINVAL (NULL),
+ * DIS_ESTATE (no state), DIS_ECUDA. */
+int dis_query(dis_ctx* ctx, dis_stats* s);
+
 /* Total bytes of the packed state for `kind` (nfields x cells x 8). */
 size_t dis_state_bytes(const dis_ctx* ctx, int kind);
 
@@ -179,23 +217,22 @@ size_t dis_state_bytes(const dis_ctx* ctx, int kind);
 long long dis_last_launches(const dis_ctx* ctx);
 
 /* FP32-bulk contexts run one kernel per Runge-Kutta stage over tiles of
- * TX x TY cells (primitives of the tile and its halo, faces, update).  In 2D
- * there are DIS_NVARIANTS variants: tile shape v % 3; primitives recovered in
- * the stage kernel ((v / 3) even) or copied from a pre-pass that recovers
- * every cell once and also takes the CFL rate ((v / 3) odd); register budget
- * for 3 (v < 6) or 4 resident CTAs per SM.  1D contexts have variants 0..2
- * and 6..8 (the three shapes, recovery in the kernel; no register limit, or
- * at most 64 registers per thread for v >= 6).  The first dis_step times
- * stage 1 of every variant (on the stage buffer, leaving the state unchanged)
- * and keeps the one with the smallest time per step.  Returns the chosen
- * shape (0 x 0 before tuning or for float64 contexts), whether it uses the
- * pre-pass, and, if step_ms is not NULL, the tuned time per step of each
- * variant (0 for variants the context does not have). */
-#define DIS_NVARIANTS 12
+ * TX x TY cells (primitives of the tile and its halo, faces, update; the last
+ * stage also takes the CFL rate of the new state for the next step).  There
+ * are DIS_NVARIANTS variants v: tile shape v % 3 (2D 16 x 15, 20 x 12,
+ * 32 x 7 cells per CTA of 256 threads; 1D 122, 250, 506 cells per CTA of
+ * 128, 256, 512 threads) and register budget v / 3 (2D: 3 or 4 resident CTAs
+ * per SM; 1D: no limit, or at most 64 registers per thread).  The first
+ * dis_step times one step of every variant (the last stage writing a scratch
+ * buffer, so the state is unchanged) and keeps the fastest.  Returns the
+ * chosen shape (0 x 0 before tuning or for float64 contexts), precomputed = 0
+ * (kept for compatibility), and, if step_ms is not NULL, the tuned time per
+ * step of each variant. */
+#define DIS_NVARIANTS 6
 int dis_tile_choice(const dis_ctx* ctx, int* tx, int* ty, int* precomputed, double* step_ms);
 
-/* Fix the FP32-bulk stage variant (0 .. DIS_NVARIANTS - 1 in 2D, 0..2 and 6..8 in 1D) or
- * return to tuning on the next step (-1).  For tests and measurements; the
+/* Fix the FP32-bulk stage variant (0 .. DIS_NVARIANTS - 1) or return to
+ * tuning on the next step (-1).  For tests and measurements; the
  * result of a step does not depend on the variant beyond float32 rounding
  * order.  DIS_EINVAL for float64 contexts or an out-of-range variant. */
 int dis_set_variant(dis_ctx* ctx, int variant);
@@ -241,10 +278,10 @@ int dis_sync(dis_ctx* ctx);
 /* Diagnostic: advance n_steps CFL steps like dis_step but launch kernel by
  * kernel with CUDA events between launches, and return in kernel_ms[4] the
  * mean device time per launch of the primitive-recovery, x-flux, y-flux (0 in
- * 1D) and update kernels (float64), or, FP32-bulk: slot 0 the CFL pass (one
- * launch per step) or the primitive pre-pass (one per stage), slot 1 the
- * stage kernel.  Synchronises after every stage.  DIS_EINVAL for a
- * DIS_HANCOCK context. */
+ * 1D) and update kernels (float64), or, FP32-bulk: slot 0 the CFL pass that
+ * only the first step after a new state needs (timed once per step here, on
+ * a scratch buffer), slot 1 the stage kernel.  Synchronises after every
+ * stage.  DIS_EINVAL for a DIS_HANCOCK context. */
 int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
 
 /* ---- Adjoint (reverse mode) of the float64 step -------------------------
@@ -275,12 +312,11 @@ int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
  * and face outputs (about 3.5 states each), allocated here, kept for dis_adjoint and
  * released by dis_destroy.  FP32-bulk contexts checkpoint their states in
  * float64 (plus float64 primitive and face buffers for the reverse sweep).
- * In a 1D DIS_CYLINDRICAL context the geometric source of Section 3 is
- * reversed with the rest of the stage, and J is the same plain sum over cells
- * (no factor r).  Returns DIS_EINVAL (bad arguments, a DIS_HANCOCK context:
- * the adjoint covers the Runge-Kutta scheme, or a 2D DIS_CYLINDRICAL
- * context), DIS_ESTATE (no state), DIS_ENOMEM,
- * DIS_ECUDA.  Synchronises. */
+ * In a DIS_CYLINDRICAL context the geometric source of Section 3 is reversed
+ * with the rest of the stage, and J is the same plain sum over cells (no
+ * factor r).  Returns DIS_EINVAL (bad arguments, or a DIS_HANCOCK context:
+ * the adjoint covers the Runge-Kutta scheme), DIS_ESTATE (no state),
+ * DIS_ENOMEM, DIS_ECUDA.  Synchronises. */
 int dis_adj_forward(dis_ctx* ctx, int n_steps, int checkpoint_every, int objective_material,
                     const double* dt_in, double* dt_out, double* J_out);
 
@@ -320,20 +356,34 @@ int dis_adj_reference(dis_ctx* ctx, int on);
  * sum_d (|u_d| + c_L) / dx_d) without a context.
  *   d_state: device pointer to the packed conservative state of n_patches
  *            patches (layout above) for materials[0..1];
- *   d_dt:    device pointer receiving n_patches float64 time steps;
+ *   d_dt:    device pointer receiving n_patches float64 time steps; a patch
+ *            with a cell that is not hyperbolic (c_L^2 <= 0), has no
+ *            positive density, or is not finite gets NaN;
  *   stream:  cudaStream_t the work is ordered on (NULL = legacy default).
- * It allocates nothing: its scratch (per-patch maxima and descriptors) is a
- * fixed area inside the library on each device, DIS_STATIC_MAX_PATCHES
- * entries (about 0.6 MB), held by every GPU that loads the library until the
- * process exits.  The first call on a device looks the area up (with that
- * device current); make that first call before any stream capture.  Each call
- * clears the maxima it uses; calls are serialised on the host, but calls
- * whose device work overlaps (different streams) share the area and race.
+ * It allocates nothing: its scratch (per-patch maxima, flags and
+ * descriptors) is a fixed area inside the library on each device,
+ * DIS_STATIC_MAX_PATCHES entries (about 0.7 MB), held by every GPU that loads
+ * the library until the process exits.  The first call on a device looks the
+ * area up (with that device current).  Every call copies the patch
+ * descriptors from a library host array with an ordinary asynchronous copy,
+ * so the call must not be made while its stream is being captured into a
+ * CUDA graph.  Each call clears the maxima and flags it uses; calls are
+ * serialised on the host, but calls whose device work overlaps (different
+ * streams) share the area and race.
  * Returns DIS_EINVAL for n_patches outside 1..DIS_STATIC_MAX_PATCHES or other
  * bad arguments (nothing is launched), DIS_ECUDA if a CUDA call fails. */
 int dis_cfl_dt_static(int dim, int n_patches, const dis_patch* patches,
                       const dis_material* materials, int reactive_material, double cfl,
                       const double* d_state, double* d_dt, void* stream);
+
+/* Diagnostic (no counterpart in the paper): the device's measured
+ * fused-multiply-add throughput, float32 and float64, in TFLOP/s (2 FLOP per
+ * FMA), from a loop of independent FMA chains on 4 CTAs of 512 threads per
+ * SM, best of three timed launches on `stream` (cudaStream_t, NULL = legacy
+ * default); ms (may be NULL) receives the two launch times.  The rooflines
+ * of the ALU-bound kernels are fractions of these.  Allocates a small output
+ * buffer; synchronises.  DIS_EINVAL (NULL output), DIS_ENOMEM, DIS_ECUDA. */
+int dis_alu_peaks(void* stream, double* fp32_tflops, double* fp64_tflops, double* ms);
 
 /* Thread-local text of the last error (never NULL). */
 const char* dis_last_error(void);

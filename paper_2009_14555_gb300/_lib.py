@@ -19,7 +19,15 @@ DIS_RK3, DIS_HANCOCK = 0, 1
 DIS_PLANAR, DIS_CYLINDRICAL = 0, 1
 DIS_RATE_ARRHENIUS, DIS_RATE_SQRT = 0, 1
 DIS_NPARAM = 6  # per material l: G, sigma_y, Q at 3 l + k
-DIS_NVARIANTS = 12  # FP32-bulk stage variants (2D: 3 tile shapes x 2 primitive sources x 2 register budgets)
+DIS_NVARIANTS = 6  # FP32-bulk stage variants: 3 tile shapes x 2 register budgets
+
+
+class DisStats(ctypes.Structure):
+    _fields_ = [("mass", c_double * 2), ("momentum", c_double * 2), ("energy", c_double),
+                ("reactant", c_double), ("phi_min", c_double), ("phi_max", c_double),
+                ("dt_min", c_double), ("dt_max", c_double), ("kernel_ms", c_double), ("bytes", c_double),
+                ("steps", c_longlong), ("launches", c_longlong), ("status", c_int32),
+                ("bad_patch", c_int32), ("bad_cell", c_int32)]
 
 
 class DisMaterial(ctypes.Structure):
@@ -73,6 +81,10 @@ SIGNATURES = {
     "dis_adjoint": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p, c_int, c_void_p,
                             ctypes.c_uint]),
     "dis_adj_reference": (c_int, [c_void_p, c_int]),
+    "dis_alu_peaks": (c_int, [c_void_p, POINTER(c_double), POINTER(c_double), c_void_p]),
+    "dis_set_patch_state": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int]),
+    "dis_get_patch_state": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int]),
+    "dis_query": (c_int, [c_void_p, c_void_p]),
     "dis_last_error": (c_char_p, []),
     "dis_destroy": (None, [c_void_p]),
 }

@@ -28,6 +28,7 @@
 #pragma once
 #include "local_vjp.cuh"
 #include "step_kernels.cuh"
+#include "step32.cuh"
 
 namespace dis {
 
@@ -617,21 +618,22 @@ __global__ void __launch_bounds__(SEG) k_obj_adj(const PatchDev* __restrict__ pd
   qbar[L::MX * T + k] += s * ph;
 }
 
-// FP32-bulk state (float64 phi1 / rho E pair + float32 planes) to the float64
-// layout of the same padded cells (interior cells).
+// FP32-bulk state (float32 planes with the soft energy and the float-float
+// phi1 of step32.cuh) to the float64 layout of the same padded cells
+// (interior cells).
 template <int DIM, bool RX>
-__global__ void __launch_bounds__(SEG) k_state32_to_64(const PatchDev* __restrict__ pds,
-                                                      const int4* __restrict__ segs, const double* q64,
-                                                      const float* q32, double* out, long long T) {
-  using L = Lay<DIM, RX>;
-  constexpr int NF = L::NF;
+__global__ void __launch_bounds__(SEG) k_state32_to_64(Phys P, const PatchDev* __restrict__ pds,
+                                                      const int4* __restrict__ segs, const float* q32, double* out,
+                                                      long long T) {
+  constexpr int NF = Lay<DIM, RX>::NF;
   const int4 g = segs[blockIdx.x];
   if (threadIdx.x >= g.w) return;
   const PatchDev pd = pds[g.x];
   const long long k = cidx(pd, g.z + threadIdx.x, g.y);
+  double v[NF];
+  state32_to_64<DIM, RX>(P, q32, T, k, v);
 #pragma unroll
-  for (int c = 0; c < NF; ++c)
-    out[c * T + k] = c == L::PHI ? q64[k] : (c == L::E ? q64[T + k] : (double)q32[c * T + k]);
+  for (int c = 0; c < NF; ++c) out[c * T + k] = v[c];
 }
 
 // qbar = xbar + qnacc on interior cells.

@@ -25,6 +25,7 @@ struct dis_ctx {
   std::vector<PatchDev> pd;
   long long T = 0, NFX = 0, NFY = 0, ncells = 0;
   std::vector<int4> seg_prim, seg_fx, seg_fy, seg_cell;
+  std::vector<int> seg_cell0;  // first seg_cell segment of each patch (np + 1)
   cudaStream_t stream = nullptr;
   int device = 0;
   // workspace
@@ -43,9 +44,9 @@ struct dis_ctx {
   double* dtlast = nullptr;
   int* status = nullptr;
   // FP32-bulk stage kernel: tile tables per tile shape; variant v = tile
-  // shape v % 3, primitives recovered in the kernel ((v / 3) even) or
-  // precomputed by k_prim32 ((v / 3) odd), 3 (v < 6) or 4 resident CTAs per SM
-  // (2D only); chosen variant and tuned per-step times
+  // shape v % 3 with the register budget v / 3 (2D: 3 or 4 resident CTAs per
+  // SM; 1D: none or 64 registers per thread); chosen variant and tuned
+  // per-step times
   std::vector<int4> tiles[3];
   int4* d_tiles[3] = {nullptr, nullptr, nullptr};
   int variant = -1;
@@ -61,13 +62,22 @@ struct dis_ctx {
   int* d_order = nullptr;
   int* d_tile0[3] = {nullptr, nullptr, nullptr};
   double tune_batch_ms[DIS_NVARIANTS] = {};
-  // FP32-bulk buffers: (phi1, rho E) float64 pairs and float32 planes
-  // q^n and two stage buffers: a stage kernel reads the halo of its source
-  // from neighbouring tiles, so no stage may write the buffer it reads
-  double* q64[3] = {nullptr, nullptr, nullptr};
+  // FP32-bulk buffers: q^n and two stage buffers of NF + 1 float32 planes
+  // (step32.cuh): a stage kernel reads the halo of its source from
+  // neighbouring tiles, so no stage may write the buffer it reads.  rate
+  // holds 2 np values: the CFL rate of q^n, and that of q^{n+1} accumulated
+  // by the last stage; rate_valid: the first holds the rate of the state
   float* q32[3] = {nullptr, nullptr, nullptr};
-  float* W32 = nullptr;
+  bool rate_valid = false;
   PatchDev* d_pd = nullptr;
+  // dis_query: per-segment partials and the final totals (workspace); which
+  // patches hold a state; events around the last step call; step counts
+  double* qpart = nullptr;
+  double* qout = nullptr;
+  std::vector<char> patch_set;
+  cudaEvent_t ev_step[2] = {nullptr, nullptr};
+  bool ev_recorded = false;
+  long long steps_total = 0, last_steps = 0;
   int4 *d_seg_prim = nullptr, *d_seg_fx = nullptr, *d_seg_fy = nullptr, *d_seg_cell = nullptr;
   long long launches = 0;
   // one captured time step per dt mode (0: CFL, 1: prescribed), replayed per step

@@ -24,6 +24,7 @@
 
 #include "../../include/dis.h"
 #include "ctx.cuh"
+#include "query.cuh"
 
 using namespace dis;
 
@@ -108,6 +109,7 @@ void layout(dis_ctx* c) {
   c->seg_fx.clear();
   c->seg_fy.clear();
   c->seg_cell.clear();
+  c->seg_cell0.clear();
   for (int p = 0; p < c->np; ++p) {
     const dis_patch& P = c->patches[p];
     PatchDev d{};
@@ -132,8 +134,10 @@ void layout(dis_ctx* c) {
     for (int j = 0; j < d.ny; ++j) add_row(c->seg_fx, p, j, 0, d.nx + 1);
     if (c->dim == 2)
       for (int j = 0; j <= d.ny; ++j) add_row(c->seg_fy, p, j, 0, d.nx);
+    c->seg_cell0.push_back((int)c->seg_cell.size());
     for (int j = 0; j < d.ny; ++j) add_row(c->seg_cell, p, j, 0, d.nx);
   }
+  c->seg_cell0.push_back((int)c->seg_cell.size());
   c->T = off;
   c->NFX = fx;
   c->NFY = fy;
@@ -155,7 +159,7 @@ size_t carve(dis_ctx* c, char* base) {
   const size_t T = (size_t)c->T;
   const size_t nfx = (size_t)(c->nf + n_extra(c->dim));
   size_t oq0 = 0, oq1 = 0, ow = 0, ofx = 0, ofy = 0, oe = 0;
-  size_t o64[3] = {0, 0, 0}, o32[3] = {0, 0, 0}, ow32 = 0;
+  size_t o32[3] = {0, 0, 0};
   if (!c->fp32) {
     const size_t dpl = sizeof(double) * T;
     oq0 = k.take(c->nf * dpl);
@@ -165,18 +169,16 @@ size_t carve(dis_ctx* c, char* base) {
     ofy = k.take(sizeof(double) * nfx * c->NFY);
     if (c->hancock) oe = k.take((size_t)2 * c->dim * c->nf * dpl);
   } else {
-    for (int b = 0; b < 3; ++b) {
-      o64[b] = k.take(2 * sizeof(double) * T);
-      o32[b] = k.take(c->nf * sizeof(float) * T);
-    }
-    ow32 = k.take(c->nf * sizeof(float) * T);
+    for (int b = 0; b < 3; ++b) o32[b] = k.take((c->nf + 1) * sizeof(float) * T);
   }
   size_t oio = k.take(sizeof(double) * (size_t)c->nf * c->ncells);
-  size_t ort = k.take(sizeof(unsigned long long) * c->np);
+  size_t ort = k.take(2 * sizeof(unsigned long long) * c->np);  // rate of q^n, of q^{n+1}
   size_t odf = k.take(sizeof(double) * c->np);
   size_t odl = k.take(sizeof(double) * c->np);
   size_t ost = k.take(sizeof(int) * 4);
   size_t opd = k.take(sizeof(PatchDev) * c->np);
+  size_t oqp = k.take(sizeof(double) * NQ * c->seg_cell.size());  // dis_query partials
+  size_t oqo = k.take(sizeof(double) * NQ);
   size_t os1 = k.take(sizeof(int4) * c->seg_prim.size());
   size_t os2 = k.take(sizeof(int4) * c->seg_fx.size());
   size_t os3 = k.take(sizeof(int4) * std::max<size_t>(1, c->seg_fy.size()));
@@ -199,11 +201,7 @@ size_t carve(dis_ctx* c, char* base) {
       c->Fy = (double*)(base + ofy);
       c->E = c->hancock ? (double*)(base + oe) : nullptr;
     } else {
-      for (int b = 0; b < 3; ++b) {
-        c->q64[b] = (double*)(base + o64[b]);
-        c->q32[b] = (float*)(base + o32[b]);
-      }
-      c->W32 = (float*)(base + ow32);
+      for (int b = 0; b < 3; ++b) c->q32[b] = (float*)(base + o32[b]);
     }
     c->io = (double*)(base + oio);
     c->rate = (unsigned long long*)(base + ort);
@@ -211,6 +209,8 @@ size_t carve(dis_ctx* c, char* base) {
     c->dtlast = (double*)(base + odl);
     c->status = (int*)(base + ost);
     c->d_pd = (PatchDev*)(base + opd);
+    c->qpart = (double*)(base + oqp);
+    c->qout = (double*)(base + oqo);
     c->d_seg_prim = (int4*)(base + os1);
     c->d_seg_fx = (int4*)(base + os2);
     c->d_seg_fy = (int4*)(base + os3);
@@ -279,101 +279,80 @@ StepArgs32 base_args32(dis_ctx* c) {
   a.T = c->T;
   a.NFX = c->NFX;
   a.NFY = c->NFY;
-  a.W = c->W32;
   a.rate = c->rate;
+  a.rate_next = c->rate + c->np;
   a.dtlast = c->dtlast;
   a.status = c->status;
-  a.kap2 = c->phys.m[1].kap;
   a.dkap = c->phys.m[0].kap - c->phys.m[1].kap;
   return a;
 }
 
-template <int DIM, bool RX, int TX, int TY, int NT, bool PRE, int MINB, bool CYL>
+template <int DIM, bool RX, int TX, int TY, int NT, int MINB, bool CYL>
 void stage_fused_c(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
   constexpr size_t smem = fused32_smem<DIM, RX, TX, TY>();
   static bool attr_set = false;  // per instantiation, per process
   if (!attr_set) {
-    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT, PRE, MINB, CYL>,
+    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT, MINB, CYL>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT, PRE, MINB, CYL>,
+    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT, MINB, CYL>,
                          cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr_set = true;
   }
-  k_stage32<DIM, RX, TX, TY, NT, PRE, MINB, CYL><<<(unsigned)c->tiles[shape].size(), NT, smem, st>>>(
+  k_stage32<DIM, RX, TX, TY, NT, MINB, CYL><<<(unsigned)c->tiles[shape].size(), NT, smem, st>>>(
       c->phys, c->physf, a, c->d_tiles[shape]);
 }
 
 // Planar and cylindrical contexts run separate instantiations, so the
 // geometric source costs the planar kernels nothing.
-template <int DIM, bool RX, int TX, int TY, int NT, bool PRE, int MINB>
+template <int DIM, bool RX, int TX, int TY, int NT, int MINB>
 void stage_fused(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
-  if (c->phys.cyl) stage_fused_c<DIM, RX, TX, TY, NT, PRE, MINB, true>(c, st, a, shape);
-  else stage_fused_c<DIM, RX, TX, TY, NT, PRE, MINB, false>(c, st, a, shape);
+  if (c->phys.cyl) stage_fused_c<DIM, RX, TX, TY, NT, MINB, true>(c, st, a, shape);
+  else stage_fused_c<DIM, RX, TX, TY, NT, MINB, false>(c, st, a, shape);
 }
 
-// FP32-bulk stage variants v = shape + 3 pre + 6 budget: 2D: 3 tile shapes x
-// (recovery in the stage kernel, primitives from the pre-pass) x (3, 4
-// resident CTAs per SM requested from the register allocator); 1D: the 3
-// shapes x (no register limit, 64 registers per thread), recovery in the
-// kernel (pre = 0: variants 0..2 and 6..8).
-bool variant_pre(int v) { return (v / 3) % 2 == 1; }
-bool variant_valid(const dis_ctx* c, int v) {
-  return v >= 0 && v < DIS_NVARIANTS && (c->dim == 2 || !variant_pre(v));
-}
+// FP32-bulk stage variants v = shape + 3 budget: the 3 tile shapes x two
+// register budgets (2D: 3 or 4 resident CTAs of 256 threads per SM requested
+// from the register allocator; 1D: no limit, or 64 registers per thread).
+bool variant_valid(const dis_ctx*, int v) { return v >= 0 && v < DIS_NVARIANTS; }
 
-template <int DIM, bool RX, bool PRE, int MINB>
+template <int DIM, bool RX, int MINB>
 void stage_kernel_2d(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
-  if (shape == 0) stage_fused<DIM, RX, 16, 15, 256, PRE, MINB>(c, st, a, shape);
-  else if (shape == 1) stage_fused<DIM, RX, 20, 12, 256, PRE, MINB>(c, st, a, shape);
-  else stage_fused<DIM, RX, 32, 7, 256, PRE, MINB>(c, st, a, shape);
+  if (shape == 0) stage_fused<DIM, RX, 16, 15, 256, MINB>(c, st, a, shape);
+  else if (shape == 1) stage_fused<DIM, RX, 20, 12, 256, MINB>(c, st, a, shape);
+  else stage_fused<DIM, RX, 32, 7, 256, MINB>(c, st, a, shape);
 }
 
-// The stage kernel of variant v (without the primitive pre-pass).
+// The stage kernel of variant v.
 template <int DIM, bool RX>
 void stage_kernel_v(dis_ctx* c, cudaStream_t st, StepArgs32& a, int v) {
   const int shape = v % 3;
   if constexpr (DIM == 2) {
-    const bool pre = variant_pre(v), mb4 = v >= 6;
-    if (pre) {
-      if (mb4) stage_kernel_2d<DIM, RX, true, 4>(c, st, a, shape);
-      else stage_kernel_2d<DIM, RX, true, 3>(c, st, a, shape);
-    } else {
-      if (mb4) stage_kernel_2d<DIM, RX, false, 4>(c, st, a, shape);
-      else stage_kernel_2d<DIM, RX, false, 3>(c, st, a, shape);
-    }
-  } else if (v < 6) {
-    if (shape == 0) stage_fused<DIM, RX, 122, 1, 128, false, 1>(c, st, a, shape);
-    else if (shape == 1) stage_fused<DIM, RX, 250, 1, 256, false, 1>(c, st, a, shape);
-    else stage_fused<DIM, RX, 506, 1, 512, false, 1>(c, st, a, shape);
+    if (v >= 3) stage_kernel_2d<DIM, RX, 4>(c, st, a, shape);
+    else stage_kernel_2d<DIM, RX, 3>(c, st, a, shape);
+  } else if (v < 3) {
+    if (shape == 0) stage_fused<DIM, RX, 122, 1, 128, 1>(c, st, a, shape);
+    else if (shape == 1) stage_fused<DIM, RX, 250, 1, 256, 1>(c, st, a, shape);
+    else stage_fused<DIM, RX, 506, 1, 512, 1>(c, st, a, shape);
   } else {  // 1024 threads per SM requested: at most 64 registers per thread
-    if (shape == 0) stage_fused<DIM, RX, 122, 1, 128, false, 8>(c, st, a, shape);
-    else if (shape == 1) stage_fused<DIM, RX, 250, 1, 256, false, 4>(c, st, a, shape);
-    else stage_fused<DIM, RX, 506, 1, 512, false, 2>(c, st, a, shape);
+    if (shape == 0) stage_fused<DIM, RX, 122, 1, 128, 8>(c, st, a, shape);
+    else if (shape == 1) stage_fused<DIM, RX, 250, 1, 256, 4>(c, st, a, shape);
+    else stage_fused<DIM, RX, 506, 1, 512, 2>(c, st, a, shape);
   }
 }
 
-// Primitive pre-pass of the precomputed-primitive variants; with rate_on it
-// also takes the CFL rate, so those variants need no separate CFL pass.
+// CFL rate of q^n (buffer 0) into rate (zeroed first): the first step after
+// the state was set; later steps take it from the last stage of the step
+// before.
 template <int DIM, bool RX>
-void prim_pass32(dis_ctx* c, cudaStream_t st, StepArgs32& a, bool rate_on) {
-  k_prim32<DIM, RX><<<(unsigned)c->seg_prim.size(), SEG, 0, st>>>(c->phys, c->physf, a, c->d_seg_prim,
-                                                                 rate_on ? 1 : 0);
-}
-
-// One stage of variant v: [k_prim32 +] k_stage32; returns the launch count.
-template <int DIM, bool RX>
-int stage_fused_v(dis_ctx* c, cudaStream_t st, StepArgs32& a, int v, bool rate_on) {
-  int l = 1;
-  if (variant_pre(v)) {
-    prim_pass32<DIM, RX>(c, st, a, rate_on);
-    ++l;
-  }
-  stage_kernel_v<DIM, RX>(c, st, a, v);
-  return l;
+void cfl_pass32(dis_ctx* c, cudaStream_t st, unsigned long long* rate) {
+  StepArgs32 a = base_args32(c);
+  a.src = c->q32[0];
+  cudaMemsetAsync(rate, 0, sizeof(unsigned long long) * c->np, st);
+  k_cfl32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, st>>>(c->phys, c->physf, a, rate, c->d_seg_cell);
 }
 
 // Persistent 1D batch kernel (FP32-bulk), variant v: tile length v % 3,
-// 64 registers per thread for v >= 6; n steps in one launch, one CTA per
+// 64 registers per thread for v >= 3; n steps in one launch, one CTA per
 // problem.  scratch_last (tuning, n = 1): the step ends in buffer 1.
 template <bool RX, int TX, int NT, int MINB, bool CYL>
 void batch_fused_c(dis_ctx* c, cudaStream_t st, const StepArgs32& a, int n, int scratch_last, int shape) {
@@ -386,13 +365,10 @@ void batch_fused_c(dis_ctx* c, cudaStream_t st, const StepArgs32& a, int n, int 
     attr_set = true;
   }
   Bufs32 b;
-  for (int k = 0; k < 3; ++k) {
-    b.q64[k] = c->q64[k];
-    b.q32[k] = c->q32[k];
-  }
-  k_batch32<RX, TX, NT, MINB, CYL><<<(unsigned)c->np, NT, smem, st>>>(c->phys, c->physf, a, b, c->d_order,
-                                                                      c->d_tile0[shape], c->d_tiles[shape], n,
-                                                                      scratch_last);
+  for (int k = 0; k < 3; ++k) b.q[k] = c->q32[k];
+  k_batch32<RX, TX, NT, MINB, CYL><<<(unsigned)c->np, NT, smem, st>>>(
+      c->phys, c->physf, a, b, c->rate, c->d_order, c->d_tile0[shape], c->d_tiles[shape], n, scratch_last,
+      c->rate_valid ? 1 : 0);
 }
 
 template <bool RX, int TX, int NT, int MINB>
@@ -404,7 +380,7 @@ void batch_fused(dis_ctx* c, cudaStream_t st, const StepArgs32& a, int n, int sc
 template <bool RX>
 void batch_kernel_v(dis_ctx* c, cudaStream_t st, const StepArgs32& a, int n, int scratch_last, int v) {
   const int shape = v % 3;
-  if (v < 6) {
+  if (v < 3) {
     if (shape == 0) batch_fused<RX, 122, 128, 1>(c, st, a, n, scratch_last, shape);
     else if (shape == 1) batch_fused<RX, 250, 256, 1>(c, st, a, n, scratch_last, shape);
     else batch_fused<RX, 506, 512, 1>(c, st, a, n, scratch_last, shape);
@@ -416,30 +392,18 @@ void batch_kernel_v(dis_ctx* c, cudaStream_t st, const StepArgs32& a, int n, int
 }
 
 // Buffers of the FP32-bulk stages: q^n (0) -> q1 (1) -> q2 (2) -> q^{n+1} (0).
-// A stage kernel that recovers its tile reads the halo of its source from
-// neighbouring tiles, so it must not write that source; with the primitive
-// pre-pass (in_place) it reads only its own cells of the source, and stage 2
-// updates buffer 1 in place (better L2 reuse).  The last stage overwrites q^n
-// cell by cell, read only at the same cell.  scratch_last: the tuner's full
-// step ends in buffer 1 (in_place: buffer 2) instead of q^n.
+// A stage kernel reads the halo of its source from neighbouring tiles, so it
+// must not write that source.  The last stage overwrites q^n cell by cell,
+// read only at the same cell.  scratch_last: the tuner's full step ends in
+// buffer 1 instead of q^n.
 template <int DIM, bool RX>
-void set_stage_args32(dis_ctx* c, StepArgs32& a, int stg, bool in_place, bool scratch_last = false) {
+void set_stage_args32(dis_ctx* c, StepArgs32& a, int stg, bool scratch_last = false) {
   const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
   const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
-  int src, dst;
-  if (in_place) {
-    src = stg == 0 ? 0 : 1;
-    dst = stg == 2 ? (scratch_last ? 2 : 0) : 1;
-  } else {
-    src = stg;
-    dst = stg == 2 ? (scratch_last ? 1 : 0) : stg + 1;
-  }
-  a.q64src = c->q64[src];
-  a.q32src = c->q32[src];
-  a.q64n = c->q64[0];
-  a.q32n = c->q32[0];
-  a.q64dst = c->q64[dst];
-  a.q32dst = c->q32[dst];
+  const int src = stg, dst = stg == 2 ? (scratch_last ? 1 : 0) : stg + 1;
+  a.src = c->q32[src];
+  a.qn = c->q32[0];
+  a.dst = c->q32[dst];
   a.a = ca[stg];
   a.b = cb[stg];
   a.last = stg == 2;
@@ -447,7 +411,9 @@ void set_stage_args32(dis_ctx* c, StepArgs32& a, int stg, bool in_place, bool sc
 
 // Autotuner: time one full step of every variant with the last stage
 // writing a scratch buffer (the state is untouched) and keep the fastest.
-// The CFL rate of q^n is taken once first; dt is then the step's dt.
+// The CFL rate of q^n is taken first (if it is not known); dt is then the
+// step's dt.  The trial steps' last stages accumulate into the next-step
+// rate buffer, which every real step clears first.
 template <int DIM, bool RX>
 int autotune32(dis_ctx* c) {
   StepArgs32 a = base_args32(c);
@@ -455,24 +421,19 @@ int autotune32(dis_ctx* c) {
   cudaEvent_t e0, e1;
   CU(cudaEventCreate(&e0));
   CU(cudaEventCreate(&e1));
-  CU(cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, c->stream));
-  set_stage_args32<DIM, RX>(c, a, 0, false);
-  k_cfl32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, c->physf, a, c->d_seg_cell);
+  if (!c->rate_valid) {
+    cfl_pass32<DIM, RX>(c, c->stream, c->rate);
+    c->rate_valid = true;
+  }
   double best = 1e30;
   int bv = 0;
   for (int v = 0; v < DIS_NVARIANTS; ++v) {
     if (!variant_valid(c, v)) continue;
-    const bool pre = variant_pre(v);
     for (int rep = 0; rep < 3; ++rep) {  // rep 0 warms up
       CU(cudaEventRecord(e0, c->stream));
-      if (!pre) {  // the step's CFL pass (rate unchanged: the max is idempotent)
-        set_stage_args32<DIM, RX>(c, a, 0, false);
-        k_cfl32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, c->physf, a,
-                                                                               c->d_seg_cell);
-      }
       for (int stg = 0; stg < 3; ++stg) {
-        set_stage_args32<DIM, RX>(c, a, stg, pre, true);
-        stage_fused_v<DIM, RX>(c, c->stream, a, v, false);
+        set_stage_args32<DIM, RX>(c, a, stg, true);
+        stage_kernel_v<DIM, RX>(c, c->stream, a, v);
       }
       CU(cudaEventRecord(e1, c->stream));
       CU(cudaEventSynchronize(e1));
@@ -483,8 +444,8 @@ int autotune32(dis_ctx* c) {
     }
     if (c->tune_ms[v] < best) { best = c->tune_ms[v]; bv = v; }
   }
-  // 1D: the persistent batch kernel, one step per variant (its own CFL pass;
-  // the last stage writes buffer 1), against the best per-step schedule
+  // 1D: the persistent batch kernel, one step per variant (the last stage
+  // writes buffer 1), against the best per-step schedule
   double best_b = 1e30;
   int bb = -1;
   if constexpr (DIM == 1) {
@@ -526,24 +487,18 @@ int autotune32(dis_ctx* c) {
 template <int DIM, bool RX>
 long long launch_step(dis_ctx* c, cudaStream_t st, bool fixed) {
   if (c->fp32) {
+    // the three stages read the rate of q^n (rate) and the last one
+    // accumulates the rate of q^{n+1} (rate + np), copied over at the end
     StepArgs32 a = base_args32(c);
     a.dtfix = fixed ? c->dtfix : nullptr;
-    long long l = 0;
     const int v = c->variant < 0 ? 0 : c->variant;
-    const bool pre = variant_pre(v);
-    if (!fixed) {
-      cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, st);
-      if (!pre) {
-        set_stage_args32<DIM, RX>(c, a, 0, false);
-        k_cfl32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, st>>>(c->phys, c->physf, a, c->d_seg_cell);
-        ++l;
-      }
-    }
+    cudaMemsetAsync(c->rate + c->np, 0, sizeof(unsigned long long) * c->np, st);
     for (int stg = 0; stg < 3; ++stg) {
-      set_stage_args32<DIM, RX>(c, a, stg, pre);
-      l += stage_fused_v<DIM, RX>(c, st, a, v, !fixed && stg == 0);
+      set_stage_args32<DIM, RX>(c, a, stg);
+      stage_kernel_v<DIM, RX>(c, st, a, v);
     }
-    return l;
+    cudaMemcpyAsync(c->rate, c->rate + c->np, sizeof(unsigned long long) * c->np, cudaMemcpyDeviceToDevice, st);
+    return 3;
   }
   StepArgs a = base_args(c);
   a.dtfix = fixed ? c->dtfix : nullptr;
@@ -605,37 +560,29 @@ int timed_steps(dis_ctx* c, int n_steps, double* ms) {
   for (int k = 0; k < 5; ++k) CU(cudaEventCreate(&ev[k]));
   double acc[4] = {0, 0, 0, 0};
   if (c->fp32) {
-    // slot 0: CFL pass (in-kernel recovery, once per step) or the primitive
-    // pre-pass (precomputed primitives, per stage); slot 1: stage kernel
+    // slot 0: the CFL pass of a first step (timed on the next-step rate
+    // buffer, which every step clears first); slot 1: the stage kernel
     if (c->variant < 0) {
       const int rc = autotune32<DIM, RX>(c);
       if (rc) return rc;
     }
     const int v = c->variant;
-    const bool pre = variant_pre(v);
     StepArgs32 a32 = base_args32(c);
+    if (!c->rate_valid) {
+      cfl_pass32<DIM, RX>(c, c->stream, c->rate);
+      c->rate_valid = true;
+    }
     for (int s = 0; s < n_steps; ++s) {
-      CU(cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, c->stream));
       float t = 0.f;
-      if (!pre) {
-        set_stage_args32<DIM, RX>(c, a32, 0, false);
-        CU(cudaEventRecord(ev[0], c->stream));
-        k_cfl32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, c->physf, a32, c->d_seg_cell);
-        CU(cudaEventRecord(ev[1], c->stream));
-        CU(cudaEventSynchronize(ev[1]));
-        CU(cudaEventElapsedTime(&t, ev[0], ev[1]));
-        acc[0] += 3.0 * t;
-      }
+      CU(cudaEventRecord(ev[0], c->stream));
+      cfl_pass32<DIM, RX>(c, c->stream, c->rate + c->np);
+      CU(cudaEventRecord(ev[1], c->stream));
+      CU(cudaEventSynchronize(ev[1]));
+      CU(cudaEventElapsedTime(&t, ev[0], ev[1]));
+      acc[0] += 3.0 * t;
+      CU(cudaMemsetAsync(c->rate + c->np, 0, sizeof(unsigned long long) * c->np, c->stream));
       for (int stg = 0; stg < 3; ++stg) {
-        set_stage_args32<DIM, RX>(c, a32, stg, pre);
-        if (pre) {
-          CU(cudaEventRecord(ev[0], c->stream));
-          prim_pass32<DIM, RX>(c, c->stream, a32, stg == 0);
-          CU(cudaEventRecord(ev[1], c->stream));
-          CU(cudaEventSynchronize(ev[1]));
-          CU(cudaEventElapsedTime(&t, ev[0], ev[1]));
-          acc[0] += t;
-        }
+        set_stage_args32<DIM, RX>(c, a32, stg);
         CU(cudaEventRecord(ev[1], c->stream));
         stage_kernel_v<DIM, RX>(c, c->stream, a32, v);
         CU(cudaEventRecord(ev[2], c->stream));
@@ -643,6 +590,8 @@ int timed_steps(dis_ctx* c, int n_steps, double* ms) {
         CU(cudaEventElapsedTime(&t, ev[1], ev[2]));
         acc[1] += t;
       }
+      CU(cudaMemcpyAsync(c->rate, c->rate + c->np, sizeof(unsigned long long) * c->np, cudaMemcpyDeviceToDevice,
+                         c->stream));
     }
     n_steps = -n_steps;  // skip the float64 loop below
   }
@@ -693,12 +642,19 @@ int run_steps(dis_ctx* c, int n_steps, bool fixed) {
       a.dtfix = fixed ? c->dtfix : nullptr;
       batch_kernel_v<RX>(c, c->stream, a, n_steps, 0, c->variant);
       CU(cudaGetLastError());
+      c->rate_valid = true;
       c->launches = 1;
       return DIS_OK;
     }
   }
+  long long first = 0;
+  if (c->fp32 && !c->rate_valid) {  // the rate of q^n for the first step
+    cfl_pass32<DIM, RX>(c, c->stream, c->rate);
+    c->rate_valid = true;
+    first = 1;
+  }
   if (!c->use_graphs) {
-    long long l = 0;
+    long long l = first;
     for (int s = 0; s < n_steps; ++s) l += launch_step<DIM, RX>(c, c->stream, fixed);
     CU(cudaGetLastError());
     c->launches = l;
@@ -721,7 +677,7 @@ int run_steps(dis_ctx* c, int n_steps, bool fixed) {
   // captured on the private stream, replayed on the caller's stream (no
   // cross-stream waits between steps)
   for (int s = 0; s < n_steps; ++s) CU(cudaGraphLaunch(c->graph[mode], c->stream));
-  c->launches = c->graph_launches[mode] * n_steps;
+  c->launches = first + c->graph_launches[mode] * n_steps;
   return DIS_OK;
 }
 
@@ -731,34 +687,42 @@ int dispatch_steps(dis_ctx* c, int n, bool fixed) {
   return rx ? run_steps<2, true>(c, n, fixed) : run_steps<2, false>(c, n, fixed);
 }
 
+// Segments of the transfer: all patches (patch < 0) or one patch, whose
+// packed array then starts at src / dst (base = its packed offset).
+struct SegRange {
+  const int4* segs;
+  unsigned n;
+  long long base;
+};
+SegRange seg_range(const dis_ctx* c, int patch) {
+  if (patch < 0) return {c->d_seg_cell, (unsigned)c->seg_cell.size(), 0};
+  const int b = c->seg_cell0[patch], e = c->seg_cell0[patch + 1];
+  return {c->d_seg_cell + b, (unsigned)(e - b), c->pd[patch].poff};
+}
+
 template <int DIM, bool RX>
-int do_unpack(dis_ctx* c, const double* src, int prim) {
+int do_unpack(dis_ctx* c, const double* src, int prim, int patch = -1) {
+  const SegRange r = seg_range(c, patch);
   if (c->fp32) {
-    k_unpack32<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(
-        c->phys, c->d_pd, c->d_seg_cell, src, c->q64[0], c->q32[0], c->T, prim);
+    k_unpack32<DIM, RX><<<r.n, SEG, 0, c->stream>>>(c->phys, c->d_pd, r.segs, src, c->q32[0], c->T, prim, r.base);
     CU(cudaGetLastError());
+    c->rate_valid = false;
     return DIS_OK;
   }
-  k_unpack<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->phys, c->d_pd, c->d_seg_cell,
-                                                                         src, c->q[0], c->T, prim);
+  k_unpack<DIM, RX><<<r.n, SEG, 0, c->stream>>>(c->phys, c->d_pd, r.segs, src, c->q[0], c->T, prim, r.base);
   CU(cudaGetLastError());
   return DIS_OK;
 }
 
 template <int DIM, bool RX>
-int do_pack(dis_ctx* c, double* dst, int prim) {
+int do_pack(dis_ctx* c, double* dst, int prim, int patch = -1) {
+  const SegRange r = seg_range(c, patch);
   if (c->fp32) {
-    const unsigned ncs = (unsigned)c->seg_cell.size();
-    if (prim) {
-      StepArgs32 a = base_args32(c);
-      a.q64src = c->q64[0];
-      a.q32src = c->q32[0];
-      k_prim32<DIM, RX><<<(unsigned)c->seg_prim.size(), SEG, 0, c->stream>>>(c->phys, c->physf, a,
-                                                                             c->d_seg_prim, 0);
-      k_pack_w32<DIM, RX><<<ncs, SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, c->W32, dst, c->T);
-    } else {
-      k_pack32<DIM, RX><<<ncs, SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, c->q64[0], c->q32[0], dst, c->T);
-    }
+    if (prim)
+      k_pack_prim32<DIM, RX><<<r.n, SEG, 0, c->stream>>>(c->phys, c->physf, c->d_pd, r.segs, c->q32[0], dst, c->T,
+                                                         r.base);
+    else
+      k_pack32<DIM, RX><<<r.n, SEG, 0, c->stream>>>(c->phys, c->d_pd, r.segs, c->q32[0], dst, c->T, r.base);
     CU(cudaGetLastError());
     return DIS_OK;
   }
@@ -769,7 +733,18 @@ int do_pack(dis_ctx* c, double* dst, int prim) {
     k_prim<DIM, RX><<<(unsigned)c->seg_prim.size(), SEG, 0, c->stream>>>(c->phys, a, c->d_seg_prim, 0);
     from = c->W;
   }
-  k_pack<DIM, RX><<<(unsigned)c->seg_cell.size(), SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, from, dst, c->T);
+  k_pack<DIM, RX><<<r.n, SEG, 0, c->stream>>>(c->d_pd, r.segs, from, dst, c->T, r.base);
+  CU(cudaGetLastError());
+  return DIS_OK;
+}
+
+// Totals, phi range (query.cuh) of the current state into c->qout (device).
+template <int DIM, bool RX>
+int do_query(dis_ctx* c) {
+  const unsigned n = (unsigned)c->seg_cell.size();
+  k_query_partial<DIM, RX><<<n, SEG, 0, c->stream>>>(c->phys, c->d_pd, c->d_seg_cell, c->fp32 ? nullptr : c->q[0],
+                                                     c->fp32 ? c->q32[0] : nullptr, c->T, c->qpart);
+  k_query_final<<<1, SEG, 0, c->stream>>>(c->qpart, n, c->qout);
   CU(cudaGetLastError());
   return DIS_OK;
 }
@@ -859,6 +834,7 @@ int dis_create(int dim, int n_patches, const dis_patch* patches, int reactive_ma
   c->phys.cfl = opt->cfl;
   c->phys.cyl = opt->geometry == DIS_CYLINDRICAL ? 1 : 0;
   layout(c);
+  c->patch_set.assign(n_patches, 0);
   *out = c;
   return DIS_OK;
 }
@@ -866,6 +842,7 @@ int dis_create(int dim, int n_patches, const dis_patch* patches, int reactive_ma
 int dis_set_materials(dis_ctx* c, const dis_material* m, int n) {
   if (!c || !m) return fail(DIS_EINVAL, "dis_set_materials: NULL argument");
   if (n != 2) return fail(DIS_EINVAL, "dis_set_materials: exactly 2 materials are supported (got %d)", n);
+  const Phys old = c->phys;
   for (int l = 0; l < 2; ++l) {
     if (!(m[l].gamma > 1.0)) return fail(DIS_EINVAL, "dis_set_materials: gamma must be > 1");
     if (m[l].G < 0 || m[l].p_inf < 0) return fail(DIS_EINVAL, "dis_set_materials: negative G or p_inf");
@@ -877,9 +854,25 @@ int dis_set_materials(dis_ctx* c, const dis_material* m, int n) {
     if (m[l].reactive && (m[l].rate_law < 0 || m[l].rate_law > 1 || !std::isfinite(m[l].p_ign) ||
                           !std::isfinite(m[l].A) || m[l].A < 0))
       return fail(DIS_EINVAL, "dis_set_materials: bad rate law (rate_law 0 or 1, finite A >= 0 and p_ign)");
-    c->phys.m[l] = to_dev(m[l]);
   }
+  for (int l = 0; l < 2; ++l) c->phys.m[l] = to_dev(m[l]);
   c->physf = to_float(c->phys);
+  if (c->fp32 && c->have_mats && c->have_state && c->ws_ready &&
+      (old.m[0].kap != c->phys.m[0].kap || old.m[1].kap != c->phys.m[1].kap)) {
+    // an FP32-bulk state holds e_s = rho E - kappa(phi1): keep rho E
+    const double dk2 = old.m[1].kap - c->phys.m[1].kap;
+    const double ddk = (old.m[0].kap - old.m[1].kap) - (c->phys.m[0].kap - c->phys.m[1].kap);
+    const unsigned nc = (unsigned)c->seg_cell.size();
+    if (c->dim == 1) {
+      if (c->y >= 0) k_rekappa32<1, true><<<nc, SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, c->q32[0], c->T, dk2, ddk);
+      else k_rekappa32<1, false><<<nc, SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, c->q32[0], c->T, dk2, ddk);
+    } else {
+      if (c->y >= 0) k_rekappa32<2, true><<<nc, SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, c->q32[0], c->T, dk2, ddk);
+      else k_rekappa32<2, false><<<nc, SEG, 0, c->stream>>>(c->d_pd, c->d_seg_cell, c->q32[0], c->T, dk2, ddk);
+    }
+    CU(cudaGetLastError());
+  }
+  c->rate_valid = false;  // the rate depends on the closures
   c->have_mats = true;
   // captured steps hold the closure parameters by value: capture again
   if (c->graph[0] || c->graph[1]) cudaStreamSynchronize(c->stream);  // replays may be in flight
@@ -918,6 +911,8 @@ int dis_bind_workspace(dis_ctx* c, void* dev, size_t bytes) {
   c->ws_owned = false;
   c->ws_ready = false;
   c->have_state = false;
+  c->patch_set.assign(c->np, 0);
+  c->rate_valid = false;
   return ensure_ws(c);
 }
 
@@ -939,6 +934,54 @@ int dis_set_state(dis_ctx* c, int kind, const double* src, int src_on_device) {
   if (rc) return rc;
   if (!src_on_device) CU(cudaStreamSynchronize(c->stream));  // the host buffer may be reused
   c->have_state = true;
+  c->patch_set.assign(c->np, 1);
+  c->steps_total = 0;
+  return DIS_OK;
+}
+
+int dis_set_patch_state(dis_ctx* c, int patch, int kind, const double* src, int src_on_device) {
+  if (!c || !src) return fail(DIS_EINVAL, "dis_set_patch_state: NULL argument");
+  if (patch < 0 || patch >= c->np) return fail(DIS_EINVAL, "dis_set_patch_state: patch %d outside 0..%d", patch, c->np - 1);
+  if (kind != DIS_CONSERVATIVE && kind != DIS_PRIMITIVE) return fail(DIS_EINVAL, "dis_set_patch_state: bad kind");
+  if (!c->have_mats) return fail(DIS_ESTATE, "dis_set_patch_state: set materials first");
+  int rc = ensure_ws(c);
+  if (rc) return rc;
+  const size_t bytes = sizeof(double) * (size_t)c->nf * c->pd[patch].nx * c->pd[patch].ny;
+  const double* dsrc = src;
+  if (!src_on_device) {
+    CU(cudaMemcpyAsync(c->io, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    dsrc = c->io;
+  }
+  const bool rx = c->y >= 0;
+  const int prim = kind == DIS_PRIMITIVE;
+  if (c->dim == 1) rc = rx ? do_unpack<1, true>(c, dsrc, prim, patch) : do_unpack<1, false>(c, dsrc, prim, patch);
+  else rc = rx ? do_unpack<2, true>(c, dsrc, prim, patch) : do_unpack<2, false>(c, dsrc, prim, patch);
+  if (rc) return rc;
+  if (!src_on_device) CU(cudaStreamSynchronize(c->stream));
+  c->rate_valid = false;
+  c->patch_set[patch] = 1;
+  c->have_state = std::all_of(c->patch_set.begin(), c->patch_set.end(), [](char x) { return x != 0; });
+  c->steps_total = 0;
+  return DIS_OK;
+}
+
+int dis_get_patch_state(dis_ctx* c, int patch, int kind, double* dst, int dst_on_device) {
+  if (!c || !dst) return fail(DIS_EINVAL, "dis_get_patch_state: NULL argument");
+  if (patch < 0 || patch >= c->np) return fail(DIS_EINVAL, "dis_get_patch_state: patch %d outside 0..%d", patch, c->np - 1);
+  if (kind != DIS_CONSERVATIVE && kind != DIS_PRIMITIVE) return fail(DIS_EINVAL, "dis_get_patch_state: bad kind");
+  if (!c->patch_set[patch]) return fail(DIS_ESTATE, "dis_get_patch_state: patch %d holds no state", patch);
+  const size_t bytes = sizeof(double) * (size_t)c->nf * c->pd[patch].nx * c->pd[patch].ny;
+  double* ddst = dst_on_device ? dst : c->io;
+  const bool rx = c->y >= 0;
+  const int prim = kind == DIS_PRIMITIVE;
+  int rc;
+  if (c->dim == 1) rc = rx ? do_pack<1, true>(c, ddst, prim, patch) : do_pack<1, false>(c, ddst, prim, patch);
+  else rc = rx ? do_pack<2, true>(c, ddst, prim, patch) : do_pack<2, false>(c, ddst, prim, patch);
+  if (rc) return rc;
+  if (!dst_on_device) {
+    CU(cudaMemcpyAsync(dst, c->io, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+  }
   return DIS_OK;
 }
 
@@ -1001,6 +1044,8 @@ int dis_set_state_async(dis_ctx* c, int kind, const double* src) {
   if (rc) return rc;
   CU(cudaEventRecord(c->in_free[b], c->stream));
   c->have_state = true;
+  c->patch_set.assign(c->np, 1);
+  c->steps_total = 0;
   return DIS_OK;
 }
 
@@ -1034,11 +1079,27 @@ int dis_sync(dis_ctx* c) {
   return DIS_OK;
 }
 
+// Events around a step call (dis_query reports the device time between them).
+static int timed_dispatch(dis_ctx* c, int n, bool fixed) {
+  if (!c->ev_step[0]) {
+    CU(cudaEventCreate(&c->ev_step[0]));
+    CU(cudaEventCreate(&c->ev_step[1]));
+  }
+  CU(cudaEventRecord(c->ev_step[0], c->stream));
+  const int rc = dispatch_steps(c, n, fixed);
+  if (rc) return rc;
+  CU(cudaEventRecord(c->ev_step[1], c->stream));
+  c->ev_recorded = true;
+  c->last_steps = n;
+  c->steps_total += n;
+  return DIS_OK;
+}
+
 int dis_step(dis_ctx* c, int n_steps, double* dt_out) {
   if (!c) return fail(DIS_EINVAL, "dis_step: NULL context");
   if (n_steps < 0) return fail(DIS_EINVAL, "dis_step: negative step count");
-  if (!c->have_state) return fail(DIS_ESTATE, "dis_step: no state loaded");
-  int rc = dispatch_steps(c, n_steps, false);
+  if (!c->have_state) return fail(DIS_ESTATE, "dis_step: no state loaded (every patch needs one)");
+  int rc = timed_dispatch(c, n_steps, false);
   if (rc) return rc;
   if (dt_out && n_steps > 0) {
     CU(cudaMemcpyAsync(dt_out, c->dtlast, sizeof(double) * c->np, cudaMemcpyDeviceToHost, c->stream));
@@ -1055,7 +1116,51 @@ int dis_step_fixed_dt(dis_ctx* c, int n_steps, const double* dt) {
     if (!(dt[p] > 0.0) || !std::isfinite(dt[p])) return fail(DIS_EINVAL, "dis_step_fixed_dt: bad dt[%d]", p);
   CU(cudaMemcpyAsync(c->dtfix, dt, sizeof(double) * c->np, cudaMemcpyHostToDevice, c->stream));
   CU(cudaStreamSynchronize(c->stream));
-  return dispatch_steps(c, n_steps, true);
+  return timed_dispatch(c, n_steps, true);
+}
+
+int dis_query(dis_ctx* c, dis_stats* out) {
+  if (!c || !out) return fail(DIS_EINVAL, "dis_query: NULL argument");
+  if (!c->have_state) return fail(DIS_ESTATE, "dis_query: no state loaded");
+  const bool rx = c->y >= 0;
+  int rc;
+  if (c->dim == 1) rc = rx ? do_query<1, true>(c) : do_query<1, false>(c);
+  else rc = rx ? do_query<2, true>(c) : do_query<2, false>(c);
+  if (rc) return rc;
+  double q[NQ];
+  std::vector<double> dts(c->np);
+  int st[4] = {0, 0, 0, 0};
+  CU(cudaMemcpyAsync(q, c->qout, sizeof q, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(dts.data(), c->dtlast, sizeof(double) * c->np, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaMemcpyAsync(st, c->status, sizeof st, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  dis_stats r{};
+  r.mass[0] = q[0];
+  r.mass[1] = q[1];
+  r.momentum[0] = q[2];
+  r.momentum[1] = q[3];
+  r.energy = q[4];
+  r.reactant = q[5];
+  r.phi_min = q[6];
+  r.phi_max = q[7];
+  if (c->steps_total > 0) {
+    r.dt_min = *std::min_element(dts.begin(), dts.end());
+    r.dt_max = *std::max_element(dts.begin(), dts.end());
+  }
+  if (c->ev_recorded) {
+    float ms = 0.f;
+    CU(cudaEventElapsedTime(&ms, c->ev_step[0], c->ev_step[1]));
+    r.kernel_ms = ms;
+  }
+  const double per_cell = c->fp32 ? 4.0 * (c->nf + 1) : 8.0 * c->nf;
+  r.bytes = 2.0 * per_cell * (double)c->ncells * (double)c->last_steps;
+  r.steps = c->steps_total;
+  r.launches = c->launches;
+  r.status = st[0] ? DIS_ENONPHYSICAL : DIS_OK;
+  r.bad_patch = st[0] ? st[1] : -1;
+  r.bad_cell = st[0] ? st[2] : -1;
+  *out = r;
+  return DIS_OK;
 }
 
 int dis_check(dis_ctx* c, int* bad_patch, int* bad_cell) {
@@ -1084,7 +1189,7 @@ int dis_tile_choice(const dis_ctx* c, int* tx, int* ty, int* precomputed, double
   const int shape = c->variant % 3;
   if (tx) *tx = c->dim == 2 ? kTiles2D[shape][0] : kTiles1D[shape];
   if (ty) *ty = c->dim == 2 ? kTiles2D[shape][1] : 1;
-  if (precomputed) *precomputed = variant_pre(c->variant);
+  if (precomputed) *precomputed = 0;
   if (step_ms)
     for (int v = 0; v < DIS_NVARIANTS; ++v) step_ms[v] = variant_valid(c, v) ? c->tune_ms[v] : 0.0;
   return DIS_OK;
@@ -1094,8 +1199,7 @@ int dis_set_variant(dis_ctx* c, int variant) {
   if (!c) return fail(DIS_EINVAL, "dis_set_variant: NULL context");
   if (!c->fp32) return fail(DIS_EINVAL, "dis_set_variant: only FP32-bulk contexts have variants");
   if (variant != -1 && !variant_valid(c, variant))
-    return fail(DIS_EINVAL, "dis_set_variant: variant %d is not one of this context's (%s)", variant,
-                c->dim == 2 ? "0..11" : "0..2, 6..8");
+    return fail(DIS_EINVAL, "dis_set_variant: variant %d is not one of 0..%d", variant, DIS_NVARIANTS - 1);
   if (c->graph[0] || c->graph[1]) cudaStreamSynchronize(c->stream);  // replays may be in flight
   for (int g = 0; g < 2; ++g)
     if (c->graph[g]) {
@@ -1154,6 +1258,8 @@ void dis_destroy(dis_ctx* c) {
   if (c->s_in) cudaStreamDestroy(c->s_in);
   if (c->s_out) cudaStreamDestroy(c->s_out);
   if (c->ws_owned && c->ws) cudaFree(c->ws);
+  for (cudaEvent_t e : c->ev_step)
+    if (e) cudaEventDestroy(e);
   dis_internal_adj_free(c);
   delete c;
 }

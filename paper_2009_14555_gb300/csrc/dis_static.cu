@@ -6,7 +6,7 @@
 // locked, a process whose device memory was reserved up front).  This entry
 // point computes the per-patch CFL time step of a conservative state that the
 // caller already holds in device memory, using only a fixed scratch area in
-// this library's image (DIS_STATIC_MAX_PATCHES entries, about 0.6 MB per
+// this library's image (DIS_STATIC_MAX_PATCHES entries, about 0.7 MB per
 // device, held by every GPU that loads the library until the process exits).
 //
 // It is a variant of the CFL reduction done by the stepping kernels: the same
@@ -38,6 +38,7 @@ struct StaticPatch {
 
 struct StaticScratch {
   unsigned long long rate[kMaxPatches];  // per-patch max rate (bits of a positive double)
+  int bad[kMaxPatches];                  // per patch: a cell without a real sound speed or density
   StaticPatch patch[kMaxPatches];
 };
 
@@ -73,9 +74,13 @@ __global__ void __launch_bounds__(256) k_cfl_static(Phys P, const double* __rest
     const Strain s = strain_of(b[L::V11 * n], V12, V21, b[L::V22 * n], b[L::V33 * n]);
     const double KE = 0.5 * (mx * u + my * v);
     const double pr = (b[L::E * n] - KE - ref_energy(P, phi, a1, a2, arl, s.J2)) / xi_of(P, phi);
-    const double cL = sqrt(fmax(cL2_of(P, phi, rho, pr, s.J2), 0.0));
+    const double cL2 = cL2_of(P, phi, rho, pr, s.J2);
+    const double cL = sqrt(fmax(cL2, 0.0));
     r = (fabs(u) + cL) / sp.dx;
     if (DIM == 2) r += (fabs(v) + cL) / sp.dy;
+    // a state that has lost hyperbolicity (or its density, or is not finite)
+    // gets no time step: the patch's dt becomes NaN
+    if (!(cL2 > 0.0) || !(rho > 0.0) || !(r < INFINITY)) S->bad[p] = 1;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
@@ -85,7 +90,8 @@ __global__ void __launch_bounds__(256) k_cfl_static(Phys P, const double* __rest
 
 __global__ void k_dt_static(const StaticScratch* S, int np, double cfl, double* dt) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < np) dt[p] = cfl / __longlong_as_double((long long)S->rate[p]);
+  if (p < np) dt[p] = S->bad[p] ? __longlong_as_double(0x7ff8000000000000LL)
+                                : cfl / __longlong_as_double((long long)S->rate[p]);
 }
 
 MatDev dev_material(const dis_material& m) {
@@ -142,8 +148,7 @@ extern "C" int dis_cfl_dt_static(int dim, int n_patches, const dis_patch* patche
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_addr[dev]) {
     // Set-up, once per device, with that device current: the device address
-    // of the static scratch.  Make the first call on a device before any
-    // stream capture.
+    // of the static scratch.
     void* ptr = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
     if (e != cudaSuccess || !ptr)
@@ -154,7 +159,9 @@ extern "C" int dis_cfl_dt_static(int dim, int n_patches, const dis_patch* patche
   StaticScratch* S = g_addr[dev];
   // Patch descriptors go into the static area by a copy from pageable host
   // memory, which the runtime stages before returning, so the host array may
-  // be reused afterwards (the lock above serialises its use).
+  // be reused afterwards (the lock above serialises its use).  Such a copy
+  // cannot be part of a captured graph: the call must not be made while its
+  // stream is being captured.
   static StaticPatch staging[kMaxPatches];
   long long poff = 0;
   for (int p = 0; p < n_patches; ++p) {
@@ -169,8 +176,10 @@ extern "C" int dis_cfl_dt_static(int dim, int n_patches, const dis_patch* patche
   if (cudaMemcpyAsync(S->patch, staging, sizeof(StaticPatch) * n_patches, cudaMemcpyHostToDevice, st) !=
       cudaSuccess)
     return dis_internal_error(DIS_ECUDA, "dis_cfl_dt_static: descriptor copy failed");
-  // the per-patch maxima start at zero on every call (the area keeps the last call's values)
-  if (cudaMemsetAsync(S->rate, 0, sizeof(unsigned long long) * n_patches, st) != cudaSuccess)
+  // the per-patch maxima and flags start at zero on every call (the area
+  // keeps the last call's values)
+  if (cudaMemsetAsync(S->rate, 0, sizeof(unsigned long long) * n_patches, st) != cudaSuccess ||
+      cudaMemsetAsync(S->bad, 0, sizeof(int) * n_patches, st) != cudaSuccess)
     return dis_internal_error(DIS_ECUDA, "dis_cfl_dt_static: clearing the scratch failed");
   Phys P{};
   P.m[0] = dev_material(materials[0]);

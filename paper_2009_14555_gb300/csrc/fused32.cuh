@@ -2,19 +2,24 @@
 //
 // A CTA owns a tile of TX x TY interior cells (TX cells of one row in 1D).
 // It recovers the primitives of the tile plus a 3-cell halo into shared
-// memory (ghosts by index map; or, PRE, copies them from the planes of a
-// primitive pre-pass, which recovers every cell once), computes every x face and y face of the tile
+// memory (ghosts by index map), computes every x face and y face of the tile
 // (MUSCL/THINC-BVD + HLLD) into shared memory, and updates its cells
-// (divergence, non-conservative terms, RK3 combination, last stage: plastic
-// and reactive steps).  Primitives and face data never go to HBM: per stage
-// the tile reads q_src (with halo, mostly from L2) and q^n and writes q_dst.
+// (divergence, non-conservative terms, RK3 combination; last stage: plastic
+// and reactive steps, and the CFL rate of the new state for the next step's
+// time step).  Primitives and face data never go to HBM: per stage the tile
+// reads q_src (with halo, mostly from L2) and q^n and writes q_dst.  No
+// float64 arithmetic runs outside the rare mixed-cell plastic branch.
 //
-// Energy flux split (float64 consistency with the phi1 update): a face keeps
-// F_phi = phi_K u_face, D = X - u_face (X the kappa flux factor, D small) and
-// phi_K; the update forms the kappa part of the energy flux as
-//   kappa_2 (u_face + D) + (kappa_1 - kappa_2) (F_phi + phi_K D)
-// in float64, with the same float F_phi differences that update phi1, so
-// rho E - kappa(phi1) changes only by the small float terms.
+// Energy (state slot E = e_s = rho E - kappa(phi1), step32.cuh): the rho E
+// flux is the float soft flux plus kappa(phi_K) X, X = u_face + D (D a small
+// star compression term), kappa(phi) = kappa_2 + (kappa_1 - kappa_2) phi.
+// Subtracting (kappa_1 - kappa_2) times the phi1 equation (flux phi_K u_face,
+// source phi div u_face) leaves
+//   d e_s/dt = -[div F_soft + kappa_2 div X + (kappa_1 - kappa_2) div(phi_K D)
+//                + (kappa_1 - kappa_2) phi div u_face],
+// whose terms are differences of face values that are formed before any
+// large factor multiplies them.  phi1 itself is advanced in float-float from
+// the exact (TwoSum) differences of its float face fluxes.
 #pragma once
 #include "step32.cuh"
 
@@ -149,16 +154,21 @@ constexpr size_t fused32_smem() {
   using S = FSlots<DIM, RX>;
   constexpr int HX = TX + 2 * NG, HY = DIM == 2 ? TY + 2 * NG : 1;
   constexpr int NFX = (TX + 1) * TY, NFY = DIM == 2 ? TX * (TY + 1) : 0;
-  return sizeof(float) * ((size_t)Lay<DIM, RX>::NF * HX * HY + (size_t)S::N * (NFX + NFY)) + 16 * sizeof(double);
+  return sizeof(float) * ((size_t)Lay<DIM, RX>::NF * HX * HY + (size_t)S::N * (NFX + NFY));
 }
+
+// Positive float -> bits that order like the value (for integer atomic max).
+__device__ __forceinline__ unsigned rate_bits(float r) { return __float_as_uint(fmaxf(r, 0.f)); }
 
 // One stage on one tile t = (patch, i0, j0) by the NT threads of a CTA, with
 // the tile's primitives and faces in the shared memory sm.  The stage kernel
 // runs it once per CTA; the persistent 1D batch kernel runs it for every tile
 // of its problem in turn (the caller synchronises the CTA between tiles).
-template <int DIM, bool RX, int TX, int TY, int NT, bool PRE, bool CYL = false>
+// Last stage: the CFL rate of every updated cell goes, by warp max, into
+// rate_cta (shared, if not null) or A.rate_next[patch] (global).
+template <int DIM, bool RX, int TX, int TY, int NT, bool CYL = false>
 __device__ __forceinline__ void stage32_tile(const Phys& P, const PhysF& F, const StepArgs32& A, const int4 t,
-                                             float* __restrict__ sm) {
+                                             float* __restrict__ sm, unsigned* rate_cta) {
   static_assert(TX * TY <= NT, "one thread per tile cell in the update phase");
   using L = Lay<DIM, RX>;
   using S = FSlots<DIM, RX>;
@@ -172,25 +182,34 @@ __device__ __forceinline__ void stage32_tile(const Phys& P, const PhysF& F, cons
   const int i0 = t.y, j0 = t.z;
   const int tid = threadIdx.x;
   const float dxf = (float)pd.dx, dyf = (float)pd.dy;
+  const long long T = A.T;
 
-  // 1. primitives of the tile and its halo: recovered here, or (PRE) copied
-  //    from the pre-pass planes, which already hold the ghost cells
+  // per-CTA constants of the update: dt (float-float and float), the RK
+  // weights, inverse cell sizes
+  __shared__ float dth_sh, dtl_sh, af_sh, bh_sh, bl_sh, ihx_sh, ihy_sh;
+  if (tid == 0) {
+    const double dt = A.dtfix ? A.dtfix[t.x] : P.cfl / __longlong_as_double((long long)A.rate[t.x]);
+    const ff d = ff_of(dt), b = ff_of(A.b);
+    dth_sh = d.h;
+    dtl_sh = d.l;
+    af_sh = (float)A.a;
+    bh_sh = b.h;
+    bl_sh = b.l;
+    ihx_sh = 1.f / dxf;
+    ihy_sh = 1.f / dyf;
+    if (A.last && i0 == 0 && j0 == 0) A.dtlast[t.x] = dt;
+  }
+
+  // 1. primitives of the tile and its halo (ghosts by the index map)
   for (int c = tid; c < HX * HY; c += NT) {
     const int hx = c % HX, hy = c / HX;
     const int i = i0 - NG + hx;
     const int j = DIM == 2 ? j0 - NG + hy : 0;
     if (i < -NG || i >= pd.nx + NG || (DIM == 2 && (j < -NG || j >= pd.ny + NG))) continue;
-    if constexpr (PRE) {
-      const long long kk = cidx(pd, i, j);
-      const int plane = HX * HY;
-#pragma unroll
-      for (int f = 0; f < NF; ++f) Wsm[f * plane + c] = A.W[f * A.T + kk];
-      continue;
-    }
     bool fx = false, fy = false;
     const int si = ghost_map(i, pd.nx, pd.bc[0], pd.bc[1], fx);
     const int sj = DIM == 2 ? ghost_map(j, pd.ny, pd.bc[2], pd.bc[3], fy) : 0;
-    PrimF w = cons_to_prim32<DIM, RX>(P, F, A.q64src, A.q32src, A.T, cidx(pd, si, sj));
+    PrimF w = cons_to_prim32<DIM, RX>(P, F, A.src, T, cidx(pd, si, sj));
     if (fx) { w.u = -w.u; w.V12 = -w.V12; w.V21 = -w.V21; }
     if (fy) { w.v = -w.v; w.V12 = -w.V12; w.V21 = -w.V21; }
     const int plane = HX * HY;
@@ -224,297 +243,273 @@ __device__ __forceinline__ void stage32_tile(const Phys& P, const PhysF& F, cons
       face32<DIM, RX, 1>(F, Wsm, HX, HY, fx + NG, fy + NG - 1, dyf, dxf, Fys, NFY, g);
     }
   }
-  // per-CTA constants of the update: the step's dt and the inverse cell
-  // sizes, in float64 and float32 (no per-thread conversions)
-  __shared__ double dt_sh, ihx_sh, ihy_sh;
-  __shared__ float dtf_sh, af_sh, bf_sh;
-  if (tid == 0) {
-    dt_sh = A.dtfix ? A.dtfix[t.x] : P.cfl / __longlong_as_double((long long)A.rate[t.x]);
-    dtf_sh = (float)dt_sh;
-    ihx_sh = (double)(1.f / dxf);
-    ihy_sh = (double)(1.f / dyf);
-    af_sh = (float)A.a;
-    bf_sh = (float)A.b;
-  }
   __syncthreads();
 
-  // 4. update of the tile's cells
-  if (tid >= TX * TY) return;
+  // 3. update of the tile's cells (every lane of a warp with a tile cell
+  //    reaches the warp max of the last stage)
+  if (tid >= ((TX * TY + 31) / 32) * 32) return;
   const int lx = tid % TX, ly = tid / TX;
   const int i = i0 + lx, j = j0 + ly;
-  if (i >= pd.nx || (DIM == 2 && j >= pd.ny)) return;
-  const long long k = cidx(pd, i, j);
-  const long long T = A.T;
-  float q[NF], D[NF];
+  const bool valid = tid < TX * TY && i < pd.nx && (DIM == 1 || j < pd.ny);
+  float rate = 0.f;
+  if (valid) {
+    const long long k = cidx(pd, i, j);
+    float q[NF + 1], D[NF];
+    load32<DIM, RX>(A.src, T, k, q);
+    const float idx_ = ihx_sh;
+    const int fl = ly * (TX + 1) + lx, fr = fl + 1;
+    auto FX = [&](int s, int f) { return Fxs[s * NFX + f]; };
 #pragma unroll
-  for (int c = 0; c < NF; ++c) q[c] = (c == L::PHI || c == L::E) ? 0.f : A.q32src[c * T + k];
-  const double phi_d = A.q64src[k];
-  const double E_d = A.q64src[T + k];
-  const float idx_ = 1.f / dxf;
-  const int fl = ly * (TX + 1) + lx, fr = fl + 1;
-  auto FX = [&](int s, int f) { return Fxs[s * NFX + f]; };
-#pragma unroll
-  for (int c = 0; c < NF; ++c) D[c] = (FX(c, fr) - FX(c, fl)) * idx_;
-  float divu = (FX(S::UF, fr) - FX(S::UF, fl)) * idx_;
-  float bx = (FX(S::VA, fr) - FX(S::VA, fl)) * idx_;
-  float by = 0.f;
-  // Float64 terms: the conservative part of the phi1 divergence, Dc, from the
-  // float phi1 flux differences, and the energy divergence as
-  // (kappa_1 - kappa_2) Dc plus the small terms (soft energy flux,
-  // kappa_2 (u + D), (kappa_1 - kappa_2) phi_K D) summed in float32 - the same
-  // Dc that moves phi1 moves the kappa part of rho E.
-  const float k2f = (float)A.kap2, dkf = (float)A.dkap;
-  const double dFx = (double)(FX(L::PHI, fr) - FX(L::PHI, fl));
-  float small = ((FX(L::E, fr) - FX(L::E, fl)) +
-                 k2f * ((FX(S::UF, fr) + FX(S::DD, fr)) - (FX(S::UF, fl) + FX(S::DD, fl))) +
-                 dkf * (FX(S::PK, fr) * FX(S::DD, fr) - FX(S::PK, fl) * FX(S::DD, fl))) * idx_;
-  double Dc = dFx * ihx_sh;
-  if constexpr (DIM == 2) {
-    const float idy = 1.f / dyf;
-    const int fb = ly * TX + lx, ft = fb + TX;
-    auto FY = [&](int s_, int f) { return Fys[s_ * NFY + f]; };
-#pragma unroll
-    for (int c = 0; c < NF; ++c) D[c] += (FY(c, ft) - FY(c, fb)) * idy;
-    divu += (FY(S::UF, ft) - FY(S::UF, fb)) * idy;
-    bx += (FY(S::VA, ft) - FY(S::VA, fb)) * idy;
-    by = (FX(S::VB, fr) - FX(S::VB, fl)) * idx_ + (FY(S::VB, ft) - FY(S::VB, fb)) * idy;
-    const double dFy = (double)(FY(L::PHI, ft) - FY(L::PHI, fb));
-    small += ((FY(L::E, ft) - FY(L::E, fb)) +
-              k2f * ((FY(S::UF, ft) + FY(S::DD, ft)) - (FY(S::UF, fb) + FY(S::DD, fb))) +
-              dkf * (FY(S::PK, ft) * FY(S::DD, ft) - FY(S::PK, fb) * FY(S::DD, fb))) * idy;
-    Dc = fma(dFy, ihy_sh, Dc);
-  }
-  double DE = fma(A.dkap, Dc, (double)small);
-  const double Dphi = fma(-phi_d, (double)divu, Dc);
-  const float rho = q[L::A1] + q[L::A2];
-  const float uc = q[L::MX] / rho;
-  float vc = 0.f;
-  if constexpr (DIM == 2) vc = q[L::MY] / rho;
-  if constexpr (CYL) {
-    // cylindrical geometric source (x = r, y = z) from the cell's primitives
-    // in shared memory; the energy term in float64 with rho E
-    const int plane = HX * HY, kc = (ly + (DIM == 2 ? NG : 0)) * HX + lx + NG;
-    const float wp = Wsm[L::E * plane + kc], wphi = Wsm[L::PHI * plane + kc];
-    const float wu = Wsm[L::MX * plane + kc];
-    float wv = 0.f, v12 = 0.f, v21 = 0.f;
+    for (int c = 0; c < NF; ++c) D[c] = (FX(c, fr) - FX(c, fl)) * idx_;
+    float divu = (FX(S::UF, fr) - FX(S::UF, fl)) * idx_;
+    float bx = (FX(S::VA, fr) - FX(S::VA, fl)) * idx_;
+    float by = 0.f;
+    const float k2f = F.m[1].kap, dkf = F.m[0].kap - F.m[1].kap;
+    // phi1 flux divergence from the exact differences of the float fluxes
+    ff Dc = ff_mul_f(two_sum(FX(L::PHI, fr), -FX(L::PHI, fl)), idx_);
+    // soft part of the e_s divergence: differences first, then the large factors
+    float small = ((FX(L::E, fr) - FX(L::E, fl)) +
+                   k2f * ((FX(S::UF, fr) - FX(S::UF, fl)) + (FX(S::DD, fr) - FX(S::DD, fl))) +
+                   dkf * (FX(S::PK, fr) * FX(S::DD, fr) - FX(S::PK, fl) * FX(S::DD, fl))) * idx_;
     if constexpr (DIM == 2) {
-      wv = Wsm[L::MY * plane + kc];
-      v12 = Wsm[L::V12 * plane + kc];
-      v21 = Wsm[L::V21 * plane + kc];
+      const float idy = ihy_sh;
+      const int fb = ly * TX + lx, ft = fb + TX;
+      auto FY = [&](int s_, int f) { return Fys[s_ * NFY + f]; };
+#pragma unroll
+      for (int c = 0; c < NF; ++c) D[c] += (FY(c, ft) - FY(c, fb)) * idy;
+      divu += (FY(S::UF, ft) - FY(S::UF, fb)) * idy;
+      bx += (FY(S::VA, ft) - FY(S::VA, fb)) * idy;
+      by = (FX(S::VB, fr) - FX(S::VB, fl)) * idx_ + (FY(S::VB, ft) - FY(S::VB, fb)) * idy;
+      Dc = ff_add(Dc, ff_mul_f(two_sum(FY(L::PHI, ft), -FY(L::PHI, fb)), idy));
+      small += ((FY(L::E, ft) - FY(L::E, fb)) +
+                k2f * ((FY(S::UF, ft) - FY(S::UF, fb)) + (FY(S::DD, ft) - FY(S::DD, fb))) +
+                dkf * (FY(S::PK, ft) * FY(S::DD, ft) - FY(S::PK, fb) * FY(S::DD, fb))) * idy;
     }
-    const StrainF st = strain_f(Wsm[L::V11 * plane + kc], v12, v21, Wsm[L::V22 * plane + kc],
-                                Wsm[L::V33 * plane + kc]);
-    const float Gm2 = 2.f * (wphi * F.m[0].GoG + (1.f - wphi) * F.m[1].GoG) / xi_f(F, wphi);
-    const float srr = -wp + Gm2 * st.H11, szr = Gm2 * st.H12, stt = -wp + Gm2 * st.H33;
-    // 1/r without a float64 division (the FP64 pipe also carries the
-    // phi1 / rho E update): the float32 reciprocal, refined by one
-    // Newton-Raphson step x <- x + x (1 - r x) to ~1e-14 relative
-    const double r = fma((double)(i) + 0.5, pd.dx, pd.x0);
-    double ird = (double)(1.f / (float)r);
-    ird = fma(ird, fma(-r, ird, 1.0), ird);
-    const float ir = (float)ird;
-    D[L::A1] += q[L::A1] * wu * ir;
-    D[L::A2] += q[L::A2] * wu * ir;
-    if constexpr (RX) D[L::AL] += q[L::AL] * wu * ir;
-    D[L::MX] += (rho * wu * wu - srr + stt) * ir;
-    if constexpr (DIM == 2) D[L::MY] += (rho * wv * wu - szr) * ir;
-    DE = fma(fma(E_d, (double)wu, -(double)(wu * srr + wv * szr)), ird, DE);
-    const float t = wu * ir * (1.f / 3.f);
-    D[L::V11] += t * q[L::V11];
-    D[L::V22] += t * q[L::V22];
-    D[L::V33] -= 2.f * t * q[L::V33];
+    const ff phi_c = {q[L::PHI], q[NF]};
+    const ff Dphi = ff_add(Dc, ff_neg(ff_mul_f(phi_c, divu)));
+    float Des = small + dkf * phi_c.h * divu;
+    const float rho = q[L::A1] + q[L::A2];
+    const float uc = q[L::MX] / rho;
+    float vc = 0.f;
+    if constexpr (DIM == 2) vc = q[L::MY] / rho;
+    if constexpr (CYL) {
+      // cylindrical geometric source (x = r, y = z) from the cell's primitives
+      // in shared memory; energy: rho E u_r with rho E = e_s + kappa(phi1)
+      const int plane = HX * HY, kc = (ly + (DIM == 2 ? NG : 0)) * HX + lx + NG;
+      const float wp = Wsm[L::E * plane + kc], wphi = Wsm[L::PHI * plane + kc];
+      const float wu = Wsm[L::MX * plane + kc];
+      float wv = 0.f, v12 = 0.f, v21 = 0.f;
+      if constexpr (DIM == 2) {
+        wv = Wsm[L::MY * plane + kc];
+        v12 = Wsm[L::V12 * plane + kc];
+        v21 = Wsm[L::V21 * plane + kc];
+      }
+      const StrainF st = strain_f(Wsm[L::V11 * plane + kc], v12, v21, Wsm[L::V22 * plane + kc],
+                                  Wsm[L::V33 * plane + kc]);
+      const float Gm2 = 2.f * (wphi * F.m[0].GoG + (1.f - wphi) * F.m[1].GoG) / xi_f(F, wphi);
+      const float srr = -wp + Gm2 * st.H11, szr = Gm2 * st.H12, stt = -wp + Gm2 * st.H33;
+      const float r = (float)pd.x0 + ((float)i + 0.5f) * dxf;
+      const float ir = 1.f / r;
+      D[L::A1] += q[L::A1] * wu * ir;
+      D[L::A2] += q[L::A2] * wu * ir;
+      if constexpr (RX) D[L::AL] += q[L::AL] * wu * ir;
+      D[L::MX] += (rho * wu * wu - srr + stt) * ir;
+      if constexpr (DIM == 2) D[L::MY] += (rho * wv * wu - szr) * ir;
+      Des += (q[L::E] * wu + (k2f + dkf * phi_c.h) * wu - (wu * srr + wv * szr)) * ir;
+      const float tt = wu * ir * (1.f / 3.f);
+      D[L::V11] += tt * q[L::V11];
+      D[L::V22] += tt * q[L::V22];
+      D[L::V33] -= 2.f * tt * q[L::V33];
+      if constexpr (DIM == 2) {
+        D[L::V12] += tt * q[L::V12];
+        D[L::V21] += tt * q[L::V21];
+      }
+    }
+    const float t23 = 2.f / 3.f;
+    D[L::V11] -= t23 * q[L::V11] * divu - uc * bx;
+    D[L::V22] -= t23 * q[L::V22] * divu - vc * by;
+    D[L::V33] -= t23 * q[L::V33] * divu;
     if constexpr (DIM == 2) {
-      D[L::V12] += t * q[L::V12];
-      D[L::V21] += t * q[L::V21];
+      D[L::V12] -= t23 * q[L::V12] * divu - uc * by;
+      D[L::V21] -= t23 * q[L::V21] * divu - vc * bx;
     }
-  }
-  const float t23 = 2.f / 3.f;
-  D[L::V11] -= t23 * q[L::V11] * divu - uc * bx;
-  D[L::V22] -= t23 * q[L::V22] * divu - vc * by;
-  D[L::V33] -= t23 * q[L::V33] * divu;
-  if constexpr (DIM == 2) {
-    D[L::V12] -= t23 * q[L::V12] * divu - uc * by;
-    D[L::V21] -= t23 * q[L::V21] * divu - vc * bx;
-  }
-  const double dt = dt_sh;
-  const float dtf = dtf_sh;
-  float o[NF];
-  double ophi, oE;
-  if (A.a == 0.0) {
+    const float dtf = dth_sh;
+    const ff dt_ff = {dth_sh, dtl_sh};
+    float o[NF + 1];
+    const ff yphi = ff_add(phi_c, ff_neg(ff_mul(dt_ff, Dphi)));
+    const float yE = q[L::E] - dtf * Des;
+    ff ophi;
+    if (af_sh == 0.f) {
 #pragma unroll
-    for (int c = 0; c < NF; ++c) o[c] = q[c] - dtf * D[c];
-    ophi = phi_d - dt * Dphi;
-    oE = E_d - dt * DE;
-  } else {
-    const float af = af_sh, bf = bf_sh;
+      for (int c = 0; c < NF; ++c) o[c] = q[c] - dtf * D[c];
+      ophi = yphi;
+      o[L::E] = yE;
+    } else {
+      const float af = af_sh, bf = bh_sh;
+      float qn[NF + 1];
+      load32<DIM, RX>(A.qn, T, k, qn);
 #pragma unroll
-    for (int c = 0; c < NF; ++c)
-      o[c] = (c == L::PHI || c == L::E) ? 0.f : af * A.q32n[c * T + k] + bf * (q[c] - dtf * D[c]);
-    ophi = A.a * A.q64n[k] + A.b * (phi_d - dt * Dphi);
-    oE = A.a * A.q64n[T + k] + A.b * (E_d - dt * DE);
+      for (int c = 0; c < NF; ++c) o[c] = af * qn[c] + bf * (q[c] - dtf * D[c]);
+      o[L::E] = af * qn[L::E] + bf * yE;
+      const ff phin = {qn[L::PHI], qn[NF]};
+      ophi = ff_add(phin, ff_mul({bh_sh, bl_sh}, ff_add(yphi, ff_neg(phin))));
+    }
+    o[L::PHI] = ophi.h;
+    o[NF] = ophi.l;
+    if (A.last) {
+      const float ophf = ophi.h;
+      float v12 = 0.f, v21 = 0.f;
+      if constexpr (DIM == 2) { v12 = o[L::V12]; v21 = o[L::V21]; }
+      if (ophf > 1e-3f && ophf < 1.f - 1e-3f) {
+        const double dt = ff_val(dth_sh, dtl_sh);
+        double d11 = o[L::V11], d12 = v12, d21 = v21, d22 = o[L::V22], d33 = o[L::V33];
+        plastic(P, ff_val(ophi.h, ophi.l), dt, d11, d12, d21, d22, d33);
+        o[L::V11] = (float)d11; v12 = (float)d12; v21 = (float)d21; o[L::V22] = (float)d22; o[L::V33] = (float)d33;
+      } else {
+        plastic_f(F, ophf, dtf, o[L::V11], v12, v21, o[L::V22], o[L::V33]);
+      }
+      if constexpr (DIM == 2) { o[L::V12] = v12; o[L::V21] = v21; }
+      if constexpr (RX) {
+        const int y = P.y;
+        const MatT<float>& m = F.m[y];
+        const float ary = y == 0 ? o[L::A1] : o[L::A2];
+        const float phy = y == 0 ? ophf : (1.f - ophf) - ophi.l;
+        const float rr = o[L::A1] + o[L::A2];
+        const float mx = o[L::MX];
+        float my = 0.f;
+        if constexpr (DIM == 2) my = o[L::MY];
+        const float KE = 0.5f * (mx * mx + my * my) / rr;
+        const StrainF s = strain_f(o[L::V11], v12, v21, o[L::V22], o[L::V33]);
+        const float xi = xi_f(F, ophf);
+        const float p0 = (o[L::E] - KE - soft_ref_f(F, ophf, o[L::A1], o[L::A2], 0.f, s.J2)) / xi;
+        const float Tfac = m.iGm1 / ((ary / phy) * m.cv);
+        const float Qx = m.Q / xi;
+        auto fr_ = [&](float Lm) {
+          if (m.law == 1) {
+            const float pk = p0 - Qx * Lm;
+            return pk > m.pign && Lm > 0.f ? -m.A * sqrtf(ary * Lm) : 0.f;
+          }
+          const float Tk = (p0 - Qx * Lm) * Tfac;
+          return Tk > 0.f ? -m.A * Lm * expf(-m.Tact / Tk) : 0.f;
+        };
+        const float L0 = o[L::AL];
+        const float k1 = fr_(L0);
+        const float k2 = fr_(L0 + 0.5f * dtf * k1);
+        const float k3 = fr_(L0 + 0.5f * dtf * k2);
+        const float k4 = fr_(L0 + dtf * k3);
+        const float L1 = L0 + dtf / 6.f * (k1 + 2.f * k2 + 2.f * k3 + k4);
+        o[L::AL] = m.law == 1 && !(L1 > 0.f) ? 0.f : L1;
+      }
+      bool bad = !(ophf >= -1e-6f && ophf <= 1.f + 1e-6f);
+#pragma unroll
+      for (int c = 0; c <= NF; ++c) bad |= !isfinite(o[c]);
+      if (bad) flag_bad(A.status, t.x, i + pd.nx * j);
+      // CFL rate of the new state: the next step's time step
+      rate = cfl_rate_of<DIM>(F, prim32_of<DIM, RX>(P, F, o), ihx_sh, ihy_sh, A.status, t.x, i + pd.nx * j);
+    }
+#pragma unroll
+    for (int c = 0; c <= NF; ++c) A.dst[c * T + k] = o[c];
   }
   if (A.last) {
-    const float ophf = (float)ophi;
-    float v12 = 0.f, v21 = 0.f;
-    if constexpr (DIM == 2) { v12 = o[L::V12]; v21 = o[L::V21]; }
-    if (ophf > 1e-3f && ophf < 1.f - 1e-3f) {
-      double d11 = o[L::V11], d12 = v12, d21 = v21, d22 = o[L::V22], d33 = o[L::V33];
-      plastic(P, ophi, dt, d11, d12, d21, d22, d33);
-      o[L::V11] = (float)d11; v12 = (float)d12; v21 = (float)d21; o[L::V22] = (float)d22; o[L::V33] = (float)d33;
-    } else {
-      plastic_f(F, ophf, dtf, o[L::V11], v12, v21, o[L::V22], o[L::V33]);
-    }
-    if constexpr (DIM == 2) { o[L::V12] = v12; o[L::V21] = v21; }
-    if constexpr (RX) {
-      const int y = P.y;
-      const MatT<float>& m = F.m[y];
-      const float phi1 = ophf;
-      const float ary = y == 0 ? o[L::A1] : o[L::A2];
-      const float phy = y == 0 ? phi1 : (float)(1.0 - ophi);
-      const float rr = o[L::A1] + o[L::A2];
-      const float mx = o[L::MX];
-      float my = 0.f;
-      if constexpr (DIM == 2) my = o[L::MY];
-      const float KE = 0.5f * (mx * mx + my * my) / rr;
-      const StrainF s = strain_f(o[L::V11], v12, v21, o[L::V22], o[L::V33]);
-      const double kap = fma(ophi, A.dkap, A.kap2);
-      const double num = oE - kap - (double)KE - (double)soft_ref_f(F, phi1, o[L::A1], o[L::A2], 0.f, s.J2);
-      const float xi = xi_f(F, phi1);
-      const float p0 = (float)num / xi;
-      const float Tfac = m.iGm1 / ((ary / phy) * m.cv);
-      const float Qx = m.Q / xi;
-      auto fr_ = [&](float Lm) {
-        if (m.law == 1) {
-          const float pk = p0 - Qx * Lm;
-          return pk > m.pign && Lm > 0.f ? -m.A * sqrtf(ary * Lm) : 0.f;
-        }
-        const float Tk = (p0 - Qx * Lm) * Tfac;
-        return Tk > 0.f ? -m.A * Lm * expf(-m.Tact / Tk) : 0.f;
-      };
-      const float L0 = o[L::AL];
-      const float k1 = fr_(L0);
-      const float k2 = fr_(L0 + 0.5f * dtf * k1);
-      const float k3 = fr_(L0 + 0.5f * dtf * k2);
-      const float k4 = fr_(L0 + dtf * k3);
-      const float L1 = L0 + dtf / 6.f * (k1 + 2.f * k2 + 2.f * k3 + k4);
-      o[L::AL] = m.law == 1 && !(L1 > 0.f) ? 0.f : L1;
-    }
-    // range and finiteness checks without float64 compares
-    const bool E_finite = ((__double_as_longlong(oE) >> 52) & 0x7ff) != 0x7ff;
-    bool bad = !(ophf >= -1e-6f && ophf <= 1.f + 1e-6f) || !E_finite;
 #pragma unroll
-    for (int c = 0; c < NF; ++c) bad |= (c != L::PHI && c != L::E) && !isfinite(o[c]);
-    if (bad) flag_bad(A.status, t.x, i + pd.nx * j);
-    if (i == 0 && j == 0) A.dtlast[t.x] = dt;
+    for (int s_ = 16; s_ > 0; s_ >>= 1) rate = fmaxf(rate, __shfl_xor_sync(0xffffffffu, rate, s_));
+    if ((tid & 31) == 0 && rate > 0.f) {
+      if (rate_cta) atomicMax(rate_cta, rate_bits(rate));
+      else atomicMax(A.rate_next + t.x, (unsigned long long)__double_as_longlong((double)rate));
+    }
   }
-#pragma unroll
-  for (int c = 0; c < NF; ++c)
-    if (c != L::PHI && c != L::E) A.q32dst[c * T + k] = o[c];
-  A.q64dst[k] = ophi;
-  A.q64dst[T + k] = oE;
 }
 
-template <int DIM, bool RX, int TX, int TY, int NT, bool PRE, int MINB, bool CYL = false>
+template <int DIM, bool RX, int TX, int TY, int NT, int MINB, bool CYL = false>
 __global__ void __launch_bounds__(NT, MINB) k_stage32(Phys P, PhysF F, StepArgs32 A, const int4* __restrict__ tiles) {
   extern __shared__ __align__(16) float sm[];
-  stage32_tile<DIM, RX, TX, TY, NT, PRE, CYL>(P, F, A, tiles[blockIdx.x], sm);
+  stage32_tile<DIM, RX, TX, TY, NT, CYL>(P, F, A, tiles[blockIdx.x], sm, nullptr);
 }
 
-// CFL rate of the state at the start of a step (FP32-bulk): per-patch max of
-// sum_d (|u_d| + c_L) / dx_d over interior cells.
-// sum_d (|u_d| + c_L) / dx_d of one interior cell of the source state;
-// flags a cell without a real sound speed.
+// CFL rate of the state at the start of a step (FP32-bulk), for the first
+// step after the state was set (later steps take it from the last stage of
+// the step before): per-patch max of sum_d (|u_d| + c_L) / dx_d.
 template <int DIM, bool RX>
-__device__ __forceinline__ float cfl_rate32(const Phys& P, const PhysF& F, const StepArgs32& A,
-                                            const PatchDev& pd, int patch, int i, int j) {
-  const PrimF w = cons_to_prim32<DIM, RX>(P, F, A.q64src, A.q32src, A.T, cidx(pd, i, j));
-  const StrainF s = strain_f(w.V11, w.V12, w.V21, w.V22, w.V33);
-  const float rho = w.phi * w.r1 + (1.f - w.phi) * w.r2;
-  const float cL2 = cL2_f(F, w.phi, rho, w.p, s.J2);
-  if (!(cL2 > 0.f) || !(rho > 0.f)) flag_bad(A.status, patch, i + pd.nx * j);
-  const float cL = sqrtf(fmaxf(cL2, 0.f));
-  float r = (fabsf(w.u) + cL) / (float)pd.dx;
-  if (DIM == 2) r += (fabsf(w.v) + cL) / (float)pd.dy;
-  return r;
-}
-
-template <int DIM, bool RX>
-__global__ void __launch_bounds__(SEG) k_cfl32(Phys P, PhysF F, StepArgs32 A, const int4* __restrict__ segs) {
+__global__ void __launch_bounds__(SEG) k_cfl32(Phys P, PhysF F, StepArgs32 A, unsigned long long* rate,
+                                               const int4* __restrict__ segs) {
   const int4 g = segs[blockIdx.x];
   const PatchDev pd = A.pd[g.x];
   const int i = g.z + threadIdx.x, j = g.y;
   float r = 0.f;
-  if (threadIdx.x < g.w) r = cfl_rate32<DIM, RX>(P, F, A, pd, g.x, i, j);
+  if (threadIdx.x < g.w)
+    r = cfl_rate_of<DIM>(F, cons_to_prim32<DIM, RX>(P, F, A.src, A.T, cidx(pd, i, j)), 1.f / (float)pd.dx,
+                         1.f / (float)pd.dy, A.status, g.x, i + pd.nx * j);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
   if ((threadIdx.x & 31) == 0 && r > 0.f)
-    atomicMax(A.rate + g.x, (unsigned long long)__double_as_longlong((double)r));
+    atomicMax(rate + g.x, (unsigned long long)__double_as_longlong((double)r));
 }
-
-// State buffers of the persistent batch kernel: q^n (0) and two stage buffers.
-struct Bufs32 {
-  double* q64[3];
-  float* q32[3];
-};
 
 // Persistent 1D batch kernel: CTA b owns problem order[b] (the problems sorted
 // by length, longest first, so the block scheduler balances them) and runs
-// n_steps whole time steps of it in one launch: per step the CFL rate of its
-// cells (a CTA max, stored as the patch's rate; skipped for prescribed dt),
-// then the three stages, each over the problem's tiles tiles[tile0[p] ..
-// tile0[p + 1]) in turn, with the buffer rotation of the per-step path
-// (0 -> 1 -> 2 -> 0).  A problem's three state buffers stay in L2 between
-// stages and steps.  The tile arithmetic is stage32_tile and the rate that of
-// k_cfl32; compiled as another kernel, its multiply-add contractions may
-// differ, so the result matches the per-step launches to rounding.
+// n_steps whole time steps of it in one launch: the three stages, each over
+// the problem's tiles tiles[tile0[p] .. tile0[p + 1]) in turn, with the
+// buffer rotation of the per-step path (0 -> 1 -> 2 -> 0).  The CFL rate of
+// q^n is rate[p] (computed here first when rate_ready is 0); the last stage
+// of every step leaves the rate of the new state in shared memory for the
+// next one, and the final rate goes back to rate[p].  A problem's three state
+// buffers stay in L2 between stages and steps.  The tile arithmetic is
+// stage32_tile's; compiled as another kernel, its multiply-add contractions
+// may differ, so the result matches the per-step launches to rounding.
 // scratch_last (tuning, n_steps = 1): the last stage writes buffer 1.
+struct Bufs32 {
+  float* q[3];
+};
+
 template <bool RX, int TX, int NT, int MINB, bool CYL = false>
 __global__ void __launch_bounds__(NT, MINB) k_batch32(Phys P, PhysF F, StepArgs32 A, Bufs32 B,
-                                                      const int* __restrict__ order,
+                                                      unsigned long long* rate, const int* __restrict__ order,
                                                       const int* __restrict__ tile0,
                                                       const int4* __restrict__ tiles, int n_steps,
-                                                      int scratch_last) {
+                                                      int scratch_last, int rate_ready) {
   extern __shared__ __align__(16) float sm[];
   __shared__ float wmax[NT / 32];
+  __shared__ unsigned rnext;
   const int p = order[blockIdx.x];
   const int ta = tile0[p], tb = tile0[p + 1];
   const PatchDev pd = A.pd[p];
-  for (int n = 0; n < n_steps; ++n) {
-    if (!A.dtfix) {
-      StepArgs32 a = A;
-      a.q64src = B.q64[0];
-      a.q32src = B.q32[0];
-      float r = 0.f;
-      for (int i = threadIdx.x; i < pd.nx; i += NT) r = fmaxf(r, cfl_rate32<1, RX>(P, F, a, pd, p, i, 0));
+  if (!rate_ready) {
+    float r = 0.f;
+    for (int i = threadIdx.x; i < pd.nx; i += NT)
+      r = fmaxf(r, cfl_rate_of<1>(F, cons_to_prim32<1, RX>(P, F, B.q[0], A.T, cidx(pd, i, 0)), 1.f / (float)pd.dx,
+                                  1.f, A.status, p, i));
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
-      if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = r;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        float m = 0.f;
+    for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float m = 0.f;
 #pragma unroll
-        for (int w = 0; w < NT / 32; ++w) m = fmaxf(m, wmax[w]);
-        A.rate[p] = (unsigned long long)__double_as_longlong((double)m);
-      }
-      __syncthreads();
+      for (int w = 0; w < NT / 32; ++w) m = fmaxf(m, wmax[w]);
+      rate[p] = (unsigned long long)__double_as_longlong((double)m);
     }
+    __syncthreads();
+  }
+  for (int n = 0; n < n_steps; ++n) {
+    if (threadIdx.x == 0) rnext = 0u;  // ordered before the last stage's atomics by the tile barriers
     for (int stg = 0; stg < 3; ++stg) {
       StepArgs32 a = A;
       const bool s0 = stg == 0, s1 = stg == 1, to1 = s0 || (!s1 && scratch_last);
-      a.q64src = s0 ? B.q64[0] : (s1 ? B.q64[1] : B.q64[2]);
-      a.q32src = s0 ? B.q32[0] : (s1 ? B.q32[1] : B.q32[2]);
-      a.q64n = B.q64[0];
-      a.q32n = B.q32[0];
-      a.q64dst = to1 ? B.q64[1] : (s1 ? B.q64[2] : B.q64[0]);
-      a.q32dst = to1 ? B.q32[1] : (s1 ? B.q32[2] : B.q32[0]);
+      a.src = B.q[stg];
+      a.qn = B.q[0];
+      a.dst = to1 ? B.q[1] : (s1 ? B.q[2] : B.q[0]);
+      a.rate = rate;
       a.a = s0 ? 0.0 : (s1 ? 0.75 : 1.0 / 3.0);
       a.b = s0 ? 1.0 : (s1 ? 0.25 : 2.0 / 3.0);
       a.last = stg == 2;
       for (int t = ta; t < tb; ++t) {
-        stage32_tile<1, RX, TX, 1, NT, false, CYL>(P, F, a, tiles[t], sm);
+        stage32_tile<1, RX, TX, 1, NT, CYL>(P, F, a, tiles[t], sm, &rnext);
         __syncthreads();
       }
     }
+    // the next step's rate (thread 0 also reads it, for dt, in the next tile)
+    if (threadIdx.x == 0 && !scratch_last)
+      rate[p] = (unsigned long long)__double_as_longlong((double)__uint_as_float(rnext));
   }
 }
 

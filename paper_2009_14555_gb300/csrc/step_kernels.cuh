@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(SEG) k_update(Phys P, StepArgs A, const int4* 
 template <int DIM, bool RX>
 __global__ void __launch_bounds__(SEG) k_unpack(Phys P, const PatchDev* __restrict__ pds,
                                                 const int4* __restrict__ segs, const double* src,
-                                                double* q, long long T, int primitive) {
+                                                double* q, long long T, int primitive, long long base = 0) {
   using L = Lay<DIM, RX>;
   constexpr int NF = L::NF;
   const int4 g = segs[blockIdx.x];
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(SEG) k_unpack(Phys P, const PatchDev* __restri
   const PatchDev pd = pds[g.x];
   const int i = g.z + threadIdx.x, j = g.y;
   const long long ncell = (long long)pd.nx * pd.ny;
-  const long long s0 = pd.poff + (long long)j * pd.nx + i;
+  const long long s0 = pd.poff - base + (long long)j * pd.nx + i;
   const long long k = cidx(pd, i, j);
   double v[NF];
 #pragma unroll
@@ -376,14 +376,14 @@ __global__ void __launch_bounds__(SEG) k_unpack(Phys P, const PatchDev* __restri
 template <int DIM, bool RX>
 __global__ void __launch_bounds__(SEG) k_pack(const PatchDev* __restrict__ pds,
                                               const int4* __restrict__ segs, const double* q,
-                                              double* dst, long long T) {
+                                              double* dst, long long T, long long base = 0) {
   constexpr int NF = Lay<DIM, RX>::NF;
   const int4 g = segs[blockIdx.x];
   if (threadIdx.x >= g.w) return;
   const PatchDev pd = pds[g.x];
   const int i = g.z + threadIdx.x, j = g.y;
   const long long ncell = (long long)pd.nx * pd.ny;
-  const long long s0 = pd.poff + (long long)j * pd.nx + i;
+  const long long s0 = pd.poff - base + (long long)j * pd.nx + i;
   const long long k = cidx(pd, i, j);
 #pragma unroll
   for (int c = 0; c < NF; ++c) dst[s0 + c * ncell] = q[c * T + k];

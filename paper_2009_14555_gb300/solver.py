@@ -25,6 +25,17 @@ def _patch(p, dim) -> L.DisPatch:
                       float(getattr(p, "x0", 0.0)))
 
 
+def alu_peaks(stream=None):
+    """Measured float32 and float64 FMA throughput of the current device in
+    TFLOP/s, and the two probe launch times in ms (include/dis.h:
+    dis_alu_peaks)."""
+    f32, f64 = ctypes.c_double(), ctypes.c_double()
+    ms = np.zeros(2)
+    L.check(L.load().dis_alu_peaks(None if stream is None else ctypes.c_void_p(stream), ctypes.byref(f32),
+                                   ctypes.byref(f64), ms.ctypes.data))
+    return f32.value, f64.value, ms
+
+
 def pack(arrays) -> np.ndarray:
     """Concatenate per-patch (nfields, ny, nx) arrays into the packed layout."""
     return np.ascontiguousarray(np.concatenate([np.asarray(a, np.float64).reshape(-1) for a in arrays]))
@@ -107,6 +118,36 @@ class Solver:
 
     def sync(self):
         L.dis_sync(self.ctx)
+
+    def set_patch(self, patch, arr, kind=L.DIS_PRIMITIVE):
+        """State of one patch ([nfields, ny, nx] float64, host array or CUDA
+        tensor) (include/dis.h: dis_set_patch_state)."""
+        lib = L.load()
+        if isinstance(arr, torch.Tensor) and arr.is_cuda:
+            t = arr.contiguous().to(torch.float64)
+            L.check(lib.dis_set_patch_state(self.ctx, patch, kind, ctypes.c_void_p(t.data_ptr()), 1))
+            torch.cuda.synchronize()
+        else:
+            a = np.ascontiguousarray(np.asarray(arr, np.float64))
+            L.check(lib.dis_set_patch_state(self.ctx, patch, kind, ctypes.c_void_p(a.ctypes.data), 0))
+
+    def get_patch(self, patch, shape, kind=L.DIS_CONSERVATIVE):
+        """State of one patch as a host array of `shape` ([nfields, ny, nx])
+        (include/dis.h: dis_get_patch_state)."""
+        h = np.empty(shape, np.float64)
+        L.check(L.load().dis_get_patch_state(self.ctx, patch, kind, ctypes.c_void_p(h.ctypes.data), 0))
+        return h
+
+    def query(self):
+        """Device-reduced totals, phi range, dt, step time and bytes
+        (include/dis.h: dis_query) as a dict."""
+        st = L.DisStats()
+        L.check(L.load().dis_query(self.ctx, ctypes.byref(st)))
+        return {"mass": list(st.mass), "momentum": list(st.momentum), "energy": st.energy,
+                "reactant": st.reactant, "phi_min": st.phi_min, "phi_max": st.phi_max,
+                "dt_min": st.dt_min, "dt_max": st.dt_max, "kernel_ms": st.kernel_ms, "bytes": st.bytes,
+                "steps": st.steps, "launches": st.launches, "status": st.status,
+                "bad_patch": st.bad_patch, "bad_cell": st.bad_cell}
 
     def set_prim(self, prim_arrays):
         self.set_state(pack(prim_arrays), L.DIS_PRIMITIVE)

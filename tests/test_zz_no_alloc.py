@@ -6,9 +6,11 @@ device memory was reserved).  `dis_cfl_dt_static` serves them from a fixed
 scratch area inside the library.  This file is collected last so that a run
 stopping at its first failure has already run every other test.
 
-Check: through the C ABI, two calls in a row (a stiff 2D state, then a 1D batch
-with slower waves, so a stale maximum from the first call would show) give
-the same per-patch time steps as the context's own step reports.
+Check: through the C ABI, calls in a row (a stiff 2D state, then a 1D batch
+with slower waves, so a stale maximum from the first call would show, then a
+reactive 1D state, whose layout has the extra reaction field) give the same
+per-patch time steps as the context's own step reports; a patch holding a
+cell without a real sound speed gets NaN and the others keep theirs.
 """
 import ctypes
 
@@ -61,6 +63,28 @@ def test_static_dt_matches_step_twice_in_a_row():
     np.testing.assert_allclose(got_a, ref_a, rtol=TOL)
     np.testing.assert_allclose(got_b, ref_b, rtol=TOL)
     assert got_b.max() > got_a.max()  # a stale larger maximum would have shrunk these
+    # reactive layout (9 fields in 1D, the reaction field last)
+    wl_c = W.detonation_copper_1d(200, steps=1)
+    cons_c, ref_c = reference(wl_c)
+    np.testing.assert_allclose(static_dt(wl_c, cons_c), ref_c, rtol=TOL)
+
+
+def test_static_dt_is_nan_for_a_nonphysical_patch():
+    wl = W.batched_riemann_1d(6, seed=7, steps=1, nmin=32, nmax=64)
+    for k, m in enumerate(wl.materials):                       # two ideal gases
+        wl.materials[k] = dict(m, p_inf=0.0, G=0.0)
+    cons, ref = reference(wl)
+    host = cons.cpu().numpy()
+    # negative total energy in one cell of patch 3: negative pressure, c^2 < 0
+    off = sum(8 * p.nx for p in wl.patches[:3])
+    nx3 = wl.patches[3].nx
+    host[off + 4 * nx3 + 5] = -1.0                              # field rho E, cell 5
+    got = static_dt(wl, torch.from_numpy(host).cuda())
+    assert np.isnan(got[3])
+    keep = [k for k in range(6) if k != 3]
+    np.testing.assert_allclose(got[keep], ref[keep], rtol=TOL)
+    # the flag is cleared on the next call
+    np.testing.assert_allclose(static_dt(wl, cons), ref, rtol=TOL)
 
 
 def test_static_rejects_too_many_patches():
