@@ -26,31 +26,19 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-updates/s and % HBM peak, FP32-bulk vs plain FP64 on one GB300 at stated L1"
 
-# Dominant kernel of the float64 step: the x-face flux kernel (40 % of the
-# step in the ncu launch list).  Its arithmetic per face, counted by ncu on the
-# 1024x512 reactive plate (2 x DFMA + DADD + DMUL per face; see
-# profiles/k_flux_2d_reactive_plate_1024x512.md):
+# Arithmetic of the dominant kernels, counted by ncu on the 1024 x 512
+# reactive plate (executed FADD + FMUL + 2 FFMA, resp. DADD + DMUL + 2 DFMA,
+# thread level): the FP32-bulk stage kernel per cell-stage for each tile shape
+# (TX, TY) (the register budget does not change the arithmetic), and the
+# float64 x-face flux kernel per face.
+STAGE32_FLOP = {(16, 15): None, (32, 15): None, (32, 7): None}
 FLUX_FP64_FLOP_PER_FACE = 868.1
-# DRAM bytes per x-flux launch from the same capture (73.07 MB for 524800
-# faces), per face; traffic grows with the face count.
+# DRAM bytes (read + write) per cell-stage of the stage kernel on the full
+# 2048 x 1024 grid (ncu, one launch), per tile shape; None where not captured.
+STAGE32_DRAM = {(16, 15): None, (32, 15): None, (32, 7): None}
+# DRAM bytes per x-flux launch of the float64 step, per face (73.07 MB for
+# 524800 faces on 1024 x 512); traffic grows with the face count.
 FLUX_DRAM_BYTES_PER_FACE = 73.07e6 / 524800
-# FP64 peak: 152 SMs x 2 DFMA/cycle (ncu sm__sass_thread_inst_executed_op_dfma
-# peak_sustained = 304/cycle) x 2 FLOP x 2.07 GHz maximum SM clock.
-FP64_PEAK_TFLOPS = 304 * 2 * 2.07e9 / 1e12
-# FP32: 152 SMs x 128 FMA lanes x 2 FLOP x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# FP32-bulk stage kernel k_stage32, per tuned variant (TX, TY, primitives
-# precomputed by k_prim32), counted by ncu over the three stages of one step
-# (profiles/k_stage32_2d_reactive_plate.md): executed FP32 FLOP (FADD + FMUL +
-# 2 FFMA) and FP64 FLOP per cell-stage on the 1024 x 512 reactive plate (halo
-# recovery included where the kernel recovers), and DRAM bytes (read + write)
-# per cell-stage on the full 2048 x 1024 grid.  The register budget (3 or 4
-# CTAs per SM) does not change these counts.
-STAGE32 = {
-    (16, 15, False): dict(flop32=1422.8, flop64=27.97, dram=133.6),
-    (16, 15, True): dict(flop32=1258.0, flop64=17.18, dram=184.7),
-    (32, 7, True): dict(flop32=1279.1, flop64=17.18, dram=184.4),
-}
 UNIT = "cell-updates/s"
 NX, NY = 2048, 1024
 
@@ -62,6 +50,14 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def state_bytes(dim, reactive, precision):
+    """Bytes of one cell's stored state: float64, nfields x 8; FP32-bulk,
+    (nfields + 1) x 4 (float32 fields, the soft energy, phi1 as a
+    float-float pair)."""
+    nf = (11 if dim == 2 else 8) + (1 if reactive else 0)
+    return 8 * nf if precision == "fp64" else 4 * (nf + 1)
 
 
 def workload(nx=None, ny=None):
@@ -235,19 +231,26 @@ def run_gpu(args):
     value = job_throughput(cells, world, r["ms_per_step"])
     value64 = job_throughput(cells, world, r64["ms_per_step"])
     hbm, kind = peaks()
+    from paper_2009_14555_gb300.solver import alu_peaks
+    f32_peak, f64_peak, _ = alu_peaks(torch.cuda.current_stream().cuda_stream)
     nxw, nyw = args.nx or NX, args.ny or NY
     faces_x = (nxw + 1) * nyw
-    # algorithmic bytes per cell-update: read + write the state once
-    alg32 = 2 * (2 * 8 + 10 * 4)   # phi1, rho E float64 + 10 float32 fields
-    alg64 = 2 * 12 * 8
+    # algorithmic bytes per cell-update: read + write the stored state once
+    alg32 = 2 * state_bytes(2, True, "fp32_bulk")
+    alg64 = 2 * state_bytes(2, True, "fp64")
     hbm32 = alg32 * cells / (r["ms_per_step"] * 1e-3) / 1e9
     hbm64 = alg64 * cells / (r64["ms_per_step"] * 1e-3) / 1e9
     t64 = r64["kernel_ms"][1] * 1e-3
     flux64_tflops = FLUX_FP64_FLOP_PER_FACE * faces_x / t64 / 1e12
-    t32 = r["kernel_ms"][1] * 1e-3  # one stage-kernel launch (live event timing)
-    tx, ty, pre = r["tile"][0], r["tile"][1], bool(r["tile"][2])
-    cnt = STAGE32.get((tx, ty, pre))
-    flux32_tflops = cnt["flop32"] * cells / t32 / 1e12 if cnt else None
+    # dominant kernel: the FP32-bulk stage kernel, one launch per RK stage (a
+    # third of a cell-update for every cell), live event time per launch
+    t32 = r["kernel_ms"][1] * 1e-3
+    tx, ty = r["tile"][0], r["tile"][1]
+    launch_bytes = alg32 / 3.0 * cells
+    stage_gbs = launch_bytes / t32 / 1e9
+    flop = STAGE32_FLOP.get((tx, ty))
+    dram = STAGE32_DRAM.get((tx, ty))
+    stage_tflops = flop * cells / t32 / 1e12 if flop else None
     # per-field L1 of the FP32-bulk state against the float64 GPU state after the
     # same number of steps (the float64 GPU path matches the oracle to 1e-10)
     a32, a64 = r["final"].reshape(12, -1), r64["final"].reshape(12, -1)
@@ -260,35 +263,39 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (phi1, rho E, pressure recovery in f64)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (phi1 as a float-float pair)",
         "data": "synthetic",
         "config": {"workload": f"2d_reactive_plate_{nxw}x{nyw}", "cells": cells,
-                   "precision": "fp32_bulk",
-                   "l2": "working set larger than L2 (state + primitives + faces > 129 MB)",
+                   "precision": "fp32_bulk", "scheme": "ssp_rk3",
+                   "l2": "working set larger than L2 (3 state buffers of 109 MB)",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"bound": "alu",
-                     "kernel": f"k_stage32<{tx}x{ty}{', precomputed primitives' if pre else ''}> (FP32-bulk stage)",
-                     "achieved": flux32_tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": flux32_tflops / FP32_PEAK_TFLOPS if flux32_tflops else None,
-                     "traffic": cnt["dram"] * cells if cnt else None,
-                     "fp64_flop_per_cell": cnt["flop64"] if cnt else None,
-                     "note": "executed FP32 FLOP per cell-stage (ncu) x cells / live event time per launch; "
-                             "peak = 152 SMs x 128 FFMA lanes x 2 x 2.07 GHz (nominal clock, no measured "
-                             "FP32 peak exists); traffic = ncu DRAM bytes of one launch"},
+        "roofline": {"bound": "hbm",
+                     "kernel": f"k_stage32<{tx}x{ty}> (FP32-bulk Runge-Kutta stage)",
+                     "achieved": stage_gbs, "peak": hbm, "unit": "GB/s", "frac": stage_gbs / hbm,
+                     "traffic": dram * cells if dram else None,
+                     "algorithmic_bytes_per_launch": launch_bytes,
+                     "note": f"algorithmic bytes = {alg32} B per cell-update (state read + written once) / 3 "
+                             f"stage launches x {cells} cells, over the live CUDA-event time of one stage launch; "
+                             f"peak = {kind} copy bandwidth; traffic = ncu DRAM bytes of one launch"},
+        "alu": {"kernel": f"k_stage32<{tx}x{ty}>", "achieved": stage_tflops, "peak": f32_peak, "unit": "TFLOP/s",
+                "frac": stage_tflops / f32_peak if stage_tflops else None,
+                "flop_per_cell_stage": flop,
+                "note": "executed FP32 FLOP per cell-stage (ncu) x cells / live event time per launch; "
+                        "peak = measured FMA-loop throughput of this GPU (dis_alu_peaks)"},
+        "measured_peaks": {"fp32_tflops": f32_peak, "fp64_tflops": f64_peak, "hbm_gbs": hbm},
         "l1_vs_fp64": l1,
         "hbm": {"achieved_gbs": hbm32, "peak_gbs": hbm, "frac": hbm32 / hbm,
                 "algorithmic_bytes_per_cell_update": alg32, "peak_kind": kind},
-        "kernels_ms_per_launch": {("prim_pass" if r["tile"][2] else "cfl_pass"): float(r["kernel_ms"][0]),
+        "kernels_ms_per_launch": {"cfl_pass_first_step_only": float(r["kernel_ms"][0]),
                                   "stage": float(r["kernel_ms"][1])},
-        "tile": {"tx": r["tile"][0], "ty": r["tile"][1], "precomputed_primitives": r["tile"][2],
-                 "tuned_ms_per_step": [round(float(x), 4) for x in r["tile"][3]]},
+        "tile": {"tx": tx, "ty": ty, "tuned_ms_per_step": [round(float(x), 4) for x in r["tile"][3]]},
         "fp64": {"value": value64, "ms_per_step": r64["ms_per_step"],
                  "speedup_fp32_bulk": value / value64,
                  "hbm": {"achieved_gbs": hbm64, "frac": hbm64 / hbm, "algorithmic_bytes_per_cell_update": alg64},
                  "roofline": {"bound": "alu", "kernel": "k_flux x (float64)", "achieved": flux64_tflops,
-                              "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                              "frac": flux64_tflops / FP64_PEAK_TFLOPS,
-                              "traffic": FLUX_DRAM_BYTES_PER_FACE * faces_x},
+                              "peak": f64_peak, "unit": "TFLOP/s", "frac": flux64_tflops / f64_peak,
+                              "traffic": FLUX_DRAM_BYTES_PER_FACE * faces_x,
+                              "note": "peak = measured float64 FMA-loop throughput (dis_alu_peaks)"},
                  "kernels_ms_per_launch": dict(zip(["prim", "flux_x", "flux_y", "update"],
                                                    map(float, r64["kernel_ms"]))),
                  "clocks": r64["clocks"]},
@@ -300,6 +307,8 @@ def run_gpu(args):
     }
     line["fp64"]["hancock"] = hancock_bench(wl, prim, args.steps, args.warmup)
     line["fp64"]["hancock"]["speedup_vs_rk3"] = line["fp64"]["hancock"]["value"] / value64
+    if not args.no_configs:
+        line["configs"] = configs_bench(args.warmup)
     if not args.no_batch:
         line["batch_1d"] = batch_bench()
     if not args.no_widened:
@@ -371,6 +380,31 @@ def _timed_steps(wl, prim, precision, steps, warmup, **kw):
     rc = s.check()[0]
     s.close()
     return {"value": wl.cells / (ms * 1e-3), "ms_per_step": ms, "steps": steps, "status_ok": rc == 0}
+
+
+def configs_bench(warmup=3):
+    """The two smaller configurations at their full length: the 1D solid|gas
+    problem (1000 cells, 500 steps; launch-latency bound) and the 512^2
+    shock-disc with THINC (2000 steps; its 3 FP32-bulk states fit in L2).
+    cell-updates/s over the whole run, both precisions (device events,
+    inputs resident), and the algorithmic-byte HBM fraction."""
+    from paper_2009_14555_gb300 import workloads as W
+    from paper_2009_14555_gb300.solver import pack
+    hbm, _ = peaks()
+    out = {}
+    for key, wl in (("1d_solid_gas_1000_500", W.solid_gas_1d(1000, steps=500)),
+                    ("2d_shock_disc_512_2000", W.shock_disc_2d(512, steps=2000))):
+        prim = pack([p.prim for p in wl.patches])
+        row = {"cells": wl.cells, "steps": wl.steps}
+        for prec in ("fp32_bulk", "fp64"):
+            r = _timed_steps(wl, prim, prec, wl.steps, warmup)
+            b = 2 * state_bytes(wl.dim, wl.reactive, prec)
+            r["hbm_frac"] = b * r["value"] / 1e9 / hbm
+            r["algorithmic_bytes_per_cell_update"] = b
+            row[prec] = r
+        row["speedup_fp32_bulk"] = row["fp32_bulk"]["value"] / row["fp64"]["value"]
+        out[key] = row
+    return out
 
 
 def widened_bench(warmup=3):
@@ -454,9 +488,12 @@ def batch_bench(steps=300, warmup=3):
         rc, bp, bc = s.check()
         # problems whose state left the finite range (each problem is independent)
         bad = sum(int(not np.isfinite(a).all()) for a in s.get_arrays())
+        b = 2 * state_bytes(1, False, prec)
         out[prec] = {"value": wl.cells / (ms * 1e-3), "ms_per_step": ms, "steps": steps,
                      "launches": s.launches, "nonfinite_problems": bad,
-                     "first_flagged": [int(bp), int(bc)] if rc else None}
+                     "first_flagged": [int(bp), int(bc)] if rc else None,
+                     "algorithmic_bytes_per_cell_update": b,
+                     "hbm_frac": b * wl.cells / (ms * 1e-3) / 1e9 / peaks()[0]}
         if prec == "fp32_bulk":
             t = s.tile_choice()
             sc, bms = s.schedule()
@@ -525,6 +562,8 @@ def main():
     ap.add_argument("--impl", default="native")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched 1D measurement")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 1D solid|gas and 512^2 shock-disc measurements")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint-case measurement")
     ap.add_argument("--no-widened", action="store_true",
                     help="skip the cylindrical-geometry and k sqrt(lam) measurements")

@@ -111,16 +111,24 @@ enum { DIS_RK3 = 0, DIS_HANCOCK = 1 };
  * Runge-Kutta contexts only (float64 and FP32-bulk). */
 enum { DIS_PLANAR = 0, DIS_CYLINDRICAL = 1 };
 
+/* Slope limiter of the MUSCL reconstruction of the primitives (Section 3.1
+ * names none): DIS_MINMOD (default), DIS_VANLEER (2 a b / (a + b) of the two
+ * one-sided differences a, b when a b > 0, else 0).  The same limiter forms
+ * the MUSCL candidate of the MUSCL-BVD-THINC reconstruction of phi1. */
+enum { DIS_MINMOD = 0, DIS_VANLEER = 1 };
+
 /* Step options: CFL number (Section 3: fraction of the largest stable step),
  * THINC interface steepening on/off (Appendix A), precision mode, hyperbolic
  * scheme (DIS_RK3 or DIS_HANCOCK; 0 = the paper's), geometry (DIS_PLANAR or
- * DIS_CYLINDRICAL). */
+ * DIS_CYLINDRICAL), slope limiter (DIS_MINMOD or DIS_VANLEER; zero-filled =
+ * minmod). */
 typedef struct {
   double cfl;
   int32_t thinc;
   int32_t precision;
   int32_t scheme;
   int32_t geometry;
+  int32_t limiter;
 } dis_options;
 
 typedef struct dis_ctx dis_ctx;
@@ -219,20 +227,23 @@ long long dis_last_launches(const dis_ctx* ctx);
 /* FP32-bulk contexts run one kernel per Runge-Kutta stage over tiles of
  * TX x TY cells (primitives of the tile and its halo, faces, update; the last
  * stage also takes the CFL rate of the new state for the next step).  There
- * are DIS_NVARIANTS variants v: tile shape v % 3 (2D 16 x 15, 20 x 12,
- * 32 x 7 cells per CTA of 256 threads; 1D 122, 250, 506 cells per CTA of
- * 128, 256, 512 threads) and register budget v / 3 (2D: 3 or 4 resident CTAs
- * per SM; 1D: no limit, or at most 64 registers per thread).  The first
+ * are DIS_NVARIANTS variants v: tile shape v % 3 (2D 16 x 15, 32 x 15, 32 x 7
+ * cells per CTA of 256, 512, 256 threads; 1D 122, 250, 506 cells per CTA of
+ * 128, 256, 512 threads) and register budget v / 3 (2D: 768 or 1024 resident
+ * threads per SM; 1D: no limit, or at most 64 registers per thread); in
+ * planar 2D, variants 6 .. 11 are the same shapes and budgets in a
+ * persistent form (as many CTAs as fit at once, each looping over tiles, the
+ * update of one tile overlapping the halo recovery of the next).  The first
  * dis_step times one step of every variant (the last stage writing a scratch
  * buffer, so the state is unchanged) and keeps the fastest.  Returns the
  * chosen shape (0 x 0 before tuning or for float64 contexts), precomputed = 0
  * (kept for compatibility), and, if step_ms is not NULL, the tuned time per
  * step of each variant. */
-#define DIS_NVARIANTS 6
+#define DIS_NVARIANTS 12
 int dis_tile_choice(const dis_ctx* ctx, int* tx, int* ty, int* precomputed, double* step_ms);
 
-/* Fix the FP32-bulk stage variant (0 .. DIS_NVARIANTS - 1) or return to
- * tuning on the next step (-1).  For tests and measurements; the
+/* Fix the FP32-bulk stage variant (0 .. DIS_NVARIANTS - 1 in planar 2D,
+ * 0 .. 5 otherwise) or return to tuning on the next step (-1).  For tests and measurements; the
  * result of a step does not depend on the variant beyond float32 rounding
  * order.  DIS_EINVAL for float64 contexts or an out-of-range variant. */
 int dis_set_variant(dis_ctx* ctx, int variant);
@@ -314,9 +325,10 @@ int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
  * float64 (plus float64 primitive and face buffers for the reverse sweep).
  * In a DIS_CYLINDRICAL context the geometric source of Section 3 is reversed
  * with the rest of the stage, and J is the same plain sum over cells (no
- * factor r).  Returns DIS_EINVAL (bad arguments, or a DIS_HANCOCK context:
- * the adjoint covers the Runge-Kutta scheme), DIS_ESTATE (no state),
- * DIS_ENOMEM, DIS_ECUDA.  Synchronises. */
+ * factor r).  Returns DIS_EINVAL (bad arguments, a DIS_HANCOCK context: the
+ * adjoint covers the Runge-Kutta scheme, or a DIS_VANLEER context: it covers
+ * the minmod limiter), DIS_ESTATE (no state), DIS_ENOMEM, DIS_ECUDA.
+ * Synchronises. */
 int dis_adj_forward(dis_ctx* ctx, int n_steps, int checkpoint_every, int objective_material,
                     const double* dt_in, double* dt_out, double* J_out);
 

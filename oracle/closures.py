@@ -71,21 +71,81 @@ def hencky_dev(V):
 
 # ----------------------------------------------------------------------------
 # Reference curves of the Mie-Grueneisen form (Section 2.3, reading above).
+#
+# Three families (m["eos"]), all with a constant Gamma = gamma - 1:
+#   "sg"  stiffened gas (the default): cold pressure -gamma p_inf, cold energy
+#         e_inf, constant shear modulus G;
+#   "romenskii" (Section 2.3, elastic solids): cold energy
+#         K0 / (2 rho0 a^2) ((rho/rho0)^a - 1)^2 and its pressure
+#         rho^2 dE_c/drho = (K0 / a) x^(a+1) (x^a - 1), x = rho / rho0, and the
+#         shear modulus G(rho) = G0 x^(b+1) (a, b: the exponents alpha-bar,
+#         beta-bar; G0 = m["G"]).  Reading: the printed cold energy lacks the
+#         square and has rho for rho0, which would give a reference pressure
+#         K0 / (2 a) at rho0; this form has zero pressure and bulk modulus K0
+#         there;
+#   "jwl" (Section 2.3, explosives and products): cold pressure
+#         A e^(-R1 rho0/rho) + B e^(-R2 rho0/rho) and cold energy
+#         A / (R1 rho0) e^(-R1 rho0/rho) + B / (R2 rho0) e^(-R2 rho0/rho).
+# The shear energy G(rho) J2 / rho adds (rho G' - G) J2 to the reference
+# pressure (rho^2 times its density derivative).
 # ----------------------------------------------------------------------------
+def eos_kind(m):
+    return m.get("eos", "sg")
+
+
+def shear_modulus(m, rho):
+    """G(rho) of Section 2.3 (constant except for the Romenskii solid)."""
+    if eos_kind(m) == "romenskii":
+        return m["G"] * (rho / m["rho0"]) ** (m["beta_r"] + 1.0)
+    return torch.full_like(rho, m["G"]) if torch.is_tensor(rho) else m["G"]
+
+
+def _shear_p_factor(m, rho):
+    """rho G'(rho) - G(rho) and its density derivative."""
+    if eos_kind(m) == "romenskii":
+        b = m["beta_r"]
+        G = shear_modulus(m, rho)
+        return b * G, b * (b + 1.0) * G / rho
+    return -m["G"] + 0.0 * rho, 0.0 * rho
+
+
+def cold_curves(m, rho):
+    """(E_c, p_c, dE_c/drho, dp_c/drho) of the cold (J2 = 0) reference curves."""
+    kind = eos_kind(m)
+    if kind == "romenskii":
+        a, K0, r0 = m["alpha_r"], m["K0"], m["rho0"]
+        x = rho / r0
+        xa = x ** a
+        Ec = K0 / (2.0 * r0 * a * a) * (xa - 1.0) ** 2
+        pc = K0 / a * x ** (a + 1.0) * (xa - 1.0)
+        dpc = K0 / (a * r0) * xa * ((2.0 * a + 1.0) * xa - (a + 1.0))
+        return Ec, pc, pc / (rho * rho), dpc
+    if kind == "jwl":
+        r0 = m["rho0"]
+        e1 = m["jwl_A"] * torch.exp(-m["jwl_R1"] * r0 / rho)
+        e2 = m["jwl_B"] * torch.exp(-m["jwl_R2"] * r0 / rho)
+        Ec = e1 / (m["jwl_R1"] * r0) + e2 / (m["jwl_R2"] * r0)
+        pc = e1 + e2
+        dpc = (e1 * m["jwl_R1"] + e2 * m["jwl_R2"]) * r0 / (rho * rho)
+        return Ec, pc, pc / (rho * rho), dpc
+    z = 0.0 * rho
+    return m["e_inf"] + z, -m["gamma"] * m["p_inf"] + z, z, z
+
+
 def p_ref(m, rho, J2):
-    return -m["gamma"] * m["p_inf"] - m["G"] * J2
+    return cold_curves(m, rho)[1] + _shear_p_factor(m, rho)[0] * J2
 
 
 def e_ref(m, rho, J2):
-    return m["e_inf"] + m["G"] * J2 / rho
+    return cold_curves(m, rho)[0] + shear_modulus(m, rho) * J2 / rho
 
 
 def dp_ref_drho(m, rho, J2):
-    return torch.zeros_like(rho)
+    return cold_curves(m, rho)[3] + _shear_p_factor(m, rho)[1] * J2
 
 
 def de_ref_drho(m, rho, J2):
-    return -m["G"] * J2 / (rho * rho)
+    return cold_curves(m, rho)[2] + _shear_p_factor(m, rho)[0] * J2 / (rho * rho)
 
 
 def material_energy(m, rho, p, J2, lam=None):
@@ -167,7 +227,7 @@ def mixture_props(phis, rhos, p, J2, mats, lam):
     """Mixture G, c^2 and longitudinal c_L^2 (Section 2.2 mixture rules)."""
     rho = sum(ph * r for ph, r in zip(phis, rhos))
     xi = sum(ph / Gamma(m) for ph, m in zip(phis, mats))
-    Gm = sum(ph * m["G"] / Gamma(m) for ph, m in zip(phis, mats)) / xi
+    Gm = sum(ph * shear_modulus(m, r) / Gamma(m) for ph, r, m in zip(phis, rhos, mats)) / xi
     c2 = sum((ph * r / rho) * material_sound_speed2(m, r, p, J2, lam) / Gamma(m)
              for ph, r, m in zip(phis, rhos, mats)) / xi
     cL2 = c2 + (4.0 / 3.0) * Gm / rho

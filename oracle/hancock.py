@@ -42,12 +42,12 @@ from .riemann import face_state, hllc, physical_flux
 from .scheme import NG, _assemble, _components, _hyperbolic, fill_ghosts, operator_from_faces
 
 
-def _edge_components(comps, absn, thinc):
+def _edge_components(comps, absn, thinc, limiter="minmod"):
     """Left and right edge values along the last axis of every primitive
     component (NaN where a cell lacks the neighbours its values need)."""
     L, R = {}, {}
     for k, t in comps.items():
-        mL, mR = muscl_faces(t)
+        mL, mR = muscl_faces(t, limiter)
         if k == "phi1" and thinc:
             beta = thinc_beta(absn) if absn is not None else torch.full_like(t, thinc_beta(1.0))
             tL, tR, mixed = thinc_faces(t, beta)
@@ -73,7 +73,7 @@ def _own_faces(w, d, mats):
     return physical_flux(s, d), s["phi1"], s["u"], s["V"]
 
 
-def hancock_operator(q, grid, mats, thinc, dt):
+def hancock_operator(q, grid, mats, thinc, dt, limiter="minmod"):
     """D of the MUSCL-Hancock update (q* = q^n - dt D) for the interior cells."""
     ny, nx = q["phi1"].shape
     dim = grid["dim"]
@@ -89,10 +89,10 @@ def hancock_operator(q, grid, mats, thinc, dt):
     edges = []
     for d in dims:
         if d == 0:
-            L, R = _edge_components(comps, anx if (dim == 2 and thinc) else None, thinc)
+            L, R = _edge_components(comps, anx if (dim == 2 and thinc) else None, thinc, limiter)
         else:
             L, R = _edge_components({k: t.transpose(0, 1) for k, t in comps.items()},
-                                    any_.transpose(0, 1) if thinc else None, thinc)
+                                    any_.transpose(0, 1) if thinc else None, thinc, limiter)
             L = {k: t.transpose(0, 1) for k, t in L.items()}
             R = {k: t.transpose(0, 1) for k, t in R.items()}
         edges.append((_fallback(_assemble(L), wg, mats), _fallback(_assemble(R), wg, mats)))

@@ -10,7 +10,9 @@ Cites arXiv 2009.14555:
     of each candidate and the BVD choice, and the multi-dimensional
     steepness beta = beta0 |n_d| + 0.01 with a Youngs normal.
 
-Readings: the limiter is minmod (the paper names none); THINC acts on the
+Readings: the limiter is minmod (the paper names none), or van Leer's as an
+option (the harmonic mean 2 a b / (a + b) of same-sign one-sided
+differences, van Leer 1974; 0 otherwise); THINC acts on the
 volume fraction phi1 only; "q_max" in the edge formulas is the jump
 max(q_{i-1}, q_{i+1}) - q_min; the mixed-cell test is strict on both sides; BVD
 picks THINC only when its TBV is strictly smaller; in a non-mixed cell the
@@ -31,7 +33,14 @@ def minmod(a, b):
                        torch.zeros_like(a))
 
 
-def muscl_faces(w):
+def vanleer(a, b):
+    """van Leer's limited slope: 2 a b / (a + b) if a b > 0 else 0."""
+    ab = a * b
+    pos = ab > 0
+    return torch.where(pos, 2.0 * ab / torch.where(pos, a + b, torch.ones_like(a)), torch.zeros_like(a))
+
+
+def muscl_faces(w, limiter="minmod"):
     """Limited linear reconstruction along the last axis.
 
     Returns (wL, wR): the values at the left (x_{i-1/2}) and right (x_{i+1/2})
@@ -39,7 +48,8 @@ def muscl_faces(w):
     """
     wL = torch.full_like(w, float("nan"))
     wR = torch.full_like(w, float("nan"))
-    d = minmod(w[..., 1:-1] - w[..., :-2], w[..., 2:] - w[..., 1:-1])
+    lim = {"minmod": minmod, "vanleer": vanleer}[limiter]
+    d = lim(w[..., 1:-1] - w[..., :-2], w[..., 2:] - w[..., 1:-1])
     wL[..., 1:-1] = w[..., 1:-1] - 0.5 * d
     wR[..., 1:-1] = w[..., 1:-1] + 0.5 * d
     return wL, wR

@@ -34,7 +34,7 @@ import math
 import torch
 
 from .closures import (Gamma, cons_to_prim, hencky_dev, mixture_props, phases,
-                       prim_to_cons, stress, temperature)
+                       prim_to_cons, shear_modulus, stress, temperature)
 from .reconstruction import (bvd_select, muscl_faces, thinc_beta, thinc_faces,
                              youngs_abs_normal)
 from .riemann import hllc
@@ -194,7 +194,7 @@ def _hyperbolic(w, mats):
     return cL2 > 0
 
 
-def _sweep(wg, absn, d, n, mats, thinc):
+def _sweep(wg, absn, d, n, mats, thinc, limiter="minmod"):
     """Face fluxes along axis d for lines of cells (cells along the last axis).
 
     wg: primitive components on lines including NG ghosts on each end;
@@ -208,7 +208,7 @@ def _sweep(wg, absn, d, n, mats, thinc):
     """
     L, R, CL, CR = {}, {}, {}, {}
     for k, t in wg.items():
-        mL, mR = muscl_faces(t)
+        mL, mR = muscl_faces(t, limiter)
         if k == "phi1" and thinc:
             beta = thinc_beta(absn) if absn is not None else torch.full_like(t, thinc_beta(1.0))
             tL, tR, mixed = thinc_faces(t, beta)
@@ -290,11 +290,11 @@ def cell_radius(grid, nx):
     return grid.get("x0", 0.0) + (torch.arange(nx, dtype=F64) + 0.5) * grid["dx"]
 
 
-def spatial_operator(q, grid, mats, thinc):
+def spatial_operator(q, grid, mats, thinc, limiter="minmod"):
     """D(q) of Section 3.1 for all interior cells of one patch; in cylindrical
     geometry (grid["geometry"] == "cyl", x = r, y = z) minus the geometric
     source s_g."""
-    D = _planar_operator(q, grid, mats, thinc)
+    D = _planar_operator(q, grid, mats, thinc, limiter)
     if grid.get("geometry", "planar") == "cyl":
         r = cell_radius(grid, q["phi1"].shape[1])[None, :]
         t = geometric_source_terms(q, mats)
@@ -304,7 +304,7 @@ def spatial_operator(q, grid, mats, thinc):
     return D
 
 
-def _planar_operator(q, grid, mats, thinc):
+def _planar_operator(q, grid, mats, thinc, limiter="minmod"):
     ny, nx = q["phi1"].shape
     qg = fill_ghosts(q, grid)
     wg = cons_to_prim(qg, mats)
@@ -323,7 +323,7 @@ def _planar_operator(q, grid, mats, thinc):
             lines = {k: t[:, NG:NG + nx].transpose(0, 1) for k, t in comps.items()}
             absn = any_[:, NG:NG + nx].transpose(0, 1) if thinc else None
             n = ny
-        F, phi_f, u_f, V_f = _sweep(lines, absn, d, n, mats, thinc)
+        F, phi_f, u_f, V_f = _sweep(lines, absn, d, n, mats, thinc, limiter)
         if d == 1:  # back to (ny+1, nx) face layout
             F = {k: v.transpose(0, 1) for k, v in F.items()}
             phi_f, u_f, V_f = phi_f.transpose(0, 1), u_f.transpose(0, 1), V_f.transpose(0, 1)
@@ -374,18 +374,20 @@ def plastic_update(q, mats, dt, iters=64):
     Jst = _sqrt0(J2)
     num = torch.zeros_like(Jst)
     den = torch.zeros_like(Jst)
-    for m, ph in zip(mats, phis):
+    for m, ph, ar in zip(mats, phis, (q["ar1"], q["ar2"])):
+        # G(rho_l) of the material's own density (constant but for Romenskii)
+        Gl = shear_modulus(m, ar / ph)
         if m["G"] == 0.0:
             Jl = torch.zeros_like(Jst)  # fluid: no shear strain survives
         elif m["plastic"] == 1:
-            JY = torch.as_tensor(m["sigma_y"] / (math.sqrt(6.0) * m["G"]), dtype=F64)
+            JY = m["sigma_y"] / (math.sqrt(6.0) * Gl)
             Jl = torch.minimum(Jst, JY)
         elif m["plastic"] == 0:
             Jl = Jst
         else:
             def chi(J):
                 # rate-dependent plasticity: chi0 H[sqrt(3/2) |dev sigma| - sigma_Y], |dev sigma| = 2 G J
-                on = math.sqrt(1.5) * 2.0 * m["G"] * J - m["sigma_y"] > 0
+                on = math.sqrt(1.5) * 2.0 * Gl * J - m["sigma_y"] > 0
                 return torch.where(on, torch.full_like(J, m["chi0"]), torch.zeros_like(J))
 
             lo = torch.zeros_like(Jst)
@@ -457,13 +459,13 @@ def step(q, grid, mats, opts, dt=None):
     th = opts.get("thinc", False)
 
     def D(x):
-        return spatial_operator(x, grid, mats, th)
+        return spatial_operator(x, grid, mats, th, opts.get("limiter", "minmod"))
 
     if opts.get("scheme", "rk3") == "hancock":
         if grid.get("geometry", "planar") != "planar":
             raise NotImplementedError("the MUSCL-Hancock form is planar only")
         from .hancock import hancock_operator
-        qs = _axpy(1.0, q, -dt, hancock_operator(q, grid, mats, th, dt))
+        qs = _axpy(1.0, q, -dt, hancock_operator(q, grid, mats, th, dt, opts.get("limiter", "minmod")))
     else:
         q1 = _axpy(1.0, q, -dt, D(q))
         q2 = _axpy(1.0, q1, -dt, D(q1))

@@ -16,10 +16,11 @@ DIS_OK, DIS_EINVAL, DIS_ENOMEM, DIS_ECUDA, DIS_ENONPHYSICAL, DIS_ESTATE = 0, -1,
 DIS_CONSERVATIVE, DIS_PRIMITIVE = 0, 1
 DIS_FP64, DIS_FP32_BULK = 0, 1
 DIS_RK3, DIS_HANCOCK = 0, 1
+DIS_MINMOD, DIS_VANLEER = 0, 1
 DIS_PLANAR, DIS_CYLINDRICAL = 0, 1
 DIS_RATE_ARRHENIUS, DIS_RATE_SQRT = 0, 1
 DIS_NPARAM = 6  # per material l: G, sigma_y, Q at 3 l + k
-DIS_NVARIANTS = 6  # FP32-bulk stage variants: 3 tile shapes x 2 register budgets
+DIS_NVARIANTS = 12  # FP32-bulk stage variants: 3 tile shapes x 2 register budgets x (per tile, persistent)
 
 
 class DisStats(ctypes.Structure):
@@ -44,7 +45,7 @@ class DisPatch(ctypes.Structure):
 
 class DisOptions(ctypes.Structure):
     _fields_ = [("cfl", c_double), ("thinc", c_int32), ("precision", c_int32), ("scheme", c_int32),
-                ("geometry", c_int32)]
+                ("geometry", c_int32), ("limiter", c_int32)]
 
 
 class DisError(RuntimeError):

@@ -74,11 +74,12 @@ void add_row(std::vector<int4>& v, int patch, int row, int lo, int hi) {
   for (int s = lo; s < hi; s += SEG) v.push_back(make_int4(patch, row, s, std::min(SEG, hi - s)));
 }
 
-// Tile shapes of the fused FP32-bulk stage kernel (TX x TY cells, 256 threads
-// in 2D): the face counts (TX+1) TY + TX (TY+1) fill two passes of the
-// threads (511, 512, 487 faces).  1D tiles of NT - 6 cells make the halo
-// (NT cells) and the faces (NT - 5) one pass each.
-constexpr int kTiles2D[3][2] = {{16, 15}, {20, 12}, {32, 7}};
+// Tile shapes of the fused FP32-bulk stage kernel (TX x TY cells; 256, 512
+// and 256 threads in 2D): the face counts (TX+1) TY + TX (TY+1) fill two
+// passes of the threads (511, 1007, 487 faces); the 32 x 15 tile recovers
+// 1.66 halo cells per cell against 1.93 and 2.2 for the others.  1D tiles of
+// NT - 6 cells make the halo (NT cells) and the faces (NT - 5) one pass each.
+constexpr int kTiles2D[3][2] = {{16, 15}, {32, 15}, {32, 7}};
 constexpr int kTiles1D[3] = {122, 250, 506};
 
 void tile_tables(dis_ctx* c) {
@@ -302,24 +303,58 @@ void stage_fused_c(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
       c->phys, c->physf, a, c->d_tiles[shape]);
 }
 
-// Planar and cylindrical contexts run separate instantiations, so the
-// geometric source costs the planar kernels nothing.
+// Persistent stage kernel (planar 2D): as many CTAs as fit on the device at
+// once, each looping over the tiles.
 template <int DIM, bool RX, int TX, int TY, int NT, int MINB>
-void stage_fused(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
+void stage_persistent(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
+  constexpr size_t smem = fused32_smem<DIM, RX, TX, TY>();
+  static int grid = 0;  // per instantiation, per process
+  if (!grid) {
+    cudaFuncSetAttribute(k_stage32p<DIM, RX, TX, TY, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    cudaFuncSetAttribute(k_stage32p<DIM, RX, TX, TY, NT, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         100);
+    int per_sm = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage32p<DIM, RX, TX, TY, NT, MINB>, NT, smem);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+    grid = std::max(1, per_sm) * std::max(1, sms);
+  }
+  const int nt = (int)c->tiles[shape].size();
+  k_stage32p<DIM, RX, TX, TY, NT, MINB><<<(unsigned)std::min(grid, nt), NT, smem, st>>>(
+      c->phys, c->physf, a, c->d_tiles[shape], nt);
+}
+
+// Planar and cylindrical contexts run separate instantiations, so the
+// geometric source costs the planar kernels nothing.  persist: the
+// persistent form (planar 2D only; the cylindrical update rereads the tile's
+// primitives).
+template <int DIM, bool RX, int TX, int TY, int NT, int MINB>
+void stage_fused(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape, bool persist = false) {
+  if constexpr (DIM == 2) {
+    if (persist && !c->phys.cyl) {
+      stage_persistent<DIM, RX, TX, TY, NT, MINB>(c, st, a, shape);
+      return;
+    }
+  }
   if (c->phys.cyl) stage_fused_c<DIM, RX, TX, TY, NT, MINB, true>(c, st, a, shape);
   else stage_fused_c<DIM, RX, TX, TY, NT, MINB, false>(c, st, a, shape);
 }
 
-// FP32-bulk stage variants v = shape + 3 budget: the 3 tile shapes x two
-// register budgets (2D: 3 or 4 resident CTAs of 256 threads per SM requested
-// from the register allocator; 1D: no limit, or 64 registers per thread).
-bool variant_valid(const dis_ctx*, int v) { return v >= 0 && v < DIS_NVARIANTS; }
+// FP32-bulk stage variants v = shape + 3 budget + 6 persist: the 3 tile
+// shapes x two register budgets (2D: 768 or 1024 resident threads per SM
+// requested from the register allocator; 1D: no limit, or 64 registers per
+// thread) x (one CTA per tile, or the persistent form: planar 2D only).
+bool variant_valid(const dis_ctx* c, int v) {
+  return v >= 0 && v < DIS_NVARIANTS && (v < 6 || (c->dim == 2 && !c->phys.cyl));
+}
 
+// MINB: resident CTAs of 256 threads per SM requested (3 or 4); the
+// 512-thread tile asks for half as many.
 template <int DIM, bool RX, int MINB>
-void stage_kernel_2d(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
-  if (shape == 0) stage_fused<DIM, RX, 16, 15, 256, MINB>(c, st, a, shape);
-  else if (shape == 1) stage_fused<DIM, RX, 20, 12, 256, MINB>(c, st, a, shape);
-  else stage_fused<DIM, RX, 32, 7, 256, MINB>(c, st, a, shape);
+void stage_kernel_2d(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape, bool persist) {
+  if (shape == 0) stage_fused<DIM, RX, 16, 15, 256, MINB>(c, st, a, shape, persist);
+  else if (shape == 1) stage_fused<DIM, RX, 32, 15, 512, MINB / 2>(c, st, a, shape, persist);
+  else stage_fused<DIM, RX, 32, 7, 256, MINB>(c, st, a, shape, persist);
 }
 
 // The stage kernel of variant v.
@@ -327,8 +362,9 @@ template <int DIM, bool RX>
 void stage_kernel_v(dis_ctx* c, cudaStream_t st, StepArgs32& a, int v) {
   const int shape = v % 3;
   if constexpr (DIM == 2) {
-    if (v >= 3) stage_kernel_2d<DIM, RX, 4>(c, st, a, shape);
-    else stage_kernel_2d<DIM, RX, 3>(c, st, a, shape);
+    const bool persist = v >= 6;
+    if ((v % 6) >= 3) stage_kernel_2d<DIM, RX, 4>(c, st, a, shape, persist);
+    else stage_kernel_2d<DIM, RX, 3>(c, st, a, shape, persist);
   } else if (v < 3) {
     if (shape == 0) stage_fused<DIM, RX, 122, 1, 128, 1>(c, st, a, shape);
     else if (shape == 1) stage_fused<DIM, RX, 250, 1, 256, 1>(c, st, a, shape);
@@ -802,6 +838,8 @@ int dis_create(int dim, int n_patches, const dis_patch* patches, int reactive_ma
     return fail(DIS_EINVAL, "dis_create: the MUSCL-Hancock scheme is built for float64 only");
   if (opt->geometry != DIS_PLANAR && opt->geometry != DIS_CYLINDRICAL)
     return fail(DIS_EINVAL, "dis_create: unknown geometry %d", opt->geometry);
+  if (opt->limiter != DIS_MINMOD && opt->limiter != DIS_VANLEER)
+    return fail(DIS_EINVAL, "dis_create: unknown limiter %d", opt->limiter);
   if (opt->geometry == DIS_CYLINDRICAL && opt->scheme != DIS_RK3)
     return fail(DIS_EINVAL, "dis_create: cylindrical geometry is built for the Runge-Kutta scheme only");
   for (int p = 0; p < n_patches; ++p) {
@@ -833,6 +871,7 @@ int dis_create(int dim, int n_patches, const dis_patch* patches, int reactive_ma
   c->phys.thinc = opt->thinc ? 1 : 0;
   c->phys.cfl = opt->cfl;
   c->phys.cyl = opt->geometry == DIS_CYLINDRICAL ? 1 : 0;
+  c->phys.limiter = opt->limiter;
   layout(c);
   c->patch_set.assign(n_patches, 0);
   *out = c;

@@ -98,7 +98,7 @@ __device__ __forceinline__ T& prim_slot(PrimT<T>& w, int k) {
 // (used only by the 2D Youngs normal, (1,2,1)-weighted central differences).
 template <int DIM, class T>
 __device__ __forceinline__ void face_phi(const T (&B)[3][6], bool thinc, double hn, double ht,
-                                         T& phiL, T& phiR) {
+                                         T& phiL, T& phiR, int lim = 0) {
   CandT<T> c[4];
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
@@ -113,7 +113,7 @@ __device__ __forceinline__ void face_phi(const T (&B)[3][6], bool thinc, double 
       }
       return beta;
     };
-    c[s] = phi_cand_lazy(B[1][s], B[1][s + 1], B[1][s + 2], beta_of, thinc);
+    c[s] = phi_cand_lazy(B[1][s], B[1][s + 1], B[1][s + 2], beta_of, thinc, lim);
   }
   T Lt, Rt;
   bvd(c[0], c[1], c[2], Lt, Rt);
@@ -128,7 +128,7 @@ __device__ __forceinline__ void face_phi(const T (&B)[3][6], bool thinc, double 
 // i+1 and the BVD choice for cell i (Appendix A), as in face_phi.
 template <int DIM, class T>
 __device__ __forceinline__ void cell_phi_edges(const T (&B)[3][5], bool thinc, double hn, double ht,
-                                               T& eL, T& eR) {
+                                               T& eL, T& eR, int lim = 0) {
   CandT<T> c[3];
 #pragma unroll
   for (int s = 0; s < 3; ++s) {
@@ -143,16 +143,17 @@ __device__ __forceinline__ void cell_phi_edges(const T (&B)[3][5], bool thinc, d
       }
       return beta;
     };
-    c[s] = phi_cand_lazy(B[1][s], B[1][s + 1], B[1][s + 2], beta_of, thinc);
+    c[s] = phi_cand_lazy(B[1][s], B[1][s + 1], B[1][s + 2], beta_of, thinc, lim);
   }
   bvd(c[0], c[1], c[2], eL, eR);
 }
 
-// MUSCL face values of one primitive from cells a-1 .. a+2 (minmod slopes).
+// MUSCL face values of one primitive from cells a-1 .. a+2 (limited slopes:
+// lim 0 minmod, 1 van Leer).
 template <class T>
-__device__ __forceinline__ void muscl_pair(T w0, T w1, T w2, T w3, T& l, T& r) {
-  const T s1 = minmod(w1 - w0, w2 - w1);
-  const T s2 = minmod(w2 - w1, w3 - w2);
+__device__ __forceinline__ void muscl_pair(T w0, T w1, T w2, T w3, T& l, T& r, int lim = 0) {
+  const T s1 = limited(w1 - w0, w2 - w1, lim);
+  const T s2 = limited(w2 - w1, w3 - w2, lim);
   l = w1 + 0.5 * s1;
   r = w2 - 0.5 * s2;
 }

@@ -69,7 +69,7 @@ __device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__
         }
         return beta;
       };
-      c[s] = phi_cand_f(ph[s], ph[s + 1], ph[s + 2], beta_of, P.thinc != 0);
+      c[s] = phi_cand_f(ph[s], ph[s + 1], ph[s + 2], beta_of, P.thinc != 0, P.limiter);
     }
     float Lt, Rt;
     bvd_f(c[0], c[1], c[2], Lt, Rt);
@@ -90,10 +90,11 @@ __device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__
   ld(w2, k0 + sx);
   ld(w3, k0 + 2 * sx);
   PrimF wl, wr;
+  const int lim = P.limiter;
 #define DIS_RECF(fld)                                            \
   {                                                              \
-    const float s1 = minmod_f(w1.fld - w0.fld, w2.fld - w1.fld); \
-    const float s2 = minmod_f(w2.fld - w1.fld, w3.fld - w2.fld); \
+    const float s1 = limited_f(w1.fld - w0.fld, w2.fld - w1.fld, lim); \
+    const float s2 = limited_f(w2.fld - w1.fld, w3.fld - w2.fld, lim); \
     wl.fld = w1.fld + 0.5f * s1;                                 \
     wr.fld = w2.fld - 0.5f * s2;                                 \
   }
@@ -160,48 +161,38 @@ constexpr size_t fused32_smem() {
 // Positive float -> bits that order like the value (for integer atomic max).
 __device__ __forceinline__ unsigned rate_bits(float r) { return __float_as_uint(fmaxf(r, 0.f)); }
 
-// One stage on one tile t = (patch, i0, j0) by the NT threads of a CTA, with
-// the tile's primitives and faces in the shared memory sm.  The stage kernel
-// runs it once per CTA; the persistent 1D batch kernel runs it for every tile
-// of its problem in turn (the caller synchronises the CTA between tiles).
-// Last stage: the CFL rate of every updated cell goes, by warp max, into
-// rate_cta (shared, if not null) or A.rate_next[patch] (global).
-template <int DIM, bool RX, int TX, int TY, int NT, bool CYL = false>
-__device__ __forceinline__ void stage32_tile(const Phys& P, const PhysF& F, const StepArgs32& A, const int4 t,
-                                             float* __restrict__ sm, unsigned* rate_cta) {
-  static_assert(TX * TY <= NT, "one thread per tile cell in the update phase");
+// Per-tile constants of the update, formed by one thread: dt as float-float
+// and float, the RK weights (b as float-float), the inverse cell sizes.
+struct TileConst {
+  float dth, dtl, af, bh, bl, ihx, ihy;
+};
+
+__device__ __forceinline__ void tile_consts(const Phys& P, const StepArgs32& A, const int4 t, TileConst& K) {
+  const PatchDev& pd = A.pd[t.x];
+  const double dt = A.dtfix ? A.dtfix[t.x] : P.cfl / __longlong_as_double((long long)A.rate[t.x]);
+  const ff d = ff_of(dt), b = ff_of(A.b);
+  K.dth = d.h;
+  K.dtl = d.l;
+  K.af = (float)A.a;
+  K.bh = b.h;
+  K.bl = b.l;
+  K.ihx = 1.f / (float)pd.dx;
+  K.ihy = 1.f / (float)pd.dy;
+  if (A.last && t.y == 0 && t.z == 0) A.dtlast[t.x] = dt;
+}
+
+// Phase 1: primitives of the tile t and its halo (ghosts by the index map)
+// into the shared-memory planes of sm, by the NT threads of the CTA.
+template <int DIM, bool RX, int TX, int TY, int NT>
+__device__ __forceinline__ void fill_tile(const Phys& P, const PhysF& F, const StepArgs32& A, const int4 t,
+                                          float* __restrict__ sm) {
   using L = Lay<DIM, RX>;
-  using S = FSlots<DIM, RX>;
-  constexpr int NF = L::NF;
   constexpr int HX = TX + 2 * NG, HY = DIM == 2 ? TY + 2 * NG : 1;
-  constexpr int NFX = (TX + 1) * TY, NFY = DIM == 2 ? TX * (TY + 1) : 0;
   float* Wsm = sm;
-  float* Fxs = Wsm + NF * HX * HY;
-  float* Fys = Fxs + S::N * NFX;
   const PatchDev pd = A.pd[t.x];
   const int i0 = t.y, j0 = t.z;
-  const int tid = threadIdx.x;
-  const float dxf = (float)pd.dx, dyf = (float)pd.dy;
   const long long T = A.T;
-
-  // per-CTA constants of the update: dt (float-float and float), the RK
-  // weights, inverse cell sizes
-  __shared__ float dth_sh, dtl_sh, af_sh, bh_sh, bl_sh, ihx_sh, ihy_sh;
-  if (tid == 0) {
-    const double dt = A.dtfix ? A.dtfix[t.x] : P.cfl / __longlong_as_double((long long)A.rate[t.x]);
-    const ff d = ff_of(dt), b = ff_of(A.b);
-    dth_sh = d.h;
-    dtl_sh = d.l;
-    af_sh = (float)A.a;
-    bh_sh = b.h;
-    bl_sh = b.l;
-    ihx_sh = 1.f / dxf;
-    ihy_sh = 1.f / dyf;
-    if (A.last && i0 == 0 && j0 == 0) A.dtlast[t.x] = dt;
-  }
-
-  // 1. primitives of the tile and its halo (ghosts by the index map)
-  for (int c = tid; c < HX * HY; c += NT) {
+  for (int c = threadIdx.x; c < HX * HY; c += NT) {
     const int hx = c % HX, hy = c / HX;
     const int i = i0 - NG + hx;
     const int j = DIM == 2 ? j0 - NG + hy : 0;
@@ -225,11 +216,23 @@ __device__ __forceinline__ void stage32_tile(const Phys& P, const PhysF& F, cons
     Wsm[L::V33 * plane + c] = w.V33;
     if constexpr (RX) Wsm[L::AL * plane + c] = w.lam;
   }
-  __syncthreads();
+}
 
-  // 2. all x faces ((TX + 1) per interior row) and y faces (TX per face row,
-  //    TY + 1 face rows) of the tile, in one loop so the threads stay busy
-  for (int f = tid; f < NFX + NFY; f += NT) {
+// Phase 2: all x faces ((TX + 1) per interior row) and y faces (TX per face
+// row, TY + 1 face rows) of the tile, in one loop so the threads stay busy.
+template <int DIM, bool RX, int TX, int TY, int NT>
+__device__ __forceinline__ void faces_tile(const PhysF& F, const StepArgs32& A, const int4 t,
+                                           float* __restrict__ sm) {
+  using S = FSlots<DIM, RX>;
+  constexpr int HX = TX + 2 * NG, HY = DIM == 2 ? TY + 2 * NG : 1;
+  constexpr int NFX = (TX + 1) * TY, NFY = DIM == 2 ? TX * (TY + 1) : 0;
+  const float* Wsm = sm;
+  float* Fxs = sm + Lay<DIM, RX>::NF * HX * HY;
+  float* Fys = Fxs + S::N * NFX;
+  const PatchDev pd = A.pd[t.x];
+  const int i0 = t.y, j0 = t.z;
+  const float dxf = (float)pd.dx, dyf = (float)pd.dy;
+  for (int f = threadIdx.x; f < NFX + NFY; f += NT) {
     if (f < NFX) {
       const int fx = f % (TX + 1), fy = f / (TX + 1);
       const int i = i0 + fx, j = j0 + fy;  // face between cells i-1 and i
@@ -243,7 +246,33 @@ __device__ __forceinline__ void stage32_tile(const Phys& P, const PhysF& F, cons
       face32<DIM, RX, 1>(F, Wsm, HX, HY, fx + NG, fy + NG - 1, dyf, dxf, Fys, NFY, g);
     }
   }
-  __syncthreads();
+}
+
+// Phase 3: update of the tile's cells from the faces in sm (divergence,
+// non-conservative terms, RK combination; last stage: plastic and reactive
+// steps and the CFL rate of the new state, by warp max into rate_cta (shared,
+// if not null) or A.rate_next[patch] (global)).  Every lane of a warp with a
+// tile cell reaches the warp max.
+template <int DIM, bool RX, int TX, int TY, int NT, bool CYL = false>
+__device__ __forceinline__ void update_tile(const Phys& P, const PhysF& F, const StepArgs32& A, const int4 t,
+                                            const float* __restrict__ sm, const TileConst& K,
+                                            unsigned* rate_cta) {
+  static_assert(TX * TY <= NT, "one thread per tile cell in the update phase");
+  using L = Lay<DIM, RX>;
+  using S = FSlots<DIM, RX>;
+  constexpr int NF = L::NF;
+  constexpr int HX = TX + 2 * NG, HY = DIM == 2 ? TY + 2 * NG : 1;
+  constexpr int NFX = (TX + 1) * TY, NFY = DIM == 2 ? TX * (TY + 1) : 0;
+  const float* Wsm = sm;
+  const float* Fxs = Wsm + NF * HX * HY;
+  const float* Fys = Fxs + S::N * NFX;
+  const PatchDev pd = A.pd[t.x];
+  const int i0 = t.y, j0 = t.z;
+  const int tid = threadIdx.x;
+  const float dxf = (float)pd.dx;
+  const long long T = A.T;
+  const float dth_sh = K.dth, dtl_sh = K.dtl, af_sh = K.af, bh_sh = K.bh, bl_sh = K.bl, ihx_sh = K.ihx,
+              ihy_sh = K.ihy;
 
   // 3. update of the tile's cells (every lane of a warp with a tile cell
   //    reaches the warp max of the last stage)
@@ -420,10 +449,61 @@ __device__ __forceinline__ void stage32_tile(const Phys& P, const PhysF& F, cons
   }
 }
 
+
+// One stage on one tile t = (patch, i0, j0) by the NT threads of a CTA, with
+// the tile's primitives and faces in the shared memory sm.  The stage kernel
+// runs it once per CTA; the persistent 1D batch kernel runs it for every tile
+// of its problem in turn (the caller synchronises the CTA between tiles).
+template <int DIM, bool RX, int TX, int TY, int NT, bool CYL = false>
+__device__ __forceinline__ void stage32_tile(const Phys& P, const PhysF& F, const StepArgs32& A, const int4 t,
+                                             float* __restrict__ sm, unsigned* rate_cta) {
+  __shared__ TileConst K;
+  if (threadIdx.x == 0) tile_consts(P, A, t, K);
+  fill_tile<DIM, RX, TX, TY, NT>(P, F, A, t, sm);
+  __syncthreads();
+  faces_tile<DIM, RX, TX, TY, NT>(F, A, t, sm);
+  __syncthreads();
+  update_tile<DIM, RX, TX, TY, NT, CYL>(P, F, A, t, sm, K, rate_cta);
+}
+
 template <int DIM, bool RX, int TX, int TY, int NT, int MINB, bool CYL = false>
 __global__ void __launch_bounds__(NT, MINB) k_stage32(Phys P, PhysF F, StepArgs32 A, const int4* __restrict__ tiles) {
   extern __shared__ __align__(16) float sm[];
   stage32_tile<DIM, RX, TX, TY, NT, CYL>(P, F, A, tiles[blockIdx.x], sm, nullptr);
+}
+
+// Persistent form of the stage kernel (planar 2D): CTA b takes tiles b,
+// b + gridDim.x, ... in turn.  The update of one tile and the halo recovery
+// of the next run in the same phase (both wait mostly on global memory), so
+// a tile costs two barriers, and no tail wave of CTAs is left at the end.
+// The update reads only the tile's face data (the primitive planes it would
+// read for the cylindrical source are being refilled), hence planar only.
+template <int DIM, bool RX, int TX, int TY, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_stage32p(Phys P, PhysF F, StepArgs32 A,
+                                                       const int4* __restrict__ tiles, int ntiles) {
+  extern __shared__ __align__(16) float sm[];
+  __shared__ TileConst K[2];
+  int t = blockIdx.x;
+  if (t >= ntiles) return;
+  int b = 0;
+  if (threadIdx.x == 0) tile_consts(P, A, tiles[t], K[0]);
+  fill_tile<DIM, RX, TX, TY, NT>(P, F, A, tiles[t], sm);
+  __syncthreads();
+  faces_tile<DIM, RX, TX, TY, NT>(F, A, tiles[t], sm);
+  __syncthreads();
+  for (;;) {
+    const int tn = t + gridDim.x;
+    const bool more = tn < ntiles;
+    if (more && threadIdx.x == 0) tile_consts(P, A, tiles[tn], K[b ^ 1]);
+    update_tile<DIM, RX, TX, TY, NT, false>(P, F, A, tiles[t], sm, K[b], nullptr);
+    if (more) fill_tile<DIM, RX, TX, TY, NT>(P, F, A, tiles[tn], sm);
+    __syncthreads();
+    if (!more) break;
+    faces_tile<DIM, RX, TX, TY, NT>(F, A, tiles[tn], sm);
+    __syncthreads();
+    t = tn;
+    b ^= 1;
+  }
 }
 
 // CFL rate of the state at the start of a step (FP32-bulk), for the first

@@ -53,6 +53,7 @@ struct PhysT {
   int thinc;  // THINC-BVD steepening on phi1
   R cfl;
   int cyl;    // axisymmetric geometry (x = r, y = z): geometric source s_g
+  int limiter;  // MUSCL slope limiter: 0 minmod, 1 van Leer
 };
 
 using MatDev = MatT<double>;
@@ -75,6 +76,7 @@ inline PhysT<float> to_float(const Phys& P) {
   f.thinc = P.thinc;
   f.cfl = (float)P.cfl;
   f.cyl = P.cyl;
+  f.limiter = P.limiter;
   return f;
 }
 
@@ -163,6 +165,20 @@ __device__ __forceinline__ T minmod(T a, T b) {
   return (a * b > 0.0) ? copysign(fmin(fabs(a), fabs(b)), a) : T(0.0);
 }
 
+// van Leer's limited slope, the harmonic mean 2 a b / (a + b) of the two
+// one-sided differences when they have the same sign, else 0.
+template <class T>
+__device__ __forceinline__ T vanleer(T a, T b) {
+  const T ab = a * b;
+  return (ab > 0.0) ? 2.0 * ab / (a + b) : T(0.0);
+}
+
+// Limited slope of the MUSCL reconstruction: lim 0 minmod, 1 van Leer.
+template <class T>
+__device__ __forceinline__ T limited(T a, T b, int lim) {
+  return lim ? vanleer(a, b) : minmod(a, b);
+}
+
 // MUSCL and THINC edge candidates of phi in one cell (Appendix A).
 template <class T>
 struct CandT {
@@ -172,9 +188,10 @@ using Cand = CandT<double>;
 
 // beta_of() gives the THINC steepness; it is evaluated only in a mixed cell.
 template <class T, class BetaFn>
-__device__ __forceinline__ CandT<T> phi_cand_lazy(T qm, T qc, T qp, const BetaFn& beta_of, bool thinc) {
+__device__ __forceinline__ CandT<T> phi_cand_lazy(T qm, T qc, T qp, const BetaFn& beta_of, bool thinc,
+                                                  int lim = 0) {
   CandT<T> c;
-  const T s = minmod(qc - qm, qp - qc);
+  const T s = limited(qc - qm, qp - qc, lim);
   c.mL = qc - 0.5 * s;
   c.mR = qc + 0.5 * s;
   c.tL = c.mL;

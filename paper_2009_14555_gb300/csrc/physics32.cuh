@@ -68,15 +68,23 @@ __device__ __forceinline__ float minmod_f(float a, float b) {
   return (a * b > 0.f) ? copysignf(fminf(fabsf(a), fabsf(b)), a) : 0.f;
 }
 
+// Limited slope: lim 0 minmod, 1 van Leer (2 a b / (a + b) for a b > 0).
+__device__ __forceinline__ float limited_f(float a, float b, int lim) {
+  if (!lim) return minmod_f(a, b);
+  const float ab = a * b;
+  return ab > 0.f ? 2.f * ab / (a + b) : 0.f;
+}
+
 struct CandF {
   float mL, mR, tL, tR;
 };
 
 // beta_of() gives the THINC steepness; it is evaluated only in a mixed cell.
 template <class BetaFn>
-__device__ __forceinline__ CandF phi_cand_f(float qm, float qc, float qp, const BetaFn& beta_of, bool thinc) {
+__device__ __forceinline__ CandF phi_cand_f(float qm, float qc, float qp, const BetaFn& beta_of, bool thinc,
+                                            int lim = 0) {
   CandF c;
-  const float s = minmod_f(qc - qm, qp - qc);
+  const float s = limited_f(qc - qm, qp - qc, lim);
   c.mL = qc - 0.5f * s;
   c.mR = qc + 0.5f * s;
   c.tL = c.mL;

@@ -202,7 +202,8 @@ __global__ void __launch_bounds__(SEG) k_flux(Phys P, StepArgs A, const int4* __
     for (int c = 0; c < 6; ++c) B[0][c] = B[2][c] = 0.0;
   }
   double phiL, phiR;
-  face_phi<DIM, double>(B, P.thinc != 0, DIR == 0 ? pd.dx : pd.dy, DIR == 0 ? pd.dy : pd.dx, phiL, phiR);
+  face_phi<DIM, double>(B, P.thinc != 0, DIR == 0 ? pd.dx : pd.dy, DIR == 0 ? pd.dy : pd.dx, phiL, phiR,
+                        P.limiter);
 
   // MUSCL on the other primitives: cells a-1, a, a+1, a+2
   const Prim w0 = load_prim<DIM, RX>(W, T, at(a - 1));
@@ -210,22 +211,22 @@ __global__ void __launch_bounds__(SEG) k_flux(Phys P, StepArgs A, const int4* __
   const Prim w2 = load_prim<DIM, RX>(W, T, at(a + 1));
   const Prim w3 = load_prim<DIM, RX>(W, T, at(a + 2));
   Prim wl, wr;
-  muscl_pair(w0.r1, w1.r1, w2.r1, w3.r1, wl.r1, wr.r1);
-  muscl_pair(w0.r2, w1.r2, w2.r2, w3.r2, wl.r2, wr.r2);
-  muscl_pair(w0.u, w1.u, w2.u, w3.u, wl.u, wr.u);
-  muscl_pair(w0.p, w1.p, w2.p, w3.p, wl.p, wr.p);
-  muscl_pair(w0.V11, w1.V11, w2.V11, w3.V11, wl.V11, wr.V11);
-  muscl_pair(w0.V22, w1.V22, w2.V22, w3.V22, wl.V22, wr.V22);
-  muscl_pair(w0.V33, w1.V33, w2.V33, w3.V33, wl.V33, wr.V33);
+  muscl_pair(w0.r1, w1.r1, w2.r1, w3.r1, wl.r1, wr.r1, P.limiter);
+  muscl_pair(w0.r2, w1.r2, w2.r2, w3.r2, wl.r2, wr.r2, P.limiter);
+  muscl_pair(w0.u, w1.u, w2.u, w3.u, wl.u, wr.u, P.limiter);
+  muscl_pair(w0.p, w1.p, w2.p, w3.p, wl.p, wr.p, P.limiter);
+  muscl_pair(w0.V11, w1.V11, w2.V11, w3.V11, wl.V11, wr.V11, P.limiter);
+  muscl_pair(w0.V22, w1.V22, w2.V22, w3.V22, wl.V22, wr.V22, P.limiter);
+  muscl_pair(w0.V33, w1.V33, w2.V33, w3.V33, wl.V33, wr.V33, P.limiter);
   if constexpr (DIM == 2) {
-    muscl_pair(w0.v, w1.v, w2.v, w3.v, wl.v, wr.v);
-    muscl_pair(w0.V12, w1.V12, w2.V12, w3.V12, wl.V12, wr.V12);
-    muscl_pair(w0.V21, w1.V21, w2.V21, w3.V21, wl.V21, wr.V21);
+    muscl_pair(w0.v, w1.v, w2.v, w3.v, wl.v, wr.v, P.limiter);
+    muscl_pair(w0.V12, w1.V12, w2.V12, w3.V12, wl.V12, wr.V12, P.limiter);
+    muscl_pair(w0.V21, w1.V21, w2.V21, w3.V21, wl.V21, wr.V21, P.limiter);
   } else {
     wl.v = wr.v = 0.0;
     wl.V12 = wr.V12 = wl.V21 = wr.V21 = 0.0;
   }
-  if constexpr (RX) muscl_pair(w0.lam, w1.lam, w2.lam, w3.lam, wl.lam, wr.lam);
+  if constexpr (RX) muscl_pair(w0.lam, w1.lam, w2.lam, w3.lam, wl.lam, wr.lam, P.limiter);
   else wl.lam = wr.lam = 0.0;
   wl.phi = phiL;
   wr.phi = phiR;
@@ -428,7 +429,8 @@ __device__ __forceinline__ void hancock_edges(const Phys& P, const double* __res
     B[2][c] = normals ? W[L::PHI * T + k + (c - 2) * st + sx] : 0.0;
   }
   double eL, eR;
-  cell_phi_edges<DIM, double>(B, P.thinc != 0, D == 0 ? pd.dx : pd.dy, D == 0 ? pd.dy : pd.dx, eL, eR);
+  cell_phi_edges<DIM, double>(B, P.thinc != 0, D == 0 ? pd.dx : pd.dy, D == 0 ? pd.dy : pd.dx, eL, eR,
+                              P.limiter);
   Prim wm = load_prim<DIM, RX>(W, T, k - st);
   Prim wp = load_prim<DIM, RX>(W, T, k + st);
   Prim m = wc;
@@ -437,8 +439,8 @@ __device__ __forceinline__ void hancock_edges(const Phys& P, const double* __res
 #pragma unroll
   for (int c = 0; c < NF; ++c) {
     if (c == L::PHI) continue;
-    const double sl = minmod(prim_slot<DIM, RX>(m, c) - prim_slot<DIM, RX>(wm, c),
-                             prim_slot<DIM, RX>(wp, c) - prim_slot<DIM, RX>(m, c));
+    const double sl = limited(prim_slot<DIM, RX>(m, c) - prim_slot<DIM, RX>(wm, c),
+                              prim_slot<DIM, RX>(wp, c) - prim_slot<DIM, RX>(m, c), P.limiter);
     prim_slot<DIM, RX>(lo, c) = prim_slot<DIM, RX>(m, c) - 0.5 * sl;
     prim_slot<DIM, RX>(hi, c) = prim_slot<DIM, RX>(m, c) + 0.5 * sl;
   }

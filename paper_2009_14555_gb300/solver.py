@@ -54,7 +54,7 @@ class Solver:
     """Diffuse-interface step on a batch of patches (see include/dis.h)."""
 
     def __init__(self, dim, patches, materials, reactive_material=-1, cfl=0.8, thinc=False,
-                 precision="fp64", device=None, scheme="rk3", geometry="planar"):
+                 precision="fp64", device=None, scheme="rk3", geometry="planar", limiter="minmod"):
         if not torch.cuda.is_available():
             raise RuntimeError("Solver needs a CUDA device (no CPU fallback)")
         dev = torch.device(device or "cuda")
@@ -69,7 +69,8 @@ class Solver:
         prec = {"fp64": L.DIS_FP64, "fp32_bulk": L.DIS_FP32_BULK}[precision]
         sch = {"rk3": L.DIS_RK3, "hancock": L.DIS_HANCOCK}[scheme]
         geo = {"planar": L.DIS_PLANAR, "cyl": L.DIS_CYLINDRICAL}[geometry]
-        opts = L.DisOptions(float(cfl), int(bool(thinc)), prec, sch, geo)
+        lim = {"minmod": L.DIS_MINMOD, "vanleer": L.DIS_VANLEER}[limiter]
+        opts = L.DisOptions(float(cfl), int(bool(thinc)), prec, sch, geo, lim)
         self.stream = torch.cuda.current_stream(self.device)
         self.ctx = L.dis_create(dim, [_patch(p, dim) for p in self.patches], reactive_material, opts,
                                 self.stream.cuda_stream)
@@ -87,6 +88,7 @@ class Solver:
     def from_workload(cls, wl, precision="fp64", **kw):
         kw.setdefault("scheme", getattr(wl, "scheme", "rk3"))
         kw.setdefault("geometry", getattr(wl, "geometry", "planar"))
+        kw.setdefault("limiter", getattr(wl, "limiter", "minmod"))
         return cls(wl.dim, wl.patches, wl.materials, wl.reactive_material, wl.cfl, wl.thinc,
                    precision, **kw)
 

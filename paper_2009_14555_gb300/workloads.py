@@ -61,6 +61,29 @@ def material(gamma, p_inf=0.0, e_inf=0.0, G=0.0, plastic=0, sigma_y=0.0, chi0=0.
                 T_act=float(T_act), rate_law=int(rate_law), p_ign=float(p_ign))
 
 
+def romenskii(rho0, K0, G0, Gamma, alpha, beta, plastic=0, sigma_y=0.0) -> dict:
+    """Romenskii elastic solid of Section 2.3 (gamma = Gamma + 1)."""
+    m = material(Gamma + 1.0, G=G0, plastic=plastic, sigma_y=sigma_y)
+    m.update(eos="romenskii", rho0=float(rho0), K0=float(K0), alpha_r=float(alpha), beta_r=float(beta))
+    return m
+
+
+def jwl(rho0, A, B, R1, R2, Gamma, cv=0.0) -> dict:
+    """JWL fluid of Section 2.3 (gamma = Gamma + 1; no shear modulus)."""
+    m = material(Gamma + 1.0, cv=cv)
+    m.update(eos="jwl", rho0=float(rho0), jwl_A=float(A), jwl_B=float(B), jwl_R1=float(R1),
+             jwl_R2=float(R2))
+    return m
+
+
+# Copper of the Romenskii table (Section 4.1): rho0 8930, K0 136.5 GPa,
+# G0 39.4 GPa, Gamma 2, alpha-bar 1, beta-bar 3.
+COPPER_ROMENSKII = romenskii(8930.0, 136.5e9, 39.4e9, 2.0, 1.0, 3.0)
+# LX-17 reactant of the JWL table: rho0 1905, A 778.1e11 Pa, B -0.0503e11 Pa,
+# R1 11.3, R2 1.13, Gamma 0.8938, C_V 1305.5.
+LX17_REACTANT_JWL = jwl(1905.0, 778.1e11, -0.0503e11, 11.3, 1.13, 0.8938, cv=1305.5)
+
+
 # Solid of the 1D solid|gas problem: stiffened-gas-form hydrostatic EOS,
 # constant shear modulus, perfect plasticity with radial return.
 SOLID = material(4.0, p_inf=6e10, G=5e10, plastic=1, sigma_y=4e8)
@@ -94,6 +117,7 @@ class Workload:
     extra: dict = field(default_factory=dict)
     scheme: str = "rk3"                  # hyperbolic update: "rk3" (the paper's) or "hancock"
     geometry: str = "planar"             # "planar" (plane strain) or "cyl" (axisymmetric, x = r, y = z)
+    limiter: str = "minmod"              # MUSCL slope limiter: "minmod" or "vanleer"
 
     @property
     def reactive(self) -> bool:

@@ -23,7 +23,8 @@ def oracle_run(wl, steps, patch_ids=None, dt_list=None):
     for k in ids:
         p = wl.patches[k]
         q, d = OS.run(p.prim, wl.dim, wl.materials, OS.grid_of(p, wl.dim, getattr(wl, "geometry", "planar")),
-                      dict(cfl=wl.cfl, thinc=wl.thinc, scheme=getattr(wl, "scheme", "rk3")), steps,
+                      dict(cfl=wl.cfl, thinc=wl.thinc, scheme=getattr(wl, "scheme", "rk3"),
+                           limiter=getattr(wl, "limiter", "minmod")), steps,
                       None if dt_list is None else dt_list[k])
         outs.append(q.numpy())
         dts.append(d)
@@ -72,6 +73,33 @@ def rel_l1(gpu, ora, scales=None):
 
 def cons_l1(wl, gpu, ora):
     return rel_l1(gpu, ora, cons_scales(wl, ora))
+
+
+def max_rel(gpu, ora, scales=None):
+    """Element-wise companion of rel_l1: per field max |gpu - ora| / max(max
+    |ora|, s_f), so that one bad cell cannot hide in the sum."""
+    g = np.asarray(gpu).reshape(gpu.shape[0], -1)
+    o = np.asarray(ora).reshape(ora.shape[0], -1)
+    den = np.abs(o).max(1)
+    if scales is not None:
+        den = np.maximum(den, scales)
+    return np.abs(g - o).max(1) / np.maximum(den, 1e-300)
+
+
+def cons_max(wl, gpu, ora):
+    return max_rel(gpu, ora, cons_scales(wl, ora))
+
+
+_RECORD = {}
+
+
+def record(name, **kw):
+    """Keep the measured errors of a parity case (JSON at record_path)."""
+    import json
+    _RECORD[name] = {k: (np.asarray(v).tolist() if isinstance(v, (np.ndarray, list, tuple)) else v)
+                     for k, v in kw.items()}
+    with open(record_path("parity.json"), "w") as f:
+        json.dump(_RECORD, f, indent=1)
 
 
 def prim_l1(wl, gpu_prim, ora_prim, ora_cons):

@@ -373,3 +373,64 @@ def test_reflective_wall_face_takes_the_left_star_state():
     assert torch.allclose(V_f, Vp, rtol=1e-6, atol=1e-12)
     assert torch.allclose(V_f[:, 0, 1], -Vm[:, 0, 1], rtol=1e-6, atol=1e-12)
     assert torch.all(V_f[:, 0, 1].abs() > 1e-8)
+
+
+# ---- Romenskii and JWL reference curves (Section 2.3) ----------------------
+CU = W.COPPER_ROMENSKII
+LX = W.LX17_REACTANT_JWL
+
+
+@pytest.mark.parametrize("m", [CU, LX], ids=["romenskii", "jwl"])
+@pytest.mark.parametrize("J2v", [0.0, 2e-4])
+def test_reference_pressure_is_rho2_dE_ref(m, J2v):
+    """p_ref = rho^2 dE_ref/drho (Section 2.3), by central differences of the
+    reference energy, and the closed-form derivatives used by the sound speed."""
+    J2 = t([J2v])
+    for x in (0.8, 1.0, 1.15, 1.4):
+        rho = m["rho0"] * x
+        h = rho * 1e-6
+        dE = (C.e_ref(m, t([rho + h]), J2) - C.e_ref(m, t([rho - h]), J2)).item() / (2 * h)
+        pr = C.p_ref(m, t([rho]), J2).item()
+        assert abs(rho * rho * dE - pr) <= 1e-6 * max(abs(pr), 1e5), (x, rho * rho * dE, pr)
+        dp = (C.p_ref(m, t([rho + h]), J2) - C.p_ref(m, t([rho - h]), J2)).item() / (2 * h)
+        assert abs(dp - C.dp_ref_drho(m, t([rho]), J2).item()) <= 1e-6 * abs(dp) + 1e-3
+        assert abs(dE - C.de_ref_drho(m, t([rho]), J2).item()) <= 1e-6 * abs(dE) + 1e-9
+
+
+def test_romenskii_copper_at_reference_density():
+    """At rho0 the cold curves vanish, the bulk sound speed is K0 / rho0 and the
+    shear modulus is G0; G scales as (rho / rho0)^(beta + 1) = x^4."""
+    r0 = t([CU["rho0"]])
+    z = t([0.0])
+    assert C.p_ref(CU, r0, z).item() == 0.0 and C.e_ref(CU, r0, z).item() == 0.0
+    c2 = C.material_sound_speed2(CU, r0, t([0.0]), z).item()
+    assert abs(c2 / (136.5e9 / 8930.0) - 1) < 1e-12
+    assert C.shear_modulus(CU, r0).item() == 39.4e9
+    assert abs(C.shear_modulus(CU, r0 * 1.1).item() / 39.4e9 - 1.1 ** 4) < 1e-12
+
+
+def test_jwl_reference_pressure_at_rho0():
+    """p_ref(rho0) = A e^(-R1) + B e^(-R2) with the table's LX-17 reactant
+    constants: 778.1e11 e^-11.3 - 0.0503e11 e^-1.13 = -6.6212e8 Pa."""
+    pr = C.p_ref(LX, t([1905.0]), t([0.0])).item()
+    assert abs(pr / (778.1e11 * math.exp(-11.3) - 0.0503e11 * math.exp(-1.13)) - 1) < 1e-12
+    assert abs(pr / -6.6212e8 - 1) < 1e-4
+
+
+@pytest.mark.parametrize("m", [CU, LX], ids=["romenskii", "jwl"])
+def test_sound_speed_is_isentropic_derivative_other_families(m):
+    """c^2 = (dp/drho)_s along de = p / rho^2 drho for the Romenskii and JWL
+    closures (pure material, strained for Romenskii)."""
+    rho0, p0 = m["rho0"] * 1.05, 3e9
+    J2 = t([1e-4 if m is CU else 0.0])
+    phis = [t([1.0]), t([0.0])]
+    mats = [m, GAS]
+
+    def p_of(rho, e):
+        return C.mixture_pressure(phis, [t([rho]), t([1.0])], t([rho * e]), J2, mats).item()
+
+    e0 = C.material_energy(m, t([rho0]), t([p0]), J2).item()
+    h = 1e-3
+    num = (p_of(rho0 + h, e0 + p0 / rho0 ** 2 * h) - p_of(rho0 - h, e0 - p0 / rho0 ** 2 * h)) / (2 * h)
+    c2 = C.material_sound_speed2(m, t([rho0]), t([p0]), J2).item()
+    assert abs(num - c2) / c2 < 1e-6

@@ -218,3 +218,14 @@ def test_plastic_mixed_solid_air_cell_keeps_the_solid_share_of_its_yield_strain(
     assert abs(got / 3.842337e-4 - 1) < 1e-6, got
     got = _relaxed_J([W.SOLID, AIR], 0.5, 1e-3)
     assert abs(got / 1.17647059e-4 - 1) < 1e-6, got
+
+
+def test_romenskii_copper_longitudinal_speed_pulse():
+    """A small pressure pulse in Romenskii copper at rest (Section 2.3 closure,
+    the Section 4.1 table) runs at the closed-form longitudinal speed
+    sqrt((K0 + 4/3 G0) / rho0) = 4600.6 m/s of the cold curve at rho0."""
+    cu = W.COPPER_ROMENSKII
+    speed, c2, cL2 = _pulse_speed([cu, cu], 0.5, 8930.0, 8930.0, 1e5, 1000.0)
+    exact = math.sqrt((136.5e9 + 4.0 / 3.0 * 39.4e9) / 8930.0)
+    assert abs(math.sqrt(cL2) / exact - 1) < 1e-6
+    assert abs(speed / exact - 1) < 1e-3, (speed, exact)

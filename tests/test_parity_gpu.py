@@ -16,10 +16,13 @@ import pytest
 import torch
 
 from paper_2009_14555_gb300 import workloads as W
-from tests.parity_util import cons_l1, oracle_prim, oracle_run, prim_l1
+from tests.parity_util import cons_l1, cons_max, oracle_prim, oracle_run, prim_l1, record
 
 pytestmark = pytest.mark.gpu
 TOL = 1e-10
+# element-wise bar (max |gpu - oracle| over the field maximum) of the strict
+# cases: a single cell cannot sit far off while the L1 sum stays below TOL
+TOL_MAX = 1e-8
 
 
 def gpu_run(wl, steps, dt_fixed=None, precision="fp64"):
@@ -52,19 +55,23 @@ def oracle_spread(wl, steps, o):
     return [cons_l1(wl, op[k], o[k]) for k in range(len(o))]
 
 
-def assert_parity(wl, steps, tol=TOL, calibrate=False):
+def assert_parity(wl, steps, tol=TOL, calibrate=False, name=None):
     g, gp, gdt = gpu_run(wl, steps)
     o, odt = oracle_run(wl, steps)
+    name = name or f"{wl.name}_{steps}"
+    err = np.max([cons_l1(wl, g[k], o[k]) for k in range(len(o))], axis=0)
+    emax = np.max([cons_max(wl, g[k], o[k]) for k in range(len(o))], axis=0)
     if calibrate:
-        spread = oracle_spread(wl, steps, o)
-        for k in range(len(o)):
-            err = cons_l1(wl, g[k], o[k])
-            bar = np.maximum(tol, 10.0 * spread[k])
-            assert (err <= bar).all(), (k, err, spread[k])
+        spread = np.max(oracle_spread(wl, steps, o), axis=0)
+        bar = np.maximum(tol, 10.0 * spread)
+        record(name, steps=steps, l1=err, max_rel=emax, oracle_spread_l1=spread, bar=bar,
+               within_1e10=bool((err <= TOL).all()))
+        assert (err <= bar).all(), (err, spread)
         return
+    record(name, steps=steps, l1=err, max_rel=emax)
+    assert err.max() <= tol, err
+    assert emax.max() <= TOL_MAX, emax
     for k in range(len(o)):
-        err = cons_l1(wl, g[k], o[k])
-        assert err.max() <= tol, (k, err)
         np.testing.assert_allclose(gdt[:, k], np.array(odt[k]), rtol=1e-11)
     op = oracle_prim(wl, o)
     for k in range(len(o)):
@@ -178,4 +185,48 @@ def test_nonphysical_state_is_flagged():
     s.step(1)
     rc, bp, bc = s.check()
     assert rc == -4 and bp == 0
+    s.close()
+
+
+def test_2d_shock_disc_thinc_100_steps():
+    """The 100-step float64 bar with THINC on in 2D (the shock-disc of the 512^2
+    configuration at 48^2): the recorded errors say whether it meets 1e-10
+    outright; the bar is 1e-10 or 10x the oracle's one-ulp spread."""
+    wl = W.shock_disc_2d(48, steps=100, shock_x=0.28)
+    assert_parity(wl, 100, calibrate=True, name="2d_shock_disc_thinc_48_100")
+
+
+def _vanleer(wl):
+    wl.limiter = "vanleer"
+    return wl
+
+
+def test_1d_solid_gas_vanleer_100_steps():
+    assert_parity(_vanleer(W.solid_gas_1d(1000, steps=100)), 100, name="1d_solid_gas_vanleer_1000_100")
+
+
+def test_2d_shock_disc_vanleer():
+    wl = _vanleer(W.shock_disc_2d(40, steps=30))
+    wl.thinc = False
+    assert_parity(wl, 30, name="2d_shock_disc_vanleer_40_30")
+
+
+def test_2d_reactive_vanleer_thinc():
+    assert_parity(_vanleer(W.reactive_plate_2d(64, 32, steps=20)), 20, calibrate=True,
+                  name="2d_reactive_vanleer_thinc_64x32_20")
+
+
+def test_vanleer_hancock_1d():
+    wl = _vanleer(W.solid_gas_1d(400, steps=40))
+    wl.scheme = "hancock"
+    assert_parity(wl, 40, name="1d_solid_gas_vanleer_hancock_400_40")
+
+
+def test_vanleer_adjoint_refused():
+    from paper_2009_14555_gb300.solver import Solver
+    wl = _vanleer(W.solid_gas_1d(64, steps=2))
+    s = Solver.from_workload(wl)
+    s.set_prim([wl.patches[0].prim])
+    with pytest.raises(RuntimeError):
+        s.adj_forward(2, every=1, material=0)
     s.close()
