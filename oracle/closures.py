@@ -97,7 +97,7 @@ def shear_modulus(m, rho):
     """G(rho) of Section 2.3 (constant except for the Romenskii solid)."""
     if eos_kind(m) == "romenskii":
         return m["G"] * (rho / m["rho0"]) ** (m["beta_r"] + 1.0)
-    return torch.full_like(rho, m["G"]) if torch.is_tensor(rho) else m["G"]
+    return m["G"] + 0.0 * rho
 
 
 def _shear_p_factor(m, rho):
