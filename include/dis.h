@@ -57,8 +57,23 @@ enum { DIS_PLASTIC_NONE = 0, DIS_PLASTIC_PERFECT = 1, DIS_PLASTIC_RATE = 2 };
 
 enum { DIS_RATE_ARRHENIUS = 0, DIS_RATE_SQRT = 1 };
 
-/* One material: stiffened-gas Mie-Grueneisen closure (Section 2.3) with a
- * constant shear modulus G, plasticity (Section 2.3.2: none, perfect = the
+/* Equation-of-state family of a material (Section 2.3), all Mie-Grueneisen
+ * with a constant Gruneisen coefficient Gamma = gamma - 1:
+ *   DIS_EOS_STIFFENED  reference pressure -gamma p_inf, energy e_inf, shear
+ *                      modulus G (the default: zero-filled);
+ *   DIS_EOS_ROMENSKII  elastic solid: reference energy
+ *                      K0 / (2 rho0 a^2) ((rho/rho0)^a - 1)^2 and its pressure
+ *                      rho^2 dE/drho, shear modulus G (rho/rho0)^(b + 1)
+ *                      (a, b = alpha, beta; G is G0; p_inf, e_inf unused);
+ *   DIS_EOS_JWL        reference pressure A e^(-R1 rho0/rho) + B e^(-R2 rho0/rho),
+ *                      energy A / (R1 rho0) e^(-R1 rho0/rho) + B / (R2 rho0)
+ *                      e^(-R2 rho0/rho) (a fluid: G must be 0).
+ * The shear energy G(rho) J^2 / rho enters the reference curves.  The
+ * reactive material must be a stiffened gas (ideal: p_inf = 0). */
+enum { DIS_EOS_STIFFENED = 0, DIS_EOS_ROMENSKII = 1, DIS_EOS_JWL = 2 };
+
+/* One material: Mie-Grueneisen closure (Section 2.3; stiffened gas by
+ * default, see above) with shear modulus G, plasticity (Section 2.3.2: none, perfect = the
  * chi0 -> infinity limit of ideal plasticity, or ideal plasticity with rate
  * chi0), and for a reactive material an ideal-gas reactant/product pair of
  * equal gamma and C_V with heat release Q (Section 2.3.1) and a rate law for
@@ -79,6 +94,10 @@ typedef struct {
   double Q, cv, A, T_act;
   int32_t rate_law; /* DIS_RATE_ARRHENIUS or DIS_RATE_SQRT */
   double p_ign;     /* DIS_RATE_SQRT: pressure above which the reaction runs, Pa */
+  int32_t eos;      /* DIS_EOS_STIFFENED, DIS_EOS_ROMENSKII or DIS_EOS_JWL */
+  double rho0;      /* Romenskii, JWL: reference density */
+  double K0, alpha, beta;                 /* Romenskii: bulk modulus, exponents */
+  double jwl_A, jwl_B, jwl_R1, jwl_R2;    /* JWL constants */
 } dis_material;
 
 /* One Cartesian patch (the single-grid unit of Section 3): nx x ny cells of
@@ -230,20 +249,19 @@ long long dis_last_launches(const dis_ctx* ctx);
  * are DIS_NVARIANTS variants v: tile shape v % 3 (2D 16 x 15, 32 x 15, 32 x 7
  * cells per CTA of 256, 512, 256 threads; 1D 122, 250, 506 cells per CTA of
  * 128, 256, 512 threads) and register budget v / 3 (2D: 768 or 1024 resident
- * threads per SM; 1D: no limit, or at most 64 registers per thread); in
- * planar 2D, variants 6 .. 11 are the same shapes and budgets in a
- * persistent form (as many CTAs as fit at once, each looping over tiles, the
- * update of one tile overlapping the halo recovery of the next).  The first
+ * threads per SM; 1D: no limit, or at most 64 registers per thread).  The
+ * limiter is compiled into the face code: a DIS_VANLEER context has one
+ * variant (5 in 2D, 1 in 1D).  The first
  * dis_step times one step of every variant (the last stage writing a scratch
  * buffer, so the state is unchanged) and keeps the fastest.  Returns the
  * chosen shape (0 x 0 before tuning or for float64 contexts), precomputed = 0
  * (kept for compatibility), and, if step_ms is not NULL, the tuned time per
  * step of each variant. */
-#define DIS_NVARIANTS 12
+#define DIS_NVARIANTS 6
 int dis_tile_choice(const dis_ctx* ctx, int* tx, int* ty, int* precomputed, double* step_ms);
 
-/* Fix the FP32-bulk stage variant (0 .. DIS_NVARIANTS - 1 in planar 2D,
- * 0 .. 5 otherwise) or return to tuning on the next step (-1).  For tests and measurements; the
+/* Fix the FP32-bulk stage variant (0 .. DIS_NVARIANTS - 1; a DIS_VANLEER
+ * context only its one variant) or return to tuning on the next step (-1).  For tests and measurements; the
  * result of a step does not depend on the variant beyond float32 rounding
  * order.  DIS_EINVAL for float64 contexts or an out-of-range variant. */
 int dis_set_variant(dis_ctx* ctx, int variant);
@@ -326,8 +344,9 @@ int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
  * In a DIS_CYLINDRICAL context the geometric source of Section 3 is reversed
  * with the rest of the stage, and J is the same plain sum over cells (no
  * factor r).  Returns DIS_EINVAL (bad arguments, a DIS_HANCOCK context: the
- * adjoint covers the Runge-Kutta scheme, or a DIS_VANLEER context: it covers
- * the minmod limiter), DIS_ESTATE (no state), DIS_ENOMEM, DIS_ECUDA.
+ * adjoint covers the Runge-Kutta scheme, a DIS_VANLEER context: it covers
+ * the minmod limiter, or a material that is not a stiffened gas), DIS_ESTATE
+ * (no state), DIS_ENOMEM, DIS_ECUDA.
  * Synchronises. */
 int dis_adj_forward(dis_ctx* ctx, int n_steps, int checkpoint_every, int objective_material,
                     const double* dt_in, double* dt_out, double* J_out);

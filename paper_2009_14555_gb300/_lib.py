@@ -17,10 +17,11 @@ DIS_CONSERVATIVE, DIS_PRIMITIVE = 0, 1
 DIS_FP64, DIS_FP32_BULK = 0, 1
 DIS_RK3, DIS_HANCOCK = 0, 1
 DIS_MINMOD, DIS_VANLEER = 0, 1
+DIS_EOS_STIFFENED, DIS_EOS_ROMENSKII, DIS_EOS_JWL = 0, 1, 2
 DIS_PLANAR, DIS_CYLINDRICAL = 0, 1
 DIS_RATE_ARRHENIUS, DIS_RATE_SQRT = 0, 1
 DIS_NPARAM = 6  # per material l: G, sigma_y, Q at 3 l + k
-DIS_NVARIANTS = 12  # FP32-bulk stage variants: 3 tile shapes x 2 register budgets x (per tile, persistent)
+DIS_NVARIANTS = 6  # FP32-bulk stage variants: 3 tile shapes x 2 register budgets
 
 
 class DisStats(ctypes.Structure):
@@ -35,7 +36,9 @@ class DisMaterial(ctypes.Structure):
     _fields_ = [("gamma", c_double), ("p_inf", c_double), ("e_inf", c_double), ("G", c_double),
                 ("plastic", c_int32), ("sigma_y", c_double), ("chi0", c_double),
                 ("reactive", c_int32), ("Q", c_double), ("cv", c_double), ("A", c_double),
-                ("T_act", c_double), ("rate_law", c_int32), ("p_ign", c_double)]
+                ("T_act", c_double), ("rate_law", c_int32), ("p_ign", c_double), ("eos", c_int32),
+                ("rho0", c_double), ("K0", c_double), ("alpha", c_double), ("beta", c_double),
+                ("jwl_A", c_double), ("jwl_B", c_double), ("jwl_R1", c_double), ("jwl_R2", c_double)]
 
 
 class DisPatch(ctypes.Structure):

@@ -288,83 +288,62 @@ StepArgs32 base_args32(dis_ctx* c) {
   return a;
 }
 
-template <int DIM, bool RX, int TX, int TY, int NT, int MINB, bool CYL>
+template <int DIM, bool RX, int TX, int TY, int NT, int MINB, bool CYL, int LIM = 0>
 void stage_fused_c(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
   constexpr size_t smem = fused32_smem<DIM, RX, TX, TY>();
   static bool attr_set = false;  // per instantiation, per process
   if (!attr_set) {
-    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT, MINB, CYL>,
+    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT, MINB, CYL, LIM>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT, MINB, CYL>,
+    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT, MINB, CYL, LIM>,
                          cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr_set = true;
   }
-  k_stage32<DIM, RX, TX, TY, NT, MINB, CYL><<<(unsigned)c->tiles[shape].size(), NT, smem, st>>>(
+  k_stage32<DIM, RX, TX, TY, NT, MINB, CYL, LIM><<<(unsigned)c->tiles[shape].size(), NT, smem, st>>>(
       c->phys, c->physf, a, c->d_tiles[shape]);
 }
 
-// Persistent stage kernel (planar 2D): as many CTAs as fit on the device at
-// once, each looping over the tiles.
-template <int DIM, bool RX, int TX, int TY, int NT, int MINB>
-void stage_persistent(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
-  constexpr size_t smem = fused32_smem<DIM, RX, TX, TY>();
-  static int grid = 0;  // per instantiation, per process
-  if (!grid) {
-    cudaFuncSetAttribute(k_stage32p<DIM, RX, TX, TY, NT, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    cudaFuncSetAttribute(k_stage32p<DIM, RX, TX, TY, NT, MINB>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         100);
-    int per_sm = 0, sms = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage32p<DIM, RX, TX, TY, NT, MINB>, NT, smem);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    grid = std::max(1, per_sm) * std::max(1, sms);
-  }
-  const int nt = (int)c->tiles[shape].size();
-  k_stage32p<DIM, RX, TX, TY, NT, MINB><<<(unsigned)std::min(grid, nt), NT, smem, st>>>(
-      c->phys, c->physf, a, c->d_tiles[shape], nt);
-}
-
 // Planar and cylindrical contexts run separate instantiations, so the
-// geometric source costs the planar kernels nothing.  persist: the
-// persistent form (planar 2D only; the cylindrical update rereads the tile's
-// primitives).
-template <int DIM, bool RX, int TX, int TY, int NT, int MINB>
-void stage_fused(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape, bool persist = false) {
-  if constexpr (DIM == 2) {
-    if (persist && !c->phys.cyl) {
-      stage_persistent<DIM, RX, TX, TY, NT, MINB>(c, st, a, shape);
-      return;
-    }
-  }
-  if (c->phys.cyl) stage_fused_c<DIM, RX, TX, TY, NT, MINB, true>(c, st, a, shape);
-  else stage_fused_c<DIM, RX, TX, TY, NT, MINB, false>(c, st, a, shape);
+// geometric source costs the planar kernels nothing.
+template <int DIM, bool RX, int TX, int TY, int NT, int MINB, int LIM = 0>
+void stage_fused(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
+  if (c->phys.cyl) stage_fused_c<DIM, RX, TX, TY, NT, MINB, true, LIM>(c, st, a, shape);
+  else stage_fused_c<DIM, RX, TX, TY, NT, MINB, false, LIM>(c, st, a, shape);
 }
 
-// FP32-bulk stage variants v = shape + 3 budget + 6 persist: the 3 tile
-// shapes x two register budgets (2D: 768 or 1024 resident threads per SM
-// requested from the register allocator; 1D: no limit, or 64 registers per
-// thread) x (one CTA per tile, or the persistent form: planar 2D only).
+// FP32-bulk stage variants v = shape + 3 budget: the 3 tile shapes x two
+// register budgets (2D: 768 or 1024 resident threads per SM requested from
+// the register allocator; 1D: no limit, or 64 registers per thread).  The
+// limiter is a compile-time choice of the face code: minmod contexts have
+// every variant; van Leer contexts one (2D: 32 x 7 tile, 1024 threads per
+// SM; 1D: 250-cell tile).
+int vanleer_variant(const dis_ctx* c) { return c->dim == 2 ? 5 : 1; }
 bool variant_valid(const dis_ctx* c, int v) {
-  return v >= 0 && v < DIS_NVARIANTS && (v < 6 || (c->dim == 2 && !c->phys.cyl));
+  if (c->phys.limiter) return v == vanleer_variant(c);
+  return v >= 0 && v < DIS_NVARIANTS;
 }
 
 // MINB: resident CTAs of 256 threads per SM requested (3 or 4); the
 // 512-thread tile asks for half as many.
 template <int DIM, bool RX, int MINB>
-void stage_kernel_2d(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape, bool persist) {
-  if (shape == 0) stage_fused<DIM, RX, 16, 15, 256, MINB>(c, st, a, shape, persist);
-  else if (shape == 1) stage_fused<DIM, RX, 32, 15, 512, MINB / 2>(c, st, a, shape, persist);
-  else stage_fused<DIM, RX, 32, 7, 256, MINB>(c, st, a, shape, persist);
+void stage_kernel_2d(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
+  if (shape == 0) stage_fused<DIM, RX, 16, 15, 256, MINB>(c, st, a, shape);
+  else if (shape == 1) stage_fused<DIM, RX, 32, 15, 512, MINB / 2>(c, st, a, shape);
+  else stage_fused<DIM, RX, 32, 7, 256, MINB>(c, st, a, shape);
 }
 
 // The stage kernel of variant v.
 template <int DIM, bool RX>
 void stage_kernel_v(dis_ctx* c, cudaStream_t st, StepArgs32& a, int v) {
   const int shape = v % 3;
+  if (c->phys.limiter) {  // van Leer: the one instantiation
+    if constexpr (DIM == 2) stage_fused<DIM, RX, 32, 7, 256, 4, 1>(c, st, a, 2);
+    else stage_fused<DIM, RX, 250, 1, 256, 1, 1>(c, st, a, 1);
+    return;
+  }
   if constexpr (DIM == 2) {
-    const bool persist = v >= 6;
-    if ((v % 6) >= 3) stage_kernel_2d<DIM, RX, 4>(c, st, a, shape, persist);
-    else stage_kernel_2d<DIM, RX, 3>(c, st, a, shape, persist);
+    if (v >= 3) stage_kernel_2d<DIM, RX, 4>(c, st, a, shape);
+    else stage_kernel_2d<DIM, RX, 3>(c, st, a, shape);
   } else if (v < 3) {
     if (shape == 0) stage_fused<DIM, RX, 122, 1, 128, 1>(c, st, a, shape);
     else if (shape == 1) stage_fused<DIM, RX, 250, 1, 256, 1>(c, st, a, shape);
@@ -390,32 +369,37 @@ void cfl_pass32(dis_ctx* c, cudaStream_t st, unsigned long long* rate) {
 // Persistent 1D batch kernel (FP32-bulk), variant v: tile length v % 3,
 // 64 registers per thread for v >= 3; n steps in one launch, one CTA per
 // problem.  scratch_last (tuning, n = 1): the step ends in buffer 1.
-template <bool RX, int TX, int NT, int MINB, bool CYL>
+template <bool RX, int TX, int NT, int MINB, bool CYL, int LIM = 0>
 void batch_fused_c(dis_ctx* c, cudaStream_t st, const StepArgs32& a, int n, int scratch_last, int shape) {
   constexpr size_t smem = fused32_smem<1, RX, TX, 1>();
   static bool attr_set = false;  // per instantiation, per process
   if (!attr_set) {
-    cudaFuncSetAttribute(k_batch32<RX, TX, NT, MINB, CYL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_batch32<RX, TX, NT, MINB, CYL, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    cudaFuncSetAttribute(k_batch32<RX, TX, NT, MINB, CYL>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_batch32<RX, TX, NT, MINB, CYL, LIM>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         100);
     attr_set = true;
   }
   Bufs32 b;
   for (int k = 0; k < 3; ++k) b.q[k] = c->q32[k];
-  k_batch32<RX, TX, NT, MINB, CYL><<<(unsigned)c->np, NT, smem, st>>>(
+  k_batch32<RX, TX, NT, MINB, CYL, LIM><<<(unsigned)c->np, NT, smem, st>>>(
       c->phys, c->physf, a, b, c->rate, c->d_order, c->d_tile0[shape], c->d_tiles[shape], n, scratch_last,
       c->rate_valid ? 1 : 0);
 }
 
-template <bool RX, int TX, int NT, int MINB>
+template <bool RX, int TX, int NT, int MINB, int LIM = 0>
 void batch_fused(dis_ctx* c, cudaStream_t st, const StepArgs32& a, int n, int scratch_last, int shape) {
-  if (c->phys.cyl) batch_fused_c<RX, TX, NT, MINB, true>(c, st, a, n, scratch_last, shape);
-  else batch_fused_c<RX, TX, NT, MINB, false>(c, st, a, n, scratch_last, shape);
+  if (c->phys.cyl) batch_fused_c<RX, TX, NT, MINB, true, LIM>(c, st, a, n, scratch_last, shape);
+  else batch_fused_c<RX, TX, NT, MINB, false, LIM>(c, st, a, n, scratch_last, shape);
 }
 
 template <bool RX>
 void batch_kernel_v(dis_ctx* c, cudaStream_t st, const StepArgs32& a, int n, int scratch_last, int v) {
   const int shape = v % 3;
+  if (c->phys.limiter) {  // van Leer: the one instantiation (250-cell tiles)
+    batch_fused<RX, 250, 256, 1, 1>(c, st, a, n, scratch_last, 1);
+    return;
+  }
   if (v < 3) {
     if (shape == 0) batch_fused<RX, 122, 128, 1>(c, st, a, n, scratch_last, shape);
     else if (shape == 1) batch_fused<RX, 250, 256, 1>(c, st, a, n, scratch_last, shape);
@@ -800,6 +784,15 @@ MatDev to_dev(const dis_material& m) {
   d.plastic = m.plastic;
   d.reactive = m.reactive;
   d.law = m.reactive ? m.rate_law : 0;
+  d.eos = m.eos;
+  d.rho0 = m.rho0;
+  d.K0 = m.K0;
+  d.ar = m.alpha;
+  d.br = m.beta;
+  d.jA = m.jwl_A;
+  d.jB = m.jwl_B;
+  d.jR1 = m.jwl_R1;
+  d.jR2 = m.jwl_R2;
   d.pign = m.reactive ? m.p_ign : 0.0;
   d.iGm1 = 1.0 / (m.gamma - 1.0);
   d.gi = m.gamma * d.iGm1;
@@ -888,6 +881,14 @@ int dis_set_materials(dis_ctx* c, const dis_material* m, int n) {
     if (m[l].plastic < 0 || m[l].plastic > 2) return fail(DIS_EINVAL, "dis_set_materials: bad plastic");
     if ((l == c->y) != (m[l].reactive != 0))
       return fail(DIS_EINVAL, "dis_set_materials: reactive flag disagrees with the context");
+    if (m[l].eos < DIS_EOS_STIFFENED || m[l].eos > DIS_EOS_JWL)
+      return fail(DIS_EINVAL, "dis_set_materials: unknown eos %d", m[l].eos);
+    if (m[l].eos == DIS_EOS_ROMENSKII && !(m[l].rho0 > 0 && m[l].K0 > 0 && m[l].alpha > 0 && m[l].beta >= 0))
+      return fail(DIS_EINVAL, "dis_set_materials: Romenskii needs rho0, K0, alpha > 0 and beta >= 0");
+    if (m[l].eos == DIS_EOS_JWL && !(m[l].rho0 > 0 && m[l].jwl_R1 > 0 && m[l].jwl_R2 > 0 && m[l].G == 0))
+      return fail(DIS_EINVAL, "dis_set_materials: JWL needs rho0, R1, R2 > 0 and G = 0");
+    if (m[l].reactive && m[l].eos != DIS_EOS_STIFFENED)
+      return fail(DIS_EINVAL, "dis_set_materials: the reactive material must be a stiffened (ideal) gas");
     if (m[l].reactive && (m[l].p_inf != 0 || m[l].G != 0 || !(m[l].cv > 0)))
       return fail(DIS_EINVAL, "dis_set_materials: a reactive material must be an ideal gas with cv > 0");
     if (m[l].reactive && (m[l].rate_law < 0 || m[l].rate_law > 1 || !std::isfinite(m[l].p_ign) ||

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) k_cfl_static(Phys P, const double* __rest
     const Strain s = strain_of(b[L::V11 * n], V12, V21, b[L::V22 * n], b[L::V33 * n]);
     const double KE = 0.5 * (mx * u + my * v);
     const double pr = (b[L::E * n] - KE - ref_energy(P, phi, a1, a2, arl, s.J2)) / xi_of(P, phi);
-    const double cL2 = cL2_of(P, phi, rho, pr, s.J2);
+    const double cL2 = cL2_of(P, phi, rho, pr, s.J2, a1 / phi, a2 / (1.0 - phi));
     const double cL = sqrt(fmax(cL2, 0.0));
     r = (fabs(u) + cL) / sp.dx;
     if (DIM == 2) r += (fabs(v) + cL) / sp.dy;
@@ -107,6 +107,15 @@ MatDev dev_material(const dis_material& m) {
   d.gG = m.gamma * m.G * d.iGm1;
   d.GoG = m.G * d.iGm1;
   d.reactive = m.reactive;
+  d.eos = m.eos;
+  d.rho0 = m.rho0;
+  d.K0 = m.K0;
+  d.ar = m.alpha;
+  d.br = m.beta;
+  d.jA = m.jwl_A;
+  d.jB = m.jwl_B;
+  d.jR1 = m.jwl_R1;
+  d.jR2 = m.jwl_R2;
   return d;
 }
 

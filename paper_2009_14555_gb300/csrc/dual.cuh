@@ -79,6 +79,11 @@ __device__ __forceinline__ Dual cbrt(Dual a) {
   const double c = ::cbrt(a.v);
   return Dual(c, a.d / (3.0 * c * c));
 }
+__device__ __forceinline__ Dual log(Dual a) { return Dual(::log(a.v), a.d / a.v); }
+__device__ __forceinline__ Dual powr(Dual a, Dual b) {
+  const double v = ::pow(a.v, b.v);
+  return Dual(v, v * (b.d * ::log(a.v) + b.v * a.d / a.v));
+}
 __device__ __forceinline__ Dual exp(Dual a) {
   const double e = ::exp(a.v);
   return Dual(e, e * a.d);

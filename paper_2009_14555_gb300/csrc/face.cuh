@@ -247,7 +247,8 @@ __device__ __forceinline__ void sources(const PhysT<T>& P, double dt, T* o) {
     v12 = o[L::V12];
     v21 = o[L::V21];
   }
-  plastic(P, o[L::PHI], T(dt), o[L::V11], v12, v21, o[L::V22], o[L::V33]);
+  plastic(P, o[L::PHI], T(dt), o[L::V11], v12, v21, o[L::V22], o[L::V33], o[L::A1] / o[L::PHI],
+          o[L::A2] / (1.0 - o[L::PHI]));
   if constexpr (DIM == 2) {
     o[L::V12] = v12;
     o[L::V21] = v21;

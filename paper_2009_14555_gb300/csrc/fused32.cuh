@@ -35,7 +35,7 @@ struct FSlots {
   static constexpr int PK = VB + 1, DD = VB + 2, N = VB + 3;
 };
 
-template <int DIM, bool RX, int DIR>
+template <int DIM, bool RX, int DIR, int LIM>
 __device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__ Wsm, int HX, int HY, int hx,
                                        int hy, float dxn, float dxt, float* __restrict__ Fsm, int nfaces,
                                        int fidx) {
@@ -69,7 +69,7 @@ __device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__
         }
         return beta;
       };
-      c[s] = phi_cand_f(ph[s], ph[s + 1], ph[s + 2], beta_of, P.thinc != 0, P.limiter);
+      c[s] = phi_cand_f<LIM>(ph[s], ph[s + 1], ph[s + 2], beta_of, P.thinc != 0);
     }
     float Lt, Rt;
     bvd_f(c[0], c[1], c[2], Lt, Rt);
@@ -90,11 +90,10 @@ __device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__
   ld(w2, k0 + sx);
   ld(w3, k0 + 2 * sx);
   PrimF wl, wr;
-  const int lim = P.limiter;
 #define DIS_RECF(fld)                                            \
   {                                                              \
-    const float s1 = limited_f(w1.fld - w0.fld, w2.fld - w1.fld, lim); \
-    const float s2 = limited_f(w2.fld - w1.fld, w3.fld - w2.fld, lim); \
+    const float s1 = limited_f<LIM>(w1.fld - w0.fld, w2.fld - w1.fld); \
+    const float s2 = limited_f<LIM>(w2.fld - w1.fld, w3.fld - w2.fld); \
     wl.fld = w1.fld + 0.5f * s1;                                 \
     wr.fld = w2.fld - 0.5f * s2;                                 \
   }
@@ -220,7 +219,7 @@ __device__ __forceinline__ void fill_tile(const Phys& P, const PhysF& F, const S
 
 // Phase 2: all x faces ((TX + 1) per interior row) and y faces (TX per face
 // row, TY + 1 face rows) of the tile, in one loop so the threads stay busy.
-template <int DIM, bool RX, int TX, int TY, int NT>
+template <int DIM, bool RX, int TX, int TY, int NT, int LIM>
 __device__ __forceinline__ void faces_tile(const PhysF& F, const StepArgs32& A, const int4 t,
                                            float* __restrict__ sm) {
   using S = FSlots<DIM, RX>;
@@ -237,13 +236,13 @@ __device__ __forceinline__ void faces_tile(const PhysF& F, const StepArgs32& A, 
       const int fx = f % (TX + 1), fy = f / (TX + 1);
       const int i = i0 + fx, j = j0 + fy;  // face between cells i-1 and i
       if (i > pd.nx || (DIM == 2 && j >= pd.ny)) continue;
-      face32<DIM, RX, 0>(F, Wsm, HX, HY, fx + NG - 1, DIM == 2 ? fy + NG : 0, dxf, dyf, Fxs, NFX, f);
+      face32<DIM, RX, 0, LIM>(F, Wsm, HX, HY, fx + NG - 1, DIM == 2 ? fy + NG : 0, dxf, dyf, Fxs, NFX, f);
     } else if constexpr (DIM == 2) {
       const int g = f - NFX;
       const int fx = g % TX, fy = g / TX;
       const int i = i0 + fx, j = j0 + fy;  // face between rows j-1 and j
       if (i >= pd.nx || j > pd.ny) continue;
-      face32<DIM, RX, 1>(F, Wsm, HX, HY, fx + NG, fy + NG - 1, dyf, dxf, Fys, NFY, g);
+      face32<DIM, RX, 1, LIM>(F, Wsm, HX, HY, fx + NG, fy + NG - 1, dyf, dxf, Fys, NFY, g);
     }
   }
 }
@@ -335,7 +334,7 @@ __device__ __forceinline__ void update_tile(const Phys& P, const PhysF& F, const
       }
       const StrainF st = strain_f(Wsm[L::V11 * plane + kc], v12, v21, Wsm[L::V22 * plane + kc],
                                   Wsm[L::V33 * plane + kc]);
-      const float Gm2 = 2.f * (wphi * F.m[0].GoG + (1.f - wphi) * F.m[1].GoG) / xi_f(F, wphi);
+      const float Gm2 = 2.f * Gmix_f(F, wphi, Wsm[L::A1 * plane + kc], Wsm[L::A2 * plane + kc]);
       const float srr = -wp + Gm2 * st.H11, szr = Gm2 * st.H12, stt = -wp + Gm2 * st.H33;
       const float r = (float)pd.x0 + ((float)i + 0.5f) * dxf;
       const float ir = 1.f / r;
@@ -389,20 +388,23 @@ __device__ __forceinline__ void update_tile(const Phys& P, const PhysF& F, const
       const float ophf = ophi.h;
       float v12 = 0.f, v21 = 0.f;
       if constexpr (DIM == 2) { v12 = o[L::V12]; v21 = o[L::V21]; }
+      const float oph2 = (1.f - ophf) - ophi.l;
+      const float or1 = o[L::A1] / ophf, or2 = o[L::A2] / oph2;
       if (ophf > 1e-3f && ophf < 1.f - 1e-3f) {
         const double dt = ff_val(dth_sh, dtl_sh);
         double d11 = o[L::V11], d12 = v12, d21 = v21, d22 = o[L::V22], d33 = o[L::V33];
-        plastic(P, ff_val(ophi.h, ophi.l), dt, d11, d12, d21, d22, d33);
+        const double ph = ff_val(ophi.h, ophi.l);
+        plastic(P, ph, dt, d11, d12, d21, d22, d33, (double)o[L::A1] / ph, (double)o[L::A2] / (1.0 - ph));
         o[L::V11] = (float)d11; v12 = (float)d12; v21 = (float)d21; o[L::V22] = (float)d22; o[L::V33] = (float)d33;
       } else {
-        plastic_f(F, ophf, dtf, o[L::V11], v12, v21, o[L::V22], o[L::V33]);
+        plastic_f(F, ophf, dtf, o[L::V11], v12, v21, o[L::V22], o[L::V33], or1, or2);
       }
       if constexpr (DIM == 2) { o[L::V12] = v12; o[L::V21] = v21; }
       if constexpr (RX) {
         const int y = P.y;
         const MatT<float>& m = F.m[y];
         const float ary = y == 0 ? o[L::A1] : o[L::A2];
-        const float phy = y == 0 ? ophf : (1.f - ophf) - ophi.l;
+        const float phy = y == 0 ? ophf : oph2;
         const float rr = o[L::A1] + o[L::A2];
         const float mx = o[L::MX];
         float my = 0.f;
@@ -410,7 +412,7 @@ __device__ __forceinline__ void update_tile(const Phys& P, const PhysF& F, const
         const float KE = 0.5f * (mx * mx + my * my) / rr;
         const StrainF s = strain_f(o[L::V11], v12, v21, o[L::V22], o[L::V33]);
         const float xi = xi_f(F, ophf);
-        const float p0 = (o[L::E] - KE - soft_ref_f(F, ophf, o[L::A1], o[L::A2], 0.f, s.J2)) / xi;
+        const float p0 = (o[L::E] - KE - soft_ref_f(F, ophf, o[L::A1], o[L::A2], 0.f, s.J2, or1, or2)) / xi;
         const float Tfac = m.iGm1 / ((ary / phy) * m.cv);
         const float Qx = m.Q / xi;
         auto fr_ = [&](float Lm) {
@@ -454,56 +456,22 @@ __device__ __forceinline__ void update_tile(const Phys& P, const PhysF& F, const
 // the tile's primitives and faces in the shared memory sm.  The stage kernel
 // runs it once per CTA; the persistent 1D batch kernel runs it for every tile
 // of its problem in turn (the caller synchronises the CTA between tiles).
-template <int DIM, bool RX, int TX, int TY, int NT, bool CYL = false>
+template <int DIM, bool RX, int TX, int TY, int NT, bool CYL = false, int LIM = 0>
 __device__ __forceinline__ void stage32_tile(const Phys& P, const PhysF& F, const StepArgs32& A, const int4 t,
                                              float* __restrict__ sm, unsigned* rate_cta) {
   __shared__ TileConst K;
   if (threadIdx.x == 0) tile_consts(P, A, t, K);
   fill_tile<DIM, RX, TX, TY, NT>(P, F, A, t, sm);
   __syncthreads();
-  faces_tile<DIM, RX, TX, TY, NT>(F, A, t, sm);
+  faces_tile<DIM, RX, TX, TY, NT, LIM>(F, A, t, sm);
   __syncthreads();
   update_tile<DIM, RX, TX, TY, NT, CYL>(P, F, A, t, sm, K, rate_cta);
 }
 
-template <int DIM, bool RX, int TX, int TY, int NT, int MINB, bool CYL = false>
+template <int DIM, bool RX, int TX, int TY, int NT, int MINB, bool CYL = false, int LIM = 0>
 __global__ void __launch_bounds__(NT, MINB) k_stage32(Phys P, PhysF F, StepArgs32 A, const int4* __restrict__ tiles) {
   extern __shared__ __align__(16) float sm[];
-  stage32_tile<DIM, RX, TX, TY, NT, CYL>(P, F, A, tiles[blockIdx.x], sm, nullptr);
-}
-
-// Persistent form of the stage kernel (planar 2D): CTA b takes tiles b,
-// b + gridDim.x, ... in turn.  The update of one tile and the halo recovery
-// of the next run in the same phase (both wait mostly on global memory), so
-// a tile costs two barriers, and no tail wave of CTAs is left at the end.
-// The update reads only the tile's face data (the primitive planes it would
-// read for the cylindrical source are being refilled), hence planar only.
-template <int DIM, bool RX, int TX, int TY, int NT, int MINB>
-__global__ void __launch_bounds__(NT, MINB) k_stage32p(Phys P, PhysF F, StepArgs32 A,
-                                                       const int4* __restrict__ tiles, int ntiles) {
-  extern __shared__ __align__(16) float sm[];
-  __shared__ TileConst K[2];
-  int t = blockIdx.x;
-  if (t >= ntiles) return;
-  int b = 0;
-  if (threadIdx.x == 0) tile_consts(P, A, tiles[t], K[0]);
-  fill_tile<DIM, RX, TX, TY, NT>(P, F, A, tiles[t], sm);
-  __syncthreads();
-  faces_tile<DIM, RX, TX, TY, NT>(F, A, tiles[t], sm);
-  __syncthreads();
-  for (;;) {
-    const int tn = t + gridDim.x;
-    const bool more = tn < ntiles;
-    if (more && threadIdx.x == 0) tile_consts(P, A, tiles[tn], K[b ^ 1]);
-    update_tile<DIM, RX, TX, TY, NT, false>(P, F, A, tiles[t], sm, K[b], nullptr);
-    if (more) fill_tile<DIM, RX, TX, TY, NT>(P, F, A, tiles[tn], sm);
-    __syncthreads();
-    if (!more) break;
-    faces_tile<DIM, RX, TX, TY, NT>(F, A, tiles[tn], sm);
-    __syncthreads();
-    t = tn;
-    b ^= 1;
-  }
+  stage32_tile<DIM, RX, TX, TY, NT, CYL, LIM>(P, F, A, tiles[blockIdx.x], sm, nullptr);
 }
 
 // CFL rate of the state at the start of a step (FP32-bulk), for the first
@@ -541,7 +509,7 @@ struct Bufs32 {
   float* q[3];
 };
 
-template <bool RX, int TX, int NT, int MINB, bool CYL = false>
+template <bool RX, int TX, int NT, int MINB, bool CYL = false, int LIM = 0>
 __global__ void __launch_bounds__(NT, MINB) k_batch32(Phys P, PhysF F, StepArgs32 A, Bufs32 B,
                                                       unsigned long long* rate, const int* __restrict__ order,
                                                       const int* __restrict__ tile0,
@@ -583,7 +551,7 @@ __global__ void __launch_bounds__(NT, MINB) k_batch32(Phys P, PhysF F, StepArgs3
       a.b = s0 ? 1.0 : (s1 ? 0.25 : 2.0 / 3.0);
       a.last = stg == 2;
       for (int t = ta; t < tb; ++t) {
-        stage32_tile<1, RX, TX, 1, NT, CYL>(P, F, a, tiles[t], sm, &rnext);
+        stage32_tile<1, RX, TX, 1, NT, CYL, LIM>(P, F, a, tiles[t], sm, &rnext);
         __syncthreads();
       }
     }

@@ -918,7 +918,8 @@ __device__ __forceinline__ void sources_vjp(const Phys& P, double dt, const doub
   if constexpr (RX) {
     // forward: V after the plastic step, then the reaction's frozen quantities
     double Vp[5] = {V[0], V[1], V[2], V[3], V[4]};
-    plastic(P, o[L::PHI], dt, Vp[0], Vp[1], Vp[2], Vp[3], Vp[4]);
+    plastic(P, o[L::PHI], dt, Vp[0], Vp[1], Vp[2], Vp[3], Vp[4], o[L::A1] / o[L::PHI],
+            o[L::A2] / (1.0 - o[L::PHI]));
     const int y = P.y;
     const MatDev& m = P.m[y];
     const double phi1 = o[L::PHI], a1 = o[L::A1], a2 = o[L::A2];

@@ -32,10 +32,20 @@ namespace dis {
 
 constexpr int NG = 3;  // ghost layers: a face's BVD choice reaches 3 cells out
 
+// Equation-of-state families of Section 2.3 (all with a constant Gruneisen
+// coefficient Gamma = gamma - 1): stiffened gas (cold pressure -gamma p_inf,
+// cold energy e_inf, constant G); Romenskii solid (cold energy
+// K0 / (2 rho0 a^2) ((rho/rho0)^a - 1)^2, shear modulus G0 (rho/rho0)^(b+1));
+// JWL (cold pressure A e^(-R1 rho0/rho) + B e^(-R2 rho0/rho), G = 0).
+enum { EOS_SG = 0, EOS_ROMENSKII = 1, EOS_JWL = 2 };
+
 template <class R>
 struct MatT {
   R gamma, pinf, einf, G, sigy, chi0, Q, cv, A, Tact;
   int plastic, reactive;
+  int eos;                  // EOS_SG, EOS_ROMENSKII or EOS_JWL
+  R rho0, K0, ar, br;       // Romenskii: reference density, K0, exponents alpha-bar, beta-bar
+  R jA, jB, jR1, jR2;       // JWL constants (rho0 shared)
   int law;  // reaction rate law: 0 Arrhenius, 1 A sqrt(lam) above the pressure pign
   R pign;
   R iGm1;  // 1 / (gamma - 1)
@@ -71,6 +81,8 @@ inline PhysT<float> to_float(const Phys& P) {
     m.law = d.law; m.pign = (float)d.pign;
     m.iGm1 = (float)d.iGm1; m.gi = (float)d.gi; m.kap = (float)d.kap; m.gG = (float)d.gG;
     m.GoG = (float)d.GoG; m.JY = (float)d.JY;
+    m.eos = d.eos; m.rho0 = (float)d.rho0; m.K0 = (float)d.K0; m.ar = (float)d.ar; m.br = (float)d.br;
+    m.jA = (float)d.jA; m.jB = (float)d.jB; m.jR1 = (float)d.jR1; m.jR2 = (float)d.jR2;
   }
   f.y = P.y;
   f.thinc = P.thinc;
@@ -126,12 +138,71 @@ __device__ __forceinline__ StrainT<T> strain_of(T a, T b, T c, T d, T e) {
   return s;
 }
 
-// The pieces of the pressure function that do not depend on the internal energy.
+// Reference curves of a Romenskii or JWL material at phasic density r and
+// strain J2: E_ref, p_ref = r^2 dE_ref/dr, and their density derivatives.
+// The shear energy G(r) J2 / r adds (r G' - G) J2 to the reference pressure.
+template <class T>
+struct RefT {
+  T e, p, dp, de;
+};
+// a^b for a > 0 (the dual-number form lives with the Dual type)
+__device__ __forceinline__ double powr(double a, double b) { return ::pow(a, b); }
+__device__ __forceinline__ float powr(float a, float b) { return ::powf(a, b); }
+template <class T, class R>
+__device__ __forceinline__ RefT<T> ref_curves(const MatT<R>& m, T r, T J2) {
+  RefT<T> o;
+  if (m.eos == EOS_ROMENSKII) {
+    const T x = r / m.rho0;
+    const T xa = powr(x, T(m.ar));
+    const T G = m.G * powr(x, T(m.br + 1.0));
+    const T pc = m.K0 / m.ar * xa * x * (xa - 1.0);
+    o.e = m.K0 / (2.0 * m.rho0 * m.ar * m.ar) * (xa - 1.0) * (xa - 1.0) + G * J2 / r;
+    o.p = pc + m.br * G * J2;
+    o.dp = m.K0 / (m.ar * m.rho0) * xa * ((2.0 * m.ar + 1.0) * xa - (m.ar + 1.0)) + m.br * (m.br + 1.0) * G / r * J2;
+    o.de = (pc + m.br * G * J2) / (r * r);
+  } else {
+    const T e1 = m.jA * exp(-m.jR1 * m.rho0 / r), e2 = m.jB * exp(-m.jR2 * m.rho0 / r);
+    o.e = e1 / (m.jR1 * m.rho0) + e2 / (m.jR2 * m.rho0);
+    o.p = e1 + e2;
+    o.dp = (e1 * m.jR1 + e2 * m.jR2) * m.rho0 / (r * r);
+    o.de = o.p / (r * r);
+  }
+  return o;
+}
+
+// Shear modulus of a material at phasic density r (constant but for Romenskii).
+template <class T, class R>
+__device__ __forceinline__ T shear_of(const MatT<R>& m, T r) {
+  if (m.eos == EOS_ROMENSKII) return m.G * powr(r / m.rho0, T(m.br + 1.0));
+  return T(m.G);
+}
+
+// The pieces of the pressure function that do not depend on the internal
+// energy: sum_l phi_l rho_l (E_ref,l - p_ref,l / (rho_l Gamma_l)) and the heat
+// release; the stiffened gas in its reduced form (kappa_l = gamma_l p_inf,l /
+// Gamma_l, gG_l = gamma_l G_l / Gamma_l), other families at rho_l = ar_l / phi_l.
 template <class T>
 __device__ __forceinline__ T ref_energy(const PhysT<T>& P, T phi1, T ar1, T ar2, T arl, T J2) {
   const T phi2 = 1.0 - phi1;
-  T s = phi1 * (P.m[0].kap + P.m[0].gG * J2) + phi2 * (P.m[1].kap + P.m[1].gG * J2) +
-             ar1 * P.m[0].einf + ar2 * P.m[1].einf;
+  T s;
+  if (P.m[0].eos == EOS_SG && P.m[1].eos == EOS_SG) {
+    s = phi1 * (P.m[0].kap + P.m[0].gG * J2) + phi2 * (P.m[1].kap + P.m[1].gG * J2) + ar1 * P.m[0].einf +
+        ar2 * P.m[1].einf;
+  } else {
+    s = T(0.0);
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      const MatT<T>& m = P.m[l];
+      const T ph = l == 0 ? phi1 : phi2, ar = l == 0 ? ar1 : ar2;
+      if (m.eos == EOS_SG) {
+        s += ph * (m.kap + m.gG * J2) + ar * m.einf;
+      } else {
+        const T r = ar / ph;
+        const RefT<T> c = ref_curves(m, r, J2);
+        s += ar * (c.e - c.p * m.iGm1 / r);
+      }
+    }
+  }
   if (P.y >= 0) {
     const T ary = P.y == 0 ? ar1 : ar2;
     s -= P.m[P.y].Q * (ary - arl);
@@ -144,20 +215,39 @@ __device__ __forceinline__ T xi_of(const PhysT<T>& P, T phi1) {
   return phi1 * P.m[0].iGm1 + (1.0 - phi1) * P.m[1].iGm1;
 }
 
-// rho c_L^2 for a state (frozen mixture sound speed plus 4/3 G_mix).
+// rho_l c_l^2 / Gamma_l of one material at pressure p (Mie-Grueneisen form,
+// c^2 = (dp/drho)_E + p / rho^2 (dp/dE)_rho at fixed strain).
 template <class T>
-__device__ __forceinline__ T cL2_of(const PhysT<T>& P, T phi1, T rho, T p, T J2) {
+__device__ __forceinline__ T rc2_of(const MatT<T>& m, T r, T p, T J2) {
+  if (m.eos == EOS_SG) return m.gi * p + m.kap + m.gG * J2;
+  const RefT<T> c = ref_curves(m, r, J2);
+  const T Gam = m.gamma - 1.0;
+  return m.iGm1 * (r * c.dp + m.gamma * p - c.p - r * r * Gam * c.de);
+}
+
+// c_L^2 for a state (frozen mixture sound speed plus 4/3 G_mix / rho); r1,
+// r2 are the phasic densities (read only by the Romenskii and JWL forms).
+template <class T>
+__device__ __forceinline__ T cL2_of(const PhysT<T>& P, T phi1, T rho, T p, T J2, T r1, T r2) {
   const T phi2 = 1.0 - phi1;
   const T xi = xi_of(P, phi1);
-  const T a = phi1 * (P.m[0].gi * p + P.m[0].kap + P.m[0].gG * J2) +
-                   phi2 * (P.m[1].gi * p + P.m[1].kap + P.m[1].gG * J2);
-  const T Gm = (phi1 * P.m[0].GoG + phi2 * P.m[1].GoG) / xi;
+  if (P.m[0].eos == EOS_SG && P.m[1].eos == EOS_SG) {
+    const T a = phi1 * (P.m[0].gi * p + P.m[0].kap + P.m[0].gG * J2) +
+                phi2 * (P.m[1].gi * p + P.m[1].kap + P.m[1].gG * J2);
+    const T Gm = (phi1 * P.m[0].GoG + phi2 * P.m[1].GoG) / xi;
+    return (a / xi + (4.0 / 3.0) * Gm) / rho;
+  }
+  const T a = phi1 * rc2_of(P.m[0], r1, p, J2) + phi2 * rc2_of(P.m[1], r2, p, J2);
+  const T Gm = (phi1 * shear_of(P.m[0], r1) * P.m[0].iGm1 + phi2 * shear_of(P.m[1], r2) * P.m[1].iGm1) / xi;
   return (a / xi + (4.0 / 3.0) * Gm) / rho;
 }
 
 template <class T>
-__device__ __forceinline__ T Gmix_of(const PhysT<T>& P, T phi1) {
-  return (phi1 * P.m[0].GoG + (1.0 - phi1) * P.m[1].GoG) / xi_of(P, phi1);
+__device__ __forceinline__ T Gmix_of(const PhysT<T>& P, T phi1, T r1, T r2) {
+  if (P.m[0].eos == EOS_SG && P.m[1].eos == EOS_SG)
+    return (phi1 * P.m[0].GoG + (1.0 - phi1) * P.m[1].GoG) / xi_of(P, phi1);
+  return (phi1 * shear_of(P.m[0], r1) * P.m[0].iGm1 + (1.0 - phi1) * shear_of(P.m[1], r2) * P.m[1].iGm1) /
+         xi_of(P, phi1);
 }
 
 template <class T>
@@ -253,7 +343,7 @@ __device__ __forceinline__ FStateT<T> face_state(const PhysT<T>& P, const PrimT<
   const T xi = xi_of(P, w.phi);
   s.rhoE = xi * w.p + ref_energy(P, w.phi, s.ar1, s.ar2, s.arl, st.J2) +
            0.5 * s.rho * (w.u * w.u + w.v * w.v);
-  const T Gm = Gmix_of(P, w.phi);
+  const T Gm = Gmix_of(P, w.phi, w.r1, w.r2);
   s.Gm = Gm;
   if (DIR == 0) {
     s.un = w.u;
@@ -265,7 +355,7 @@ __device__ __forceinline__ FStateT<T> face_state(const PhysT<T>& P, const PrimT<
     s.snn = -w.p + 2.0 * Gm * st.H22;
   }
   s.snt = 2.0 * Gm * st.H12;
-  s.cL = cL2_of(P, w.phi, s.rho, w.p, st.J2);  // squared here; k_flux takes the root
+  s.cL = cL2_of(P, w.phi, s.rho, w.p, st.J2, w.r1, w.r2);  // squared here; k_flux takes the root
   s.V11 = w.V11;
   s.V12 = w.V12;
   s.V21 = w.V21;
@@ -400,10 +490,11 @@ __device__ __forceinline__ FaceOutT<T> hllc(const FStateT<T>& L, const FStateT<T
   return o;
 }
 
-// Plastic update of Section 3.2 on one cell's stretch tensor (in place).
+// Plastic update of Section 3.2 on one cell's stretch tensor (in place).  r1,
+// r2: phasic densities (the Romenskii yield strain sigma_y / (sqrt 6 G(r))).
 template <class T>
 __device__ __forceinline__ void plastic(const PhysT<T>& P, T phi1, T dt, T& V11,
-                                        T& V12, T& V21, T& V22, T& V33) {
+                                        T& V12, T& V21, T& V22, T& V33, T r1, T r2) {
   const StrainT<T> s = strain_of(V11, V12, V21, V22, V33);
   const T Js = sqrt(s.J2);
   T num = 0.0, den = 0.0;
@@ -411,13 +502,14 @@ __device__ __forceinline__ void plastic(const PhysT<T>& P, T phi1, T dt, T& V11,
   for (int l = 0; l < 2; ++l) {
     const MatT<T>& m = P.m[l];
     const T ph = l == 0 ? phi1 : 1.0 - phi1;
+    const T JY = m.eos == EOS_ROMENSKII ? m.sigy / (2.449489742783178 * shear_of(m, l == 0 ? r1 : r2)) : m.JY;
     T Jl;
     if (m.G == 0.0) {
       Jl = T(0.0);  // a fluid keeps no shear strain
     } else if (m.plastic == 1) {
-      Jl = fmin(Js, m.JY);
+      Jl = fmin(Js, JY);
     } else if (m.plastic == 2) {
-      Jl = Js > m.JY ? fmax(Js - dt * m.chi0, m.JY) : Js;
+      Jl = Js > JY ? fmax(Js - dt * m.chi0, JY) : Js;
     } else {
       Jl = Js;
     }

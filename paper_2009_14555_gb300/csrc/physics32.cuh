@@ -47,30 +47,63 @@ __device__ __forceinline__ float xi_f(const PhysF& P, float phi1) {
   return phi1 * P.m[0].iGm1 + (1.f - phi1) * P.m[1].iGm1;
 }
 
-// Reference energy without the stiff kappa part: shear, e_inf and heat release.
+// Reference energy without the stiff kappa part: shear, e_inf and heat
+// release of a stiffened gas; the whole reference part ar_l (E_ref,l -
+// p_ref,l / (rho_l Gamma_l)) of a Romenskii or JWL material (their kappa is
+// zero) at its phasic density r_l.
 __device__ __forceinline__ float soft_ref_f(const PhysF& P, float phi1, float ar1, float ar2, float arl,
-                                            float J2) {
-  float s = (phi1 * P.m[0].gG + (1.f - phi1) * P.m[1].gG) * J2 + ar1 * P.m[0].einf + ar2 * P.m[1].einf;
+                                            float J2, float r1, float r2) {
+  float s;
+  if (P.m[0].eos == EOS_SG && P.m[1].eos == EOS_SG) {
+    s = (phi1 * P.m[0].gG + (1.f - phi1) * P.m[1].gG) * J2 + ar1 * P.m[0].einf + ar2 * P.m[1].einf;
+  } else {
+    s = 0.f;
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      const MatT<float>& m = P.m[l];
+      const float ar = l == 0 ? ar1 : ar2, r = l == 0 ? r1 : r2;
+      if (m.eos == EOS_SG) {
+        s += (l == 0 ? phi1 : 1.f - phi1) * m.gG * J2 + ar * m.einf;
+      } else {
+        const RefT<float> c = ref_curves(m, r, J2);
+        s += ar * (c.e - c.p * m.iGm1 / r);
+      }
+    }
+  }
   if (P.y >= 0) s -= P.m[P.y].Q * ((P.y == 0 ? ar1 : ar2) - arl);
   return s;
 }
 
-__device__ __forceinline__ float cL2_f(const PhysF& P, float phi1, float rho, float p, float J2) {
+// Mixture shear modulus (phi / Gamma weights) at the phasic densities.
+__device__ __forceinline__ float Gmix_f(const PhysF& P, float phi1, float r1, float r2) {
+  const float ixi = 1.f / xi_f(P, phi1);
+  if (P.m[0].eos == EOS_SG && P.m[1].eos == EOS_SG) return (phi1 * P.m[0].GoG + (1.f - phi1) * P.m[1].GoG) * ixi;
+  return (phi1 * shear_of(P.m[0], r1) * P.m[0].iGm1 + (1.f - phi1) * shear_of(P.m[1], r2) * P.m[1].iGm1) * ixi;
+}
+
+__device__ __forceinline__ float cL2_f(const PhysF& P, float phi1, float rho, float p, float J2, float r1,
+                                       float r2) {
   const float phi2 = 1.f - phi1;
   const float ixi = 1.f / xi_f(P, phi1);
-  const float a = phi1 * (P.m[0].gi * p + P.m[0].kap + P.m[0].gG * J2) +
-                  phi2 * (P.m[1].gi * p + P.m[1].kap + P.m[1].gG * J2);
-  const float Gm = (phi1 * P.m[0].GoG + phi2 * P.m[1].GoG) * ixi;
-  return (a * ixi + (4.f / 3.f) * Gm) / rho;
+  if (P.m[0].eos == EOS_SG && P.m[1].eos == EOS_SG) {
+    const float a = phi1 * (P.m[0].gi * p + P.m[0].kap + P.m[0].gG * J2) +
+                    phi2 * (P.m[1].gi * p + P.m[1].kap + P.m[1].gG * J2);
+    const float Gm = (phi1 * P.m[0].GoG + phi2 * P.m[1].GoG) * ixi;
+    return (a * ixi + (4.f / 3.f) * Gm) / rho;
+  }
+  const float a = phi1 * rc2_of(P.m[0], r1, p, J2) + phi2 * rc2_of(P.m[1], r2, p, J2);
+  return (a * ixi + (4.f / 3.f) * Gmix_f(P, phi1, r1, r2)) / rho;
 }
 
 __device__ __forceinline__ float minmod_f(float a, float b) {
   return (a * b > 0.f) ? copysignf(fminf(fabsf(a), fabsf(b)), a) : 0.f;
 }
 
-// Limited slope: lim 0 minmod, 1 van Leer (2 a b / (a + b) for a b > 0).
-__device__ __forceinline__ float limited_f(float a, float b, int lim) {
-  if (!lim) return minmod_f(a, b);
+// Limited slope: LIM 0 minmod, 1 van Leer (2 a b / (a + b) for a b > 0);
+// a compile-time choice, so the default minmod kernels carry no branch.
+template <int LIM>
+__device__ __forceinline__ float limited_f(float a, float b) {
+  if constexpr (LIM == 0) return minmod_f(a, b);
   const float ab = a * b;
   return ab > 0.f ? 2.f * ab / (a + b) : 0.f;
 }
@@ -80,11 +113,10 @@ struct CandF {
 };
 
 // beta_of() gives the THINC steepness; it is evaluated only in a mixed cell.
-template <class BetaFn>
-__device__ __forceinline__ CandF phi_cand_f(float qm, float qc, float qp, const BetaFn& beta_of, bool thinc,
-                                            int lim = 0) {
+template <int LIM = 0, class BetaFn>
+__device__ __forceinline__ CandF phi_cand_f(float qm, float qc, float qp, const BetaFn& beta_of, bool thinc) {
   CandF c;
-  const float s = limited_f(qc - qm, qp - qc, lim);
+  const float s = limited_f<LIM>(qc - qm, qp - qc);
   c.mL = qc - 0.5f * s;
   c.mR = qc + 0.5f * s;
   c.tL = c.mL;
@@ -130,9 +162,9 @@ __device__ __forceinline__ FStateF face_state_f(const PhysF& P, const PrimF& w) 
   s.arl = 0.f;
   if (P.y >= 0) s.arl = (P.y == 0 ? s.ar1 : s.ar2) * w.lam;
   const float ixi = 1.f / xi_f(P, w.phi);
-  s.rhoE = w.p / ixi + soft_ref_f(P, w.phi, s.ar1, s.ar2, s.arl, st.J2) +
+  s.rhoE = w.p / ixi + soft_ref_f(P, w.phi, s.ar1, s.ar2, s.arl, st.J2, w.r1, w.r2) +
            0.5f * s.rho * (w.u * w.u + w.v * w.v);
-  const float Gm = (w.phi * P.m[0].GoG + (1.f - w.phi) * P.m[1].GoG) * ixi;
+  const float Gm = Gmix_f(P, w.phi, w.r1, w.r2);
   s.Gm = Gm;
   if (DIR == 0) {
     s.un = w.u;
@@ -144,7 +176,7 @@ __device__ __forceinline__ FStateF face_state_f(const PhysF& P, const PrimF& w) 
     s.snn = -w.p + 2.f * Gm * st.H22;
   }
   s.snt = 2.f * Gm * st.H12;
-  s.cL = cL2_f(P, w.phi, s.rho, w.p, st.J2);  // squared; k_flux32 takes the root
+  s.cL = cL2_f(P, w.phi, s.rho, w.p, st.J2, w.r1, w.r2);  // squared; k_flux32 takes the root
   s.V11 = w.V11;
   s.V12 = w.V12;
   s.V21 = w.V21;
@@ -249,9 +281,10 @@ __device__ __forceinline__ FaceOutF hlld_f(const FStateF& L, const FStateF& R) {
   return o;
 }
 
-// Plastic update of Section 3.2 in float.
+// Plastic update of Section 3.2 in float; r1, r2 the phasic densities (the
+// Romenskii yield strain sigma_y / (sqrt 6 G(r))).
 __device__ __forceinline__ void plastic_f(const PhysF& P, float phi1, float dt, float& V11, float& V12,
-                                          float& V21, float& V22, float& V33) {
+                                          float& V21, float& V22, float& V33, float r1, float r2) {
   const StrainF s = strain_f(V11, V12, V21, V22, V33);
   const float Js = sqrtf(s.J2);
   float num = 0.f, den = 0.f;
@@ -259,10 +292,11 @@ __device__ __forceinline__ void plastic_f(const PhysF& P, float phi1, float dt, 
   for (int l = 0; l < 2; ++l) {
     const MatT<float>& m = P.m[l];
     const float ph = l == 0 ? phi1 : 1.f - phi1;
+    const float JY = m.eos == EOS_ROMENSKII ? m.sigy / (2.4494897f * shear_of(m, l == 0 ? r1 : r2)) : m.JY;
     float Jl;
     if (m.G == 0.f) Jl = 0.f;
-    else if (m.plastic == 1) Jl = fminf(Js, m.JY);
-    else if (m.plastic == 2) Jl = Js > m.JY ? fmaxf(Js - dt * m.chi0, m.JY) : Js;
+    else if (m.plastic == 1) Jl = fminf(Js, JY);
+    else if (m.plastic == 2) Jl = Js > JY ? fmaxf(Js - dt * m.chi0, JY) : Js;
     else Jl = Js;
     num += ph * m.iGm1 * Jl;
     den += ph * m.iGm1;

@@ -118,7 +118,7 @@ __device__ __forceinline__ PrimF prim32_of(const Phys& P, const PhysF& F, const 
   }
   const StrainF s = strain_f(w.V11, w.V12, w.V21, w.V22, w.V33);
   const float KE = 0.5f * (mx * w.u + my * w.v);
-  w.p = (v[L::E] - (KE + soft_ref_f(F, phi, a1, a2, arl, s.J2))) / xi_f(F, phi);
+  w.p = (v[L::E] - (KE + soft_ref_f(F, phi, a1, a2, arl, s.J2, w.r1, w.r2))) / xi_f(F, phi);
   return w;
 }
 
@@ -144,7 +144,7 @@ __device__ __forceinline__ float cfl_rate_of(const PhysF& F, const PrimF& w, flo
                                              int patch, int cell) {
   const StrainF s = strain_f(w.V11, w.V12, w.V21, w.V22, w.V33);
   const float rho = w.phi * w.r1 + (1.f - w.phi) * w.r2;
-  const float cL2 = cL2_f(F, w.phi, rho, w.p, s.J2);
+  const float cL2 = cL2_f(F, w.phi, rho, w.p, s.J2, w.r1, w.r2);
   if (!(cL2 > 0.f) || !(rho > 0.f)) flag_bad(status, patch, cell);
   const float cL = sqrtf(fmaxf(cL2, 0.f));
   float r = (fabsf(w.u) + cL) * idx;

@@ -13,10 +13,16 @@ import torch
 from . import _lib as L
 
 
+_EOS = {"sg": L.DIS_EOS_STIFFENED, "romenskii": L.DIS_EOS_ROMENSKII, "jwl": L.DIS_EOS_JWL}
+
+
 def _material(m: dict) -> L.DisMaterial:
     return L.DisMaterial(m["gamma"], m["p_inf"], m["e_inf"], m["G"], m["plastic"], m["sigma_y"],
                          m["chi0"], m["reactive"], m["Q"], m["cv"], m["A"], m["T_act"],
-                         int(m.get("rate_law", 0)), float(m.get("p_ign", 0.0)))
+                         int(m.get("rate_law", 0)), float(m.get("p_ign", 0.0)), _EOS[m.get("eos", "sg")],
+                         float(m.get("rho0", 0.0)), float(m.get("K0", 0.0)), float(m.get("alpha_r", 0.0)),
+                         float(m.get("beta_r", 0.0)), float(m.get("jwl_A", 0.0)), float(m.get("jwl_B", 0.0)),
+                         float(m.get("jwl_R1", 0.0)), float(m.get("jwl_R2", 0.0)))
 
 
 def _patch(p, dim) -> L.DisPatch:

@@ -297,22 +297,23 @@ def reactive_plate_2d(nx: int = 2048, ny: int = 1024, steps: int = 1000, seed: i
                     steps, True, reactive_material=1, extra=dict(T0=T0))
 
 
-def detonation_copper_1d(n: int = 1000, steps: int = 400, name=None) -> Workload:
+def detonation_copper_1d(n: int = 1000, steps: int = 400, name=None, copper: str = "romenskii") -> Workload:
     """The shape of the one-dimensional test of Section 4.1 on [0, 0.4] m:
     quiescent elastic copper for x < 0.15, ambient explosive for
     0.15 < x < 0.35, a booster of the same explosive at 1e9 Pa for x > 0.35,
     1e5 Pa elsewhere; the reactant burns at lam_dot = -k sqrt(lam),
     k = 2e6 1/s, once the pressure exceeds 1e8 Pa; CFL 0.9, transmissive ends.
 
-    Stand-in closures (the Romenskii copper and the multiphase explosive of
-    the paper are not among the closures built here): copper as a stiffened
-    gas with rho 8930 kg/m^3, Gamma 2 (gamma 3), gamma p_inf = K0 = 136.5 GPa
-    and G = 39.4 GPa (no plasticity), the Romenskii table's rho_0, K_0, G_0
-    and Gamma; the explosive as an ideal-gas reactant/product pair with the
-    product's gamma 3, c_V 1000 and Q = 3.68 MJ/kg and the reactant's
-    rho_0 = 1600 kg/m^3 from the table of the generic explosive.
+    Copper: the Romenskii solid of the paper's table (rho_0 8930 kg/m^3,
+    K_0 136.5 GPa, G_0 39.4 GPa, Gamma 2, alpha 1, beta 3; no plasticity), or
+    with copper="stiffened" a stiffened gas of the same rho_0, Gamma,
+    gamma p_inf = K_0 and constant G = G_0.  The explosive is a stand-in (the
+    paper's two-EOS multiphase explosive is not among the closures built
+    here): an ideal-gas reactant/product pair with the product's gamma 3,
+    c_V 1000 and Q = 3.68 MJ/kg and the reactant's rho_0 = 1600 kg/m^3 from the
+    table of the generic explosive.
     """
-    copper = material(3.0, p_inf=136.5e9 / 3.0, G=39.4e9)
+    copper = (COPPER_ROMENSKII if copper == "romenskii" else material(3.0, p_inf=136.5e9 / 3.0, G=39.4e9))
     expl = material(3.0, reactive=1, Q=3.68e6, cv=1000.0, A=2.0e6, rate_law=1, p_ign=1.0e8)
     w, k = _blank(1, True, 1, n)
     dx = 0.4 / n

@@ -153,7 +153,7 @@ def _detonation_partial_burn():
     # the k sqrt(lam) law with its pressure switch (Section 4.1), k lowered to
     # 2e5 1/s so that at 100 cells the booster burns over several steps
     # (partially burnt cells rather than a clamp to lam = 0 in one step)
-    wl = W.perturbed(W.detonation_copper_1d(100, steps=8))
+    wl = W.perturbed(W.detonation_copper_1d(100, steps=8, copper="stiffened"))
     wl.materials[1]["A"] = 2e5
     return wl
 

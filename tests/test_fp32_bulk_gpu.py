@@ -70,11 +70,11 @@ def test_fp32_water_air_thinc():
     check32("1d_water_air_thinc_257_100steps", wl, 100)
 
 
-@pytest.mark.parametrize("variant", range(12))
+@pytest.mark.parametrize("variant", range(6))
 def test_fp32_every_stage_variant(variant):
-    """Every stage variant (3 tile shapes x two register budgets x one CTA per
-    tile or the persistent form) meets the same bar on a patch whose sides
-    are not multiples of any tile (ragged tiles on both axes)."""
+    """Every stage variant (3 tile shapes x two register budgets) meets the
+    same bar on a patch whose sides are not multiples of any tile (ragged
+    tiles on both axes)."""
     from paper_2009_14555_gb300.solver import Solver
     wl = W.reactive_plate_2d(45, 23, steps=12)
     s = Solver.from_workload(wl, precision="fp32_bulk")
@@ -194,14 +194,13 @@ def test_fp32_variants_agree_at_full_size():
     tile shape and the register budget do not change the arithmetic of a
     cell, and no stage reads a buffer that another CTA of the same launch
     writes (a halo race would change cells near moving waves by the size of
-    a stage update and make the result depend on CTA scheduling).  The
-    persistent variants are deterministic and agree to float32 rounding."""
+    a stage update and make the result depend on CTA scheduling)."""
     from paper_2009_14555_gb300.solver import Solver, pack
     wl = W.reactive_plate_2d(2048, 1024, steps=3)
     prim = pack([p.prim for p in wl.patches])
     nf = len(W.cons_names(2, True))
     runs = {}
-    for v in (0, 1, 2, 3, 5, 0, 6, 8, 11, 6):
+    for v in (0, 1, 2, 3, 5, 0):
         s = Solver.from_workload(wl, precision="fp32_bulk")
         s.set_variant(v)
         s.set_state(prim)
@@ -219,9 +218,7 @@ def test_fp32_variants_agree_at_full_size():
     with open(record_path("fp32_l1.json"), "w") as f:
         json.dump(RESULTS, f, indent=1)
     for v, d in diffs.items():
-        # the persistent kernel runs the same tile functions in another kernel,
-        # where the code generator may contract multiply-adds differently
-        assert max(d) == 0.0 if v < 6 else max(d) <= 1e-5, (v, d)
+        assert max(d) == 0.0, (v, d)
 
 
 def test_fp32_vanleer_reactive_plate():

@@ -33,10 +33,15 @@ def test_detonation_workload_takes_the_printed_values():
     assert p.nx == n and abs(p.nx * p.dx - g["domain_length_m"]) < 1e-15
     assert wl.cfl == g["cfl"]
     copper, expl = wl.materials
-    # copper: stiffened gas with Gamma = gamma - 1 and bulk modulus gamma p_inf
+    # copper: the Romenskii solid of the table (Gamma = gamma - 1)
+    assert copper["eos"] == "romenskii"
     assert abs((copper["gamma"] - 1.0) - g["copper_Gamma"]) < 1e-15
-    assert abs(copper["gamma"] * copper["p_inf"] - g["copper_K0_pa"]) < 1e-3
+    assert copper["K0"] == g["copper_K0_pa"] and copper["rho0"] == g["copper_rho0"]
+    assert copper["alpha_r"] == g["copper_alpha"] and copper["beta_r"] == g["copper_beta"]
     assert copper["G"] == g["copper_G0_pa"] and copper["plastic"] == 0
+    # the stiffened stand-in keeps the bulk modulus gamma p_inf = K0
+    cs = W.detonation_copper_1d(n, copper="stiffened").materials[0]
+    assert abs(cs["gamma"] * cs["p_inf"] - g["copper_K0_pa"]) < 1e-3
     # explosive: the product's constants, the k sqrt(lam) law and its switch
     assert expl["gamma"] == g["explosive_product_gamma"]
     assert expl["cv"] == g["explosive_product_cv"]
