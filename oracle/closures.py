@@ -148,13 +148,98 @@ def de_ref_drho(m, rho, J2):
     return cold_curves(m, rho)[2] + _shear_p_factor(m, rho)[0] * J2 / (rho * rho)
 
 
+# ----------------------------------------------------------------------------
+# Reactive physical mixture with distinct reactant and product closures
+# (Section 2.3.1, Appendix B).  Both components are stiffened gases (no shear
+# modulus): the reactant takes the material's gamma, p_inf, C_V; the product
+# m["prod_gamma"], m["prod_p_inf"], m["prod_cv"] and the heat release Q.  With
+# s = lam rho_y / rho_alpha the reactant's share of the mixture's volume
+# (the mixture rule 1/rho_y = lam/rho_alpha + (1 - lam)/rho_beta is
+# s + (1 - s) = 1), the pressure function of Appendix B depends on the
+# densities only through s, and the temperature equality T_alpha = T_beta
+# fixes s: in closed form when p is known (primitive variables), by
+# bisection on s in [0, 1] with the pressure function otherwise (the paper's
+# bisection on rho_alpha, over the bounded variable).  Identical closures give
+# s = lam, rho_alpha = rho_beta = rho_y (the closed form of the other reactive
+# closure).  Sound speed: the lam-weighted form of Section 2.3.1 with
+# (d rho_k / d rho_y)_p = rho_k / rho_y (reading: the paper leaves this
+# derivative unstated; this is compression at fixed composition).
+# ----------------------------------------------------------------------------
+def two_eos(m):
+    return bool(m["reactive"]) and ("prod_gamma" in m or "prod_p_inf" in m or "prod_cv" in m)
+
+
+def _comps(m):
+    g_a, pi_a, cv_a = m["gamma"], m["p_inf"], m["cv"]
+    return ((g_a, pi_a, cv_a),
+            (m.get("prod_gamma", g_a), m.get("prod_p_inf", pi_a), m.get("prod_cv", cv_a)))
+
+
+def reactant_share(m, lam, p):
+    """s of the temperature equality at pressure p (closed form)."""
+    (ga, pa, ca), (gb, pb, cb) = _comps(m)
+    wa = lam * (ga - 1.0) * ca * (p + gb * pb)
+    wb = (1.0 - lam) * (gb - 1.0) * cb * (p + ga * pa)
+    return wa / (wa + wb)
+
+
+def _mix_terms(m, s):
+    """(1/Gamma_y, sum_k share_k kappa_k) of the mixture at reactant share s."""
+    (ga, pa, ca), (gb, pb, cb) = _comps(m)
+    iG = s / (ga - 1.0) + (1.0 - s) / (gb - 1.0)
+    kap = s * ga * pa / (ga - 1.0) + (1.0 - s) * gb * pb / (gb - 1.0)
+    return iG, kap
+
+
+def mixture_share(phis, rhos, rhoe, mats, lam, iters=64):
+    """Reactant share s of the reactive material from the conservative state:
+    bisection of (T_alpha - T_beta) lam (1 - lam) on [0, 1], the pressure from
+    the pressure function at each trial s (Appendix B)."""
+    y = next(i for i, m in enumerate(mats) if m["reactive"])
+    m = mats[y]
+    (ga, pa, ca), (gb, pb, cb) = _comps(m)
+    num0 = rhoe.clone()
+    den0 = torch.zeros_like(rhoe)
+    J2 = torch.zeros_like(rhoe)
+    for l, (mm, phi, rho) in enumerate(zip(mats, phis, rhos)):
+        if l == y:
+            continue
+        G = Gamma(mm)
+        num0 = num0 + phi * rho * (p_ref(mm, rho, J2) / (rho * G) - e_ref(mm, rho, J2))
+        den0 = den0 + phi / G
+    phy, rhy = phis[y], rhos[y]
+
+    def pressure(s):
+        iG, kap = _mix_terms(m, s)
+        return (num0 - phy * kap + phy * rhy * (1.0 - lam) * m["Q"]) / (den0 + phy * iG)
+
+    def g(s):
+        p = pressure(s)
+        return (1.0 - lam) * (gb - 1.0) * cb * (p + ga * pa) * s - lam * (ga - 1.0) * ca * (p + gb * pb) * (1.0 - s)
+
+    lo = torch.zeros_like(rhoe)
+    hi = torch.ones_like(rhoe)
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        neg = g(mid) < 0
+        lo = torch.where(neg, mid, lo)
+        hi = torch.where(neg, hi, mid)
+    return 0.5 * (lo + hi)
+
+
 def material_energy(m, rho, p, J2, lam=None):
     """Specific internal energy of one material from the MG form (Section 2.3).
 
     For a reactive material, E = lam E_alpha + (1 - lam) E_beta with the product
-    reference energy shifted by -Q (Section 2.3.1) and rho_alpha = rho_beta = rho.
+    reference energy shifted by -Q (Section 2.3.1) and rho_alpha = rho_beta = rho
+    (identical closures) or the temperature-equality densities (two closures).
     """
     G = Gamma(m)
+    if two_eos(m):
+        s = reactant_share(m, lam, p)
+        iG, kap = _mix_terms(m, s)
+        # rho_y E = sum_k share_k (p + gamma_k p_inf,k) / Gamma_k - rho_y (1 - lam) Q
+        return (p * iG + kap) / rho - (1.0 - lam) * m["Q"]
     if m["reactive"]:
         e_a = (p - p_ref(m, rho, J2)) / (rho * G) + e_ref(m, rho, J2)
         e_b = (p - p_ref(m, rho, J2)) / (rho * G) + e_ref(m, rho, J2) - m["Q"]
@@ -171,11 +256,17 @@ def mixture_pressure(phis, rhos, rhoe, J2, mats, lam=None):
         / [sum_x phi_x/Gamma_x + phi_y rho_y lam/(rho_a Gamma_a)
                                + phi_y rho_y (1-lam)/(rho_b Gamma_b)]
     """
+    if any(two_eos(m) for m in mats):
+        s = mixture_share(phis, rhos, rhoe, mats, lam)
     num = rhoe.clone()
     den = torch.zeros_like(rhoe)
     for m, phi, rho in zip(mats, phis, rhos):
         G = Gamma(m)
-        if m["reactive"]:
+        if two_eos(m):
+            iG, kap = _mix_terms(m, s)
+            num = num - phi * kap + phi * rho * (1.0 - lam) * m["Q"]
+            den = den + phi * iG
+        elif m["reactive"]:
             ra = rb = rho  # temperature equality with equal Gamma, C_V
             num = num + phi * rho * lam * (p_ref(m, ra, J2) / (ra * G) - e_ref(m, ra, J2))
             num = num + phi * rho * (1 - lam) * (p_ref(m, rb, J2) / (rb * G)
@@ -196,6 +287,11 @@ def material_sound_speed2(m, rho, p, J2, lam=None):
     with rho_alpha = rho_beta = rho so (d rho_alpha/d rho)_p = 1.
     """
     G = Gamma(m)
+    if two_eos(m):
+        s = reactant_share(m, lam, p)
+        iG, kap = _mix_terms(m, s)
+        # [p + sum_k share_k (p + gamma_k p_inf,k) / Gamma_k] / (rho / Gamma_y)
+        return (p + p * iG + kap) / (rho * iG)
     if m["reactive"]:
         dEdp = lam / (rho * G) + (1 - lam) / (rho * G)
         # (dE_k/drho_k)_p for the MG form: -(p - p_ref)/(rho^2 G) + dp_ref/drho/(... ) terms
@@ -209,9 +305,22 @@ def material_sound_speed2(m, rho, p, J2, lam=None):
     return dpdrho + p / (rho * rho) * dpde
 
 
-def temperature(m, rho, p, J2):
-    """T = (p - p_ref) / (rho Gamma C_V)  (Appendix B)."""
+def temperature(m, rho, p, J2, lam=None):
+    """T = (p - p_ref) / (rho Gamma C_V)  (Appendix B); for two closures the
+    common temperature sum_k share_k (p + gamma_k p_inf,k) / (Gamma_k C_V,k) / rho_y."""
+    if two_eos(m):
+        (ga, pa, ca), (gb, pb, cb) = _comps(m)
+        s = reactant_share(m, lam, p)
+        return (s * (p + ga * pa) / ((ga - 1.0) * ca) + (1.0 - s) * (p + gb * pb) / ((gb - 1.0) * cb)) / rho
     return (p - p_ref(m, rho, J2)) / (rho * Gamma(m) * m["cv"])
+
+
+def inv_gamma(m, p=None, lam=None):
+    """1 / Gamma of a material in the mixture rules (phi / Gamma weights):
+    s / Gamma_alpha + (1 - s) / Gamma_beta for two reactive closures."""
+    if two_eos(m):
+        return _mix_terms(m, reactant_share(m, lam, p))[0]
+    return 1.0 / Gamma(m)
 
 
 # ----------------------------------------------------------------------------
@@ -226,10 +335,11 @@ def phases(phi1):
 def mixture_props(phis, rhos, p, J2, mats, lam):
     """Mixture G, c^2 and longitudinal c_L^2 (Section 2.2 mixture rules)."""
     rho = sum(ph * r for ph, r in zip(phis, rhos))
-    xi = sum(ph / Gamma(m) for ph, m in zip(phis, mats))
-    Gm = sum(ph * shear_modulus(m, r) / Gamma(m) for ph, r, m in zip(phis, rhos, mats)) / xi
-    c2 = sum((ph * r / rho) * material_sound_speed2(m, r, p, J2, lam) / Gamma(m)
-             for ph, r, m in zip(phis, rhos, mats)) / xi
+    ig = [inv_gamma(m, p, lam) for m in mats]
+    xi = sum(ph * g for ph, g in zip(phis, ig))
+    Gm = sum(ph * shear_modulus(m, r) * g for ph, r, m, g in zip(phis, rhos, mats, ig)) / xi
+    c2 = sum((ph * r / rho) * material_sound_speed2(m, r, p, J2, lam) * g
+             for ph, r, m, g in zip(phis, rhos, mats, ig)) / xi
     cL2 = c2 + (4.0 / 3.0) * Gm / rho
     return rho, Gm, c2, cL2
 

@@ -431,7 +431,7 @@ def reaction_update(q, mats, dt):
             return ary * torch.where(on, lam_dot, torch.zeros_like(lam))
         rho_y = w["rho1" if y == 0 else "rho2"]
         _, J2 = hencky_dev(w["V"])
-        T = temperature(m, rho_y, w["p"], J2)
+        T = temperature(m, rho_y, w["p"], J2, lam)
         arr = torch.where(T > 0, torch.exp(-m["T_act"] / torch.where(T > 0, T, torch.ones_like(T))),
                           torch.zeros_like(T))
         return ary * (-m["A"] * lam * arr)

@@ -76,6 +76,18 @@ def jwl(rho0, A, B, R1, R2, Gamma, cv=0.0) -> dict:
     return m
 
 
+def generic_explosive(A=2.0e6, rate_law=1, p_ign=1.0e8, T_act=0.0) -> dict:
+    """The generic multiphase explosive of the paper's table (Section 4.1):
+    reactant a stiffened gas (gamma 4, p_inf 1 GPa, C_V 2000), product an ideal
+    gas (gamma 3, C_V 1000) with Q = 3.68 MJ/kg; distinct closures, so the
+    mixture's component densities come from the temperature equality of
+    Appendix B."""
+    m = material(4.0, p_inf=1.0e9, reactive=1, Q=3.68e6, cv=2000.0, A=A, T_act=T_act, rate_law=rate_law,
+                 p_ign=p_ign)
+    m.update(prod_gamma=3.0, prod_p_inf=0.0, prod_cv=1000.0)
+    return m
+
+
 # Copper of the Romenskii table (Section 4.1): rho0 8930, K0 136.5 GPa,
 # G0 39.4 GPa, Gamma 2, alpha-bar 1, beta-bar 3.
 COPPER_ROMENSKII = romenskii(8930.0, 136.5e9, 39.4e9, 2.0, 1.0, 3.0)

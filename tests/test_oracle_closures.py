@@ -434,3 +434,70 @@ def test_sound_speed_is_isentropic_derivative_other_families(m):
     num = (p_of(rho0 + h, e0 + p0 / rho0 ** 2 * h) - p_of(rho0 - h, e0 - p0 / rho0 ** 2 * h)) / (2 * h)
     c2 = C.material_sound_speed2(m, t([rho0]), t([p0]), J2).item()
     assert abs(num - c2) / c2 < 1e-6
+
+
+# ---- Reactive mixture with distinct closures: Appendix B ------------------
+EXPL = W.generic_explosive()
+
+
+def _mix_state(lam, p, rho_y=1600.0, phi_y=1.0 - 1e-8):
+    """A cell of copper trace + explosive (primitive), as the oracle's dicts."""
+    cu = W.material(3.0, p_inf=136.5e9 / 3.0, G=39.4e9)
+    mats = [cu, EXPL]
+    one = torch.ones(1, dtype=F64)
+    w = dict(phi1=one * (1 - phi_y), rho1=one * 8930.0, rho2=one * rho_y,
+             u=torch.zeros(1, 3, dtype=F64), p=one * p, V=torch.eye(3, dtype=F64)[None], lam=one * lam)
+    return w, mats
+
+
+def test_mixture_temperature_equality_and_mixture_rule():
+    """At the share s found from the conservative state (bisection), the
+    reactant and product temperatures are equal and the component densities
+    satisfy the mixture rule 1/rho_y = lam/rho_a + (1 - lam)/rho_b."""
+    for lam in (0.05, 0.3, 0.5, 0.9):
+        for p in (1e5, 1e9, 2e10):
+            w, mats = _mix_state(lam, p)
+            q = C.prim_to_cons(w, mats)
+            back = C.cons_to_prim(q, mats)
+            # the reactant's stiff part gamma p_inf = 4e9 Pa sets the round-off scale
+            assert abs(back["p"].item() - p) < 1e-13 * (p + 4e9), (lam, p, back["p"].item())
+            s = C.reactant_share(EXPL, torch.tensor(lam, dtype=F64), back["p"]).item()
+            ry = 1600.0
+            ra, rb = lam * ry / s, (1 - lam) * ry / (1 - s)
+            Ta = (p + 4.0 * 1e9) / (ra * 3.0 * 2000.0)
+            Tb = (p + 0.0) / (rb * 2.0 * 1000.0)
+            assert abs(Ta / Tb - 1) < 1e-10, (lam, p, Ta, Tb)
+            assert abs(1 / ry - (lam / ra + (1 - lam) / rb)) < 1e-12 / ry
+
+
+def test_mixture_share_hand_solution():
+    """lam = 0.5 at p = 1 GPa: s = lam G_a Cv_a (p + gb pb) / (...) with
+    Gamma_a C_V,a = 3 x 2000 = 6000, Gamma_b C_V,b = 2 x 1000 = 2000,
+    p + gamma_a p_inf,a = 5e9, p + gamma_b p_inf,b = 1e9:
+    s = 0.5 x 6000 x 1e9 / (0.5 x 6000 x 1e9 + 0.5 x 2000 x 5e9) = 3/8."""
+    s = C.reactant_share(EXPL, torch.tensor(0.5, dtype=F64), torch.tensor(1e9, dtype=F64)).item()
+    assert abs(s - 0.375) < 1e-15
+
+
+def test_identical_closures_reduce_to_the_closed_form():
+    """Giving the product the reactant's closure explicitly (two-closure path,
+    bisection) reproduces the closed-form pressure of identical closures."""
+    m1 = W.material(1.4, reactive=1, Q=2e6, cv=717.5, A=1.0, T_act=1.0)
+    m2 = dict(m1, prod_gamma=1.4, prod_p_inf=0.0, prod_cv=717.5)
+    air = W.AIR
+    for lam in (0.2, 0.7):
+        one = torch.ones(1, dtype=F64)
+        w = dict(phi1=one * 0.3, rho1=one * 1.2, rho2=one * 2.0, u=torch.zeros(1, 3, dtype=F64),
+                 p=one * 3e5, V=torch.eye(3, dtype=F64)[None], lam=one * lam)
+        q1 = C.prim_to_cons(w, [air, m1])
+        q2 = C.prim_to_cons(w, [air, m2])
+        assert torch.allclose(q1["E"], q2["E"], rtol=1e-14)
+        p2 = C.cons_to_prim(q1, [air, m2])["p"]
+        assert abs(p2.item() / 3e5 - 1) < 1e-12
+
+
+def test_mixture_sound_speed_limits():
+    """lam = 1: the reactant's gamma (p + p_inf) / rho; lam = 0: the product's."""
+    for lam, g, pi in ((1.0, 4.0, 1e9), (0.0, 3.0, 0.0)):
+        c2 = C.material_sound_speed2(EXPL, t([1600.0]), t([2e9]), t([0.0]), t([lam])).item()
+        assert abs(c2 / (g * (2e9 + pi) / 1600.0) - 1) < 1e-12
