@@ -69,7 +69,8 @@ enum { DIS_RATE_ARRHENIUS = 0, DIS_RATE_SQRT = 1 };
  *                      energy A / (R1 rho0) e^(-R1 rho0/rho) + B / (R2 rho0)
  *                      e^(-R2 rho0/rho) (a fluid: G must be 0).
  * The shear energy G(rho) J^2 / rho enters the reference curves.  The
- * reactive material must be a stiffened gas (ideal: p_inf = 0). */
+ * reactive material must be a stiffened gas without shear modulus (ideal,
+ * p_inf = 0, unless it has a product closure of its own). */
 enum { DIS_EOS_STIFFENED = 0, DIS_EOS_ROMENSKII = 1, DIS_EOS_JWL = 2 };
 
 /* One material: Mie-Grueneisen closure (Section 2.3; stiffened gas by
@@ -98,6 +99,12 @@ typedef struct {
   double rho0;      /* Romenskii, JWL: reference density */
   double K0, alpha, beta;                 /* Romenskii: bulk modulus, exponents */
   double jwl_A, jwl_B, jwl_R1, jwl_R2;    /* JWL constants */
+  /* Reactive material only: a product closure of its own (stiffened gas
+   * prod_gamma, prod_p_inf, prod_cv; prod_gamma 0 = the reactant's closure).
+   * The reactant is then the material's gamma, p_inf, cv, and the mixture's
+   * component densities follow from the temperature equality of Appendix B
+   * (a bisection over the reactant's volume share).  Float64 contexts only. */
+  double prod_gamma, prod_p_inf, prod_cv;
 } dis_material;
 
 /* One Cartesian patch (the single-grid unit of Section 3): nx x ny cells of
@@ -345,7 +352,8 @@ int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
  * with the rest of the stage, and J is the same plain sum over cells (no
  * factor r).  Returns DIS_EINVAL (bad arguments, a DIS_HANCOCK context: the
  * adjoint covers the Runge-Kutta scheme, a DIS_VANLEER context: it covers
- * the minmod limiter, or a material that is not a stiffened gas), DIS_ESTATE
+ * the minmod limiter, a material that is not a stiffened gas, or a reactive
+ * material with a product closure of its own), DIS_ESTATE
  * (no state), DIS_ENOMEM, DIS_ECUDA.
  * Synchronises. */
 int dis_adj_forward(dis_ctx* ctx, int n_steps, int checkpoint_every, int objective_material,
@@ -401,8 +409,10 @@ int dis_adj_reference(dis_ctx* ctx, int on);
  * CUDA graph.  Each call clears the maxima and flags it uses; calls are
  * serialised on the host, but calls whose device work overlaps (different
  * streams) share the area and race.
- * Returns DIS_EINVAL for n_patches outside 1..DIS_STATIC_MAX_PATCHES or other
- * bad arguments (nothing is launched), DIS_ECUDA if a CUDA call fails. */
+ * Returns DIS_EINVAL for n_patches outside 1..DIS_STATIC_MAX_PATCHES, a
+ * reactive material with a product closure of its own (not covered), or
+ * other bad arguments (nothing is launched), DIS_ECUDA if a CUDA call
+ * fails. */
 int dis_cfl_dt_static(int dim, int n_patches, const dis_patch* patches,
                       const dis_material* materials, int reactive_material, double cfl,
                       const double* d_state, double* d_dt, void* stream);

@@ -33,8 +33,8 @@ import math
 
 import torch
 
-from .closures import (Gamma, cons_to_prim, hencky_dev, mixture_props, phases,
-                       prim_to_cons, shear_modulus, stress, temperature)
+from .closures import (Gamma, cons_to_prim, hencky_dev, inv_gamma, mixture_props, phases,
+                       prim_to_cons, shear_modulus, stress, temperature, two_eos)
 from .reconstruction import (bvd_select, muscl_faces, thinc_beta, thinc_faces,
                              youngs_abs_normal)
 from .riemann import hllc
@@ -374,7 +374,16 @@ def plastic_update(q, mats, dt, iters=64):
     Jst = _sqrt0(J2)
     num = torch.zeros_like(Jst)
     den = torch.zeros_like(Jst)
-    for m, ph, ar in zip(mats, phis, (q["ar1"], q["ar2"])):
+    # phi_l / Gamma_l weights (a two-closure reactive mixture: 1 / Gamma_y at
+    # the state's own reactant share)
+    if any(two_eos(m) for m in mats):
+        wq = cons_to_prim(q, mats)
+        y = next(i for i, m in enumerate(mats) if m["reactive"])
+        lam_q = q["arl"] / q["ar1" if y == 0 else "ar2"]
+        igs = [inv_gamma(m, wq["p"], lam_q) for m in mats]
+    else:
+        igs = [1.0 / Gamma(m) for m in mats]
+    for m, ph, ar, ig in zip(mats, phis, (q["ar1"], q["ar2"]), igs):
         # G(rho_l) of the material's own density (constant but for Romenskii)
         Gl = shear_modulus(m, ar / ph)
         if m["G"] == 0.0:
@@ -399,8 +408,8 @@ def plastic_update(q, mats, dt, iters=64):
                 lo = torch.where(neg, mid, lo)
                 hi = torch.where(neg, hi, mid)
             Jl = 0.5 * (lo + hi)
-        num = num + ph / Gamma(m) * Jl
-        den = den + ph / Gamma(m)
+        num = num + ph * ig * Jl
+        den = den + ph * ig
     Jnew = num / den
     scale = torch.where(Jst > 0, Jnew / torch.where(Jst > 0, Jst, torch.ones_like(Jst)),
                         torch.zeros_like(Jst))

@@ -38,7 +38,8 @@ class DisMaterial(ctypes.Structure):
                 ("reactive", c_int32), ("Q", c_double), ("cv", c_double), ("A", c_double),
                 ("T_act", c_double), ("rate_law", c_int32), ("p_ign", c_double), ("eos", c_int32),
                 ("rho0", c_double), ("K0", c_double), ("alpha", c_double), ("beta", c_double),
-                ("jwl_A", c_double), ("jwl_B", c_double), ("jwl_R1", c_double), ("jwl_R2", c_double)]
+                ("jwl_A", c_double), ("jwl_B", c_double), ("jwl_R1", c_double), ("jwl_R2", c_double),
+                ("prod_gamma", c_double), ("prod_p_inf", c_double), ("prod_cv", c_double)]
 
 
 class DisPatch(ctypes.Structure):

@@ -49,6 +49,7 @@ __device__ __forceinline__ PhysT<Dual> lift_phys(const Phys& P, int k) {
     d.iGm1 = m.iGm1; d.gi = m.gi; d.kap = m.kap; d.gG = m.gG; d.GoG = m.GoG; d.JY = m.JY;
     d.eos = m.eos; d.rho0 = m.rho0; d.K0 = m.K0; d.ar = m.ar; d.br = m.br;
     d.jA = m.jA; d.jB = m.jB; d.jR1 = m.jR1; d.jR2 = m.jR2;
+    d.two = m.two; d.pg = m.pg; d.ppi = m.ppi; d.pcv = m.pcv;
   }
   D.y = P.y;
   D.thinc = P.thinc;

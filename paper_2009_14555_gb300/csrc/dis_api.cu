@@ -793,6 +793,10 @@ MatDev to_dev(const dis_material& m) {
   d.jB = m.jwl_B;
   d.jR1 = m.jwl_R1;
   d.jR2 = m.jwl_R2;
+  d.two = m.reactive && m.prod_gamma > 0.0 ? 1 : 0;
+  d.pg = d.two ? m.prod_gamma : m.gamma;
+  d.ppi = d.two ? m.prod_p_inf : m.p_inf;
+  d.pcv = d.two ? m.prod_cv : m.cv;
   d.pign = m.reactive ? m.p_ign : 0.0;
   d.iGm1 = 1.0 / (m.gamma - 1.0);
   d.gi = m.gamma * d.iGm1;
@@ -889,7 +893,14 @@ int dis_set_materials(dis_ctx* c, const dis_material* m, int n) {
       return fail(DIS_EINVAL, "dis_set_materials: JWL needs rho0, R1, R2 > 0 and G = 0");
     if (m[l].reactive && m[l].eos != DIS_EOS_STIFFENED)
       return fail(DIS_EINVAL, "dis_set_materials: the reactive material must be a stiffened (ideal) gas");
-    if (m[l].reactive && (m[l].p_inf != 0 || m[l].G != 0 || !(m[l].cv > 0)))
+    const bool two = m[l].reactive && m[l].prod_gamma > 0.0;
+    if (two && (!(m[l].prod_gamma > 1.0) || m[l].prod_p_inf < 0 || !(m[l].prod_cv > 0) || m[l].G != 0 ||
+                !(m[l].cv > 0)))
+      return fail(DIS_EINVAL, "dis_set_materials: product closure needs prod_gamma > 1, prod_p_inf >= 0, "
+                              "prod_cv > 0 (and G = 0, cv > 0)");
+    if (two && c->fp32)
+      return fail(DIS_EINVAL, "dis_set_materials: two reactive closures are built for float64 contexts only");
+    if (m[l].reactive && !two && (m[l].p_inf != 0 || m[l].G != 0 || !(m[l].cv > 0)))
       return fail(DIS_EINVAL, "dis_set_materials: a reactive material must be an ideal gas with cv > 0");
     if (m[l].reactive && (m[l].rate_law < 0 || m[l].rate_law > 1 || !std::isfinite(m[l].p_ign) ||
                           !std::isfinite(m[l].A) || m[l].A < 0))

@@ -116,6 +116,7 @@ MatDev dev_material(const dis_material& m) {
   d.jB = m.jwl_B;
   d.jR1 = m.jwl_R1;
   d.jR2 = m.jwl_R2;
+  d.two = 0;
   return d;
 }
 
@@ -138,8 +139,11 @@ extern "C" int dis_cfl_dt_static(int dim, int n_patches, const dis_patch* patche
   if (!(cfl > 0.0 && cfl <= 1.0)) return dis_internal_error(DIS_EINVAL, "dis_cfl_dt_static: cfl not in (0, 1]");
   if (reactive_material < -1 || reactive_material > 1)
     return dis_internal_error(DIS_EINVAL, "dis_cfl_dt_static: reactive_material must be -1, 0 or 1");
-  for (int l = 0; l < 2; ++l)
+  for (int l = 0; l < 2; ++l) {
     if (!(materials[l].gamma > 1.0)) return dis_internal_error(DIS_EINVAL, "dis_cfl_dt_static: gamma <= 1");
+    if (materials[l].reactive && materials[l].prod_gamma > 0.0)
+      return dis_internal_error(DIS_EINVAL, "dis_cfl_dt_static: a reactive material with two closures is not covered");
+  }
   const int nf = (dim == 2 ? 11 : 8) + (reactive_material >= 0 ? 1 : 0);
   long long maxcells = 0;
   for (int p = 0; p < n_patches; ++p) {

@@ -45,15 +45,21 @@ __device__ __forceinline__ PrimT<T> prim_of(const PhysT<T>& P, const T* q) {
   }
   const StrainT<T> s = strain_of(w.V11, w.V12, w.V21, w.V22, w.V33);
   const T KE = 0.5 * (mx * w.u + my * w.v);
-  w.p = (E - KE - ref_energy(P, phi, a1, a2, arl, s.J2)) / xi_of(P, phi);
+  if (RX && P.m[P.y].two) {
+    T sh;
+    w.p = mixture_pressure(P, phi, a1, a2, arl, E - KE, s.J2, sh);
+  } else {
+    w.p = (E - KE - ref_energy(P, phi, a1, a2, arl, s.J2)) / xi_of(P, phi);
+  }
   return w;
 }
 
 // Primitive -> conservative state of one cell (mixture rules; the energy from
 // the Mie-Grueneisen form), in place on the NF slots.
 template <int DIM, bool RX, class T>
-__device__ __forceinline__ void cons_of(const PhysT<T>& P, T* v) {
+__device__ __forceinline__ void cons_of(const PhysT<T>& P0, T* v) {
   using L = Lay<DIM, RX>;
+  const PhysT<T> P = at_state(P0, RX ? v[Lay<DIM, RX>::AL > 0 ? Lay<DIM, RX>::AL : 0] : T(0.0), v[L::E]);
   const T phi = v[L::PHI], r1 = v[L::A1], r2 = v[L::A2];
   const T u = v[L::MX], p = v[L::E];
   T vv = 0.0, v12 = 0.0, v21 = 0.0, arl = 0.0;
@@ -247,7 +253,22 @@ __device__ __forceinline__ void sources(const PhysT<T>& P, double dt, T* o) {
     v12 = o[L::V12];
     v21 = o[L::V21];
   }
-  plastic(P, o[L::PHI], T(dt), o[L::V11], v12, v21, o[L::V22], o[L::V33], o[L::A1] / o[L::PHI],
+  // (a two-closure reactive mixture weighs its material by 1 / Gamma_y at the
+  // state's own share, from the pressure of the conservative state)
+  PhysT<T> Pp = P;
+  if constexpr (RX) {
+    if (P.m[P.y].two) {
+      const T rr = o[L::A1] + o[L::A2];
+      T my_ = 0.0;
+      if constexpr (DIM == 2) my_ = o[L::MY];
+      const T KE0 = 0.5 * (o[L::MX] * o[L::MX] + my_ * my_) / rr;
+      const StrainT<T> s0 = strain_of(o[L::V11], v12, v21, o[L::V22], o[L::V33]);
+      T sh;
+      const T p0 = mixture_pressure(P, o[L::PHI], o[L::A1], o[L::A2], o[L::AL], o[L::E] - KE0, s0.J2, sh);
+      Pp = at_state(P, o[L::AL] / (P.y == 0 ? o[L::A1] : o[L::A2]), p0);
+    }
+  }
+  plastic(Pp, o[L::PHI], T(dt), o[L::V11], v12, v21, o[L::V22], o[L::V33], o[L::A1] / o[L::PHI],
           o[L::A2] / (1.0 - o[L::PHI]));
   if constexpr (DIM == 2) {
     o[L::V12] = v12;
@@ -269,13 +290,19 @@ __device__ __forceinline__ void sources(const PhysT<T>& P, double dt, T* o) {
     const T p0 = (o[L::E] - KE - ref_energy(P, phi1, o[L::A1], o[L::A2], T(0.0), s.J2)) / xi;
     const T Tfac = m.iGm1 / ((ary / phy) * m.cv);  // T = p / (rho_y Gamma c_V)
     const T Qx = m.Q / xi;
-    // the rate of phi_y rho_y lam at Lm = phi_y rho_y lam, other fields frozen
+    // the rate of phi_y rho_y lam at Lm = phi_y rho_y lam, other fields frozen;
+    // two closures: the pressure of each stage from the root finder
     auto f = [&](T Lm) -> T {
-      if (m.law == 1) {  // -k sqrt(lam) rho_y phi_y where p > p_ign
-        const T pk = p0 - Qx * Lm;
-        return pk > m.pign && Lm > 0.0 ? -m.A * sqrt(ary * Lm) : T(0.0);
+      T pk;
+      if (m.two) {
+        T sh;
+        pk = mixture_pressure(P, phi1, o[L::A1], o[L::A2], Lm, o[L::E] - KE, s.J2, sh);
+      } else {
+        pk = p0 - Qx * Lm;
       }
-      const T Tk = (p0 - Qx * Lm) * Tfac;
+      if (m.law == 1)  // -k sqrt(lam) rho_y phi_y where p > p_ign
+        return pk > m.pign && Lm > 0.0 ? -m.A * sqrt(ary * Lm) : T(0.0);
+      const T Tk = m.two ? mix_temperature(m, Lm / ary, pk, ary / phy) : pk * Tfac;
       return Tk > 0.0 ? -m.A * Lm * exp(-m.Tact / Tk) : T(0.0);
     };
     const T L0 = o[L::AL];

@@ -46,6 +46,8 @@ struct MatT {
   int eos;                  // EOS_SG, EOS_ROMENSKII or EOS_JWL
   R rho0, K0, ar, br;       // Romenskii: reference density, K0, exponents alpha-bar, beta-bar
   R jA, jB, jR1, jR2;       // JWL constants (rho0 shared)
+  int two;                  // reactive material with a product closure of its own
+  R pg, ppi, pcv;           // product gamma, p_inf, C_V (two closures)
   int law;  // reaction rate law: 0 Arrhenius, 1 A sqrt(lam) above the pressure pign
   R pign;
   R iGm1;  // 1 / (gamma - 1)
@@ -83,6 +85,7 @@ inline PhysT<float> to_float(const Phys& P) {
     m.GoG = (float)d.GoG; m.JY = (float)d.JY;
     m.eos = d.eos; m.rho0 = (float)d.rho0; m.K0 = (float)d.K0; m.ar = (float)d.ar; m.br = (float)d.br;
     m.jA = (float)d.jA; m.jB = (float)d.jB; m.jR1 = (float)d.jR1; m.jR2 = (float)d.jR2;
+    m.two = d.two; m.pg = (float)d.pg; m.ppi = (float)d.ppi; m.pcv = (float)d.pcv;
   }
   f.y = P.y;
   f.thinc = P.thinc;
@@ -170,6 +173,50 @@ __device__ __forceinline__ RefT<T> ref_curves(const MatT<R>& m, T r, T J2) {
   return o;
 }
 
+// Reactive material with distinct reactant and product closures (Section
+// 2.3.1, Appendix B), both stiffened gases without shear modulus: the
+// reactant takes the material's gamma, p_inf, C_V, the product pg, ppi, pcv.
+// With s = lam rho_y / rho_alpha the reactant's share of the mixture volume,
+// the pressure function depends on the densities through s only:
+// 1 / Gamma_y = s / Gamma_a + (1 - s) / Gamma_b, kappa_y = s kappa_a +
+// (1 - s) kappa_b; the temperature equality T_a = T_b gives s in closed form
+// at a known pressure, and by bisection over s in [0, 1] from the
+// conservative state (mixture_pressure).
+template <class T>
+__device__ __forceinline__ T mix_share(const MatT<T>& m, T lam, T p) {
+  const T wa = lam * (m.gamma - 1.0) * m.cv * (p + m.pg * m.ppi);
+  const T wb = (1.0 - lam) * (m.pg - 1.0) * m.pcv * (p + m.gamma * m.pinf);
+  return wa / (wa + wb);
+}
+template <class T>
+__device__ __forceinline__ void mix_consts(const MatT<T>& m, T s, T& iG, T& kap) {
+  iG = s / (m.gamma - 1.0) + (1.0 - s) / (m.pg - 1.0);
+  kap = s * (m.gamma * m.pinf / (m.gamma - 1.0)) + (1.0 - s) * (m.pg * m.ppi / (m.pg - 1.0));
+}
+// The closures with the reactive material's effective constants at (lam, p)
+// (unchanged without two closures), so the reduced stiffened-gas forms hold:
+// gi p + kap = rho_y c_y^2 / Gamma_y with gi = 1 + 1 / Gamma_y.
+template <class T>
+__device__ __forceinline__ PhysT<T> at_state(const PhysT<T>& P, T lam, T p) {
+  PhysT<T> Q = P;
+  if (P.y >= 0 && P.m[P.y].two) {
+    MatT<T>& m = Q.m[P.y];
+    T iG, kap;
+    mix_consts(m, mix_share(m, lam, p), iG, kap);
+    m.iGm1 = iG;
+    m.kap = kap;
+    m.gi = 1.0 + iG;
+  }
+  return Q;
+}
+// Common temperature of a two-closure mixture at phasic density r:
+// sum_k share_k (p + gamma_k p_inf,k) / (Gamma_k C_V,k) / r.
+template <class T>
+__device__ __forceinline__ T mix_temperature(const MatT<T>& m, T lam, T p, T r) {
+  const T s = mix_share(m, lam, p);
+  return (s * (p + m.gamma * m.pinf) / ((m.gamma - 1.0) * m.cv) + (1.0 - s) * (p + m.pg * m.ppi) / ((m.pg - 1.0) * m.pcv)) / r;
+}
+
 // Shear modulus of a material at phasic density r (constant but for Romenskii).
 template <class T, class R>
 __device__ __forceinline__ T shear_of(const MatT<R>& m, T r) {
@@ -213,6 +260,47 @@ __device__ __forceinline__ T ref_energy(const PhysT<T>& P, T phi1, T ar1, T ar2,
 template <class T>
 __device__ __forceinline__ T xi_of(const PhysT<T>& P, T phi1) {
   return phi1 * P.m[0].iGm1 + (1.0 - phi1) * P.m[1].iGm1;
+}
+
+// Pressure of a state whose reactive material has two closures, from its
+// conservative variables (Appendix B): bisection of the temperature-equality
+// residual (1 - lam)(pg - 1) pcv (p + gamma p_inf) s - lam (gamma - 1) cv
+// (p + pg ppi)(1 - s) over s in [0, 1] (64 halvings), the pressure at each s
+// from the pressure function; s_out receives the share.
+template <class T>
+__device__ __forceinline__ T mixture_pressure(const PhysT<T>& P, T phi1, T ar1, T ar2, T arl, T rhoe, T J2,
+                                              T& s_out) {
+  const int y = P.y, x = 1 - P.y;
+  const MatT<T>& m = P.m[y];
+  const MatT<T>& mi = P.m[x];
+  const T phx = x == 0 ? phi1 : 1.0 - phi1, phy = y == 0 ? phi1 : 1.0 - phi1;
+  const T arx = x == 0 ? ar1 : ar2, ary = y == 0 ? ar1 : ar2;
+  T Rx;
+  if (mi.eos == EOS_SG) {
+    Rx = phx * (mi.kap + mi.gG * J2) + arx * mi.einf;
+  } else {
+    const T r = arx / phx;
+    const RefT<T> c = ref_curves(mi, r, J2);
+    Rx = arx * (c.e - c.p * mi.iGm1 / r);
+  }
+  const T xix = phx * mi.iGm1;
+  const T num0 = rhoe - Rx + m.Q * (ary - arl);
+  const T lam = arl / ary;
+  T lo = 0.0, hi = 1.0;
+  for (int it = 0; it < 64; ++it) {
+    const T s = 0.5 * (lo + hi);
+    T iG, kap;
+    mix_consts(m, s, iG, kap);
+    const T p = (num0 - phy * kap) / (xix + phy * iG);
+    const T g = (1.0 - lam) * (m.pg - 1.0) * m.pcv * (p + m.gamma * m.pinf) * s -
+                lam * (m.gamma - 1.0) * m.cv * (p + m.pg * m.ppi) * (1.0 - s);
+    if (g < 0.0) lo = s;
+    else hi = s;
+  }
+  s_out = 0.5 * (lo + hi);
+  T iG, kap;
+  mix_consts(m, s_out, iG, kap);
+  return (num0 - phy * kap) / (xix + phy * iG);
 }
 
 // rho_l c_l^2 / Gamma_l of one material at pressure p (Mie-Grueneisen form,
@@ -331,7 +419,8 @@ struct FStateT {
 using FState = FStateT<double>;
 
 template <int DIR, class T>
-__device__ __forceinline__ FStateT<T> face_state(const PhysT<T>& P, const PrimT<T>& w) {
+__device__ __forceinline__ FStateT<T> face_state(const PhysT<T>& P0, const PrimT<T>& w) {
+  const PhysT<T> P = at_state(P0, w.lam, w.p);  // two-closure reactive mixture at (lam, p)
   FStateT<T> s;
   const StrainT<T> st = strain_of(w.V11, w.V12, w.V21, w.V22, w.V33);
   s.phi = w.phi;

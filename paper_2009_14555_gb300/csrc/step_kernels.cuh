@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(SEG) k_prim(Phys P, StepArgs A, const int4* __
     if (rate_on && i >= 0 && i < pd.nx && j >= 0 && j < pd.ny) {
       const Strain s = strain_of(w.V11, w.V12, w.V21, w.V22, w.V33);
       const double rho = w.phi * w.r1 + (1.0 - w.phi) * w.r2;
-      const double cL2 = cL2_of(P, w.phi, rho, w.p, s.J2, w.r1, w.r2);
+      const double cL2 = cL2_of(at_state(P, w.lam, w.p), w.phi, rho, w.p, s.J2, w.r1, w.r2);
       // a state that has lost hyperbolicity (or a density) is reported, not stepped silently
       if (!(cL2 > 0.0) || !(rho > 0.0)) flag_bad(A.status, g.x, i + pd.nx * j);
       const double cL = sqrt(fmax(cL2, 0.0));
@@ -257,7 +257,7 @@ __device__ __forceinline__ void add_geometric(const Phys& P, const double* q, co
   using L = Lay<DIM, RX>;
   const double ir = 1.0 / r;
   const Strain st = strain_of(w.V11, w.V12, w.V21, w.V22, w.V33);
-  const double Gm2 = 2.0 * Gmix_of(P, w.phi, w.r1, w.r2);
+  const double Gm2 = 2.0 * Gmix_of(at_state(P, w.lam, w.p), w.phi, w.r1, w.r2);
   const double srr = -w.p + Gm2 * st.H11, szr = Gm2 * st.H12, stt = -w.p + Gm2 * st.H33;
   const double ur = w.u, uz = w.v;
   const double rho = q[L::A1] + q[L::A2];
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(SEG) k_pack(const PatchDev* __restrict__ pds,
 __device__ __forceinline__ bool hyperbolic(const Phys& P, const Prim& w) {
   const Strain st = strain_of(w.V11, w.V12, w.V21, w.V22, w.V33);
   const double rho = w.phi * w.r1 + (1.0 - w.phi) * w.r2;
-  return cL2_of(P, w.phi, rho, w.p, st.J2, w.r1, w.r2) > 0.0;
+  return cL2_of(at_state(P, w.lam, w.p), w.phi, rho, w.p, st.J2, w.r1, w.r2) > 0.0;
 }
 
 // Edge states of cell k along axis D (MUSCL, MUSCL-BVD-THINC on phi, the

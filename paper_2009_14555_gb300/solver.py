@@ -22,7 +22,9 @@ def _material(m: dict) -> L.DisMaterial:
                          int(m.get("rate_law", 0)), float(m.get("p_ign", 0.0)), _EOS[m.get("eos", "sg")],
                          float(m.get("rho0", 0.0)), float(m.get("K0", 0.0)), float(m.get("alpha_r", 0.0)),
                          float(m.get("beta_r", 0.0)), float(m.get("jwl_A", 0.0)), float(m.get("jwl_B", 0.0)),
-                         float(m.get("jwl_R1", 0.0)), float(m.get("jwl_R2", 0.0)))
+                         float(m.get("jwl_R1", 0.0)), float(m.get("jwl_R2", 0.0)),
+                         float(m.get("prod_gamma", 0.0)), float(m.get("prod_p_inf", 0.0)),
+                         float(m.get("prod_cv", 0.0)))
 
 
 def _patch(p, dim) -> L.DisPatch:

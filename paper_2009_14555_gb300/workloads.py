@@ -309,7 +309,8 @@ def reactive_plate_2d(nx: int = 2048, ny: int = 1024, steps: int = 1000, seed: i
                     steps, True, reactive_material=1, extra=dict(T0=T0))
 
 
-def detonation_copper_1d(n: int = 1000, steps: int = 400, name=None, copper: str = "romenskii") -> Workload:
+def detonation_copper_1d(n: int = 1000, steps: int = 400, name=None, copper: str = "romenskii",
+                         explosive: str = "standin") -> Workload:
     """The shape of the one-dimensional test of Section 4.1 on [0, 0.4] m:
     quiescent elastic copper for x < 0.15, ambient explosive for
     0.15 < x < 0.35, a booster of the same explosive at 1e9 Pa for x > 0.35,
@@ -323,10 +324,12 @@ def detonation_copper_1d(n: int = 1000, steps: int = 400, name=None, copper: str
     paper's two-EOS multiphase explosive is not among the closures built
     here): an ideal-gas reactant/product pair with the product's gamma 3,
     c_V 1000 and Q = 3.68 MJ/kg and the reactant's rho_0 = 1600 kg/m^3 from the
-    table of the generic explosive.
+    table of the generic explosive; explosive="generic" takes that table's
+    two closures (generic_explosive, float64 contexts).
     """
     copper = (COPPER_ROMENSKII if copper == "romenskii" else material(3.0, p_inf=136.5e9 / 3.0, G=39.4e9))
-    expl = material(3.0, reactive=1, Q=3.68e6, cv=1000.0, A=2.0e6, rate_law=1, p_ign=1.0e8)
+    expl = (generic_explosive() if explosive == "generic" else
+            material(3.0, reactive=1, Q=3.68e6, cv=1000.0, A=2.0e6, rate_law=1, p_ign=1.0e8))
     w, k = _blank(1, True, 1, n)
     dx = 0.4 / n
     xc = (np.arange(n) + 0.5) * dx

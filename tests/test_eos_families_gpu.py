@@ -93,3 +93,34 @@ def test_no_alloc_cfl_dt_on_romenskii_state():
     wl = _copper_disc_2d(48, 1)
     cons, ref = reference(wl)
     np.testing.assert_allclose(static_dt(wl, cons), ref, rtol=1e-12)
+
+
+# ---- the generic explosive: reactant and product closures of their own,
+# ---- component densities from the temperature equality (Appendix B)
+def _generic_detonation(n=200, steps=30):
+    return W.detonation_copper_1d(n, steps=steps, explosive="generic",
+                                  name=f"1d_detonation_generic_explosive_{n}")
+
+
+def test_generic_explosive_detonation_fp64():
+    """Section 4.1's test with the table's explosive and Romenskii copper:
+    booster ignition and the detonation's first 30 steps, strict bar."""
+    assert_parity(_generic_detonation(), 30)
+
+
+def test_generic_explosive_detonation_to_the_copper_fp64():
+    """150 steps: the detonation runs into the copper (bar 1e-10 or 10x the
+    oracle's one-ulp spread)."""
+    assert_parity(_generic_detonation(200, 150), 150, calibrate=True)
+
+
+def test_generic_explosive_refused_in_fp32_bulk_and_adjoint():
+    from paper_2009_14555_gb300.solver import Solver
+    wl = _generic_detonation(64, 2)
+    with pytest.raises(RuntimeError):
+        Solver.from_workload(wl, precision="fp32_bulk")
+    s = Solver.from_workload(wl)
+    s.set_prim([wl.patches[0].prim])
+    with pytest.raises(RuntimeError):
+        s.adj_forward(2, every=1, material=0)
+    s.close()
