@@ -487,10 +487,11 @@ def batch_bench(steps=300, warmup=3):
         ms = e0.elapsed_time(e1) / steps
         rc, bp, bc = s.check()
         # problems whose state left the finite range (each problem is independent)
-        bad = sum(int(not np.isfinite(a).all()) for a in s.get_arrays())
+        bad_ids = [k for k, a in enumerate(s.get_arrays()) if not np.isfinite(a).all()]
+        bad = len(bad_ids)
         b = 2 * state_bytes(1, False, prec)
         out[prec] = {"value": wl.cells / (ms * 1e-3), "ms_per_step": ms, "steps": steps,
-                     "launches": s.launches, "nonfinite_problems": bad,
+                     "launches": s.launches, "nonfinite_problems": bad, "nonfinite_ids": bad_ids[:16],
                      "first_flagged": [int(bp), int(bc)] if rc else None,
                      "algorithmic_bytes_per_cell_update": b,
                      "hbm_frac": b * wl.cells / (ms * 1e-3) / 1e9 / peaks()[0]}

@@ -257,8 +257,11 @@ long long dis_last_launches(const dis_ctx* ctx);
  * cells per CTA of 256, 512, 256 threads; 1D 122, 250, 506 cells per CTA of
  * 128, 256, 512 threads) and register budget v / 3 (2D: 768 or 1024 resident
  * threads per SM; 1D: no limit, or at most 64 registers per thread).  The
- * limiter is compiled into the face code: a DIS_VANLEER context has one
- * variant (5 in 2D, 1 in 1D).  The first
+ * limiter and the closure family are compiled into the kernels: a
+ * DIS_VANLEER context of stiffened gases has one variant (5 in 2D, 1 in 1D),
+ * a context with a Romenskii or JWL material one (2 in 2D, 1 in 1D; limiter
+ * read at run time); changing the materials between the families returns a
+ * fixed variant that no longer applies to tuning.  The first
  * dis_step times one step of every variant (the last stage writing a scratch
  * buffer, so the state is unchanged) and keeps the fastest.  Returns the
  * chosen shape (0 x 0 before tuning or for float64 contexts), precomputed = 0
@@ -267,8 +270,8 @@ long long dis_last_launches(const dis_ctx* ctx);
 #define DIS_NVARIANTS 6
 int dis_tile_choice(const dis_ctx* ctx, int* tx, int* ty, int* precomputed, double* step_ms);
 
-/* Fix the FP32-bulk stage variant (0 .. DIS_NVARIANTS - 1; a DIS_VANLEER
- * context only its one variant) or return to tuning on the next step (-1).  For tests and measurements; the
+/* Fix the FP32-bulk stage variant (0 .. DIS_NVARIANTS - 1; a context with
+ * one variant only that one) or return to tuning on the next step (-1).  For tests and measurements; the
  * result of a step does not depend on the variant beyond float32 rounding
  * order.  DIS_EINVAL for float64 contexts or an out-of-range variant. */
 int dis_set_variant(dis_ctx* ctx, int variant);

@@ -288,38 +288,45 @@ StepArgs32 base_args32(dis_ctx* c) {
   return a;
 }
 
-template <int DIM, bool RX, int TX, int TY, int NT, int MINB, bool CYL, int LIM = 0>
+template <int DIM, bool RX, int TX, int TY, int NT, int MINB, bool CYL, int LIM = 0, bool GEN = false>
 void stage_fused_c(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
   constexpr size_t smem = fused32_smem<DIM, RX, TX, TY>();
   static bool attr_set = false;  // per instantiation, per process
   if (!attr_set) {
-    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT, MINB, CYL, LIM>,
+    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT, MINB, CYL, LIM, GEN>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT, MINB, CYL, LIM>,
+    cudaFuncSetAttribute(k_stage32<DIM, RX, TX, TY, NT, MINB, CYL, LIM, GEN>,
                          cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr_set = true;
   }
-  k_stage32<DIM, RX, TX, TY, NT, MINB, CYL, LIM><<<(unsigned)c->tiles[shape].size(), NT, smem, st>>>(
+  k_stage32<DIM, RX, TX, TY, NT, MINB, CYL, LIM, GEN><<<(unsigned)c->tiles[shape].size(), NT, smem, st>>>(
       c->phys, c->physf, a, c->d_tiles[shape]);
 }
 
 // Planar and cylindrical contexts run separate instantiations, so the
 // geometric source costs the planar kernels nothing.
-template <int DIM, bool RX, int TX, int TY, int NT, int MINB, int LIM = 0>
+template <int DIM, bool RX, int TX, int TY, int NT, int MINB, int LIM = 0, bool GEN = false>
 void stage_fused(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
-  if (c->phys.cyl) stage_fused_c<DIM, RX, TX, TY, NT, MINB, true, LIM>(c, st, a, shape);
-  else stage_fused_c<DIM, RX, TX, TY, NT, MINB, false, LIM>(c, st, a, shape);
+  if (c->phys.cyl) stage_fused_c<DIM, RX, TX, TY, NT, MINB, true, LIM, GEN>(c, st, a, shape);
+  else stage_fused_c<DIM, RX, TX, TY, NT, MINB, false, LIM, GEN>(c, st, a, shape);
 }
+
+// A Romenskii or JWL material in the context: the kernels carry the general
+// closures (stiffened-gas contexts run kernels without that code).
+bool general_closures(const dis_ctx* c) { return c->phys.m[0].eos != EOS_SG || c->phys.m[1].eos != EOS_SG; }
 
 // FP32-bulk stage variants v = shape + 3 budget: the 3 tile shapes x two
 // register budgets (2D: 768 or 1024 resident threads per SM requested from
 // the register allocator; 1D: no limit, or 64 registers per thread).  The
-// limiter is a compile-time choice of the face code: minmod contexts have
-// every variant; van Leer contexts one (2D: 32 x 7 tile, 1024 threads per
-// SM; 1D: 250-cell tile).
-int vanleer_variant(const dis_ctx* c) { return c->dim == 2 ? 5 : 1; }
+// limiter and the closure family are compile-time choices of the kernels:
+// stiffened-gas minmod contexts have every variant; van Leer contexts and
+// contexts with general closures one (1D: the 250-cell tile; 2D: the 32 x 7
+// tile at 1024 threads per SM for van Leer, at 768 for the general closures,
+// whose code would spill at 64 registers; the general-closure kernel takes
+// the limiter at run time).
+int single_variant(const dis_ctx* c) { return c->dim == 2 ? (general_closures(c) ? 2 : 5) : 1; }
 bool variant_valid(const dis_ctx* c, int v) {
-  if (c->phys.limiter) return v == vanleer_variant(c);
+  if (c->phys.limiter || general_closures(c)) return v == single_variant(c);
   return v >= 0 && v < DIS_NVARIANTS;
 }
 
@@ -336,6 +343,11 @@ void stage_kernel_2d(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
 template <int DIM, bool RX>
 void stage_kernel_v(dis_ctx* c, cudaStream_t st, StepArgs32& a, int v) {
   const int shape = v % 3;
+  if (general_closures(c)) {  // the one general-closure instantiation
+    if constexpr (DIM == 2) stage_fused<DIM, RX, 32, 7, 256, 3, -1, true>(c, st, a, 2);
+    else stage_fused<DIM, RX, 250, 1, 256, 1, -1, true>(c, st, a, 1);
+    return;
+  }
   if (c->phys.limiter) {  // van Leer: the one instantiation
     if constexpr (DIM == 2) stage_fused<DIM, RX, 32, 7, 256, 4, 1>(c, st, a, 2);
     else stage_fused<DIM, RX, 250, 1, 256, 1, 1>(c, st, a, 1);
@@ -369,33 +381,37 @@ void cfl_pass32(dis_ctx* c, cudaStream_t st, unsigned long long* rate) {
 // Persistent 1D batch kernel (FP32-bulk), variant v: tile length v % 3,
 // 64 registers per thread for v >= 3; n steps in one launch, one CTA per
 // problem.  scratch_last (tuning, n = 1): the step ends in buffer 1.
-template <bool RX, int TX, int NT, int MINB, bool CYL, int LIM = 0>
+template <bool RX, int TX, int NT, int MINB, bool CYL, int LIM = 0, bool GEN = false>
 void batch_fused_c(dis_ctx* c, cudaStream_t st, const StepArgs32& a, int n, int scratch_last, int shape) {
   constexpr size_t smem = fused32_smem<1, RX, TX, 1>();
   static bool attr_set = false;  // per instantiation, per process
   if (!attr_set) {
-    cudaFuncSetAttribute(k_batch32<RX, TX, NT, MINB, CYL, LIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_batch32<RX, TX, NT, MINB, CYL, LIM, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
-    cudaFuncSetAttribute(k_batch32<RX, TX, NT, MINB, CYL, LIM>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         100);
+    cudaFuncSetAttribute(k_batch32<RX, TX, NT, MINB, CYL, LIM, GEN>,
+                         cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     attr_set = true;
   }
   Bufs32 b;
   for (int k = 0; k < 3; ++k) b.q[k] = c->q32[k];
-  k_batch32<RX, TX, NT, MINB, CYL, LIM><<<(unsigned)c->np, NT, smem, st>>>(
+  k_batch32<RX, TX, NT, MINB, CYL, LIM, GEN><<<(unsigned)c->np, NT, smem, st>>>(
       c->phys, c->physf, a, b, c->rate, c->d_order, c->d_tile0[shape], c->d_tiles[shape], n, scratch_last,
       c->rate_valid ? 1 : 0);
 }
 
-template <bool RX, int TX, int NT, int MINB, int LIM = 0>
+template <bool RX, int TX, int NT, int MINB, int LIM = 0, bool GEN = false>
 void batch_fused(dis_ctx* c, cudaStream_t st, const StepArgs32& a, int n, int scratch_last, int shape) {
-  if (c->phys.cyl) batch_fused_c<RX, TX, NT, MINB, true, LIM>(c, st, a, n, scratch_last, shape);
-  else batch_fused_c<RX, TX, NT, MINB, false, LIM>(c, st, a, n, scratch_last, shape);
+  if (c->phys.cyl) batch_fused_c<RX, TX, NT, MINB, true, LIM, GEN>(c, st, a, n, scratch_last, shape);
+  else batch_fused_c<RX, TX, NT, MINB, false, LIM, GEN>(c, st, a, n, scratch_last, shape);
 }
 
 template <bool RX>
 void batch_kernel_v(dis_ctx* c, cudaStream_t st, const StepArgs32& a, int n, int scratch_last, int v) {
   const int shape = v % 3;
+  if (general_closures(c)) {  // the one general-closure instantiation (250-cell tiles)
+    batch_fused<RX, 250, 256, 1, -1, true>(c, st, a, n, scratch_last, 1);
+    return;
+  }
   if (c->phys.limiter) {  // van Leer: the one instantiation (250-cell tiles)
     batch_fused<RX, 250, 256, 1, 1>(c, st, a, n, scratch_last, 1);
     return;
@@ -908,6 +924,7 @@ int dis_set_materials(dis_ctx* c, const dis_material* m, int n) {
   }
   for (int l = 0; l < 2; ++l) c->phys.m[l] = to_dev(m[l]);
   c->physf = to_float(c->phys);
+  if (c->fp32 && c->variant >= 0 && !variant_valid(c, c->variant)) c->variant = -1;  // tune again
   if (c->fp32 && c->have_mats && c->have_state && c->ws_ready &&
       (old.m[0].kap != c->phys.m[0].kap || old.m[1].kap != c->phys.m[1].kap)) {
     // an FP32-bulk state holds e_s = rho E - kappa(phi1): keep rho E

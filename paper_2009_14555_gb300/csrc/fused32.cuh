@@ -35,7 +35,7 @@ struct FSlots {
   static constexpr int PK = VB + 1, DD = VB + 2, N = VB + 3;
 };
 
-template <int DIM, bool RX, int DIR, int LIM>
+template <int DIM, bool RX, int DIR, int LIM, bool GEN>
 __device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__ Wsm, int HX, int HY, int hx,
                                        int hy, float dxn, float dxt, float* __restrict__ Fsm, int nfaces,
                                        int fidx) {
@@ -69,7 +69,7 @@ __device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__
         }
         return beta;
       };
-      c[s] = phi_cand_f<LIM>(ph[s], ph[s + 1], ph[s + 2], beta_of, P.thinc != 0);
+      c[s] = phi_cand_f<LIM>(ph[s], ph[s + 1], ph[s + 2], beta_of, P.thinc != 0, P.limiter);
     }
     float Lt, Rt;
     bvd_f(c[0], c[1], c[2], Lt, Rt);
@@ -92,8 +92,8 @@ __device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__
   PrimF wl, wr;
 #define DIS_RECF(fld)                                            \
   {                                                              \
-    const float s1 = limited_f<LIM>(w1.fld - w0.fld, w2.fld - w1.fld); \
-    const float s2 = limited_f<LIM>(w2.fld - w1.fld, w3.fld - w2.fld); \
+    const float s1 = limited_f<LIM>(w1.fld - w0.fld, w2.fld - w1.fld, P.limiter); \
+    const float s2 = limited_f<LIM>(w2.fld - w1.fld, w3.fld - w2.fld, P.limiter); \
     wl.fld = w1.fld + 0.5f * s1;                                 \
     wr.fld = w2.fld - 0.5f * s2;                                 \
   }
@@ -104,10 +104,10 @@ __device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__
 #undef DIS_RECF
   wl.phi = phiL;
   wr.phi = phiR;
-  FStateF sl = face_state_f<DIR>(P, wl);
-  if (!(sl.cL > 0.f)) sl = face_state_f<DIR>(P, w1);
-  FStateF sr = face_state_f<DIR>(P, wr);
-  if (!(sr.cL > 0.f)) sr = face_state_f<DIR>(P, w2);
+  FStateF sl = face_state_f<DIR, GEN>(P, wl);
+  if (!(sl.cL > 0.f)) sl = face_state_f<DIR, GEN>(P, w1);
+  FStateF sr = face_state_f<DIR, GEN>(P, wr);
+  if (!(sr.cL > 0.f)) sr = face_state_f<DIR, GEN>(P, w2);
   sl.cL = sqrtf(sl.cL);
   sr.cL = sqrtf(sr.cL);
   const FaceOutF o = hlld_f<DIR>(sl, sr);
@@ -182,7 +182,7 @@ __device__ __forceinline__ void tile_consts(const Phys& P, const StepArgs32& A, 
 
 // Phase 1: primitives of the tile t and its halo (ghosts by the index map)
 // into the shared-memory planes of sm, by the NT threads of the CTA.
-template <int DIM, bool RX, int TX, int TY, int NT>
+template <int DIM, bool RX, int TX, int TY, int NT, bool GEN>
 __device__ __forceinline__ void fill_tile(const Phys& P, const PhysF& F, const StepArgs32& A, const int4 t,
                                           float* __restrict__ sm) {
   using L = Lay<DIM, RX>;
@@ -199,7 +199,7 @@ __device__ __forceinline__ void fill_tile(const Phys& P, const PhysF& F, const S
     bool fx = false, fy = false;
     const int si = ghost_map(i, pd.nx, pd.bc[0], pd.bc[1], fx);
     const int sj = DIM == 2 ? ghost_map(j, pd.ny, pd.bc[2], pd.bc[3], fy) : 0;
-    PrimF w = cons_to_prim32<DIM, RX>(P, F, A.src, T, cidx(pd, si, sj));
+    PrimF w = cons_to_prim32<DIM, RX, GEN>(P, F, A.src, T, cidx(pd, si, sj));
     if (fx) { w.u = -w.u; w.V12 = -w.V12; w.V21 = -w.V21; }
     if (fy) { w.v = -w.v; w.V12 = -w.V12; w.V21 = -w.V21; }
     const int plane = HX * HY;
@@ -219,7 +219,7 @@ __device__ __forceinline__ void fill_tile(const Phys& P, const PhysF& F, const S
 
 // Phase 2: all x faces ((TX + 1) per interior row) and y faces (TX per face
 // row, TY + 1 face rows) of the tile, in one loop so the threads stay busy.
-template <int DIM, bool RX, int TX, int TY, int NT, int LIM>
+template <int DIM, bool RX, int TX, int TY, int NT, int LIM, bool GEN>
 __device__ __forceinline__ void faces_tile(const PhysF& F, const StepArgs32& A, const int4 t,
                                            float* __restrict__ sm) {
   using S = FSlots<DIM, RX>;
@@ -236,13 +236,13 @@ __device__ __forceinline__ void faces_tile(const PhysF& F, const StepArgs32& A, 
       const int fx = f % (TX + 1), fy = f / (TX + 1);
       const int i = i0 + fx, j = j0 + fy;  // face between cells i-1 and i
       if (i > pd.nx || (DIM == 2 && j >= pd.ny)) continue;
-      face32<DIM, RX, 0, LIM>(F, Wsm, HX, HY, fx + NG - 1, DIM == 2 ? fy + NG : 0, dxf, dyf, Fxs, NFX, f);
+      face32<DIM, RX, 0, LIM, GEN>(F, Wsm, HX, HY, fx + NG - 1, DIM == 2 ? fy + NG : 0, dxf, dyf, Fxs, NFX, f);
     } else if constexpr (DIM == 2) {
       const int g = f - NFX;
       const int fx = g % TX, fy = g / TX;
       const int i = i0 + fx, j = j0 + fy;  // face between rows j-1 and j
       if (i >= pd.nx || j > pd.ny) continue;
-      face32<DIM, RX, 1, LIM>(F, Wsm, HX, HY, fx + NG, fy + NG - 1, dyf, dxf, Fys, NFY, g);
+      face32<DIM, RX, 1, LIM, GEN>(F, Wsm, HX, HY, fx + NG, fy + NG - 1, dyf, dxf, Fys, NFY, g);
     }
   }
 }
@@ -252,7 +252,7 @@ __device__ __forceinline__ void faces_tile(const PhysF& F, const StepArgs32& A, 
 // steps and the CFL rate of the new state, by warp max into rate_cta (shared,
 // if not null) or A.rate_next[patch] (global)).  Every lane of a warp with a
 // tile cell reaches the warp max.
-template <int DIM, bool RX, int TX, int TY, int NT, bool CYL = false>
+template <int DIM, bool RX, int TX, int TY, int NT, bool CYL, bool GEN>
 __device__ __forceinline__ void update_tile(const Phys& P, const PhysF& F, const StepArgs32& A, const int4 t,
                                             const float* __restrict__ sm, const TileConst& K,
                                             unsigned* rate_cta) {
@@ -334,7 +334,7 @@ __device__ __forceinline__ void update_tile(const Phys& P, const PhysF& F, const
       }
       const StrainF st = strain_f(Wsm[L::V11 * plane + kc], v12, v21, Wsm[L::V22 * plane + kc],
                                   Wsm[L::V33 * plane + kc]);
-      const float Gm2 = 2.f * Gmix_f(F, wphi, Wsm[L::A1 * plane + kc], Wsm[L::A2 * plane + kc]);
+      const float Gm2 = 2.f * Gmix_f<GEN>(F, wphi, Wsm[L::A1 * plane + kc], Wsm[L::A2 * plane + kc]);
       const float srr = -wp + Gm2 * st.H11, szr = Gm2 * st.H12, stt = -wp + Gm2 * st.H33;
       const float r = (float)pd.x0 + ((float)i + 0.5f) * dxf;
       const float ir = 1.f / r;
@@ -397,7 +397,7 @@ __device__ __forceinline__ void update_tile(const Phys& P, const PhysF& F, const
         plastic(P, ph, dt, d11, d12, d21, d22, d33, (double)o[L::A1] / ph, (double)o[L::A2] / (1.0 - ph));
         o[L::V11] = (float)d11; v12 = (float)d12; v21 = (float)d21; o[L::V22] = (float)d22; o[L::V33] = (float)d33;
       } else {
-        plastic_f(F, ophf, dtf, o[L::V11], v12, v21, o[L::V22], o[L::V33], or1, or2);
+        plastic_f<GEN>(F, ophf, dtf, o[L::V11], v12, v21, o[L::V22], o[L::V33], or1, or2);
       }
       if constexpr (DIM == 2) { o[L::V12] = v12; o[L::V21] = v21; }
       if constexpr (RX) {
@@ -412,7 +412,7 @@ __device__ __forceinline__ void update_tile(const Phys& P, const PhysF& F, const
         const float KE = 0.5f * (mx * mx + my * my) / rr;
         const StrainF s = strain_f(o[L::V11], v12, v21, o[L::V22], o[L::V33]);
         const float xi = xi_f(F, ophf);
-        const float p0 = (o[L::E] - KE - soft_ref_f(F, ophf, o[L::A1], o[L::A2], 0.f, s.J2, or1, or2)) / xi;
+        const float p0 = (o[L::E] - KE - soft_ref_f<GEN>(F, ophf, o[L::A1], o[L::A2], 0.f, s.J2, or1, or2)) / xi;
         const float Tfac = m.iGm1 / ((ary / phy) * m.cv);
         const float Qx = m.Q / xi;
         auto fr_ = [&](float Lm) {
@@ -436,7 +436,8 @@ __device__ __forceinline__ void update_tile(const Phys& P, const PhysF& F, const
       for (int c = 0; c <= NF; ++c) bad |= !isfinite(o[c]);
       if (bad) flag_bad(A.status, t.x, i + pd.nx * j);
       // CFL rate of the new state: the next step's time step
-      rate = cfl_rate_of<DIM>(F, prim32_of<DIM, RX>(P, F, o), ihx_sh, ihy_sh, A.status, t.x, i + pd.nx * j);
+      rate = cfl_rate_of<DIM, GEN>(F, prim32_of<DIM, RX, GEN>(P, F, o), ihx_sh, ihy_sh, A.status, t.x,
+                                   i + pd.nx * j);
     }
 #pragma unroll
     for (int c = 0; c <= NF; ++c) A.dst[c * T + k] = o[c];
@@ -456,22 +457,22 @@ __device__ __forceinline__ void update_tile(const Phys& P, const PhysF& F, const
 // the tile's primitives and faces in the shared memory sm.  The stage kernel
 // runs it once per CTA; the persistent 1D batch kernel runs it for every tile
 // of its problem in turn (the caller synchronises the CTA between tiles).
-template <int DIM, bool RX, int TX, int TY, int NT, bool CYL = false, int LIM = 0>
+template <int DIM, bool RX, int TX, int TY, int NT, bool CYL = false, int LIM = 0, bool GEN = false>
 __device__ __forceinline__ void stage32_tile(const Phys& P, const PhysF& F, const StepArgs32& A, const int4 t,
                                              float* __restrict__ sm, unsigned* rate_cta) {
   __shared__ TileConst K;
   if (threadIdx.x == 0) tile_consts(P, A, t, K);
-  fill_tile<DIM, RX, TX, TY, NT>(P, F, A, t, sm);
+  fill_tile<DIM, RX, TX, TY, NT, GEN>(P, F, A, t, sm);
   __syncthreads();
-  faces_tile<DIM, RX, TX, TY, NT, LIM>(F, A, t, sm);
+  faces_tile<DIM, RX, TX, TY, NT, LIM, GEN>(F, A, t, sm);
   __syncthreads();
-  update_tile<DIM, RX, TX, TY, NT, CYL>(P, F, A, t, sm, K, rate_cta);
+  update_tile<DIM, RX, TX, TY, NT, CYL, GEN>(P, F, A, t, sm, K, rate_cta);
 }
 
-template <int DIM, bool RX, int TX, int TY, int NT, int MINB, bool CYL = false, int LIM = 0>
+template <int DIM, bool RX, int TX, int TY, int NT, int MINB, bool CYL = false, int LIM = 0, bool GEN = false>
 __global__ void __launch_bounds__(NT, MINB) k_stage32(Phys P, PhysF F, StepArgs32 A, const int4* __restrict__ tiles) {
   extern __shared__ __align__(16) float sm[];
-  stage32_tile<DIM, RX, TX, TY, NT, CYL, LIM>(P, F, A, tiles[blockIdx.x], sm, nullptr);
+  stage32_tile<DIM, RX, TX, TY, NT, CYL, LIM, GEN>(P, F, A, tiles[blockIdx.x], sm, nullptr);
 }
 
 // CFL rate of the state at the start of a step (FP32-bulk), for the first
@@ -509,7 +510,7 @@ struct Bufs32 {
   float* q[3];
 };
 
-template <bool RX, int TX, int NT, int MINB, bool CYL = false, int LIM = 0>
+template <bool RX, int TX, int NT, int MINB, bool CYL = false, int LIM = 0, bool GEN = false>
 __global__ void __launch_bounds__(NT, MINB) k_batch32(Phys P, PhysF F, StepArgs32 A, Bufs32 B,
                                                       unsigned long long* rate, const int* __restrict__ order,
                                                       const int* __restrict__ tile0,
@@ -524,8 +525,8 @@ __global__ void __launch_bounds__(NT, MINB) k_batch32(Phys P, PhysF F, StepArgs3
   if (!rate_ready) {
     float r = 0.f;
     for (int i = threadIdx.x; i < pd.nx; i += NT)
-      r = fmaxf(r, cfl_rate_of<1>(F, cons_to_prim32<1, RX>(P, F, B.q[0], A.T, cidx(pd, i, 0)), 1.f / (float)pd.dx,
-                                  1.f, A.status, p, i));
+      r = fmaxf(r, cfl_rate_of<1, GEN>(F, cons_to_prim32<1, RX, GEN>(P, F, B.q[0], A.T, cidx(pd, i, 0)),
+                                       1.f / (float)pd.dx, 1.f, A.status, p, i));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, o));
     if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = r;
@@ -551,7 +552,7 @@ __global__ void __launch_bounds__(NT, MINB) k_batch32(Phys P, PhysF F, StepArgs3
       a.b = s0 ? 1.0 : (s1 ? 0.25 : 2.0 / 3.0);
       a.last = stg == 2;
       for (int t = ta; t < tb; ++t) {
-        stage32_tile<1, RX, TX, 1, NT, CYL, LIM>(P, F, a, tiles[t], sm, &rnext);
+        stage32_tile<1, RX, TX, 1, NT, CYL, LIM, GEN>(P, F, a, tiles[t], sm, &rnext);
         __syncthreads();
       }
     }

@@ -51,10 +51,13 @@ __device__ __forceinline__ float xi_f(const PhysF& P, float phi1) {
 // release of a stiffened gas; the whole reference part ar_l (E_ref,l -
 // p_ref,l / (rho_l Gamma_l)) of a Romenskii or JWL material (their kappa is
 // zero) at its phasic density r_l.
+// GEN: the kernels of contexts with a Romenskii or JWL material (GEN false:
+// stiffened gases only, and none of the general code is compiled in).
+template <bool GEN = true>
 __device__ __forceinline__ float soft_ref_f(const PhysF& P, float phi1, float ar1, float ar2, float arl,
                                             float J2, float r1, float r2) {
   float s;
-  if (P.m[0].eos == EOS_SG && P.m[1].eos == EOS_SG) {
+  if (!GEN || (P.m[0].eos == EOS_SG && P.m[1].eos == EOS_SG)) {
     s = (phi1 * P.m[0].gG + (1.f - phi1) * P.m[1].gG) * J2 + ar1 * P.m[0].einf + ar2 * P.m[1].einf;
   } else {
     s = 0.f;
@@ -75,24 +78,27 @@ __device__ __forceinline__ float soft_ref_f(const PhysF& P, float phi1, float ar
 }
 
 // Mixture shear modulus (phi / Gamma weights) at the phasic densities.
+template <bool GEN = true>
 __device__ __forceinline__ float Gmix_f(const PhysF& P, float phi1, float r1, float r2) {
   const float ixi = 1.f / xi_f(P, phi1);
-  if (P.m[0].eos == EOS_SG && P.m[1].eos == EOS_SG) return (phi1 * P.m[0].GoG + (1.f - phi1) * P.m[1].GoG) * ixi;
+  if (!GEN || (P.m[0].eos == EOS_SG && P.m[1].eos == EOS_SG))
+    return (phi1 * P.m[0].GoG + (1.f - phi1) * P.m[1].GoG) * ixi;
   return (phi1 * shear_of(P.m[0], r1) * P.m[0].iGm1 + (1.f - phi1) * shear_of(P.m[1], r2) * P.m[1].iGm1) * ixi;
 }
 
+template <bool GEN = true>
 __device__ __forceinline__ float cL2_f(const PhysF& P, float phi1, float rho, float p, float J2, float r1,
                                        float r2) {
   const float phi2 = 1.f - phi1;
   const float ixi = 1.f / xi_f(P, phi1);
-  if (P.m[0].eos == EOS_SG && P.m[1].eos == EOS_SG) {
+  if (!GEN || (P.m[0].eos == EOS_SG && P.m[1].eos == EOS_SG)) {
     const float a = phi1 * (P.m[0].gi * p + P.m[0].kap + P.m[0].gG * J2) +
                     phi2 * (P.m[1].gi * p + P.m[1].kap + P.m[1].gG * J2);
     const float Gm = (phi1 * P.m[0].GoG + phi2 * P.m[1].GoG) * ixi;
     return (a * ixi + (4.f / 3.f) * Gm) / rho;
   }
   const float a = phi1 * rc2_of(P.m[0], r1, p, J2) + phi2 * rc2_of(P.m[1], r2, p, J2);
-  return (a * ixi + (4.f / 3.f) * Gmix_f(P, phi1, r1, r2)) / rho;
+  return (a * ixi + (4.f / 3.f) * Gmix_f<GEN>(P, phi1, r1, r2)) / rho;
 }
 
 __device__ __forceinline__ float minmod_f(float a, float b) {
@@ -102,8 +108,11 @@ __device__ __forceinline__ float minmod_f(float a, float b) {
 // Limited slope: LIM 0 minmod, 1 van Leer (2 a b / (a + b) for a b > 0);
 // a compile-time choice, so the default minmod kernels carry no branch.
 template <int LIM>
-__device__ __forceinline__ float limited_f(float a, float b) {
+__device__ __forceinline__ float limited_f(float a, float b, int lim_rt = 0) {
   if constexpr (LIM == 0) return minmod_f(a, b);
+  if constexpr (LIM < 0) {  // chosen at run time (the general-closure kernels)
+    if (!lim_rt) return minmod_f(a, b);
+  }
   const float ab = a * b;
   return ab > 0.f ? 2.f * ab / (a + b) : 0.f;
 }
@@ -114,9 +123,10 @@ struct CandF {
 
 // beta_of() gives the THINC steepness; it is evaluated only in a mixed cell.
 template <int LIM = 0, class BetaFn>
-__device__ __forceinline__ CandF phi_cand_f(float qm, float qc, float qp, const BetaFn& beta_of, bool thinc) {
+__device__ __forceinline__ CandF phi_cand_f(float qm, float qc, float qp, const BetaFn& beta_of, bool thinc,
+                                            int lim_rt = 0) {
   CandF c;
-  const float s = limited_f<LIM>(qc - qm, qp - qc);
+  const float s = limited_f<LIM>(qc - qm, qp - qc, lim_rt);
   c.mL = qc - 0.5f * s;
   c.mR = qc + 0.5f * s;
   c.tL = c.mL;
@@ -151,7 +161,7 @@ struct FStateF {
   float V11, V12, V21, V22, V33;
 };
 
-template <int DIR>
+template <int DIR, bool GEN = true>
 __device__ __forceinline__ FStateF face_state_f(const PhysF& P, const PrimF& w) {
   FStateF s;
   const StrainF st = strain_f(w.V11, w.V12, w.V21, w.V22, w.V33);
@@ -162,9 +172,9 @@ __device__ __forceinline__ FStateF face_state_f(const PhysF& P, const PrimF& w) 
   s.arl = 0.f;
   if (P.y >= 0) s.arl = (P.y == 0 ? s.ar1 : s.ar2) * w.lam;
   const float ixi = 1.f / xi_f(P, w.phi);
-  s.rhoE = w.p / ixi + soft_ref_f(P, w.phi, s.ar1, s.ar2, s.arl, st.J2, w.r1, w.r2) +
+  s.rhoE = w.p / ixi + soft_ref_f<GEN>(P, w.phi, s.ar1, s.ar2, s.arl, st.J2, w.r1, w.r2) +
            0.5f * s.rho * (w.u * w.u + w.v * w.v);
-  const float Gm = Gmix_f(P, w.phi, w.r1, w.r2);
+  const float Gm = Gmix_f<GEN>(P, w.phi, w.r1, w.r2);
   s.Gm = Gm;
   if (DIR == 0) {
     s.un = w.u;
@@ -176,7 +186,7 @@ __device__ __forceinline__ FStateF face_state_f(const PhysF& P, const PrimF& w) 
     s.snn = -w.p + 2.f * Gm * st.H22;
   }
   s.snt = 2.f * Gm * st.H12;
-  s.cL = cL2_f(P, w.phi, s.rho, w.p, st.J2, w.r1, w.r2);  // squared; k_flux32 takes the root
+  s.cL = cL2_f<GEN>(P, w.phi, s.rho, w.p, st.J2, w.r1, w.r2);  // squared; k_flux32 takes the root
   s.V11 = w.V11;
   s.V12 = w.V12;
   s.V21 = w.V21;
@@ -283,6 +293,7 @@ __device__ __forceinline__ FaceOutF hlld_f(const FStateF& L, const FStateF& R) {
 
 // Plastic update of Section 3.2 in float; r1, r2 the phasic densities (the
 // Romenskii yield strain sigma_y / (sqrt 6 G(r))).
+template <bool GEN = true>
 __device__ __forceinline__ void plastic_f(const PhysF& P, float phi1, float dt, float& V11, float& V12,
                                           float& V21, float& V22, float& V33, float r1, float r2) {
   const StrainF s = strain_f(V11, V12, V21, V22, V33);
@@ -292,7 +303,7 @@ __device__ __forceinline__ void plastic_f(const PhysF& P, float phi1, float dt, 
   for (int l = 0; l < 2; ++l) {
     const MatT<float>& m = P.m[l];
     const float ph = l == 0 ? phi1 : 1.f - phi1;
-    const float JY = m.eos == EOS_ROMENSKII ? m.sigy / (2.4494897f * shear_of(m, l == 0 ? r1 : r2)) : m.JY;
+    const float JY = GEN && m.eos == EOS_ROMENSKII ? m.sigy / (2.4494897f * shear_of(m, l == 0 ? r1 : r2)) : m.JY;
     float Jl;
     if (m.G == 0.f) Jl = 0.f;
     else if (m.plastic == 1) Jl = fminf(Js, JY);

@@ -83,7 +83,7 @@ struct StepArgs32 {
 // Primitives of one cell from its FP32-bulk state v (NF + 1 values, slot E =
 // e_s, slot PHI and plane NF = phi1 high and low parts).  Also returns
 // 1 - phi1 from the float-float pair (the partial density of a trace phase).
-template <int DIM, bool RX>
+template <int DIM, bool RX, bool GEN = true>
 __device__ __forceinline__ PrimF prim32_of(const Phys& P, const PhysF& F, const float* v) {
   using L = Lay<DIM, RX>;
   constexpr int NF = L::NF;
@@ -118,7 +118,7 @@ __device__ __forceinline__ PrimF prim32_of(const Phys& P, const PhysF& F, const 
   }
   const StrainF s = strain_f(w.V11, w.V12, w.V21, w.V22, w.V33);
   const float KE = 0.5f * (mx * w.u + my * w.v);
-  w.p = (v[L::E] - (KE + soft_ref_f(F, phi, a1, a2, arl, s.J2, w.r1, w.r2))) / xi_f(F, phi);
+  w.p = (v[L::E] - (KE + soft_ref_f<GEN>(F, phi, a1, a2, arl, s.J2, w.r1, w.r2))) / xi_f(F, phi);
   return w;
 }
 
@@ -129,22 +129,22 @@ __device__ __forceinline__ void load32(const float* q, long long T, long long k,
   for (int c = 0; c < NS; ++c) v[c] = q[c * T + k];
 }
 
-template <int DIM, bool RX>
+template <int DIM, bool RX, bool GEN = true>
 __device__ __forceinline__ PrimF cons_to_prim32(const Phys& P, const PhysF& F, const float* q, long long T,
                                                 long long k) {
   float v[Lay<DIM, RX>::NF + 1];
   load32<DIM, RX>(q, T, k, v);
-  return prim32_of<DIM, RX>(P, F, v);
+  return prim32_of<DIM, RX, GEN>(P, F, v);
 }
 
 // CFL rate sum_d (|u_d| + c_L) / dx_d of one cell from its primitives; flags
 // a cell without a real sound speed or a positive density.
-template <int DIM>
+template <int DIM, bool GEN = true>
 __device__ __forceinline__ float cfl_rate_of(const PhysF& F, const PrimF& w, float idx, float idy, int* status,
                                              int patch, int cell) {
   const StrainF s = strain_f(w.V11, w.V12, w.V21, w.V22, w.V33);
   const float rho = w.phi * w.r1 + (1.f - w.phi) * w.r2;
-  const float cL2 = cL2_f(F, w.phi, rho, w.p, s.J2, w.r1, w.r2);
+  const float cL2 = cL2_f<GEN>(F, w.phi, rho, w.p, s.J2, w.r1, w.r2);
   if (!(cL2 > 0.f) || !(rho > 0.f)) flag_bad(status, patch, cell);
   const float cL = sqrtf(fmaxf(cL2, 0.f));
   float r = (fabsf(w.u) + cL) * idx;
