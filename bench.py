@@ -307,6 +307,9 @@ def run_gpu(args):
     }
     line["fp64"]["hancock"] = hancock_bench(wl, prim, args.steps, args.warmup)
     line["fp64"]["hancock"]["speedup_vs_rk3"] = line["fp64"]["hancock"]["value"] / value64
+    h32 = hancock_bench(wl, prim, args.steps, args.warmup, precision="fp32_bulk")
+    h32["speedup_vs_rk3"] = h32["value"] / value
+    line["fp32_bulk_hancock"] = h32
     if not args.no_configs:
         line["configs"] = configs_bench(args.warmup)
     if not args.no_batch:
@@ -440,12 +443,14 @@ def widened_bench(warmup=3):
     return out
 
 
-def hancock_bench(wl, prim, steps, warmup):
-    """The float64 step with the single-stage MUSCL-Hancock update on the same
-    workload: cell-updates/s (device events, inputs resident)."""
+def hancock_bench(wl, prim, steps, warmup, precision="fp64"):
+    """The step with the single-stage MUSCL-Hancock update on the same
+    workload: cell-updates/s (device events, inputs resident).  FP32-bulk: one
+    fused kernel per step, so the step time is the kernel's (plus the rate
+    buffer's clear and copy), and the HBM fraction is that of the kernel."""
     import torch
     from paper_2009_14555_gb300.solver import Solver
-    s = Solver.from_workload(wl, precision="fp64", scheme="hancock")
+    s = Solver.from_workload(wl, precision=precision, scheme="hancock")
     s.set_state(prim, kind=1)
     s.step(warmup)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -457,16 +462,24 @@ def hancock_bench(wl, prim, steps, warmup):
     ms = e0.elapsed_time(e1) / steps
     rc = s.check()[0]
     launches = s.launches
+    out = {"value": wl.cells / (ms * 1e-3), "ms_per_step": ms, "steps": steps,
+           "launches_per_step": launches // steps, "status_ok": rc == 0}
+    if precision == "fp32_bulk":
+        b = 2 * state_bytes(wl.dim, wl.reactive, precision)
+        t = s.tile_choice()
+        out.update(tile=list(t[:2]), tuned_ms_per_step=[round(float(x), 4) for x in t[3][:3]],
+                   algorithmic_bytes_per_cell_update=b,
+                   hbm_frac=b * wl.cells / (ms * 1e-3) / 1e9 / peaks()[0])
     s.close()
-    return {"value": wl.cells / (ms * 1e-3), "ms_per_step": ms, "steps": steps,
-            "launches_per_step": launches // steps, "status_ok": rc == 0}
+    return out
 
 
 def batch_bench(steps=300, warmup=3):
     """4096 independent 1D two-material problems (256-4096 cells, seed 3) in one
     batch, 300 steps in one dis_step call: cell-updates/s for both precisions
     (each problem has its own dt; FP32-bulk: the tuner's schedule, per-step
-    launches or the persistent batch kernel)."""
+    launches or the persistent batch kernel), and the FP32-bulk single-stage
+    MUSCL-Hancock form (one kernel per step)."""
     import torch
     from paper_2009_14555_gb300 import workloads as W
     from paper_2009_14555_gb300.solver import Solver, pack
@@ -474,8 +487,9 @@ def batch_bench(steps=300, warmup=3):
     prim = pack([p.prim for p in wl.patches])
     out = {"workload": "1d_batch_4096 (256-4096 cells log-uniform, seed 3)", "cells": wl.cells,
            "problems": len(wl.patches)}
-    for prec in ("fp32_bulk", "fp64"):
-        s = Solver.from_workload(wl, precision=prec)
+    for prec in ("fp32_bulk", "fp64", "fp32_bulk_hancock"):
+        scheme = "hancock" if prec.endswith("hancock") else "rk3"
+        s = Solver.from_workload(wl, precision=prec.replace("_hancock", ""), scheme=scheme)
         s.set_state(prim, kind=1)
         s.step(warmup)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -489,13 +503,13 @@ def batch_bench(steps=300, warmup=3):
         # problems whose state left the finite range (each problem is independent)
         bad_ids = [k for k, a in enumerate(s.get_arrays()) if not np.isfinite(a).all()]
         bad = len(bad_ids)
-        b = 2 * state_bytes(1, False, prec)
+        b = 2 * state_bytes(1, False, prec.replace("_hancock", ""))
         out[prec] = {"value": wl.cells / (ms * 1e-3), "ms_per_step": ms, "steps": steps,
                      "launches": s.launches, "nonfinite_problems": bad, "nonfinite_ids": bad_ids[:16],
                      "first_flagged": [int(bp), int(bc)] if rc else None,
                      "algorithmic_bytes_per_cell_update": b,
                      "hbm_frac": b * wl.cells / (ms * 1e-3) / 1e9 / peaks()[0]}
-        if prec == "fp32_bulk":
+        if prec.startswith("fp32_bulk"):
             t = s.tile_choice()
             sc, bms = s.schedule()
             out[prec]["tile"] = list(t[:3])

@@ -124,7 +124,10 @@ typedef struct {
  * DIS_HANCOCK the single-stage MUSCL-Hancock predictor-corrector (one Riemann
  * solve per face and step, second order; no counterpart in the paper): the
  * per-cell edge states of the same reconstruction move by half a step of the
- * cell's own operator before the face Riemann problems.  Float64 only. */
+ * cell's own operator before the face Riemann problems.  Planar geometry.
+ * In FP32-bulk contexts one fused kernel per step reads the state and writes
+ * a second buffer; the two exchange roles from step to step (the workspace
+ * holds two state buffers, the Runge-Kutta form three). */
 enum { DIS_RK3 = 0, DIS_HANCOCK = 1 };
 
 /* Geometry: DIS_PLANAR is the Cartesian plane-strain system; DIS_CYLINDRICAL
@@ -261,7 +264,10 @@ long long dis_last_launches(const dis_ctx* ctx);
  * DIS_VANLEER context of stiffened gases has one variant (5 in 2D, 1 in 1D),
  * a context with a Romenskii or JWL material one (2 in 2D, 1 in 1D; limiter
  * read at run time); changing the materials between the families returns a
- * fixed variant that no longer applies to tuning.  The first
+ * fixed variant that no longer applies to tuning.  A DIS_HANCOCK context has
+ * variants 0 .. 2 (the tile shapes; one kernel per step, about 104 KB of
+ * shared memory per 2D CTA), van Leer and general closures the 32 x 7 tile
+ * (2) in 2D and the 250-cell tile (1) in 1D.  The first
  * dis_step times one step of every variant (the last stage writing a scratch
  * buffer, so the state is unchanged) and keeps the fastest.  Returns the
  * chosen shape (0 x 0 before tuning or for float64 contexts), precomputed = 0

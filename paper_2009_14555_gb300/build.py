@@ -19,11 +19,12 @@ LIB = os.path.join(HERE, "libdis.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]
-# dis_api.cu instantiates the FP32-bulk kernels: their float32 divisions and
-# square roots use the approximate (2 ulp) forms and float32 denormals flush
-# to zero.  Float64 arithmetic (the whole float64 path, the float64 parts of
-# FP32-bulk) is unaffected by these options.
-FILE_FLAGS = {"dis_api.cu": ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]}
+# dis_api.cu and hancock32_{1d,2d}.cu instantiate the FP32-bulk kernels: their
+# float32 divisions and square roots use the approximate (2 ulp) forms and
+# float32 denormals flush to zero.  Float64 arithmetic (the whole float64
+# path, the float64 parts of FP32-bulk) is unaffected by these options.
+_FP32_FLAGS = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
+FILE_FLAGS = {"dis_api.cu": _FP32_FLAGS, "hancock32_1d.cu": _FP32_FLAGS, "hancock32_2d.cu": _FP32_FLAGS}
 
 
 def nvcc() -> str:

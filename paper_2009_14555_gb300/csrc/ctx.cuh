@@ -82,8 +82,12 @@ struct dis_ctx {
   long long launches = 0;
   // one captured time step per dt mode (0: CFL, 1: prescribed), replayed per step
   cudaStream_t cap = nullptr;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  long long graph_launches[2] = {0, 0};
+  // captured steps: index mode (0 CFL dt, 1 fixed dt) + 2 parity (the
+  // FP32-bulk MUSCL-Hancock step alternates its two state buffers; parity 1:
+  // the state is in the buffer carved second)
+  cudaGraphExec_t graph[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long graph_launches[4] = {0, 0, 0, 0};
+  float* q32_home = nullptr;  // the buffer carved first
   bool use_graphs = true;
   dis_adj* adj = nullptr;  // created by the first dis_adj_forward
   // pipelined host transfers (dis_set_state_async / dis_get_state_async): two
@@ -105,3 +109,13 @@ int dis_internal_ensure_ws(dis_ctx* c);
 int dis_internal_steps(dis_ctx* c, int n, bool fixed);
 // Release the adjoint buffers of a context.
 void dis_internal_adj_free(dis_ctx* c);
+// A Romenskii or JWL material in the context (the kernels with the general
+// closures run).
+bool general_closures(const dis_ctx* c);
+// FP32-bulk MUSCL-Hancock (hancock32_1d.cu, hancock32_2d.cu): one step of
+// variant v (the tile shape) from a.src to a.dst; the persistent 1D batch
+// form, n steps alternating between q0 (the state) and q1.
+void hancock32_step_1d(dis_ctx* c, cudaStream_t st, const dis::StepArgs32& a, int v);
+void hancock32_step_2d(dis_ctx* c, cudaStream_t st, const dis::StepArgs32& a, int v);
+void hancock32_batch_1d(dis_ctx* c, cudaStream_t st, const dis::StepArgs32& a, float* q0, float* q1, int n,
+                        int scratch, int v);

@@ -65,6 +65,10 @@ int dis_internal_error(int code, const char* fmt, ...) {
 }
 
 
+// A Romenskii or JWL material in the context: the kernels carry the general
+// closures (stiffened-gas contexts run kernels without that code).
+bool general_closures(const dis_ctx* c) { return c->phys.m[0].eos != EOS_SG || c->phys.m[1].eos != EOS_SG; }
+
 namespace {
 
 int n_extra(int dim) { return dim == 2 ? 3 : 2; }
@@ -170,7 +174,9 @@ size_t carve(dis_ctx* c, char* base) {
     ofy = k.take(sizeof(double) * nfx * c->NFY);
     if (c->hancock) oe = k.take((size_t)2 * c->dim * c->nf * dpl);
   } else {
-    for (int b = 0; b < 3; ++b) o32[b] = k.take((c->nf + 1) * sizeof(float) * T);
+    // Runge-Kutta: q^n and two stage buffers; MUSCL-Hancock: a pair that
+    // alternates from step to step
+    for (int b = 0; b < (c->hancock ? 2 : 3); ++b) o32[b] = k.take((c->nf + 1) * sizeof(float) * T);
   }
   size_t oio = k.take(sizeof(double) * (size_t)c->nf * c->ncells);
   size_t ort = k.take(2 * sizeof(unsigned long long) * c->np);  // rate of q^n, of q^{n+1}
@@ -202,7 +208,8 @@ size_t carve(dis_ctx* c, char* base) {
       c->Fy = (double*)(base + ofy);
       c->E = c->hancock ? (double*)(base + oe) : nullptr;
     } else {
-      for (int b = 0; b < 3; ++b) c->q32[b] = (float*)(base + o32[b]);
+      for (int b = 0; b < 3; ++b) c->q32[b] = (c->hancock && b == 2) ? nullptr : (float*)(base + o32[b]);
+      c->q32_home = c->q32[0];
     }
     c->io = (double*)(base + oio);
     c->rate = (unsigned long long*)(base + ort);
@@ -311,10 +318,6 @@ void stage_fused(dis_ctx* c, cudaStream_t st, StepArgs32& a, int shape) {
   else stage_fused_c<DIM, RX, TX, TY, NT, MINB, false, LIM, GEN>(c, st, a, shape);
 }
 
-// A Romenskii or JWL material in the context: the kernels carry the general
-// closures (stiffened-gas contexts run kernels without that code).
-bool general_closures(const dis_ctx* c) { return c->phys.m[0].eos != EOS_SG || c->phys.m[1].eos != EOS_SG; }
-
 // FP32-bulk stage variants v = shape + 3 budget: the 3 tile shapes x two
 // register budgets (2D: 768 or 1024 resident threads per SM requested from
 // the register allocator; 1D: no limit, or 64 registers per thread).  The
@@ -324,11 +327,51 @@ bool general_closures(const dis_ctx* c) { return c->phys.m[0].eos != EOS_SG || c
 // tile at 1024 threads per SM for van Leer, at 768 for the general closures,
 // whose code would spill at 64 registers; the general-closure kernel takes
 // the limiter at run time).
-int single_variant(const dis_ctx* c) { return c->dim == 2 ? (general_closures(c) ? 2 : 5) : 1; }
+//
+// MUSCL-Hancock contexts: variant = tile shape (0 .. 2); van Leer and general
+// closures the 32 x 7 tile (2D) or the 250-cell tile (1D).
+int single_variant(const dis_ctx* c) {
+  if (c->hancock) return c->dim == 2 ? 2 : 1;
+  return c->dim == 2 ? (general_closures(c) ? 2 : 5) : 1;
+}
 bool variant_valid(const dis_ctx* c, int v) {
   if (c->phys.limiter || general_closures(c)) return v == single_variant(c);
-  return v >= 0 && v < DIS_NVARIANTS;
+  return v >= 0 && v < (c->hancock ? 3 : DIS_NVARIANTS);
 }
+
+// One FP32-bulk MUSCL-Hancock step of variant v: q32[0] -> q32[1] (the
+// caller exchanges the two after enqueueing it; the tuner times it as is).
+void hancock32_step(dis_ctx* c, cudaStream_t st, StepArgs32& a, int v) {
+  a.src = c->q32[0];
+  a.qn = c->q32[0];
+  a.dst = c->q32[1];
+  a.a = 0.0;
+  a.b = 1.0;
+  a.last = 1;
+  if (c->dim == 2) hancock32_step_2d(c, st, a, v);
+  else hancock32_step_1d(c, st, a, v);
+}
+
+// The state-buffer parity of an FP32-bulk MUSCL-Hancock context (1: the
+// state is in the buffer carved second) and the exchange after each step.
+bool any_graph(const dis_ctx* c) {
+  for (cudaGraphExec_t g : c->graph)
+    if (g) return true;
+  return false;
+}
+
+// Destroy the captured step graphs (after the replays in flight).
+void drop_graphs(dis_ctx* c) {
+  if (any_graph(c)) cudaStreamSynchronize(c->stream);
+  for (cudaGraphExec_t& g : c->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+int h_parity(const dis_ctx* c) { return c->fp32 && c->hancock && c->q32[0] != c->q32_home ? 1 : 0; }
+void h_swap(dis_ctx* c) { std::swap(c->q32[0], c->q32[1]); }
 
 // MINB: resident CTAs of 256 threads per SM requested (3 or 4); the
 // 512-thread tile asks for half as many.
@@ -467,9 +510,13 @@ int autotune32(dis_ctx* c) {
     if (!variant_valid(c, v)) continue;
     for (int rep = 0; rep < 3; ++rep) {  // rep 0 warms up
       CU(cudaEventRecord(e0, c->stream));
-      for (int stg = 0; stg < 3; ++stg) {
-        set_stage_args32<DIM, RX>(c, a, stg, true);
-        stage_kernel_v<DIM, RX>(c, c->stream, a, v);
+      if (c->hancock) {
+        hancock32_step(c, c->stream, a, v);
+      } else {
+        for (int stg = 0; stg < 3; ++stg) {
+          set_stage_args32<DIM, RX>(c, a, stg, true);
+          stage_kernel_v<DIM, RX>(c, c->stream, a, v);
+        }
       }
       CU(cudaEventRecord(e1, c->stream));
       CU(cudaEventSynchronize(e1));
@@ -493,7 +540,8 @@ int autotune32(dis_ctx* c) {
         if (!variant_valid(c, v)) continue;
         for (int rep = 0; rep < 3; ++rep) {
           CU(cudaEventRecord(e0, c->stream));
-          batch_kernel_v<RX>(c, c->stream, ab, 1, 1, v);
+          if (c->hancock) hancock32_batch_1d(c, c->stream, ab, c->q32[0], c->q32[1], 1, 1, v);
+          else batch_kernel_v<RX>(c, c->stream, ab, 1, 1, v);
           CU(cudaEventRecord(e1, c->stream));
           CU(cudaEventSynchronize(e1));
           float ms = 0.f;
@@ -525,16 +573,21 @@ long long launch_step(dis_ctx* c, cudaStream_t st, bool fixed) {
   if (c->fp32) {
     // the three stages read the rate of q^n (rate) and the last one
     // accumulates the rate of q^{n+1} (rate + np), copied over at the end
+    // (MUSCL-Hancock: one kernel, q32[0] -> q32[1]; the caller exchanges them)
     StepArgs32 a = base_args32(c);
     a.dtfix = fixed ? c->dtfix : nullptr;
     const int v = c->variant < 0 ? 0 : c->variant;
     cudaMemsetAsync(c->rate + c->np, 0, sizeof(unsigned long long) * c->np, st);
-    for (int stg = 0; stg < 3; ++stg) {
-      set_stage_args32<DIM, RX>(c, a, stg);
-      stage_kernel_v<DIM, RX>(c, st, a, v);
+    if (c->hancock) {
+      hancock32_step(c, st, a, v);
+    } else {
+      for (int stg = 0; stg < 3; ++stg) {
+        set_stage_args32<DIM, RX>(c, a, stg);
+        stage_kernel_v<DIM, RX>(c, st, a, v);
+      }
     }
     cudaMemcpyAsync(c->rate, c->rate + c->np, sizeof(unsigned long long) * c->np, cudaMemcpyDeviceToDevice, st);
-    return 3;
+    return c->hancock ? 1 : 3;
   }
   StepArgs a = base_args(c);
   a.dtfix = fixed ? c->dtfix : nullptr;
@@ -676,7 +729,12 @@ int run_steps(dis_ctx* c, int n_steps, bool fixed) {
     if (c->fp32 && sched == 1) {  // all n steps in one persistent launch
       StepArgs32 a = base_args32(c);
       a.dtfix = fixed ? c->dtfix : nullptr;
-      batch_kernel_v<RX>(c, c->stream, a, n_steps, 0, c->variant);
+      if (c->hancock) {
+        hancock32_batch_1d(c, c->stream, a, c->q32[0], c->q32[1], n_steps, 0, c->variant);
+        if (n_steps & 1) h_swap(c);
+      } else {
+        batch_kernel_v<RX>(c, c->stream, a, n_steps, 0, c->variant);
+      }
       CU(cudaGetLastError());
       c->rate_valid = true;
       c->launches = 1;
@@ -689,9 +747,13 @@ int run_steps(dis_ctx* c, int n_steps, bool fixed) {
     c->rate_valid = true;
     first = 1;
   }
+  const bool alternate = c->fp32 && c->hancock;  // the state moves to the other buffer each step
   if (!c->use_graphs) {
     long long l = first;
-    for (int s = 0; s < n_steps; ++s) l += launch_step<DIM, RX>(c, c->stream, fixed);
+    for (int s = 0; s < n_steps; ++s) {
+      l += launch_step<DIM, RX>(c, c->stream, fixed);
+      if (alternate) h_swap(c);
+    }
     CU(cudaGetLastError());
     c->launches = l;
     return DIS_OK;
@@ -699,21 +761,27 @@ int run_steps(dis_ctx* c, int n_steps, bool fixed) {
   if (!c->cap) {
     CU(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   }
-  if (!c->graph[mode]) {
-    cudaGraph_t g = nullptr;
-    CU(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-    const long long l = launch_step<DIM, RX>(c, c->cap, fixed);
-    const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
-    if (e != cudaSuccess) return fail(DIS_ECUDA, "step capture failed: %s", cudaGetErrorString(e));
-    const cudaError_t e2 = cudaGraphInstantiate(&c->graph[mode], g, 0);
-    cudaGraphDestroy(g);
-    if (e2 != cudaSuccess) return fail(DIS_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e2));
-    c->graph_launches[mode] = l;
+  // captured on the private stream (one graph per mode and buffer parity),
+  // replayed on the caller's stream (no cross-stream waits between steps)
+  long long l = first;
+  for (int s = 0; s < n_steps; ++s) {
+    const int gi = mode + 2 * h_parity(c);
+    if (!c->graph[gi]) {
+      cudaGraph_t g = nullptr;
+      CU(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+      const long long lc = launch_step<DIM, RX>(c, c->cap, fixed);
+      const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+      if (e != cudaSuccess) return fail(DIS_ECUDA, "step capture failed: %s", cudaGetErrorString(e));
+      const cudaError_t e2 = cudaGraphInstantiate(&c->graph[gi], g, 0);
+      cudaGraphDestroy(g);
+      if (e2 != cudaSuccess) return fail(DIS_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e2));
+      c->graph_launches[gi] = lc;
+    }
+    CU(cudaGraphLaunch(c->graph[gi], c->stream));
+    l += c->graph_launches[gi];
+    if (alternate) h_swap(c);
   }
-  // captured on the private stream, replayed on the caller's stream (no
-  // cross-stream waits between steps)
-  for (int s = 0; s < n_steps; ++s) CU(cudaGraphLaunch(c->graph[mode], c->stream));
-  c->launches = first + c->graph_launches[mode] * n_steps;
+  c->launches = l;
   return DIS_OK;
 }
 
@@ -847,8 +915,6 @@ int dis_create(int dim, int n_patches, const dis_patch* patches, int reactive_ma
     return fail(DIS_EINVAL, "dis_create: unknown precision %d", opt->precision);
   if (opt->scheme != DIS_RK3 && opt->scheme != DIS_HANCOCK)
     return fail(DIS_EINVAL, "dis_create: unknown scheme %d", opt->scheme);
-  if (opt->scheme == DIS_HANCOCK && opt->precision != DIS_FP64)
-    return fail(DIS_EINVAL, "dis_create: the MUSCL-Hancock scheme is built for float64 only");
   if (opt->geometry != DIS_PLANAR && opt->geometry != DIS_CYLINDRICAL)
     return fail(DIS_EINVAL, "dis_create: unknown geometry %d", opt->geometry);
   if (opt->limiter != DIS_MINMOD && opt->limiter != DIS_VANLEER)
@@ -943,12 +1009,7 @@ int dis_set_materials(dis_ctx* c, const dis_material* m, int n) {
   c->rate_valid = false;  // the rate depends on the closures
   c->have_mats = true;
   // captured steps hold the closure parameters by value: capture again
-  if (c->graph[0] || c->graph[1]) cudaStreamSynchronize(c->stream);  // replays may be in flight
-  for (int g = 0; g < 2; ++g)
-    if (c->graph[g]) {
-      cudaGraphExecDestroy(c->graph[g]);
-      c->graph[g] = nullptr;
-    }
+  drop_graphs(c);
   return DIS_OK;
 }
 
@@ -967,13 +1028,9 @@ int dis_bind_workspace(dis_ctx* c, void* dev, size_t bytes) {
   if (((uintptr_t)dev) & 255) return fail(DIS_EINVAL, "dis_bind_workspace: pointer not 256-byte aligned");
   const size_t need = carve(c, nullptr);
   if (bytes < need) return fail(DIS_ENOMEM, "dis_bind_workspace: %zu bytes given, %zu needed", bytes, need);
-  if (c->graph[0] || c->graph[1] || c->ws_owned) cudaStreamSynchronize(c->stream);  // work may be in flight
+  if (c->ws_owned) cudaStreamSynchronize(c->stream);  // work may be in flight
+  drop_graphs(c);
   if (c->ws_owned) cudaFree(c->ws);
-  for (int m = 0; m < 2; ++m)
-    if (c->graph[m]) {
-      cudaGraphExecDestroy(c->graph[m]);
-      c->graph[m] = nullptr;
-    }
   c->ws = (char*)dev;
   c->ws_bytes = bytes;
   c->ws_owned = false;
@@ -1267,13 +1324,8 @@ int dis_set_variant(dis_ctx* c, int variant) {
   if (!c) return fail(DIS_EINVAL, "dis_set_variant: NULL context");
   if (!c->fp32) return fail(DIS_EINVAL, "dis_set_variant: only FP32-bulk contexts have variants");
   if (variant != -1 && !variant_valid(c, variant))
-    return fail(DIS_EINVAL, "dis_set_variant: variant %d is not one of 0..%d", variant, DIS_NVARIANTS - 1);
-  if (c->graph[0] || c->graph[1]) cudaStreamSynchronize(c->stream);  // replays may be in flight
-  for (int g = 0; g < 2; ++g)
-    if (c->graph[g]) {
-      cudaGraphExecDestroy(c->graph[g]);
-      c->graph[g] = nullptr;
-    }
+    return fail(DIS_EINVAL, "dis_set_variant: variant %d is not a variant of this context", variant);
+  drop_graphs(c);
   c->variant = variant;
   return DIS_OK;
 }
@@ -1312,8 +1364,7 @@ int dis_step_timed(dis_ctx* c, int n_steps, double* kernel_ms) {
 void dis_destroy(dis_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);  // replays of the step graphs run on the caller's stream
-  for (int m = 0; m < 2; ++m)
-    if (c->graph[m]) cudaGraphExecDestroy(c->graph[m]);
+  drop_graphs(c);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->s_in) cudaStreamSynchronize(c->s_in);
   if (c->s_out) cudaStreamSynchronize(c->s_out);

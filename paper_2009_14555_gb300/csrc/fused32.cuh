@@ -35,85 +35,33 @@ struct FSlots {
   static constexpr int PK = VB + 1, DD = VB + 2, N = VB + 3;
 };
 
-template <int DIM, bool RX, int DIR, int LIM, bool GEN>
-__device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__ Wsm, int HX, int HY, int hx,
-                                       int hy, float dxn, float dxt, float* __restrict__ Fsm, int nfaces,
-                                       int fidx) {
-  // hx, hy: SMEM coordinates of the face's left (DIR 0) or lower (DIR 1) cell
+// THINC steepness of the cell at SMEM index k (phi plane Wphi; sx along the
+// sweep, sy across it): Youngs normal from the 3 x 3 neighbourhood in 2D
+// (Appendix A), the 1D value otherwise.
+template <int DIM>
+__device__ __forceinline__ float thinc_beta_f(const PhysF& P, const float* __restrict__ Wphi, int k, int sx,
+                                              int sy, float dxn, float dxt) {
+  float beta = 2.51f;
+  if (DIM == 2 && P.thinc) {
+    const float dn = (Wphi[k + sx + sy] + 2.f * Wphi[k + sx] + Wphi[k + sx - sy]) -
+                     (Wphi[k - sx + sy] + 2.f * Wphi[k - sx] + Wphi[k - sx - sy]);
+    const float dt_ = (Wphi[k + sy + sx] + 2.f * Wphi[k + sy] + Wphi[k + sy - sx]) -
+                      (Wphi[k - sy + sx] + 2.f * Wphi[k - sy] + Wphi[k - sy - sx]);
+    const float gn = dn / dxn, gt = dt_ / dxt;
+    const float nrm = sqrtf(gn * gn + gt * gt);
+    beta = 2.5f * (nrm == 0.f ? 1.f : fabsf(gn) / nrm) + 0.01f;
+  }
+  return beta;
+}
+
+// The face slots (FSlots) of a face output o on a face normal to DIR, through
+// put(slot, value).
+template <int DIM, bool RX, int DIR, class Put>
+__device__ __forceinline__ void face_slots_f(const FaceOutF& o, const Put& put) {
   using L = Lay<DIM, RX>;
   using S = FSlots<DIM, RX>;
-  const int plane = HX * HY;
-  const int sx = DIR == 0 ? 1 : HX;  // along the sweep
-  const int sy = DIR == 0 ? HX : 1;  // across it
-  const int k0 = hy * HX + hx;       // cell a
-  auto Wv = [&](int f, int k) { return Wsm[f * plane + k]; };
-  float ph[6];
-#pragma unroll
-  for (int s = 0; s < 6; ++s) ph[s] = Wv(L::PHI, k0 + (s - 2) * sx);
-  float phiL, phiR;
-  {
-    CandF c[4];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      auto beta_of = [&]() -> float {
-        float beta = 2.51f;
-        if (DIM == 2 && P.thinc) {
-          const int k = k0 + (s - 1) * sx;
-          const float dn = (Wv(L::PHI, k + sx + sy) + 2.f * Wv(L::PHI, k + sx) + Wv(L::PHI, k + sx - sy)) -
-                           (Wv(L::PHI, k - sx + sy) + 2.f * Wv(L::PHI, k - sx) + Wv(L::PHI, k - sx - sy));
-          const float dt_ = (Wv(L::PHI, k + sy + sx) + 2.f * Wv(L::PHI, k + sy) + Wv(L::PHI, k + sy - sx)) -
-                            (Wv(L::PHI, k - sy + sx) + 2.f * Wv(L::PHI, k - sy) + Wv(L::PHI, k - sy - sx));
-          const float gn = dn / dxn, gt = dt_ / dxt;
-          const float nrm = sqrtf(gn * gn + gt * gt);
-          beta = 2.5f * (nrm == 0.f ? 1.f : fabsf(gn) / nrm) + 0.01f;
-        }
-        return beta;
-      };
-      c[s] = phi_cand_f<LIM>(ph[s], ph[s + 1], ph[s + 2], beta_of, P.thinc != 0, P.limiter);
-    }
-    float Lt, Rt;
-    bvd_f(c[0], c[1], c[2], Lt, Rt);
-    phiL = Rt;
-    bvd_f(c[1], c[2], c[3], Lt, Rt);
-    phiR = Lt;
-  }
-  PrimF w0, w1, w2, w3;
-  auto ld = [&](PrimF& w, int k) {
-    w.phi = Wv(L::PHI, k); w.r1 = Wv(L::A1, k); w.r2 = Wv(L::A2, k); w.u = Wv(L::MX, k);
-    w.p = Wv(L::E, k); w.V11 = Wv(L::V11, k); w.V22 = Wv(L::V22, k); w.V33 = Wv(L::V33, k);
-    w.v = 0.f; w.V12 = 0.f; w.V21 = 0.f; w.lam = 0.f;
-    if constexpr (DIM == 2) { w.v = Wv(L::MY, k); w.V12 = Wv(L::V12, k); w.V21 = Wv(L::V21, k); }
-    if constexpr (RX) w.lam = Wv(L::AL, k);
-  };
-  ld(w0, k0 - sx);
-  ld(w1, k0);
-  ld(w2, k0 + sx);
-  ld(w3, k0 + 2 * sx);
-  PrimF wl, wr;
-#define DIS_RECF(fld)                                            \
-  {                                                              \
-    const float s1 = limited_f<LIM>(w1.fld - w0.fld, w2.fld - w1.fld, P.limiter); \
-    const float s2 = limited_f<LIM>(w2.fld - w1.fld, w3.fld - w2.fld, P.limiter); \
-    wl.fld = w1.fld + 0.5f * s1;                                 \
-    wr.fld = w2.fld - 0.5f * s2;                                 \
-  }
-  DIS_RECF(r1) DIS_RECF(r2) DIS_RECF(u) DIS_RECF(p) DIS_RECF(V11) DIS_RECF(V22) DIS_RECF(V33)
-  if constexpr (DIM == 2) { DIS_RECF(v) DIS_RECF(V12) DIS_RECF(V21) }
-  else { wl.v = wr.v = 0.f; wl.V12 = wr.V12 = wl.V21 = wr.V21 = 0.f; }
-  if constexpr (RX) { DIS_RECF(lam) } else { wl.lam = wr.lam = 0.f; }
-#undef DIS_RECF
-  wl.phi = phiL;
-  wr.phi = phiR;
-  FStateF sl = face_state_f<DIR, GEN>(P, wl);
-  if (!(sl.cL > 0.f)) sl = face_state_f<DIR, GEN>(P, w1);
-  FStateF sr = face_state_f<DIR, GEN>(P, wr);
-  if (!(sr.cL > 0.f)) sr = face_state_f<DIR, GEN>(P, w2);
-  sl.cL = sqrtf(sl.cL);
-  sr.cL = sqrtf(sr.cL);
-  const FaceOutF o = hlld_f<DIR>(sl, sr);
   const float fu = DIR == 0 ? o.un : o.ut;
   const float fv = DIR == 0 ? o.ut : o.un;
-  auto put = [&](int slot, float v) { Fsm[slot * nfaces + fidx] = v; };
   put(L::PHI, o.phi * o.un);
   put(L::A1, o.Far1);
   put(L::A2, o.Far2);
@@ -146,6 +94,79 @@ __device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__
     put(S::VA, o.V21);
     put(S::VB, o.V22);
   }
+}
+
+// Primitives of the SMEM cell k (planes of `plane` floats, slots as the
+// conservative layout: PHI phi1, A1 rho1, A2 rho2, MX u, MY v, E p, V, AL lam).
+template <int DIM, bool RX>
+__device__ __forceinline__ void load_prim_sm(const float* __restrict__ Wsm, int plane, int k, PrimF& w) {
+  using L = Lay<DIM, RX>;
+  auto Wv = [&](int f) { return Wsm[f * plane + k]; };
+  w.phi = Wv(L::PHI); w.r1 = Wv(L::A1); w.r2 = Wv(L::A2); w.u = Wv(L::MX);
+  w.p = Wv(L::E); w.V11 = Wv(L::V11); w.V22 = Wv(L::V22); w.V33 = Wv(L::V33);
+  w.v = 0.f; w.V12 = 0.f; w.V21 = 0.f; w.lam = 0.f;
+  if constexpr (DIM == 2) { w.v = Wv(L::MY); w.V12 = Wv(L::V12); w.V21 = Wv(L::V21); }
+  if constexpr (RX) w.lam = Wv(L::AL);
+}
+
+template <int DIM, bool RX, int DIR, int LIM, bool GEN>
+__device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__ Wsm, int HX, int HY, int hx,
+                                       int hy, float dxn, float dxt, float* __restrict__ Fsm, int nfaces,
+                                       int fidx) {
+  // hx, hy: SMEM coordinates of the face's left (DIR 0) or lower (DIR 1) cell
+  using L = Lay<DIM, RX>;
+  const int plane = HX * HY;
+  const int sx = DIR == 0 ? 1 : HX;  // along the sweep
+  const int sy = DIR == 0 ? HX : 1;  // across it
+  const int k0 = hy * HX + hx;       // cell a
+  auto Wv = [&](int f, int k) { return Wsm[f * plane + k]; };
+  float ph[6];
+#pragma unroll
+  for (int s = 0; s < 6; ++s) ph[s] = Wv(L::PHI, k0 + (s - 2) * sx);
+  float phiL, phiR;
+  {
+    CandF c[4];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      auto beta_of = [&]() -> float {
+        return thinc_beta_f<DIM>(P, Wsm + L::PHI * plane, k0 + (s - 1) * sx, sx, sy, dxn, dxt);
+      };
+      c[s] = phi_cand_f<LIM>(ph[s], ph[s + 1], ph[s + 2], beta_of, P.thinc != 0, P.limiter);
+    }
+    float Lt, Rt;
+    bvd_f(c[0], c[1], c[2], Lt, Rt);
+    phiL = Rt;
+    bvd_f(c[1], c[2], c[3], Lt, Rt);
+    phiR = Lt;
+  }
+  PrimF w0, w1, w2, w3;
+  load_prim_sm<DIM, RX>(Wsm, plane, k0 - sx, w0);
+  load_prim_sm<DIM, RX>(Wsm, plane, k0, w1);
+  load_prim_sm<DIM, RX>(Wsm, plane, k0 + sx, w2);
+  load_prim_sm<DIM, RX>(Wsm, plane, k0 + 2 * sx, w3);
+  PrimF wl, wr;
+#define DIS_RECF(fld)                                            \
+  {                                                              \
+    const float s1 = limited_f<LIM>(w1.fld - w0.fld, w2.fld - w1.fld, P.limiter); \
+    const float s2 = limited_f<LIM>(w2.fld - w1.fld, w3.fld - w2.fld, P.limiter); \
+    wl.fld = w1.fld + 0.5f * s1;                                 \
+    wr.fld = w2.fld - 0.5f * s2;                                 \
+  }
+  DIS_RECF(r1) DIS_RECF(r2) DIS_RECF(u) DIS_RECF(p) DIS_RECF(V11) DIS_RECF(V22) DIS_RECF(V33)
+  if constexpr (DIM == 2) { DIS_RECF(v) DIS_RECF(V12) DIS_RECF(V21) }
+  else { wl.v = wr.v = 0.f; wl.V12 = wr.V12 = wl.V21 = wr.V21 = 0.f; }
+  if constexpr (RX) { DIS_RECF(lam) } else { wl.lam = wr.lam = 0.f; }
+#undef DIS_RECF
+  wl.phi = phiL;
+  wr.phi = phiR;
+  FStateF sl = face_state_f<DIR, GEN>(P, wl);
+  if (!(sl.cL > 0.f)) sl = face_state_f<DIR, GEN>(P, w1);
+  FStateF sr = face_state_f<DIR, GEN>(P, wr);
+  if (!(sr.cL > 0.f)) sr = face_state_f<DIR, GEN>(P, w2);
+  sl.cL = sqrtf(sl.cL);
+  sr.cL = sqrtf(sr.cL);
+  const FaceOutF o = hlld_f<DIR>(sl, sr);
+  face_slots_f<DIM, RX, DIR>(o, [&](int slot, float v) { Fsm[slot * nfaces + fidx] = v; });
 }
 
 // Shared memory bytes of a tile.

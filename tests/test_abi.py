@@ -63,9 +63,9 @@ def test_create_validates_arguments(lib):
     assert b"x0" in lib.dis_last_error()
     assert lib.dis_create(1, 1, arr, -1, ctypes.byref(cyl), None, ctypes.byref(out)) == L.DIS_OK
     lib.dis_destroy(out)
-    hancock32 = L.DisOptions(0.8, 0, L.DIS_FP32_BULK, L.DIS_HANCOCK)
-    assert lib.dis_create(1, 1, arr, -1, ctypes.byref(hancock32), None, ctypes.byref(out)) == L.DIS_EINVAL
-    assert b"float64" in lib.dis_last_error()
+    cyl_h32 = L.DisOptions(0.8, 0, L.DIS_FP32_BULK, L.DIS_HANCOCK, L.DIS_CYLINDRICAL)
+    assert lib.dis_create(1, 1, arr, -1, ctypes.byref(cyl_h32), None, ctypes.byref(out)) == L.DIS_EINVAL
+    assert b"cylindrical" in lib.dis_last_error()
 
 
 def test_hancock_workspace_holds_the_evolved_edge_states(lib):
@@ -80,6 +80,21 @@ def test_hancock_workspace_holds_the_evolved_edge_states(lib):
         lib.dis_destroy(out)
     T = (100 + 6 + 31) // 32 * 32
     assert sizes[1] - sizes[0] >= 2 * 1 * 8 * 8 * T
+
+
+def test_fp32_hancock_workspace_holds_two_state_buffers(lib):
+    """FP32-bulk MUSCL-Hancock alternates two state buffers of nf + 1 float
+    planes (the Runge-Kutta form holds three)."""
+    out = ctypes.c_void_p()
+    arr = (L.DisPatch * 1)(_patch(1000))
+    sizes = []
+    for scheme in (L.DIS_RK3, L.DIS_HANCOCK):
+        opts = L.DisOptions(0.8, 0, L.DIS_FP32_BULK, scheme)
+        assert lib.dis_create(1, 1, arr, -1, ctypes.byref(opts), None, ctypes.byref(out)) == L.DIS_OK
+        sizes.append(lib.dis_workspace_bytes(out))
+        lib.dis_destroy(out)
+    T = (1000 + 6 + 31) // 32 * 32
+    assert sizes[0] - sizes[1] >= 4 * 9 * T
 
 
 def test_host_side_sizes_and_materials(lib):
