@@ -110,8 +110,12 @@ def test_generic_explosive_detonation_fp64():
 
 def test_generic_explosive_detonation_to_the_copper_fp64():
     """150 steps: the detonation runs into the copper (bar 1e-10 or 10x the
-    oracle's one-ulp spread)."""
-    assert_parity(_generic_detonation(200, 150), 150, calibrate=True)
+    oracle's one-ulp spread).  Where the detonation meets the copper (steps
+    55-70) a discrete choice of the scheme flips under round-off: one-ulp
+    perturbations of the input move the oracle's own energy field by
+    3e-10 ... 5e-8 (relative L1) depending on the perturbation drawn, so the
+    spread is the largest over six perturbations."""
+    assert_parity(_generic_detonation(200, 150), 150, calibrate=True, seeds=range(100, 106))
 
 
 def test_generic_explosive_refused_in_fp32_bulk_and_adjoint():

@@ -43,26 +43,31 @@ def gpu_run(wl, steps, dt_fixed=None, precision="fp64"):
     return out, prim, np.array(dts)
 
 
-def oracle_spread(wl, steps, o):
+def oracle_spread(wl, steps, o, seeds=(123,)):
     """Per-patch, per-field L1 between the oracle and the oracle on inputs
-    perturbed by one ulp (random sign per value)."""
+    perturbed by one ulp (random sign per value), the largest over the
+    perturbations drawn with `seeds`."""
     import copy
-    rng = np.random.default_rng(123)
-    wp = copy.deepcopy(wl)
-    for p in wp.patches:
-        p.prim = p.prim * (1 + np.sign(rng.standard_normal(p.prim.shape)) * 2.0 ** -52)
-    op, _ = oracle_run(wp, steps)
-    return [cons_l1(wl, op[k], o[k]) for k in range(len(o))]
+    worst = None
+    for seed in seeds:
+        rng = np.random.default_rng(seed)
+        wp = copy.deepcopy(wl)
+        for p in wp.patches:
+            p.prim = p.prim * (1 + np.sign(rng.standard_normal(p.prim.shape)) * 2.0 ** -52)
+        op, _ = oracle_run(wp, steps)
+        s = np.array([cons_l1(wl, op[k], o[k]) for k in range(len(o))])
+        worst = s if worst is None else np.maximum(worst, s)
+    return list(worst)
 
 
-def assert_parity(wl, steps, tol=TOL, calibrate=False, name=None):
+def assert_parity(wl, steps, tol=TOL, calibrate=False, name=None, seeds=(123,)):
     g, gp, gdt = gpu_run(wl, steps)
     o, odt = oracle_run(wl, steps)
     name = name or f"{wl.name}_{steps}"
     err = np.max([cons_l1(wl, g[k], o[k]) for k in range(len(o))], axis=0)
     emax = np.max([cons_max(wl, g[k], o[k]) for k in range(len(o))], axis=0)
     if calibrate:
-        spread = np.max(oracle_spread(wl, steps, o), axis=0)
+        spread = np.max(oracle_spread(wl, steps, o, seeds), axis=0)
         bar = np.maximum(tol, 10.0 * spread)
         record(name, steps=steps, l1=err, max_rel=emax, oracle_spread_l1=spread, bar=bar,
                within_1e10=bool((err <= TOL).all()))
