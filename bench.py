@@ -34,8 +34,13 @@ METRIC = "cell-updates/s and % HBM peak, FP32-bulk vs plain FP64 on one GB300 at
 STAGE32_FLOP = {(16, 15): 1454.0, (32, 15): 1418.6, (32, 7): 1499.1}
 FLUX_FP64_FLOP_PER_FACE = 868.1
 # DRAM bytes (read + write) per cell-stage of the stage kernel on the full
-# 2048 x 1024 grid (ncu, one launch), per tile shape; None where not captured.
-STAGE32_DRAM = {(16, 15): None, (32, 15): None, (32, 7): None}
+# 2048 x 1024 grid (ncu, one launch: stage 2, which reads two states and
+# writes one), per tile shape; None where not captured.
+STAGE32_DRAM = {(16, 15): None, (32, 15): 146.6, (32, 7): None}
+# The FP32-bulk MUSCL-Hancock kernel on the same grid (ncu, one launch of the
+# 32 x 7 tile): FP32 FLOP and DRAM bytes per cell-update.
+HANCOCK32_FLOP = {(32, 7): 2678.0}
+HANCOCK32_DRAM = {(32, 7): 85.1}
 # DRAM bytes per x-flux launch of the float64 step, per face (73.07 MB for
 # 524800 faces on 1024 x 512); traffic grows with the face count.
 FLUX_DRAM_BYTES_PER_FACE = 73.07e6 / 524800
@@ -467,9 +472,16 @@ def hancock_bench(wl, prim, steps, warmup, precision="fp64"):
     if precision == "fp32_bulk":
         b = 2 * state_bytes(wl.dim, wl.reactive, precision)
         t = s.tile_choice()
+        hbm = peaks()[0]
+        gbs = b * wl.cells / (ms * 1e-3) / 1e9
+        dram = HANCOCK32_DRAM.get(tuple(t[:2]))
         out.update(tile=list(t[:2]), tuned_ms_per_step=[round(float(x), 4) for x in t[3][:3]],
-                   algorithmic_bytes_per_cell_update=b,
-                   hbm_frac=b * wl.cells / (ms * 1e-3) / 1e9 / peaks()[0])
+                   algorithmic_bytes_per_cell_update=b, hbm_frac=gbs / hbm,
+                   roofline={"bound": "hbm", "kernel": f"k_hancock32<{t[0]}x{t[1]}> (one launch per step)",
+                             "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                             "traffic": dram * wl.cells if dram else None,
+                             "note": "algorithmic bytes of the step over the step time (one kernel per step "
+                                     "plus the rate buffer's clear and copy)"})
     s.close()
     return out
 
