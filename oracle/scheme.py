@@ -305,8 +305,14 @@ def spatial_operator(q, grid, mats, thinc, limiter="minmod"):
 
 
 def _planar_operator(q, grid, mats, thinc, limiter="minmod"):
+    return operator_padded(q, fill_ghosts(q, grid), grid, mats, thinc, limiter)[0]
+
+
+def operator_padded(q, qg, grid, mats, thinc, limiter="minmod"):
+    """D of Section 3.1 (planar) for the interior cells of q, from qg: q with
+    NG ghost layers on each side (filled by the caller).  Also returns the
+    face outputs of each axis (conservative fluxes, face phi, u, V)."""
     ny, nx = q["phi1"].shape
-    qg = fill_ghosts(q, grid)
     wg = cons_to_prim(qg, mats)
     comps = _components(wg)
     dims = [0] if grid["dim"] == 1 else [0, 1]
@@ -328,7 +334,7 @@ def _planar_operator(q, grid, mats, thinc, limiter="minmod"):
             F = {k: v.transpose(0, 1) for k, v in F.items()}
             phi_f, u_f, V_f = phi_f.transpose(0, 1), u_f.transpose(0, 1), V_f.transpose(0, 1)
         faces.append((F, phi_f, u_f, V_f))
-    return operator_from_faces(q, faces, grid)
+    return operator_from_faces(q, faces, grid), faces
 
 
 # ----------------------------------------------------------------------------
