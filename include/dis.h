@@ -50,7 +50,10 @@ enum {
   DIS_ESTATE = -5        /* call out of order (e.g. step before set_state) */
 };
 
-enum { DIS_BC_TRANSMISSIVE = 0, DIS_BC_PERIODIC = 1, DIS_BC_REFLECTIVE = 2 };
+/* DIS_BC_EXTERNAL: the ghost layers of that side are read as stored in the
+ * state (filled by the AMR hierarchy's ghost-cell kernel); not accepted by
+ * dis_create. */
+enum { DIS_BC_TRANSMISSIVE = 0, DIS_BC_PERIODIC = 1, DIS_BC_REFLECTIVE = 2, DIS_BC_EXTERNAL = 3 };
 enum { DIS_CONSERVATIVE = 0, DIS_PRIMITIVE = 1 };
 enum { DIS_FP64 = 0, DIS_FP32_BULK = 1 };
 enum { DIS_PLASTIC_NONE = 0, DIS_PLASTIC_PERFECT = 1, DIS_PLASTIC_RATE = 2 };
@@ -434,6 +437,72 @@ int dis_cfl_dt_static(int dim, int n_patches, const dis_patch* patches,
  * of the ALU-bound kernels are fractions of these.  Allocates a small output
  * buffer; synchronises.  DIS_EINVAL (NULL output), DIS_ENOMEM, DIS_ECUDA. */
 int dis_alu_peaks(void* stream, double* fp32_tflops, double* fp64_tflops, double* ms);
+
+/* ------------------------------------------------------------------------
+ * Structured adaptive mesh refinement (Section 3, the AMR platform
+ * paragraph: a hierarchy of levels refined recursively by a flagging
+ * criterion, ratio 2 in space and time per level, the single-grid update
+ * applied to every patch of a level; Section 4.2: difference-based
+ * flagging).  The hierarchy covers one rectangular domain.  Level 0 is one
+ * patch; level l + 1 refines whole blocks of block x block cells of level l
+ * (block cells in 1D) into patches of 2 block x 2 block cells, stepped as
+ * one batch.  Per level-0 step (dt_0 = min over levels of 2^l times the CFL
+ * step of the cells level l owns), level l takes 2^l steps of dt_0 / 2^l;
+ * before each Runge-Kutta stage the ghost cells of level l >= 1 come from
+ * level l (copies) or from level l - 1 (conservative linear interpolation in
+ * space, minmod slopes, and linear interpolation in time); after the two
+ * steps of level l + 1 its mean replaces each covered cell of level l and the
+ * conservative rows (phi_l rho_l, rho u, rho E, phi_y rho_y lam) of the level l
+ * cells next to it are refluxed with the time- and area-averaged fine fluxes.
+ * Every regrid_every level-0 steps the levels are rebuilt from the coarsest:
+ * a cell is tagged when the fractional change of phi1, phi_l rho_l, p or a
+ * velocity component to a face neighbour exceeds eps (floors: 1 for phi1,
+ * u_floor for velocities), tags are dilated by `buffer` cells, and a block is
+ * refined when it holds a tag and, on levels >= 1, its neighbouring blocks
+ * are refined (proper nesting).  Float64, SSP-RK3, planar.  No counterpart
+ * in the paper for the block and nesting rules: the paper's platform leaves
+ * them to AMReX. */
+typedef struct dis_amr dis_amr;
+typedef struct {
+  int32_t max_levels;   /* 1 .. 4 */
+  int32_t block;        /* block edge in cells of the coarser level, >= 4; divides nx (and ny) */
+  double eps;           /* flagging threshold (fractional change) */
+  int32_t buffer;       /* tag dilation in cells */
+  double u_floor;       /* velocity floor of the fractional change (m/s) */
+  int32_t regrid_every; /* level-0 steps between regrids (0 = never after the first) */
+} dis_amr_options;
+
+/* domain: the level-0 patch (bc: transmissive, periodic or reflective);
+ * opt: as dis_create (precision DIS_FP64, scheme DIS_RK3, geometry
+ * DIS_PLANAR).  DIS_EINVAL for other options or a block that does not divide
+ * the domain; DIS_ECUDA. */
+int dis_amr_create(int dim, const dis_patch* domain, int reactive_material, const dis_options* opt,
+                   const dis_amr_options* aopt, void* stream, dis_amr** out);
+/* Materials of every level (as dis_set_materials). */
+int dis_amr_set_materials(dis_amr* h, const dis_material* m, int n);
+/* Level-0 state (host or device pointer, kind DIS_CONSERVATIVE or
+ * DIS_PRIMITIVE, the layout of dis_set_state for the domain patch); builds
+ * the finer levels by flagging and conservative interpolation. */
+int dis_amr_set_state(dis_amr* h, const double* src, int kind);
+/* n level-0 steps (all levels subcycled, regrids as configured); dt_out
+ * (host, may be NULL) receives the n level-0 time steps.  Synchronises.
+ * DIS_ENONPHYSICAL if a level lost hyperbolicity (dis_amr_check). */
+int dis_amr_step(dis_amr* h, int n_steps, double* dt_out);
+/* Number of levels in use and blocks (patches) per level (counts[max_levels],
+ * level 0 counts 1). */
+int dis_amr_levels(const dis_amr* h, int* n_levels, int* counts);
+/* Level `level` as a dense array of the whole domain at that level's
+ * resolution (host; the dis_get_state layout of a patch of nx 2^l x ny 2^l
+ * cells, kind DIS_CONSERVATIVE or DIS_PRIMITIVE); cells the level does not
+ * own hold NaN; active (host, may be NULL) receives 1 for owned cells. */
+int dis_amr_get_level(dis_amr* h, int level, int kind, double* dst, unsigned char* active);
+/* Sum over the cells no finer level covers of each conservative field times
+ * the cell volume (nf values, host). */
+int dis_amr_totals(dis_amr* h, double* out);
+/* Status of the levels: DIS_OK or DIS_ENONPHYSICAL with the level, block and
+ * cell of the first bad cell. */
+int dis_amr_check(dis_amr* h, int* level, int* patch, int* cell);
+void dis_amr_destroy(dis_amr* h);
 
 /* Thread-local text of the last error (never NULL). */
 const char* dis_last_error(void);

@@ -44,8 +44,10 @@ Readings (the paper leaves these to its platform):
     the same face.  phi1 and V carry non-conservative terms and are not
     refluxed.
   * Regridding every `regrid_every` level-0 steps, level by level from the
-    coarsest: cells that stay refined keep their values, new ones take the
-    interpolation of the (current) coarser level.
+    coarsest: the cells level l does not own first take the interpolation of
+    the (current) level l - 1, then level l is tagged; cells that stay
+    refined keep their values, new ones take the interpolation of the
+    (current) coarser level.
 
 Representation: every level holds a dense array of the whole domain at its
 resolution and a mask of the cells it owns; cells it does not own hold the
@@ -220,6 +222,10 @@ class Hierarchy:
     def regrid(self):
         """Rebuild levels 1 .. max_level - 1 from the data of the coarser ones."""
         for l in range(self.max_level - 1):
+            if l >= 1:  # cells level l does not own: the interpolation of the (current) level l - 1
+                f = interp_fine(self.q[l - 1], self.grids[l - 1])
+                a = self.active[l]
+                self.q[l] = {k: torch.where(a.reshape(a.shape + _trail(v)), v, f[k]) for k, v in self.q[l].items()}
             blocks = self._new_blocks(l)
             act = _expand(blocks, self.B, self.dim)
             fine = interp_fine(self.q[l], self.grids[l])

@@ -109,6 +109,20 @@ int dis_internal_ensure_ws(dis_ctx* c);
 int dis_internal_steps(dis_ctx* c, int n, bool fixed);
 // Release the adjoint buffers of a context.
 void dis_internal_adj_free(dis_ctx* c);
+// Hooks of dis_internal_step64_hooked: before(user, stage, stage source
+// state), after_flux(user, stage), enqueued on the context's stream.
+struct StepHooks {
+  void (*before)(void* user, int stage, double* qsrc) = nullptr;
+  void (*after_flux)(void* user, int stage) = nullptr;
+  void* user = nullptr;
+};
+int dis_internal_step64_hooked(dis_ctx* c, const StepHooks& h);
+// Per-patch CFL rate sum_d (|u_d| + c_L) / dx_d, max over the interior
+// cells of q^n (host, np values; synchronises).
+int dis_internal_rates(dis_ctx* c, double* host);
+// dis_create that accepts DIS_BC_EXTERNAL sides (the AMR levels).
+int dis_internal_create_external(int dim, int n_patches, const dis_patch* patches, int reactive_material,
+                                 const dis_options* opt, void* stream, dis_ctx** out);
 // A Romenskii or JWL material in the context (the kernels with the general
 // closures run).
 bool general_closures(const dis_ctx* c);

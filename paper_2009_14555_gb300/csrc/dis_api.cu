@@ -897,6 +897,77 @@ int dis_internal_ensure_ws(dis_ctx* c) { return ensure_ws(c); }
 
 int dis_internal_steps(dis_ctx* c, int n, bool fixed) { return dispatch_steps(c, n, fixed); }
 
+// One float64 Runge-Kutta step with the per-patch dt of c->dtfix, calling
+// h.before(stage, source state) before each stage's recovery and
+// h.after_flux(stage) after its flux kernels (all on c->stream).
+namespace {
+template <int DIM, bool RX>
+void step64_hooked(dis_ctx* c, const StepHooks& h) {
+  StepArgs a = base_args(c);
+  a.dtfix = c->dtfix;
+  const double ca[3] = {0.0, 0.75, 1.0 / 3.0};
+  const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
+  const unsigned np = (unsigned)c->seg_prim.size(), nfx = (unsigned)c->seg_fx.size(),
+                 nfy = (unsigned)c->seg_fy.size(), nc = (unsigned)c->seg_cell.size();
+  for (int stg = 0; stg < 3; ++stg) {
+    a.qsrc = stg == 0 ? c->q[0] : c->q[1];
+    a.qn = c->q[0];
+    a.qdst = stg == 2 ? c->q[0] : c->q[1];
+    a.a = ca[stg];
+    a.b = cb[stg];
+    a.last = stg == 2;
+    if (h.before) h.before(h.user, stg, a.qsrc);
+    k_prim<DIM, RX><<<np, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_prim, 0);
+    k_flux<DIM, RX, 0><<<nfx, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_fx);
+    if constexpr (DIM == 2) k_flux<DIM, RX, 1><<<nfy, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_fy);
+    if (h.after_flux) h.after_flux(h.user, stg);
+    k_update<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_cell);
+  }
+}
+
+// Per-patch CFL rate max of the state q[0] (interior cells) into c->rate.
+template <int DIM, bool RX>
+void rates64(dis_ctx* c) {
+  StepArgs a = base_args(c);
+  a.qsrc = c->q[0];
+  cudaMemsetAsync(c->rate, 0, sizeof(unsigned long long) * c->np, c->stream);
+  k_prim<DIM, RX><<<(unsigned)c->seg_prim.size(), SEG, 0, c->stream>>>(c->phys, a, c->d_seg_prim, 1);
+}
+}  // namespace
+
+int dis_internal_step64_hooked(dis_ctx* c, const StepHooks& h) {
+  const bool rx = c->y >= 0;
+  if (c->dim == 1) rx ? step64_hooked<1, true>(c, h) : step64_hooked<1, false>(c, h);
+  else rx ? step64_hooked<2, true>(c, h) : step64_hooked<2, false>(c, h);
+  CU(cudaGetLastError());
+  return DIS_OK;
+}
+
+int dis_internal_rates(dis_ctx* c, double* host) {
+  const bool rx = c->y >= 0;
+  if (c->dim == 1) rx ? rates64<1, true>(c) : rates64<1, false>(c);
+  else rx ? rates64<2, true>(c) : rates64<2, false>(c);
+  CU(cudaGetLastError());
+  std::vector<unsigned long long> r(c->np);
+  CU(cudaMemcpyAsync(r.data(), c->rate, sizeof(unsigned long long) * c->np, cudaMemcpyDeviceToHost, c->stream));
+  CU(cudaStreamSynchronize(c->stream));
+  for (int p = 0; p < c->np; ++p) {
+    double v;
+    std::memcpy(&v, &r[p], sizeof v);
+    host[p] = v;
+  }
+  return DIS_OK;
+}
+
+thread_local bool g_allow_external = false;
+int dis_internal_create_external(int dim, int n_patches, const dis_patch* patches, int reactive_material,
+                                 const dis_options* opt, void* stream, dis_ctx** out) {
+  g_allow_external = true;
+  const int rc = dis_create(dim, n_patches, patches, reactive_material, opt, stream, out);
+  g_allow_external = false;
+  return rc;
+}
+
 extern "C" {
 
 const char* dis_last_error(void) { return g_err.c_str(); }
@@ -930,7 +1001,8 @@ int dis_create(int dim, int n_patches, const dis_patch* patches, int reactive_ma
     if ((long long)P.nx * ny > (1LL << 31))
       return fail(DIS_EINVAL, "dis_create: patch %d is too large", p);
     for (int k = 0; k < (dim == 2 ? 4 : 2); ++k)
-      if (P.bc[k] < 0 || P.bc[k] > 2) return fail(DIS_EINVAL, "dis_create: patch %d bad bc", p);
+      if (P.bc[k] < 0 || P.bc[k] > (g_allow_external ? 3 : 2))
+        return fail(DIS_EINVAL, "dis_create: patch %d bad bc", p);
     if (opt->geometry == DIS_CYLINDRICAL && !(P.x0 >= 0.0))
       return fail(DIS_EINVAL, "dis_create: patch %d has x0 %g < 0 (a radius)", p, P.x0);
   }

@@ -53,11 +53,13 @@ __device__ __forceinline__ long long cidx(const PatchDev& p, int i, int j) {
 // reflective boundary flips this axis' normal velocity.
 __device__ __forceinline__ int ghost_map(int i, int n, int bclo, int bchi, bool& flip) {
   if (i < 0) {
+    if (bclo == 3) return i;  // external: the stored ghost layer
     if (bclo == 1) return i + n;
     if (bclo == 2) { flip = !flip; return -1 - i; }
     return 0;
   }
   if (i >= n) {
+    if (bchi == 3) return i;
     if (bchi == 1) return i - n;
     if (bchi == 2) { flip = !flip; return 2 * n - 1 - i; }
     return n - 1;
