@@ -21,6 +21,7 @@ DIS_EOS_STIFFENED, DIS_EOS_ROMENSKII, DIS_EOS_JWL = 0, 1, 2
 DIS_PLANAR, DIS_CYLINDRICAL = 0, 1
 DIS_RATE_ARRHENIUS, DIS_RATE_SQRT = 0, 1
 DIS_NPARAM = 6  # per material l: G, sigma_y, Q at 3 l + k
+DIS_BC_TRANSMISSIVE, DIS_BC_PERIODIC, DIS_BC_REFLECTIVE, DIS_BC_EXTERNAL = 0, 1, 2, 3
 DIS_NVARIANTS = 6  # FP32-bulk stage variants: 3 tile shapes x 2 register budgets
 
 
@@ -50,6 +51,11 @@ class DisPatch(ctypes.Structure):
 class DisOptions(ctypes.Structure):
     _fields_ = [("cfl", c_double), ("thinc", c_int32), ("precision", c_int32), ("scheme", c_int32),
                 ("geometry", c_int32), ("limiter", c_int32)]
+
+
+class DisAmrOptions(ctypes.Structure):
+    _fields_ = [("max_levels", c_int32), ("block", c_int32), ("eps", c_double), ("buffer", c_int32),
+                ("u_floor", c_double), ("regrid_every", c_int32)]
 
 
 class DisError(RuntimeError):
@@ -90,6 +96,16 @@ SIGNATURES = {
     "dis_set_patch_state": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int]),
     "dis_get_patch_state": (c_int, [c_void_p, c_int, c_int, c_void_p, c_int]),
     "dis_query": (c_int, [c_void_p, c_void_p]),
+    "dis_amr_create": (c_int, [c_int, POINTER(DisPatch), c_int, POINTER(DisOptions), POINTER(DisAmrOptions),
+                               c_void_p, POINTER(c_void_p)]),
+    "dis_amr_set_materials": (c_int, [c_void_p, POINTER(DisMaterial), c_int]),
+    "dis_amr_set_state": (c_int, [c_void_p, c_void_p, c_int]),
+    "dis_amr_step": (c_int, [c_void_p, c_int, c_void_p]),
+    "dis_amr_levels": (c_int, [c_void_p, POINTER(c_int), c_void_p]),
+    "dis_amr_get_level": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "dis_amr_totals": (c_int, [c_void_p, c_void_p]),
+    "dis_amr_check": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    "dis_amr_destroy": (None, [c_void_p]),
     "dis_last_error": (c_char_p, []),
     "dis_destroy": (None, [c_void_p]),
 }

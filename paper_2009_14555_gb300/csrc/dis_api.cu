@@ -916,7 +916,7 @@ void step64_hooked(dis_ctx* c, const StepHooks& h) {
     a.a = ca[stg];
     a.b = cb[stg];
     a.last = stg == 2;
-    if (h.before) h.before(h.user, stg, a.qsrc);
+    if (h.before) h.before(h.user, stg, stg == 0 ? c->q[0] : c->q[1]);
     k_prim<DIM, RX><<<np, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_prim, 0);
     k_flux<DIM, RX, 0><<<nfx, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_fx);
     if constexpr (DIM == 2) k_flux<DIM, RX, 1><<<nfy, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_fy);

@@ -294,3 +294,82 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class AmrSolver:
+    """The structured AMR hierarchy of include/dis.h (dis_amr_*) over the
+    domain of a one-patch workload; float64 SSP-RK3, planar."""
+
+    def __init__(self, wl, max_levels=2, block=8, eps=0.1, buffer=2, u_floor=1.0, regrid_every=4,
+                 device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("AmrSolver needs a CUDA device (no CPU fallback)")
+        assert len(wl.patches) == 1
+        dev = torch.device(device or "cuda")
+        if dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        torch.cuda.set_device(dev)
+        self.device = dev
+        self.wl = wl
+        self.dim = wl.dim
+        self.reactive = wl.reactive_material >= 0
+        self.nf = (11 if wl.dim == 2 else 8) + (1 if self.reactive else 0)
+        self.stream = torch.cuda.current_stream(dev)
+        opts = L.DisOptions(float(wl.cfl), int(bool(wl.thinc)), L.DIS_FP64, L.DIS_RK3, L.DIS_PLANAR,
+                            {"minmod": L.DIS_MINMOD, "vanleer": L.DIS_VANLEER}[getattr(wl, "limiter", "minmod")])
+        aopt = L.DisAmrOptions(int(max_levels), int(block), float(eps), int(buffer), float(u_floor),
+                               int(regrid_every))
+        self.max_levels = int(max_levels)
+        p = wl.patches[0]
+        self.base = (p.nx, p.ny if wl.dim == 2 else 1)
+        lib = L.load()
+        out = ctypes.c_void_p()
+        dp = _patch(p, wl.dim)
+        L.check(lib.dis_amr_create(wl.dim, ctypes.byref(dp), wl.reactive_material, ctypes.byref(opts),
+                                   ctypes.byref(aopt), ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(out)))
+        self.h = out
+        mats = (L.DisMaterial * 2)(*[_material(m) for m in wl.materials])
+        L.check(lib.dis_amr_set_materials(self.h, mats, 2))
+
+    def set_prim(self, prim):
+        a = np.ascontiguousarray(prim, dtype=np.float64)
+        L.check(L.load().dis_amr_set_state(self.h, a.ctypes.data, L.DIS_PRIMITIVE))
+
+    def step(self, n=1):
+        dts = np.zeros(n)
+        L.check(L.load().dis_amr_step(self.h, n, dts.ctypes.data))
+        return dts
+
+    def levels(self):
+        n = ctypes.c_int()
+        counts = (ctypes.c_int * self.max_levels)()
+        L.check(L.load().dis_amr_levels(self.h, ctypes.byref(n), counts))
+        return n.value, list(counts)
+
+    def get_level(self, level, kind=L.DIS_CONSERVATIVE):
+        nx, ny = self.base[0] << level, (self.base[1] << level) if self.dim == 2 else 1
+        out = np.empty((self.nf, ny, nx))
+        act = np.zeros((ny, nx), dtype=np.uint8)
+        L.check(L.load().dis_amr_get_level(self.h, level, kind, out.ctypes.data, act.ctypes.data))
+        return out, act.astype(bool)
+
+    def totals(self):
+        out = np.zeros(self.nf)
+        L.check(L.load().dis_amr_totals(self.h, out.ctypes.data))
+        return out
+
+    def check(self):
+        lv, p, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        rc = L.load().dis_amr_check(self.h, ctypes.byref(lv), ctypes.byref(p), ctypes.byref(c))
+        return rc, lv.value, p.value, c.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            L.load().dis_amr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

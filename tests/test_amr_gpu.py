@@ -1,0 +1,135 @@
+"""The structured AMR hierarchy (dis_amr_*; Section 3, the AMR platform
+paragraph; Section 4.2 flagging) against the oracle's hierarchy
+(oracle/amr.py) through the C ABI, float64: the same levels and blocks (the
+cell masks of every level equal), the same level-0 time steps (rtol 1e-12),
+and every owned cell of every level at the parity bar (per-field relative
+L1 1e-10 over the owned cells, element-wise 1e-8 of the field's range).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import amr as A
+from oracle import closures as C
+from oracle import scheme as S
+from paper_2009_14555_gb300 import workloads as W
+from tests.parity_util import record
+
+pytestmark = pytest.mark.gpu
+TOL, TOL_MAX = 1e-10, 1e-8
+
+
+def _oracle(wl, **kw):
+    p = wl.patches[0]
+    q = C.prim_to_cons(S.prim_from_array(p.prim, wl.dim, wl.reactive), wl.materials)
+    return A.Hierarchy(q, S.grid_of(p, wl.dim), wl.materials, dict(cfl=wl.cfl, thinc=wl.thinc, scheme="rk3"), **kw)
+
+
+def _gpu(wl, **kw):
+    from paper_2009_14555_gb300.solver import AmrSolver
+    s = AmrSolver(wl, max_levels=kw["max_level"], block=kw["block"], eps=kw["eps"], buffer=kw.get("buffer", 2),
+                  regrid_every=kw.get("regrid_every", 4))
+    s.set_prim(wl.patches[0].prim)
+    return s
+
+
+def compare(wl, steps, name, **kw):
+    o = _oracle(wl, **kw)
+    g = _gpu(wl, **kw)
+    n, counts = g.levels()
+    assert n == o.n_levels(), (n, o.n_levels())
+    odts = [o.step() for _ in range(steps)]
+    gdts = g.step(steps)
+    rc = g.check()
+    assert rc[0] == 0, rc
+    np.testing.assert_allclose(gdts, odts, rtol=1e-12)
+    n, counts = g.levels()
+    assert n == o.n_levels(), (n, o.n_levels())
+    errs, maxs = [], []
+    for l in range(n):
+        ga, act = g.get_level(l)
+        assert np.array_equal(act, o.active[l].numpy()), f"level {l} blocks differ"
+        oa = np.asarray(S.cons_to_array(o.q[l], wl.dim, wl.reactive))
+        ga = ga.reshape(ga.shape[0], -1)[:, act.reshape(-1)]
+        oa = oa.reshape(oa.shape[0], -1)[:, act.reshape(-1)]
+        scale = np.maximum(np.abs(oa).max(axis=1), 1e-300)
+        l1 = np.abs(ga - oa).sum(axis=1) / np.maximum(np.abs(oa).sum(axis=1), 1e-300)
+        mx = np.abs(ga - oa).max(axis=1) / scale
+        errs.append(l1)
+        maxs.append(mx)
+    err = np.max(errs, axis=0)
+    emax = np.max(maxs, axis=0)
+    record(name, steps=steps, l1=err, max_rel=emax, levels=int(n), blocks=counts)
+    g.close()
+    assert err.max() <= TOL, err
+    assert emax.max() <= TOL_MAX, emax
+    return o
+
+
+def test_amr_1d_solid_gas_three_levels():
+    compare(W.solid_gas_1d(128, steps=8), 8, "amr_1d_solid_gas_128_3levels_8",
+            max_level=3, block=8, eps=0.05, regrid_every=2)
+
+
+def test_amr_1d_periodic():
+    wl = W.solid_gas_1d(64, steps=8)
+    wl.patches[0].bc = [S.BC_PERIODIC] * 4
+    compare(wl, 8, "amr_1d_periodic_64_3levels_8", max_level=3, block=8, eps=0.05, regrid_every=2)
+
+
+def test_amr_2d_shock_disc():
+    wl = W.shock_disc_2d(64, steps=6, shock_x=0.3)
+    wl.thinc = False
+    compare(wl, 6, "amr_2d_shock_disc_64_2levels_6", max_level=2, block=8, eps=0.3, regrid_every=2)
+
+
+def test_amr_2d_shock_disc_thinc_three_levels():
+    wl = W.shock_disc_2d(64, steps=4, shock_x=0.3)
+    compare(wl, 4, "amr_2d_shock_disc_thinc_64_3levels_4", max_level=3, block=8, eps=0.3, regrid_every=2)
+
+
+def test_amr_2d_reactive_plate():
+    wl = W.reactive_plate_2d(64, 32, steps=4)
+    compare(wl, 4, "amr_2d_reactive_plate_64x32_2levels_4", max_level=2, block=8, eps=0.2, regrid_every=2)
+
+
+def test_amr_conservation_periodic_2d():
+    """Composite totals of the conservative rows on a periodic domain stay
+    constant to round-off (refluxing and average-down on the GPU)."""
+    from paper_2009_14555_gb300.solver import AmrSolver
+    wl = W.smooth_disc_2d(n=64, steps=1, u0=150.0)
+    g = AmrSolver(wl, max_levels=2, block=8, eps=0.5, buffer=0, regrid_every=2)
+    g.set_prim(wl.patches[0].prim)
+    n, counts = g.levels()
+    assert n == 2 and 0 < counts[1] < 64
+    t0 = g.totals()
+    g.step(6)
+    t1 = g.totals()
+    names = W.cons_names(2, False)
+    for k in ("ar1", "ar2", "mx", "my", "E"):
+        i = names.index(k)
+        scale = max(abs(t0[i]), abs(t0[names.index("E")]) * 1e-6)
+        assert abs(t1[i] - t0[i]) <= 1e-13 * scale, (k, t0[i], t1[i])
+    g.close()
+
+
+def test_amr_full_refinement_is_the_fine_grid():
+    """Every block refined: level 1 steps exactly as the uniform grid of twice
+    the resolution (the same kernels on the same data, dt_0 / 2 per step)."""
+    from paper_2009_14555_gb300.solver import AmrSolver, Solver
+    wl = W.solid_gas_1d(64, steps=4)
+    g = AmrSolver(wl, max_levels=2, block=8, eps=-1.0, regrid_every=0)
+    g.set_prim(wl.patches[0].prim)
+    q1, act = g.get_level(1)
+    assert act.all()
+    fw = W.solid_gas_1d(128, steps=4)
+    f = Solver.from_workload(fw)
+    f.set_state(q1.reshape(-1), kind=0)
+    dts = g.step(4)
+    for dt in dts:
+        f.step_fixed_dt(2, np.array([dt / 2]))
+    out = f.get_arrays()[0]
+    q1, _ = g.get_level(1)
+    np.testing.assert_array_equal(q1.reshape(out.shape), out)
+    f.close()
+    g.close()
