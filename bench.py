@@ -445,7 +445,55 @@ def widened_bench(warmup=3):
     for prec, steps in (("fp32_bulk", 200), ("fp64", 30)):
         det[prec] = _timed_steps(wl, prim, prec, steps, warmup)
     out["sqrt_rate_law"] = det
+    out["amr"] = amr_bench()
     return out
+
+
+def amr_bench(n=256, levels=3, steps=12, warmup=2):
+    """The structured AMR hierarchy (float64) on the 2D shock-disc: an n x n
+    base and `levels` levels of ratio 2 (finest n 2^(L-1) squared), block 16,
+    flagging threshold 0.3, regrid every 4 level-0 steps; against the uniform
+    grid of the finest resolution over the same physical time (2^(L-1) of its
+    steps per level-0 step)."""
+    import torch
+    from paper_2009_14555_gb300 import workloads as W
+    from paper_2009_14555_gb300.solver import AmrSolver, Solver
+    wl = W.shock_disc_2d(n, steps=0, shock_x=0.3)
+    g = AmrSolver(wl, max_levels=levels, block=16, eps=0.3, regrid_every=4)
+    g.set_prim(wl.patches[0].prim)
+    g.step(warmup)
+    nl, counts = g.levels()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dts = g.step(steps)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / steps
+    nl2, counts2 = g.levels()
+    rc = g.check()[0]
+    # cells each level owns (blocks of (2 x 16)^2 cells) and the level steps per level-0 step
+    upd = n * n + sum(counts2[l] * (32 * 32) * 2 ** l for l in range(1, nl2))
+    g.close()
+    fine = n << (levels - 1)
+    fw = W.shock_disc_2d(fine, steps=0, shock_x=0.3)
+    f = Solver.from_workload(fw)
+    from paper_2009_14555_gb300.solver import pack
+    f.set_state(pack([fw.patches[0].prim]), kind=1)
+    f.step(2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(f.stream)
+    f.step(2 ** (levels - 1))
+    e1.record(f.stream)
+    torch.cuda.synchronize()
+    ms_fine = e0.elapsed_time(e1)
+    f.close()
+    return {"workload": f"2d_shock_disc_{n}x{n} base, {levels} levels (finest {fine}x{fine}), block 16, eps 0.3",
+            "precision": "fp64", "ms_per_level0_step": ms, "levels_used": nl2, "blocks_per_level": counts2,
+            "cell_updates_per_level0_step": upd, "value": upd / (ms * 1e-3), "unit": UNIT,
+            "finest_equivalent_cell_updates_per_s": fine * fine * 2 ** (levels - 1) / (ms * 1e-3),
+            "uniform_finest_ms_same_time": ms_fine, "speedup_vs_uniform_finest": ms_fine / ms,
+            "status_ok": rc == 0, "note": "wall time per level-0 step (the hierarchy synchronises each step); "
+                                          "uniform: 2^(L-1) float64 steps of the finest grid, CUDA events"}
 
 
 def hancock_bench(wl, prim, steps, warmup, precision="fp64"):
