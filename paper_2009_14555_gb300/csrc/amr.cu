@@ -150,6 +150,11 @@ __global__ void k_amr_reg(const RegE* __restrict__ R, int n, Fields F, const dou
   for (int k = 0; k < F.ncons; ++k) acc[(long long)e * F.ncons + k] += wdt * P[F.cons[k] * NFc + r.face];
 }
 
+__global__ void k_amr_setdt(double* dtfix, int n, double dt) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) dtfix[e] = dt;
+}
+
 // substep totals of the fine registers: R = T (first substep) or R + T; T = 0
 __global__ void k_amr_close(int n, double* T, double* R, int first) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -630,8 +635,7 @@ int advance(dis_amr* h, int l, double dt, double t0, double len) {
     ACU(cudaMemcpyAsync(L.q_old, L.c->q[0], bytes, cudaMemcpyDeviceToDevice, h->st));
     if (L.n_creg) ACU(cudaMemsetAsync(L.d_C, 0, sizeof(double) * (size_t)L.n_creg * h->F.ncons, h->st));
   }
-  std::vector<double> dts(L.c->np, dt);
-  ACU(cudaMemcpyAsync(L.c->dtfix, dts.data(), sizeof(double) * dts.size(), cudaMemcpyHostToDevice, h->st));
+  k_amr_setdt<<<nblk(L.c->np), TPB, 0, h->st>>>(L.c->dtfix, L.c->np, dt);
   h->hl = l;
   h->hdt = dt;
   h->ht0 = t0;
@@ -736,6 +740,12 @@ int regrid(dis_amr* h) {
       for (size_t k = l + 1; k < h->lev.size(); ++k) free_level(h->lev[k]);
       h->lev.resize(l + 1);
       break;
+    }
+    if ((int)h->lev.size() > l + 1) {  // the same blocks: level l + 1 keeps its context and data
+      const std::vector<int2>& oo = h->lev[l + 1].org;
+      bool same = oo.size() == org.size();
+      for (size_t b = 0; same && b < org.size(); ++b) same = oo[b].x == org[b].x && oo[b].y == org[b].y;
+      if (same) continue;
     }
     dis_amr_level N;
     if ((rc = make_level(h, l + 1, org, N))) {
@@ -888,26 +898,39 @@ int dis_amr_set_state(dis_amr* h, const double* src, int kind) {
 int dis_amr_step(dis_amr* h, int n_steps, double* dt_out) {
   if (!h) return AFAIL(DIS_EINVAL, "dis_amr_step: NULL argument");
   if (!h->have_state) return AFAIL(DIS_ESTATE, "dis_amr_step: no state");
+  int rc;
   for (int s = 0; s < n_steps; ++s) {
+    // the CFL rates of every level, one wait for all of them
+    std::vector<std::vector<unsigned long long>> r(h->lev.size());
+    for (size_t l = 0; l < h->lev.size(); ++l)
+      if ((rc = dis_internal_rates_enqueue(h->lev[l].c))) return rc;
+    for (size_t l = 0; l < h->lev.size(); ++l) {
+      r[l].resize(h->lev[l].c->np);
+      ACU(cudaMemcpyAsync(r[l].data(), h->lev[l].c->rate, sizeof(unsigned long long) * r[l].size(),
+                          cudaMemcpyDeviceToHost, h->st));
+    }
+    ACU(cudaStreamSynchronize(h->st));
     double dt = 0.0;
     for (size_t l = 0; l < h->lev.size(); ++l) {
-      dis_amr_level& L = h->lev[l];
-      std::vector<double> r(L.c->np);
-      int rc = dis_internal_rates(L.c, r.data());
-      if (rc) return rc;
       double m = 0.0;
-      for (double v : r) m = std::max(m, v);
+      for (unsigned long long bits : r[l]) {
+        double v;
+        std::memcpy(&v, &bits, sizeof v);
+        m = std::max(m, v);
+      }
       const double d = h->opt.cfl / m * (double)(1 << l);
       dt = l == 0 ? d : std::min(dt, d);
     }
-    int rc = advance(h, 0, dt, 0.0, 1.0);
-    if (rc) return rc;
-    ACU(cudaStreamSynchronize(h->st));
+    if ((rc = advance(h, 0, dt, 0.0, 1.0))) return rc;
     if (dt_out) dt_out[s] = dt;
     ++h->steps;
-    if ((rc = check_all(h, nullptr, nullptr, nullptr))) return rc;
-    if (h->regrid_every && h->steps % h->regrid_every == 0 && (rc = regrid(h))) return rc;
+    if (h->regrid_every && h->steps % h->regrid_every == 0) {
+      if ((rc = check_all(h, nullptr, nullptr, nullptr))) return rc;
+      if ((rc = regrid(h))) return rc;
+    }
   }
+  ACU(cudaStreamSynchronize(h->st));
+  if ((rc = check_all(h, nullptr, nullptr, nullptr))) return rc;
   return DIS_OK;
 }
 

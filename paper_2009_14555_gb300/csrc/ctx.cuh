@@ -120,6 +120,8 @@ int dis_internal_step64_hooked(dis_ctx* c, const StepHooks& h);
 // Per-patch CFL rate sum_d (|u_d| + c_L) / dx_d, max over the interior
 // cells of q^n (host, np values; synchronises).
 int dis_internal_rates(dis_ctx* c, double* host);
+// The same into c->rate (np values, the bits of doubles), without waiting.
+int dis_internal_rates_enqueue(dis_ctx* c);
 // dis_create that accepts DIS_BC_EXTERNAL sides (the AMR levels).
 int dis_internal_create_external(int dim, int n_patches, const dis_patch* patches, int reactive_material,
                                  const dis_options* opt, void* stream, dis_ctx** out);

@@ -943,6 +943,14 @@ int dis_internal_step64_hooked(dis_ctx* c, const StepHooks& h) {
   return DIS_OK;
 }
 
+int dis_internal_rates_enqueue(dis_ctx* c) {
+  const bool rx = c->y >= 0;
+  if (c->dim == 1) rx ? rates64<1, true>(c) : rates64<1, false>(c);
+  else rx ? rates64<2, true>(c) : rates64<2, false>(c);
+  CU(cudaGetLastError());
+  return DIS_OK;
+}
+
 int dis_internal_rates(dis_ctx* c, double* host) {
   const bool rx = c->y >= 0;
   if (c->dim == 1) rx ? rates64<1, true>(c) : rates64<1, false>(c);
