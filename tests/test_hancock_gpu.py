@@ -123,7 +123,7 @@ def test_fixed_dt_and_launch_count():
     s.close()
 
 
-def test_hancock_refuses_adjoint_and_fp32():
+def test_hancock_refuses_adjoint_and_cylindrical():
     from paper_2009_14555_gb300.solver import Solver
     wl = hancock(W.solid_gas_1d(64, steps=2))
     s = Solver.from_workload(wl)
@@ -131,8 +131,9 @@ def test_hancock_refuses_adjoint_and_fp32():
     with pytest.raises(RuntimeError):
         s.adj_forward(2, every=1, material=0)
     s.close()
-    with pytest.raises(RuntimeError):
-        Solver.from_workload(wl, precision="fp32_bulk")
+    for prec in ("fp64", "fp32_bulk"):
+        with pytest.raises(RuntimeError):
+            Solver.from_workload(wl, precision=prec, geometry="cyl")
 
 
 def test_adjoint_refuses_hancock():
