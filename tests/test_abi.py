@@ -134,3 +134,43 @@ def test_rate_law_validation(lib):
     assert lib.dis_set_materials(ctx, (L.DisMaterial * 2)(gas, rx(L.DIS_RATE_SQRT)), 2) == L.DIS_OK
     assert lib.dis_set_materials(ctx, (L.DisMaterial * 2)(gas, rx(L.DIS_RATE_ARRHENIUS)), 2) == L.DIS_OK
     lib.dis_destroy(ctx)
+
+
+def test_amr_create_validates_arguments(lib):
+    """dis_amr_create: float64 SSP-RK3 planar only, levels 1..4, block >= 4
+    dividing the domain, known boundary kinds (no device work here)."""
+    out = ctypes.c_void_p()
+    dom = L.DisPatch(64, 1, 1.0 / 64, 1.0, (ctypes.c_int32 * 4)(0, 0, 0, 0))
+    opts = L.DisOptions(0.8, 0, L.DIS_FP64, L.DIS_RK3)
+    ok = L.DisAmrOptions(3, 8, 0.1, 2, 1.0, 4)
+    assert lib.dis_amr_create(1, ctypes.byref(dom), -1, ctypes.byref(opts), ctypes.byref(ok), None,
+                              ctypes.byref(out)) == L.DIS_OK
+    lib.dis_amr_destroy(out)
+    for bad in (L.DisAmrOptions(5, 8, 0.1, 2, 1.0, 4), L.DisAmrOptions(0, 8, 0.1, 2, 1.0, 4),
+                L.DisAmrOptions(2, 3, 0.1, 2, 1.0, 4), L.DisAmrOptions(2, 24, 0.1, 2, 1.0, 4),
+                L.DisAmrOptions(2, 8, 0.1, -1, 1.0, 4)):
+        assert lib.dis_amr_create(1, ctypes.byref(dom), -1, ctypes.byref(opts), ctypes.byref(bad), None,
+                                  ctypes.byref(out)) == L.DIS_EINVAL
+    for o in (L.DisOptions(0.8, 0, L.DIS_FP32_BULK, L.DIS_RK3), L.DisOptions(0.8, 0, L.DIS_FP64, L.DIS_HANCOCK),
+              L.DisOptions(0.8, 0, L.DIS_FP64, L.DIS_RK3, L.DIS_CYLINDRICAL)):
+        assert lib.dis_amr_create(1, ctypes.byref(dom), -1, ctypes.byref(o), ctypes.byref(ok), None,
+                                  ctypes.byref(out)) == L.DIS_EINVAL
+    ext = L.DisPatch(64, 1, 1.0 / 64, 1.0, (ctypes.c_int32 * 4)(L.DIS_BC_EXTERNAL, 0, 0, 0))
+    assert lib.dis_amr_create(1, ctypes.byref(ext), -1, ctypes.byref(opts), ctypes.byref(ok), None,
+                              ctypes.byref(out)) == L.DIS_EINVAL
+    # the external kind is internal to the hierarchy's levels
+    arr = (L.DisPatch * 1)(ext)
+    assert lib.dis_create(1, 1, arr, -1, ctypes.byref(opts), None, ctypes.byref(out)) == L.DIS_EINVAL
+    assert lib.dis_amr_step(None, 1, None) == L.DIS_EINVAL
+
+
+def test_amr_solver_refuses_without_a_gpu():
+    """No CPU fallback: the Python hierarchy needs a CUDA device."""
+    import pytest
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2009_14555_gb300 import workloads as W
+    from paper_2009_14555_gb300.solver import AmrSolver
+    with pytest.raises(RuntimeError):
+        AmrSolver(W.solid_gas_1d(64, steps=1))
