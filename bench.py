@@ -446,7 +446,48 @@ def widened_bench(warmup=3):
         det[prec] = _timed_steps(wl, prim, prec, steps, warmup)
     out["sqrt_rate_law"] = det
     out["amr"] = amr_bench()
+    out["amr_detonation_1d"] = amr_detonation_bench()
     return out
+
+
+def amr_detonation_bench(n=1000, levels=3, steps=100, warmup=2):
+    """The one-dimensional test of Section 4.1 in its AMR setting: 1000 base
+    cells and two more levels of ratio 2 (effective 4000 cells), the generic
+    explosive against Romenskii copper, float64; against the uniform
+    4000-cell grid over the same physical time."""
+    import torch
+    from paper_2009_14555_gb300 import workloads as W
+    from paper_2009_14555_gb300.solver import AmrSolver, Solver, pack
+    wl = W.detonation_copper_1d(n, steps=0, explosive="generic")
+    g = AmrSolver(wl, max_levels=levels, block=8, eps=0.1, regrid_every=2)
+    g.set_prim(wl.patches[0].prim)
+    g.step(warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.step(steps)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / steps
+    nl, counts = g.levels()
+    rc = g.check()[0]
+    g.close()
+    fine = n << (levels - 1)
+    fw = W.detonation_copper_1d(fine, steps=0, explosive="generic")
+    f = Solver.from_workload(fw)
+    f.set_state(pack([fw.patches[0].prim]), kind=1)
+    f.step(2)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(f.stream)
+    f.step(2 ** (levels - 1) * 10)
+    e1.record(f.stream)
+    torch.cuda.synchronize()
+    ms_fine = e0.elapsed_time(e1) / 10
+    f.close()
+    return {"workload": f"1d_detonation_generic_explosive_{n} base, {levels} levels (effective {fine} cells)",
+            "precision": "fp64", "ms_per_level0_step": ms, "levels_used": nl, "blocks_per_level": counts,
+            "uniform_finest_ms_same_time": ms_fine, "speedup_vs_uniform_finest": ms_fine / ms,
+            "status_ok": rc == 0,
+            "note": "a single 1D problem: launch- and host-latency bound on either path"}
 
 
 def amr_bench(n=256, levels=3, steps=12, warmup=2):

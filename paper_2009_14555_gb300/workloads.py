@@ -320,12 +320,13 @@ def detonation_copper_1d(n: int = 1000, steps: int = 400, name=None, copper: str
     Copper: the Romenskii solid of the paper's table (rho_0 8930 kg/m^3,
     K_0 136.5 GPa, G_0 39.4 GPa, Gamma 2, alpha 1, beta 3; no plasticity), or
     with copper="stiffened" a stiffened gas of the same rho_0, Gamma,
-    gamma p_inf = K_0 and constant G = G_0.  The explosive is a stand-in (the
-    paper's two-EOS multiphase explosive is not among the closures built
-    here): an ideal-gas reactant/product pair with the product's gamma 3,
-    c_V 1000 and Q = 3.68 MJ/kg and the reactant's rho_0 = 1600 kg/m^3 from the
-    table of the generic explosive; explosive="generic" takes that table's
-    two closures (generic_explosive, float64 contexts).
+    gamma p_inf = K_0 and constant G = G_0.  Explosive: explosive="generic"
+    is the generic explosive of the paper's table (reactant and product
+    stiffened gases with closures of their own, component densities from
+    the temperature equality of Appendix B; float64 contexts), the default
+    "standin" one ideal gas for reactant and product with the product's
+    gamma 3, c_V 1000, Q = 3.68 MJ/kg and the reactant's rho_0 = 1600 kg/m^3
+    (every precision and the adjoint accept it).
     """
     copper = (COPPER_ROMENSKII if copper == "romenskii" else material(3.0, p_inf=136.5e9 / 3.0, G=39.4e9))
     expl = (generic_explosive() if explosive == "generic" else

@@ -129,6 +129,17 @@ def test_amr_2d_reactive_plate():
     compare(wl, 4, "amr_2d_reactive_plate_64x32_2levels_4", max_level=2, block=8, eps=0.2, regrid_every=2)
 
 
+def test_amr_detonation_section_4_1():
+    """The one-dimensional test of Section 4.1 in the paper's AMR setting (a
+    base grid and two more levels of ratio 2): the generic explosive (two
+    closures, the Appendix B root finder) against Romenskii copper, THINC on;
+    200 base cells (the paper: 1000), 30 level-0 steps; bar 1e-10 or 10 x the
+    oracle's one-ulp spread."""
+    wl = W.detonation_copper_1d(200, steps=30, explosive="generic")
+    compare(wl, 30, "amr_detonation_generic_200_3levels_30", calibrate=True, max_level=3, block=8, eps=0.1,
+            regrid_every=2)
+
+
 def test_amr_conservation_periodic_2d():
     """Composite totals of the conservative rows on a periodic domain stay
     constant to round-off (refluxing and average-down on the GPU)."""
