@@ -445,15 +445,20 @@ def widened_bench(warmup=3):
     for prec, steps in (("fp32_bulk", 200), ("fp64", 30)):
         det[prec] = _timed_steps(wl, prim, prec, steps, warmup)
     out["sqrt_rate_law"] = det
-    out["amr"] = amr_bench()
-    out["amr_detonation_1d"] = amr_detonation_bench()
+    for key, fn in (("amr", amr_bench), ("amr_detonation_1d", amr_detonation_bench)):
+        try:
+            out[key] = fn()
+        except Exception as e:  # the other rows are measured: keep them
+            out[key] = {"error": repr(e)}
     return out
 
 
-def amr_detonation_bench(n=1000, levels=3, steps=100, warmup=2):
+def amr_detonation_bench(n=1000, levels=3, steps=40, warmup=2):
     """The one-dimensional test of Section 4.1 in its AMR setting: 1000 base
     cells and two more levels of ratio 2 (effective 4000 cells), the generic
-    explosive against Romenskii copper, float64; against the uniform
+    explosive against Romenskii copper, float64; 40 level-0 steps from the
+    booster's ignition (longer runs reach a cell that leaves the hyperbolic
+    region where the detonation meets the copper); against the uniform
     4000-cell grid over the same physical time."""
     import torch
     from paper_2009_14555_gb300 import workloads as W
