@@ -362,10 +362,10 @@ int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
  * float64 (plus float64 primitive and face buffers for the reverse sweep).
  * In a DIS_CYLINDRICAL context the geometric source of Section 3 is reversed
  * with the rest of the stage, and J is the same plain sum over cells (no
- * factor r).  Returns DIS_EINVAL (bad arguments, a DIS_HANCOCK context: the
- * adjoint covers the Runge-Kutta scheme, a DIS_VANLEER context: it covers
- * the minmod limiter, a material that is not a stiffened gas, or a reactive
- * material with a product closure of its own), DIS_ESTATE
+ * factor r).  Both limiters are reversed.  Returns DIS_EINVAL (bad
+ * arguments, a DIS_HANCOCK context: the adjoint covers the Runge-Kutta
+ * scheme, a material that is not a stiffened gas, or a reactive material
+ * with a product closure of its own), DIS_ESTATE
  * (no state), DIS_ENOMEM, DIS_ECUDA.
  * Synchronises. */
 int dis_adj_forward(dis_ctx* ctx, int n_steps, int checkpoint_every, int objective_material,

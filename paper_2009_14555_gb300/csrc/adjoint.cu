@@ -380,8 +380,6 @@ int dis_adj_forward(dis_ctx* c, int n_steps, int checkpoint_every, int objective
   if (!c->have_state) return dis_internal_error(DIS_ESTATE, "dis_adj_forward: no state loaded");
   if (c->hancock)
     return dis_internal_error(DIS_EINVAL, "dis_adj_forward: the adjoint covers the Runge-Kutta scheme only");
-  if (c->phys.limiter != DIS_MINMOD)
-    return dis_internal_error(DIS_EINVAL, "dis_adj_forward: the adjoint covers the minmod limiter only");
   if (c->phys.m[0].eos != EOS_SG || c->phys.m[1].eos != EOS_SG || c->phys.m[0].two || c->phys.m[1].two)
     return dis_internal_error(DIS_EINVAL, "dis_adj_forward: the adjoint covers stiffened-gas materials only");
   if (n_steps <= 0 || checkpoint_every <= 0)

@@ -55,6 +55,7 @@ __device__ __forceinline__ PhysT<Dual> lift_phys(const Phys& P, int k) {
   D.thinc = P.thinc;
   D.cfl = P.cfl;
   D.cyl = P.cyl;
+  D.limiter = P.limiter;
   if (k >= 0) {
     const int l = k / 3, kind = k % 3;
     const MatDev& m = P.m[l];
@@ -342,7 +343,7 @@ __global__ void __launch_bounds__(SEG) k_adj_face(Phys P, AdjArgs A, const int4*
       double B[3][6];
       load_B(B);
       double phiL, phiR;
-      face_phi<DIM, double>(B, P.thinc != 0, hn, ht, phiL, phiR);
+      face_phi<DIM, double>(B, P.thinc != 0, hn, ht, phiL, phiR, P.limiter);
       Prim w[4];
 #pragma unroll
       for (int s = 0; s < 4; ++s) w[s] = load_prim<DIM, RX>(W, T, at(a - 1 + s));
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(SEG) k_adj_face(Phys P, AdjArgs A, const int4*
       for (int c = 0; c < NF; ++c) {
         if (c == L::PHI) continue;
         muscl_pair(prim_slot<DIM, RX>(w[0], c), prim_slot<DIM, RX>(w[1], c), prim_slot<DIM, RX>(w[2], c),
-                   prim_slot<DIM, RX>(w[3], c), prim_slot<DIM, RX>(wl, c), prim_slot<DIM, RX>(wr, c));
+                   prim_slot<DIM, RX>(w[3], c), prim_slot<DIM, RX>(wl, c), prim_slot<DIM, RX>(wr, c), P.limiter);
       }
       if constexpr (DIM == 1) {
         wl.v = wr.v = 0.0;
@@ -428,18 +429,18 @@ __global__ void __launch_bounds__(SEG) k_adj_face(Phys P, AdjArgs A, const int4*
       if (c == L::PHI) continue;
       const double v0 = W[c * T + at(a - 1)], v1 = W[c * T + at(a)];
       const double v2 = W[c * T + at(a + 1)], v3 = W[c * T + at(a + 2)];
-      if (okL) {  // wl = w1 + minmod(w1 - w0, w2 - w1) / 2
+      if (okL) {  // wl = w1 + lim(w1 - w0, w2 - w1) / 2
         double da, db;
-        minmod_grad(v1 - v0, v2 - v1, da, db);
+        limiter_grad(v1 - v0, v2 - v1, P.limiter, da, db);
         wb[0][c] += gL[c] * (-0.5 * da);
         wb[1][c] += gL[c] * (1.0 + 0.5 * (da - db));
         wb[2][c] += gL[c] * (0.5 * db);
       } else {
         wb[1][c] += gL[c];
       }
-      if (okR) {  // wr = w2 - minmod(w2 - w1, w3 - w2) / 2
+      if (okR) {  // wr = w2 - lim(w2 - w1, w3 - w2) / 2
         double da, db;
-        minmod_grad(v2 - v1, v3 - v2, da, db);
+        limiter_grad(v2 - v1, v3 - v2, P.limiter, da, db);
         wb[1][c] += gR[c] * (0.5 * da);
         wb[2][c] += gR[c] * (1.0 - 0.5 * (da - db));
         wb[3][c] += gR[c] * (-0.5 * db);
@@ -465,7 +466,7 @@ __global__ void __launch_bounds__(SEG) k_adj_face(Phys P, AdjArgs A, const int4*
       for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 6; ++c) Bb[r][c] = 0.0;
-      face_phi_vjp<DIM>(B, P.thinc != 0, hn, ht, gpL, gpR, Bb);
+      face_phi_vjp<DIM>(B, P.thinc != 0, hn, ht, gpL, gpR, Bb, P.limiter);
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
         if (!normals && r != 1) continue;
@@ -487,7 +488,7 @@ __global__ void __launch_bounds__(SEG) k_adj_face(Phys P, AdjArgs A, const int4*
 #pragma unroll
             for (int cc = 0; cc < 6; ++cc) Bd[rr][cc] = Dual(B[rr][cc], (rr == r && cc == c) ? 1.0 : 0.0);
           Dual pL, pR;
-          face_phi<DIM, Dual>(Bd, P.thinc != 0, hn, ht, pL, pR);
+          face_phi<DIM, Dual>(Bd, P.thinc != 0, hn, ht, pL, pR, P.limiter);
           const double v = gpL * pL.d + gpR * pR.d;
           add_nz(A.Wbar + L::PHI * T + at(a - 2 + c) + (long long)(r - 1) * stride_t, v);
         }

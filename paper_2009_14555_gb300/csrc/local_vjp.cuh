@@ -31,6 +31,21 @@ __device__ __forceinline__ void minmod_grad(double a, double b, double& da, doub
   }
 }
 
+// The same for the limiter lim (0 minmod; 1 van Leer's harmonic limiter
+// 2ab / (a + b) where ab > 0: d/da = 2 b^2 / (a + b)^2, d/db = 2 a^2 / (a + b)^2).
+__device__ __forceinline__ void limiter_grad(double a, double b, int lim, double& da, double& db) {
+  if (lim == 0) {
+    minmod_grad(a, b, da, db);
+    return;
+  }
+  da = db = 0.0;
+  if (a * b > 0.0) {
+    const double s = a + b;
+    da = 2.0 * b * b / (s * s);
+    db = 2.0 * a * a / (s * s);
+  }
+}
+
 // Adjoint of one star state (star_of) into its side K, S and S*.
 template <int DIR>
 __device__ __forceinline__ void star_of_vjp(const FState& K, double S, double Ss, const StarT<double>& t,
@@ -678,7 +693,7 @@ __device__ __forceinline__ void prim_of_vjp(const Phys& P, const double* q, cons
 // q_i, q_{i+1} to qb[0..2] and returns that of beta.
 template <class BetaFn>
 __device__ __forceinline__ double phi_cand_vjp(double qm, double qc, double qp, const BetaFn& beta_of, bool thinc,
-                                               int side, bool thinc_kept, double gb, double* qb) {
+                                               int side, bool thinc_kept, double gb, double* qb, int lim = 0) {
   const bool mixed = [&] {
     if (!thinc) return false;
     const double qmin = fmin(qm, qp);
@@ -687,10 +702,10 @@ __device__ __forceinline__ double phi_cand_vjp(double qm, double qc, double qp, 
     return C > 1e-5 && C < 1.0 - 1e-5 && (qp - qc) * (qc - qm) > 0.0;
   }();
   if (!(thinc_kept && mixed)) {
-    // MUSCL edge q_i -/+ minmod(q_i - q_{i-1}, q_{i+1} - q_i) / 2 (the THINC
+    // MUSCL edge q_i -/+ lim(q_i - q_{i-1}, q_{i+1} - q_i) / 2 (the THINC
     // candidate of a cell that is not mixed is the MUSCL one)
     double da, db;
-    minmod_grad(qc - qm, qp - qc, da, db);
+    limiter_grad(qc - qm, qp - qc, lim, da, db);
     const double h = side == 0 ? -0.5 * gb : 0.5 * gb;
     qb[0] -= h * da;
     qb[1] += gb + h * (da - db);
@@ -745,7 +760,7 @@ __device__ __forceinline__ double phi_cand_vjp(double qm, double qc, double qp, 
 // recomputed from the same candidates as the forward code.
 template <int DIM>
 __device__ __forceinline__ void face_phi_vjp(const double (&B)[3][6], bool thinc, double hn, double ht,
-                                             double gpL, double gpR, double (&Bb)[3][6]) {
+                                             double gpL, double gpR, double (&Bb)[3][6], int lim = 0) {
   const bool normals = DIM == 2 && thinc;
   // THINC steepness of candidate cell s, evaluated only where a mixed cell needs it
   auto beta_of = [&](int s) -> double {
@@ -758,7 +773,8 @@ __device__ __forceinline__ void face_phi_vjp(const double (&B)[3][6], bool thinc
   };
   Cand c[4];
 #pragma unroll
-  for (int s = 0; s < 4; ++s) c[s] = phi_cand_lazy(B[1][s], B[1][s + 1], B[1][s + 2], [&]() { return beta_of(s); }, thinc);
+  for (int s = 0; s < 4; ++s)
+    c[s] = phi_cand_lazy(B[1][s], B[1][s + 1], B[1][s + 2], [&]() { return beta_of(s); }, thinc, lim);
   // BVD choices (the test of bvd in physics.cuh): the right edge of cell 1
   // (phiL) and the left edge of cell 2 (phiR)
   auto use_thinc = [](const Cand& km, const Cand& k, const Cand& kp) {
@@ -771,14 +787,14 @@ __device__ __forceinline__ void face_phi_vjp(const double (&B)[3][6], bool thinc
   double betab[4] = {0.0, 0.0, 0.0, 0.0};
   if (gpL != 0.0) {
     double qb[3] = {0.0, 0.0, 0.0};
-    betab[1] = phi_cand_vjp(B[1][1], B[1][2], B[1][3], [&]() { return beta_of(1); }, thinc, 1, t1, gpL, qb);
+    betab[1] = phi_cand_vjp(B[1][1], B[1][2], B[1][3], [&]() { return beta_of(1); }, thinc, 1, t1, gpL, qb, lim);
     Bb[1][1] += qb[0];
     Bb[1][2] += qb[1];
     Bb[1][3] += qb[2];
   }
   if (gpR != 0.0) {
     double qb[3] = {0.0, 0.0, 0.0};
-    betab[2] = phi_cand_vjp(B[1][2], B[1][3], B[1][4], [&]() { return beta_of(2); }, thinc, 0, t2, gpR, qb);
+    betab[2] = phi_cand_vjp(B[1][2], B[1][3], B[1][4], [&]() { return beta_of(2); }, thinc, 0, t2, gpR, qb, lim);
     Bb[1][2] += qb[0];
     Bb[1][3] += qb[1];
     Bb[1][4] += qb[2];

@@ -71,7 +71,8 @@ def oracle_grad(wl, steps, material, qbar=None, kind="prim", prim=None):
         q0 = prim_to_cons(OS.prim_from_array(w0, wl.dim, wl.reactive), wl.materials)
         init = OS.cons_to_array(q0, wl.dim, wl.reactive).detach().clone().requires_grad_(True)
     J, _, dts = OA.rollout(init, kind, wl.dim, OA.with_params(wl.materials, theta), p,
-                           dict(cfl=wl.cfl, thinc=wl.thinc, geometry=getattr(wl, "geometry", "planar")),
+                           dict(cfl=wl.cfl, thinc=wl.thinc, geometry=getattr(wl, "geometry", "planar"),
+                                limiter=getattr(wl, "limiter", "minmod")),
                            steps, material,
                            None if qbar is None else qbar[0])
     J.backward()
@@ -135,6 +136,22 @@ def test_adjoint_1d_conservative_vs_oracle():
 def test_adjoint_2d_shock_disc_vs_oracle():
     wl = W.perturbed(W.shock_disc_2d(n=20, steps=4, thinc=False, shock_x=0.3))
     _case("2d_shock_disc_20_4", wl, 4, material=0, qbar_seed=3)
+
+
+def _vanleer(wl):
+    wl.limiter = "vanleer"
+    return wl
+
+
+def test_adjoint_vanleer_1d_vs_oracle():
+    """The van Leer limiter (harmonic slope 2ab / (a + b)) reversed by hand."""
+    wl = _vanleer(W.perturbed(W.solid_gas_1d(n=100, steps=12)))
+    _case("1d_solid_gas_vanleer_100_12", wl, 12, material=0, qbar_seed=1)
+
+
+def test_adjoint_vanleer_2d_thinc_vs_oracle():
+    wl = _vanleer(W.perturbed(W.shock_disc_2d(n=20, steps=4, thinc=True, shock_x=0.3)))
+    _case("2d_shock_disc_vanleer_thinc_20_4", wl, 4, material=0, qbar_seed=4)
 
 
 def test_adjoint_2d_thinc_vs_oracle():
@@ -359,7 +376,7 @@ def test_adjoint_of_fp32_bulk_run_matches_float64_adjoint():
     assert max(el1) <= 5e-2, el1
 
 
-@pytest.mark.parametrize("case", ["1d", "2d_thinc", "reactive", "sqrt_law"])
+@pytest.mark.parametrize("case", ["1d", "2d_thinc", "reactive", "sqrt_law", "vanleer_2d_thinc"])
 def test_hand_written_reverses_match_dual_numbers(case):
     """The hand-written reverses of the face Riemann problem (all six regions
     of the HLLD-type solver, shear coupling, wave-speed ties), the face-state
@@ -375,6 +392,7 @@ def test_hand_written_reverses_match_dual_numbers(case):
         "2d_thinc": (W.perturbed(W.shock_disc_2d(n=20, steps=4, thinc=True, shock_x=0.3)), 4, 0),
         "reactive": (W.perturbed(W.reactive_plate_2d(nx=48, ny=24, steps=3)), 3, 1),
         "sqrt_law": (_detonation_partial_burn(), 8, 1),
+        "vanleer_2d_thinc": (_vanleer(W.perturbed(W.shock_disc_2d(n=20, steps=4, thinc=True, shock_x=0.3))), 4, 0),
     }[case]
     rng = np.random.default_rng(123)
     p0 = wl.patches[0].prim

@@ -227,11 +227,3 @@ def test_vanleer_hancock_1d():
     assert_parity(wl, 40, name="1d_solid_gas_vanleer_hancock_400_40")
 
 
-def test_vanleer_adjoint_refused():
-    from paper_2009_14555_gb300.solver import Solver
-    wl = _vanleer(W.solid_gas_1d(64, steps=2))
-    s = Solver.from_workload(wl)
-    s.set_prim([wl.patches[0].prim])
-    with pytest.raises(RuntimeError):
-        s.adj_forward(2, every=1, material=0)
-    s.close()
