@@ -12,7 +12,7 @@ from __future__ import annotations
 
 import torch
 
-from .closures import phases, prim_to_cons
+from .closures import history_material, phases, prim_to_cons
 from .scheme import cons_from_array, cons_to_array, grid_of, prim_from_array, step
 
 PARAM_KEYS = ("G", "sigma_y", "Q")
@@ -24,7 +24,7 @@ def rollout(init, kind, dim, mats, patch, opts, steps, material=-1, qbar=None, d
     init: (nfields, ny, nx) primitive (kind "prim") or conservative array;
     mats: oracle material dicts whose G, sigma_y, Q entries may be tensors.
     """
-    reactive = any(m["reactive"] for m in mats)
+    reactive = history_material(mats) is not None
     if kind == "prim":
         q = prim_to_cons(prim_from_array(init, dim, reactive), mats)
     else:

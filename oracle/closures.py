@@ -24,7 +24,14 @@ Readings taken where the paper is silent or garbled:
   * dev(H) is taken as dev(1/4 (B - B^-1)) with B = V V^T (explicit deviator);
   * a reactive material has identical ideal-gas reactant and product closures
     (same gamma and C_V), so the temperature equality of Appendix B gives
-    rho_alpha = rho_beta = rho_y and the pressure function is closed form.
+    rho_alpha = rho_beta = rho_y and the pressure function is closed form;
+  * Johnson-Cook solid (Section 2.3.2): its temperature carries the thermal
+    energy of Section 2.2, E_t = C_V (T - T0 theta_D(rho)), with the Debye
+    temperature theta_D = (rho/rho0)^Gamma of a constant Grueneisen
+    coefficient (Gamma = rho theta_D' / theta_D; the printed derivative with
+    respect to ln(1/rho) has the opposite sign), and T0 the Johnson-Cook
+    reference temperature (298 K); the homologous temperature of the thermal
+    softening is clamped to [0, 1].
 """
 from __future__ import annotations
 
@@ -33,9 +40,22 @@ import torch
 F64 = torch.float64
 
 
+PLASTIC_NONE, PLASTIC_PERFECT, PLASTIC_IDEAL, PLASTIC_JC = 0, 1, 2, 3
+
+
 def Gamma(m) -> float:
     """Grueneisen coefficient Gamma = gamma - 1 (Section 2.3, ideal/stiffened gas)."""
     return m["gamma"] - 1.0
+
+
+def history_material(mats):
+    """Index of the material carrying the history row rho_y phi_y alpha_y of
+    Section 2.1: the reactive material (alpha = lam, Section 2.3.1) or a
+    Johnson-Cook solid (alpha = eps_p, Section 2.3.2); None without one."""
+    for i, m in enumerate(mats):
+        if m["reactive"] or m["plastic"] == PLASTIC_JC:
+            return i
+    return None
 
 
 # ----------------------------------------------------------------------------
@@ -315,6 +335,23 @@ def temperature(m, rho, p, J2, lam=None):
     return (p - p_ref(m, rho, J2)) / (rho * Gamma(m) * m["cv"])
 
 
+def jc_temperature(m, rho, p, J2):
+    """Temperature of a Johnson-Cook (Romenskii) solid at density rho and
+    pressure p: E - E_ref = C_V (T - T0 theta_D(rho)) (Section 2.2) with
+    E - E_ref = (p - p_ref) / (rho Gamma) (the Mie-Grueneisen form, Section
+    2.3) and theta_D = (rho/rho0)^Gamma."""
+    return m["jc_T0"] * (rho / m["rho0"]) ** Gamma(m) + (p - p_ref(m, rho, J2)) / (rho * Gamma(m) * m["cv"])
+
+
+def jc_yield(m, eps_p, T):
+    """Johnson-Cook yield stress of Section 2.3.2,
+    sigma_Y = (c1 + c2 eps_p^n) (1 - T*^m), T* = (T - T0) / (T_melt - T0)
+    clamped to [0, 1] (no softening below T0, no strength above T_melt);
+    eps_p^n of max(eps_p, 0).  c1 is the material's sigma_y."""
+    Ts = ((T - m["jc_T0"]) / (m["jc_Tmelt"] - m["jc_T0"])).clamp(0.0, 1.0)
+    return (m["sigma_y"] + m["jc_c2"] * eps_p.clamp(min=0.0) ** m["jc_n"]) * (1.0 - Ts ** m["jc_m"])
+
+
 def inv_gamma(m, p=None, lam=None):
     """1 / Gamma of a material in the mixture rules (phi / Gamma weights):
     s / Gamma_alpha + (1 - s) / Gamma_beta for two reactive closures."""
@@ -362,7 +399,7 @@ def prim_to_cons(w, mats):
     q = dict(phi1=w["phi1"], ar1=phis[0] * rhos[0], ar2=phis[1] * rhos[1],
              mom=rho[..., None] * w["u"], E=rhoe + ke, V=w["V"])
     if "lam" in w:
-        y = next(i for i, m in enumerate(mats) if m["reactive"])
+        y = history_material(mats)
         q["arl"] = q["ar1" if y == 0 else "ar2"] * w["lam"]
     return q
 
@@ -378,7 +415,7 @@ def cons_to_prim(q, mats):
     devH, J2 = hencky_dev(q["V"])
     lam = None
     if "arl" in q:
-        y = next(i for i, m in enumerate(mats) if m["reactive"])
+        y = history_material(mats)
         lam = q["arl"] / ars[y]
     p = mixture_pressure(phis, rhos, rhoe, J2, mats, lam)
     w = dict(phi1=q["phi1"], rho1=rhos[0], rho2=rhos[1], u=u, p=p, V=q["V"])

@@ -43,7 +43,7 @@ from __future__ import annotations
 
 import torch
 
-from .closures import hencky_dev, mixture_props, phases, stress, material_energy
+from .closures import history_material, hencky_dev, mixture_props, phases, stress, material_energy
 
 CONS_KEYS = ("ar1", "ar2", "mom", "E", "arl")
 
@@ -63,7 +63,7 @@ def face_state(w, mats):
              E=rhoe + 0.5 * rho * (w["u"] * w["u"]).sum(-1),
              sigma=stress(w["p"], Gm, devH), cL=torch.sqrt(cL2))
     if lam is not None:
-        y = next(i for i, m in enumerate(mats) if m["reactive"])
+        y = history_material(mats)
         s["arl"] = s["ar1" if y == 0 else "ar2"] * lam
     return s
 

@@ -33,8 +33,9 @@ import math
 
 import torch
 
-from .closures import (Gamma, cons_to_prim, hencky_dev, inv_gamma, mixture_props, phases,
-                       prim_to_cons, shear_modulus, stress, temperature, two_eos)
+from .closures import (PLASTIC_JC, Gamma, cons_to_prim, hencky_dev, history_material, inv_gamma,
+                       jc_temperature, jc_yield, mixture_props, phases, prim_to_cons, shear_modulus,
+                       stress, temperature, two_eos)
 from .reconstruction import (bvd_select, muscl_faces, thinc_beta, thinc_faces,
                              youngs_abs_normal)
 from .riemann import hllc
@@ -374,12 +375,21 @@ def plastic_update(q, mats, dt, iters=64):
     Perfect plasticity returns radially onto the yield surface,
     J*_l = min(J*, J_Y) with J_Y = sigma_Y / (sqrt(6) G) (the chi0 -> infinity
     limit of the relaxation objective); a finite rate chi0 solves the objective
-    R(J) = J - J* + dt chi(J) by bisection on [0, J*]."""
+    R(J) = J - J* + dt chi(J) by bisection on [0, J*].
+
+    Johnson-Cook (Section 2.3.2): chi = chi0 exp((sqrt(3/2) |dev sigma| /
+    sigma_Y(eps_p) - 1) / c3) with |dev sigma| = 2 G J, the objective's plastic
+    strain eps_p*(J) = eps_p + (J* - J) (the strain rate chi integrated over
+    the step, dt chi = J* - J at the root), and the temperature of the state
+    entering the step (frozen during it).  The history row rho_l phi_l eps_p
+    then grows by rho_l phi_l (J* - J*_l), the source of its evolution
+    equation over the step."""
     phis = phases(q["phi1"])
     devH, J2 = hencky_dev(q["V"])
     Jst = _sqrt0(J2)
     num = torch.zeros_like(Jst)
     den = torch.zeros_like(Jst)
+    arl_new = None
     # phi_l / Gamma_l weights (a two-closure reactive mixture: 1 / Gamma_y at
     # the state's own reactant share)
     if any(two_eos(m) for m in mats):
@@ -399,6 +409,28 @@ def plastic_update(q, mats, dt, iters=64):
             Jl = torch.minimum(Jst, JY)
         elif m["plastic"] == 0:
             Jl = Jst
+        elif m["plastic"] == PLASTIC_JC:
+            w0 = cons_to_prim(q, mats)
+            T = jc_temperature(m, ar / ph, w0["p"], J2)
+            eps0 = q["arl"] / ar
+
+            def chi_jc(J):
+                sY = jc_yield(m, eps0 + (Jst - J), T)
+                ratio = math.sqrt(1.5) * 2.0 * Gl * J / torch.where(sY > 0, sY, torch.ones_like(sY))
+                rate = m["chi0"] * torch.exp((ratio - 1.0) / m["jc_c3"])
+                # no strength left (at or above the melting temperature): the rate is unbounded
+                return torch.where(sY > 0, rate, torch.full_like(J, math.inf))
+
+            lo = torch.zeros_like(Jst)
+            hi = Jst.clone()
+            for _ in range(iters):  # bisection of R(J) = J - J* + dt chi(J, eps_p*(J)) on [0, J*]
+                mid = 0.5 * (lo + hi)
+                Rm = mid - Jst + dt * chi_jc(mid)
+                neg = Rm < 0
+                lo = torch.where(neg, mid, lo)
+                hi = torch.where(neg, hi, mid)
+            Jl = 0.5 * (lo + hi)
+            arl_new = q["arl"] + ar * (Jst - Jl)
         else:
             def chi(J):
                 # rate-dependent plasticity: chi0 H[sqrt(3/2) |dev sigma| - sigma_Y], |dev sigma| = 2 G J
@@ -424,6 +456,8 @@ def plastic_update(q, mats, dt, iters=64):
     Vn = torch.linalg.inv(eye - 0.5 * Hn) @ (eye + 0.5 * Hn)
     out = dict(q)
     out["V"] = Vn
+    if arl_new is not None:
+        out["arl"] = arl_new
     return out
 
 
@@ -500,7 +534,7 @@ def grid_of(patch, dim, geometry="planar"):
 
 def run(prim_array, dim, mats, grid, opts, steps, dt_list=None):
     """Initialise from primitives and take `steps` steps.  Returns (cons array, dts)."""
-    reactive = any(m["reactive"] for m in mats)
+    reactive = history_material(mats) is not None
     q = prim_to_cons(prim_from_array(prim_array, dim, reactive), mats)
     dts = []
     for s in range(steps):

@@ -13,18 +13,21 @@ volume fraction is stored:
     1D : phi1, rho1, rho2, u, p, V11, V22, V33, [lam]
     2D : phi1, rho1, rho2, u, v, p, V11, V12, V21, V22, V33, [lam]
 
-`lam` is the reaction progress variable of the reactive material (1 = reactant,
-0 = products, Section 2.3.1) and is present only when a material is reactive.
-Arrays are float64 with shape (nfields, ny, nx) (ny = 1 in 1D).
+`lam` is the history variable of Section 2.1 carried by one material: the
+reaction progress variable of the reactive material (1 = reactant, 0 =
+products, Section 2.3.1), or the equivalent plastic strain eps_p of a
+Johnson-Cook solid (Section 2.3.2); it is present only when a material carries
+one.  Arrays are float64 with shape (nfields, ny, nx) (ny = 1 in 1D).
 
 Materials are plain dicts with the keys
-    gamma, p_inf, e_inf, G, plastic (0 none, 1 perfect, 2 rate), sigma_y, chi0,
-    reactive (0/1), Q, cv, A, T_act, rate_law, p_ign
+    gamma, p_inf, e_inf, G, plastic (0 none, 1 perfect, 2 rate, 3 Johnson-Cook),
+    sigma_y, chi0, reactive (0/1), Q, cv, A, T_act, rate_law, p_ign
 (stiffened-gas Mie-Grueneisen closures, Section 2.3; perfect plasticity is the
 chi0 -> infinity limit of the ideal-plasticity rate, Section 2.3.2; the rate
 parameters only apply to a reactive material: rate_law 0 is the Arrhenius law
 with A, T_act, rate_law 1 the k sqrt(lam) law of Section 4.1 with k = A,
-switched on above the pressure p_ign).
+switched on above the pressure p_ign), plus the Romenskii, JWL, product-closure
+and Johnson-Cook (jc_*) keys of the helpers below.
 """
 from __future__ import annotations
 
@@ -88,9 +91,26 @@ def generic_explosive(A=2.0e6, rate_law=1, p_ign=1.0e8, T_act=0.0) -> dict:
     return m
 
 
+def johnson_cook(m, c1, c2, c3, n, m_exp, T_melt, T0=298.0, chi0=1.0, cv=385.0) -> dict:
+    """A Romenskii solid m with the Johnson-Cook plasticity of Section 2.3.2:
+    chi = chi0 exp((sqrt(3/2) |dev sigma| / sigma_Y - 1) / c3) with
+    sigma_Y = (c1 + c2 eps_p^n)(1 - ((T - T0)/(T_melt - T0))^m_exp).  The
+    material then carries the history row rho phi eps_p (the workload's
+    reactive_material names it).  chi0 = 1/s, the Johnson-Cook reference strain
+    rate, and cv = 385 J/(kg K), copper's specific heat, are not in the
+    paper's tables."""
+    out = dict(m)
+    out.update(plastic=3, sigma_y=float(c1), chi0=float(chi0), cv=float(cv), jc_c2=float(c2),
+               jc_c3=float(c3), jc_n=float(n), jc_m=float(m_exp), jc_Tmelt=float(T_melt), jc_T0=float(T0))
+    return out
+
+
 # Copper of the Romenskii table (Section 4.1): rho0 8930, K0 136.5 GPa,
 # G0 39.4 GPa, Gamma 2, alpha-bar 1, beta-bar 3.
 COPPER_ROMENSKII = romenskii(8930.0, 136.5e9, 39.4e9, 2.0, 1.0, 3.0)
+# The same copper with the Johnson-Cook table of the indentation tests
+# (Section 4.4): c1 0.4 GPa, c2 0.177 GPa, c3 0.025, n 1, m 1.09, T_melt 1358 K.
+COPPER_JC = johnson_cook(COPPER_ROMENSKII, 0.4e9, 0.177e9, 0.025, 1.0, 1.09, 1358.0)
 # LX-17 reactant of the JWL table: rho0 1905, A 778.1e11 Pa, B -0.0503e11 Pa,
 # R1 11.3, R2 1.13, Gamma 0.8938, C_V 1305.5.
 LX17_REACTANT_JWL = jwl(1905.0, 778.1e11, -0.0503e11, 11.3, 1.13, 0.8938, cv=1305.5)
@@ -125,7 +145,7 @@ class Workload:
     cfl: float
     steps: int
     thinc: bool
-    reactive_material: int = -1          # 0-based index of the reactive material, -1 none
+    reactive_material: int = -1          # material carrying the history row (reactive: lam; Johnson-Cook: eps_p), -1 none
     extra: dict = field(default_factory=dict)
     scheme: str = "rk3"                  # hyperbolic update: "rk3" (the paper's) or "hancock"
     geometry: str = "planar"             # "planar" (plane strain) or "cyl" (axisymmetric, x = r, y = z)
@@ -342,6 +362,63 @@ def detonation_copper_1d(n: int = 1000, steps: int = 400, name=None, copper: str
     p = Patch(nx=n, ny=1, dx=dx, dy=1.0, prim=w)
     return Workload(name or f"1d_detonation_copper_{n}", 1, [copper, expl], [p], 0.9, steps, True,
                     reactive_material=1)
+
+
+def jc_flyer_1d(n: int = 400, steps: int = 200, u_flyer: float = 876.0, name=None) -> Workload:
+    """Johnson-Cook copper plate impact on [0, 40] mm: a copper flyer
+    (x < 10 mm) at u_flyer m/s strikes copper at rest (10 < x < 30 mm), air
+    (ideal, gamma 1.4, 1.2 kg/m^3) beyond; 1e5 Pa everywhere, eps_p = 0;
+    CFL 0.6, transmissive ends, THINC on."""
+    air = material(1.4)
+    w, k = _blank(1, True, 1, n)
+    dx = 0.04 / n
+    xc = (np.arange(n) + 0.5) * dx
+    cu = xc < 0.03
+    w[k["phi1"], 0] = np.where(cu, 1.0 - EPS_PHI, EPS_PHI)
+    w[k["rho1"], 0] = 8930.0
+    w[k["rho2"], 0] = 1.2
+    w[k["u"], 0] = np.where(xc < 0.01, u_flyer, 0.0)
+    w[k["p"], 0] = 1.0e5
+    w[k["lam"], 0] = 0.0
+    p = Patch(nx=n, ny=1, dx=dx, dy=1.0, prim=w)
+    return Workload(name or f"1d_jc_flyer_{n}", 1, [COPPER_JC, air], [p], 0.6, steps, True,
+                    reactive_material=0)
+
+
+def indentation_rz(nr: int = 64, steps: int = 200, radius: float = 4.0e-3, u_drive: float = 876.0,
+                   name=None) -> Workload:
+    """The shock-driven hemispherical indentation of Section 4.4 in its
+    axisymmetric form (x = r, y = z): (r, z) in [0, 6.4] x [0, 32] mm, nr x 5 nr
+    square cells; Johnson-Cook copper below z = 20 mm with a hemispherical
+    indentation of the given radius centred on the axis at z = 20 mm, air
+    (gamma 1.4) above and inside it; the copper below z = 2 mm (14 mm of plate
+    under the indentation) moves at u_drive in +z, the driven base; 1e5 Pa,
+    eps_p = 0; reflective axis, transmissive elsewhere; CFL 0.6, THINC on.
+    Volume fractions are the copper's area share of each cell (8 x 8 point
+    sampling)."""
+    air = material(1.4)
+    nz = 5 * nr
+    d = 6.4e-3 / nr
+    w, k = _blank(2, True, nz, nr)
+    sub = 8
+    off = (np.arange(sub) + 0.5) / sub
+    rs = (np.arange(nr)[:, None] + off[None, :]) * d          # (nr, sub)
+    zs = (np.arange(nz)[:, None] + off[None, :]) * d          # (nz, sub)
+    zt = 0.02
+    below = zs[:, None, :, None] < zt                          # nz, 1, sub, 1
+    inside = (rs[None, :, None, :] ** 2 + (zs[:, None, :, None] - zt) ** 2) < radius * radius
+    frac = (below & ~inside).mean(axis=(2, 3))
+    w[k["phi1"]] = EPS_PHI + (1 - 2 * EPS_PHI) * frac
+    w[k["rho1"]] = 8930.0
+    w[k["rho2"]] = 1.2
+    w[k["p"]] = 1.0e5
+    zc = (np.arange(nz) + 0.5) * d
+    w[k["v"]] = np.where(zc < 0.002, u_drive, 0.0)[:, None]
+    w[k["lam"]] = 0.0
+    p = Patch(nx=nr, ny=nz, dx=d, dy=d, x0=0.0,
+              bc=(BC_REFLECTIVE, BC_TRANSMISSIVE, BC_TRANSMISSIVE, BC_TRANSMISSIVE), prim=w)
+    return Workload(name or f"2d_indentation_rz_{nr}x{nz}", 2, [COPPER_JC, air], [p], 0.6, steps, True,
+                    reactive_material=0, geometry="cyl")
 
 
 def batched_riemann_1d(n_problems: int = 4096, seed: int = 3, steps: int = 300,
