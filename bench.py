@@ -422,7 +422,9 @@ def widened_bench(warmup=3):
     cells, stepped with the geometric source and, for the cost of s_g, the
     same input in planar geometry.  The k sqrt(lam) reaction law: 1024 copies
     of the 4000-cell detonation-into-copper problem (the resolution of the
-    paper's one-dimensional test) in one batch."""
+    paper's one-dimensional test) in one batch.  Johnson-Cook plasticity, the
+    AMR hierarchy and the AMR form of the one-dimensional test follow, each
+    measured on its own (jc_bench, amr_bench, amr_detonation_bench)."""
     import copy
     from paper_2009_14555_gb300 import workloads as W
     from paper_2009_14555_gb300.solver import pack
@@ -445,12 +447,34 @@ def widened_bench(warmup=3):
     for prec, steps in (("fp32_bulk", 200), ("fp64", 30)):
         det[prec] = _timed_steps(wl, prim, prec, steps, warmup)
     out["sqrt_rate_law"] = det
-    for key, fn in (("amr", amr_bench), ("amr_detonation_1d", amr_detonation_bench)):
+    for key, fn in (("johnson_cook", jc_bench), ("amr", amr_bench), ("amr_detonation_1d", amr_detonation_bench)):
         try:
             out[key] = fn()
         except Exception as e:  # the other rows are measured: keep them
             out[key] = {"error": repr(e)}
     return out
+
+
+def jc_bench(nr=512, steps=30, warmup=3):
+    """Johnson-Cook plasticity (float64): the shock-driven hemispherical
+    indentation of Section 4.4 in (r, z), nr x 5 nr cells, and the same input
+    with the copper's plasticity replaced by perfect plasticity at c1 (the
+    cost of the Johnson-Cook relaxation's bisection and temperature)."""
+    from paper_2009_14555_gb300 import workloads as W
+    from paper_2009_14555_gb300.solver import pack
+    wl = W.indentation_rz(nr, steps=0)
+    prim = pack([p.prim for p in wl.patches])
+    row = {"workload": f"2d_indentation_rz_{nr}x{5 * nr} (Johnson-Cook copper, x = r, y = z)", "cells": wl.cells,
+           "precision": "fp64"}
+    row["johnson_cook"] = _timed_steps(wl, prim, "fp64", steps, warmup)
+    perfect = dict(wl.materials[0], plastic=1)
+    wp = W.indentation_rz(nr, steps=0)
+    wp.materials = [perfect, wp.materials[1]]
+    wp.reactive_material = -1
+    prim_p = pack([p.prim[:-1] for p in wp.patches])
+    row["perfect_plasticity"] = _timed_steps(wp, prim_p, "fp64", steps, warmup)
+    row["jc_over_perfect"] = row["johnson_cook"]["ms_per_step"] / row["perfect_plasticity"]["ms_per_step"]
+    return row
 
 
 def amr_detonation_bench(n=1000, levels=3, steps=40, warmup=2):

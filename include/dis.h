@@ -56,7 +56,7 @@ enum {
 enum { DIS_BC_TRANSMISSIVE = 0, DIS_BC_PERIODIC = 1, DIS_BC_REFLECTIVE = 2, DIS_BC_EXTERNAL = 3 };
 enum { DIS_CONSERVATIVE = 0, DIS_PRIMITIVE = 1 };
 enum { DIS_FP64 = 0, DIS_FP32_BULK = 1 };
-enum { DIS_PLASTIC_NONE = 0, DIS_PLASTIC_PERFECT = 1, DIS_PLASTIC_RATE = 2 };
+enum { DIS_PLASTIC_NONE = 0, DIS_PLASTIC_PERFECT = 1, DIS_PLASTIC_RATE = 2, DIS_PLASTIC_JC = 3 };
 
 enum { DIS_RATE_ARRHENIUS = 0, DIS_RATE_SQRT = 1 };
 
@@ -78,8 +78,8 @@ enum { DIS_EOS_STIFFENED = 0, DIS_EOS_ROMENSKII = 1, DIS_EOS_JWL = 2 };
 
 /* One material: Mie-Grueneisen closure (Section 2.3; stiffened gas by
  * default, see above) with shear modulus G, plasticity (Section 2.3.2: none, perfect = the
- * chi0 -> infinity limit of ideal plasticity, or ideal plasticity with rate
- * chi0), and for a reactive material an ideal-gas reactant/product pair of
+ * chi0 -> infinity limit of ideal plasticity, ideal plasticity with rate
+ * chi0, or Johnson-Cook, below), and for a reactive material an ideal-gas reactant/product pair of
  * equal gamma and C_V with heat release Q (Section 2.3.1) and a rate law for
  * the reactant fraction lam (1 = reactant):
  *   DIS_RATE_ARRHENIUS  lam_dot = -A lam exp(-T_act / T)   (zero where T <= 0);
@@ -108,6 +108,18 @@ typedef struct {
    * component densities follow from the temperature equality of Appendix B
    * (a bisection over the reactant's volume share).  Float64 contexts only. */
   double prod_gamma, prod_p_inf, prod_cv;
+  /* DIS_PLASTIC_JC (Section 2.3.2), a Romenskii solid with cv > 0: the
+   * plastic strain rate chi0 exp((sqrt(3/2) |dev sigma| / sigma_Y - 1) / c3)
+   * with sigma_Y = (sigma_y + jc_c2 eps_p^jc_n)(1 - T*^jc_m),
+   * T* = (T - jc_T0) / (jc_Tmelt - jc_T0) clamped to [0, 1], and the
+   * temperature T = jc_T0 (rho/rho0)^Gamma + (p - p_ref) / (rho Gamma cv) of
+   * the Debye form of the thermal energy (Section 2.2), taken at the state
+   * entering the plastic step.  The relaxation objective of Section 3.2,
+   * J - J* + dt chi(J, eps_p + J* - J), is solved by bisection on [0, J*]
+   * (64 halvings) and the material's eps_p grows by J* - J.  The material
+   * carries the context's history row (see dis_create).  Float64 contexts,
+   * not the adjoint. */
+  double jc_c2, jc_c3, jc_n, jc_m, jc_Tmelt, jc_T0;
 } dis_material;
 
 /* One Cartesian patch (the single-grid unit of Section 3): nx x ny cells of
@@ -166,14 +178,23 @@ typedef struct {
 typedef struct dis_ctx dis_ctx;
 
 /* Create a context for `n_patches` patches of dimension `dim` (1 or 2) with
- * two materials, material `reactive_material` (0, 1, or -1 for none) being
- * the reactive one.  `stream` is a cudaStream_t (NULL = legacy default).
- * Copies `patches` and `opt`.  Returns DIS_EINVAL for bad sizes. */
+ * two materials.  Material `reactive_material` (0, 1, or -1 for none)
+ * carries the history row phi_y rho_y alpha_y of Section 2.1 (the last
+ * conservative field, advected with the material): alpha = lam if it is the
+ * reactive material, alpha = eps_p if it is a Johnson-Cook solid
+ * (DIS_PLASTIC_JC); one material carries it, so a context holds either a
+ * reactive material or a Johnson-Cook one.  `stream` is a cudaStream_t (NULL
+ * = legacy default).  Copies `patches` and `opt`.  Returns DIS_EINVAL for
+ * bad sizes. */
 int dis_create(int dim, int n_patches, const dis_patch* patches, int reactive_material,
                const dis_options* opt, void* stream, dis_ctx** out);
 
 /* Set the two materials (n must be 2).  Copies `m`.  May be called again
- * between steps (new parameters take effect from the next step). */
+ * between steps (new parameters take effect from the next step).  Returns
+ * DIS_EINVAL for bad parameters, for a history-row material that is neither
+ * reactive nor Johnson-Cook (or a reactive or Johnson-Cook material that is
+ * not the history-row material), and for a Johnson-Cook material in an
+ * FP32-bulk context. */
 int dis_set_materials(dis_ctx* ctx, const dis_material* m, int n);
 
 /* Bytes of device workspace the context needs (state buffers, primitives,
@@ -364,8 +385,8 @@ int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
  * with the rest of the stage, and J is the same plain sum over cells (no
  * factor r).  Both limiters are reversed.  Returns DIS_EINVAL (bad
  * arguments, a DIS_HANCOCK context: the adjoint covers the Runge-Kutta
- * scheme, a material that is not a stiffened gas, or a reactive material
- * with a product closure of its own), DIS_ESTATE
+ * scheme, a material that is not a stiffened gas, a Johnson-Cook material,
+ * or a reactive material with a product closure of its own), DIS_ESTATE
  * (no state), DIS_ENOMEM, DIS_ECUDA.
  * Synchronises. */
 int dis_adj_forward(dis_ctx* ctx, int n_steps, int checkpoint_every, int objective_material,

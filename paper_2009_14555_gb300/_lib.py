@@ -40,7 +40,9 @@ class DisMaterial(ctypes.Structure):
                 ("T_act", c_double), ("rate_law", c_int32), ("p_ign", c_double), ("eos", c_int32),
                 ("rho0", c_double), ("K0", c_double), ("alpha", c_double), ("beta", c_double),
                 ("jwl_A", c_double), ("jwl_B", c_double), ("jwl_R1", c_double), ("jwl_R2", c_double),
-                ("prod_gamma", c_double), ("prod_p_inf", c_double), ("prod_cv", c_double)]
+                ("prod_gamma", c_double), ("prod_p_inf", c_double), ("prod_cv", c_double),
+                ("jc_c2", c_double), ("jc_c3", c_double), ("jc_n", c_double), ("jc_m", c_double),
+                ("jc_Tmelt", c_double), ("jc_T0", c_double)]
 
 
 class DisPatch(ctypes.Structure):

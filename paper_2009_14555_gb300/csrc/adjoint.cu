@@ -382,6 +382,8 @@ int dis_adj_forward(dis_ctx* c, int n_steps, int checkpoint_every, int objective
     return dis_internal_error(DIS_EINVAL, "dis_adj_forward: the adjoint covers the Runge-Kutta scheme only");
   if (c->phys.m[0].eos != EOS_SG || c->phys.m[1].eos != EOS_SG || c->phys.m[0].two || c->phys.m[1].two)
     return dis_internal_error(DIS_EINVAL, "dis_adj_forward: the adjoint covers stiffened-gas materials only");
+  if (c->phys.m[0].plastic == 3 || c->phys.m[1].plastic == 3)
+    return dis_internal_error(DIS_EINVAL, "dis_adj_forward: the adjoint does not cover Johnson-Cook plasticity");
   if (n_steps <= 0 || checkpoint_every <= 0)
     return dis_internal_error(DIS_EINVAL, "dis_adj_forward: n_steps and checkpoint_every must be positive");
   if (objective_material < -1 || objective_material > 1)

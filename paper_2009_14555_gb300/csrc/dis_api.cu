@@ -861,7 +861,7 @@ MatDev to_dev(const dis_material& m) {
   d.G = m.G;
   d.sigy = m.sigma_y;
   d.chi0 = m.chi0;
-  d.Q = m.Q;
+  d.Q = m.reactive ? m.Q : 0.0;  // the history row of a Johnson-Cook material releases no heat
   d.cv = m.cv;
   d.A = m.A;
   d.Tact = m.T_act;
@@ -888,6 +888,12 @@ MatDev to_dev(const dis_material& m) {
   d.gG = m.gamma * m.G * d.iGm1;
   d.GoG = m.G * d.iGm1;
   d.JY = (m.plastic && m.G > 0) ? m.sigma_y / (std::sqrt(6.0) * m.G) : INFINITY;
+  d.jc2 = m.jc_c2;
+  d.jc3 = m.jc_c3;
+  d.jcn = m.jc_n;
+  d.jcm = m.jc_m;
+  d.jcTm = m.jc_Tmelt;
+  d.jcT0 = m.jc_T0;
   return d;
 }
 
@@ -1044,9 +1050,21 @@ int dis_set_materials(dis_ctx* c, const dis_material* m, int n) {
   for (int l = 0; l < 2; ++l) {
     if (!(m[l].gamma > 1.0)) return fail(DIS_EINVAL, "dis_set_materials: gamma must be > 1");
     if (m[l].G < 0 || m[l].p_inf < 0) return fail(DIS_EINVAL, "dis_set_materials: negative G or p_inf");
-    if (m[l].plastic < 0 || m[l].plastic > 2) return fail(DIS_EINVAL, "dis_set_materials: bad plastic");
-    if ((l == c->y) != (m[l].reactive != 0))
-      return fail(DIS_EINVAL, "dis_set_materials: reactive flag disagrees with the context");
+    if (m[l].plastic < DIS_PLASTIC_NONE || m[l].plastic > DIS_PLASTIC_JC)
+      return fail(DIS_EINVAL, "dis_set_materials: bad plastic");
+    const bool jc = m[l].plastic == DIS_PLASTIC_JC;
+    if (jc && m[l].reactive)
+      return fail(DIS_EINVAL, "dis_set_materials: a material carries one history row (reactive or Johnson-Cook)");
+    if ((l == c->y) != (m[l].reactive != 0 || jc))
+      return fail(DIS_EINVAL, "dis_set_materials: the context's history-row material must be the reactive or "
+                              "Johnson-Cook one");
+    if (jc && !(m[l].eos == DIS_EOS_ROMENSKII && m[l].G > 0 && m[l].cv > 0 && m[l].chi0 > 0 && m[l].jc_c3 > 0 &&
+                m[l].sigma_y >= 0 && m[l].jc_c2 >= 0 && m[l].jc_n > 0 && m[l].jc_m > 0 && m[l].jc_T0 >= 0 &&
+                m[l].jc_Tmelt > m[l].jc_T0 && std::isfinite(m[l].jc_Tmelt)))
+      return fail(DIS_EINVAL, "dis_set_materials: Johnson-Cook needs a Romenskii solid with G, cv, chi0, c3, n, "
+                              "m > 0, sigma_y, c2, T0 >= 0 and finite T_melt > T0");
+    if (jc && c->fp32)
+      return fail(DIS_EINVAL, "dis_set_materials: Johnson-Cook plasticity is built for float64 contexts only");
     if (m[l].eos < DIS_EOS_STIFFENED || m[l].eos > DIS_EOS_JWL)
       return fail(DIS_EINVAL, "dis_set_materials: unknown eos %d", m[l].eos);
     if (m[l].eos == DIS_EOS_ROMENSKII && !(m[l].rho0 > 0 && m[l].K0 > 0 && m[l].alpha > 0 && m[l].beta >= 0))

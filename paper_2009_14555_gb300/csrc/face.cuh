@@ -268,13 +268,41 @@ __device__ __forceinline__ void sources(const PhysT<T>& P, double dt, T* o) {
       Pp = at_state(P, o[L::AL] / (P.y == 0 ? o[L::A1] : o[L::A2]), p0);
     }
   }
+  // a Johnson-Cook material: its temperature at the state entering the step
+  // (Debye form of the thermal energy, Section 2.2: T0 (r/rho0)^Gamma +
+  // (p - p_ref) / (r Gamma C_V) at the mixture pressure) and its plastic strain
+  JcIn<T> jc{T(0.0), T(0.0)};
+  bool is_jc = false;
+  if constexpr (RX) {
+    const MatT<T>& m = P.m[P.y];
+    if (m.plastic == 3) {
+      is_jc = true;
+      const T rr = o[L::A1] + o[L::A2];
+      T my_ = 0.0;
+      if constexpr (DIM == 2) my_ = o[L::MY];
+      const T KE0 = 0.5 * (o[L::MX] * o[L::MX] + my_ * my_) / rr;
+      const StrainT<T> s0 = strain_of(o[L::V11], v12, v21, o[L::V22], o[L::V33]);
+      const T p0 = (o[L::E] - KE0 - ref_energy(P, o[L::PHI], o[L::A1], o[L::A2], o[L::AL], s0.J2)) /
+                   xi_of(P, o[L::PHI]);
+      const T ary = P.y == 0 ? o[L::A1] : o[L::A2];
+      const T ry = P.y == 0 ? o[L::A1] / o[L::PHI] : o[L::A2] / (1.0 - o[L::PHI]);
+      const RefT<T> c = ref_curves(m, ry, s0.J2);
+      jc.temp = m.jcT0 * powr(ry / m.rho0, T(m.gamma - 1.0)) + (p0 - c.p) / (ry * (m.gamma - 1.0) * m.cv);
+      jc.eps = o[L::AL] / ary;
+    }
+  }
+  T deps = 0.0;
   plastic(Pp, o[L::PHI], T(dt), o[L::V11], v12, v21, o[L::V22], o[L::V33], o[L::A1] / o[L::PHI],
-          o[L::A2] / (1.0 - o[L::PHI]));
+          o[L::A2] / (1.0 - o[L::PHI]), is_jc ? &jc : nullptr, &deps);
   if constexpr (DIM == 2) {
     o[L::V12] = v12;
     o[L::V21] = v21;
   }
   if constexpr (RX) {
+    if (is_jc) {  // the history row's source over the step: rho_y phi_y (J* - J*_y)
+      o[L::AL] += (P.y == 0 ? o[L::A1] : o[L::A2]) * deps;
+      return;
+    }
     const int y = P.y;
     const MatT<T>& m = P.m[y];
     const T phi1 = o[L::PHI];

@@ -56,6 +56,8 @@ struct MatT {
   R gG;    // gamma G / (gamma - 1)
   R GoG;   // G / (gamma - 1)
   R JY;    // yield strain invariant sigma_y / (sqrt(6) G)
+  // Johnson-Cook plasticity (plastic == 3; sigy is c1): c2, c3, n, m, T_melt, T0
+  R jc2, jc3, jcn, jcm, jcTm, jcT0;
 };
 
 template <class R>
@@ -86,6 +88,8 @@ inline PhysT<float> to_float(const Phys& P) {
     m.eos = d.eos; m.rho0 = (float)d.rho0; m.K0 = (float)d.K0; m.ar = (float)d.ar; m.br = (float)d.br;
     m.jA = (float)d.jA; m.jB = (float)d.jB; m.jR1 = (float)d.jR1; m.jR2 = (float)d.jR2;
     m.two = d.two; m.pg = (float)d.pg; m.ppi = (float)d.ppi; m.pcv = (float)d.pcv;
+    m.jc2 = (float)d.jc2; m.jc3 = (float)d.jc3; m.jcn = (float)d.jcn; m.jcm = (float)d.jcm;
+    m.jcTm = (float)d.jcTm; m.jcT0 = (float)d.jcT0;
   }
   f.y = P.y;
   f.thinc = P.thinc;
@@ -579,11 +583,49 @@ __device__ __forceinline__ FaceOutT<T> hllc(const FStateT<T>& L, const FStateT<T
   return o;
 }
 
+// Johnson-Cook input of the plastic step: the material's temperature at the
+// state entering the step and its plastic strain eps_p.
+template <class T>
+struct JcIn {
+  T temp, eps;
+};
+
+// Johnson-Cook relaxed strain norm of one material (Section 2.3.2 rate law
+// in the objective of Section 3.2): bisection (64 halvings) of
+// R(J) = J - J* + dt chi0 exp((sqrt(3/2) 2 G J / sigma_Y - 1) / c3) on [0, J*]
+// with sigma_Y = (c1 + c2 max(eps_p + J* - J, 0)^n)(1 - T*^m), T* the
+// homologous temperature clamped to [0, 1]; no strength (sigma_Y <= 0) makes
+// the rate unbounded and the root 0.
+template <class T, class R>
+__device__ __forceinline__ T jc_relax(const MatT<R>& m, T Js, T Gl, T dt, const JcIn<T>& in) {
+  T Ts = (in.temp - m.jcT0) / (m.jcTm - m.jcT0);
+  Ts = fmin(fmax(Ts, T(0.0)), T(1.0));
+  const T soft = 1.0 - powr(Ts, T(m.jcm));
+  const T k = sqrt(T(1.5)) * T(2.0);
+  T lo = 0.0, hi = Js;
+  for (int it = 0; it < 64; ++it) {
+    const T mid = 0.5 * (lo + hi);
+    const T e = fmax(in.eps + (Js - mid), T(0.0));
+    const T sY = (m.sigy + m.jc2 * (m.jcn == 1.0 ? e : powr(e, T(m.jcn)))) * soft;  // e^1 = e exactly
+    bool neg = false;
+    if (sY > 0.0) {
+      const T rate = m.chi0 * exp((k * Gl * mid / sY - 1.0) / m.jc3);
+      neg = mid - Js + dt * rate < 0.0;
+    }
+    if (neg) lo = mid;
+    else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
 // Plastic update of Section 3.2 on one cell's stretch tensor (in place).  r1,
 // r2: phasic densities (the Romenskii yield strain sigma_y / (sqrt 6 G(r))).
+// A Johnson-Cook material reads jc (its temperature and plastic strain) and
+// returns the growth J* - J*_l of its plastic strain in *deps.
 template <class T>
 __device__ __forceinline__ void plastic(const PhysT<T>& P, T phi1, T dt, T& V11,
-                                        T& V12, T& V21, T& V22, T& V33, T r1, T r2) {
+                                        T& V12, T& V21, T& V22, T& V33, T r1, T r2,
+                                        const JcIn<T>* jc = nullptr, T* deps = nullptr) {
   const StrainT<T> s = strain_of(V11, V12, V21, V22, V33);
   const T Js = sqrt(s.J2);
   T num = 0.0, den = 0.0;
@@ -599,6 +641,9 @@ __device__ __forceinline__ void plastic(const PhysT<T>& P, T phi1, T dt, T& V11,
       Jl = fmin(Js, JY);
     } else if (m.plastic == 2) {
       Jl = Js > JY ? fmax(Js - dt * m.chi0, JY) : Js;
+    } else if (m.plastic == 3 && jc) {
+      Jl = jc_relax(m, Js, shear_of(m, l == 0 ? r1 : r2), dt, *jc);
+      if (deps) *deps = Js - Jl;
     } else {
       Jl = Js;
     }

@@ -24,7 +24,9 @@ def _material(m: dict) -> L.DisMaterial:
                          float(m.get("beta_r", 0.0)), float(m.get("jwl_A", 0.0)), float(m.get("jwl_B", 0.0)),
                          float(m.get("jwl_R1", 0.0)), float(m.get("jwl_R2", 0.0)),
                          float(m.get("prod_gamma", 0.0)), float(m.get("prod_p_inf", 0.0)),
-                         float(m.get("prod_cv", 0.0)))
+                         float(m.get("prod_cv", 0.0)), float(m.get("jc_c2", 0.0)), float(m.get("jc_c3", 0.0)),
+                         float(m.get("jc_n", 0.0)), float(m.get("jc_m", 0.0)), float(m.get("jc_Tmelt", 0.0)),
+                         float(m.get("jc_T0", 0.0)))
 
 
 def _patch(p, dim) -> L.DisPatch:

@@ -136,6 +136,43 @@ def test_rate_law_validation(lib):
     lib.dis_destroy(ctx)
 
 
+def test_johnson_cook_validation(lib):
+    """Johnson-Cook plasticity: the history-row material must be the
+    Johnson-Cook one, a Romenskii solid with positive rates and exponents and
+    T_melt > T0; not reactive; float64 contexts only."""
+    from paper_2009_14555_gb300 import workloads as W
+    from paper_2009_14555_gb300.solver import _material
+    air = _material(W.material(1.4))
+    cu = W.COPPER_JC
+
+    def ctx_of(row, precision=0):
+        out = ctypes.c_void_p()
+        opts = L.DisOptions(0.6, 0, precision)
+        arr = (L.DisPatch * 1)(_patch(64))
+        assert lib.dis_create(1, 1, arr, row, ctypes.byref(opts), None, ctypes.byref(out)) == L.DIS_OK
+        return out
+
+    ctx = ctx_of(0)
+    assert lib.dis_set_materials(ctx, (L.DisMaterial * 2)(_material(cu), air), 2) == L.DIS_OK
+    for key, val in (("jc_c3", 0.0), ("jc_n", 0.0), ("jc_m", -1.0), ("chi0", 0.0), ("cv", 0.0),
+                     ("jc_Tmelt", 298.0), ("jc_Tmelt", float("inf")), ("jc_c2", -1.0), ("sigma_y", -1.0)):
+        assert lib.dis_set_materials(ctx, (L.DisMaterial * 2)(_material(dict(cu, **{key: val})), air), 2) \
+            == L.DIS_EINVAL, key
+    sg = W.material(3.0, p_inf=4.55e10, G=39.4e9)
+    sg.update({k: v for k, v in cu.items() if k.startswith("jc_") or k in ("plastic", "sigma_y", "chi0", "cv")})
+    assert lib.dis_set_materials(ctx, (L.DisMaterial * 2)(_material(sg), air), 2) == L.DIS_EINVAL
+    rx = dict(cu, reactive=1, Q=1e6, cv=385.0)
+    assert lib.dis_set_materials(ctx, (L.DisMaterial * 2)(_material(rx), air), 2) == L.DIS_EINVAL
+    lib.dis_destroy(ctx)
+    for row in (-1, 1):  # the Johnson-Cook material does not carry the row
+        ctx = ctx_of(row)
+        assert lib.dis_set_materials(ctx, (L.DisMaterial * 2)(_material(cu), air), 2) == L.DIS_EINVAL
+        lib.dis_destroy(ctx)
+    ctx = ctx_of(0, precision=L.DIS_FP32_BULK)
+    assert lib.dis_set_materials(ctx, (L.DisMaterial * 2)(_material(cu), air), 2) == L.DIS_EINVAL
+    lib.dis_destroy(ctx)
+
+
 def test_amr_create_validates_arguments(lib):
     """dis_amr_create: float64 SSP-RK3 planar only, levels 1..4, block >= 4
     dividing the domain, known boundary kinds (no device work here)."""
