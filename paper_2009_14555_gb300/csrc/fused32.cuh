@@ -25,15 +25,84 @@
 
 namespace dis {
 
-// shared-memory face slots (per face): nf fluxes (phi slot = F_phi, E slot =
-// soft energy flux), u_face, V row (1 or 2), phi_K, D
-template <int DIM, bool RX>
-struct FSlots {
+// Shared-memory records.  A tile keeps its primitives and its face data as
+// records of consecutive floats, read and written as float4 (and float2 or
+// float4 tails), so a cell or a face costs a few 128-bit shared-memory
+// accesses instead of one access per field:
+//   * a cell: PR = 12 floats, the primitives in the slots of the conservative
+//     layout (PHI phi1, A1 rho1, A2 rho2, MX u, MY v, E p, V, AL lam), plus a
+//     separate plane of phi1 for the THINC stencils;
+//   * a face normal to DIR: Rec<DIM, RX, DIR> below, FA = 12 floats plus (2D)
+//     FB = 4 floats held apart.
+// A stride of 12 floats (48 B) maps the 8 lanes of a quarter warp onto
+// distinct banks, so the float4 accesses of consecutive cells or faces are
+// free of bank conflicts.
+constexpr int PR = 12;
+constexpr int FA = 12;
+
+template <int DIM>
+constexpr int face_fb() {
+  return DIM == 2 ? 4 : 0;
+}
+
+// Face record along DIR: the fluxes of the fields that have one (the V row
+// fluxes V_ij u_d - V_dj u_i vanish for i = d: V11 and V12 on x faces, V21
+// and V22 on y faces), then u_face, the V row of the face (VA, and VB in 2D),
+// phi_K and D.  The phi slot holds F_phi = phi_K u_face, the E slot the soft
+// energy flux.
+template <int DIM, bool RX, int DIR>
+struct Rec {
   using L = Lay<DIM, RX>;
-  static constexpr int NF = L::NF;
-  static constexpr int UF = NF, VA = NF + 1, VB = DIM == 2 ? NF + 2 : NF + 1;
-  static constexpr int PK = VB + 1, DD = VB + 2, N = VB + 3;
+  static constexpr bool zero(int c) {
+    return DIR == 0 ? (c == L::V11 || (DIM == 2 && c == L::V12)) : (c == L::V21 || c == L::V22);
+  }
+  static constexpr int pos(int c) {
+    int p = 0;
+    for (int k = 0; k < c; ++k) p += zero(k) ? 0 : 1;
+    return p;
+  }
+  static constexpr int NFL = L::NF - (DIM == 2 ? 2 : 1);
+  static constexpr int UF = NFL, VA = NFL + 1, VB = DIM == 2 ? NFL + 2 : -1;
+  static constexpr int PK = DIM == 2 ? NFL + 3 : NFL + 2, DD = PK + 1, N = DD + 1;
+  static_assert(N <= FA + face_fb<DIM>(), "face record size");
 };
+
+// Offsets (in floats) of a tile's shared-memory regions: cell records, the
+// phi1 plane (padded to a multiple of 4), face records A, face records B.
+template <int DIM, bool RX, int TX, int TY>
+struct TileLay {
+  static constexpr int HX = TX + 2 * NG, HY = DIM == 2 ? TY + 2 * NG : 1, PLANE = HX * HY;
+  static constexpr int NFX = (TX + 1) * TY, NFY = DIM == 2 ? TX * (TY + 1) : 0, NFA = NFX + NFY;
+  static constexpr int PHI = PR * PLANE;
+  static constexpr int FAO = PHI + ((PLANE + 3) / 4) * 4;
+  static constexpr int FBO = FAO + FA * NFA;
+  static constexpr int END = FBO + face_fb<DIM>() * NFA;
+};
+
+// Face record r (N values of Rec) of face f into / out of shared memory.
+template <int DIM>
+__device__ __forceinline__ void store_face(float* __restrict__ Fa, float* __restrict__ Fb, int f, const float* r) {
+  float4* a = reinterpret_cast<float4*>(Fa + FA * f);
+  a[0] = make_float4(r[0], r[1], r[2], r[3]);
+  a[1] = make_float4(r[4], r[5], r[6], r[7]);
+  a[2] = make_float4(r[8], r[9], r[10], r[11]);
+  if constexpr (DIM == 2)
+    reinterpret_cast<float4*>(Fb)[f] = make_float4(r[12], r[13], r[14], r[15]);
+}
+template <int DIM>
+__device__ __forceinline__ void load_face(const float* __restrict__ Fa, const float* __restrict__ Fb, int f,
+                                          float* r) {
+  const float4* a = reinterpret_cast<const float4*>(Fa + FA * f);
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    const float4 x = a[v];
+    r[4 * v] = x.x; r[4 * v + 1] = x.y; r[4 * v + 2] = x.z; r[4 * v + 3] = x.w;
+  }
+  if constexpr (DIM == 2) {
+    const float4 x = reinterpret_cast<const float4*>(Fb)[f];
+    r[12] = x.x; r[13] = x.y; r[14] = x.z; r[15] = x.w;
+  }
+}
 
 // THINC steepness of the cell at SMEM index k (phi plane Wphi; sx along the
 // sweep, sy across it): Youngs normal from the 3 x 3 neighbourhood in 2D
@@ -54,82 +123,113 @@ __device__ __forceinline__ float thinc_beta_f(const PhysF& P, const float* __res
   return beta;
 }
 
-// The face slots (FSlots) of a face output o on a face normal to DIR, through
-// put(slot, value).
+// The face record (Rec) of a face output o on a face normal to DIR, through
+// put(position, value).
 template <int DIM, bool RX, int DIR, class Put>
 __device__ __forceinline__ void face_slots_f(const FaceOutF& o, const Put& put) {
   using L = Lay<DIM, RX>;
-  using S = FSlots<DIM, RX>;
+  using R = Rec<DIM, RX, DIR>;
   const float fu = DIR == 0 ? o.un : o.ut;
   const float fv = DIR == 0 ? o.ut : o.un;
-  put(L::PHI, o.phi * o.un);
-  put(L::A1, o.Far1);
-  put(L::A2, o.Far2);
-  put(L::MX, DIR == 0 ? o.Fmn : o.Fmt);
-  if constexpr (DIM == 2) put(L::MY, DIR == 0 ? o.Fmt : o.Fmn);
-  put(L::E, o.FE);
-  if constexpr (RX) put(L::AL, o.Farl);
-  put(S::UF, o.un);
-  put(S::PK, o.phi);
-  put(S::DD, o.D);
+  put(R::pos(L::PHI), o.phi * o.un);
+  put(R::pos(L::A1), o.Far1);
+  put(R::pos(L::A2), o.Far2);
+  put(R::pos(L::MX), DIR == 0 ? o.Fmn : o.Fmt);
+  if constexpr (DIM == 2) put(R::pos(L::MY), DIR == 0 ? o.Fmt : o.Fmn);
+  put(R::pos(L::E), o.FE);
+  if constexpr (RX) put(R::pos(L::AL), o.Farl);
+  put(R::UF, o.un);
+  put(R::PK, o.phi);
+  put(R::DD, o.D);
   if constexpr (DIR == 0) {
-    put(L::V11, 0.f);
     if constexpr (DIM == 2) {
-      put(L::V12, 0.f);
-      put(L::V21, o.V21 * fu - o.V11 * fv);
-      put(L::V22, o.V22 * fu - o.V12 * fv);
-      put(S::VA, o.V11);
-      put(S::VB, o.V12);
+      put(R::pos(L::V21), o.V21 * fu - o.V11 * fv);
+      put(R::pos(L::V22), o.V22 * fu - o.V12 * fv);
+      put(R::VA, o.V11);
+      put(R::VB, o.V12);
     } else {
-      put(L::V22, o.V22 * fu);
-      put(S::VA, o.V11);
+      put(R::pos(L::V22), o.V22 * fu);
+      put(R::VA, o.V11);
     }
-    put(L::V33, o.V33 * fu);
+    put(R::pos(L::V33), o.V33 * fu);
   } else if constexpr (DIM == 2) {
-    put(L::V11, o.V11 * fv - o.V21 * fu);
-    put(L::V12, o.V12 * fv - o.V22 * fu);
-    put(L::V21, 0.f);
-    put(L::V22, 0.f);
-    put(L::V33, o.V33 * fv);
-    put(S::VA, o.V21);
-    put(S::VB, o.V22);
+    put(R::pos(L::V11), o.V11 * fv - o.V21 * fu);
+    put(R::pos(L::V12), o.V12 * fv - o.V22 * fu);
+    put(R::pos(L::V33), o.V33 * fv);
+    put(R::VA, o.V21);
+    put(R::VB, o.V22);
   }
 }
 
-// Primitives of the SMEM cell k (planes of `plane` floats, slots as the
+// Face record of o into face f of (Fa, Fb).
+template <int DIM, bool RX, int DIR>
+__device__ __forceinline__ void put_face(const FaceOutF& o, float* __restrict__ Fa, float* __restrict__ Fb,
+                                         int f) {
+  float r[FA + 4];
+#pragma unroll
+  for (int k = 0; k < FA + 4; ++k) r[k] = 0.f;
+  face_slots_f<DIM, RX, DIR>(o, [&](int k, float v) { r[k] = v; });
+  store_face<DIM>(Fa, Fb, f, r);
+}
+
+// Primitives of the SMEM cell k (its record of PR floats, slots as the
 // conservative layout: PHI phi1, A1 rho1, A2 rho2, MX u, MY v, E p, V, AL lam).
 template <int DIM, bool RX>
-__device__ __forceinline__ void load_prim_sm(const float* __restrict__ Wsm, int plane, int k, PrimF& w) {
+__device__ __forceinline__ void load_prim_sm(const float* __restrict__ Wsm, int k, PrimF& w) {
   using L = Lay<DIM, RX>;
-  auto Wv = [&](int f) { return Wsm[f * plane + k]; };
-  w.phi = Wv(L::PHI); w.r1 = Wv(L::A1); w.r2 = Wv(L::A2); w.u = Wv(L::MX);
-  w.p = Wv(L::E); w.V11 = Wv(L::V11); w.V22 = Wv(L::V22); w.V33 = Wv(L::V33);
+  constexpr int NV = (L::NF + 3) / 4;
+  float r[PR];
+  const float4* a = reinterpret_cast<const float4*>(Wsm + PR * k);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const float4 x = a[v];
+    r[4 * v] = x.x; r[4 * v + 1] = x.y; r[4 * v + 2] = x.z; r[4 * v + 3] = x.w;
+  }
+  w.phi = r[L::PHI]; w.r1 = r[L::A1]; w.r2 = r[L::A2]; w.u = r[L::MX];
+  w.p = r[L::E]; w.V11 = r[L::V11]; w.V22 = r[L::V22]; w.V33 = r[L::V33];
   w.v = 0.f; w.V12 = 0.f; w.V21 = 0.f; w.lam = 0.f;
-  if constexpr (DIM == 2) { w.v = Wv(L::MY); w.V12 = Wv(L::V12); w.V21 = Wv(L::V21); }
-  if constexpr (RX) w.lam = Wv(L::AL);
+  if constexpr (DIM == 2) { w.v = r[L::MY]; w.V12 = r[L::V12]; w.V21 = r[L::V21]; }
+  if constexpr (RX) w.lam = r[L::AL];
+}
+
+// The record of SMEM cell c and its entry in the phi1 plane (plane cells).
+template <int DIM, bool RX>
+__device__ __forceinline__ void store_prim_sm(float* __restrict__ Wsm, int plane, int c, const PrimF& w) {
+  using L = Lay<DIM, RX>;
+  constexpr int NV = (L::NF + 3) / 4;
+  float r[PR];
+#pragma unroll
+  for (int k = 0; k < PR; ++k) r[k] = 0.f;
+  r[L::PHI] = w.phi; r[L::A1] = w.r1; r[L::A2] = w.r2; r[L::MX] = w.u;
+  r[L::E] = w.p; r[L::V11] = w.V11; r[L::V22] = w.V22; r[L::V33] = w.V33;
+  if constexpr (DIM == 2) { r[L::MY] = w.v; r[L::V12] = w.V12; r[L::V21] = w.V21; }
+  if constexpr (RX) r[L::AL] = w.lam;
+  float4* a = reinterpret_cast<float4*>(Wsm + PR * c);
+#pragma unroll
+  for (int v = 0; v < NV; ++v) a[v] = make_float4(r[4 * v], r[4 * v + 1], r[4 * v + 2], r[4 * v + 3]);
+  Wsm[PR * plane + c] = w.phi;
 }
 
 template <int DIM, bool RX, int DIR, int LIM, bool GEN>
 __device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__ Wsm, int HX, int HY, int hx,
-                                       int hy, float dxn, float dxt, float* __restrict__ Fsm, int nfaces,
-                                       int fidx) {
+                                       int hy, float dxn, float dxt, float* __restrict__ Fa,
+                                       float* __restrict__ Fb, int fidx) {
   // hx, hy: SMEM coordinates of the face's left (DIR 0) or lower (DIR 1) cell
-  using L = Lay<DIM, RX>;
   const int plane = HX * HY;
   const int sx = DIR == 0 ? 1 : HX;  // along the sweep
   const int sy = DIR == 0 ? HX : 1;  // across it
   const int k0 = hy * HX + hx;       // cell a
-  auto Wv = [&](int f, int k) { return Wsm[f * plane + k]; };
+  const float* Wphi = Wsm + PR * plane;
   float ph[6];
 #pragma unroll
-  for (int s = 0; s < 6; ++s) ph[s] = Wv(L::PHI, k0 + (s - 2) * sx);
+  for (int s = 0; s < 6; ++s) ph[s] = Wphi[k0 + (s - 2) * sx];
   float phiL, phiR;
   {
     CandF c[4];
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
       auto beta_of = [&]() -> float {
-        return thinc_beta_f<DIM>(P, Wsm + L::PHI * plane, k0 + (s - 1) * sx, sx, sy, dxn, dxt);
+        return thinc_beta_f<DIM>(P, Wphi, k0 + (s - 1) * sx, sx, sy, dxn, dxt);
       };
       c[s] = phi_cand_f<LIM>(ph[s], ph[s + 1], ph[s + 2], beta_of, P.thinc != 0, P.limiter);
     }
@@ -140,10 +240,10 @@ __device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__
     phiR = Lt;
   }
   PrimF w0, w1, w2, w3;
-  load_prim_sm<DIM, RX>(Wsm, plane, k0 - sx, w0);
-  load_prim_sm<DIM, RX>(Wsm, plane, k0, w1);
-  load_prim_sm<DIM, RX>(Wsm, plane, k0 + sx, w2);
-  load_prim_sm<DIM, RX>(Wsm, plane, k0 + 2 * sx, w3);
+  load_prim_sm<DIM, RX>(Wsm, k0 - sx, w0);
+  load_prim_sm<DIM, RX>(Wsm, k0, w1);
+  load_prim_sm<DIM, RX>(Wsm, k0 + sx, w2);
+  load_prim_sm<DIM, RX>(Wsm, k0 + 2 * sx, w3);
   PrimF wl, wr;
 #define DIS_RECF(fld)                                            \
   {                                                              \
@@ -166,16 +266,13 @@ __device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__
   sl.cL = sqrtf(sl.cL);
   sr.cL = sqrtf(sr.cL);
   const FaceOutF o = hlld_f<DIR>(sl, sr);
-  face_slots_f<DIM, RX, DIR>(o, [&](int slot, float v) { Fsm[slot * nfaces + fidx] = v; });
+  put_face<DIM, RX, DIR>(o, Fa, Fb, fidx);
 }
 
 // Shared memory bytes of a tile.
 template <int DIM, bool RX, int TX, int TY>
 constexpr size_t fused32_smem() {
-  using S = FSlots<DIM, RX>;
-  constexpr int HX = TX + 2 * NG, HY = DIM == 2 ? TY + 2 * NG : 1;
-  constexpr int NFX = (TX + 1) * TY, NFY = DIM == 2 ? TX * (TY + 1) : 0;
-  return sizeof(float) * ((size_t)Lay<DIM, RX>::NF * HX * HY + (size_t)S::N * (NFX + NFY));
+  return sizeof(float) * (size_t)TileLay<DIM, RX, TX, TY>::END;
 }
 
 // Positive float -> bits that order like the value (for integer atomic max).
@@ -223,18 +320,7 @@ __device__ __forceinline__ void fill_tile(const Phys& P, const PhysF& F, const S
     PrimF w = cons_to_prim32<DIM, RX, GEN>(P, F, A.src, T, cidx(pd, si, sj));
     if (fx) { w.u = -w.u; w.V12 = -w.V12; w.V21 = -w.V21; }
     if (fy) { w.v = -w.v; w.V12 = -w.V12; w.V21 = -w.V21; }
-    const int plane = HX * HY;
-    Wsm[L::PHI * plane + c] = w.phi;
-    Wsm[L::A1 * plane + c] = w.r1;
-    Wsm[L::A2 * plane + c] = w.r2;
-    Wsm[L::MX * plane + c] = w.u;
-    if constexpr (DIM == 2) Wsm[L::MY * plane + c] = w.v;
-    Wsm[L::E * plane + c] = w.p;
-    Wsm[L::V11 * plane + c] = w.V11;
-    if constexpr (DIM == 2) { Wsm[L::V12 * plane + c] = w.V12; Wsm[L::V21 * plane + c] = w.V21; }
-    Wsm[L::V22 * plane + c] = w.V22;
-    Wsm[L::V33 * plane + c] = w.V33;
-    if constexpr (RX) Wsm[L::AL * plane + c] = w.lam;
+    store_prim_sm<DIM, RX>(Wsm, HX * HY, c, w);
   }
 }
 
@@ -243,12 +329,11 @@ __device__ __forceinline__ void fill_tile(const Phys& P, const PhysF& F, const S
 template <int DIM, bool RX, int TX, int TY, int NT, int LIM, bool GEN>
 __device__ __forceinline__ void faces_tile(const PhysF& F, const StepArgs32& A, const int4 t,
                                            float* __restrict__ sm) {
-  using S = FSlots<DIM, RX>;
-  constexpr int HX = TX + 2 * NG, HY = DIM == 2 ? TY + 2 * NG : 1;
-  constexpr int NFX = (TX + 1) * TY, NFY = DIM == 2 ? TX * (TY + 1) : 0;
+  using TL = TileLay<DIM, RX, TX, TY>;
+  constexpr int HX = TL::HX, HY = TL::HY, NFX = TL::NFX, NFY = TL::NFY;
   const float* Wsm = sm;
-  float* Fxs = sm + Lay<DIM, RX>::NF * HX * HY;
-  float* Fys = Fxs + S::N * NFX;
+  float* Fa = sm + TL::FAO;
+  float* Fb = sm + TL::FBO;
   const PatchDev pd = A.pd[t.x];
   const int i0 = t.y, j0 = t.z;
   const float dxf = (float)pd.dx, dyf = (float)pd.dy;
@@ -257,13 +342,13 @@ __device__ __forceinline__ void faces_tile(const PhysF& F, const StepArgs32& A, 
       const int fx = f % (TX + 1), fy = f / (TX + 1);
       const int i = i0 + fx, j = j0 + fy;  // face between cells i-1 and i
       if (i > pd.nx || (DIM == 2 && j >= pd.ny)) continue;
-      face32<DIM, RX, 0, LIM, GEN>(F, Wsm, HX, HY, fx + NG - 1, DIM == 2 ? fy + NG : 0, dxf, dyf, Fxs, NFX, f);
+      face32<DIM, RX, 0, LIM, GEN>(F, Wsm, HX, HY, fx + NG - 1, DIM == 2 ? fy + NG : 0, dxf, dyf, Fa, Fb, f);
     } else if constexpr (DIM == 2) {
       const int g = f - NFX;
       const int fx = g % TX, fy = g / TX;
       const int i = i0 + fx, j = j0 + fy;  // face between rows j-1 and j
       if (i >= pd.nx || j > pd.ny) continue;
-      face32<DIM, RX, 1, LIM, GEN>(F, Wsm, HX, HY, fx + NG, fy + NG - 1, dyf, dxf, Fys, NFY, g);
+      face32<DIM, RX, 1, LIM, GEN>(F, Wsm, HX, HY, fx + NG, fy + NG - 1, dyf, dxf, Fa, Fb, f);
     }
   }
 }
@@ -279,13 +364,12 @@ __device__ __forceinline__ void update_tile(const Phys& P, const PhysF& F, const
                                             unsigned* rate_cta) {
   static_assert(TX * TY <= NT, "one thread per tile cell in the update phase");
   using L = Lay<DIM, RX>;
-  using S = FSlots<DIM, RX>;
+  using TL = TileLay<DIM, RX, TX, TY>;
   constexpr int NF = L::NF;
-  constexpr int HX = TX + 2 * NG, HY = DIM == 2 ? TY + 2 * NG : 1;
-  constexpr int NFX = (TX + 1) * TY, NFY = DIM == 2 ? TX * (TY + 1) : 0;
+  constexpr int HX = TL::HX, NFX = TL::NFX;
   const float* Wsm = sm;
-  const float* Fxs = Wsm + NF * HX * HY;
-  const float* Fys = Fxs + S::N * NFX;
+  const float* Fa = sm + TL::FAO;
+  const float* Fb = sm + TL::FBO;
   const PatchDev pd = A.pd[t.x];
   const int i0 = t.y, j0 = t.z;
   const int tid = threadIdx.x;
@@ -307,32 +391,41 @@ __device__ __forceinline__ void update_tile(const Phys& P, const PhysF& F, const
     load32<DIM, RX>(A.src, T, k, q);
     const float idx_ = ihx_sh;
     const int fl = ly * (TX + 1) + lx, fr = fl + 1;
-    auto FX = [&](int s, int f) { return Fxs[s * NFX + f]; };
+    using RXf = Rec<DIM, RX, 0>;
+    float xl[FA + 4], xr[FA + 4];
+    load_face<DIM>(Fa, Fb, fl, xl);
+    load_face<DIM>(Fa, Fb, fr, xr);
+    auto FX = [&](int s, bool right) { return right ? xr[s] : xl[s]; };
 #pragma unroll
-    for (int c = 0; c < NF; ++c) D[c] = (FX(c, fr) - FX(c, fl)) * idx_;
-    float divu = (FX(S::UF, fr) - FX(S::UF, fl)) * idx_;
-    float bx = (FX(S::VA, fr) - FX(S::VA, fl)) * idx_;
+    for (int c = 0; c < NF; ++c)
+      D[c] = RXf::zero(c) ? 0.f : (FX(RXf::pos(c), true) - FX(RXf::pos(c), false)) * idx_;
+    float divu = (FX(RXf::UF, true) - FX(RXf::UF, false)) * idx_;
+    float bx = (FX(RXf::VA, true) - FX(RXf::VA, false)) * idx_;
     float by = 0.f;
     const float k2f = F.m[1].kap, dkf = F.m[0].kap - F.m[1].kap;
     // phi1 flux divergence from the exact differences of the float fluxes
-    ff Dc = ff_mul_f(two_sum(FX(L::PHI, fr), -FX(L::PHI, fl)), idx_);
+    ff Dc = ff_mul_f(two_sum(xr[RXf::pos(L::PHI)], -xl[RXf::pos(L::PHI)]), idx_);
     // soft part of the e_s divergence: differences first, then the large factors
-    float small = ((FX(L::E, fr) - FX(L::E, fl)) +
-                   k2f * ((FX(S::UF, fr) - FX(S::UF, fl)) + (FX(S::DD, fr) - FX(S::DD, fl))) +
-                   dkf * (FX(S::PK, fr) * FX(S::DD, fr) - FX(S::PK, fl) * FX(S::DD, fl))) * idx_;
+    float small = ((xr[RXf::pos(L::E)] - xl[RXf::pos(L::E)]) +
+                   k2f * ((xr[RXf::UF] - xl[RXf::UF]) + (xr[RXf::DD] - xl[RXf::DD])) +
+                   dkf * (xr[RXf::PK] * xr[RXf::DD] - xl[RXf::PK] * xl[RXf::DD])) * idx_;
     if constexpr (DIM == 2) {
+      using RYf = Rec<DIM, RX, 1>;
       const float idy = ihy_sh;
-      const int fb = ly * TX + lx, ft = fb + TX;
-      auto FY = [&](int s_, int f) { return Fys[s_ * NFY + f]; };
+      const int fb = NFX + ly * TX + lx, ft = fb + TX;
+      float yb[FA + 4], yt[FA + 4];
+      load_face<DIM>(Fa, Fb, fb, yb);
+      load_face<DIM>(Fa, Fb, ft, yt);
 #pragma unroll
-      for (int c = 0; c < NF; ++c) D[c] += (FY(c, ft) - FY(c, fb)) * idy;
-      divu += (FY(S::UF, ft) - FY(S::UF, fb)) * idy;
-      bx += (FY(S::VA, ft) - FY(S::VA, fb)) * idy;
-      by = (FX(S::VB, fr) - FX(S::VB, fl)) * idx_ + (FY(S::VB, ft) - FY(S::VB, fb)) * idy;
-      Dc = ff_add(Dc, ff_mul_f(two_sum(FY(L::PHI, ft), -FY(L::PHI, fb)), idy));
-      small += ((FY(L::E, ft) - FY(L::E, fb)) +
-                k2f * ((FY(S::UF, ft) - FY(S::UF, fb)) + (FY(S::DD, ft) - FY(S::DD, fb))) +
-                dkf * (FY(S::PK, ft) * FY(S::DD, ft) - FY(S::PK, fb) * FY(S::DD, fb))) * idy;
+      for (int c = 0; c < NF; ++c)
+        if (!RYf::zero(c)) D[c] += (yt[RYf::pos(c)] - yb[RYf::pos(c)]) * idy;
+      divu += (yt[RYf::UF] - yb[RYf::UF]) * idy;
+      bx += (yt[RYf::VA] - yb[RYf::VA]) * idy;
+      by = (xr[RXf::VB] - xl[RXf::VB]) * idx_ + (yt[RYf::VB] - yb[RYf::VB]) * idy;
+      Dc = ff_add(Dc, ff_mul_f(two_sum(yt[RYf::pos(L::PHI)], -yb[RYf::pos(L::PHI)]), idy));
+      small += ((yt[RYf::pos(L::E)] - yb[RYf::pos(L::E)]) +
+                k2f * ((yt[RYf::UF] - yb[RYf::UF]) + (yt[RYf::DD] - yb[RYf::DD])) +
+                dkf * (yt[RYf::PK] * yt[RYf::DD] - yb[RYf::PK] * yb[RYf::DD])) * idy;
     }
     const ff phi_c = {q[L::PHI], q[NF]};
     const ff Dphi = ff_add(Dc, ff_neg(ff_mul_f(phi_c, divu)));
@@ -344,18 +437,12 @@ __device__ __forceinline__ void update_tile(const Phys& P, const PhysF& F, const
     if constexpr (CYL) {
       // cylindrical geometric source (x = r, y = z) from the cell's primitives
       // in shared memory; energy: rho E u_r with rho E = e_s + kappa(phi1)
-      const int plane = HX * HY, kc = (ly + (DIM == 2 ? NG : 0)) * HX + lx + NG;
-      const float wp = Wsm[L::E * plane + kc], wphi = Wsm[L::PHI * plane + kc];
-      const float wu = Wsm[L::MX * plane + kc];
-      float wv = 0.f, v12 = 0.f, v21 = 0.f;
-      if constexpr (DIM == 2) {
-        wv = Wsm[L::MY * plane + kc];
-        v12 = Wsm[L::V12 * plane + kc];
-        v21 = Wsm[L::V21 * plane + kc];
-      }
-      const StrainF st = strain_f(Wsm[L::V11 * plane + kc], v12, v21, Wsm[L::V22 * plane + kc],
-                                  Wsm[L::V33 * plane + kc]);
-      const float Gm2 = 2.f * Gmix_f<GEN>(F, wphi, Wsm[L::A1 * plane + kc], Wsm[L::A2 * plane + kc]);
+      const int kc = (ly + (DIM == 2 ? NG : 0)) * HX + lx + NG;
+      PrimF wc;
+      load_prim_sm<DIM, RX>(Wsm, kc, wc);
+      const float wp = wc.p, wphi = wc.phi, wu = wc.u, wv = wc.v;
+      const StrainF st = strain_f(wc.V11, wc.V12, wc.V21, wc.V22, wc.V33);
+      const float Gm2 = 2.f * Gmix_f<GEN>(F, wphi, wc.r1, wc.r2);
       const float srr = -wp + Gm2 * st.H11, szr = Gm2 * st.H12, stt = -wp + Gm2 * st.H33;
       const float r = (float)pd.x0 + ((float)i + 0.5f) * dxf;
       const float ir = 1.f / r;

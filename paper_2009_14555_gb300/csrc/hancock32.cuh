@@ -30,12 +30,12 @@
 
 namespace dis {
 
-// Shared memory: the stage kernel's primitives and face slots, then the
+// Shared memory: the stage kernel's primitives and face records, then the
 // evolved edge states of both sides of every face (2 NF values per face).
 template <int DIM, bool RX, int TX, int TY>
 constexpr size_t hancock32_smem() {
-  constexpr int NFX = (TX + 1) * TY, NFY = DIM == 2 ? TX * (TY + 1) : 0;
-  return fused32_smem<DIM, RX, TX, TY>() + sizeof(float) * (size_t)2 * Lay<DIM, RX>::NF * (NFX + NFY);
+  using TL = TileLay<DIM, RX, TX, TY>;
+  return sizeof(float) * ((size_t)TL::END + (size_t)2 * Lay<DIM, RX>::NF * TL::NFA);
 }
 
 // Physical flux of one state as a face output (no star region: D = 0).
@@ -114,7 +114,7 @@ __device__ __forceinline__ void cell_edges_f(const PhysF& P, const float* __rest
                                              PrimF& hi) {
   using L = Lay<DIM, RX>;
   const int sx = DIR == 0 ? 1 : HX, sy = DIR == 0 ? HX : 1;
-  const float* Wphi = Wsm + L::PHI * plane;
+  const float* Wphi = Wsm + PR * plane;
   float ph[5];
 #pragma unroll
   for (int s = 0; s < 5; ++s) ph[s] = Wphi[kc + (s - 2) * sx];
@@ -126,8 +126,8 @@ __device__ __forceinline__ void cell_edges_f(const PhysF& P, const float* __rest
   }
   bvd_f(c[0], c[1], c[2], lo.phi, hi.phi);
   PrimF wm, wp;
-  load_prim_sm<DIM, RX>(Wsm, plane, kc - sx, wm);
-  load_prim_sm<DIM, RX>(Wsm, plane, kc + sx, wp);
+  load_prim_sm<DIM, RX>(Wsm, kc - sx, wm);
+  load_prim_sm<DIM, RX>(Wsm, kc + sx, wp);
 #define DIS_EDGE(fld)                                                                \
   {                                                                                  \
     const float s_ = limited_f<LIM>(wc.fld - wm.fld, wp.fld - wc.fld, P.limiter);    \
@@ -149,17 +149,18 @@ template <int DIM, bool RX, int DIR>
 __device__ __forceinline__ void own_flux_diff(const FStateF& lo, const FStateF& hi, float ih, float k2f,
                                               float* D, float& divu, float& bx, float& by, float& small) {
   using L = Lay<DIM, RX>;
-  using S = FSlots<DIM, RX>;
-  float a[S::N], b[S::N];
+  using R = Rec<DIM, RX, DIR>;
+  float a[FA + 4], b[FA + 4];
   face_slots_f<DIM, RX, DIR>(phys_out_f(lo), [&](int s, float v) { a[s] = v; });
   face_slots_f<DIM, RX, DIR>(phys_out_f(hi), [&](int s, float v) { b[s] = v; });
 #pragma unroll
-  for (int c = 0; c < L::NF; ++c) D[c] += (b[c] - a[c]) * ih;
-  const float du = b[S::UF] - a[S::UF];
+  for (int c = 0; c < L::NF; ++c)
+    if (!R::zero(c)) D[c] += (b[R::pos(c)] - a[R::pos(c)]) * ih;
+  const float du = b[R::UF] - a[R::UF];
   divu += du * ih;
-  bx += (b[S::VA] - a[S::VA]) * ih;
-  if constexpr (DIM == 2) by += (b[S::VB] - a[S::VB]) * ih;
-  small += ((b[L::E] - a[L::E]) + k2f * du) * ih;
+  bx += (b[R::VA] - a[R::VA]) * ih;
+  if constexpr (DIM == 2) by += (b[R::VB] - a[R::VB]) * ih;
+  small += ((b[R::pos(L::E)] - a[R::pos(L::E)]) + k2f * du) * ih;
 }
 
 // The conservative state (phi1, partial densities, momentum, e_s, V, the
@@ -209,14 +210,13 @@ template <int DIM, bool RX, int TX, int TY, int NT, int LIM, bool GEN>
 __device__ __forceinline__ void predict_tile(const PhysF& F, const StepArgs32& A, const int4 t,
                                              float* __restrict__ sm, const TileConst& K) {
   using L = Lay<DIM, RX>;
-  using S = FSlots<DIM, RX>;
+  using TL = TileLay<DIM, RX, TX, TY>;
   constexpr int NF = L::NF;
-  constexpr int HX = TX + 2 * NG, HY = DIM == 2 ? TY + 2 * NG : 1;
-  constexpr int plane = HX * HY;
-  constexpr int NFX = (TX + 1) * TY, NFY = DIM == 2 ? TX * (TY + 1) : 0, NFA = NFX + NFY;
+  constexpr int HX = TL::HX, plane = TL::PLANE;
+  constexpr int NFX = TL::NFX, NFA = TL::NFA;
   constexpr int NI = TX * TY, NRX = DIM == 2 ? 2 * TY : 2, NRY = DIM == 2 ? 2 * TX : 0;
   const float* Wsm = sm;
-  float* E = sm + NF * plane + S::N * NFA;
+  float* E = sm + TL::END;
   const PatchDev pd = A.pd[t.x];
   const int i0 = t.y, j0 = t.z;
   const float dxf = (float)pd.dx, dyf = (float)pd.dy;
@@ -250,7 +250,7 @@ __device__ __forceinline__ void predict_tile(const PhysF& F, const StepArgs32& A
     if (!(xlo || xhi || ylo || yhi)) continue;
     const int kc = (ly + (DIM == 2 ? NG : 0)) * HX + lx + NG;
     PrimF wc;
-    load_prim_sm<DIM, RX>(Wsm, plane, kc, wc);
+    load_prim_sm<DIM, RX>(Wsm, kc, wc);
     float D[NF];
 #pragma unroll
     for (int q = 0; q < NF; ++q) D[q] = 0.f;
@@ -305,9 +305,9 @@ __device__ __forceinline__ void predict_tile(const PhysF& F, const StepArgs32& A
 // of sides 0 and 1 of face f (SMEM cells ka, kb for the fallback), into the
 // face slots fidx of Fsm.
 template <int DIM, bool RX, int DIR, bool GEN>
-__device__ __forceinline__ void corr_face(const PhysF& F, const float* __restrict__ Wsm, int plane,
+__device__ __forceinline__ void corr_face(const PhysF& F, const float* __restrict__ Wsm,
                                           const float* __restrict__ E, int NFA, int f, int ka, int kb,
-                                          float* __restrict__ Fsm, int nfaces, int fidx) {
+                                          float* __restrict__ Fa, float* __restrict__ Fb) {
   constexpr int NF = Lay<DIM, RX>::NF;
   float v[NF];
 #pragma unroll
@@ -315,7 +315,7 @@ __device__ __forceinline__ void corr_face(const PhysF& F, const float* __restric
   FStateF sl = face_state_cons_f<DIM, RX, DIR, GEN>(F, v);
   if (!(sl.cL > 0.f)) {
     PrimF w;
-    load_prim_sm<DIM, RX>(Wsm, plane, ka, w);
+    load_prim_sm<DIM, RX>(Wsm, ka, w);
     sl = face_state_f<DIR, GEN>(F, w);
   }
 #pragma unroll
@@ -323,28 +323,25 @@ __device__ __forceinline__ void corr_face(const PhysF& F, const float* __restric
   FStateF sr = face_state_cons_f<DIM, RX, DIR, GEN>(F, v);
   if (!(sr.cL > 0.f)) {
     PrimF w;
-    load_prim_sm<DIM, RX>(Wsm, plane, kb, w);
+    load_prim_sm<DIM, RX>(Wsm, kb, w);
     sr = face_state_f<DIR, GEN>(F, w);
   }
   sl.cL = sqrtf(sl.cL);
   sr.cL = sqrtf(sr.cL);
   const FaceOutF o = hlld_f<DIR>(sl, sr);
-  face_slots_f<DIM, RX, DIR>(o, [&](int slot, float val) { Fsm[slot * nfaces + fidx] = val; });
+  put_face<DIM, RX, DIR>(o, Fa, Fb, f);
 }
 
 // Phase 3: the corrector over all x and y faces of the tile.
 template <int DIM, bool RX, int TX, int TY, int NT, bool GEN>
 __device__ __forceinline__ void correct_tile(const PhysF& F, const StepArgs32& A, const int4 t,
                                              float* __restrict__ sm) {
-  using S = FSlots<DIM, RX>;
-  constexpr int NF = Lay<DIM, RX>::NF;
-  constexpr int HX = TX + 2 * NG, HY = DIM == 2 ? TY + 2 * NG : 1;
-  constexpr int plane = HX * HY;
-  constexpr int NFX = (TX + 1) * TY, NFY = DIM == 2 ? TX * (TY + 1) : 0, NFA = NFX + NFY;
+  using TL = TileLay<DIM, RX, TX, TY>;
+  constexpr int HX = TL::HX, NFX = TL::NFX, NFA = TL::NFA;
   const float* Wsm = sm;
-  float* Fxs = sm + NF * plane;
-  float* Fys = Fxs + S::N * NFX;
-  const float* E = Fxs + S::N * NFA;
+  float* Fa = sm + TL::FAO;
+  float* Fb = sm + TL::FBO;
+  const float* E = sm + TL::END;
   const PatchDev pd = A.pd[t.x];
   const int i0 = t.y, j0 = t.z;
   for (int f = threadIdx.x; f < NFA; f += NT) {
@@ -352,13 +349,13 @@ __device__ __forceinline__ void correct_tile(const PhysF& F, const StepArgs32& A
       const int fx = f % (TX + 1), fy = f / (TX + 1);
       if (i0 + fx > pd.nx || (DIM == 2 && j0 + fy >= pd.ny)) continue;
       const int kb = (DIM == 2 ? fy + NG : 0) * HX + fx + NG;  // the cell right of the face
-      corr_face<DIM, RX, 0, GEN>(F, Wsm, plane, E, NFA, f, kb - 1, kb, Fxs, NFX, f);
+      corr_face<DIM, RX, 0, GEN>(F, Wsm, E, NFA, f, kb - 1, kb, Fa, Fb);
     } else if constexpr (DIM == 2) {
       const int g = f - NFX;
       const int fx = g % TX, fy = g / TX;
       if (i0 + fx >= pd.nx || j0 + fy > pd.ny) continue;
       const int kb = (fy + NG) * HX + fx + NG;  // the cell above the face
-      corr_face<DIM, RX, 1, GEN>(F, Wsm, plane, E, NFA, f, kb - HX, kb, Fys, NFY, g);
+      corr_face<DIM, RX, 1, GEN>(F, Wsm, E, NFA, f, kb - HX, kb, Fa, Fb);
     }
   }
 }

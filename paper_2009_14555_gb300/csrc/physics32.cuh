@@ -101,8 +101,10 @@ __device__ __forceinline__ float cL2_f(const PhysF& P, float phi1, float rho, fl
   return (a * ixi + (4.f / 3.f) * Gmix_f<GEN>(P, phi1, r1, r2)) / rho;
 }
 
+// minmod(a, b) as the median of (0, a, b): the smaller magnitude for equal
+// signs, 0 otherwise; four min/max operations and no multiply.
 __device__ __forceinline__ float minmod_f(float a, float b) {
-  return (a * b > 0.f) ? copysignf(fminf(fabsf(a), fabsf(b)), a) : 0.f;
+  return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.f));
 }
 
 // Limited slope: LIM 0 minmod, 1 van Leer (2 a b / (a + b) for a b > 0);
@@ -262,8 +264,10 @@ __device__ __forceinline__ FaceOutF hlld_f(const FStateF& L, const FStateF& R) {
     o.X = un + S * r1;
     o.D = (Ss - un) * Ss / (S - Ss);
     o.un = Ss;
-    const float c1 = cbrtf(r);
-    const float cn = 1.f / (c1 * c1);
+    // r^(1/3) and r^(-2/3) as powers of two of log2(r) / 3 (r > 0)
+    const float lr = __log2f(r) * (1.f / 3.f);
+    const float c1 = exp2f(lr);
+    const float cn = exp2f(-2.f * lr);
     if (DIR == 0) {
       o.V11 = cn * V11; o.V12 = cn * V12; o.V21 = c1 * V21; o.V22 = c1 * V22;
     } else {
