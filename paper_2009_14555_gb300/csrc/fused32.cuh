@@ -239,30 +239,35 @@ __device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__
     bvd_f(c[1], c[2], c[3], Lt, Rt);
     phiR = Lt;
   }
-  PrimF w0, w1, w2, w3;
-  load_prim_sm<DIM, RX>(Wsm, k0 - sx, w0);
-  load_prim_sm<DIM, RX>(Wsm, k0, w1);
-  load_prim_sm<DIM, RX>(Wsm, k0 + sx, w2);
-  load_prim_sm<DIM, RX>(Wsm, k0 + 2 * sx, w3);
-  PrimF wl, wr;
-#define DIS_RECF(fld)                                            \
-  {                                                              \
-    const float s1 = limited_f<LIM>(w1.fld - w0.fld, w2.fld - w1.fld, P.limiter); \
-    const float s2 = limited_f<LIM>(w2.fld - w1.fld, w3.fld - w2.fld, P.limiter); \
-    wl.fld = w1.fld + 0.5f * s1;                                 \
-    wr.fld = w2.fld - 0.5f * s2;                                 \
-  }
-  DIS_RECF(r1) DIS_RECF(r2) DIS_RECF(u) DIS_RECF(p) DIS_RECF(V11) DIS_RECF(V22) DIS_RECF(V33)
-  if constexpr (DIM == 2) { DIS_RECF(v) DIS_RECF(V12) DIS_RECF(V21) }
-  else { wl.v = wr.v = 0.f; wl.V12 = wr.V12 = wl.V21 = wr.V21 = 0.f; }
-  if constexpr (RX) { DIS_RECF(lam) } else { wl.lam = wr.lam = 0.f; }
+  // the two edge states one after the other (fewer values live at once):
+  // cell a's right edge from cells a - 1, a, a + 1, cell a + 1's left edge
+  // from cells a, a + 1, a + 2
+  auto edge = [&](int kc, float sgn, float phi_e, PrimF& we, PrimF& wc) {
+    PrimF wm, wp;
+    load_prim_sm<DIM, RX>(Wsm, kc - sx, wm);
+    load_prim_sm<DIM, RX>(Wsm, kc, wc);
+    load_prim_sm<DIM, RX>(Wsm, kc + sx, wp);
+#define DIS_RECF(fld) we.fld = wc.fld + sgn * (0.5f * limited_f<LIM>(wc.fld - wm.fld, wp.fld - wc.fld, P.limiter));
+    DIS_RECF(r1) DIS_RECF(r2) DIS_RECF(u) DIS_RECF(p) DIS_RECF(V11) DIS_RECF(V22) DIS_RECF(V33)
+    if constexpr (DIM == 2) { DIS_RECF(v) DIS_RECF(V12) DIS_RECF(V21) }
+    else { we.v = 0.f; we.V12 = we.V21 = 0.f; }
+    if constexpr (RX) { DIS_RECF(lam) } else { we.lam = 0.f; }
 #undef DIS_RECF
-  wl.phi = phiL;
-  wr.phi = phiR;
-  FStateF sl = face_state_f<DIR, GEN>(P, wl);
-  if (!(sl.cL > 0.f)) sl = face_state_f<DIR, GEN>(P, w1);
-  FStateF sr = face_state_f<DIR, GEN>(P, wr);
-  if (!(sr.cL > 0.f)) sr = face_state_f<DIR, GEN>(P, w2);
+    we.phi = phi_e;
+  };
+  FStateF sl, sr;
+  {
+    PrimF we, wc;
+    edge(k0, 1.f, phiL, we, wc);
+    sl = face_state_f<DIR, GEN>(P, we);
+    if (!(sl.cL > 0.f)) sl = face_state_f<DIR, GEN>(P, wc);
+  }
+  {
+    PrimF we, wc;
+    edge(k0 + sx, -1.f, phiR, we, wc);
+    sr = face_state_f<DIR, GEN>(P, we);
+    if (!(sr.cL > 0.f)) sr = face_state_f<DIR, GEN>(P, wc);
+  }
   sl.cL = sqrtf(sl.cL);
   sr.cL = sqrtf(sr.cL);
   const FaceOutF o = hlld_f<DIR>(sl, sr);
@@ -309,18 +314,34 @@ __device__ __forceinline__ void fill_tile(const Phys& P, const PhysF& F, const S
   const PatchDev pd = A.pd[t.x];
   const int i0 = t.y, j0 = t.z;
   const long long T = A.T;
-  for (int c = threadIdx.x; c < HX * HY; c += NT) {
-    const int hx = c % HX, hy = c / HX;
-    const int i = i0 - NG + hx;
-    const int j = DIM == 2 ? j0 - NG + hy : 0;
-    if (i < -NG || i >= pd.nx + NG || (DIM == 2 && (j < -NG || j >= pd.ny + NG))) continue;
-    bool fx = false, fy = false;
-    const int si = ghost_map(i, pd.nx, pd.bc[0], pd.bc[1], fx);
-    const int sj = DIM == 2 ? ghost_map(j, pd.ny, pd.bc[2], pd.bc[3], fy) : 0;
-    PrimF w = cons_to_prim32<DIM, RX, GEN>(P, F, A.src, T, cidx(pd, si, sj));
-    if (fx) { w.u = -w.u; w.V12 = -w.V12; w.V21 = -w.V21; }
-    if (fy) { w.v = -w.v; w.V12 = -w.V12; w.V21 = -w.V21; }
-    store_prim_sm<DIM, RX>(Wsm, HX * HY, c, w);
+  constexpr int NC = HX * HY, NS = Lay<DIM, RX>::NF + 1;
+  // two cells per thread and pass: both cells' loads are in flight before
+  // either recovery starts
+  for (int c0 = threadIdx.x; c0 < NC; c0 += 2 * NT) {
+    float v[2][NS];
+    bool ok[2], fx[2], fy[2];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const int c = c0 + m * NT;
+      const int hx = c % HX, hy = c / HX;
+      const int i = i0 - NG + hx;
+      const int j = DIM == 2 ? j0 - NG + hy : 0;
+      ok[m] = c < NC && !(i < -NG || i >= pd.nx + NG || (DIM == 2 && (j < -NG || j >= pd.ny + NG)));
+      fx[m] = fy[m] = false;
+      if (ok[m]) {
+        const int si = ghost_map(i, pd.nx, pd.bc[0], pd.bc[1], fx[m]);
+        const int sj = DIM == 2 ? ghost_map(j, pd.ny, pd.bc[2], pd.bc[3], fy[m]) : 0;
+        load32<DIM, RX>(A.src, T, cidx(pd, si, sj), v[m]);
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      if (!ok[m]) continue;
+      PrimF w = prim32_of<DIM, RX, GEN>(P, F, v[m]);
+      if (fx[m]) { w.u = -w.u; w.V12 = -w.V12; w.V21 = -w.V21; }
+      if (fy[m]) { w.v = -w.v; w.V12 = -w.V12; w.V21 = -w.V21; }
+      store_prim_sm<DIM, RX>(Wsm, NC, c0 + m * NT, w);
+    }
   }
 }
 
@@ -402,6 +423,7 @@ __device__ __forceinline__ void update_tile(const Phys& P, const PhysF& F, const
     float divu = (FX(RXf::UF, true) - FX(RXf::UF, false)) * idx_;
     float bx = (FX(RXf::VA, true) - FX(RXf::VA, false)) * idx_;
     float by = 0.f;
+    if constexpr (DIM == 2) by = (xr[RXf::VB] - xl[RXf::VB]) * idx_;
     const float k2f = F.m[1].kap, dkf = F.m[0].kap - F.m[1].kap;
     // phi1 flux divergence from the exact differences of the float fluxes
     ff Dc = ff_mul_f(two_sum(xr[RXf::pos(L::PHI)], -xl[RXf::pos(L::PHI)]), idx_);
@@ -421,7 +443,7 @@ __device__ __forceinline__ void update_tile(const Phys& P, const PhysF& F, const
         if (!RYf::zero(c)) D[c] += (yt[RYf::pos(c)] - yb[RYf::pos(c)]) * idy;
       divu += (yt[RYf::UF] - yb[RYf::UF]) * idy;
       bx += (yt[RYf::VA] - yb[RYf::VA]) * idy;
-      by = (xr[RXf::VB] - xl[RXf::VB]) * idx_ + (yt[RYf::VB] - yb[RYf::VB]) * idy;
+      by += (yt[RYf::VB] - yb[RYf::VB]) * idy;
       Dc = ff_add(Dc, ff_mul_f(two_sum(yt[RYf::pos(L::PHI)], -yb[RYf::pos(L::PHI)]), idy));
       small += ((yt[RYf::pos(L::E)] - yb[RYf::pos(L::E)]) +
                 k2f * ((yt[RYf::UF] - yb[RYf::UF]) + (yt[RYf::DD] - yb[RYf::DD])) +
