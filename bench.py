@@ -26,21 +26,20 @@ sys.path.insert(0, ROOT)
 
 METRIC = "cell-updates/s and % HBM peak, FP32-bulk vs plain FP64 on one GB300 at stated L1"
 
-# Arithmetic of the dominant kernels, counted by ncu on the 1024 x 512
-# reactive plate (executed FADD + FMUL + 2 FFMA, resp. DADD + DMUL + 2 DFMA,
-# thread level): the FP32-bulk stage kernel per cell-stage for each tile shape
-# (TX, TY) (the register budget does not change the arithmetic), and the
-# float64 x-face flux kernel per face.
-STAGE32_FLOP = {(16, 15): 1454.0, (32, 15): 1418.6, (32, 7): 1499.1}
+# Arithmetic and DRAM traffic of the dominant kernels, counted by ncu on the
+# kernels as built (executed FADD + FMUL + 2 FFMA, resp. DADD + DMUL + 2 DFMA,
+# thread level).  FP32-bulk stage kernel, per cell-stage, one launch on the
+# full 2048 x 1024 reactive plate (stage 2, which reads two states and writes
+# one), per tile shape (TX, TY); None where that shape was not captured (the
+# register budget does not change the arithmetic).
+STAGE32_FLOP = {(16, 15): None, (32, 15): 1336.1, (32, 7): None}
+# float64 x-face flux kernel: FP64 FLOP per face (1024 x 512 capture)
 FLUX_FP64_FLOP_PER_FACE = 868.1
-# DRAM bytes (read + write) per cell-stage of the stage kernel on the full
-# 2048 x 1024 grid (ncu, one launch: stage 2, which reads two states and
-# writes one), per tile shape; None where not captured.
-STAGE32_DRAM = {(16, 15): None, (32, 15): 146.6, (32, 7): None}
-# The FP32-bulk MUSCL-Hancock kernel on the same grid (ncu, one launch of the
+STAGE32_DRAM = {(16, 15): None, (32, 15): 145.7, (32, 7): None}
+# The FP32-bulk MUSCL-Hancock kernel on the same grid (one launch of the
 # 32 x 7 tile): FP32 FLOP and DRAM bytes per cell-update.
-HANCOCK32_FLOP = {(32, 7): 2678.0}
-HANCOCK32_DRAM = {(32, 7): 85.1}
+HANCOCK32_FLOP = {(32, 7): 2606.7}
+HANCOCK32_DRAM = {(32, 7): 85.6}
 # DRAM bytes per x-flux launch of the float64 step, per face (73.07 MB for
 # 524800 faces on 1024 x 512); traffic grows with the face count.
 FLUX_DRAM_BYTES_PER_FACE = 73.07e6 / 524800
