@@ -223,21 +223,23 @@ __device__ __forceinline__ void face32(const PhysF& P, const float* __restrict__
   float ph[6];
 #pragma unroll
   for (int s = 0; s < 6; ++s) ph[s] = Wphi[k0 + (s - 2) * sx];
-  float phiL, phiR;
-  {
-    CandF c[4];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      auto beta_of = [&]() -> float {
-        return thinc_beta_f<DIM>(P, Wphi, k0 + (s - 1) * sx, sx, sy, dxn, dxt);
-      };
-      c[s] = phi_cand_f<LIM>(ph[s], ph[s + 1], ph[s + 2], beta_of, P.thinc != 0, P.limiter);
-    }
-    float Lt, Rt;
-    bvd_f(c[0], c[1], c[2], Lt, Rt);
-    phiL = Rt;
-    bvd_f(c[1], c[2], c[3], Lt, Rt);
-    phiR = Lt;
+  // MUSCL-BVD-THINC edge values of cells a and a + 1.  A cell that is not
+  // mixed has identical MUSCL and THINC candidates, so the BVD choice (and
+  // the candidate of its outer neighbour, which only that choice reads) is
+  // needed only for a mixed cell.
+  auto cand = [&](int s) {
+    auto beta_of = [&]() -> float { return thinc_beta_f<DIM>(P, Wphi, k0 + (s - 1) * sx, sx, sy, dxn, dxt); };
+    return phi_cand_f<LIM>(ph[s], ph[s + 1], ph[s + 2], beta_of, P.thinc != 0, P.limiter);
+  };
+  const CandF c1 = cand(1), c2 = cand(2);
+  float phiL = c1.mR, phiR = c2.mL;
+  if (c1.mixed) {
+    float Lt;
+    bvd_f(cand(0), c1, c2, Lt, phiL);
+  }
+  if (c2.mixed) {
+    float Rt;
+    bvd_f(c1, c2, cand(3), phiR, Rt);
   }
   // the two edge states one after the other (fewer values live at once):
   // cell a's right edge from cells a - 1, a, a + 1, cell a + 1's left edge

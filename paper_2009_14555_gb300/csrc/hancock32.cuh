@@ -118,13 +118,16 @@ __device__ __forceinline__ void cell_edges_f(const PhysF& P, const float* __rest
   float ph[5];
 #pragma unroll
   for (int s = 0; s < 5; ++s) ph[s] = Wphi[kc + (s - 2) * sx];
-  CandF c[3];
-#pragma unroll
-  for (int s = 0; s < 3; ++s) {
+  auto cand = [&](int s) {
     auto beta_of = [&]() -> float { return thinc_beta_f<DIM>(P, Wphi, kc + (s - 1) * sx, sx, sy, dxn, dxt); };
-    c[s] = phi_cand_f<LIM>(ph[s], ph[s + 1], ph[s + 2], beta_of, P.thinc != 0, P.limiter);
-  }
-  bvd_f(c[0], c[1], c[2], lo.phi, hi.phi);
+    return phi_cand_f<LIM>(ph[s], ph[s + 1], ph[s + 2], beta_of, P.thinc != 0, P.limiter);
+  };
+  // a cell that is not mixed keeps its MUSCL values (its THINC candidate is
+  // the same), so the BVD choice is made only in a mixed cell
+  const CandF c1 = cand(1);
+  lo.phi = c1.mL;
+  hi.phi = c1.mR;
+  if (c1.mixed) bvd_f(cand(0), c1, cand(2), lo.phi, hi.phi);
   PrimF wm, wp;
   load_prim_sm<DIM, RX>(Wsm, kc - sx, wm);
   load_prim_sm<DIM, RX>(Wsm, kc + sx, wp);

@@ -121,6 +121,7 @@ __device__ __forceinline__ float limited_f(float a, float b, int lim_rt = 0) {
 
 struct CandF {
   float mL, mR, tL, tR;
+  bool mixed;  // THINC applied (tL, tR differ from mL, mR only then)
 };
 
 // beta_of() gives the THINC steepness; it is evaluated only in a mixed cell.
@@ -133,6 +134,7 @@ __device__ __forceinline__ CandF phi_cand_f(float qm, float qc, float qp, const 
   c.mR = qc + 0.5f * s;
   c.tL = c.mL;
   c.tR = c.mR;
+  c.mixed = false;
   if (thinc) {
     const float qmin = fminf(qm, qp);
     const float jump = fmaxf(qm, qp) - qmin;
@@ -145,6 +147,7 @@ __device__ __forceinline__ CandF phi_cand_f(float qm, float qc, float qp, const 
       const float A = (B / coshf(beta) - 1.f) / tb;
       c.tL = qmin + 0.5f * jump * (1.f + th * A);
       c.tR = qmin + 0.5f * jump * (1.f + th * (tb + A) / (1.f + A * tb));
+      c.mixed = true;
     }
   }
   return c;
