@@ -43,6 +43,17 @@ Readings (the paper leaves these to its platform):
     replaced by the time- and area-average of the level l + 1 fluxes through
     the same face.  phi1 and V carry non-conservative terms and are not
     refluxed.
+  * Cylindrical geometry (x = r, y = z; Section 3, cylindrical symmetry).
+    The single-grid scheme is the planar scheme plus the cell-centre
+    geometric source s_g, so the conservative variables are per unit (r, z)
+    area, and the hierarchy keeps the planar forms above: interpolation,
+    average-down and refluxing of those variables (the flux registers hold
+    the planar face fluxes); each level adds s_g at its own cell-centre
+    radii r = x0 + (i + 1/2) dx_l in every stage.
+  * The single-stage MUSCL-Hancock update (oracle/hancock.py; planar) in
+    place of SSP-RK3: the ghost cells of level l >= 1 take the coarser
+    level's interpolation at the start of each of its steps, and the
+    registers hold the corrector's face fluxes times dt (weight 1).
   * Regridding every `regrid_every` level-0 steps, level by level from the
     coarsest: the cells level l does not own first take the interpolation of
     the (current) level l - 1, then level l is tagged; cells that stay
@@ -58,8 +69,9 @@ from __future__ import annotations
 import torch
 
 from .closures import cons_to_prim, hencky_dev, mixture_props, phases
+from .hancock import hancock_operator_padded
 from .scheme import (NG, BC_PERIODIC, F64, _axpy, cfl_rate, fill_ghosts, operator_padded, plastic_update,
-                     reaction_update)
+                     reaction_update, with_geometric_source)
 
 CONSERVED = ("ar1", "ar2", "mom", "E", "arl")
 RK3 = ((0.0, 1.0, 0.0, 1.0 / 6.0), (0.75, 0.25, 1.0, 1.0 / 6.0), (1.0 / 3.0, 2.0 / 3.0, 0.5, 2.0 / 3.0))
@@ -174,7 +186,9 @@ class Hierarchy:
 
     def __init__(self, q0, grid0, mats, opts, max_level=2, block=8, eps=0.1, buffer=2,
                  u_floor=1.0, regrid_every=4, extra_tags=None):
-        assert opts.get("scheme", "rk3") == "rk3" and grid0.get("geometry", "planar") == "planar"
+        assert opts.get("scheme", "rk3") in ("rk3", "hancock")
+        assert grid0.get("geometry", "planar") == "planar" or (
+            grid0["geometry"] == "cyl" and opts.get("scheme", "rk3") == "rk3")
         self.extra_tags = extra_tags  # optional (level, grid) -> bool cell mask added to the tags
         self.dim = grid0["dim"]
         self.mats = mats
@@ -267,8 +281,8 @@ class Hierarchy:
         return {k: torch.where(a.reshape(a.shape + _trail(v)), v, f[k]) for k, v in qs.items()}
 
     def _level_step(self, l, dt, t0_frac, frac_len):
-        """One SSP-RK3 step of level l plus sources; returns the
-        Runge-Kutta-weighted face fluxes (conservative rows) times dt.
+        """One SSP-RK3 (or MUSCL-Hancock) step of level l plus sources;
+        returns the stage-weighted face fluxes (conservative rows) times dt.
         t0_frac, frac_len: start and length of the step as fractions of the
         step of level l - 1 (for the time interpolation)."""
         g = self.grids[l]
@@ -276,14 +290,23 @@ class Hierarchy:
         qn = self.q[l]
         x = qn
         reg = None
-        for a, b, ts, w in RK3:
-            xs = self._filled(l, x, t0_frac + ts * frac_len)
-            D, faces = operator_padded(xs, fill_ghosts(xs, g), g, self.mats, opts.get("thinc", False),
-                                       opts.get("limiter", "minmod"))
-            Fw = [{k: w * dt * F[k] for k in F if k in CONSERVED} for F, _, _, _ in faces]
-            reg = Fw if reg is None else [{k: r[k] + f[k] for k in r} for r, f in zip(reg, Fw)]
-            y = _axpy(1.0, xs, -dt, D)
-            x = y if a == 0.0 else _axpy(a, self._filled(l, qn, t0_frac), b, y)
+        if opts.get("scheme", "rk3") == "hancock":
+            # one stage: ghost cells at the start of the step, fluxes of weight 1
+            xs = self._filled(l, qn, t0_frac)
+            D, faces = hancock_operator_padded(xs, fill_ghosts(xs, g), g, self.mats, opts.get("thinc", False), dt,
+                                               opts.get("limiter", "minmod"))
+            reg = [{k: dt * F[k] for k in F if k in CONSERVED} for F, _, _, _ in faces]
+            x = _axpy(1.0, xs, -dt, D)
+        else:
+            for a, b, ts, w in RK3:
+                xs = self._filled(l, x, t0_frac + ts * frac_len)
+                D, faces = operator_padded(xs, fill_ghosts(xs, g), g, self.mats, opts.get("thinc", False),
+                                           opts.get("limiter", "minmod"))
+                D = with_geometric_source(D, xs, g, self.mats)
+                Fw = [{k: w * dt * F[k] for k in F if k in CONSERVED} for F, _, _, _ in faces]
+                reg = Fw if reg is None else [{k: r[k] + f[k] for k in r} for r, f in zip(reg, Fw)]
+                y = _axpy(1.0, xs, -dt, D)
+                x = y if a == 0.0 else _axpy(a, self._filled(l, qn, t0_frac), b, y)
         x = plastic_update(x, self.mats, dt)
         if any(m["reactive"] for m in self.mats):
             x = reaction_update(x, self.mats, dt)

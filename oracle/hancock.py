@@ -75,9 +75,16 @@ def _own_faces(w, d, mats):
 
 def hancock_operator(q, grid, mats, thinc, dt, limiter="minmod"):
     """D of the MUSCL-Hancock update (q* = q^n - dt D) for the interior cells."""
+    return hancock_operator_padded(q, fill_ghosts(q, grid), grid, mats, thinc, dt, limiter)[0]
+
+
+def hancock_operator_padded(q, qg, grid, mats, thinc, dt, limiter="minmod"):
+    """D of the MUSCL-Hancock update for the interior cells of q, from qg: q
+    with NG ghost layers on each side (filled by the caller); also returns
+    the face outputs of the corrector along each axis (conservative fluxes,
+    face phi, u, V)."""
     ny, nx = q["phi1"].shape
     dim = grid["dim"]
-    qg = fill_ghosts(q, grid)
     wg = cons_to_prim(qg, mats)
     comps = _components(wg)
     dims = [0] if dim == 1 else [0, 1]
@@ -140,4 +147,4 @@ def hancock_operator(q, grid, mats, thinc, dt, limiter="minmod"):
             left = {k: t[NG - 1:NG + ny, cols] for k, t in wp.items()}
             right = {k: t[NG:NG + ny + 1, cols] for k, t in wm.items()}
         faces.append(hllc(left, right, d, mats))
-    return operator_from_faces(q, faces, grid)
+    return operator_from_faces(q, faces, grid), faces

@@ -295,13 +295,21 @@ def spatial_operator(q, grid, mats, thinc, limiter="minmod"):
     """D(q) of Section 3.1 for all interior cells of one patch; in cylindrical
     geometry (grid["geometry"] == "cyl", x = r, y = z) minus the geometric
     source s_g."""
-    D = _planar_operator(q, grid, mats, thinc, limiter)
-    if grid.get("geometry", "planar") == "cyl":
-        r = cell_radius(grid, q["phi1"].shape[1])[None, :]
-        t = geometric_source_terms(q, mats)
-        for k in D:
-            rr = r.reshape(r.shape + (1,) * (D[k].dim() - 2))
-            D[k] = D[k] + t[k] / rr
+    return with_geometric_source(_planar_operator(q, grid, mats, thinc, limiter), q, grid, mats)
+
+
+def with_geometric_source(D, q, grid, mats):
+    """D of the cells of q minus the geometric source s_g = -(1/r) t of
+    cylindrical geometry (Section 3, cylindrical symmetry), t the bracket of
+    geometric_source_terms, r the cell-centre radius of grid; D itself for a
+    planar grid."""
+    if grid.get("geometry", "planar") != "cyl":
+        return D
+    r = cell_radius(grid, q["phi1"].shape[1])[None, :]
+    t = geometric_source_terms(q, mats)
+    for k in D:
+        rr = r.reshape(r.shape + (1,) * (D[k].dim() - 2))
+        D[k] = D[k] + t[k] / rr
     return D
 
 

@@ -197,3 +197,136 @@ def test_refined_interface_is_closer_to_the_fine_grid():
     e_amr = float((h.q[0]["E"] - ref["E"])[cov].abs().sum())
     e_coarse = float((qc["E"] - ref["E"])[cov].abs().sum())
     assert e_amr < 0.5 * e_coarse, (e_amr, e_coarse)
+
+
+def _cons_geo(wl):
+    p = wl.patches[0]
+    return (C.prim_to_cons(S.prim_from_array(p.prim, wl.dim, wl.reactive), wl.materials),
+            S.grid_of(p, wl.dim, wl.geometry))
+
+
+def test_one_level_is_the_plain_step_cylindrical():
+    """Cylindrical geometry (x = r on [0, 1] with the axis at x = 0): a single
+    level is the single-grid cylindrical step, geometric source included."""
+    wl = W.cylinder_core_1d(96, steps=5)
+    q, g = _cons_geo(wl)
+    assert g["geometry"] == "cyl"
+    h = A.Hierarchy(q, g, wl.materials, _opts(wl), max_level=1, block=8)
+    for _ in range(5):
+        dt = h.step()
+        q, dt_ref = S.step(q, g, wl.materials, _opts(wl))
+        assert dt == float(dt_ref)
+    _same(h.q[0], q)
+
+
+def _full_refinement_cyl(wl, steps):
+    q, g = _cons_geo(wl)
+    h = A.Hierarchy(q, g, wl.materials, _opts(wl), max_level=2, block=8, eps=-1.0)
+    assert bool(h.active[1].all())
+    qf = A.interp_fine(q, g)
+    gf = dict(g, dx=g["dx"] / 2, dy=g["dy"] / 2 if wl.dim == 2 else g["dy"])
+    for _ in range(steps):
+        dt = h.step()
+        for _ in range(2):
+            qf, _ = S.step(qf, gf, wl.materials, _opts(wl), dt=dt / 2)
+    _same(h.q[1], qf)
+    _same(h.q[0], A.average_down(qf, wl.dim))
+    return h
+
+
+def test_full_refinement_is_the_fine_grid_cylindrical_1d():
+    """Every cell refined: level 1 evolves as the uniform cylindrical grid of
+    twice the resolution, so its geometric source is taken at the fine
+    cell-centre radii (i + 1/2) dx / 2, and level 0 is its average."""
+    h = _full_refinement_cyl(W.cylinder_core_1d(64, steps=4), 4)
+    # the geometric source acts: the same hierarchy in planar geometry differs
+    wl = W.cylinder_core_1d(64, steps=4)
+    wl.geometry = "planar"
+    q, g = _cons_geo(wl)
+    hp = A.Hierarchy(q, g, wl.materials, _opts(wl), max_level=2, block=8, eps=-1.0)
+    for _ in range(4):
+        hp.step()
+    assert not torch.equal(hp.q[1]["mom"], h.q[1]["mom"])
+
+
+def test_full_refinement_is_the_fine_grid_cylindrical_2d():
+    """The same in (r, z): the shock-sphere problem on 16 x 32 cells."""
+    _full_refinement_cyl(W.sphere_shock_rz(32, steps=2, thinc=False), 2)
+
+
+# --- the single-stage MUSCL-Hancock update in the hierarchy ----------------
+def _hopts(wl):
+    return dict(cfl=wl.cfl, thinc=wl.thinc, scheme="hancock")
+
+
+def test_one_level_is_the_plain_step_hancock():
+    """MUSCL-Hancock: a single level is the single-grid MUSCL-Hancock step."""
+    wl = W.solid_gas_1d(96, steps=6)
+    q, g = _cons(wl)
+    h = A.Hierarchy(q, g, wl.materials, _hopts(wl), max_level=1, block=8)
+    for _ in range(6):
+        dt = h.step()
+        q, dt_ref = S.step(q, g, wl.materials, _hopts(wl))
+        assert dt == float(dt_ref)
+    _same(h.q[0], q)
+
+
+def test_full_refinement_is_the_fine_grid_hancock():
+    """MUSCL-Hancock, every cell refined (1D solid|gas and the 2D
+    shock-disc with THINC): level 1 is the uniform fine grid bit for bit."""
+    for wl, steps in ((W.solid_gas_1d(64, steps=4), 4), (W.shock_disc_2d(32, steps=2, shock_x=0.3), 2)):
+        q, g = _cons(wl)
+        h = A.Hierarchy(q, g, wl.materials, _hopts(wl), max_level=2, block=8, eps=-1.0)
+        assert bool(h.active[1].all())
+        qf = A.interp_fine(q, g)
+        gf = dict(g, dx=g["dx"] / 2, dy=g["dy"] / 2 if wl.dim == 2 else g["dy"])
+        for _ in range(steps):
+            dt = h.step()
+            for _ in range(2):
+                qf, _ = S.step(qf, gf, wl.materials, _hopts(wl), dt=dt / 2)
+        _same(h.q[1], qf)
+        _same(h.q[0], A.average_down(qf, wl.dim))
+
+
+def test_conservation_across_levels_hancock():
+    """MUSCL-Hancock on periodic domains: the composite totals stay constant
+    to round-off through regrids (1D, three levels) and across a refined
+    ring (2D): the registers hold the corrector's fluxes."""
+    wl = W.solid_gas_1d(64, steps=1)
+    wl.patches[0].bc = [S.BC_PERIODIC] * 4
+    cases = [(wl, dict(max_level=3, block=8, eps=0.05, regrid_every=2), 8),
+             (W.smooth_disc_2d(n=64, steps=1, u0=150.0), dict(max_level=2, block=8, eps=0.5, buffer=0,
+                                                               regrid_every=2), 4)]
+    for wl, kw, steps in cases:
+        q, g = _cons(wl)
+        h = A.Hierarchy(q, g, wl.materials, _hopts(wl), **kw)
+        assert h.n_levels() >= 2 and not bool(h.active[1].all())
+        t0 = h.composite_totals()
+        for _ in range(steps):
+            h.step()
+        t1 = h.composite_totals()
+        for k in ("ar1", "ar2", "mom", "E"):
+            scale = float(t0[k].abs().max()) or 1.0
+            err = float((t1[k] - t0[k]).abs().max()) / scale
+            assert err < 1e-13, (wl.name, k, err)
+
+
+def test_uniform_state_stays_uniform_hancock():
+    """MUSCL-Hancock free stream across coarse-fine boundaries."""
+    wl = W.riemann_1d(64, dict(mat=1, rho=1.2, u=50.0, p=1e5), dict(mat=1, rho=1.2, u=50.0, p=1e5),
+                      materials=[W.AIR, W.AIR], steps=1)
+    q, g = _cons(wl)
+
+    def force(l, grid, shape):
+        m = torch.zeros(shape, dtype=torch.bool)
+        m[..., 20:40] = True
+        return m
+
+    h = A.Hierarchy(q, g, wl.materials, _hopts(wl), max_level=2, block=8, eps=1e9, extra_tags=force)
+    assert h.n_levels() == 2 and not bool(h.active[1].all())
+    for _ in range(5):
+        h.step()
+    for l in range(2):
+        for k, v in h.q[l].items():
+            a = v[h.active[l]]
+            assert float((a - a[0]).abs().max()) == 0.0, (l, k)
