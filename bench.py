@@ -422,8 +422,9 @@ def widened_bench(warmup=3):
     same input in planar geometry.  The k sqrt(lam) reaction law: 1024 copies
     of the 4000-cell detonation-into-copper problem (the resolution of the
     paper's one-dimensional test) in one batch.  Johnson-Cook plasticity, the
-    AMR hierarchy and the AMR form of the one-dimensional test follow, each
-    measured on its own (jc_bench, amr_bench, amr_detonation_bench)."""
+    AMR hierarchy (SSP-RK3, MUSCL-Hancock, and SSP-RK3 in (r, z)) and the AMR
+    form of the one-dimensional test follow, each measured on its own
+    (jc_bench, amr_bench, amr_detonation_bench)."""
     import copy
     from paper_2009_14555_gb300 import workloads as W
     from paper_2009_14555_gb300.solver import pack
@@ -446,7 +447,10 @@ def widened_bench(warmup=3):
     for prec, steps in (("fp32_bulk", 200), ("fp64", 30)):
         det[prec] = _timed_steps(wl, prim, prec, steps, warmup)
     out["sqrt_rate_law"] = det
-    for key, fn in (("johnson_cook", jc_bench), ("amr", amr_bench), ("amr_detonation_1d", amr_detonation_bench)):
+    for key, fn in (("johnson_cook", jc_bench), ("amr", amr_bench),
+                    ("amr_hancock", lambda: amr_bench(kind="hancock")),
+                    ("amr_cylindrical", lambda: amr_bench(kind="cylindrical")),
+                    ("amr_detonation_1d", amr_detonation_bench)):
         try:
             out[key] = fn()
         except Exception as e:  # the other rows are measured: keep them
@@ -518,16 +522,30 @@ def amr_detonation_bench(n=1000, levels=3, steps=40, warmup=2):
             "note": "a single 1D problem: launch- and host-latency bound on either path"}
 
 
-def amr_bench(n=256, levels=3, steps=12, warmup=2):
-    """The structured AMR hierarchy (float64) on the 2D shock-disc: an n x n
-    base and `levels` levels of ratio 2 (finest n 2^(L-1) squared), block 16,
-    flagging threshold 0.3, regrid every 4 level-0 steps; against the uniform
-    grid of the finest resolution over the same physical time (2^(L-1) of its
-    steps per level-0 step)."""
-    import torch
+def _amr_case(kind, n):
+    """Base workload of an AMR bench row: the 2D shock-disc on n x n cells
+    (SSP-RK3 or MUSCL-Hancock), or its (r, z) form, the shock-sphere on
+    n/2 x n cells."""
     from paper_2009_14555_gb300 import workloads as W
-    from paper_2009_14555_gb300.solver import AmrSolver, Solver
+    if kind == "cylindrical":
+        return W.sphere_shock_rz(n, steps=0, shock_z=0.3)
     wl = W.shock_disc_2d(n, steps=0, shock_x=0.3)
+    if kind == "hancock":
+        wl.scheme = "hancock"
+    return wl
+
+
+def amr_bench(n=256, levels=3, steps=12, warmup=2, kind="rk3"):
+    """The structured AMR hierarchy (float64) on the 2D shock-disc (kind
+    "rk3", "hancock") or the (r, z) shock-sphere (kind "cylindrical"): an
+    n x n base (n/2 x n in (r, z)) and `levels` levels of ratio 2, block 16,
+    flagging threshold 0.3, regrid every 4 level-0 steps; against the
+    uniform grid of the finest resolution over the same physical time
+    (2^(L-1) of its steps per level-0 step)."""
+    import torch
+    from paper_2009_14555_gb300.solver import AmrSolver, Solver
+    wl = _amr_case(kind, n)
+    nx0, ny0 = wl.patches[0].nx, wl.patches[0].ny
     g = AmrSolver(wl, max_levels=levels, block=16, eps=0.3, regrid_every=4)
     g.set_prim(wl.patches[0].prim)
     g.step(warmup)
@@ -540,10 +558,10 @@ def amr_bench(n=256, levels=3, steps=12, warmup=2):
     nl2, counts2 = g.levels()
     rc = g.check()[0]
     # cells each level owns (blocks of (2 x 16)^2 cells) and the level steps per level-0 step
-    upd = n * n + sum(counts2[l] * (32 * 32) * 2 ** l for l in range(1, nl2))
+    upd = nx0 * ny0 + sum(counts2[l] * (32 * 32) * 2 ** l for l in range(1, nl2))
     g.close()
     fine = n << (levels - 1)
-    fw = W.shock_disc_2d(fine, steps=0, shock_x=0.3)
+    fw = _amr_case(kind, fine)
     f = Solver.from_workload(fw)
     from paper_2009_14555_gb300.solver import pack
     f.set_state(pack([fw.patches[0].prim]), kind=1)
@@ -556,10 +574,13 @@ def amr_bench(n=256, levels=3, steps=12, warmup=2):
     torch.cuda.synchronize()
     ms_fine = e0.elapsed_time(e1)
     f.close()
-    return {"workload": f"2d_shock_disc_{n}x{n} base, {levels} levels (finest {fine}x{fine}), block 16, eps 0.3",
-            "precision": "fp64", "ms_per_level0_step": ms, "levels_used": nl2, "blocks_per_level": counts2,
+    shape = (f"2d_shock_disc_{n}x{n}" if kind != "cylindrical" else f"2d_sphere_shock_rz_{n // 2}x{n} (x = r, y = z)")
+    fx, fy = nx0 << (levels - 1), ny0 << (levels - 1)
+    return {"workload": f"{shape} base, {levels} levels (finest {fx}x{fy}), block 16, eps 0.3",
+            "precision": "fp64", "scheme": wl.scheme, "geometry": wl.geometry,
+            "ms_per_level0_step": ms, "levels_used": nl2, "blocks_per_level": counts2,
             "cell_updates_per_level0_step": upd, "value": upd / (ms * 1e-3), "unit": UNIT,
-            "finest_equivalent_cell_updates_per_s": fine * fine * 2 ** (levels - 1) / (ms * 1e-3),
+            "finest_equivalent_cell_updates_per_s": fx * fy * 2 ** (levels - 1) / (ms * 1e-3),
             "uniform_finest_ms_same_time": ms_fine, "speedup_vs_uniform_finest": ms_fine / ms,
             "status_ok": rc == 0, "note": "wall time per level-0 step (the hierarchy synchronises each step); "
                                           "uniform: 2^(L-1) float64 steps of the finest grid, CUDA events"}

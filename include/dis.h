@@ -480,9 +480,17 @@ int dis_alu_peaks(void* stream, double* fp32_tflops, double* fp64_tflops, double
  * velocity component to a face neighbour exceeds eps (floors: 1 for phi1,
  * u_floor for velocities), tags are dilated by `buffer` cells, and a block is
  * refined when it holds a tag and, on levels >= 1, its neighbouring blocks
- * are refined (proper nesting).  Float64, SSP-RK3, planar.  No counterpart
- * in the paper for the block and nesting rules: the paper's platform leaves
- * them to AMReX. */
+ * are refined (proper nesting).  Float64; SSP-RK3 in planar or cylindrical
+ * geometry (Section 3, cylindrical symmetry: x = r, y = z), or the
+ * single-stage MUSCL-Hancock update (DIS_HANCOCK) in planar geometry, whose
+ * one stage takes its ghost cells at the start of each step and registers
+ * its fluxes with weight 1.  The cylindrical
+ * step is the planar step plus the cell-centre geometric source, so the
+ * conservative variables are per unit (r, z) area and the interpolation,
+ * average-down and refluxing above act on them as in planar geometry; each
+ * level takes the geometric source at its own cell-centre radii.  No
+ * counterpart in the paper for the block and nesting rules: the paper's
+ * platform leaves them to AMReX. */
 typedef struct dis_amr dis_amr;
 typedef struct {
   int32_t max_levels;   /* 1 .. 4 */
@@ -493,10 +501,12 @@ typedef struct {
   int32_t regrid_every; /* level-0 steps between regrids (0 = never after the first) */
 } dis_amr_options;
 
-/* domain: the level-0 patch (bc: transmissive, periodic or reflective);
- * opt: as dis_create (precision DIS_FP64, scheme DIS_RK3, geometry
- * DIS_PLANAR).  DIS_EINVAL for other options or a block that does not divide
- * the domain; DIS_ECUDA. */
+/* domain: the level-0 patch (bc: transmissive, periodic or reflective; in
+ * cylindrical geometry x0 >= 0 is the radius of its axis-side face, and a
+ * domain on the axis has x0 = 0 and a reflective x-low side); opt: as
+ * dis_create (precision DIS_FP64; scheme DIS_RK3 with geometry DIS_PLANAR
+ * or DIS_CYLINDRICAL, or DIS_HANCOCK with DIS_PLANAR).  DIS_EINVAL for other
+ * options or a block that does not divide the domain; DIS_ECUDA. */
 int dis_amr_create(int dim, const dis_patch* domain, int reactive_material, const dis_options* opt,
                    const dis_amr_options* aopt, void* stream, dis_amr** out);
 /* Materials of every level (as dis_set_materials). */

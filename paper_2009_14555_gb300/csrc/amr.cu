@@ -365,8 +365,10 @@ int make_level(dis_amr* h, int l, const std::vector<int2>& org, dis_amr_level& L
     p.ny = h->dim == 2 ? S : 1;
     p.dx = h->dom.dx / (1 << l);
     p.dy = h->dim == 2 ? h->dom.dy / (1 << l) : h->dom.dy;
-    p.x0 = 0.0;
     const int I0 = org[b].x, J0 = org[b].y;
+    // x of the block's low face: the radius of its axis-side face in
+    // cylindrical geometry (the geometric source takes r at cell centres)
+    p.x0 = h->dom.x0 + I0 * p.dx;
     const bool edge[4] = {I0 == 0, I0 + S == L.NX, J0 == 0, J0 + S == L.NY};
     for (int k = 0; k < 4; ++k) {
       const int dbc = h->dom.bc[k];
@@ -606,19 +608,21 @@ void fill(dis_amr* h, int l, double* q, double theta, bool current) {
 }
 
 // Runge-Kutta stage data: the time of each stage input (fraction of dt) and
-// the weight of its fluxes in the step.
+// the weight of its fluxes in the step.  The MUSCL-Hancock update has one
+// stage: input at the start of the step, flux weight 1.
 const double kStageT[3] = {0.0, 1.0, 0.5};
 const double kStageW[3] = {1.0 / 6.0, 1.0 / 6.0, 2.0 / 3.0};
 
 void hook_before(void* u, int stage, double* qsrc) {
   dis_amr* h = (dis_amr*)u;
-  if (h->hl >= 1) fill(h, h->hl, qsrc, h->ht0 + kStageT[stage] * h->hlen, false);
+  const double ts = h->opt.scheme == DIS_HANCOCK ? 0.0 : kStageT[stage];
+  if (h->hl >= 1) fill(h, h->hl, qsrc, h->ht0 + ts * h->hlen, false);
 }
 
 void hook_after_flux(void* u, int stage) {
   dis_amr* h = (dis_amr*)u;
   dis_amr_level& L = h->lev[h->hl];
-  const double wdt = kStageW[stage] * h->hdt;
+  const double wdt = (h->opt.scheme == DIS_HANCOCK ? 1.0 : kStageW[stage]) * h->hdt;
   if (h->hl >= 1 && L.n_freg)
     k_amr_reg<<<nblk(L.n_freg), TPB, 0, h->st>>>(L.d_freg, L.n_freg, h->F, L.c->Fx, L.c->NFX, L.c->Fy, L.c->NFY,
                                                   wdt, L.d_T);
@@ -828,8 +832,14 @@ int dis_amr_create(int dim, const dis_patch* domain, int reactive_material, cons
                    const dis_amr_options* a, void* stream, dis_amr** out) {
   if (!out || !domain || !opt || !a) return AFAIL(DIS_EINVAL, "dis_amr_create: NULL argument");
   *out = nullptr;
-  if (opt->precision != DIS_FP64 || opt->scheme != DIS_RK3 || opt->geometry != DIS_PLANAR)
-    return AFAIL(DIS_EINVAL, "dis_amr_create: the hierarchy is built for float64 SSP-RK3 in planar geometry");
+  if (opt->precision != DIS_FP64 || (opt->scheme != DIS_RK3 && opt->scheme != DIS_HANCOCK) ||
+      (opt->geometry != DIS_PLANAR && opt->geometry != DIS_CYLINDRICAL) ||
+      (opt->scheme == DIS_HANCOCK && opt->geometry != DIS_PLANAR))
+    return AFAIL(DIS_EINVAL,
+                 "dis_amr_create: the hierarchy is built for float64 SSP-RK3 (planar or cylindrical) and float64 "
+                 "MUSCL-Hancock (planar)");
+  if (opt->geometry == DIS_CYLINDRICAL && !(domain->x0 >= 0.0))
+    return AFAIL(DIS_EINVAL, "dis_amr_create: cylindrical domain with x0 %g < 0 (a radius)", domain->x0);
   if (a->max_levels < 1 || a->max_levels > 4) return AFAIL(DIS_EINVAL, "dis_amr_create: max_levels in 1..4");
   if (a->block < 4) return AFAIL(DIS_EINVAL, "dis_amr_create: block must be >= 4");
   if (domain->nx % a->block || (dim == 2 && domain->ny % a->block))

@@ -903,9 +903,11 @@ int dis_internal_ensure_ws(dis_ctx* c) { return ensure_ws(c); }
 
 int dis_internal_steps(dis_ctx* c, int n, bool fixed) { return dispatch_steps(c, n, fixed); }
 
-// One float64 Runge-Kutta step with the per-patch dt of c->dtfix, calling
+// One float64 step with the per-patch dt of c->dtfix, calling
 // h.before(stage, source state) before each stage's recovery and
-// h.after_flux(stage) after its flux kernels (all on c->stream).
+// h.after_flux(stage) after its flux kernels (all on c->stream): three
+// Runge-Kutta stages, or the one stage (stage 0) of the MUSCL-Hancock
+// update, in place.
 namespace {
 template <int DIM, bool RX>
 void step64_hooked(dis_ctx* c, const StepHooks& h) {
@@ -915,6 +917,22 @@ void step64_hooked(dis_ctx* c, const StepHooks& h) {
   const double cb[3] = {1.0, 0.25, 2.0 / 3.0};
   const unsigned np = (unsigned)c->seg_prim.size(), nfx = (unsigned)c->seg_fx.size(),
                  nfy = (unsigned)c->seg_fy.size(), nc = (unsigned)c->seg_cell.size();
+  if (c->hancock) {
+    a.qsrc = c->q[0];
+    a.qn = c->q[0];
+    a.qdst = c->q[0];
+    a.a = 0.0;
+    a.b = 1.0;
+    a.last = 1;
+    if (h.before) h.before(h.user, 0, c->q[0]);
+    k_prim<DIM, RX><<<np, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_prim, 0);
+    k_hancock<DIM, RX><<<np, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_prim);
+    k_flux_h<DIM, RX, 0><<<nfx, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_fx);
+    if constexpr (DIM == 2) k_flux_h<DIM, RX, 1><<<nfy, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_fy);
+    if (h.after_flux) h.after_flux(h.user, 0);
+    k_update<DIM, RX><<<nc, SEG, 0, c->stream>>>(c->phys, a, c->d_seg_cell);
+    return;
+  }
   for (int stg = 0; stg < 3; ++stg) {
     a.qsrc = stg == 0 ? c->q[0] : c->q[1];
     a.qn = c->q[0];

@@ -300,7 +300,9 @@ class Solver:
 
 class AmrSolver:
     """The structured AMR hierarchy of include/dis.h (dis_amr_*) over the
-    domain of a one-patch workload; float64 SSP-RK3, planar."""
+    domain of a one-patch workload, float64: the workload's scheme (SSP-RK3,
+    or MUSCL-Hancock in planar geometry) and geometry (planar or
+    cylindrical)."""
 
     def __init__(self, wl, max_levels=2, block=8, eps=0.1, buffer=2, u_floor=1.0, regrid_every=4,
                  device=None):
@@ -317,7 +319,9 @@ class AmrSolver:
         self.reactive = wl.reactive_material >= 0
         self.nf = (11 if wl.dim == 2 else 8) + (1 if self.reactive else 0)
         self.stream = torch.cuda.current_stream(dev)
-        opts = L.DisOptions(float(wl.cfl), int(bool(wl.thinc)), L.DIS_FP64, L.DIS_RK3, L.DIS_PLANAR,
+        geo = {"planar": L.DIS_PLANAR, "cyl": L.DIS_CYLINDRICAL}[getattr(wl, "geometry", "planar")]
+        sch = {"rk3": L.DIS_RK3, "hancock": L.DIS_HANCOCK}[getattr(wl, "scheme", "rk3")]
+        opts = L.DisOptions(float(wl.cfl), int(bool(wl.thinc)), L.DIS_FP64, sch, geo,
                             {"minmod": L.DIS_MINMOD, "vanleer": L.DIS_VANLEER}[getattr(wl, "limiter", "minmod")])
         aopt = L.DisAmrOptions(int(max_levels), int(block), float(eps), int(buffer), float(u_floor),
                                int(regrid_every))

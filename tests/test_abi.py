@@ -174,8 +174,9 @@ def test_johnson_cook_validation(lib):
 
 
 def test_amr_create_validates_arguments(lib):
-    """dis_amr_create: float64 SSP-RK3 planar only, levels 1..4, block >= 4
-    dividing the domain, known boundary kinds (no device work here)."""
+    """dis_amr_create: float64, SSP-RK3 (planar or cylindrical with x0 >= 0)
+    or MUSCL-Hancock (planar), levels 1..4, block >= 4 dividing the domain,
+    known boundary kinds (no device work here)."""
     out = ctypes.c_void_p()
     dom = L.DisPatch(64, 1, 1.0 / 64, 1.0, (ctypes.c_int32 * 4)(0, 0, 0, 0))
     opts = L.DisOptions(0.8, 0, L.DIS_FP64, L.DIS_RK3)
@@ -188,10 +189,24 @@ def test_amr_create_validates_arguments(lib):
                 L.DisAmrOptions(2, 8, 0.1, -1, 1.0, 4)):
         assert lib.dis_amr_create(1, ctypes.byref(dom), -1, ctypes.byref(opts), ctypes.byref(bad), None,
                                   ctypes.byref(out)) == L.DIS_EINVAL
-    for o in (L.DisOptions(0.8, 0, L.DIS_FP32_BULK, L.DIS_RK3), L.DisOptions(0.8, 0, L.DIS_FP64, L.DIS_HANCOCK),
-              L.DisOptions(0.8, 0, L.DIS_FP64, L.DIS_RK3, L.DIS_CYLINDRICAL)):
+    hk = L.DisOptions(0.8, 0, L.DIS_FP64, L.DIS_HANCOCK)
+    assert lib.dis_amr_create(1, ctypes.byref(dom), -1, ctypes.byref(hk), ctypes.byref(ok), None,
+                              ctypes.byref(out)) == L.DIS_OK
+    lib.dis_amr_destroy(out)
+    for o in (L.DisOptions(0.8, 0, L.DIS_FP32_BULK, L.DIS_RK3), L.DisOptions(0.8, 0, L.DIS_FP64, 5),
+              L.DisOptions(0.8, 0, L.DIS_FP64, L.DIS_RK3, 7),
+              L.DisOptions(0.8, 0, L.DIS_FP64, L.DIS_HANCOCK, L.DIS_CYLINDRICAL)):
         assert lib.dis_amr_create(1, ctypes.byref(dom), -1, ctypes.byref(o), ctypes.byref(ok), None,
                                   ctypes.byref(out)) == L.DIS_EINVAL
+    cyl = L.DisOptions(0.8, 0, L.DIS_FP64, L.DIS_RK3, L.DIS_CYLINDRICAL)
+    axis = L.DisPatch(64, 1, 1.0 / 64, 1.0, (ctypes.c_int32 * 4)(L.DIS_BC_REFLECTIVE, 0, 0, 0), 0.0)
+    assert lib.dis_amr_create(1, ctypes.byref(axis), -1, ctypes.byref(cyl), ctypes.byref(ok), None,
+                              ctypes.byref(out)) == L.DIS_OK
+    lib.dis_amr_destroy(out)
+    neg = L.DisPatch(64, 1, 1.0 / 64, 1.0, (ctypes.c_int32 * 4)(0, 0, 0, 0), -0.5)
+    assert lib.dis_amr_create(1, ctypes.byref(neg), -1, ctypes.byref(cyl), ctypes.byref(ok), None,
+                              ctypes.byref(out)) == L.DIS_EINVAL
+    assert b"radius" in lib.dis_last_error()
     ext = L.DisPatch(64, 1, 1.0 / 64, 1.0, (ctypes.c_int32 * 4)(L.DIS_BC_EXTERNAL, 0, 0, 0))
     assert lib.dis_amr_create(1, ctypes.byref(ext), -1, ctypes.byref(opts), ctypes.byref(ok), None,
                               ctypes.byref(out)) == L.DIS_EINVAL
