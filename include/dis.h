@@ -383,11 +383,14 @@ int dis_step_timed(dis_ctx* ctx, int n_steps, double* kernel_ms);
  * float64 (plus float64 primitive and face buffers for the reverse sweep).
  * In a DIS_CYLINDRICAL context the geometric source of Section 3 is reversed
  * with the rest of the stage, and J is the same plain sum over cells (no
- * factor r).  Both limiters are reversed.  Returns DIS_EINVAL (bad
- * arguments, a DIS_HANCOCK context: the adjoint covers the Runge-Kutta
- * scheme, a material that is not a stiffened gas, a Johnson-Cook material,
- * or a reactive material with a product closure of its own), DIS_ESTATE
- * (no state), DIS_ENOMEM, DIS_ECUDA.
+ * factor r).  Both limiters are reversed.  Stiffened-gas contexts reverse
+ * every local map by hand; a context with a Romenskii material (Section
+ * 2.3) reverses them by dual-number evaluation of the forward closure code
+ * (planar geometry only; its G is G_0, and its yield strain follows G(rho)).
+ * Returns DIS_EINVAL (bad arguments, a DIS_HANCOCK context: the adjoint
+ * covers the Runge-Kutta scheme, a JWL or Johnson-Cook material, a reactive
+ * material with a product closure of its own, or a Romenskii material in
+ * cylindrical geometry), DIS_ESTATE (no state), DIS_ENOMEM, DIS_ECUDA.
  * Synchronises. */
 int dis_adj_forward(dis_ctx* ctx, int n_steps, int checkpoint_every, int objective_material,
                     const double* dt_in, double* dt_out, double* J_out);

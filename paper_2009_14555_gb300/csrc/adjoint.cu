@@ -305,7 +305,12 @@ void reverse_stage(dis_ctx* c, const double* x, const double* opre, double a_, d
   A.last = last;
   A.first = first;
   A.pmask = pmask;
-  if (d->dual_riemann) reverse_kernels<DIM, RX, true>(c, A);
+  // A material that is not a stiffened gas (the adjoint admits the
+  // Romenskii solid): the hand-written reverses of the local maps cover the
+  // stiffened gas only, so such contexts reverse every local map (recovery,
+  // face states and Riemann problem, THINC-BVD edge values, source steps) by
+  // its dual-number form, which evaluates the family's forward closure code.
+  if (d->dual_riemann || general_closures(c)) reverse_kernels<DIM, RX, true>(c, A);
   else reverse_kernels<DIM, RX, false>(c, A);
 }
 
@@ -380,10 +385,18 @@ int dis_adj_forward(dis_ctx* c, int n_steps, int checkpoint_every, int objective
   if (!c->have_state) return dis_internal_error(DIS_ESTATE, "dis_adj_forward: no state loaded");
   if (c->hancock)
     return dis_internal_error(DIS_EINVAL, "dis_adj_forward: the adjoint covers the Runge-Kutta scheme only");
-  if (c->phys.m[0].eos != EOS_SG || c->phys.m[1].eos != EOS_SG || c->phys.m[0].two || c->phys.m[1].two)
-    return dis_internal_error(DIS_EINVAL, "dis_adj_forward: the adjoint covers stiffened-gas materials only");
+  if (c->phys.m[0].two || c->phys.m[1].two)
+    return dis_internal_error(DIS_EINVAL,
+                              "dis_adj_forward: the adjoint does not cover two-closure reactive materials");
   if (c->phys.m[0].plastic == 3 || c->phys.m[1].plastic == 3)
     return dis_internal_error(DIS_EINVAL, "dis_adj_forward: the adjoint does not cover Johnson-Cook plasticity");
+  for (int l = 0; l < 2; ++l)
+    if (c->phys.m[l].eos != EOS_SG && c->phys.m[l].eos != EOS_ROMENSKII)
+      return dis_internal_error(DIS_EINVAL, "dis_adj_forward: the adjoint does not cover JWL materials");
+  if (general_closures(c) && c->phys.cyl)
+    return dis_internal_error(DIS_EINVAL,
+                              "dis_adj_forward: the adjoint of Romenskii materials is built for planar geometry "
+                              "only");
   if (n_steps <= 0 || checkpoint_every <= 0)
     return dis_internal_error(DIS_EINVAL, "dis_adj_forward: n_steps and checkpoint_every must be positive");
   if (objective_material < -1 || objective_material > 1)

@@ -213,6 +213,42 @@ def test_adjoint_cylindrical_2d_vs_oracle():
     _case("2d_sphere_shock_rz_40_4", wl, 4, material=0, qbar_seed=10)
 
 
+def _romenskii_copper(wl, seed):
+    """Romenskii copper (the Section 4.1 table) with perfect plasticity at
+    sigma_y = 0.4 GPa in place of material 0, perturbed."""
+    wl.materials = [dict(W.COPPER_ROMENSKII, plastic=1, sigma_y=0.4e9), W.AIR]
+    k = W.prim_names(wl.dim, wl.reactive).index("rho1")
+    for p in wl.patches:
+        p.prim[k] = 8930.0
+    return W.perturbed(wl, seed=seed)
+
+
+def test_adjoint_romenskii_1d_vs_oracle():
+    """Romenskii copper striking air at 500 m/s: the local maps reversed by
+    dual numbers through the Romenskii closure (G(rho) = G_0 (rho/rho_0)^(b+1)
+    in the stress, the sound speed and the yield strain); parameters G_0 and
+    sigma_y of the copper."""
+    wl = _romenskii_copper(W.riemann_1d(100, dict(mat=0, rho=8930.0, u=500.0, p=1e5),
+                                        dict(mat=1, rho=1.2, u=0.0, p=1e5),
+                                        materials=[W.COPPER_ROMENSKII, W.AIR], steps=10), seed=31)
+    _case("1d_romenskii_copper_air_100_10", wl, 10, material=0, qbar_seed=11, params=(0, 1))
+
+
+def test_adjoint_romenskii_detonation_vs_oracle():
+    """The k sqrt(lam) detonation driven into Romenskii copper (the Section
+    4.1 closures but for the explosive's single closure): reaction and
+    Romenskii solid in one reversed step."""
+    wl = W.perturbed(W.detonation_copper_1d(100, steps=8, copper="romenskii", explosive="standin"))
+    wl.materials[1]["A"] = 2e5
+    _case("1d_detonation_romenskii_100_8", wl, 8, material=1, qbar_seed=13, params=(5,))
+
+
+def test_adjoint_romenskii_2d_vs_oracle():
+    """A Romenskii copper disc struck by the Mach-2 air shock (2D)."""
+    wl = _romenskii_copper(W.shock_disc_2d(20, steps=4, thinc=False, shock_x=0.28), seed=32)
+    _case("2d_romenskii_disc_20_4", wl, 4, material=0, qbar_seed=12, params=(0, 1))
+
+
 def test_adjoint_smooth_vs_oracle():
     wl = W.perturbed(W.smooth_disc_2d(n=16, steps=8, sigma_y=4e7))
     _case("2d_smooth_disc_16_8", wl, 8, material=0)

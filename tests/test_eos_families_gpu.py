@@ -77,14 +77,19 @@ def test_eos_families_hancock_fp64():
     assert_parity(wl, 40, name="1d_romenskii_copper_air_hancock_300_40")
 
 
-def test_adjoint_refuses_other_families():
+def test_adjoint_refuses_jwl_and_cylindrical_romenskii():
+    """The adjoint covers Romenskii solids in planar geometry (their reverse
+    by dual numbers, tests/test_adjoint_gpu.py); JWL materials and
+    cylindrical Romenskii contexts are refused."""
     from paper_2009_14555_gb300.solver import Solver
-    wl = _copper_air_1d(64, 2)
-    s = Solver.from_workload(wl)
-    s.set_prim([wl.patches[0].prim])
-    with pytest.raises(RuntimeError):
-        s.adj_forward(2, every=1, material=0)
-    s.close()
+    for wl in (_jwl_air_1d(64, 2), _copper_air_1d(64, 2)):
+        if wl.materials[0] is CU:
+            wl.geometry = "cyl"
+        s = Solver.from_workload(wl)
+        s.set_prim([wl.patches[0].prim])
+        with pytest.raises(RuntimeError):
+            s.adj_forward(2, every=1, material=0)
+        s.close()
 
 
 def test_no_alloc_cfl_dt_on_romenskii_state():
