@@ -90,3 +90,33 @@ def test_oracle_perfect_plasticity_is_radial_return():
     b = OS.plastic_update(q, mats_rate, dt, iters=200)
     assert torch.allclose(a["V"], b["V"], rtol=1e-13, atol=1e-14)
     assert not torch.allclose(a["V"], V)  # the state yielded
+
+
+def test_oracle_reverse_mode_vs_fd_romenskii():
+    """The same pin with the solid on the Romenskii form (Section 2.3:
+    G(rho) = G_0 (rho / rho_0)^(beta + 1) in the stress, the sound speed and
+    the yield strain): state direction, G_0 and sigma_y of the solid.  This
+    is the reference of the GPU adjoint of Romenskii contexts."""
+    wl = W.smooth_disc_2d(n=10, steps=4, sigma_y=4e7)
+    cu = dict(W.COPPER_ROMENSKII, plastic=1, sigma_y=4e7)
+    wl.materials = [cu, wl.materials[1]]
+    k = {n: i for i, n in enumerate(W.prim_names(2, False))}
+    p = wl.patches[0]
+    p.prim[k["rho1"]] *= cu["rho0"] / W.SOLID_RHO0
+    gw, gth, J_at, w0, th0 = _grads(wl, 4, 0)
+    assert torch.isfinite(gw).all() and torch.isfinite(gth).all()
+    d = torch.zeros_like(w0)
+    d[k["rho1"]] = w0[k["rho1"]] * torch.linspace(-1, 1, 100, dtype=torch.float64).reshape(10, 10)
+    d[k["u"]] = 10.0
+    d[k["p"]] = 1e3
+    eps = 1e-6
+    fd = (J_at(w0 + eps * d, th0) - J_at(w0 - eps * d, th0)) / (2 * eps)
+    an = float((gw * d).sum())
+    assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
+    for kk in (0, 1):  # G_0 and yield stress of the copper
+        assert float(gth[kk]) != 0.0
+        h = 1e-5 * float(th0[kk])
+        e = torch.zeros_like(th0)
+        e[kk] = h
+        fdk = (J_at(w0, th0 + e) - J_at(w0, th0 - e)) / (2 * h)
+        assert abs(fdk - float(gth[kk])) <= 1e-6 * abs(float(gth[kk])), (kk, fdk, float(gth[kk]))
