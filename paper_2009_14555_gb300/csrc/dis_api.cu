@@ -232,7 +232,10 @@ int ensure_ws(dis_ctx* c) {
   if (!c->ws) {
     const size_t need = carve(c, nullptr);
     void* p = nullptr;
-    CU(cudaMalloc(&p, need));
+    if (cudaMalloc(&p, need) != cudaSuccess) {
+      const cudaError_t e = cudaGetLastError();
+      return fail(DIS_ENOMEM, "workspace: cannot allocate %zu bytes (%s)", need, cudaGetErrorString(e));
+    }
     c->ws = (char*)p;
     c->ws_bytes = need;
     c->ws_owned = true;

@@ -226,3 +226,34 @@ def test_amr_solver_refuses_without_a_gpu():
     from paper_2009_14555_gb300.solver import AmrSolver
     with pytest.raises(RuntimeError):
         AmrSolver(W.solid_gas_1d(64, steps=1))
+
+
+def test_allocation_and_workspace_failures_are_reported(lib):
+    """Fault injection on the host: a caller's workspace one byte too small
+    (DIS_ENOMEM), a misaligned one (DIS_EINVAL), and a failed device
+    allocation (the machine without a GPU makes cudaMalloc fail: DIS_ENOMEM
+    with the CUDA text).  The context stays usable: nothing was loaded, a
+    step is refused as out of order, and it is destroyed cleanly."""
+    import numpy as np
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present: the device allocation would succeed")
+    out = ctypes.c_void_p()
+    opts = L.DisOptions(0.8, 0, 0)
+    arr = (L.DisPatch * 1)(_patch(64))
+    assert lib.dis_create(1, 1, arr, -1, ctypes.byref(opts), None, ctypes.byref(out)) == L.DIS_OK
+    ctx = out
+    gas = L.DisMaterial(1.4, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0)
+    assert lib.dis_set_materials(ctx, (L.DisMaterial * 2)(gas, gas), 2) == L.DIS_OK
+    need = lib.dis_workspace_bytes(ctx)
+    # the pointers are never dereferenced: the size and alignment checks come first
+    assert lib.dis_bind_workspace(ctx, ctypes.c_void_p(1 << 20), need - 1) == L.DIS_ENOMEM
+    assert b"needed" in lib.dis_last_error()
+    assert lib.dis_bind_workspace(ctx, ctypes.c_void_p((1 << 20) + 8), need) == L.DIS_EINVAL
+    prim = np.zeros((8, 1, 64))
+    prim[0], prim[1], prim[2], prim[4] = 0.5, 1.2, 1.2, 1e5
+    prim[5:8] = 1.0
+    assert lib.dis_set_state(ctx, L.DIS_PRIMITIVE, ctypes.c_void_p(prim.ctypes.data), 0) == L.DIS_ENOMEM
+    assert b"cannot allocate" in lib.dis_last_error()
+    assert lib.dis_step(ctx, 1, None) == L.DIS_ESTATE
+    lib.dis_destroy(ctx)
