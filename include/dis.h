@@ -46,7 +46,8 @@ enum {
   DIS_EINVAL = -1,       /* bad argument; nothing was changed */
   DIS_ENOMEM = -2,       /* workspace missing or too small, or allocation failed */
   DIS_ECUDA = -3,        /* a CUDA runtime call failed (text in dis_last_error) */
-  DIS_ENONPHYSICAL = -4, /* a step produced a non-finite value or phi outside [-1e-6, 1+1e-6] */
+  DIS_ENONPHYSICAL = -4, /* a step met a state without a real sound speed or positive density, or
+                            produced a non-finite value or phi outside [-1e-6, 1+1e-6] */
   DIS_ESTATE = -5        /* call out of order (e.g. step before set_state) */
 };
 
