@@ -670,10 +670,10 @@ def batch_bench(steps=300, warmup=3):
     return out
 
 
-def cpu_baseline(budget_s=15.0, steps=None, nx=256, ny=128):
-    """The float64 CPU oracle on a bounded sample of the same workload (the
-    reactive plate on an nx x ny grid)."""
-    import torch
+def _oracle_rate(budget_s, steps, nx, ny):
+    """Cell-updates/s of the float64 CPU oracle stepping the reactive plate on
+    an nx x ny grid: `steps` steps, or as many as fit in budget_s (at least
+    one); returns (rate, steps, seconds)."""
     from oracle import scheme as OS
     from oracle import closures as OC
     wl = workload(nx, ny)
@@ -688,10 +688,29 @@ def cpu_baseline(budget_s=15.0, steps=None, nx=256, ny=128):
         el = time.perf_counter() - t0
         if (steps is not None and n >= steps) or (steps is None and el > budget_s):
             break
-    return {"value": nx * ny * n / el, "unit": UNIT, "cores": torch.get_num_threads(),
-            "kind": "oracle",
-            "sample": f"{n} steps of the reactive plate at {nx}x{ny} (same physics, smaller grid)",
-            "seconds": el}
+    return nx * ny * n / el, n, el
+
+
+def cpu_baseline(budget_s=15.0, steps=None, nx=256, ny=128, single_core_s=5.0):
+    """The float64 CPU oracle on a bounded sample of the same workload (the
+    reactive plate on an nx x ny grid) with all host threads, and (unless
+    single_core_s is None) on one thread on a quarter of that grid."""
+    import torch
+    rate, n, el = _oracle_rate(budget_s, steps, nx, ny)
+    out = {"value": rate, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+           "sample": f"{n} steps of the reactive plate at {nx}x{ny} (same physics, smaller grid)",
+           "seconds": el}
+    if single_core_s is None:
+        return out
+    threads = torch.get_num_threads()
+    torch.set_num_threads(1)
+    try:
+        r1, n1, el1 = _oracle_rate(single_core_s, None if steps is None else 1, nx // 2, ny // 2)
+    finally:
+        torch.set_num_threads(threads)
+    out["single_core"] = {"value": r1, "unit": UNIT, "cores": 1,
+                          "sample": f"{n1} steps of the reactive plate at {nx // 2}x{ny // 2}", "seconds": el1}
+    return out
 
 
 def run_reference(args):
@@ -704,8 +723,8 @@ def run_reference(args):
     ny = int(max(8, min(128, np.sqrt(6.0e3 * per_step_s / 2.0))))
     nx = 2 * ny
     for _ in range(args.warmup):
-        cpu_baseline(steps=1, nx=nx, ny=ny)
-    res = cpu_baseline(steps=max(1, args.steps), nx=nx, ny=ny)
+        cpu_baseline(steps=1, nx=nx, ny=ny, single_core_s=None)
+    res = cpu_baseline(steps=max(1, args.steps), nx=nx, ny=ny, single_core_s=None)
     line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": res["seconds"] / max(1, args.steps) * 1e3, "higher_is_better": True,
