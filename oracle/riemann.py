@@ -153,8 +153,16 @@ def hllc(wL, wR, d, mats):
     # shear waves in the star regions
     rsL = QsL["ar1"] + QsL["ar2"]
     rsR = QsR["ar1"] + QsR["ar2"]
-    csL = torch.sqrt(L["Gm"] / rsL)
-    csR = torch.sqrt(R["Gm"] / rsR)
+    # shear wave speeds sqrt(G_mix / rho*); a face between fluids has
+    # G_mix = 0, where they vanish and the solver drops the shear waves (the
+    # sqrt is taken on a stand-in there so that the reverse mode, whose
+    # derivative of sqrt at 0 is unbounded, stays finite; values unchanged)
+    def shear_speed(G, r):
+        pos = G > 0
+        return torch.where(pos, torch.sqrt(torch.where(pos, G / r, torch.ones_like(r))), torch.zeros_like(r))
+
+    csL = shear_speed(L["Gm"], rsL)
+    csR = shear_speed(R["Gm"], rsR)
     ZL, ZR = rsL * csL, rsR * csR
     SsL, SsR = Sst - csL, Sst + csR
     tmask = torch.ones(3, dtype=unL.dtype)

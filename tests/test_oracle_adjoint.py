@@ -120,3 +120,22 @@ def test_oracle_reverse_mode_vs_fd_romenskii():
         e[kk] = h
         fdk = (J_at(w0, th0 + e) - J_at(w0, th0 - e)) / (2 * h)
         assert abs(fdk - float(gth[kk])) <= 1e-6 * abs(float(gth[kk])), (kk, fdk, float(gth[kk]))
+
+
+def test_oracle_reverse_mode_vs_fd_two_fluids():
+    """Two fluids (LX-17 reactant on its JWL form expanding into air): the
+    mixture shear modulus is zero at every face, where the HLLD-type solver
+    drops its shear waves; the reverse mode stays finite there and matches
+    central differences along a state direction."""
+    wl = W.perturbed(W.riemann_1d(40, dict(mat=0, rho=1905.0, u=0.0, p=1e9), dict(mat=1, rho=1.2, u=0.0, p=1e5),
+                                  materials=[W.LX17_REACTANT_JWL, W.AIR], steps=3), seed=33)
+    gw, gth, J_at, w0, th0 = _grads(wl, 3, 0)
+    assert torch.isfinite(gw).all() and torch.isfinite(gth).all()
+    k = {n: i for i, n in enumerate(W.prim_names(1, False))}
+    d = torch.zeros_like(w0)
+    d[k["rho1"]] = w0[k["rho1"]] * torch.linspace(-1, 1, 40, dtype=torch.float64).reshape(1, 40)
+    d[k["p"]] = 1e5
+    eps = 1e-6
+    fd = (J_at(w0 + eps * d, th0) - J_at(w0 - eps * d, th0)) / (2 * eps)
+    an = float((gw * d).sum())
+    assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
