@@ -154,12 +154,15 @@ def hllc(wL, wR, d, mats):
     rsL = QsL["ar1"] + QsL["ar2"]
     rsR = QsR["ar1"] + QsR["ar2"]
     # shear wave speeds sqrt(G_mix / rho*); a face between fluids has
-    # G_mix = 0, where they vanish and the solver drops the shear waves (the
-    # sqrt is taken on a stand-in there so that the reverse mode, whose
-    # derivative of sqrt at 0 is unbounded, stays finite; values unchanged)
+    # G_mix = 0, where they vanish and the solver drops the shear waves.
+    # There the value is kept but not differentiated (the derivative of sqrt
+    # at 0 is unbounded and would turn the reverse mode's zero weights into
+    # NaN); every forward value is the plain sqrt(G_mix / rho*).
     def shear_speed(G, r):
-        pos = G > 0
-        return torch.where(pos, torch.sqrt(torch.where(pos, G / r, torch.ones_like(r))), torch.zeros_like(r))
+        zero = G == 0
+        exact = torch.sqrt(G / r).detach()
+        safe = torch.sqrt(torch.where(zero, torch.ones_like(r), G / r))
+        return torch.where(zero, exact, safe)
 
     csL = shear_speed(L["Gm"], rsL)
     csR = shear_speed(R["Gm"], rsR)
